@@ -1,0 +1,183 @@
+"""The Leja/Newton iteration for phi_k(hA)v and the two exponential steps.
+
+ORACLE — test infrastructure only (see oracle/__init__.py).
+
+Paper anchors: the exponential Euler method (Eq. (2)), matrix functions by
+polynomial interpolation at Leja points reduced to repeated products
+(alpha*A + beta*I)x (Eq. (3), Sec. II-C and Sec. III-C).  The loop below
+writes out the Newton form of that interpolant:
+
+    w_0 = r,  p_0 = d_0 w_0,
+    w_{j+1} = (A w_j)/gamma - (c/gamma + xi_j) w_j      (an Eq. (3) product)
+    p_{j+1} = p_j + d_{j+1} w_{j+1},
+    stop when |d_{j+1}| * ||w_{j+1}||_2 <= tol * ||p_{j+1}||_2,
+
+and, where s > 1 substeps are needed, integrates y' = A y + v from y = 0
+(y(h) = h phi_1(hA) v exactly):  y_{i+1} = y_i + tau * phi_1(tau A)(A y_i + v).
+Readings where the paper is silent: the tolerance applies per substep and is
+relative to ||p||; a substep that reaches m_max without meeting it doubles s
+and restarts; ||v|| = 0 returns 0; gamma = 0 (A = cI) returns phi_k(hc) v.
+"""
+from __future__ import annotations
+
+from dataclasses import dataclass, field
+
+import numpy as np
+
+from . import leja as L
+from .operators import ShiftedOperator
+
+NONLIN_NONE = 0
+NONLIN_LOGISTIC = 1
+
+
+class NotConverged(RuntimeError):
+    pass
+
+
+@dataclass
+class Stats:
+    alpha: float = 0.0
+    beta: float = 0.0
+    s: int = 1
+    degrees: list = field(default_factory=list)   # Newton degree per substep (final attempt)
+    matvecs: int = 0
+    restarts: int = 0
+    m_sched: int = 0
+
+
+def _norm(x):
+    return float(np.sqrt(np.sum(x * x)))
+
+
+def newton_phi(op, r, d, xi, c, gamma, tol, m_max, stats):
+    """p ~= phi_k(tau A) r for the divided differences d of phi_k(tau*(c+gamma*xi)).
+    Returns (p, degree, converged)."""
+    if _norm(r) == 0.0:
+        return np.zeros_like(r), 0, True
+    w = r.copy()
+    p = d[0] * w
+    for j in range(m_max):
+        shift = c / gamma + xi[j]
+        w = op.matvec(w) / gamma - shift * w
+        stats.matvecs += 1
+        p = p + d[j + 1] * w
+        if abs(d[j + 1]) * _norm(w) <= tol * _norm(p):
+            return p, j + 1, True
+    return p, m_max, False
+
+
+def _interval(op):
+    alpha, beta = op.gershgorin()
+    return alpha, beta, 0.5 * (alpha + beta), 0.25 * (beta - alpha)
+
+
+def h_phi1_substeps(op, h, v, tol, stats, m_max=L.M_MAX, xi=None):
+    """y_s ~= h * phi_1(hA) v by s substeps of y' = A y + v from y = 0."""
+    alpha, beta, c, gamma = _interval(op)
+    stats.alpha, stats.beta = alpha, beta
+    v = np.asarray(v, dtype=np.float64).reshape(op.shape)
+    if _norm(v) == 0.0:
+        stats.s, stats.degrees = 1, [0]
+        return np.zeros_like(v)
+    if gamma == 0.0:
+        stats.s, stats.degrees = 1, [0]
+        return h * L.phi_scalar(1, h * c) * v
+    if xi is None:
+        xi = L.leja_points(m_max)
+    s, stats.m_sched, _ = L.plain_schedule(1, h, c, gamma, tol, xi, m_max)
+    while s <= L.S_MAX:
+        tau = h / s
+        d = L.divided_differences(1, tau, c, gamma, xi[: m_max + 1])
+        y = np.zeros_like(v)
+        degrees = []
+        ok = True
+        for i in range(s):
+            if i == 0:
+                r = v.copy()
+            else:
+                r = op.matvec(y) + v
+                stats.matvecs += 1
+            p, deg, conv = newton_phi(op, r, d, xi, c, gamma, tol, m_max, stats)
+            degrees.append(deg)
+            if not conv:
+                ok = False
+                break
+            y = y + tau * p
+        if ok:
+            stats.s, stats.degrees = s, degrees
+            return y
+        stats.restarts += 1
+        s *= 2
+    raise NotConverged("phi_1: no s <= S_MAX converged")
+
+
+def phi_apply(op, k, h, v, tol, m_max=L.M_MAX, xi=None):
+    """phi_k(hA) v.  k = 1: substepped ODE form; k = 0: (e^{tau A})^s v;
+    k >= 2: a single step (s = 1) or NotConverged.  Returns (result, Stats)."""
+    stats = Stats()
+    v = np.asarray(v, dtype=np.float64).reshape(op.shape)
+    if k == 1:
+        y = h_phi1_substeps(op, h, v, tol, stats, m_max, xi)
+        return y / h, stats
+    alpha, beta, c, gamma = _interval(op)
+    stats.alpha, stats.beta = alpha, beta
+    if _norm(v) == 0.0:
+        stats.degrees = [0]
+        return np.zeros_like(v), stats
+    if gamma == 0.0:
+        stats.degrees = [0]
+        return L.phi_scalar(k, h * c) * v, stats
+    if xi is None:
+        xi = L.leja_points(m_max)
+    s, stats.m_sched, _ = L.plain_schedule(k, h, c, gamma, tol, xi, m_max)
+    while s <= L.S_MAX:
+        if k >= 2 and s > 1:
+            raise NotConverged("phi_k, k >= 2, needs more than one substep")
+        tau = h / s
+        d = L.divided_differences(k, tau, c, gamma, xi[: m_max + 1])
+        y = v.copy()
+        degrees = []
+        ok = True
+        for _ in range(s):
+            y, deg, conv = newton_phi(op, y, d, xi, c, gamma, tol, m_max, stats)
+            degrees.append(deg)
+            if not conv:
+                ok = False
+                break
+        if ok:
+            stats.s, stats.degrees = s, degrees
+            return y, stats
+        stats.restarts += 1
+        s *= 2
+    raise NotConverged("phi_k: no s <= S_MAX converged")
+
+
+def nonlinearity(u, kind):
+    """g(u) and g'(u): none (0, 0) or logistic u(1-u), 1-2u."""
+    if kind == NONLIN_LOGISTIC:
+        return u * (1.0 - u), 1.0 - 2.0 * u
+    return np.zeros_like(u), np.zeros_like(u)
+
+
+def exp_euler_step(op, u, h, tol, nonlin=NONLIN_NONE, xi=None):
+    """Eq. (2) with A -> -A:  u_{n+1} = e^{hA}u_n + h phi_1(hA) g(u_n)
+    = u_n + h phi_1(hA)(A u_n + g(u_n))."""
+    stats = Stats()
+    u = np.asarray(u, dtype=np.float64).reshape(op.shape)
+    g, _ = nonlinearity(u, nonlin)
+    F = op.matvec(u) + g
+    stats.matvecs += 1
+    return u + h_phi1_substeps(op, h, F, tol, stats, xi=xi), stats
+
+
+def exp_rosenbrock_step(op, u, h, tol, nonlin=NONLIN_LOGISTIC, xi=None):
+    """Exponential Rosenbrock-Euler: J_n = A + diag(g'(u_n)),
+    u_{n+1} = u_n + h phi_1(h J_n)(A u_n + g(u_n))."""
+    stats = Stats()
+    u = np.asarray(u, dtype=np.float64).reshape(op.shape)
+    g, dg = nonlinearity(u, nonlin)
+    F = op.matvec(u) + g
+    stats.matvecs += 1
+    J = ShiftedOperator(op, dg)
+    return u + h_phi1_substeps(J, h, F, tol, stats, xi=xi), stats
