@@ -1,0 +1,182 @@
+/*
+ * ei.h — C ABI of the GB300 exponential-integrator library.
+ *
+ * The library computes the action phi_k(hA)v of the phi-functions of a large
+ * sparse matrix A by Newton interpolation at real Leja points on the
+ * Gershgorin interval of A, and takes exponential Euler and exponential
+ * Rosenbrock-Euler steps with it.  Paper: Einkemmer & Ostermann,
+ * "Exponential Integrators on Graphic Processing Units" (HPCS 2013):
+ *   - the semilinear problem and the exponential Euler method, Sec. II-C,
+ *     Eq. (1)-(2);
+ *   - matrix functions by polynomial interpolation on a bound of the field of
+ *     values, reduced by Horner's scheme to products (alpha*A + beta*I)x,
+ *     Sec. II-C, Eq. (3); interpolation at Leja points, Sec. III-C;
+ *   - stencil operators with boundary conditions and position-dependent
+ *     coefficients folded into the kernel, Sec. III-A and III-B;
+ *   - CSR operators for unstructured A, Sec. III-D.
+ *
+ * Sign convention: the library integrates u' = A u + g(u).  The paper writes
+ * u' + A_p u = g(u), i.e. A = -A_p; the spectrum of A lies in Re <= ~0.
+ *
+ * General rules for every call:
+ *   - Return codes only; nothing is thrown across the ABI.  A failed call
+ *     leaves every caller buffer it would have written unmodified and the
+ *     context usable.
+ *   - Vectors and coefficient arrays are DEVICE pointers on the context's
+ *     device, owned by the caller, contiguous, x fastest ([z][y][x]).  The
+ *     library keeps coefficient pointers by reference until the next
+ *     set_operator or ei_destroy and never frees them.  Workspaces are owned
+ *     by the library: allocated by set_operator, freed by ei_destroy.
+ *   - All device work is ordered on the context's CUDA stream.  Calls that
+ *     return results to the host (spectrum, stats) synchronise that stream.
+ *   - Element type of vectors and coefficient arrays follows the operator's
+ *     precision: EI_PREC_F64 -> double, EI_PREC_F32 -> float.
+ */
+#ifndef EI_H
+#define EI_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct ei_ctx ei_ctx; /* opaque, library-owned */
+
+typedef enum {
+  EI_OK = 0,
+  EI_ERR_INVALID_ARG = 1,   /* bad size, null pointer, k < 0, h <= 0, tol <= 0 ... */
+  EI_ERR_NONFINITE = 2,     /* NaN/Inf met in the input vector or the iteration */
+  EI_ERR_NOT_CONVERGED = 3, /* no substep count s <= 2^20 met tol (k >= 2: s > 1) */
+  EI_ERR_TIMEOUT = 4,       /* a bounded device wait ran out */
+  EI_ERR_CUDA = 5,          /* a CUDA runtime call failed */
+  EI_ERR_NOMEM = 6,         /* workspace allocation failed */
+  EI_ERR_STATE = 7          /* call out of order (e.g. phi_apply before set_operator) */
+} ei_status;
+
+/* Boundary condition per face (x-lo, x-hi, y-lo, y-hi, z-lo, z-hi),
+ * Sec. III-A: homogeneous conditions folded into the kernel.
+ *   DIRICHLET0: ghost value 0 one spacing outside the face (vertex-centred grids).
+ *   NEUMANN0:   ghost mirrors the boundary value (cell-centred grids): no
+ *               diffusive flux through the face, one-sided advection. */
+enum { EI_BC_DIRICHLET0 = 0, EI_BC_NEUMANN0 = 1 };
+
+/* Storage/arithmetic precision of vectors and of the matvec.
+ *   F64: vectors exchanged as double; inside the library the Newton vectors
+ *        are float-float pairs (48-bit significand) on the FP32 pipes.
+ *   F32: vectors and stencil matvec in float with float accumulation; the
+ *        divided differences, the spectral interval and the Newton sum p
+ *        (float-float) keep FP64-class precision. */
+enum { EI_PREC_F64 = 0, EI_PREC_F32 = 1 };
+
+/* Arithmetic of the F64 path (ei_options.arith). */
+enum { EI_ARITH_DF = 0, EI_ARITH_NATIVE_F64 = 1 };
+
+enum { EI_EXP_EULER = 0, EI_EXP_ROSENBROCK = 1 };
+enum { EI_NONLIN_NONE = 0, EI_NONLIN_LOGISTIC = 1 }; /* g = 0 | g = u(1-u) */
+
+typedef struct {
+  int m_max;      /* largest Newton degree per substep; 0 -> 100 (max 100) */
+  int arith;      /* EI_ARITH_*, F64 operators only; default EI_ARITH_DF */
+  int fixed_s;    /* > 0: use this substep count instead of the a-priori rule */
+  int reserved[5];
+} ei_options;
+
+#define EI_STATS_MAX_SUBSTEPS 64
+typedef struct {
+  double alpha, beta;   /* Gershgorin interval used */
+  int s;                /* substeps of the accepted attempt */
+  int restarts;         /* attempts rejected (m_max reached) before it */
+  int matvecs;          /* operator applications, all attempts */
+  int degree_sum;       /* sum of Newton degrees of the accepted attempt */
+  int degree_max;
+  int m_sched;          /* degree the a-priori rule predicted */
+  int degrees[EI_STATS_MAX_SUBSTEPS]; /* per substep, first 64 substeps */
+} ei_stats;
+
+/* Create a context on CUDA device `device`, ordering work on `cuda_stream`
+ * (a cudaStream_t; NULL = the legacy default stream).  *out receives the
+ * context; on error *out is NULL. */
+ei_status ei_create(ei_ctx** out, int device, void* cuda_stream);
+
+/* Destroy the context and free its workspaces (after a stream sync). */
+void ei_destroy(ei_ctx* ctx);
+
+/* Change the stream later calls are ordered on. */
+ei_status ei_set_stream(ei_ctx* ctx, void* cuda_stream);
+
+/* Stencil operator, Sec. III-A (seven-point formula) and III-B
+ * (position-dependent diffusion), conservative form:
+ *   (A u)_i = sum_e [ D_{i+e/2}(u_{i+e} - u_i) + D_{i-e/2}(u_{i-e} - u_i) ] / dx_e^2
+ *           + sum_e b_e,i (u_{i+e} - u_{i-e}) / (2 dx_e) + c_i u_i,
+ *   D_{i+e/2} = (D_i + D_{i+e}) / 2  (at a face, the ghost D is D_i).
+ * dim      2 or 3 (dim 2: n[2], dx[2], b[2], bc[4..5] are ignored).
+ * n        grid points per axis (x, y, z), each >= 1.
+ * dx       spacing per axis, > 0.
+ * D        device array of n0*n1*n2 values, or NULL to use D_const.
+ * b        three device arrays or NULLs; a NULL component uses b_const[e].
+ * c        device array or NULL to use c_const (a fixed diagonal term).
+ * bc       six face codes EI_BC_*.
+ * prec     EI_PREC_F64 (arrays of double) or EI_PREC_F32 (arrays of float).
+ * Allocates the library's workspaces (about 8 vectors of the grid size). */
+ei_status ei_set_operator_stencil(ei_ctx* ctx, int dim, const int64_t n[3], const double dx[3],
+                                  const void* D, double D_const, const void* const b[3],
+                                  const double b_const[3], const void* c, double c_const,
+                                  const int bc[6], int prec);
+
+/* Sparse operator in CSR, Sec. III-D: A = W + diag(diag).
+ * rowptr  int64[n+1] (device), col int32[nnz] (device), val[nnz] (device),
+ * diag    device array of n values or NULL (zero).  Entries with col == row
+ *         are allowed and count as diagonal.  prec as above. */
+ei_status ei_set_operator_csr(ei_ctx* ctx, int64_t n, int64_t nnz, const int64_t* rowptr,
+                              const int32_t* col, const void* val, const void* diag, int prec);
+
+/* Gershgorin interval of the operator (FP64):
+ *   alpha = min_i (a_ii - r_i),  beta = max_i (a_ii + r_i),  r_i = sum_{j!=i} |a_ij|.
+ * The paper assumes "a bound of the field of values ... known a priori"
+ * (Sec. II-C); this is that bound for the real-Leja method.  Host outputs. */
+ei_status ei_estimate_spectrum(ei_ctx* ctx, double* alpha, double* beta);
+
+/* out = phi_k(hA) v  (Eq. (2) for k = 1; phi_0 = exp).  v, out: device
+ * vectors of the operator's size and precision; they may alias.
+ * k = 1: substepped ODE form; k = 0: (e^{(h/s)A})^s v; k >= 2: one substep
+ * only (EI_ERR_NOT_CONVERGED if the a-priori rule asks for more).
+ * tol: relative stop tolerance of the a-posteriori estimate
+ *   |d_{j+1}| ||w_{j+1}||_2 <= tol ||p_{j+1}||_2, per substep.
+ * opt may be NULL (defaults).  stats may be NULL. */
+ei_status ei_phi_apply(ei_ctx* ctx, int k, double h, const void* v, void* out, double tol,
+                       const ei_options* opt, ei_stats* stats);
+
+/* One step of size h of u' = A u + g(u), in place on the device vector u.
+ * method EI_EXP_EULER:      u <- u + h phi_1(hA)(A u + g(u))          (Eq. (2))
+ * method EI_EXP_ROSENBROCK: u <- u + h phi_1(hJ)(A u + g(u)), J = A + diag(g'(u))
+ * nonlin EI_NONLIN_NONE (g = 0) or EI_NONLIN_LOGISTIC (g = u(1-u)). */
+ei_status ei_step(ei_ctx* ctx, int method, double h, void* u, int nonlin, double tol,
+                  const ei_options* opt, ei_stats* stats);
+
+/* ei_step on a HOST vector: copies u to the device, steps, copies it back,
+ * all on the context's stream (pinned host memory gives asynchronous copies).
+ * Returns after the copy back completed. */
+ei_status ei_step_host(ei_ctx* ctx, int method, double h, void* u_host, int nonlin, double tol,
+                       const ei_options* opt, ei_stats* stats);
+
+/* Host-side pieces of the method, exported for inspection and tests. */
+/* Leja points xi_0..xi_m on [-2,2]: xi_0 = 2, xi_j maximises prod_{i<j}|x - xi_i|,
+ * ties to the larger x.  out: host array of m+1 doubles, m <= 100. */
+ei_status ei_leja_points(int m, double* out);
+/* Divided differences d_j = f[xi_0..xi_j], f(xi) = phi_k(tau*c + tau*gamma*xi),
+ * j = 0..m (m <= 100), by Opitz's theorem: the first column of
+ * phi_k(tau*c*I + tau*gamma*Z), Z lower bidiagonal (diag xi, subdiag 1),
+ * evaluated by scaling and squaring on a shifted nonnegative matrix.  Host out. */
+ei_status ei_divided_differences(int k, double tau, double c, double gamma, int m, double* out);
+/* The a-priori substep rule: smallest s = 2^q such that some degree <= m_max
+ * meets max_G |f - p_m| <= tol max_G |f| on 2001 points G of [-2,2]. */
+ei_status ei_schedule(int k, double h, double c, double gamma, double tol, int m_max,
+                      int* s_out, int* m_out);
+
+const char* ei_status_string(ei_status st);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* EI_H */

@@ -17,7 +17,8 @@ mathematical definition:
     ties broken towards the larger x (a reading: the paper is silent);
   * Newton divided differences d_j = f[xi_0..xi_j] of
     f(xi) = phi_k(tau*c + tau*gamma*xi), computed here by the plain recurrence
-    in 120-digit decimal arithmetic;
+    in decimal arithmetic at a precision raised until it no longer changes
+    any entry;
   * the plain a-priori substep rule: the smallest s = 2^q for which the
     degree-<=m_max scalar interpolant meets max_G |f - p_m| <= tol*max_G |f|
     on 2001 equispaced points G of [-2, 2] (a reading of "conservative a
@@ -32,7 +33,8 @@ import numpy as np
 
 M_MAX = 100          # largest Newton degree per substep
 S_MAX = 2 ** 20      # largest number of substeps
-DEC_PREC = 120       # decimal digits for scalar phi and divided differences
+DEC_PREC = 120       # decimal digits for scalar phi (and the starting precision of the
+                     # divided differences)
 N_GRID = 2001        # points of G in the schedule rule
 TIE_LOG = 1e-12      # two Leja candidates tie when their log-products differ less
 
@@ -86,14 +88,14 @@ def leja_points(m: int = M_MAX) -> np.ndarray:
 # --------------------------------------------------------------------------
 # Scalar phi_k
 # --------------------------------------------------------------------------
-def phi_dec(k: int, z: Decimal) -> Decimal:
+def phi_dec(k: int, z: Decimal, prec: int = DEC_PREC) -> Decimal:
     """phi_k(z) = sum_{i>=0} z^i/(i+k)!  (phi_0 = exp), in the current
     decimal context.  Series for |z| < 1, else the recurrence
     phi_j(z) = (phi_{j-1}(z) - 1/(j-1)!)/z from phi_0 = exp(z)."""
     if abs(z) < 1:
         term = Decimal(1) / Decimal(math.factorial(k))
         total = term
-        eps = Decimal(10) ** (-(DEC_PREC + 10))
+        eps = Decimal(10) ** (-(prec + 10))
         i = 0
         while abs(term) > eps:
             term = term * z / (i + k + 1)
@@ -116,23 +118,38 @@ def phi_scalar(k: int, z: float) -> float:
 # --------------------------------------------------------------------------
 # Divided differences
 # --------------------------------------------------------------------------
+def _dd_at(k, tau, c, gamma, xi, prec):
+    with localcontext() as ctx:
+        ctx.prec = prec
+        T, C, G = Decimal(tau), Decimal(c), Decimal(gamma)
+        xs = [Decimal(float(x)) for x in xi]
+        tab = [phi_dec(k, T * C + T * G * x, prec) for x in xs]
+        n = len(xs)
+        for j in range(1, n):
+            for i in range(n - 1, j - 1, -1):
+                tab[i] = (tab[i] - tab[i - 1]) / (xs[i] - xs[i - j])
+        return tab
+
+
 def divided_differences(k: int, tau: float, c: float, gamma: float,
                         xi: np.ndarray) -> np.ndarray:
     """d_j = f[xi_0..xi_j] for f(xi) = phi_k(tau*c + tau*gamma*xi).
 
     Plain Newton recurrence f[x_i..x_j] = (f[x_{i+1}..x_j] - f[x_i..x_{j-1}])
-    / (x_j - x_i) in 120-digit decimal arithmetic; the inputs (doubles) are
-    converted exactly, the results rounded to doubles."""
-    with localcontext() as ctx:
-        ctx.prec = DEC_PREC
-        T, C, G = Decimal(tau), Decimal(c), Decimal(gamma)
-        xs = [Decimal(float(x)) for x in xi]
-        tab = [phi_dec(k, T * C + T * G * x) for x in xs]
-        n = len(xs)
-        for j in range(1, n):
-            for i in range(n - 1, j - 1, -1):
-                tab[i] = (tab[i] - tab[i - 1]) / (xs[i] - xs[i - j])
-        return np.array([float(t) for t in tab], dtype=np.float64)
+    / (x_j - x_i) in decimal arithmetic; the inputs (doubles) are converted
+    exactly.  The recurrence cancels about as many digits as the smallest d_j
+    is below max|f|, so it is run at a working precision P and again at P+64
+    digits, and P grows until every entry of the two runs agrees to 1e-20
+    relative; the results are rounded to doubles."""
+    prec = DEC_PREC
+    prev = _dd_at(k, tau, c, gamma, xi, prec)
+    while True:
+        nxt = _dd_at(k, tau, c, gamma, xi, prec + 64)
+        ok = all(abs(a - b) <= Decimal("1e-20") * abs(b) for a, b in zip(prev, nxt))
+        if ok or prec > 4000:
+            return np.array([float(t) for t in nxt], dtype=np.float64)
+        prec += 64
+        prev = nxt
 
 
 def newton_eval(d: np.ndarray, xi: np.ndarray, x: np.ndarray) -> np.ndarray:

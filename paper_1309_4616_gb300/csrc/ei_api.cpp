@@ -1,0 +1,683 @@
+// Host orchestration of the C ABI declared in include/ei.h.
+//
+// phi_k(hA)v by Newton interpolation at Leja points (Sec. II-C, Eq. (3);
+// Sec. III-C): the Gershgorin interval [alpha, beta] gives c and gamma; the
+// a-priori rule gives the substep count s; per substep the Newton loop is a
+// chain of fused kernel launches (one per degree) whose stop test runs on the
+// device, so the host launches a predicted batch and synchronises once per
+// substep to read the outcome.  Exponential Euler (Eq. (2)) and exponential
+// Rosenbrock-Euler integrate z' = J z + F from z = 0 by the same substeps.
+#include <cuda_runtime.h>
+#include <math.h>
+#include <stdio.h>
+#include <stdlib.h>
+#include <string.h>
+
+#include <vector>
+
+#include "ei.h"
+#include "ei_internal.h"
+
+namespace ei {
+const double* leja_table();
+void divided_differences(int k, double tau, double c, double gamma, int m, double* out);
+int schedule(int k, double h, double c, double gamma, double tol, int m_max, int* s_out,
+             int* m_out);
+double phi_scalar(int k, double z);
+}  // namespace ei
+
+using namespace ei;
+
+enum { KIND_NONE = 0, KIND_STENCIL = 1, KIND_CSR = 2 };
+
+// Operator data and workspaces in one vector format.
+struct Prepared {
+  bool ready = false;
+  int fmt = VF_DF;
+  void* D = nullptr;       // stencil: D / (2 dx_x^2)
+  void* B[3] = {nullptr, nullptr, nullptr};  // stencil: b_e / (2 dx_e)
+  void* cbase = nullptr;   // the fixed diagonal c_i (stencil) / diag (CSR)
+  void* qc = nullptr;      // per-step diagonal c_i + g'(u_i)
+  void* w[2] = {nullptr, nullptr};
+  void* p = nullptr;       // Newton sum (float-float or double)
+  void* y = nullptr;       // substep accumulator
+  void* r = nullptr;       // substep residual / k = 0 carry
+  void* v = nullptr;       // imported right-hand side / F
+  void* u = nullptr;       // imported state
+  void* csr_val = nullptr; // CSR values in the matvec precision
+};
+
+struct ei_ctx {
+  int device = 0;
+  cudaStream_t stream = nullptr;
+  int kind = KIND_NONE;
+  int prec = EI_PREC_F64;
+  int64_t n = 0;
+  // stencil description (caller's arrays are referenced, not copied)
+  StencilDev sd{};
+  double dx[3] = {1, 1, 1};
+  const void* Du = nullptr;
+  double Dc = 0;
+  const void* bu[3] = {nullptr, nullptr, nullptr};
+  double bcst[3] = {0, 0, 0};
+  const void* cu = nullptr;
+  double cc = 0;
+  // CSR description
+  CsrDev cd{};
+  int64_t nnz = 0;
+  const void* val_u = nullptr;
+  const void* diag_u = nullptr;
+  // Gershgorin rows of A (without the per-step g') and their interval
+  double* ger_lo = nullptr;
+  double* ger_hi = nullptr;
+  double alphaA = 0, betaA = 0;
+  // device control, reduction partials, pinned mirror
+  DevCtl* ctl = nullptr;
+  DevCtl* h_ctl = nullptr;
+  double* partials = nullptr;
+  int max_blocks = 0;
+  Prepared prep[3];
+  // staging for ei_step_host
+  void* host_stage = nullptr;
+};
+
+#define EI_TRY_CUDA(expr)                        \
+  do {                                           \
+    cudaError_t e_ = (expr);                     \
+    if (e_ != cudaSuccess) {                     \
+      ei_log_cuda(e_, #expr, __LINE__);          \
+      return EI_ERR_CUDA;                        \
+    }                                            \
+  } while (0)
+
+#define EI_TRY(expr)                             \
+  do {                                           \
+    ei_status s_ = (expr);                       \
+    if (s_ != EI_OK) return s_;                  \
+  } while (0)
+
+static void ei_log_cuda(cudaError_t e, const char* what, int line) {
+  const char* lg = getenv("EI_LOG");
+  if (lg && *lg == '1') fprintf(stderr, "ei: CUDA error %s at %s (line %d)\n", cudaGetErrorString(e), what, line);
+}
+
+static bool log_on() {
+  const char* lg = getenv("EI_LOG");
+  return lg && *lg == '1';
+}
+
+static int vec_fmt_for(const ei_ctx* c, const ei_options* opt) {
+  if (c->prec == EI_PREC_F32) return VF_F32;
+  if (opt && opt->arith == EI_ARITH_NATIVE_F64) return VF_F64;
+  return VF_DF;
+}
+
+static void free_prepared(Prepared& p) {
+  void** arrs[] = {&p.D, &p.B[0], &p.B[1], &p.B[2], &p.cbase, &p.qc, &p.w[0], &p.w[1],
+                   &p.p, &p.y, &p.r, &p.v, &p.u, &p.csr_val};
+  for (void** a : arrs) {
+    if (*a) cudaFree(*a);
+    *a = nullptr;
+  }
+  p.ready = false;
+}
+
+static void free_operator(ei_ctx* c) {
+  for (auto& p : c->prep) free_prepared(p);
+  if (c->ger_lo) cudaFree(c->ger_lo);
+  if (c->ger_hi) cudaFree(c->ger_hi);
+  if (c->partials) cudaFree(c->partials);
+  if (c->host_stage) cudaFree(c->host_stage);
+  c->ger_lo = c->ger_hi = nullptr;
+  c->partials = nullptr;
+  c->host_stage = nullptr;
+  c->max_blocks = 0;
+  c->kind = KIND_NONE;
+}
+
+static ei_status alloc(void** p, size_t bytes) {
+  if (bytes == 0) bytes = 16;
+  cudaError_t e = cudaMalloc(p, bytes);
+  if (e != cudaSuccess) {
+    cudaGetLastError();
+    *p = nullptr;
+    return e == cudaErrorMemoryAllocation ? EI_ERR_NOMEM : EI_ERR_CUDA;
+  }
+  return EI_OK;
+}
+
+// Build the operator arrays and workspaces of one vector format.
+static ei_status prepare(ei_ctx* c, int fmt) {
+  Prepared& P = c->prep[fmt];
+  if (P.ready) return EI_OK;
+  P.fmt = fmt;
+  const int64_t n = c->n;
+  const size_t vb = vec_elem_bytes(fmt) * (size_t)n, pb = p_elem_bytes(fmt) * (size_t)n;
+  ei_status s;
+  void** vecs[] = {&P.cbase, &P.qc, &P.w[0], &P.w[1], &P.y, &P.r, &P.v, &P.u};
+  for (void** a : vecs)
+    if ((s = alloc(a, vb)) != EI_OK) { free_prepared(P); return s; }
+  if ((s = alloc(&P.p, pb)) != EI_OK) { free_prepared(P); return s; }
+  if (c->kind == KIND_STENCIL) {
+    if ((s = alloc(&P.D, vb)) != EI_OK) { free_prepared(P); return s; }
+    for (int e = 0; e < 3; ++e)
+      if ((s = alloc(&P.B[e], vb)) != EI_OK) { free_prepared(P); return s; }
+    const double kx = 1.0 / (2.0 * c->dx[0] * c->dx[0]);
+    EI_TRY_CUDA(launch_fill_coef(P.D, fmt, n, c->Du, c->prec, c->Dc, kx, c->stream));
+    for (int e = 0; e < 3; ++e) {
+      const bool active = e < c->sd.dim;
+      EI_TRY_CUDA(launch_fill_coef(P.B[e], fmt, n, active ? c->bu[e] : nullptr, c->prec,
+                                   active ? c->bcst[e] : 0.0, 1.0 / (2.0 * c->dx[e]), c->stream));
+    }
+    EI_TRY_CUDA(launch_fill_coef(P.cbase, fmt, n, c->cu, c->prec, c->cc, 1.0, c->stream));
+  } else {
+    if ((s = alloc(&P.csr_val, vec_elem_bytes(fmt) * (size_t)c->nnz)) != EI_OK) { free_prepared(P); return s; }
+    EI_TRY_CUDA(launch_fill_coef(P.csr_val, fmt, c->nnz, c->val_u, c->prec, 0.0, 1.0, c->stream));
+    EI_TRY_CUDA(launch_fill_coef(P.cbase, fmt, n, c->diag_u, c->prec, 0.0, 1.0, c->stream));
+  }
+  P.ready = true;
+  return EI_OK;
+}
+
+static StencilDev stencil_view(const ei_ctx* c, const Prepared& P, const void* qc) {
+  StencilDev s = c->sd;
+  s.D = P.D;
+  for (int e = 0; e < 3; ++e) s.B[e] = P.B[e];
+  s.qc = qc;
+  return s;
+}
+
+static CsrDev csr_view(const ei_ctx* c, const Prepared& P, const void* qc) {
+  CsrDev d = c->cd;
+  d.val = P.csr_val;
+  d.qc = qc;
+  return d;
+}
+
+static ei_status read_ctl(ei_ctx* c) {
+  EI_TRY_CUDA(cudaMemcpyAsync(c->h_ctl, c->ctl, sizeof(DevCtl), cudaMemcpyDeviceToHost, c->stream));
+  EI_TRY_CUDA(cudaStreamSynchronize(c->stream));
+  return EI_OK;
+}
+
+static ei_status reset_done(ei_ctx* c) {
+  EI_TRY_CUDA(cudaMemsetAsync(&c->ctl->done, 0, 2 * sizeof(int), c->stream));
+  return EI_OK;
+}
+
+static cudaError_t op_residual(ei_ctx* c, Prepared& P, const void* qc, const void* y,
+                               const void* v, void* r) {
+  if (c->kind == KIND_STENCIL)
+    return launch_stencil_residual(stencil_view(c, P, qc), y, v, r, P.fmt, c->partials, c->ctl,
+                                   c->stream);
+  return launch_csr_residual(csr_view(c, P, qc), y, v, r, P.fmt, c->partials, c->ctl, c->stream);
+}
+
+static cudaError_t op_newton(ei_ctx* c, Prepared& P, const void* qc, const void* w_in,
+                             void* w_out, const NewtonScalars& s) {
+  if (c->kind == KIND_STENCIL)
+    return launch_stencil_newton(stencil_view(c, P, qc), w_in, w_out, P.p, s, P.fmt, c->partials,
+                                 c->ctl, c->stream);
+  return launch_csr_newton(csr_view(c, P, qc), w_in, w_out, P.p, s, P.fmt, c->partials, c->ctl,
+                           c->stream);
+}
+
+// One Newton loop on w_0 = r into P.p.  Returns the degree in *deg; *ok = 0
+// when m_max was reached without meeting tol.
+static ei_status newton_loop(ei_ctx* c, Prepared& P, const void* qc, const void* r,
+                             const std::vector<double>& d, double cc, double gamma, double tol,
+                             int m_max, int m_pred, int* deg, int* ok) {
+  const double* xi = leja_table();
+  EI_TRY(reset_done(c));
+  NewtonScalars s{};
+  s.d0 = d[0];
+  s.inv_gamma = 1.0 / gamma;
+  s.tol = tol;
+  s.m_max = m_max;
+  int j = 0;
+  int batch = m_pred > 0 ? m_pred : 8;
+  while (true) {
+    const int jend = (j + batch < m_max) ? j + batch : m_max;
+    for (; j < jend; ++j) {
+      s.j = j;
+      s.d_next = d[j + 1];
+      s.shift = cc / gamma + xi[j];
+      const void* w_in = (j == 0) ? r : P.w[(j - 1) & 1];
+      EI_TRY_CUDA(op_newton(c, P, qc, w_in, P.w[j & 1], s));
+    }
+    EI_TRY(read_ctl(c));
+    const int done = c->h_ctl->done;
+    if (done == 1) { *deg = c->h_ctl->degree; *ok = 1; return EI_OK; }
+    if (done == 2) { *deg = c->h_ctl->degree; *ok = 0; return EI_OK; }
+    if (done == 4) return EI_ERR_NONFINITE;
+    if (j >= m_max) { *deg = m_max; *ok = 0; return EI_OK; }
+    batch = 8;
+  }
+}
+
+// Interval of the current operator: A alone, or J = A + diag(g'(u)).
+static void interval(double alpha, double beta, double* cc, double* gamma) {
+  *cc = 0.5 * (alpha + beta);
+  *gamma = 0.25 * (beta - alpha);
+}
+
+static void stats_reset(ei_stats* st) {
+  if (st) memset(st, 0, sizeof(*st));
+}
+
+// Integrate y' = J y + v from 0 over h by s substeps: returns y_s in the
+// buffer *result (vector format if *result_is_p == 0, Newton-sum format if 1).
+// k = 1 only.  v: imported vector (P.v); qc: J's diagonal array.
+static ei_status phi1_substeps(ei_ctx* c, Prepared& P, const void* qc, double h, double alpha,
+                               double beta, double tol, const ei_options* opt, ei_stats* st,
+                               const void** result, int* result_is_p, double* result_scale) {
+  double cc, gamma;
+  interval(alpha, beta, &cc, &gamma);
+  const int m_max = (opt && opt->m_max > 0 && opt->m_max <= 100) ? opt->m_max : 100;
+  int s = 1, m_pred = 0;
+  if (opt && opt->fixed_s > 0) {
+    s = opt->fixed_s;
+  } else if (schedule(1, h, cc, gamma, tol, m_max, &s, &m_pred) != 0) {
+    return EI_ERR_NOT_CONVERGED;
+  }
+  if (st) st->m_sched = m_pred;
+  std::vector<double> d(m_max + 1);
+  int restarts = 0, matvecs = 0;
+  while (s <= (1 << 20)) {
+    const double tau = h / s;
+    divided_differences(1, tau, cc, gamma, m_max, d.data());
+    if (s > 1) EI_TRY_CUDA(launch_zero(P.y, P.fmt, c->n, c->stream));
+    bool ok_all = true;
+    int dsum = 0, dmax = 0;
+    for (int i = 0; i < s; ++i) {
+      const void* r = P.v;
+      if (i > 0) {
+        EI_TRY_CUDA(op_residual(c, P, qc, P.y, P.v, P.r));
+        r = P.r;
+        ++matvecs;
+      }
+      int deg = 0, ok = 0;
+      EI_TRY(newton_loop(c, P, qc, r, d, cc, gamma, tol, m_max, m_pred, &deg, &ok));
+      matvecs += deg;
+      if (!ok) { ok_all = false; break; }
+      if (st && i < EI_STATS_MAX_SUBSTEPS) st->degrees[i] = deg;
+      dsum += deg;
+      if (deg > dmax) dmax = deg;
+      if (s > 1) EI_TRY_CUDA(launch_axpy(P.y, P.p, P.fmt, c->n, tau, c->stream));
+    }
+    if (ok_all) {
+      if (st) {
+        st->s = s;
+        st->restarts = restarts;
+        st->matvecs += matvecs;
+        st->degree_sum = dsum;
+        st->degree_max = dmax;
+        st->alpha = alpha;
+        st->beta = beta;
+      }
+      if (s == 1) {  // y_1 = tau * p
+        *result = P.p;
+        *result_is_p = 1;
+        *result_scale = h;
+      } else {
+        *result = P.y;
+        *result_is_p = 0;
+        *result_scale = 1.0;
+      }
+      return EI_OK;
+    }
+    ++restarts;
+    if (st) memset(st->degrees, 0, sizeof(st->degrees));
+    s *= 2;
+  }
+  return EI_ERR_NOT_CONVERGED;
+}
+
+static void log_stats(const char* what, const ei_stats* st, ei_status rc) {
+  if (!log_on() || !st) return;
+  fprintf(stderr,
+          "{\"ei\": \"%s\", \"status\": %d, \"alpha\": %.17g, \"beta\": %.17g, \"s\": %d, "
+          "\"restarts\": %d, \"matvecs\": %d, \"degree_sum\": %d, \"degree_max\": %d, "
+          "\"m_sched\": %d}\n",
+          what, (int)rc, st->alpha, st->beta, st->s, st->restarts, st->matvecs, st->degree_sum,
+          st->degree_max, st->m_sched);
+}
+
+// ===========================================================================
+// C ABI
+// ===========================================================================
+extern "C" {
+
+const char* ei_status_string(ei_status s) {
+  switch (s) {
+    case EI_OK: return "ok";
+    case EI_ERR_INVALID_ARG: return "invalid argument";
+    case EI_ERR_NONFINITE: return "non-finite value";
+    case EI_ERR_NOT_CONVERGED: return "not converged";
+    case EI_ERR_TIMEOUT: return "device wait timed out";
+    case EI_ERR_CUDA: return "CUDA error";
+    case EI_ERR_NOMEM: return "out of device memory";
+    case EI_ERR_STATE: return "call out of order";
+  }
+  return "unknown status";
+}
+
+ei_status ei_create(ei_ctx** out, int device, void* stream) {
+  if (!out) return EI_ERR_INVALID_ARG;
+  *out = nullptr;
+  int ndev = 0;
+  if (cudaGetDeviceCount(&ndev) != cudaSuccess || device < 0 || device >= ndev) {
+    cudaGetLastError();
+    return device < 0 ? EI_ERR_INVALID_ARG : EI_ERR_CUDA;
+  }
+  EI_TRY_CUDA(cudaSetDevice(device));
+  ei_ctx* c = new ei_ctx();
+  c->device = device;
+  c->stream = (cudaStream_t)stream;
+  if (cudaMalloc(&c->ctl, sizeof(DevCtl)) != cudaSuccess ||
+      cudaMallocHost(&c->h_ctl, sizeof(DevCtl)) != cudaSuccess) {
+    cudaGetLastError();
+    if (c->ctl) cudaFree(c->ctl);
+    delete c;
+    return EI_ERR_NOMEM;
+  }
+  cudaMemset(c->ctl, 0, sizeof(DevCtl));
+  memset(c->h_ctl, 0, sizeof(DevCtl));
+  *out = c;
+  return EI_OK;
+}
+
+void ei_destroy(ei_ctx* c) {
+  if (!c) return;
+  cudaSetDevice(c->device);
+  cudaStreamSynchronize(c->stream);
+  free_operator(c);
+  if (c->ctl) cudaFree(c->ctl);
+  if (c->h_ctl) cudaFreeHost(c->h_ctl);
+  delete c;
+}
+
+ei_status ei_set_stream(ei_ctx* c, void* stream) {
+  if (!c) return EI_ERR_INVALID_ARG;
+  c->stream = (cudaStream_t)stream;
+  return EI_OK;
+}
+
+ei_status ei_set_operator_stencil(ei_ctx* c, int dim, const int64_t n[3], const double dx[3],
+                                  const void* D, double D_const, const void* const b[3],
+                                  const double b_const[3], const void* cdiag, double c_const,
+                                  const int bc[6], int prec) {
+  if (!c || !n || !dx || !bc || (dim != 2 && dim != 3) ||
+      (prec != EI_PREC_F64 && prec != EI_PREC_F32))
+    return EI_ERR_INVALID_ARG;
+  int64_t ext[3] = {n[0], n[1], dim == 3 ? n[2] : 1};
+  for (int e = 0; e < 3; ++e)
+    if (ext[e] < 1 || ext[e] > (1 << 30)) return EI_ERR_INVALID_ARG;
+  for (int e = 0; e < dim; ++e)
+    if (!(dx[e] > 0) || !isfinite(dx[e])) return EI_ERR_INVALID_ARG;
+  for (int f = 0; f < 2 * dim; ++f)
+    if (bc[f] != EI_BC_DIRICHLET0 && bc[f] != EI_BC_NEUMANN0) return EI_ERR_INVALID_ARG;
+  if (!isfinite(D_const) || !isfinite(c_const)) return EI_ERR_INVALID_ARG;
+  if (b_const)
+    for (int e = 0; e < dim; ++e)
+      if (!isfinite(b_const[e])) return EI_ERR_INVALID_ARG;
+  // grid limits of the stencil kernels: 32 x 8 x 16 points per block
+  if ((double)ext[0] * ext[1] * ext[2] > 4.0e9 || ext[1] > 65535 * 8 || ext[2] > 65535 * 16)
+    return EI_ERR_INVALID_ARG;
+  EI_TRY_CUDA(cudaSetDevice(c->device));
+  cudaStreamSynchronize(c->stream);
+  free_operator(c);
+  c->kind = KIND_STENCIL;
+  c->prec = prec;
+  c->n = ext[0] * ext[1] * ext[2];
+  StencilDev& s = c->sd;
+  s = StencilDev{};
+  s.dim = dim;
+  s.nx = (int)ext[0];
+  s.ny = (int)ext[1];
+  s.nz = (int)ext[2];
+  for (int f = 0; f < 6; ++f) s.bc[f] = (f < 2 * dim) ? bc[f] : EI_BC_NEUMANN0;
+  for (int e = 0; e < 3; ++e) c->dx[e] = (e < dim) ? dx[e] : 1.0;
+  s.uniform = 1;
+  for (int e = 0; e < 3; ++e) {
+    s.ratio[e] = (c->dx[0] * c->dx[0]) / (c->dx[e] * c->dx[e]);
+    if (e < dim && s.ratio[e] != 1.0) s.uniform = 0;
+  }
+  c->Du = D;
+  c->Dc = D_const;
+  for (int e = 0; e < 3; ++e) {
+    c->bu[e] = (b && e < dim) ? b[e] : nullptr;
+    c->bcst[e] = (b_const && e < dim) ? b_const[e] : 0.0;
+  }
+  c->cu = cdiag;
+  c->cc = c_const;
+  // Gershgorin rows of A (FP64 from the caller's arrays) and reduction space
+  int nb = stencil_blocks(s);
+  if (nb < reduction_capacity()) nb = reduction_capacity();
+  c->max_blocks = nb;
+  ei_status st;
+  if ((st = alloc((void**)&c->partials, sizeof(double) * 2 * nb)) != EI_OK) { free_operator(c); return st; }
+  if ((st = alloc((void**)&c->ger_lo, sizeof(double) * c->n)) != EI_OK) { free_operator(c); return st; }
+  if ((st = alloc((void**)&c->ger_hi, sizeof(double) * c->n)) != EI_OK) { free_operator(c); return st; }
+  const void* bptr[3] = {c->bu[0], c->bu[1], c->bu[2]};
+  cudaError_t e = launch_stencil_gershgorin(s, prec, c->dx, D, D_const, bptr, c->bcst, cdiag,
+                                            c_const, c->ger_lo, c->ger_hi, c->partials, c->ctl,
+                                            c->stream);
+  if (e != cudaSuccess) { free_operator(c); return EI_ERR_CUDA; }
+  if ((st = prepare(c, prec == EI_PREC_F32 ? VF_F32 : VF_DF)) != EI_OK) { free_operator(c); return st; }
+  if ((st = read_ctl(c)) != EI_OK) { free_operator(c); return st; }
+  c->alphaA = c->h_ctl->mn;
+  c->betaA = c->h_ctl->mx;
+  if (!isfinite(c->alphaA) || !isfinite(c->betaA)) { free_operator(c); return EI_ERR_NONFINITE; }
+  return EI_OK;
+}
+
+ei_status ei_set_operator_csr(ei_ctx* c, int64_t n, int64_t nnz, const int64_t* rowptr,
+                              const int32_t* col, const void* val, const void* diag, int prec) {
+  if (!c || n < 1 || n > ((int64_t)1 << 31) - 1 || nnz < 0 || !rowptr ||
+      (nnz > 0 && (!col || !val)) || (prec != EI_PREC_F64 && prec != EI_PREC_F32))
+    return EI_ERR_INVALID_ARG;
+  EI_TRY_CUDA(cudaSetDevice(c->device));
+  cudaStreamSynchronize(c->stream);
+  free_operator(c);
+  c->kind = KIND_CSR;
+  c->prec = prec;
+  c->n = n;
+  c->nnz = nnz;
+  c->val_u = val;
+  c->diag_u = diag;
+  c->cd = CsrDev{};
+  c->cd.n = n;
+  c->cd.rowptr = rowptr;
+  c->cd.col = col;
+  int nb = csr_blocks(n);
+  if (nb < reduction_capacity()) nb = reduction_capacity();
+  c->max_blocks = nb;
+  ei_status st;
+  if ((st = alloc((void**)&c->partials, sizeof(double) * 2 * nb)) != EI_OK) { free_operator(c); return st; }
+  if ((st = alloc((void**)&c->ger_lo, sizeof(double) * n)) != EI_OK) { free_operator(c); return st; }
+  if ((st = alloc((void**)&c->ger_hi, sizeof(double) * n)) != EI_OK) { free_operator(c); return st; }
+  cudaError_t e = launch_csr_gershgorin(c->cd, prec, val, diag, c->ger_lo, c->ger_hi, c->partials,
+                                        c->ctl, c->stream);
+  if (e != cudaSuccess) { free_operator(c); return EI_ERR_CUDA; }
+  if ((st = prepare(c, prec == EI_PREC_F32 ? VF_F32 : VF_DF)) != EI_OK) { free_operator(c); return st; }
+  if ((st = read_ctl(c)) != EI_OK) { free_operator(c); return st; }
+  c->alphaA = c->h_ctl->mn;
+  c->betaA = c->h_ctl->mx;
+  if (!isfinite(c->alphaA) || !isfinite(c->betaA)) { free_operator(c); return EI_ERR_NONFINITE; }
+  return EI_OK;
+}
+
+ei_status ei_estimate_spectrum(ei_ctx* c, double* alpha, double* beta) {
+  if (!c || !alpha || !beta) return EI_ERR_INVALID_ARG;
+  if (c->kind == KIND_NONE) return EI_ERR_STATE;
+  *alpha = c->alphaA;
+  *beta = c->betaA;
+  return EI_OK;
+}
+
+ei_status ei_phi_apply(ei_ctx* c, int k, double h, const void* v, void* out, double tol,
+                       const ei_options* opt, ei_stats* st) {
+  stats_reset(st);
+  if (!c || !v || !out) return EI_ERR_INVALID_ARG;
+  if (c->kind == KIND_NONE) return EI_ERR_STATE;
+  if (k < 0 || k > 8 || !(h > 0) || !isfinite(h) || !(tol > 0) || !isfinite(tol))
+    return EI_ERR_INVALID_ARG;
+  EI_TRY_CUDA(cudaSetDevice(c->device));
+  const int fmt = vec_fmt_for(c, opt);
+  EI_TRY(prepare(c, fmt));
+  Prepared& P = c->prep[fmt];
+  const int64_t n = c->n;
+  EI_TRY_CUDA(launch_import(P.v, fmt, v, c->prec, n, c->partials, c->ctl, c->stream));
+  EI_TRY(read_ctl(c));
+  if (c->h_ctl->sum1 != 1.0) return EI_ERR_NONFINITE;
+  const double vnorm2 = c->h_ctl->sum0;
+  const double alpha = c->alphaA, beta = c->betaA;
+  double cc, gamma;
+  interval(alpha, beta, &cc, &gamma);
+  if (st) { st->alpha = alpha; st->beta = beta; st->s = 1; }
+  if (vnorm2 == 0.0) {  // phi_k(hA) 0 = 0
+    EI_TRY_CUDA(launch_export(out, c->prec, P.v, fmt, 0, n, 0.0, c->stream));
+    EI_TRY_CUDA(cudaStreamSynchronize(c->stream));
+    return EI_OK;
+  }
+  if (gamma == 0.0) {  // A = cI
+    EI_TRY_CUDA(launch_export(out, c->prec, P.v, fmt, 0, n, phi_scalar(k, h * cc), c->stream));
+    EI_TRY_CUDA(cudaStreamSynchronize(c->stream));
+    return EI_OK;
+  }
+  ei_status rc = EI_OK;
+  if (k == 1) {
+    const void* res = nullptr;
+    int is_p = 0;
+    double scale = 1.0;
+    rc = phi1_substeps(c, P, P.cbase, h, alpha, beta, tol, opt, st, &res, &is_p, &scale);
+    if (rc == EI_OK) {
+      EI_TRY_CUDA(launch_export(out, c->prec, res, fmt, is_p, n, scale / h, c->stream));
+      EI_TRY_CUDA(cudaStreamSynchronize(c->stream));
+    }
+  } else {
+    const int m_max = (opt && opt->m_max > 0 && opt->m_max <= 100) ? opt->m_max : 100;
+    int s = 1, m_pred = 0;
+    if (opt && opt->fixed_s > 0) s = opt->fixed_s;
+    else if (schedule(k, h, cc, gamma, tol, m_max, &s, &m_pred) != 0) return EI_ERR_NOT_CONVERGED;
+    if (st) st->m_sched = m_pred;
+    std::vector<double> d(m_max + 1);
+    int restarts = 0;
+    rc = EI_ERR_NOT_CONVERGED;
+    while (s <= (1 << 20)) {
+      if (k >= 2 && s > 1) { rc = EI_ERR_NOT_CONVERGED; break; }
+      const double tau = h / s;
+      divided_differences(k, tau, cc, gamma, m_max, d.data());
+      bool ok_all = true;
+      int dsum = 0, dmax = 0;
+      const void* cur = P.v;
+      for (int i = 0; i < s; ++i) {
+        if (i > 0) {
+          EI_TRY_CUDA(launch_p_to_vec(P.r, P.p, fmt, n, c->stream));
+          cur = P.r;
+        }
+        int deg = 0, ok = 0;
+        EI_TRY(newton_loop(c, P, P.cbase, cur, d, cc, gamma, tol, m_max, m_pred, &deg, &ok));
+        if (st) st->matvecs += deg;
+        if (!ok) { ok_all = false; break; }
+        if (st && i < EI_STATS_MAX_SUBSTEPS) st->degrees[i] = deg;
+        dsum += deg;
+        if (deg > dmax) dmax = deg;
+      }
+      if (ok_all) {
+        if (st) {
+          st->s = s; st->restarts = restarts; st->degree_sum = dsum; st->degree_max = dmax;
+        }
+        EI_TRY_CUDA(launch_export(out, c->prec, P.p, fmt, 1, n, 1.0, c->stream));
+        EI_TRY_CUDA(cudaStreamSynchronize(c->stream));
+        rc = EI_OK;
+        break;
+      }
+      ++restarts;
+      s *= 2;
+    }
+  }
+  log_stats("phi_apply", st, rc);
+  return rc;
+}
+
+static ei_status step_impl(ei_ctx* c, int method, double h, void* u, int nonlin, double tol,
+                           const ei_options* opt, ei_stats* st) {
+  const int fmt = vec_fmt_for(c, opt);
+  EI_TRY(prepare(c, fmt));
+  Prepared& P = c->prep[fmt];
+  const int64_t n = c->n;
+  const int rosen = (method == EI_EXP_ROSENBROCK);
+  // import u; F = A u + g(u); J's diagonal; the interval of J
+  EI_TRY_CUDA(launch_import(P.u, fmt, u, c->prec, n, c->partials, c->ctl, c->stream));
+  if (c->kind == KIND_STENCIL) {
+    EI_TRY_CUDA(launch_stencil_F(stencil_view(c, P, P.cbase), P.u, P.v, P.qc, P.cbase, nonlin,
+                                 rosen, fmt, c->partials, c->ctl, c->stream));
+  } else {
+    EI_TRY_CUDA(launch_csr_F(csr_view(c, P, P.cbase), P.u, P.v, P.qc, P.cbase, nonlin, rosen,
+                             fmt, c->partials, c->ctl, c->stream));
+  }
+  if (rosen)
+    EI_TRY_CUDA(launch_shifted_minmax(n, c->ger_lo, c->ger_hi, u, c->prec, nonlin, c->partials,
+                                      c->ctl, c->stream));
+  EI_TRY(read_ctl(c));
+  if (c->h_ctl->sum1 != 1.0) return EI_ERR_NONFINITE;
+  const double fnorm2 = c->h_ctl->sum0;
+  const double alpha = rosen ? c->h_ctl->mn : c->alphaA;
+  const double beta = rosen ? c->h_ctl->mx : c->betaA;
+  if (!isfinite(alpha) || !isfinite(beta)) return EI_ERR_NONFINITE;
+  if (st) { st->alpha = alpha; st->beta = beta; st->s = 1; st->matvecs = 1; }
+  if (fnorm2 == 0.0) return EI_OK;  // u is an equilibrium: u_{n+1} = u_n
+  double cc, gamma;
+  interval(alpha, beta, &cc, &gamma);
+  const void* qc = rosen ? P.qc : P.cbase;
+  if (gamma == 0.0) {  // J = cI: z(h) = h phi_1(hc) F
+    EI_TRY_CUDA(launch_add_export(u, c->prec, P.v, fmt, 0, n, h * phi_scalar(1, h * cc), c->stream));
+    EI_TRY_CUDA(cudaStreamSynchronize(c->stream));
+    return EI_OK;
+  }
+  const void* res = nullptr;
+  int is_p = 0;
+  double scale = 1.0;
+  EI_TRY(phi1_substeps(c, P, qc, h, alpha, beta, tol, opt, st, &res, &is_p, &scale));
+  EI_TRY_CUDA(launch_add_export(u, c->prec, res, fmt, is_p, n, scale, c->stream));
+  EI_TRY_CUDA(cudaStreamSynchronize(c->stream));
+  return EI_OK;
+}
+
+ei_status ei_step(ei_ctx* c, int method, double h, void* u, int nonlin, double tol,
+                  const ei_options* opt, ei_stats* st) {
+  stats_reset(st);
+  if (!c || !u) return EI_ERR_INVALID_ARG;
+  if (c->kind == KIND_NONE) return EI_ERR_STATE;
+  if ((method != EI_EXP_EULER && method != EI_EXP_ROSENBROCK) ||
+      (nonlin != EI_NONLIN_NONE && nonlin != EI_NONLIN_LOGISTIC) || !(h > 0) || !isfinite(h) ||
+      !(tol > 0) || !isfinite(tol))
+    return EI_ERR_INVALID_ARG;
+  EI_TRY_CUDA(cudaSetDevice(c->device));
+  ei_status rc = step_impl(c, method, h, u, nonlin, tol, opt, st);
+  log_stats("step", st, rc);
+  return rc;
+}
+
+ei_status ei_step_host(ei_ctx* c, int method, double h, void* u_host, int nonlin, double tol,
+                       const ei_options* opt, ei_stats* st) {
+  stats_reset(st);
+  if (!c || !u_host) return EI_ERR_INVALID_ARG;
+  if (c->kind == KIND_NONE) return EI_ERR_STATE;
+  EI_TRY_CUDA(cudaSetDevice(c->device));
+  const size_t bytes = (size_t)c->n * (c->prec == EI_PREC_F32 ? 4 : 8);
+  if (!c->host_stage) {
+    ei_status s = alloc(&c->host_stage, bytes);
+    if (s != EI_OK) return s;
+  }
+  EI_TRY_CUDA(cudaMemcpyAsync(c->host_stage, u_host, bytes, cudaMemcpyHostToDevice, c->stream));
+  ei_status rc = ei_step(c, method, h, c->host_stage, nonlin, tol, opt, st);
+  if (rc != EI_OK) return rc;
+  EI_TRY_CUDA(cudaMemcpyAsync(u_host, c->host_stage, bytes, cudaMemcpyDeviceToHost, c->stream));
+  EI_TRY_CUDA(cudaStreamSynchronize(c->stream));
+  return EI_OK;
+}
+
+}  // extern "C"

@@ -1,0 +1,255 @@
+"""Python binding of the C ABI in include/ei.h (ctypes; argument marshalling only).
+
+Every step of the computation runs in libei.so; this module converts torch
+tensors to device pointers and status codes to exceptions.  It fails loudly
+when the library is missing: there is no fallback path.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+
+_LIB = None
+_LIB_PATH = os.path.join(os.path.dirname(os.path.abspath(__file__)), "libei.so")
+
+OK, ERR_INVALID_ARG, ERR_NONFINITE, ERR_NOT_CONVERGED, ERR_TIMEOUT, ERR_CUDA, ERR_NOMEM, \
+    ERR_STATE = range(8)
+BC_DIRICHLET0, BC_NEUMANN0 = 0, 1
+PREC_F64, PREC_F32 = 0, 1
+ARITH_DF, ARITH_NATIVE_F64 = 0, 1
+EXP_EULER, EXP_ROSENBROCK = 0, 1
+NONLIN_NONE, NONLIN_LOGISTIC = 0, 1
+STATS_MAX_SUBSTEPS = 64
+
+# every symbol include/ei.h declares
+EXPORTS = [
+    "ei_create", "ei_destroy", "ei_set_stream", "ei_set_operator_stencil",
+    "ei_set_operator_csr", "ei_estimate_spectrum", "ei_phi_apply", "ei_step",
+    "ei_step_host", "ei_leja_points", "ei_divided_differences", "ei_schedule",
+    "ei_status_string",
+]
+
+
+class Options(C.Structure):
+    _fields_ = [("m_max", C.c_int), ("arith", C.c_int), ("fixed_s", C.c_int),
+                ("reserved", C.c_int * 5)]
+
+
+class Stats(C.Structure):
+    _fields_ = [("alpha", C.c_double), ("beta", C.c_double), ("s", C.c_int),
+                ("restarts", C.c_int), ("matvecs", C.c_int), ("degree_sum", C.c_int),
+                ("degree_max", C.c_int), ("m_sched", C.c_int),
+                ("degrees", C.c_int * STATS_MAX_SUBSTEPS)]
+
+    def degree_list(self):
+        return [int(self.degrees[i]) for i in range(min(self.s, STATS_MAX_SUBSTEPS))]
+
+    def as_dict(self):
+        return {"alpha": self.alpha, "beta": self.beta, "s": self.s, "restarts": self.restarts,
+                "matvecs": self.matvecs, "degree_sum": self.degree_sum,
+                "degree_max": self.degree_max, "m_sched": self.m_sched,
+                "degrees": self.degree_list()}
+
+
+class EIError(RuntimeError):
+    def __init__(self, status, where):
+        self.status = status
+        super().__init__(f"{where}: {status_string(status)} ({status})")
+
+
+def lib():
+    global _LIB
+    if _LIB is None:
+        if not os.path.exists(_LIB_PATH):
+            raise RuntimeError(f"{_LIB_PATH} is not built; run __graft_entry__.build()")
+        L = C.CDLL(_LIB_PATH)
+        vp, i64p, dp, ip = C.c_void_p, C.POINTER(C.c_int64), C.POINTER(C.c_double), C.POINTER(C.c_int)
+        L.ei_create.argtypes = [C.POINTER(C.c_void_p), C.c_int, vp]
+        L.ei_destroy.argtypes = [vp]
+        L.ei_destroy.restype = None
+        L.ei_set_stream.argtypes = [vp, vp]
+        L.ei_set_operator_stencil.argtypes = [vp, C.c_int, i64p, dp, vp, C.c_double,
+                                              C.POINTER(C.c_void_p), dp, vp, C.c_double, ip,
+                                              C.c_int]
+        L.ei_set_operator_csr.argtypes = [vp, C.c_int64, C.c_int64, vp, vp, vp, vp, C.c_int]
+        L.ei_estimate_spectrum.argtypes = [vp, dp, dp]
+        L.ei_phi_apply.argtypes = [vp, C.c_int, C.c_double, vp, vp, C.c_double,
+                                   C.POINTER(Options), C.POINTER(Stats)]
+        L.ei_step.argtypes = [vp, C.c_int, C.c_double, vp, C.c_int, C.c_double,
+                              C.POINTER(Options), C.POINTER(Stats)]
+        L.ei_step_host.argtypes = L.ei_step.argtypes
+        L.ei_leja_points.argtypes = [C.c_int, dp]
+        L.ei_divided_differences.argtypes = [C.c_int, C.c_double, C.c_double, C.c_double,
+                                             C.c_int, dp]
+        L.ei_schedule.argtypes = [C.c_int, C.c_double, C.c_double, C.c_double, C.c_double,
+                                  C.c_int, ip, ip]
+        L.ei_status_string.argtypes = [C.c_int]
+        L.ei_status_string.restype = C.c_char_p
+        for name in EXPORTS:
+            f = getattr(L, name)
+            if name not in ("ei_destroy", "ei_status_string"):
+                f.restype = C.c_int
+        _LIB = L
+    return _LIB
+
+
+def status_string(st):
+    return lib().ei_status_string(int(st)).decode()
+
+
+def _check(st, where):
+    if st != OK:
+        raise EIError(st, where)
+
+
+# ---- host-side pieces ------------------------------------------------------
+def leja_points(m=100):
+    import numpy as np
+    out = np.zeros(m + 1)
+    _check(lib().ei_leja_points(m, out.ctypes.data_as(C.POINTER(C.c_double))), "ei_leja_points")
+    return out
+
+
+def divided_differences(k, tau, c, gamma, m=100):
+    import numpy as np
+    out = np.zeros(m + 1)
+    _check(lib().ei_divided_differences(k, tau, c, gamma, m,
+                                        out.ctypes.data_as(C.POINTER(C.c_double))),
+           "ei_divided_differences")
+    return out
+
+
+def schedule(k, h, c, gamma, tol, m_max=100):
+    s, m = C.c_int(0), C.c_int(0)
+    _check(lib().ei_schedule(k, h, c, gamma, tol, m_max, C.byref(s), C.byref(m)), "ei_schedule")
+    return s.value, m.value
+
+
+# ---- context ---------------------------------------------------------------
+def _dev_ptr(t, dtype, n=None, name="tensor"):
+    if t is None:
+        return None
+    if not t.is_cuda or not t.is_contiguous() or t.dtype != dtype:
+        raise ValueError(f"{name}: expected a contiguous CUDA {dtype} tensor")
+    if n is not None and t.numel() != n:
+        raise ValueError(f"{name}: expected {n} elements, got {t.numel()}")
+    return C.c_void_p(t.data_ptr())
+
+
+class Context:
+    """One library context on one device and stream."""
+
+    def __init__(self, device=0, stream=None):
+        import torch
+        self._torch = torch
+        self.device = device
+        if stream is None:
+            stream = torch.cuda.current_stream(device)
+        self.stream = stream
+        h = C.c_void_p()
+        _check(lib().ei_create(C.byref(h), device, C.c_void_p(stream.cuda_stream)), "ei_create")
+        self._h = h
+        self._keep = []
+        self.prec = PREC_F64
+        self.n = 0
+
+    def close(self):
+        if getattr(self, "_h", None):
+            lib().ei_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def _dtype(self, prec):
+        return self._torch.float64 if prec == PREC_F64 else self._torch.float32
+
+    def set_operator_stencil(self, n, dx, D, b, c=0.0, bc=None, prec=PREC_F64):
+        """n = (nx, ny[, nz]); D, each b[e] and c are CUDA tensors (shape [nz,]ny,nx)
+        or Python floats (constants)."""
+        dim = len(n)
+        npts = 1
+        for v in n:
+            npts *= int(v)
+        dt = self._dtype(prec)
+        n3 = (C.c_int64 * 3)(*(list(n) + [1] * (3 - dim)))
+        dx3 = (C.c_double * 3)(*(list(dx) + [1.0] * (3 - dim)))
+        bc = bc if bc is not None else [BC_DIRICHLET0] * (2 * dim)
+        bc6 = (C.c_int * 6)(*(list(bc) + [BC_NEUMANN0] * (6 - len(bc))))
+
+        def arr_or_const(x, name):
+            if isinstance(x, (int, float)):
+                return None, float(x)
+            return _dev_ptr(x, dt, npts, name), 0.0
+
+        Dp, Dc = arr_or_const(D, "D")
+        bptr = (C.c_void_p * 3)()
+        bcst = (C.c_double * 3)()
+        for e in range(3):
+            if e < dim:
+                p_, c_ = arr_or_const(b[e], f"b[{e}]")
+                bptr[e] = p_.value if p_ is not None else None
+                bcst[e] = c_
+        cp, cc = arr_or_const(c, "c")
+        self._keep = [D, b, c]
+        _check(lib().ei_set_operator_stencil(self._h, dim, n3, dx3, Dp, Dc, bptr, bcst, cp, cc,
+                                             bc6, prec), "ei_set_operator_stencil")
+        self.prec = prec
+        self.n = npts
+
+    def set_operator_csr(self, n, rowptr, col, val, diag=None, prec=PREC_F64):
+        torch = self._torch
+        dt = self._dtype(prec)
+        nnz = int(col.numel())
+        self._keep = [rowptr, col, val, diag]
+        _check(lib().ei_set_operator_csr(
+            self._h, int(n), nnz, _dev_ptr(rowptr, torch.int64, int(n) + 1, "rowptr"),
+            _dev_ptr(col, torch.int32, nnz, "col"), _dev_ptr(val, dt, nnz, "val"),
+            _dev_ptr(diag, dt, int(n), "diag"), prec), "ei_set_operator_csr")
+        self.prec = prec
+        self.n = int(n)
+
+    def estimate_spectrum(self):
+        a, b = C.c_double(), C.c_double()
+        _check(lib().ei_estimate_spectrum(self._h, C.byref(a), C.byref(b)), "ei_estimate_spectrum")
+        return a.value, b.value
+
+    @staticmethod
+    def _opts(options):
+        if options is None:
+            return None
+        if isinstance(options, Options):
+            return C.byref(options)
+        o = Options()
+        for k, v in options.items():
+            setattr(o, k, v)
+        return C.byref(o)
+
+    def phi_apply(self, k, h, v, out, tol, options=None):
+        dt = self._dtype(self.prec)
+        st = Stats()
+        _check(lib().ei_phi_apply(self._h, k, h, _dev_ptr(v, dt, self.n, "v"),
+                                  _dev_ptr(out, dt, self.n, "out"), tol, self._opts(options),
+                                  C.byref(st)), "ei_phi_apply")
+        return st
+
+    def step(self, method, h, u, nonlin, tol, options=None):
+        dt = self._dtype(self.prec)
+        st = Stats()
+        _check(lib().ei_step(self._h, method, h, _dev_ptr(u, dt, self.n, "u"), nonlin, tol,
+                             self._opts(options), C.byref(st)), "ei_step")
+        return st
+
+    def step_host(self, method, h, u_host, nonlin, tol, options=None):
+        """u_host: a CPU tensor (pinned for asynchronous copies)."""
+        dt = self._dtype(self.prec)
+        if u_host.is_cuda or not u_host.is_contiguous() or u_host.dtype != dt or \
+                u_host.numel() != self.n:
+            raise ValueError("u_host: expected a contiguous CPU tensor of the operator's size")
+        st = Stats()
+        _check(lib().ei_step_host(self._h, method, h, C.c_void_p(u_host.data_ptr()), nonlin,
+                                  tol, self._opts(options), C.byref(st)), "ei_step_host")
+        return st

@@ -1,0 +1,77 @@
+"""The C ABI library on the CPU: it loads, exports every symbol include/ei.h
+declares, and its host-side pieces (Leja points, divided differences, the
+a-priori schedule) agree with the oracle.  No device compute is called."""
+import os
+import re
+
+import numpy as np
+import pytest
+
+from oracle import leja as L
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+@pytest.fixture(scope="module")
+def ei():
+    from paper_1309_4616_gb300 import build
+    build.build()
+    from paper_1309_4616_gb300 import ei as mod
+    return mod
+
+
+def test_header_symbols_exported(ei):
+    hdr = open(os.path.join(ROOT, "include", "ei.h")).read()
+    declared = set(re.findall(r"\b(ei_[a-z_]+)\s*\(", hdr)) - {"ei_ctx"}
+    assert declared == set(ei.EXPORTS)
+    L_ = ei.lib()
+    for name in declared:
+        assert hasattr(L_, name), name
+
+
+def test_status_strings(ei):
+    assert ei.status_string(0) == "ok"
+    assert "not converged" in ei.status_string(3)
+
+
+def test_leja_points_match_oracle(ei):
+    xi = ei.leja_points(100)
+    xo = L.leja_points(100)
+    assert np.abs(xi - xo).max() <= 1e-14
+
+
+@pytest.mark.parametrize("k,tau,c,gamma", [
+    (1, 1e-3, -1690.0, 845.0),          # the 64^2 advection-diffusion interval
+    (1, 1e-4, -5.9e5, 2.95e5),           # the 256^3 interval, h = 1e-4
+    (0, 0.37, -3.1, 1.3),
+    (2, 0.5, -20.0, 10.0),
+    (1, 1.0, -60.0, 30.0),
+    (1, 1e-2, -2.0e4, 1.0e4),
+])
+def test_divided_differences_match_oracle(ei, k, tau, c, gamma):
+    xi = L.leja_points(100)
+    d = ei.divided_differences(k, tau, c, gamma, 100)
+    do = L.divided_differences(k, tau, c, gamma, xi)
+    big = np.abs(do) > 1e-300
+    rel = np.abs(d[big] - do[big]) / np.abs(do[big])
+    assert rel.max() <= 1e-13
+
+
+@pytest.mark.parametrize("k,h,c,gamma,tol", [
+    (1, 1e-3, -1690.0, 845.0, 1e-10),
+    (1, 1e-4, -5.9e5, 2.95e5, 1e-10),
+    (1, 5e-5, -2.4e6, 1.2e6, 1e-6),
+    (1, 1e-2, -4 * 513 ** 2, 2 * 513 ** 2, 1e-10),
+    (0, 0.5, -30.0, 15.0, 1e-12),
+])
+def test_schedule_matches_oracle(ei, k, h, c, gamma, tol):
+    xi = L.leja_points(100)
+    assert ei.schedule(k, h, c, gamma, tol) == L.plain_schedule(k, h, c, gamma, tol, xi)[:2]
+
+
+def test_invalid_arguments(ei):
+    with pytest.raises(ei.EIError) as e:
+        ei.divided_differences(1, -1.0, 0.0, 1.0)
+    assert e.value.status == ei.ERR_INVALID_ARG
+    with pytest.raises(ei.EIError):
+        ei.leja_points(101)

@@ -1,0 +1,304 @@
+"""Parity of the CUDA path (through the C ABI) with the CPU oracle.
+
+Bar: FP64 results within 1e-9 relative 2-norm of the oracle, Leja degree per
+substep and substep count identical, Gershgorin interval within 1e-13
+relative; the FP32 form within 1e-5.  Grid sizes span several kernel tiles
+(32 x 8 x 16 points) with ragged tails in every axis.
+"""
+import numpy as np
+import pytest
+
+from oracle import leja as L
+from oracle import newton as Nw
+from oracle import operators as O
+from paper_1309_4616_gb300 import workloads as W
+
+from gpu_helpers import dev, rel_err, require_gpu, stencil_context
+
+pytestmark = pytest.mark.gpu
+
+FP64_TOL = 1e-9
+FP32_TOL = 1e-5
+
+
+@pytest.fixture(scope="module")
+def env():
+    return require_gpu()
+
+
+@pytest.fixture(scope="module")
+def xi():
+    return L.leja_points(100)
+
+
+def _check_stats(st, ost):
+    assert st.s == ost.s, (st.s, ost.s)
+    assert st.degree_list() == list(ost.degrees)[: len(st.degree_list())], \
+        (st.degree_list(), ost.degrees)
+    assert st.alpha == pytest.approx(ost.alpha, rel=1e-13, abs=1e-9)
+    assert st.beta == pytest.approx(ost.beta, rel=1e-13, abs=1e-9)
+
+
+# --------------------------------------------------------------------------
+# 2D advection-diffusion on 64 x 64, the small configuration in full
+# --------------------------------------------------------------------------
+@pytest.mark.parametrize("arith", [0, 1])
+def test_adv_diff_2d_phi1(env, xi, arith):
+    torch, ei = env
+    w = W.adv_diff_2d()
+    op = O.StencilOperator(w.n, w.dx, w.D, w.b, bc=w.bc)
+    ref, ost = Nw.phi_apply(op, 1, w.h, w.v, w.tol, xi=xi)
+    ctx = stencil_context(torch, ei, w.n, w.dx, w.D, w.b, 0.0, w.bc)
+    a, b = ctx.estimate_spectrum()
+    assert a == pytest.approx(-3380.0, rel=1e-13) and abs(b) < 1e-9
+    v = dev(torch, w.v)
+    out = torch.empty_like(v)
+    st = ctx.phi_apply(1, w.h, v, out, w.tol, {"arith": arith})
+    assert rel_err(out.cpu().numpy(), ref) <= FP64_TOL
+    _check_stats(st, ost)
+
+
+# --------------------------------------------------------------------------
+# 3D variable coefficients, ragged tiles
+# --------------------------------------------------------------------------
+def _fields_3d(rng, n):
+    nx, ny, nz = n
+    D = rng.uniform(0.5, 1.5, (nz, ny, nx))
+    b = tuple(rng.uniform(-2, 2, (nz, ny, nx)) for _ in range(3))
+    return D, b
+
+
+@pytest.mark.parametrize("method", [Nw.NONLIN_LOGISTIC])
+@pytest.mark.parametrize("arith", [0, 1])
+def test_rosenbrock_3d_neumann(env, xi, method, arith):
+    torch, ei = env
+    rng = np.random.default_rng(21)
+    n = (37, 29, 21)
+    dx = (1 / 37, 1 / 37, 1 / 37)
+    D, b = _fields_3d(rng, n)
+    u0 = rng.uniform(0, 1, (21, 29, 37))
+    op = O.StencilOperator(n, dx, D, b, bc=(O.NEUMANN0,) * 6)
+    h, tol = 2e-4, 1e-10
+    ref, ost = Nw.exp_rosenbrock_step(op, u0, h, tol, xi=xi)
+    ctx = stencil_context(torch, ei, n, dx, D, b, 0.0, (1,) * 6)
+    u = dev(torch, u0)
+    st = ctx.step(ei.EXP_ROSENBROCK, h, u, ei.NONLIN_LOGISTIC, tol, {"arith": arith})
+    got = u.cpu().numpy()
+    assert rel_err(got - u0, ref - u0) <= FP64_TOL
+    assert rel_err(got, ref) <= FP64_TOL
+    _check_stats(st, ost)
+
+
+def test_exp_euler_3d_mixed_bc_with_c(env, xi):
+    torch, ei = env
+    rng = np.random.default_rng(22)
+    n = (45, 17, 33)
+    dx = (0.02, 0.025, 0.03)
+    D, b = _fields_3d(rng, n)
+    c = rng.uniform(-3, 1, (33, 17, 45))
+    bc = (0, 1, 1, 0, 0, 1)
+    u0 = rng.uniform(0, 1, (33, 17, 45))
+    op = O.StencilOperator(n, dx, D, b, c=c, bc=bc)
+    h, tol = 1e-4, 1e-10
+    ref, ost = Nw.exp_euler_step(op, u0, h, tol, Nw.NONLIN_LOGISTIC, xi=xi)
+    ctx = stencil_context(torch, ei, n, dx, D, b, c, bc)
+    u = dev(torch, u0)
+    st = ctx.step(ei.EXP_EULER, h, u, ei.NONLIN_LOGISTIC, tol)
+    got = u.cpu().numpy()
+    assert rel_err(got - u0, ref - u0) <= FP64_TOL
+    _check_stats(st, ost)
+
+
+def test_substeps_2d_mixed(env, xi):
+    # a large h makes the a-priori rule ask for several substeps
+    torch, ei = env
+    rng = np.random.default_rng(23)
+    n = (70, 43)
+    dx = (1 / 71, 1 / 44)
+    D = rng.uniform(0.2, 1.0, (43, 70))
+    b = (rng.uniform(-1, 1, (43, 70)), rng.uniform(-1, 1, (43, 70)))
+    bc = (1, 0, 0, 1)
+    v0 = rng.standard_normal((43, 70))
+    op = O.StencilOperator(n, dx, D, b, bc=bc)
+    h, tol = 0.02, 1e-10
+    ref, ost = Nw.phi_apply(op, 1, h, v0, tol, xi=xi)
+    assert ost.s > 1
+    ctx = stencil_context(torch, ei, n, dx, D, b, 0.0, bc)
+    v = dev(torch, v0)
+    out = torch.empty_like(v)
+    st = ctx.phi_apply(1, h, v, out, tol)
+    assert rel_err(out.cpu().numpy(), ref) <= FP64_TOL
+    _check_stats(st, ost)
+
+
+@pytest.mark.parametrize("k", [0, 2])
+def test_phi_k_other_orders(env, xi, k):
+    torch, ei = env
+    rng = np.random.default_rng(30 + k)
+    n = (33, 9)
+    dx = (1 / 34, 1 / 10)
+    D = rng.uniform(0.1, 0.3, (9, 33))
+    b = (rng.uniform(-1, 1, (9, 33)), rng.uniform(-1, 1, (9, 33)))
+    v0 = rng.standard_normal((9, 33))
+    op = O.StencilOperator(n, dx, D, b)
+    h, tol = (2e-3 if k == 0 else 2e-4), 1e-11
+    ref, ost = Nw.phi_apply(op, k, h, v0, tol, xi=xi)
+    ctx = stencil_context(torch, ei, n, dx, D, b)
+    v = dev(torch, v0)
+    out = torch.empty_like(v)
+    st = ctx.phi_apply(k, h, v, out, tol)
+    assert rel_err(out.cpu().numpy(), ref) <= FP64_TOL
+    _check_stats(st, ost)
+
+
+def test_fp32_form(env, xi):
+    # FP32 vectors and matvec; FP64-class divided differences, interval and sum
+    torch, ei = env
+    rng = np.random.default_rng(24)
+    n = (40, 24, 20)
+    dx = (1 / 40,) * 3
+    D, b = _fields_3d(rng, n)
+    D32 = D.astype(np.float32)
+    b32 = tuple(x.astype(np.float32) for x in b)
+    u0 = rng.uniform(0, 1, (20, 24, 40)).astype(np.float32)
+    # the oracle runs in FP64 on the same (FP32-representable) inputs
+    op = O.StencilOperator(n, dx, D32.astype(np.float64), [x.astype(np.float64) for x in b32],
+                           bc=(1,) * 6)
+    h, tol = 5e-5, 1e-6
+    ref, ost = Nw.exp_euler_step(op, u0.astype(np.float64), h, tol, Nw.NONLIN_LOGISTIC, xi=xi)
+    ctx = stencil_context(torch, ei, n, dx, D32, b32, 0.0, (1,) * 6, prec=1)
+    u = dev(torch, u0)
+    ctx.step(ei.EXP_EULER, h, u, ei.NONLIN_LOGISTIC, tol)
+    got = u.cpu().numpy().astype(np.float64)
+    assert rel_err(got, ref) <= FP32_TOL
+    assert rel_err(got - u0, ref - u0) <= 1e-4
+
+
+# --------------------------------------------------------------------------
+# CSR
+# --------------------------------------------------------------------------
+def _graph(n, seed):
+    g = W.rgg_graph(n=n, mean_degree=12.0, seed=seed)
+    return g
+
+
+@pytest.mark.parametrize("order", ["morton", "random"])
+def test_csr_graph_phi1(env, xi, order):
+    torch, ei = env
+    g = W.rgg_graph(n=3000, mean_degree=12.0, seed=77, order=order)
+    op = O.CsrOperator(g.n, g.rowptr, g.col, g.val, -g.deg_w)
+    v0 = W.random_vector(g.n, 5)
+    h = 40.0 / (2 * g.deg_w.max())
+    ref, ost = Nw.phi_apply(op, 1, h, v0, 1e-10, xi=xi)
+    ctx = ei.Context()
+    ctx.set_operator_csr(g.n, dev(torch, g.rowptr), dev(torch, g.col), dev(torch, g.val),
+                         dev(torch, -g.deg_w))
+    a, b = ctx.estimate_spectrum()
+    assert a == pytest.approx(-2 * g.deg_w.max(), rel=1e-13)
+    v = dev(torch, v0)
+    out = torch.empty_like(v)
+    st = ctx.phi_apply(1, h, v, out, 1e-10)
+    assert rel_err(out.cpu().numpy(), ref) <= FP64_TOL
+    _check_stats(st, ost)
+
+
+def test_csr_rosenbrock(env, xi):
+    torch, ei = env
+    g = W.rgg_graph(n=2000, mean_degree=12.0, seed=78)
+    op = O.CsrOperator(g.n, g.rowptr, g.col, g.val, -g.deg_w)
+    u0 = np.random.default_rng(3).uniform(0, 1, g.n)
+    h = 0.5
+    ref, ost = Nw.exp_rosenbrock_step(op, u0, h, 1e-10, xi=xi)
+    ctx = ei.Context()
+    ctx.set_operator_csr(g.n, dev(torch, g.rowptr), dev(torch, g.col), dev(torch, g.val),
+                         dev(torch, -g.deg_w))
+    u = dev(torch, u0)
+    st = ctx.step(ei.EXP_ROSENBROCK, h, u, ei.NONLIN_LOGISTIC, 1e-10)
+    got = u.cpu().numpy()
+    assert rel_err(got - u0, ref - u0) <= FP64_TOL
+    _check_stats(st, ost)
+
+
+# --------------------------------------------------------------------------
+# edge cases
+# --------------------------------------------------------------------------
+def test_zero_vector_and_scalar_operator(env, xi):
+    torch, ei = env
+    ctx = stencil_context(torch, ei, (19, 5, 3), (0.1, 0.1, 0.1), 1.0, (0.0, 0.0, 0.0), 0.0,
+                          (1,) * 6)
+    z = torch.zeros(3 * 5 * 19, dtype=torch.float64, device="cuda")
+    out = torch.full_like(z, 7.0)
+    st = ctx.phi_apply(1, 0.01, z, out, 1e-10)
+    assert not out.any().item() and st.degree_sum == 0
+    # A = cI: D = 0, b = 0, Neumann everywhere, c = -3 -> gamma = 0
+    ctx2 = stencil_context(torch, ei, (11, 4), (0.1, 0.1), 0.0, (0.0, 0.0), -3.0, (1,) * 4)
+    assert ctx2.estimate_spectrum() == (-3.0, -3.0)
+    v0 = np.random.default_rng(1).standard_normal(44)
+    v = dev(torch, v0)
+    out = torch.empty_like(v)
+    for k in (0, 1, 2):
+        ctx2.phi_apply(k, 0.1, v, out, 1e-10)
+        assert np.allclose(out.cpu().numpy(), L.phi_scalar(k, -0.3) * v0, rtol=1e-14)
+
+
+def test_single_point_and_thin_grids(env, xi):
+    torch, ei = env
+    for n, bc in [((1, 1, 1), (0,) * 6), ((1, 7, 1), (0, 1, 1, 0, 0, 1)), ((65, 1), (0, 0, 1, 1))]:
+        dim = len(n)
+        rng = np.random.default_rng(sum(n))
+        shape = tuple(reversed(n))
+        D = rng.uniform(0.5, 1.5, shape)
+        b = tuple(rng.uniform(-1, 1, shape) for _ in range(dim))
+        dx = tuple([0.1] * dim)
+        v0 = rng.standard_normal(shape)
+        op = O.StencilOperator(n, dx, D, b, bc=bc)
+        ref, ost = Nw.phi_apply(op, 1, 1e-3, v0, 1e-10, xi=xi)
+        ctx = stencil_context(torch, ei, n, dx, D, b, 0.0, bc)
+        v = dev(torch, v0)
+        out = torch.empty_like(v)
+        st = ctx.phi_apply(1, 1e-3, v, out, 1e-10)
+        assert rel_err(out.cpu().numpy(), ref) <= FP64_TOL
+        _check_stats(st, ost)
+
+
+def test_errors_leave_outputs_untouched(env):
+    torch, ei = env
+    ctx = ei.Context()
+    v = torch.ones(8, dtype=torch.float64, device="cuda")
+    out = torch.full_like(v, 5.0)
+    with pytest.raises(ei.EIError) as e:
+        ctx.phi_apply(1, 0.1, v, out, 1e-10)
+    assert e.value.status == ei.ERR_STATE
+    ctx = stencil_context(torch, ei, (4, 2), (0.1, 0.1), 1.0, (0.0, 0.0), 0.0)
+    for args in [(-1, 0.1, 1e-10), (1, 0.0, 1e-10), (1, 0.1, 0.0), (1, float("nan"), 1e-10)]:
+        with pytest.raises(ei.EIError) as e:
+            ctx.phi_apply(args[0], args[1], v, out, args[2])
+        assert e.value.status == ei.ERR_INVALID_ARG
+    bad = v.clone()
+    bad[3] = float("nan")
+    with pytest.raises(ei.EIError) as e:
+        ctx.phi_apply(1, 0.1, bad, out, 1e-10)
+    assert e.value.status == ei.ERR_NONFINITE
+    assert (out == 5.0).all().item()
+    u = bad.clone()
+    with pytest.raises(ei.EIError) as e:
+        ctx.step(ei.EXP_EULER, 0.1, u, ei.NONLIN_LOGISTIC, 1e-10)
+    assert e.value.status == ei.ERR_NONFINITE
+    assert torch.equal(torch.isnan(u), torch.isnan(bad))
+    with pytest.raises(ei.EIError) as e:
+        ctx.step(7, 0.1, u, ei.NONLIN_LOGISTIC, 1e-10)
+    assert e.value.status == ei.ERR_INVALID_ARG
+
+
+def test_step_host_equals_step(env, xi):
+    torch, ei = env
+    rng = np.random.default_rng(40)
+    n = (20, 12, 9)
+    D, b = _fields_3d(rng, n)
+    u0 = rng.uniform(0, 1, (9, 12, 20))
+    ctx = stencil_context(torch, ei, n, (0.05,) * 3, D, b, 0.0, (1,) * 6)
+    ud = dev(torch, u0)
+    ctx.step(ei.EXP_ROSENBROCK, 1e-4, ud, ei.NONLIN_LOGISTIC, 1e-10)
+    uh = torch.from_numpy(u0.copy()).pin_memory()
+    ctx.step_host(ei.EXP_ROSENBROCK, 1e-4, uh, ei.NONLIN_LOGISTIC, 1e-10)
+    assert torch.equal(uh, ud.cpu())
