@@ -79,7 +79,9 @@ typedef struct {
   int m_max;      /* largest Newton degree per substep; 0 -> 100 (max 100) */
   int arith;      /* EI_ARITH_*, F64 operators only; default EI_ARITH_DF */
   int fixed_s;    /* > 0: use this substep count instead of the a-priori rule */
-  int reserved[5];
+  int profile;    /* 1: time every Newton-iteration launch with CUDA events on the
+                     context's stream (stats.newton_ms / newton_timed) */
+  int reserved[4];
 } ei_options;
 
 #define EI_STATS_MAX_SUBSTEPS 64
@@ -92,6 +94,9 @@ typedef struct {
   int degree_max;
   int m_sched;          /* degree the a-priori rule predicted */
   int degrees[EI_STATS_MAX_SUBSTEPS]; /* per substep, first 64 substeps */
+  int launches;         /* kernels this call launched */
+  int newton_timed;     /* Newton-iteration launches timed (options.profile) */
+  double newton_ms;     /* their summed device time (launches that did work) */
 } ei_stats;
 
 /* Create a context on CUDA device `device`, ordering work on `cuda_stream`
@@ -133,8 +138,9 @@ ei_status ei_set_operator_csr(ei_ctx* ctx, int64_t n, int64_t nnz, const int64_t
 
 /* Gershgorin interval of the operator (FP64):
  *   alpha = min_i (a_ii - r_i),  beta = max_i (a_ii + r_i),  r_i = sum_{j!=i} |a_ij|.
- * The paper assumes "a bound of the field of values ... known a priori"
- * (Sec. II-C); this is that bound for the real-Leja method.  Host outputs. */
+ * Sec. II-C of the paper presupposes a bound on the field of values that is
+ * available in advance; this interval is that bound for the real-Leja
+ * method.  Host outputs. */
 ei_status ei_estimate_spectrum(ei_ctx* ctx, double* alpha, double* beta);
 
 /* out = phi_k(hA) v  (Eq. (2) for k = 1; phi_0 = exp).  v, out: device

@@ -12,7 +12,7 @@
 #pragma once
 #include <cuda_runtime.h>
 
-struct df {
+struct __align__(8) df {
   float hi, lo;
 };
 

@@ -45,6 +45,14 @@ struct Prepared {
   void* v = nullptr;       // imported right-hand side / F
   void* u = nullptr;       // imported state
   void* csr_val = nullptr; // CSR values in the matvec precision
+  void* a[6] = {nullptr, nullptr, nullptr, nullptr, nullptr, nullptr};  // stencil coefficients
+  void* diagA = nullptr;   // stencil: diagonal of A (coefficient layout)
+  bool coef7 = false;      // stencil layout of this format: explicit coefficients or flux form
+  int64_t n_alloc = 0;     // elements per vector including row padding
+  // TMA descriptors of the stencil Newton kernel
+  CUtensorMap map_in[4];   // w-input candidates: v, r, w[0], w[1] (halo box)
+  CUtensorMap map_c[6];    // coef7: a[0..5]; flux: D (halo), B[0..2]
+  CUtensorMap map_diagA, map_cbase, map_qc, map_p;
 };
 
 struct ei_ctx {
@@ -79,6 +87,12 @@ struct ei_ctx {
   Prepared prep[3];
   // staging for ei_step_host
   void* host_stage = nullptr;
+  // launch accounting and optional per-launch timing of the Newton kernel
+  int launches = 0;
+  bool profile = false;
+  int newton_timed = 0;
+  double newton_ms = 0.0;
+  std::vector<cudaEvent_t> ev;
 };
 
 #define EI_TRY_CUDA(expr)                        \
@@ -88,6 +102,12 @@ struct ei_ctx {
       ei_log_cuda(e_, #expr, __LINE__);          \
       return EI_ERR_CUDA;                        \
     }                                            \
+  } while (0)
+
+#define EI_LAUNCH(expr)                          \
+  do {                                           \
+    ++c->launches;                               \
+    EI_TRY_CUDA(expr);                           \
   } while (0)
 
 #define EI_TRY(expr)                             \
@@ -106,6 +126,13 @@ static bool log_on() {
   return lg && *lg == '1';
 }
 
+// layout of the library's vectors: (nx, ny, pitch); CSR vectors are 1D
+static int geo_nx(const ei_ctx* c) { return c->kind == KIND_STENCIL ? c->sd.nx : (int)c->n; }
+static int geo_pitch(const ei_ctx* c) { return c->kind == KIND_STENCIL ? c->sd.pitch : (int)c->n; }
+static int64_t n_alloc_of(const ei_ctx* c) {
+  return c->kind == KIND_STENCIL ? (int64_t)c->sd.pitch * c->sd.ny * c->sd.nz : c->n;
+}
+
 static int vec_fmt_for(const ei_ctx* c, const ei_options* opt) {
   if (c->prec == EI_PREC_F32) return VF_F32;
   if (opt && opt->arith == EI_ARITH_NATIVE_F64) return VF_F64;
@@ -113,8 +140,9 @@ static int vec_fmt_for(const ei_ctx* c, const ei_options* opt) {
 }
 
 static void free_prepared(Prepared& p) {
-  void** arrs[] = {&p.D, &p.B[0], &p.B[1], &p.B[2], &p.cbase, &p.qc, &p.w[0], &p.w[1],
-                   &p.p, &p.y, &p.r, &p.v, &p.u, &p.csr_val};
+  void** arrs[] = {&p.D,    &p.B[0], &p.B[1], &p.B[2], &p.cbase, &p.qc,   &p.w[0],
+                   &p.w[1], &p.p,    &p.y,    &p.r,    &p.v,     &p.u,    &p.csr_val,
+                   &p.a[0], &p.a[1], &p.a[2], &p.a[3], &p.a[4],  &p.a[5], &p.diagA};
   for (void** a : arrs) {
     if (*a) cudaFree(*a);
     *a = nullptr;
@@ -146,44 +174,92 @@ static ei_status alloc(void** p, size_t bytes) {
   return EI_OK;
 }
 
-// Build the operator arrays and workspaces of one vector format.
+// Build the operator arrays and workspaces of one vector format.  Stencil
+// formats with 8-byte elements use explicit coefficients (7 arrays; the
+// Newton kernel then needs no boundary logic and little arithmetic per point);
+// the float format keeps the flux form (D, b, c), which moves fewer bytes.
 static ei_status prepare(ei_ctx* c, int fmt) {
   Prepared& P = c->prep[fmt];
   if (P.ready) return EI_OK;
   P.fmt = fmt;
   const int64_t n = c->n;
-  const size_t vb = vec_elem_bytes(fmt) * (size_t)n, pb = p_elem_bytes(fmt) * (size_t)n;
+  const int64_t na = n_alloc_of(c);
+  P.n_alloc = na;
+  const size_t vb = vec_elem_bytes(fmt) * (size_t)na, pb = p_elem_bytes(fmt) * (size_t)na;
+  const int nx = geo_nx(c), ny = c->kind == KIND_STENCIL ? c->sd.ny : 1, pitch = geo_pitch(c);
   ei_status s;
+  auto take = [&](void** a, size_t bytes) {
+    ei_status r = alloc(a, bytes);
+    if (r == EI_OK && cudaMemsetAsync(*a, 0, bytes, c->stream) != cudaSuccess) r = EI_ERR_CUDA;
+    return r;
+  };
   void** vecs[] = {&P.cbase, &P.qc, &P.w[0], &P.w[1], &P.y, &P.r, &P.v, &P.u};
   for (void** a : vecs)
-    if ((s = alloc(a, vb)) != EI_OK) { free_prepared(P); return s; }
-  if ((s = alloc(&P.p, pb)) != EI_OK) { free_prepared(P); return s; }
+    if ((s = take(a, vb)) != EI_OK) { free_prepared(P); return s; }
+  if ((s = take(&P.p, pb)) != EI_OK) { free_prepared(P); return s; }
   if (c->kind == KIND_STENCIL) {
-    if ((s = alloc(&P.D, vb)) != EI_OK) { free_prepared(P); return s; }
-    for (int e = 0; e < 3; ++e)
-      if ((s = alloc(&P.B[e], vb)) != EI_OK) { free_prepared(P); return s; }
-    const double kx = 1.0 / (2.0 * c->dx[0] * c->dx[0]);
-    EI_TRY_CUDA(launch_fill_coef(P.D, fmt, n, c->Du, c->prec, c->Dc, kx, c->stream));
-    for (int e = 0; e < 3; ++e) {
-      const bool active = e < c->sd.dim;
-      EI_TRY_CUDA(launch_fill_coef(P.B[e], fmt, n, active ? c->bu[e] : nullptr, c->prec,
-                                   active ? c->bcst[e] : 0.0, 1.0 / (2.0 * c->dx[e]), c->stream));
+    P.coef7 = (fmt != VF_F32);
+    if (P.coef7) {
+      for (int k = 0; k < 6; ++k)
+        if ((s = take(&P.a[k], vb)) != EI_OK) { free_prepared(P); return s; }
+      if ((s = take(&P.diagA, vb)) != EI_OK) { free_prepared(P); return s; }
+      const void* bptr[3] = {c->bu[0], c->bu[1], c->bu[2]};
+      EI_LAUNCH(launch_stencil_coef(c->sd, c->prec, c->dx, c->Du, c->Dc, bptr, c->bcst, c->cu,
+                                    c->cc, P.a, P.diagA, fmt, c->stream));
+    } else {
+      if ((s = take(&P.D, vb)) != EI_OK) { free_prepared(P); return s; }
+      for (int e = 0; e < 3; ++e)
+        if ((s = take(&P.B[e], vb)) != EI_OK) { free_prepared(P); return s; }
+      const double kx = 1.0 / (2.0 * c->dx[0] * c->dx[0]);
+      EI_LAUNCH(launch_fill_coef(P.D, fmt, n, nx, ny, pitch, c->Du, c->prec, c->Dc, kx, c->stream));
+      for (int e = 0; e < 3; ++e) {
+        const bool active = e < c->sd.dim;
+        EI_LAUNCH(launch_fill_coef(P.B[e], fmt, n, nx, ny, pitch, active ? c->bu[e] : nullptr,
+                                   c->prec, active ? c->bcst[e] : 0.0, 1.0 / (2.0 * c->dx[e]),
+                                   c->stream));
+      }
+      EI_LAUNCH(launch_fill_coef(P.cbase, fmt, n, nx, ny, pitch, c->cu, c->prec, c->cc, 1.0,
+                                 c->stream));
     }
-    EI_TRY_CUDA(launch_fill_coef(P.cbase, fmt, n, c->cu, c->prec, c->cc, 1.0, c->stream));
+    // tensor maps over the padded arrays
+    const int eb = (int)vec_elem_bytes(fmt);
+    const void* ins[4] = {P.v, P.r, P.w[0], P.w[1]};
+    bool ok = true;
+    for (int i = 0; i < 4; ++i) ok = ok && encode_map(&P.map_in[i], ins[i], eb, c->sd, 1);
+    if (P.coef7) {
+      for (int k = 0; k < 6; ++k) ok = ok && encode_map(&P.map_c[k], P.a[k], eb, c->sd, 0);
+      ok = ok && encode_map(&P.map_diagA, P.diagA, eb, c->sd, 0);
+    } else {
+      ok = ok && encode_map(&P.map_c[0], P.D, eb, c->sd, 1);
+      for (int e = 0; e < 3; ++e) ok = ok && encode_map(&P.map_c[1 + e], P.B[e], eb, c->sd, 0);
+      ok = ok && encode_map(&P.map_cbase, P.cbase, eb, c->sd, 0);
+    }
+    ok = ok && encode_map(&P.map_qc, P.qc, eb, c->sd, 0);
+    ok = ok && encode_map(&P.map_p, P.p, 8, c->sd, 0);
+    if (!ok) { free_prepared(P); return EI_ERR_CUDA; }
   } else {
     if ((s = alloc(&P.csr_val, vec_elem_bytes(fmt) * (size_t)c->nnz)) != EI_OK) { free_prepared(P); return s; }
-    EI_TRY_CUDA(launch_fill_coef(P.csr_val, fmt, c->nnz, c->val_u, c->prec, 0.0, 1.0, c->stream));
-    EI_TRY_CUDA(launch_fill_coef(P.cbase, fmt, n, c->diag_u, c->prec, 0.0, 1.0, c->stream));
+    EI_LAUNCH(launch_fill_coef(P.csr_val, fmt, c->nnz, (int)c->nnz, 1, (int)c->nnz, c->val_u,
+                               c->prec, 0.0, 1.0, c->stream));
+    EI_LAUNCH(launch_fill_coef(P.cbase, fmt, n, nx, ny, pitch, c->diag_u, c->prec, 0.0, 1.0,
+                               c->stream));
   }
   P.ready = true;
   return EI_OK;
 }
 
-static StencilDev stencil_view(const ei_ctx* c, const Prepared& P, const void* qc) {
+// the fixed diagonal of A in this format's layout (stencil coef7: diagA; flux
+// form and CSR: c / diag)
+static void* base_diag(Prepared& P) { return P.coef7 ? P.diagA : P.cbase; }
+
+static StencilDev stencil_view(const ei_ctx* c, const Prepared& P, const void* diag) {
   StencilDev s = c->sd;
+  s.coef7 = P.coef7 ? 1 : 0;
+  for (int k = 0; k < 6; ++k) s.a[k] = P.a[k];
+  s.diag = diag;
   s.D = P.D;
   for (int e = 0; e < 3; ++e) s.B[e] = P.B[e];
-  s.qc = qc;
+  s.qc = diag;
   return s;
 }
 
@@ -201,12 +277,13 @@ static ei_status read_ctl(ei_ctx* c) {
 }
 
 static ei_status reset_done(ei_ctx* c) {
-  EI_TRY_CUDA(cudaMemsetAsync(&c->ctl->done, 0, 2 * sizeof(int), c->stream));
+  EI_TRY_CUDA(cudaMemsetAsync(&c->ctl->done, 0, 3 * sizeof(int), c->stream));  // done, degree, err
   return EI_OK;
 }
 
 static cudaError_t op_residual(ei_ctx* c, Prepared& P, const void* qc, const void* y,
                                const void* v, void* r) {
+  ++c->launches;
   if (c->kind == KIND_STENCIL)
     return launch_stencil_residual(stencil_view(c, P, qc), y, v, r, P.fmt, c->partials, c->ctl,
                                    c->stream);
@@ -215,9 +292,26 @@ static cudaError_t op_residual(ei_ctx* c, Prepared& P, const void* qc, const voi
 
 static cudaError_t op_newton(ei_ctx* c, Prepared& P, const void* qc, const void* w_in,
                              void* w_out, const NewtonScalars& s) {
-  if (c->kind == KIND_STENCIL)
-    return launch_stencil_newton(stencil_view(c, P, qc), w_in, w_out, P.p, s, P.fmt, c->partials,
-                                 c->ctl, c->stream);
+  ++c->launches;
+  if (c->kind == KIND_STENCIL) {
+    NewtonMaps M;
+    const void* ins[4] = {P.v, P.r, P.w[0], P.w[1]};
+    int wi = -1;
+    for (int i = 0; i < 4; ++i)
+      if (ins[i] == w_in) wi = i;
+    if (wi < 0) return cudaErrorInvalidValue;
+    M.w = P.map_in[wi];
+    for (int k = 0; k < 6; ++k) M.c[k] = P.map_c[k];
+    const CUtensorMap& md = (qc == P.qc) ? P.map_qc : (P.coef7 ? P.map_diagA : P.map_cbase);
+    if (P.coef7) {
+      M.c[6] = md;
+    } else {
+      M.c[4] = md;  // flux form: D, B0, B1, B2, diagonal term
+    }
+    M.p = P.map_p;
+    return launch_newton_tma(stencil_view(c, P, qc), M, w_out, P.p, s, P.fmt, c->partials,
+                             c->ctl, c->stream);
+  }
   return launch_csr_newton(csr_view(c, P, qc), w_in, w_out, P.p, s, P.fmt, c->partials, c->ctl,
                            c->stream);
 }
@@ -234,6 +328,13 @@ static ei_status newton_loop(ei_ctx* c, Prepared& P, const void* qc, const void*
   s.inv_gamma = 1.0 / gamma;
   s.tol = tol;
   s.m_max = m_max;
+  if (c->profile && c->ev.size() < (size_t)(2 * m_max + 2)) {
+    while (c->ev.size() < (size_t)(2 * m_max + 2)) {
+      cudaEvent_t e;
+      EI_TRY_CUDA(cudaEventCreate(&e));
+      c->ev.push_back(e);
+    }
+  }
   int j = 0;
   int batch = m_pred > 0 ? m_pred : 8;
   while (true) {
@@ -243,13 +344,27 @@ static ei_status newton_loop(ei_ctx* c, Prepared& P, const void* qc, const void*
       s.d_next = d[j + 1];
       s.shift = cc / gamma + xi[j];
       const void* w_in = (j == 0) ? r : P.w[(j - 1) & 1];
+      if (c->profile) EI_TRY_CUDA(cudaEventRecord(c->ev[2 * j], c->stream));
       EI_TRY_CUDA(op_newton(c, P, qc, w_in, P.w[j & 1], s));
+      if (c->profile) EI_TRY_CUDA(cudaEventRecord(c->ev[2 * j + 1], c->stream));
     }
     EI_TRY(read_ctl(c));
     const int done = c->h_ctl->done;
-    if (done == 1) { *deg = c->h_ctl->degree; *ok = 1; return EI_OK; }
-    if (done == 2) { *deg = c->h_ctl->degree; *ok = 0; return EI_OK; }
+    if (done == 1 || done == 2) {
+      *deg = c->h_ctl->degree;
+      *ok = (done == 1);
+      if (c->profile) {  // launches j < degree did the work; later ones exited at once
+        for (int i = 0; i < *deg && i < j; ++i) {
+          float ms = 0.f;
+          EI_TRY_CUDA(cudaEventElapsedTime(&ms, c->ev[2 * i], c->ev[2 * i + 1]));
+          c->newton_ms += ms;
+          ++c->newton_timed;
+        }
+      }
+      return EI_OK;
+    }
     if (done == 4) return EI_ERR_NONFINITE;
+    if (done == 5) return EI_ERR_TIMEOUT;
     if (j >= m_max) { *deg = m_max; *ok = 0; return EI_OK; }
     batch = 8;
   }
@@ -286,7 +401,7 @@ static ei_status phi1_substeps(ei_ctx* c, Prepared& P, const void* qc, double h,
   while (s <= (1 << 20)) {
     const double tau = h / s;
     divided_differences(1, tau, cc, gamma, m_max, d.data());
-    if (s > 1) EI_TRY_CUDA(launch_zero(P.y, P.fmt, c->n, c->stream));
+    if (s > 1) EI_LAUNCH(launch_zero(P.y, P.fmt, P.n_alloc, c->stream));
     bool ok_all = true;
     int dsum = 0, dmax = 0;
     for (int i = 0; i < s; ++i) {
@@ -303,7 +418,7 @@ static ei_status phi1_substeps(ei_ctx* c, Prepared& P, const void* qc, double h,
       if (st && i < EI_STATS_MAX_SUBSTEPS) st->degrees[i] = deg;
       dsum += deg;
       if (deg > dmax) dmax = deg;
-      if (s > 1) EI_TRY_CUDA(launch_axpy(P.y, P.p, P.fmt, c->n, tau, c->stream));
+      if (s > 1) EI_LAUNCH(launch_axpy(P.y, P.p, P.fmt, P.n_alloc, tau, c->stream));
     }
     if (ok_all) {
       if (st) {
@@ -392,6 +507,7 @@ void ei_destroy(ei_ctx* c) {
   cudaSetDevice(c->device);
   cudaStreamSynchronize(c->stream);
   free_operator(c);
+  for (cudaEvent_t e : c->ev) cudaEventDestroy(e);
   if (c->ctl) cudaFree(c->ctl);
   if (c->h_ctl) cudaFreeHost(c->h_ctl);
   delete c;
@@ -436,6 +552,7 @@ ei_status ei_set_operator_stencil(ei_ctx* c, int dim, const int64_t n[3], const 
   s.nx = (int)ext[0];
   s.ny = (int)ext[1];
   s.nz = (int)ext[2];
+  s.pitch = (int)((ext[0] + 3) / 4 * 4);  // rows start on 16-byte boundaries
   for (int f = 0; f < 6; ++f) s.bc[f] = (f < 2 * dim) ? bc[f] : EI_BC_NEUMANN0;
   for (int e = 0; e < 3; ++e) c->dx[e] = (e < dim) ? dx[e] : 1.0;
   s.uniform = 1;
@@ -452,7 +569,7 @@ ei_status ei_set_operator_stencil(ei_ctx* c, int dim, const int64_t n[3], const 
   c->cu = cdiag;
   c->cc = c_const;
   // Gershgorin rows of A (FP64 from the caller's arrays) and reduction space
-  int nb = stencil_blocks(s);
+  int nb = newton_tma_blocks(s);
   if (nb < reduction_capacity()) nb = reduction_capacity();
   c->max_blocks = nb;
   ei_status st;
@@ -516,10 +633,36 @@ ei_status ei_estimate_spectrum(ei_ctx* c, double* alpha, double* beta) {
   return EI_OK;
 }
 
+static void acct_begin(ei_ctx* c, const ei_options* opt) {
+  c->launches = 0;
+  c->newton_timed = 0;
+  c->newton_ms = 0.0;
+  c->profile = opt && opt->profile;
+}
+
+static void acct_end(ei_ctx* c, ei_stats* st) {
+  if (!st) return;
+  st->launches = c->launches;
+  st->newton_timed = c->newton_timed;
+  st->newton_ms = c->newton_ms;
+}
+
+static ei_status phi_apply_impl(ei_ctx* c, int k, double h, const void* v, void* out, double tol,
+                                const ei_options* opt, ei_stats* st);
+
 ei_status ei_phi_apply(ei_ctx* c, int k, double h, const void* v, void* out, double tol,
                        const ei_options* opt, ei_stats* st) {
   stats_reset(st);
   if (!c || !v || !out) return EI_ERR_INVALID_ARG;
+  acct_begin(c, opt);
+  ei_status rc = phi_apply_impl(c, k, h, v, out, tol, opt, st);
+  acct_end(c, st);
+  log_stats("phi_apply", st, rc);
+  return rc;
+}
+
+static ei_status phi_apply_impl(ei_ctx* c, int k, double h, const void* v, void* out, double tol,
+                                const ei_options* opt, ei_stats* st) {
   if (c->kind == KIND_NONE) return EI_ERR_STATE;
   if (k < 0 || k > 8 || !(h > 0) || !isfinite(h) || !(tol > 0) || !isfinite(tol))
     return EI_ERR_INVALID_ARG;
@@ -528,7 +671,8 @@ ei_status ei_phi_apply(ei_ctx* c, int k, double h, const void* v, void* out, dou
   EI_TRY(prepare(c, fmt));
   Prepared& P = c->prep[fmt];
   const int64_t n = c->n;
-  EI_TRY_CUDA(launch_import(P.v, fmt, v, c->prec, n, c->partials, c->ctl, c->stream));
+  EI_LAUNCH(launch_import(P.v, fmt, v, c->prec, n, geo_nx(c), c->kind == KIND_STENCIL ? c->sd.ny : 1, geo_pitch(c), c->partials, c->ctl,
+                         c->stream));
   EI_TRY(read_ctl(c));
   if (c->h_ctl->sum1 != 1.0) return EI_ERR_NONFINITE;
   const double vnorm2 = c->h_ctl->sum0;
@@ -537,12 +681,13 @@ ei_status ei_phi_apply(ei_ctx* c, int k, double h, const void* v, void* out, dou
   interval(alpha, beta, &cc, &gamma);
   if (st) { st->alpha = alpha; st->beta = beta; st->s = 1; }
   if (vnorm2 == 0.0) {  // phi_k(hA) 0 = 0
-    EI_TRY_CUDA(launch_export(out, c->prec, P.v, fmt, 0, n, 0.0, c->stream));
+    EI_LAUNCH(launch_export(out, c->prec, P.v, fmt, 0, n, geo_nx(c), c->kind == KIND_STENCIL ? c->sd.ny : 1, geo_pitch(c), 0.0, c->stream));
     EI_TRY_CUDA(cudaStreamSynchronize(c->stream));
     return EI_OK;
   }
   if (gamma == 0.0) {  // A = cI
-    EI_TRY_CUDA(launch_export(out, c->prec, P.v, fmt, 0, n, phi_scalar(k, h * cc), c->stream));
+    EI_LAUNCH(launch_export(out, c->prec, P.v, fmt, 0, n, geo_nx(c), c->kind == KIND_STENCIL ? c->sd.ny : 1, geo_pitch(c), phi_scalar(k, h * cc),
+                         c->stream));
     EI_TRY_CUDA(cudaStreamSynchronize(c->stream));
     return EI_OK;
   }
@@ -551,9 +696,9 @@ ei_status ei_phi_apply(ei_ctx* c, int k, double h, const void* v, void* out, dou
     const void* res = nullptr;
     int is_p = 0;
     double scale = 1.0;
-    rc = phi1_substeps(c, P, P.cbase, h, alpha, beta, tol, opt, st, &res, &is_p, &scale);
+    rc = phi1_substeps(c, P, base_diag(P), h, alpha, beta, tol, opt, st, &res, &is_p, &scale);
     if (rc == EI_OK) {
-      EI_TRY_CUDA(launch_export(out, c->prec, res, fmt, is_p, n, scale / h, c->stream));
+      EI_LAUNCH(launch_export(out, c->prec, res, fmt, is_p, n, geo_nx(c), c->kind == KIND_STENCIL ? c->sd.ny : 1, geo_pitch(c), scale / h, c->stream));
       EI_TRY_CUDA(cudaStreamSynchronize(c->stream));
     }
   } else {
@@ -574,11 +719,11 @@ ei_status ei_phi_apply(ei_ctx* c, int k, double h, const void* v, void* out, dou
       const void* cur = P.v;
       for (int i = 0; i < s; ++i) {
         if (i > 0) {
-          EI_TRY_CUDA(launch_p_to_vec(P.r, P.p, fmt, n, c->stream));
+          EI_LAUNCH(launch_p_to_vec(P.r, P.p, fmt, P.n_alloc, c->stream));
           cur = P.r;
         }
         int deg = 0, ok = 0;
-        EI_TRY(newton_loop(c, P, P.cbase, cur, d, cc, gamma, tol, m_max, m_pred, &deg, &ok));
+        EI_TRY(newton_loop(c, P, base_diag(P), cur, d, cc, gamma, tol, m_max, m_pred, &deg, &ok));
         if (st) st->matvecs += deg;
         if (!ok) { ok_all = false; break; }
         if (st && i < EI_STATS_MAX_SUBSTEPS) st->degrees[i] = deg;
@@ -589,7 +734,7 @@ ei_status ei_phi_apply(ei_ctx* c, int k, double h, const void* v, void* out, dou
         if (st) {
           st->s = s; st->restarts = restarts; st->degree_sum = dsum; st->degree_max = dmax;
         }
-        EI_TRY_CUDA(launch_export(out, c->prec, P.p, fmt, 1, n, 1.0, c->stream));
+        EI_LAUNCH(launch_export(out, c->prec, P.p, fmt, 1, n, geo_nx(c), c->kind == KIND_STENCIL ? c->sd.ny : 1, geo_pitch(c), 1.0, c->stream));
         EI_TRY_CUDA(cudaStreamSynchronize(c->stream));
         rc = EI_OK;
         break;
@@ -598,7 +743,6 @@ ei_status ei_phi_apply(ei_ctx* c, int k, double h, const void* v, void* out, dou
       s *= 2;
     }
   }
-  log_stats("phi_apply", st, rc);
   return rc;
 }
 
@@ -610,16 +754,17 @@ static ei_status step_impl(ei_ctx* c, int method, double h, void* u, int nonlin,
   const int64_t n = c->n;
   const int rosen = (method == EI_EXP_ROSENBROCK);
   // import u; F = A u + g(u); J's diagonal; the interval of J
-  EI_TRY_CUDA(launch_import(P.u, fmt, u, c->prec, n, c->partials, c->ctl, c->stream));
+  EI_LAUNCH(launch_import(P.u, fmt, u, c->prec, n, geo_nx(c), c->kind == KIND_STENCIL ? c->sd.ny : 1, geo_pitch(c), c->partials, c->ctl,
+                         c->stream));
   if (c->kind == KIND_STENCIL) {
-    EI_TRY_CUDA(launch_stencil_F(stencil_view(c, P, P.cbase), P.u, P.v, P.qc, P.cbase, nonlin,
-                                 rosen, fmt, c->partials, c->ctl, c->stream));
+    EI_LAUNCH(launch_stencil_F(stencil_view(c, P, base_diag(P)), P.u, P.v, base_diag(P), P.qc,
+                               nonlin, rosen, fmt, c->partials, c->ctl, c->stream));
   } else {
-    EI_TRY_CUDA(launch_csr_F(csr_view(c, P, P.cbase), P.u, P.v, P.qc, P.cbase, nonlin, rosen,
+    EI_LAUNCH(launch_csr_F(csr_view(c, P, P.cbase), P.u, P.v, P.qc, P.cbase, nonlin, rosen,
                              fmt, c->partials, c->ctl, c->stream));
   }
   if (rosen)
-    EI_TRY_CUDA(launch_shifted_minmax(n, c->ger_lo, c->ger_hi, u, c->prec, nonlin, c->partials,
+    EI_LAUNCH(launch_shifted_minmax(n, c->ger_lo, c->ger_hi, u, c->prec, nonlin, c->partials,
                                       c->ctl, c->stream));
   EI_TRY(read_ctl(c));
   if (c->h_ctl->sum1 != 1.0) return EI_ERR_NONFINITE;
@@ -631,9 +776,10 @@ static ei_status step_impl(ei_ctx* c, int method, double h, void* u, int nonlin,
   if (fnorm2 == 0.0) return EI_OK;  // u is an equilibrium: u_{n+1} = u_n
   double cc, gamma;
   interval(alpha, beta, &cc, &gamma);
-  const void* qc = rosen ? P.qc : P.cbase;
+  const void* qc = rosen ? P.qc : base_diag(P);
   if (gamma == 0.0) {  // J = cI: z(h) = h phi_1(hc) F
-    EI_TRY_CUDA(launch_add_export(u, c->prec, P.v, fmt, 0, n, h * phi_scalar(1, h * cc), c->stream));
+    EI_LAUNCH(launch_add_export(u, c->prec, P.v, fmt, 0, n, geo_nx(c), c->kind == KIND_STENCIL ? c->sd.ny : 1, geo_pitch(c),
+                            h * phi_scalar(1, h * cc), c->stream));
     EI_TRY_CUDA(cudaStreamSynchronize(c->stream));
     return EI_OK;
   }
@@ -641,7 +787,7 @@ static ei_status step_impl(ei_ctx* c, int method, double h, void* u, int nonlin,
   int is_p = 0;
   double scale = 1.0;
   EI_TRY(phi1_substeps(c, P, qc, h, alpha, beta, tol, opt, st, &res, &is_p, &scale));
-  EI_TRY_CUDA(launch_add_export(u, c->prec, res, fmt, is_p, n, scale, c->stream));
+  EI_LAUNCH(launch_add_export(u, c->prec, res, fmt, is_p, n, geo_nx(c), c->kind == KIND_STENCIL ? c->sd.ny : 1, geo_pitch(c), scale, c->stream));
   EI_TRY_CUDA(cudaStreamSynchronize(c->stream));
   return EI_OK;
 }
@@ -656,7 +802,9 @@ ei_status ei_step(ei_ctx* c, int method, double h, void* u, int nonlin, double t
       !(tol > 0) || !isfinite(tol))
     return EI_ERR_INVALID_ARG;
   EI_TRY_CUDA(cudaSetDevice(c->device));
+  acct_begin(c, opt);
   ei_status rc = step_impl(c, method, h, u, nonlin, tol, opt, st);
+  acct_end(c, st);
   log_stats("step", st, rc);
   return rc;
 }

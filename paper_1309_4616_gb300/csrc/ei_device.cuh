@@ -1,0 +1,171 @@
+// Device-side building blocks shared by the kernel translation units:
+// arithmetic over the three vector formats (float-float pairs, double,
+// float), loads and stores, block reductions and the last-block pattern.
+#pragma once
+#include <cuda_runtime.h>
+#include <math.h>
+#include <stdint.h>
+
+#include "df.cuh"
+#include "ei_internal.h"
+
+namespace ei {
+
+#define EI_BX 32
+#define EI_BY 8
+#define EI_ZC 16
+#define EI_TPB 256
+
+// ---------------------------------------------------------------------------
+// scalar arithmetic over the three formats
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ double add(double a, double b) { return a + b; }
+__device__ __forceinline__ double sub(double a, double b) { return a - b; }
+__device__ __forceinline__ double mul(double a, double b) { return a * b; }
+__device__ __forceinline__ double mac(double acc, double a, double b) { return fma(a, b, acc); }
+__device__ __forceinline__ float add(float a, float b) { return a + b; }
+__device__ __forceinline__ float sub(float a, float b) { return a - b; }
+__device__ __forceinline__ float mul(float a, float b) { return a * b; }
+__device__ __forceinline__ float mac(float acc, float a, float b) { return fmaf(a, b, acc); }
+__device__ __forceinline__ df add(df a, df b) { return df_add(a, b); }
+__device__ __forceinline__ df sub(df a, df b) { return df_sub(a, b); }
+__device__ __forceinline__ df mul(df a, df b) { return df_mul(a, b); }
+__device__ __forceinline__ df mac(df acc, df a, df b) { return df_mac(acc, a, b); }
+
+template <class T> __device__ __forceinline__ T zero();
+template <> __device__ __forceinline__ double zero<double>() { return 0.0; }
+template <> __device__ __forceinline__ float zero<float>() { return 0.0f; }
+template <> __device__ __forceinline__ df zero<df>() { return df{0.0f, 0.0f}; }
+
+template <class T> __device__ __forceinline__ T from_d(double x);
+template <> __device__ __forceinline__ double from_d<double>(double x) { return x; }
+template <> __device__ __forceinline__ float from_d<float>(double x) { return (float)x; }
+template <> __device__ __forceinline__ df from_d<df>(double x) { return df_from_double(x); }
+
+__device__ __forceinline__ double to_d(double x) { return x; }
+__device__ __forceinline__ double to_d(float x) { return (double)x; }
+__device__ __forceinline__ double to_d(df x) { return df_to_double(x); }
+
+// widen a vector value to the Newton-sum type
+__device__ __forceinline__ df to_p(df x) { return x; }
+__device__ __forceinline__ df to_p(float x) { return df{x, 0.0f}; }
+__device__ __forceinline__ double to_p(double x) { return x; }
+
+__device__ __forceinline__ bool finite_d(double x) { return isfinite(x); }
+
+// loads / stores (read-only path for data the kernel does not write)
+__device__ __forceinline__ df ldg(const df* p, int64_t i) {
+  float2 v = __ldg(reinterpret_cast<const float2*>(p) + i);
+  return df{v.x, v.y};
+}
+__device__ __forceinline__ double ldg(const double* p, int64_t i) { return __ldg(p + i); }
+__device__ __forceinline__ float ldg(const float* p, int64_t i) { return __ldg(p + i); }
+__device__ __forceinline__ df ld(const df* p, int64_t i) {
+  float2 v = reinterpret_cast<const float2*>(p)[i];
+  return df{v.x, v.y};
+}
+__device__ __forceinline__ double ld(const double* p, int64_t i) { return p[i]; }
+__device__ __forceinline__ float ld(const float* p, int64_t i) { return p[i]; }
+__device__ __forceinline__ void st(df* p, int64_t i, df v) {
+  reinterpret_cast<float2*>(p)[i] = make_float2(v.hi, v.lo);
+}
+__device__ __forceinline__ void st(double* p, int64_t i, double v) { p[i] = v; }
+__device__ __forceinline__ void st(float* p, int64_t i, float v) { p[i] = v; }
+
+template <int FMT> struct VT;
+template <> struct VT<VF_DF> { using T = df; using P = df; };
+template <> struct VT<VF_F64> { using T = double; using P = double; };
+template <> struct VT<VF_F32> { using T = float; using P = df; };
+
+// ---------------------------------------------------------------------------
+// block reductions and the last-block pattern
+// ---------------------------------------------------------------------------
+enum { RED_SUM = 0, RED_MINMAX = 1 };
+
+template <int OP>
+__device__ __forceinline__ void comb(double& a, double& b, double a2, double b2) {
+  if (OP == RED_SUM) {
+    a += a2;
+    b += b2;
+  } else {
+    a = fmin(a, a2);
+    b = fmax(b, b2);
+  }
+}
+
+// Reduce (a, b) over the block; result valid in thread 0.  Fixed order.
+template <int OP>
+__device__ __forceinline__ void block_reduce2(double& a, double& b) {
+  __shared__ double sa[32], sb[32];
+  const int tid = threadIdx.x + blockDim.x * (threadIdx.y + blockDim.y * threadIdx.z);
+  const int nthr = blockDim.x * blockDim.y * blockDim.z;
+  const int lane = tid & 31, wid = tid >> 5;
+#pragma unroll
+  for (int off = 16; off > 0; off >>= 1) {
+    double a2 = __shfl_down_sync(0xffffffffu, a, off);
+    double b2 = __shfl_down_sync(0xffffffffu, b, off);
+    comb<OP>(a, b, a2, b2);
+  }
+  if (lane == 0) {
+    sa[wid] = a;
+    sb[wid] = b;
+  }
+  __syncthreads();
+  const int nw = (nthr + 31) >> 5;
+  if (wid == 0) {
+    if (OP == RED_SUM) {
+      a = lane < nw ? sa[lane] : 0.0;
+      b = lane < nw ? sb[lane] : 0.0;
+    } else {
+      a = lane < nw ? sa[lane] : INFINITY;
+      b = lane < nw ? sb[lane] : -INFINITY;
+    }
+#pragma unroll
+    for (int off = 16; off > 0; off >>= 1) {
+      double a2 = __shfl_down_sync(0xffffffffu, a, off);
+      double b2 = __shfl_down_sync(0xffffffffu, b, off);
+      comb<OP>(a, b, a2, b2);
+    }
+  }
+  __syncthreads();
+}
+
+// Every block publishes its pair; the last block to arrive reduces all pairs
+// in block order and returns true (in all its threads) with the totals.
+template <int OP>
+__device__ bool last_block_reduce2(double& a, double& b, double* partials, DevCtl* ctl) {
+  __shared__ bool am_last;
+  const int tid = threadIdx.x + blockDim.x * (threadIdx.y + blockDim.y * threadIdx.z);
+  const int nthr = blockDim.x * blockDim.y * blockDim.z;
+  const unsigned nblk = gridDim.x * gridDim.y * gridDim.z;
+  const unsigned bid = blockIdx.x + gridDim.x * (blockIdx.y + gridDim.y * blockIdx.z);
+  block_reduce2<OP>(a, b);
+  if (tid == 0) {
+    partials[2 * bid] = a;
+    partials[2 * bid + 1] = b;
+    __threadfence();
+    unsigned t = atomicAdd(&ctl->count, 1u);
+    am_last = (t == nblk - 1);
+  }
+  __syncthreads();
+  if (!am_last) return false;
+  __threadfence();
+  double ra = (OP == RED_SUM) ? 0.0 : INFINITY, rb = (OP == RED_SUM) ? 0.0 : -INFINITY;
+  for (unsigned i = tid; i < nblk; i += nthr) {
+    comb<OP>(ra, rb, __ldcg(partials + 2 * i), __ldcg(partials + 2 * i + 1));
+  }
+  block_reduce2<OP>(ra, rb);
+  __shared__ double fa, fb;
+  if (tid == 0) {
+    fa = ra;
+    fb = rb;
+    ctl->count = 0;
+  }
+  __syncthreads();
+  a = fa;
+  b = fb;
+  return true;
+}
+
+
+}  // namespace ei

@@ -1,6 +1,7 @@
 // Internal interface between the host orchestration (ei_api.cpp) and the
-// CUDA kernels (ei_kernels.cu).  Not part of the public ABI.
+// CUDA kernels (ei_kernels.cu, ei_newton_tma.cu).  Not part of the public ABI.
 #pragma once
+#include <cuda.h>
 #include <cuda_runtime.h>
 #include <stdint.h>
 
@@ -13,26 +14,31 @@ enum VecFmt { VF_DF = 0, VF_F64 = 1, VF_F32 = 2 };
 // the results of the small reductions.  One per context.
 struct DevCtl {
   unsigned int count;  // arrivals of the current launch (reset by its last block)
-  int done;            // Newton: 0 running, 1 converged, 2 m_max reached, 3 zero input, 4 non-finite
+  int done;            // Newton: 0 running, 1 converged, 2 m_max reached,
+                       //         4 non-finite, 5 a bounded device wait ran out
   int degree;          // Newton degree at stop
-  int pad;
+  int err;             // set by a block whose bounded wait ran out
   double sum0, sum1;   // import / F / residual: squared norm, finiteness flag (1 = finite)
   double mn, mx;       // Gershgorin reductions: min_i (a_ii - r_i), max_i (a_ii + r_i)
   double nw2, np2;     // squared norms of the last Newton iterate / sum
 };
 
-// Stencil operator as the kernels see it.  Arrays are in the context's
-// vector format (df pairs, double or float); D is pre-scaled by 1/(2 dx_x^2),
-// B_e by 1/(2 dx_e); qc is the diagonal term (c_i + g'(u_i)).
+// Grid geometry of the stencil operator.  Library-owned arrays are stored
+// with a padded row pitch (a multiple of 4 elements, so every row starts on a
+// 16-byte boundary as TMA requires): element (x, y, z) is at
+// (z*ny + y)*pitch + x; padding elements hold zeros.
 struct StencilDev {
   int dim;
-  int nx, ny, nz;
+  int nx, ny, nz, pitch;
   int bc[6];
-  const void* D;
-  const void* B[3];
-  const void* qc;
-  double ratio[3];     // k_e / k_x with k_e = 1/(2 dx_e^2)
-  int uniform;         // all ratios == 1
+  int coef7;           // 1: explicit coefficients a[6] + diag; 0: flux form D, B, qc
+  const void* a[6];    // coef7: neighbour coefficients x-, x+, y-, y+, z-, z+ (0 at a boundary)
+  const void* diag;    // coef7: diagonal of the operator in use (A, or J = A + diag g'(u))
+  const void* D;       // flux form: D / (2 dx_x^2)
+  const void* B[3];    // flux form: b_e / (2 dx_e)
+  const void* qc;      // flux form: diagonal term c_i (+ g'(u_i))
+  double ratio[3];     // flux form: k_e / k_x with k_e = 1/(2 dx_e^2)
+  int uniform;         // flux form: all ratios == 1
 };
 
 // CSR operator: y = W x + diag .* x.
@@ -40,8 +46,8 @@ struct CsrDev {
   int64_t n;
   const int64_t* rowptr;
   const int32_t* col;
-  const void* val;     // W values (double or float, matching the precision)
-  const void* qc;      // diagonal (c + g'), in vector format
+  const void* val;     // W values in the vector format
+  const void* qc;      // diagonal, in the vector format
 };
 
 struct NewtonScalars {
@@ -54,76 +60,91 @@ struct NewtonScalars {
   int m_max;
 };
 
-// ---- launchers (all asynchronous on `st`) ----------------------------------
-// number of blocks the stencil kernels use for a grid (partials capacity)
-int stencil_blocks(const StencilDev& op);
-int csr_blocks(int64_t n);
-// upper bound of the block count of every grid-stride (elementwise, CSR) kernel
-int reduction_capacity();
+// Tensor maps of the TMA-staged Newton kernel (3D maps over the padded
+// arrays; x extent = nx, so columns beyond nx and planes outside [0, nz) read
+// as zeros).
+struct NewtonMaps {
+  CUtensorMap w;       // w_in, halo box
+  CUtensorMap c[7];    // coef7: a[0..5], diag (interior box); flux: D (halo box), B0..2, qc
+  CUtensorMap p;       // Newton sum, interior box
+};
 
-// Per-row Gershgorin bounds of the stencil operator A (FP64, from the user's
-// arrays), written to lo/hi, and their min/max reduced into ctl->mn/mx.
-cudaError_t launch_stencil_gershgorin(const StencilDev& user, int user_prec, const double dx[3],
-                                      const void* Duser, double Dconst, const void* const buser[3],
-                                      const double bconst[3], const void* cuser, double cconst,
-                                      double* lo, double* hi, double* partials, DevCtl* ctl,
-                                      cudaStream_t st);
+// ---- launchers (all asynchronous on `st`) ----------------------------------
+int csr_blocks(int64_t n);
+int reduction_capacity();        // block bound of the grid-stride kernels
+int newton_tma_blocks(const StencilDev& op);
+
+// tensor maps: encode one 3D map over a padded array (elem 4 or 8 bytes);
+// halo = 1 widens the box by the 16-byte aligned x halo and one row in y.
+bool encode_map(CUtensorMap* m, const void* base, int elem_bytes, const StencilDev& g, int halo);
+
+// Coefficients of the stencil operator in the vector format (coef7 layout),
+// from the caller's arrays (FP64 arithmetic).
+cudaError_t launch_stencil_coef(const StencilDev& g, int user_prec, const double dx[3],
+                                const void* D, double Dc, const void* const b[3],
+                                const double bc[3], const void* c, double cc, void* const a[6],
+                                void* diag, int fmt, cudaStream_t st);
+// Per-row Gershgorin bounds of the stencil operator A (FP64, from the caller's
+// arrays, contiguous layout), written to lo/hi, min/max into ctl->mn/mx.
+cudaError_t launch_stencil_gershgorin(const StencilDev& g, int user_prec, const double dx[3],
+                                      const void* D, double Dc, const void* const b[3],
+                                      const double bc[3], const void* c, double cc, double* lo,
+                                      double* hi, double* partials, DevCtl* ctl, cudaStream_t st);
 cudaError_t launch_csr_gershgorin(const CsrDev& op, int prec, const void* val_user,
                                   const void* diag_user, double* lo, double* hi,
                                   double* partials, DevCtl* ctl, cudaStream_t st);
-// min/max over rows of (lo + q), (hi + q) with q = g'(u) (Rosenbrock), or of lo, hi
+// min/max over rows of (lo + q), (hi + q) with q = g'(u) (Rosenbrock)
 cudaError_t launch_shifted_minmax(int64_t n, const double* lo, const double* hi, const void* u,
                                   int prec, int nonlin, double* partials, DevCtl* ctl,
                                   cudaStream_t st);
 
-// Fill a coefficient array in vector format from a user array or a constant,
-// times `scale`.
-cudaError_t launch_fill_coef(void* dst, int fmt, int64_t n, const void* src, int src_prec,
-                             double cst, double scale, cudaStream_t st);
-
-// dst (vector format) = src (user precision); sum of squares into ctl->sum0 and
-// a finiteness flag into ctl->sum1 (1 if finite).
-cudaError_t launch_import(void* dst, int fmt, const void* src, int src_prec, int64_t n,
-                          double* partials, DevCtl* ctl, cudaStream_t st);
-// dst (user precision) = scale * src; src in vector format (src_is_p = 0) or
-// in the Newton-sum format (src_is_p = 1)
+// dst (vector format, padded by (nx, ny, pitch)) = scale * (src or cst)
+cudaError_t launch_fill_coef(void* dst, int fmt, int64_t n, int nx, int ny, int pitch,
+                             const void* src, int src_prec, double cst, double scale,
+                             cudaStream_t st);
+// dst (vector format, padded) = src (caller precision, contiguous); squared
+// norm into ctl->sum0, finiteness flag into ctl->sum1.
+cudaError_t launch_import(void* dst, int fmt, const void* src, int src_prec, int64_t n, int nx,
+                          int ny, int pitch, double* partials, DevCtl* ctl, cudaStream_t st);
+// dst (caller precision, contiguous) = scale * src (vector or Newton-sum format)
 cudaError_t launch_export(void* dst, int dst_prec, const void* src, int fmt, int src_is_p,
-                          int64_t n, double scale, cudaStream_t st);
-// u (user precision) += scale * y; y in vector or Newton-sum format
-cudaError_t launch_add_export(void* u, int prec, const void* y, int fmt, int src_is_p,
-                              int64_t n, double scale, cudaStream_t st);
-// dst (vector format) = src (Newton-sum format)
-cudaError_t launch_p_to_vec(void* dst, const void* p, int fmt, int64_t n, cudaStream_t st);
-// y (vector format) += tau * p (p float-float or double)
-cudaError_t launch_axpy(void* y, const void* p, int fmt, int64_t n, double tau, cudaStream_t st);
-cudaError_t launch_zero(void* x, int fmt, int64_t n, cudaStream_t st);
+                          int64_t n, int nx, int ny, int pitch, double scale, cudaStream_t st);
+// u (caller precision, contiguous) += scale * y (vector or Newton-sum format)
+cudaError_t launch_add_export(void* u, int prec, const void* y, int fmt, int src_is_p, int64_t n,
+                              int nx, int ny, int pitch, double scale, cudaStream_t st);
+// elementwise over whole (padded) arrays of n_alloc elements
+cudaError_t launch_p_to_vec(void* dst, const void* p, int fmt, int64_t n_alloc, cudaStream_t st);
+cudaError_t launch_axpy(void* y, const void* p, int fmt, int64_t n_alloc, double tau,
+                        cudaStream_t st);
+cudaError_t launch_zero(void* x, int fmt, int64_t n_alloc, cudaStream_t st);
 
-// Step start: F = A u + g(u) and qc = c + g'(u) (Rosenbrock) or c.  u in vector
-// format.  ||F||^2 into ctl->sum0, finiteness into ctl->sum1.
-cudaError_t launch_stencil_F(const StencilDev& op, const void* u, void* F, void* qc_out,
-                             const void* c_base, int nonlin, int rosenbrock, int fmt,
+// Step start: F = A u + g(u), with A's diagonal from `diag_base` (coef7: the
+// operator's diagonal; flux: c), and diag_out = diag_base + g'(u) (Rosenbrock).
+// u in vector format.  ||F||^2 into ctl->sum0, finiteness into ctl->sum1.
+cudaError_t launch_stencil_F(const StencilDev& op, const void* u, void* F, const void* diag_base,
+                             void* diag_out, int nonlin, int rosenbrock, int fmt,
                              double* partials, DevCtl* ctl, cudaStream_t st);
 cudaError_t launch_csr_F(const CsrDev& op, const void* u, void* F, void* qc_out,
                          const void* c_base, int nonlin, int rosenbrock, int fmt,
                          double* partials, DevCtl* ctl, cudaStream_t st);
 
-// r = A y + v (substep residual, A includes qc); ||r||^2 into ctl->sum0.
+// r = J y + v (substep residual); ||r||^2 into ctl->sum0.
 cudaError_t launch_stencil_residual(const StencilDev& op, const void* y, const void* v, void* r,
                                     int fmt, double* partials, DevCtl* ctl, cudaStream_t st);
 cudaError_t launch_csr_residual(const CsrDev& op, const void* y, const void* v, void* r, int fmt,
                                 double* partials, DevCtl* ctl, cudaStream_t st);
 
-// One Newton iteration j: w_out = (A w_in)/gamma - shift w_in; p += d_{j+1} w_out;
+// One Newton iteration j: w_out = (J w_in)/gamma - shift w_in; p += d_{j+1} w_out;
 // norms and the device-side stop test.  Skips itself when ctl->done != 0.
-cudaError_t launch_stencil_newton(const StencilDev& op, const void* w_in, void* w_out, void* p,
-                                  const NewtonScalars& s, int fmt, double* partials,
-                                  DevCtl* ctl, cudaStream_t st);
+cudaError_t launch_newton_tma(const StencilDev& op, const NewtonMaps& M, void* w_out, void* p,
+                              const NewtonScalars& s, int fmt, double* partials, DevCtl* ctl,
+                              cudaStream_t st);
 cudaError_t launch_csr_newton(const CsrDev& op, const void* w_in, void* w_out, void* p,
                               const NewtonScalars& s, int fmt, double* partials, DevCtl* ctl,
                               cudaStream_t st);
 
-// size in bytes of one vector element / of the p element
+// size in bytes of one vector element / of one Newton-sum element
 inline size_t vec_elem_bytes(int fmt) { return fmt == VF_F32 ? 4 : 8; }
-inline size_t p_elem_bytes(int fmt) { return 8; }
+inline size_t p_elem_bytes(int) { return 8; }
 
 }  // namespace ei

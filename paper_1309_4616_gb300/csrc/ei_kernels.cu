@@ -1,367 +1,260 @@
-// CUDA kernels of the Leja exponential-integrator hot path (sm_103a).
+// CUDA kernels of the Leja exponential-integrator path other than the
+// TMA-staged stencil Newton iteration (ei_newton_tma.cu): operator setup
+// (coefficients, Gershgorin rows), the per-step F = A u + g(u) evaluation, the
+// substep residual, the CSR Newton iteration, and the elementwise moves
+// between the caller's contiguous vectors and the library's padded formats.
 //
-// The hot loop is one fused kernel per Newton iteration (Eq. (3): products
-// (alpha*A + beta*I)x with alpha = 1/gamma, beta = -(c/gamma + xi_j)):
-//     w_{j+1} = (A w_j)/gamma - (c/gamma + xi_j) w_j,   p += d_{j+1} w_{j+1},
-// fused with the squared norms ||w_{j+1}||^2, ||p||^2 (block partials, a
-// fixed-order last-block reduction) and the device-side stop test, so that a
-// whole Newton loop can be launched without host round trips.  A is a
-// matrix-free stencil with the boundary conditions folded in (Sec. III-A) and
-// position-dependent coefficients read from arrays (Sec. III-B), or CSR
-// (Sec. III-D).
-//
-// Vector formats: float-float pairs (FP64-accurate on the FP32 pipes), IEEE
-// double (for comparison), float (reduced-precision form).  The Newton sum p
-// is float-float except in the double format.
+// A is a matrix-free stencil with the boundary conditions folded in (Sec.
+// III-A of the paper) and position-dependent coefficients (Sec. III-B), or a
+// CSR matrix (Sec. III-D).
 #include <cuda_runtime.h>
 #include <math.h>
 #include <stdint.h>
 
-#include "df.cuh"
-#include "ei_internal.h"
+#include "ei_device.cuh"
 
 namespace ei {
 
-#define EI_BX 32
-#define EI_BY 8
-#define EI_ZC 16
-#define EI_TPB 256
-
-// ---------------------------------------------------------------------------
-// scalar arithmetic over the three formats
-// ---------------------------------------------------------------------------
-__device__ __forceinline__ double add(double a, double b) { return a + b; }
-__device__ __forceinline__ double sub(double a, double b) { return a - b; }
-__device__ __forceinline__ double mul(double a, double b) { return a * b; }
-__device__ __forceinline__ double mac(double acc, double a, double b) { return fma(a, b, acc); }
-__device__ __forceinline__ float add(float a, float b) { return a + b; }
-__device__ __forceinline__ float sub(float a, float b) { return a - b; }
-__device__ __forceinline__ float mul(float a, float b) { return a * b; }
-__device__ __forceinline__ float mac(float acc, float a, float b) { return fmaf(a, b, acc); }
-__device__ __forceinline__ df add(df a, df b) { return df_add(a, b); }
-__device__ __forceinline__ df sub(df a, df b) { return df_sub(a, b); }
-__device__ __forceinline__ df mul(df a, df b) { return df_mul(a, b); }
-__device__ __forceinline__ df mac(df acc, df a, df b) { return df_mac(acc, a, b); }
-
-template <class T> __device__ __forceinline__ T zero();
-template <> __device__ __forceinline__ double zero<double>() { return 0.0; }
-template <> __device__ __forceinline__ float zero<float>() { return 0.0f; }
-template <> __device__ __forceinline__ df zero<df>() { return df{0.0f, 0.0f}; }
-
-template <class T> __device__ __forceinline__ T from_d(double x);
-template <> __device__ __forceinline__ double from_d<double>(double x) { return x; }
-template <> __device__ __forceinline__ float from_d<float>(double x) { return (float)x; }
-template <> __device__ __forceinline__ df from_d<df>(double x) { return df_from_double(x); }
-
-__device__ __forceinline__ double to_d(double x) { return x; }
-__device__ __forceinline__ double to_d(float x) { return (double)x; }
-__device__ __forceinline__ double to_d(df x) { return df_to_double(x); }
-
-// widen a vector value to the Newton-sum type
-__device__ __forceinline__ df to_p(df x) { return x; }
-__device__ __forceinline__ df to_p(float x) { return df{x, 0.0f}; }
-__device__ __forceinline__ double to_p(double x) { return x; }
-
-__device__ __forceinline__ bool finite_d(double x) { return isfinite(x); }
-
-// loads / stores (read-only path for data the kernel does not write)
-__device__ __forceinline__ df ldg(const df* p, int64_t i) {
-  float2 v = __ldg(reinterpret_cast<const float2*>(p) + i);
-  return df{v.x, v.y};
-}
-__device__ __forceinline__ double ldg(const double* p, int64_t i) { return __ldg(p + i); }
-__device__ __forceinline__ float ldg(const float* p, int64_t i) { return __ldg(p + i); }
-__device__ __forceinline__ df ld(const df* p, int64_t i) {
-  float2 v = reinterpret_cast<const float2*>(p)[i];
-  return df{v.x, v.y};
-}
-__device__ __forceinline__ double ld(const double* p, int64_t i) { return p[i]; }
-__device__ __forceinline__ void st(df* p, int64_t i, df v) {
-  reinterpret_cast<float2*>(p)[i] = make_float2(v.hi, v.lo);
-}
-__device__ __forceinline__ void st(double* p, int64_t i, double v) { p[i] = v; }
-__device__ __forceinline__ void st(float* p, int64_t i, float v) { p[i] = v; }
-
-template <int FMT> struct VT;
-template <> struct VT<VF_DF> { using T = df; using P = df; };
-template <> struct VT<VF_F64> { using T = double; using P = double; };
-template <> struct VT<VF_F32> { using T = float; using P = df; };
-
-// ---------------------------------------------------------------------------
-// block reductions and the last-block pattern
-// ---------------------------------------------------------------------------
-enum { RED_SUM = 0, RED_MINMAX = 1 };
-
-template <int OP>
-__device__ __forceinline__ void comb(double& a, double& b, double a2, double b2) {
-  if (OP == RED_SUM) {
-    a += a2;
-    b += b2;
-  } else {
-    a = fmin(a, a2);
-    b = fmax(b, b2);
-  }
+// logical point i (x fastest, contiguous) -> padded index
+__device__ __forceinline__ int64_t pidx(int64_t i, int nx, int pitch) {
+  const int64_t t = i / nx;  // z*ny + y
+  return t * pitch + (i - t * nx);
 }
 
-// Reduce (a, b) over the block; result valid in thread 0.  Fixed order.
-template <int OP>
-__device__ __forceinline__ void block_reduce2(double& a, double& b) {
-  __shared__ double sa[32], sb[32];
-  const int tid = threadIdx.x + blockDim.x * (threadIdx.y + blockDim.y * threadIdx.z);
-  const int nthr = blockDim.x * blockDim.y * blockDim.z;
-  const int lane = tid & 31, wid = tid >> 5;
+// ---------------------------------------------------------------------------
+// one row of the stencil operator in FP64 (shared by the Gershgorin bounds and
+// the coefficient arrays): for each axis e and side s,
+//   neighbour inside : a = D_face/dx_e^2 + s*b_e/(2 dx_e), diag -= D_face/dx_e^2
+//   Dirichlet ghost  : a = 0, diag -= D_i/dx_e^2          (ghost u = 0, ghost D = D_i)
+//   Neumann ghost    : a = 0, diag += s*b_e/(2 dx_e)      (ghost u = u_i: no flux)
+// with D_face = (D_i + D_nb)/2, plus diag += c_i.
+// ---------------------------------------------------------------------------
+template <class U>
+__device__ __forceinline__ double uval(const void* p, double cst, int64_t i) {
+  return p ? (double)__ldg(static_cast<const U*>(p) + i) : cst;
+}
+
+struct UserCoef {
+  int dim, nx, ny, nz;
+  int bc[6];
+  double dx[3];
+  const void* D;
+  double Dc;
+  const void* b[3];
+  double bc_[3];
+  const void* c;
+  double cc;
+};
+
+template <class U>
+__device__ __forceinline__ void stencil_row(const UserCoef& u, int64_t i, int x, int y, int z,
+                                            double a[6], double& diag, double& rad) {
+  const int crd[3] = {x, y, z};
+  const int ext[3] = {u.nx, u.ny, u.nz};
+  const int64_t str[3] = {1, u.nx, (int64_t)u.nx * u.ny};
+  const double Di = uval<U>(u.D, u.Dc, i);
+  diag = uval<U>(u.c, u.cc, i);
+  rad = 0.0;
 #pragma unroll
-  for (int off = 16; off > 0; off >>= 1) {
-    double a2 = __shfl_down_sync(0xffffffffu, a, off);
-    double b2 = __shfl_down_sync(0xffffffffu, b, off);
-    comb<OP>(a, b, a2, b2);
-  }
-  if (lane == 0) {
-    sa[wid] = a;
-    sb[wid] = b;
-  }
-  __syncthreads();
-  const int nw = (nthr + 31) >> 5;
-  if (wid == 0) {
-    if (OP == RED_SUM) {
-      a = lane < nw ? sa[lane] : 0.0;
-      b = lane < nw ? sb[lane] : 0.0;
-    } else {
-      a = lane < nw ? sa[lane] : INFINITY;
-      b = lane < nw ? sb[lane] : -INFINITY;
-    }
+  for (int k = 0; k < 6; ++k) a[k] = 0.0;
 #pragma unroll
-    for (int off = 16; off > 0; off >>= 1) {
-      double a2 = __shfl_down_sync(0xffffffffu, a, off);
-      double b2 = __shfl_down_sync(0xffffffffu, b, off);
-      comb<OP>(a, b, a2, b2);
-    }
-  }
-  __syncthreads();
-}
-
-// Every block publishes its pair; the last block to arrive reduces all pairs
-// in block order and returns true (in all its threads) with the totals.
-template <int OP>
-__device__ bool last_block_reduce2(double& a, double& b, double* partials, DevCtl* ctl) {
-  __shared__ bool am_last;
-  const int tid = threadIdx.x + blockDim.x * (threadIdx.y + blockDim.y * threadIdx.z);
-  const int nthr = blockDim.x * blockDim.y * blockDim.z;
-  const unsigned nblk = gridDim.x * gridDim.y * gridDim.z;
-  const unsigned bid = blockIdx.x + gridDim.x * (blockIdx.y + gridDim.y * blockIdx.z);
-  block_reduce2<OP>(a, b);
-  if (tid == 0) {
-    partials[2 * bid] = a;
-    partials[2 * bid + 1] = b;
-    __threadfence();
-    unsigned t = atomicAdd(&ctl->count, 1u);
-    am_last = (t == nblk - 1);
-  }
-  __syncthreads();
-  if (!am_last) return false;
-  __threadfence();
-  double ra = (OP == RED_SUM) ? 0.0 : INFINITY, rb = (OP == RED_SUM) ? 0.0 : -INFINITY;
-  for (unsigned i = tid; i < nblk; i += nthr) {
-    comb<OP>(ra, rb, __ldcg(partials + 2 * i), __ldcg(partials + 2 * i + 1));
-  }
-  block_reduce2<OP>(ra, rb);
-  __shared__ double fa, fb;
-  if (tid == 0) {
-    fa = ra;
-    fb = rb;
-    ctl->count = 0;
-  }
-  __syncthreads();
-  a = fa;
-  b = fb;
-  return true;
-}
-
-// ---------------------------------------------------------------------------
-// the stencil operator at one grid point
-// ---------------------------------------------------------------------------
-// (A w)_i = sum_e r_e [ (D_i + D_{i+e})(w_{i+e} - w_i) + (D_i + D_{i-e})(w_{i-e} - w_i) ]
-//         + sum_e B_e,i (w_{i+e} - w_{i-e}) + qc_i w_i
-// with D pre-scaled by 1/(2 dx_x^2) and B_e by 1/(2 dx_e).  A missing
-// neighbour is a ghost: 0 (Dirichlet) or w_i (Neumann); its D is D_i.
-template <class T, int DIM>
-__device__ __forceinline__ T stencil_apply(const StencilDev& op, const T* __restrict__ w,
-                                           const T* __restrict__ qc, int x, int y, int z,
-                                           int64_t idx, T& wc) {
-  const T* __restrict__ D = static_cast<const T*>(op.D);
-  wc = ldg(w, idx);
-  const T Dc = ldg(D, idx);
-  const T zro = zero<T>();
-  T acc;
-  {  // x
-    const bool hm = x > 0, hp = x < op.nx - 1;
-    const T wm = hm ? ldg(w, idx - 1) : (op.bc[0] ? wc : zro);
-    const T wp = hp ? ldg(w, idx + 1) : (op.bc[1] ? wc : zro);
-    const T Dm = hm ? ldg(D, idx - 1) : Dc;
-    const T Dp = hp ? ldg(D, idx + 1) : Dc;
-    acc = mul(add(Dc, Dp), sub(wp, wc));
-    acc = mac(acc, add(Dc, Dm), sub(wm, wc));
-    acc = mac(acc, ldg(static_cast<const T*>(op.B[0]), idx), sub(wp, wm));
-  }
-  {  // y
-    const int64_t s = op.nx;
-    const bool hm = y > 0, hp = y < op.ny - 1;
-    const T wm = hm ? ldg(w, idx - s) : (op.bc[2] ? wc : zro);
-    const T wp = hp ? ldg(w, idx + s) : (op.bc[3] ? wc : zro);
-    const T Dm = hm ? ldg(D, idx - s) : Dc;
-    const T Dp = hp ? ldg(D, idx + s) : Dc;
-    T ay = mul(add(Dc, Dp), sub(wp, wc));
-    ay = mac(ay, add(Dc, Dm), sub(wm, wc));
-    acc = op.uniform ? add(acc, ay) : mac(acc, from_d<T>(op.ratio[1]), ay);
-    acc = mac(acc, ldg(static_cast<const T*>(op.B[1]), idx), sub(wp, wm));
-  }
-  if (DIM == 3) {  // z
-    const int64_t s = (int64_t)op.nx * op.ny;
-    const bool hm = z > 0, hp = z < op.nz - 1;
-    const T wm = hm ? ldg(w, idx - s) : (op.bc[4] ? wc : zro);
-    const T wp = hp ? ldg(w, idx + s) : (op.bc[5] ? wc : zro);
-    const T Dm = hm ? ldg(D, idx - s) : Dc;
-    const T Dp = hp ? ldg(D, idx + s) : Dc;
-    T az = mul(add(Dc, Dp), sub(wp, wc));
-    az = mac(az, add(Dc, Dm), sub(wm, wc));
-    acc = op.uniform ? add(acc, az) : mac(acc, from_d<T>(op.ratio[2]), az);
-    acc = mac(acc, ldg(static_cast<const T*>(op.B[2]), idx), sub(wp, wm));
-  }
-  return mac(acc, ldg(qc, idx), wc);
-}
-
-// ---------------------------------------------------------------------------
-// the fused Newton iteration, stencil
-// ---------------------------------------------------------------------------
-template <int FMT, int DIM>
-__global__ void __launch_bounds__(EI_TPB)
-k_stencil_newton(StencilDev op, const void* __restrict__ w_in_, void* __restrict__ w_out_,
-                 void* __restrict__ p_, NewtonScalars s, double* partials, DevCtl* ctl) {
-  using T = typename VT<FMT>::T;
-  using P = typename VT<FMT>::P;
-  if (*(volatile int*)&ctl->done != 0) return;
-  const T* __restrict__ w_in = static_cast<const T*>(w_in_);
-  T* __restrict__ w_out = static_cast<T*>(w_out_);
-  P* __restrict__ p = static_cast<P*>(p_);
-  const T* __restrict__ qc = static_cast<const T*>(op.qc);
-  const int x = blockIdx.x * EI_BX + threadIdx.x;
-  const int y = blockIdx.y * EI_BY + threadIdx.y;
-  const int z0 = blockIdx.z * EI_ZC;
-  const int z1 = min(z0 + EI_ZC, op.nz);
-  const T invg = from_d<T>(s.inv_gamma);
-  const T nshift = from_d<T>(-s.shift);
-  const P dn = from_d<P>(s.d_next);
-  const P d0 = from_d<P>(s.d0);
-  T aw = zero<T>();
-  P ap = zero<P>();
-  if (x < op.nx && y < op.ny) {
-    for (int z = z0; z < z1; ++z) {
-      const int64_t idx = ((int64_t)z * op.ny + y) * op.nx + x;
-      T wc;
-      const T Aw = stencil_apply<T, DIM>(op, w_in, qc, x, y, z, idx, wc);
-      const T wn = mac(mul(Aw, invg), nshift, wc);
-      const P pold = (s.j == 0) ? mul(d0, to_p(wc)) : ld(p, idx);
-      const P pn = mac(pold, dn, to_p(wn));
-      st(w_out, idx, wn);
-      st(p, idx, pn);
-      aw = mac(aw, wn, wn);
-      ap = mac(ap, pn, pn);
-    }
-  }
-  double nw2 = to_d(aw), np2 = to_d(ap);
-  if (last_block_reduce2<RED_SUM>(nw2, np2, partials, ctl)) {
-    if (threadIdx.x == 0 && threadIdx.y == 0) {
-      ctl->nw2 = nw2;
-      ctl->np2 = np2;
-      if (!finite_d(nw2) || !finite_d(np2)) {
-        ctl->done = 4;
-        ctl->degree = s.j + 1;
-      } else if (s.j == 0 && np2 == 0.0) {  // zero input: p = 0 at degree 0
-        ctl->done = 1;
-        ctl->degree = 0;
-      } else if (fabs(s.d_next) * sqrt(nw2) <= s.tol * sqrt(np2)) {
-        ctl->done = 1;
-        ctl->degree = s.j + 1;
-      } else if (s.j + 1 >= s.m_max) {
-        ctl->done = 2;
-        ctl->degree = s.j + 1;
+  for (int e = 0; e < 3; ++e) {
+    if (e >= u.dim) break;
+    const double h2 = u.dx[e] * u.dx[e];
+    const double be = uval<U>(u.b[e], u.bc_[e], i);
+#pragma unroll
+    for (int side = 0; side < 2; ++side) {
+      const int sgn = side ? 1 : -1;
+      const bool has = side ? crd[e] < ext[e] - 1 : crd[e] > 0;
+      if (has) {
+        const double Df = 0.5 * (Di + uval<U>(u.D, u.Dc, i + sgn * str[e]));
+        a[2 * e + side] = Df / h2 + sgn * be / (2.0 * u.dx[e]);
+        rad += fabs(a[2 * e + side]);
+        diag -= Df / h2;
+      } else if (u.bc[2 * e + side] == 1) {
+        diag += sgn * be / (2.0 * u.dx[e]);
+      } else {
+        diag -= Di / h2;
       }
     }
   }
 }
 
-// r = A y + v, ||r||^2
-template <int FMT, int DIM>
+template <class U>
 __global__ void __launch_bounds__(EI_TPB)
-k_stencil_residual(StencilDev op, const void* __restrict__ y_, const void* __restrict__ v_,
+k_stencil_gershgorin(UserCoef u, double* lo, double* hi, double* partials, DevCtl* ctl) {
+  const int64_t n = (int64_t)u.nx * u.ny * u.nz;
+  double mn = INFINITY, mx = -INFINITY;
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;
+       i += (int64_t)gridDim.x * blockDim.x) {
+    const int x = (int)(i % u.nx);
+    const int y = (int)((i / u.nx) % u.ny);
+    const int z = (int)(i / ((int64_t)u.nx * u.ny));
+    double a[6], diag, rad;
+    stencil_row<U>(u, i, x, y, z, a, diag, rad);
+    lo[i] = diag - rad;
+    hi[i] = diag + rad;
+    mn = fmin(mn, diag - rad);
+    mx = fmax(mx, diag + rad);
+  }
+  if (last_block_reduce2<RED_MINMAX>(mn, mx, partials, ctl)) {
+    if (threadIdx.x == 0) {
+      ctl->mn = mn;
+      ctl->mx = mx;
+    }
+  }
+}
+
+template <int FMT, class U>
+__global__ void __launch_bounds__(EI_TPB)
+k_stencil_coef(UserCoef u, int pitch, void* a0, void* a1, void* a2, void* a3, void* a4, void* a5,
+               void* diag_out) {
+  using T = typename VT<FMT>::T;
+  T* out[6] = {static_cast<T*>(a0), static_cast<T*>(a1), static_cast<T*>(a2),
+               static_cast<T*>(a3), static_cast<T*>(a4), static_cast<T*>(a5)};
+  const int64_t n = (int64_t)u.nx * u.ny * u.nz;
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;
+       i += (int64_t)gridDim.x * blockDim.x) {
+    const int x = (int)(i % u.nx);
+    const int y = (int)((i / u.nx) % u.ny);
+    const int z = (int)(i / ((int64_t)u.nx * u.ny));
+    double a[6], diag, rad;
+    stencil_row<U>(u, i, x, y, z, a, diag, rad);
+    const int64_t j = pidx(i, u.nx, pitch);
+#pragma unroll
+    for (int k = 0; k < 6; ++k) st(out[k], j, from_d<T>(a[k]));
+    st(static_cast<T*>(diag_out), j, from_d<T>(diag));
+  }
+}
+
+// ---------------------------------------------------------------------------
+// the stencil operator at one point, from global memory (padded arrays)
+// ---------------------------------------------------------------------------
+// explicit coefficients: (A w)_i = diag_i w_i + sum_nb a_nb,i w_nb
+template <class T>
+__device__ __forceinline__ T apply_coef7(const StencilDev& g, const T* __restrict__ w,
+                                         const T* __restrict__ diag, int x, int y, int z,
+                                         int64_t idx, T& wc) {
+  const int64_t sy = g.pitch, sz = (int64_t)g.pitch * g.ny;
+  wc = ldg(w, idx);
+  T acc = mul(ldg(diag, idx), wc);
+  if (x > 0) acc = mac(acc, ldg(static_cast<const T*>(g.a[0]), idx), ldg(w, idx - 1));
+  if (x < g.nx - 1) acc = mac(acc, ldg(static_cast<const T*>(g.a[1]), idx), ldg(w, idx + 1));
+  if (y > 0) acc = mac(acc, ldg(static_cast<const T*>(g.a[2]), idx), ldg(w, idx - sy));
+  if (y < g.ny - 1) acc = mac(acc, ldg(static_cast<const T*>(g.a[3]), idx), ldg(w, idx + sy));
+  if (z > 0) acc = mac(acc, ldg(static_cast<const T*>(g.a[4]), idx), ldg(w, idx - sz));
+  if (z < g.nz - 1) acc = mac(acc, ldg(static_cast<const T*>(g.a[5]), idx), ldg(w, idx + sz));
+  return acc;
+}
+
+// flux form: sum_e r_e [(D_i + D_{i+e})(w_{i+e} - w_i) + (D_i + D_{i-e})(w_{i-e} - w_i)]
+//            + sum_e B_e (w_{i+e} - w_{i-e}) + qc_i w_i, ghosts as in the row rule
+template <class T>
+__device__ __forceinline__ T apply_flux(const StencilDev& g, const T* __restrict__ w,
+                                        const T* __restrict__ qc, int x, int y, int z,
+                                        int64_t idx, T& wc) {
+  const T* __restrict__ D = static_cast<const T*>(g.D);
+  wc = ldg(w, idx);
+  const T Dc = ldg(D, idx);
+  const T zro = zero<T>();
+  const int crd[3] = {x, y, z};
+  const int ext[3] = {g.nx, g.ny, g.nz};
+  const int64_t str[3] = {1, g.pitch, (int64_t)g.pitch * g.ny};
+  T acc = zero<T>();
+#pragma unroll
+  for (int e = 0; e < 3; ++e) {
+    if (e >= g.dim) break;
+    const bool hm = crd[e] > 0, hp = crd[e] < ext[e] - 1;
+    const T wm = hm ? ldg(w, idx - str[e]) : (g.bc[2 * e] ? wc : zro);
+    const T wp = hp ? ldg(w, idx + str[e]) : (g.bc[2 * e + 1] ? wc : zro);
+    const T Dm = hm ? ldg(D, idx - str[e]) : Dc;
+    const T Dp = hp ? ldg(D, idx + str[e]) : Dc;
+    T ae = mul(add(Dc, Dp), sub(wp, wc));
+    ae = mac(ae, add(Dc, Dm), sub(wm, wc));
+    acc = (e == 0 || g.uniform) ? add(acc, ae) : mac(acc, from_d<T>(g.ratio[e]), ae);
+    acc = mac(acc, ldg(static_cast<const T*>(g.B[e]), idx), sub(wp, wm));
+  }
+  return mac(acc, ldg(qc, idx), wc);
+}
+
+template <class T>
+__device__ __forceinline__ T apply_stencil(const StencilDev& g, const T* w, const T* diag_or_qc,
+                                           int x, int y, int z, int64_t idx, T& wc) {
+  return g.coef7 ? apply_coef7<T>(g, w, diag_or_qc, x, y, z, idx, wc)
+                 : apply_flux<T>(g, w, diag_or_qc, x, y, z, idx, wc);
+}
+
+// r = J y + v, ||r||^2 (J's diagonal: g.diag (coef7) or g.qc (flux))
+template <int FMT>
+__global__ void __launch_bounds__(EI_TPB)
+k_stencil_residual(StencilDev g, const void* __restrict__ y_, const void* __restrict__ v_,
                    void* __restrict__ r_, double* partials, DevCtl* ctl) {
   using T = typename VT<FMT>::T;
   const T* __restrict__ yv = static_cast<const T*>(y_);
   const T* __restrict__ v = static_cast<const T*>(v_);
   T* __restrict__ r = static_cast<T*>(r_);
-  const T* __restrict__ qc = static_cast<const T*>(op.qc);
-  const int x = blockIdx.x * EI_BX + threadIdx.x;
-  const int y = blockIdx.y * EI_BY + threadIdx.y;
-  const int z0 = blockIdx.z * EI_ZC;
-  const int z1 = min(z0 + EI_ZC, op.nz);
+  const T* dg = static_cast<const T*>(g.coef7 ? g.diag : g.qc);
+  const int64_t n = (int64_t)g.nx * g.ny * g.nz;
   T ar = zero<T>();
-  if (x < op.nx && y < op.ny) {
-    for (int z = z0; z < z1; ++z) {
-      const int64_t idx = ((int64_t)z * op.ny + y) * op.nx + x;
-      T yc;
-      const T Ay = stencil_apply<T, DIM>(op, yv, qc, x, y, z, idx, yc);
-      const T rv = add(Ay, ldg(v, idx));
-      st(r, idx, rv);
-      ar = mac(ar, rv, rv);
-    }
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;
+       i += (int64_t)gridDim.x * blockDim.x) {
+    const int x = (int)(i % g.nx);
+    const int64_t t = i / g.nx;
+    const int y = (int)(t % g.ny);
+    const int z = (int)(t / g.ny);
+    const int64_t idx = t * g.pitch + x;
+    T yc;
+    const T Ay = apply_stencil<T>(g, yv, dg, x, y, z, idx, yc);
+    const T rv = add(Ay, ldg(v, idx));
+    st(r, idx, rv);
+    ar = mac(ar, rv, rv);
   }
   double a = to_d(ar), b = 0.0;
   if (last_block_reduce2<RED_SUM>(a, b, partials, ctl)) {
-    if (threadIdx.x == 0 && threadIdx.y == 0) ctl->sum0 = a;
+    if (threadIdx.x == 0) ctl->sum0 = a;
   }
 }
 
-// F = A u + g(u) (A with the base diagonal c), qc_out = c + g'(u) (Rosenbrock) or c
-template <int FMT, int DIM>
+// F = A u + g(u); diag_out = diag_base + g'(u) (Rosenbrock)
+template <int FMT>
 __global__ void __launch_bounds__(EI_TPB)
-k_stencil_F(StencilDev op, const void* __restrict__ u_, void* __restrict__ F_,
-            void* __restrict__ qc_out_, const void* __restrict__ cbase_, int nonlin,
-            int rosenbrock, double* partials, DevCtl* ctl) {
+k_stencil_F(StencilDev g, const void* __restrict__ u_, void* __restrict__ F_,
+            const void* __restrict__ db_, void* __restrict__ dout_, int nonlin, int rosenbrock,
+            double* partials, DevCtl* ctl) {
   using T = typename VT<FMT>::T;
   const T* __restrict__ u = static_cast<const T*>(u_);
-  const T* __restrict__ cb = static_cast<const T*>(cbase_);
+  const T* __restrict__ db = static_cast<const T*>(db_);
   T* __restrict__ F = static_cast<T*>(F_);
-  T* __restrict__ qo = static_cast<T*>(qc_out_);
-  const int x = blockIdx.x * EI_BX + threadIdx.x;
-  const int y = blockIdx.y * EI_BY + threadIdx.y;
-  const int z0 = blockIdx.z * EI_ZC;
-  const int z1 = min(z0 + EI_ZC, op.nz);
-  const T one = from_d<T>(1.0);
+  T* __restrict__ dout = static_cast<T*>(dout_);
+  const T one = from_d<T>(1.0), mtwo = from_d<T>(-2.0);
+  const int64_t n = (int64_t)g.nx * g.ny * g.nz;
   T af = zero<T>();
-  if (x < op.nx && y < op.ny) {
-    for (int z = z0; z < z1; ++z) {
-      const int64_t idx = ((int64_t)z * op.ny + y) * op.nx + x;
-      T uc;
-      T Fv = stencil_apply<T, DIM>(op, u, cb, x, y, z, idx, uc);
-      if (nonlin) Fv = mac(Fv, uc, sub(one, uc));  // g(u) = u(1-u)
-      st(F, idx, Fv);
-      if (rosenbrock) {
-        T q = ldg(cb, idx);
-        if (nonlin) q = add(q, mac(one, from_d<T>(-2.0), uc));  // g'(u) = 1 - 2u
-        st(qo, idx, q);
-      }
-      af = mac(af, Fv, Fv);
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;
+       i += (int64_t)gridDim.x * blockDim.x) {
+    const int x = (int)(i % g.nx);
+    const int64_t t = i / g.nx;
+    const int y = (int)(t % g.ny);
+    const int z = (int)(t / g.ny);
+    const int64_t idx = t * g.pitch + x;
+    T uc;
+    T Fv = apply_stencil<T>(g, u, db, x, y, z, idx, uc);
+    if (nonlin) Fv = mac(Fv, uc, sub(one, uc));  // g(u) = u(1-u)
+    st(F, idx, Fv);
+    if (rosenbrock) {
+      T q = ldg(db, idx);
+      if (nonlin) q = add(q, mac(one, mtwo, uc));  // g'(u) = 1 - 2u
+      st(dout, idx, q);
     }
+    af = mac(af, Fv, Fv);
   }
   double a = to_d(af), b = 0.0;
   if (last_block_reduce2<RED_SUM>(a, b, partials, ctl)) {
-    if (threadIdx.x == 0 && threadIdx.y == 0) {
+    if (threadIdx.x == 0) {
       ctl->sum0 = a;
       ctl->sum1 = finite_d(a) ? 1.0 : 0.0;
     }
   }
 }
-
 
 // ---------------------------------------------------------------------------
 // CSR operator (Sec. III-D): a group of EI_LPR lanes per row.  The paper found
@@ -549,67 +442,6 @@ k_csr_gershgorin(int64_t n, const int64_t* __restrict__ rowptr, const int32_t* _
   }
 }
 
-// ---------------------------------------------------------------------------
-// Gershgorin interval (FP64, from the caller's arrays)
-// ---------------------------------------------------------------------------
-template <class U>
-__device__ __forceinline__ double uval(const void* p, double cst, int64_t i) {
-  return p ? (double)__ldg(static_cast<const U*>(p) + i) : cst;
-}
-
-template <class U>
-__global__ void __launch_bounds__(EI_TPB)
-k_stencil_gershgorin(int dim, int nx, int ny, int nz, int bc0, int bc1, int bc2, int bc3,
-                     int bc4, int bc5, double dx0, double dx1, double dx2, const void* D,
-                     double Dc, const void* b0, const void* b1, const void* b2, double bc_0,
-                     double bc_1, double bc_2, const void* c, double cc, double* lo,
-                     double* hi, double* partials, DevCtl* ctl) {
-  const int64_t n = (int64_t)nx * ny * nz;
-  const int bcs[6] = {bc0, bc1, bc2, bc3, bc4, bc5};
-  const double dxs[3] = {dx0, dx1, dx2};
-  const void* bs[3] = {b0, b1, b2};
-  const double bcst[3] = {bc_0, bc_1, bc_2};
-  double mn = INFINITY, mx = -INFINITY;
-  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;
-       i += (int64_t)gridDim.x * blockDim.x) {
-    const int x = (int)(i % nx);
-    const int y = (int)((i / nx) % ny);
-    const int z = (int)(i / ((int64_t)nx * ny));
-    const int crd[3] = {x, y, z};
-    const int ext[3] = {nx, ny, nz};
-    const int64_t str[3] = {1, nx, (int64_t)nx * ny};
-    const double Di = uval<U>(D, Dc, i);
-    double diag = uval<U>(c, cc, i), rad = 0.0;
-    for (int e = 0; e < dim; ++e) {
-      const double h2 = dxs[e] * dxs[e];
-      const double be = uval<U>(bs[e], bcst[e], i);
-      for (int sgn = -1; sgn <= 1; sgn += 2) {
-        const bool has = sgn < 0 ? crd[e] > 0 : crd[e] < ext[e] - 1;
-        const int face = 2 * e + (sgn > 0);
-        if (has) {
-          const double Df = 0.5 * (Di + uval<U>(D, Dc, i + sgn * str[e]));
-          rad += fabs(Df / h2 + sgn * be / (2.0 * dxs[e]));
-          diag -= Df / h2;
-        } else if (bcs[face] == 1) {
-          diag += sgn * be / (2.0 * dxs[e]);
-        } else {
-          diag -= Di / h2;
-        }
-      }
-    }
-    lo[i] = diag - rad;
-    hi[i] = diag + rad;
-    mn = fmin(mn, diag - rad);
-    mx = fmax(mx, diag + rad);
-  }
-  if (last_block_reduce2<RED_MINMAX>(mn, mx, partials, ctl)) {
-    if (threadIdx.x == 0) {
-      ctl->mn = mn;
-      ctl->mx = mx;
-    }
-  }
-}
-
 // min/max of (lo + q), (hi + q), q = g'(u) = 1 - 2u for the logistic g
 template <class U>
 __global__ void __launch_bounds__(EI_TPB)
@@ -630,30 +462,33 @@ k_shifted_minmax(int64_t n, const double* __restrict__ lo, const double* __restr
   }
 }
 
+
 // ---------------------------------------------------------------------------
-// elementwise helpers
+// elementwise moves (caller's contiguous layout <-> padded vector formats)
 // ---------------------------------------------------------------------------
 template <int FMT, class U>
-__global__ void k_fill_coef(void* dst_, int64_t n, const U* src, double cst, double scale) {
+__global__ void k_fill_coef(void* dst_, int64_t n, int nx, int pitch, const U* src, double cst,
+                            double scale) {
   using T = typename VT<FMT>::T;
   T* dst = static_cast<T*>(dst_);
   for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;
        i += (int64_t)gridDim.x * blockDim.x) {
     const double v = (src ? (double)src[i] : cst) * scale;
-    st(dst, i, from_d<T>(v));
+    st(dst, pidx(i, nx, pitch), from_d<T>(v));
   }
 }
 
 template <int FMT, class U>
 __global__ void __launch_bounds__(EI_TPB)
-k_import(void* dst_, const U* __restrict__ src, int64_t n, double* partials, DevCtl* ctl) {
+k_import(void* dst_, const U* __restrict__ src, int64_t n, int nx, int pitch, double* partials,
+         DevCtl* ctl) {
   using T = typename VT<FMT>::T;
   T* dst = static_cast<T*>(dst_);
   double a = 0.0, b = 0.0;
   for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;
        i += (int64_t)gridDim.x * blockDim.x) {
     const double v = (double)src[i];
-    st(dst, i, from_d<T>(v));
+    st(dst, pidx(i, nx, pitch), from_d<T>(v));
     a = fma(v, v, a);
   }
   if (last_block_reduce2<RED_SUM>(a, b, partials, ctl)) {
@@ -665,18 +500,20 @@ k_import(void* dst_, const U* __restrict__ src, int64_t n, double* partials, Dev
 }
 
 template <class S, class U>
-__global__ void k_export(U* dst, const S* __restrict__ src, int64_t n, double scale) {
+__global__ void k_export(U* dst, const S* __restrict__ src, int64_t n, int nx, int pitch,
+                         double scale) {
   for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;
        i += (int64_t)gridDim.x * blockDim.x) {
-    dst[i] = (U)(to_d(ldg(src, i)) * scale);
+    dst[i] = (U)(to_d(ldg(src, pidx(i, nx, pitch))) * scale);
   }
 }
 
 template <class S, class U>
-__global__ void k_add_export(U* u, const S* __restrict__ y, int64_t n, double scale) {
+__global__ void k_add_export(U* u, const S* __restrict__ y, int64_t n, int nx, int pitch,
+                             double scale) {
   for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;
        i += (int64_t)gridDim.x * blockDim.x) {
-    u[i] = (U)fma(to_d(ldg(y, i)), scale, (double)u[i]);
+    u[i] = (U)fma(to_d(ldg(y, pidx(i, nx, pitch))), scale, (double)u[i]);
   }
 }
 
@@ -746,69 +583,85 @@ static int ew_blocks(int64_t n) {
   return (int)b;
 }
 
-static dim3 stencil_grid(const StencilDev& op) {
-  return dim3((op.nx + EI_BX - 1) / EI_BX, (op.ny + EI_BY - 1) / EI_BY,
-              (op.nz + EI_ZC - 1) / EI_ZC);
-}
-
-int stencil_blocks(const StencilDev& op) {
-  dim3 g = stencil_grid(op);
-  return (int)(g.x * g.y * g.z);
-}
-
 int reduction_capacity() { return num_sms() * 8; }
 
 int csr_blocks(int64_t n) {
-  int64_t b = (n + (EI_TPB / 4) - 1) / (EI_TPB / 4);
+  int64_t b = (n + (EI_TPB / EI_LPR) - 1) / (EI_TPB / EI_LPR);
   int64_t cap = (int64_t)num_sms() * 8;
   if (b > cap) b = cap;
   if (b < 1) b = 1;
   return (int)b;
 }
 
-#define EI_DISPATCH_FMT(fmt, KERNEL_CALL)        \
-  switch (fmt) {                                 \
+#define EI_DISPATCH_FMT(fmt, KERNEL_CALL)                           \
+  switch (fmt) {                                                    \
     case VF_DF: { constexpr int F_ = VF_DF; KERNEL_CALL; } break;   \
     case VF_F64: { constexpr int F_ = VF_F64; KERNEL_CALL; } break; \
     default: { constexpr int F_ = VF_F32; KERNEL_CALL; } break;     \
   }
 
-cudaError_t launch_stencil_newton(const StencilDev& op, const void* w_in, void* w_out, void* p,
-                                  const NewtonScalars& s, int fmt, double* partials,
-                                  DevCtl* ctl, cudaStream_t stm) {
-  dim3 g = stencil_grid(op), b(EI_BX, EI_BY, 1);
-  if (op.dim == 3) {
-    EI_DISPATCH_FMT(fmt, (k_stencil_newton<F_, 3><<<g, b, 0, stm>>>(op, w_in, w_out, p, s, partials, ctl)));
+static UserCoef user_coef(const StencilDev& g, const double dx[3], const void* D, double Dc,
+                          const void* const b[3], const double bc[3], const void* c, double cc) {
+  UserCoef u;
+  u.dim = g.dim;
+  u.nx = g.nx;
+  u.ny = g.ny;
+  u.nz = g.nz;
+  for (int f = 0; f < 6; ++f) u.bc[f] = g.bc[f];
+  for (int e = 0; e < 3; ++e) {
+    u.dx[e] = dx[e];
+    u.b[e] = b[e];
+    u.bc_[e] = bc[e];
+  }
+  u.D = D;
+  u.Dc = Dc;
+  u.c = c;
+  u.cc = cc;
+  return u;
+}
+
+cudaError_t launch_stencil_gershgorin(const StencilDev& g, int prec, const double dx[3],
+                                      const void* D, double Dc, const void* const b[3],
+                                      const double bc[3], const void* c, double cc, double* lo,
+                                      double* hi, double* partials, DevCtl* ctl,
+                                      cudaStream_t stm) {
+  const UserCoef u = user_coef(g, dx, D, Dc, b, bc, c, cc);
+  const int nb = ew_blocks((int64_t)g.nx * g.ny * g.nz);
+  if (prec == 0)
+    k_stencil_gershgorin<double><<<nb, EI_TPB, 0, stm>>>(u, lo, hi, partials, ctl);
+  else
+    k_stencil_gershgorin<float><<<nb, EI_TPB, 0, stm>>>(u, lo, hi, partials, ctl);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_stencil_coef(const StencilDev& g, int prec, const double dx[3], const void* D,
+                                double Dc, const void* const b[3], const double bc[3],
+                                const void* c, double cc, void* const a[6], void* diag, int fmt,
+                                cudaStream_t stm) {
+  const UserCoef u = user_coef(g, dx, D, Dc, b, bc, c, cc);
+  const int nb = ew_blocks((int64_t)g.nx * g.ny * g.nz);
+  if (prec == 0) {
+    EI_DISPATCH_FMT(fmt, (k_stencil_coef<F_, double><<<nb, EI_TPB, 0, stm>>>(u, g.pitch, a[0], a[1], a[2], a[3], a[4], a[5], diag)));
   } else {
-    EI_DISPATCH_FMT(fmt, (k_stencil_newton<F_, 2><<<g, b, 0, stm>>>(op, w_in, w_out, p, s, partials, ctl)));
+    EI_DISPATCH_FMT(fmt, (k_stencil_coef<F_, float><<<nb, EI_TPB, 0, stm>>>(u, g.pitch, a[0], a[1], a[2], a[3], a[4], a[5], diag)));
   }
   return cudaGetLastError();
 }
 
-cudaError_t launch_stencil_residual(const StencilDev& op, const void* y, const void* v, void* r,
+cudaError_t launch_stencil_residual(const StencilDev& g, const void* y, const void* v, void* r,
                                     int fmt, double* partials, DevCtl* ctl, cudaStream_t stm) {
-  dim3 g = stencil_grid(op), b(EI_BX, EI_BY, 1);
-  if (op.dim == 3) {
-    EI_DISPATCH_FMT(fmt, (k_stencil_residual<F_, 3><<<g, b, 0, stm>>>(op, y, v, r, partials, ctl)));
-  } else {
-    EI_DISPATCH_FMT(fmt, (k_stencil_residual<F_, 2><<<g, b, 0, stm>>>(op, y, v, r, partials, ctl)));
-  }
+  const int nb = ew_blocks((int64_t)g.nx * g.ny * g.nz);
+  EI_DISPATCH_FMT(fmt, (k_stencil_residual<F_><<<nb, EI_TPB, 0, stm>>>(g, y, v, r, partials, ctl)));
   return cudaGetLastError();
 }
 
-cudaError_t launch_stencil_F(const StencilDev& op, const void* u, void* F, void* qc_out,
-                             const void* c_base, int nonlin, int rosenbrock, int fmt,
+cudaError_t launch_stencil_F(const StencilDev& g, const void* u, void* F, const void* diag_base,
+                             void* diag_out, int nonlin, int rosenbrock, int fmt,
                              double* partials, DevCtl* ctl, cudaStream_t stm) {
-  dim3 g = stencil_grid(op), b(EI_BX, EI_BY, 1);
-  if (op.dim == 3) {
-    EI_DISPATCH_FMT(fmt, (k_stencil_F<F_, 3><<<g, b, 0, stm>>>(op, u, F, qc_out, c_base, nonlin, rosenbrock, partials, ctl)));
-  } else {
-    EI_DISPATCH_FMT(fmt, (k_stencil_F<F_, 2><<<g, b, 0, stm>>>(op, u, F, qc_out, c_base, nonlin, rosenbrock, partials, ctl)));
-  }
+  const int nb = ew_blocks((int64_t)g.nx * g.ny * g.nz);
+  EI_DISPATCH_FMT(fmt, (k_stencil_F<F_><<<nb, EI_TPB, 0, stm>>>(g, u, F, diag_base, diag_out, nonlin, rosenbrock, partials, ctl)));
   return cudaGetLastError();
 }
-
-
 cudaError_t launch_csr_newton(const CsrDev& op, const void* w_in, void* w_out, void* p,
                               const NewtonScalars& s, int fmt, double* partials, DevCtl* ctl,
                               cudaStream_t stm) {
@@ -845,24 +698,6 @@ cudaError_t launch_csr_gershgorin(const CsrDev& op, int prec, const void* val_us
   return cudaGetLastError();
 }
 
-cudaError_t launch_stencil_gershgorin(const StencilDev& u, int prec, const double dx[3],
-                                      const void* D, double Dc, const void* const b[3],
-                                      const double bc[3], const void* c, double cc, double* lo,
-                                      double* hi, double* partials, DevCtl* ctl,
-                                      cudaStream_t stm) {
-  const int64_t n = (int64_t)u.nx * u.ny * u.nz;
-  const int nb = ew_blocks(n);
-  if (prec == 0)
-    k_stencil_gershgorin<double><<<nb, EI_TPB, 0, stm>>>(
-        u.dim, u.nx, u.ny, u.nz, u.bc[0], u.bc[1], u.bc[2], u.bc[3], u.bc[4], u.bc[5], dx[0],
-        dx[1], dx[2], D, Dc, b[0], b[1], b[2], bc[0], bc[1], bc[2], c, cc, lo, hi, partials, ctl);
-  else
-    k_stencil_gershgorin<float><<<nb, EI_TPB, 0, stm>>>(
-        u.dim, u.nx, u.ny, u.nz, u.bc[0], u.bc[1], u.bc[2], u.bc[3], u.bc[4], u.bc[5], dx[0],
-        dx[1], dx[2], D, Dc, b[0], b[1], b[2], bc[0], bc[1], bc[2], c, cc, lo, hi, partials, ctl);
-  return cudaGetLastError();
-}
-
 cudaError_t launch_shifted_minmax(int64_t n, const double* lo, const double* hi, const void* u,
                                   int prec, int nonlin, double* partials, DevCtl* ctl,
                                   cudaStream_t stm) {
@@ -876,64 +711,70 @@ cudaError_t launch_shifted_minmax(int64_t n, const double* lo, const double* hi,
   return cudaGetLastError();
 }
 
-cudaError_t launch_fill_coef(void* dst, int fmt, int64_t n, const void* src, int src_prec,
-                             double cst, double scale, cudaStream_t stm) {
+
+cudaError_t launch_fill_coef(void* dst, int fmt, int64_t n, int nx, int ny, int pitch,
+                             const void* src, int src_prec, double cst, double scale,
+                             cudaStream_t stm) {
+  (void)ny;
   const int nb = ew_blocks(n);
   if (src_prec == 0) {
-    EI_DISPATCH_FMT(fmt, (k_fill_coef<F_, double><<<nb, EI_TPB, 0, stm>>>(dst, n, static_cast<const double*>(src), cst, scale)));
+    EI_DISPATCH_FMT(fmt, (k_fill_coef<F_, double><<<nb, EI_TPB, 0, stm>>>(dst, n, nx, pitch, static_cast<const double*>(src), cst, scale)));
   } else {
-    EI_DISPATCH_FMT(fmt, (k_fill_coef<F_, float><<<nb, EI_TPB, 0, stm>>>(dst, n, static_cast<const float*>(src), cst, scale)));
+    EI_DISPATCH_FMT(fmt, (k_fill_coef<F_, float><<<nb, EI_TPB, 0, stm>>>(dst, n, nx, pitch, static_cast<const float*>(src), cst, scale)));
   }
   return cudaGetLastError();
 }
 
-cudaError_t launch_import(void* dst, int fmt, const void* src, int src_prec, int64_t n,
-                          double* partials, DevCtl* ctl, cudaStream_t stm) {
+cudaError_t launch_import(void* dst, int fmt, const void* src, int src_prec, int64_t n, int nx,
+                          int ny, int pitch, double* partials, DevCtl* ctl, cudaStream_t stm) {
+  (void)ny;
   const int nb = ew_blocks(n);
   if (src_prec == 0) {
-    EI_DISPATCH_FMT(fmt, (k_import<F_, double><<<nb, EI_TPB, 0, stm>>>(dst, static_cast<const double*>(src), n, partials, ctl)));
+    EI_DISPATCH_FMT(fmt, (k_import<F_, double><<<nb, EI_TPB, 0, stm>>>(dst, static_cast<const double*>(src), n, nx, pitch, partials, ctl)));
   } else {
-    EI_DISPATCH_FMT(fmt, (k_import<F_, float><<<nb, EI_TPB, 0, stm>>>(dst, static_cast<const float*>(src), n, partials, ctl)));
+    EI_DISPATCH_FMT(fmt, (k_import<F_, float><<<nb, EI_TPB, 0, stm>>>(dst, static_cast<const float*>(src), n, nx, pitch, partials, ctl)));
   }
   return cudaGetLastError();
 }
 
 template <class U>
-static void export_dispatch(U* dst, const void* src, int fmt, int src_is_p, int64_t n,
-                            double scale, bool add, cudaStream_t stm) {
+static void export_dispatch(U* dst, const void* src, int fmt, int src_is_p, int64_t n, int nx,
+                            int pitch, double scale, bool add, cudaStream_t stm) {
   const int nb = ew_blocks(n);
-  // element type of the source: df for the float-float format and for every
-  // Newton sum except the double format's
+  // source element type: df for the float-float format and for the Newton
+  // sum of every format but the double one
   if (fmt == VF_F64) {
     const double* s = static_cast<const double*>(src);
-    if (add) k_add_export<double, U><<<nb, EI_TPB, 0, stm>>>(dst, s, n, scale);
-    else k_export<double, U><<<nb, EI_TPB, 0, stm>>>(dst, s, n, scale);
+    if (add) k_add_export<double, U><<<nb, EI_TPB, 0, stm>>>(dst, s, n, nx, pitch, scale);
+    else k_export<double, U><<<nb, EI_TPB, 0, stm>>>(dst, s, n, nx, pitch, scale);
   } else if (fmt == VF_DF || src_is_p) {
     const df* s = static_cast<const df*>(src);
-    if (add) k_add_export<df, U><<<nb, EI_TPB, 0, stm>>>(dst, s, n, scale);
-    else k_export<df, U><<<nb, EI_TPB, 0, stm>>>(dst, s, n, scale);
+    if (add) k_add_export<df, U><<<nb, EI_TPB, 0, stm>>>(dst, s, n, nx, pitch, scale);
+    else k_export<df, U><<<nb, EI_TPB, 0, stm>>>(dst, s, n, nx, pitch, scale);
   } else {
     const float* s = static_cast<const float*>(src);
-    if (add) k_add_export<float, U><<<nb, EI_TPB, 0, stm>>>(dst, s, n, scale);
-    else k_export<float, U><<<nb, EI_TPB, 0, stm>>>(dst, s, n, scale);
+    if (add) k_add_export<float, U><<<nb, EI_TPB, 0, stm>>>(dst, s, n, nx, pitch, scale);
+    else k_export<float, U><<<nb, EI_TPB, 0, stm>>>(dst, s, n, nx, pitch, scale);
   }
 }
 
 cudaError_t launch_export(void* dst, int dst_prec, const void* src, int fmt, int src_is_p,
-                          int64_t n, double scale, cudaStream_t stm) {
+                          int64_t n, int nx, int ny, int pitch, double scale, cudaStream_t stm) {
+  (void)ny;
   if (dst_prec == 0)
-    export_dispatch(static_cast<double*>(dst), src, fmt, src_is_p, n, scale, false, stm);
+    export_dispatch(static_cast<double*>(dst), src, fmt, src_is_p, n, nx, pitch, scale, false, stm);
   else
-    export_dispatch(static_cast<float*>(dst), src, fmt, src_is_p, n, scale, false, stm);
+    export_dispatch(static_cast<float*>(dst), src, fmt, src_is_p, n, nx, pitch, scale, false, stm);
   return cudaGetLastError();
 }
 
 cudaError_t launch_add_export(void* u, int prec, const void* y, int fmt, int src_is_p, int64_t n,
-                              double scale, cudaStream_t stm) {
+                              int nx, int ny, int pitch, double scale, cudaStream_t stm) {
+  (void)ny;
   if (prec == 0)
-    export_dispatch(static_cast<double*>(u), y, fmt, src_is_p, n, scale, true, stm);
+    export_dispatch(static_cast<double*>(u), y, fmt, src_is_p, n, nx, pitch, scale, true, stm);
   else
-    export_dispatch(static_cast<float*>(u), y, fmt, src_is_p, n, scale, true, stm);
+    export_dispatch(static_cast<float*>(u), y, fmt, src_is_p, n, nx, pitch, scale, true, stm);
   return cudaGetLastError();
 }
 

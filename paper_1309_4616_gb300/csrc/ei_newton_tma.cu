@@ -1,0 +1,373 @@
+// The fused Newton iteration of the stencil path, staged through shared
+// memory by TMA (sm_103a).
+//
+// One iteration is one product of Eq. (3) of the paper, (alpha*A + beta*I)w
+// with alpha = 1/gamma and beta = -(c/gamma + xi_j), fused with the Newton sum
+// p += d_{j+1} w_{j+1}, the squared norms of w_{j+1} and p (block partials and
+// a fixed-order last-block reduction) and the stop test of the a-posteriori
+// estimate |d_{j+1}| ||w_{j+1}|| <= tol ||p||.
+//
+// Tiling: a block owns a 32 x 8 column of the grid and marches along z over a
+// chunk of planes (Sec. III-A of the paper keeps a 2D slice on chip and iterates
+// over the third index; here the slice is fed by TMA).  Per plane, one thread
+// issues cp.async.bulk.tensor loads of the w tile with its x/y halo (x start
+// rounded down to a 16-byte boundary), the coefficient tiles and the p tile
+// into a 4-stage ring; an mbarrier per stage carries the transaction bytes.
+// Planes z-1, z, z+1 are resident while plane z is computed and plane z+2 is
+// in flight.  Halo columns and planes outside the grid arrive as zeros (TMA
+// out-of-bounds fill); with the explicit-coefficient layout every coefficient
+// that would touch them is zero, so no boundary branches are needed.
+//
+// Every mbarrier wait is bounded (0.5 s of %globaltimer); a block that gives up
+// records it in ctl->err, waits (bounded) for its own copies in flight and
+// still takes part in the reduction, whose last block reports status 5.
+#include <cuda.h>
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "ei_device.cuh"
+
+namespace ei {
+
+template <int FMT, bool COEF7>
+struct TmaCfg {
+  using T = typename VT<FMT>::T;
+  using P = typename VT<FMT>::P;
+  static constexpr int TX = 32, TY = 8, NST = 4;
+  static constexpr int HX = 16 / (int)sizeof(T);  // x halo, rounded to 16 bytes
+  static constexpr int WX = TX + 2 * HX, WY = TY + 2;
+  static constexpr int al(int b) { return (b + 127) / 128 * 128; }
+  static constexpr int W_BYTES = WX * WY * (int)sizeof(T);
+  static constexpr int C_BYTES = TX * TY * (int)sizeof(T);
+  static constexpr int P_BYTES = TX * TY * (int)sizeof(P);
+  static constexpr int N_CT = COEF7 ? 7 : 4;      // interior coefficient tiles
+  static constexpr int OFF_W = 0;
+  static constexpr int OFF_D = al(W_BYTES);       // flux form: D halo tile
+  static constexpr int OFF_CT = COEF7 ? al(W_BYTES) : al(W_BYTES) + al(W_BYTES);
+  static constexpr int OFF_P = OFF_CT + N_CT * C_BYTES;
+  static constexpr int STAGE = al(OFF_P + P_BYTES);
+  static constexpr int SMEM = NST * STAGE + 128 + 128;  // + mbarriers + alignment slack
+};
+
+// ---- PTX wrappers ------------------------------------------------------------
+__device__ __forceinline__ uint32_t smem_u32(const void* p) {
+  return (uint32_t)__cvta_generic_to_shared(p);
+}
+__device__ __forceinline__ void mbar_init(uint32_t bar, uint32_t count) {
+  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(bar), "r"(count) : "memory");
+}
+__device__ __forceinline__ void fence_mbar_init() {
+  asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+}
+__device__ __forceinline__ void fence_proxy_async() {
+  asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+}
+__device__ __forceinline__ void mbar_expect_tx(uint32_t bar, uint32_t bytes) {
+  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(bar), "r"(bytes)
+               : "memory");
+}
+__device__ __forceinline__ void tma_load_3d(uint32_t dst, const CUtensorMap* map, int x, int y,
+                                            int z, uint32_t bar) {
+  asm volatile(
+      "cp.async.bulk.tensor.3d.shared::cluster.global.mbarrier::complete_tx::bytes"
+      " [%0], [%1, {%2, %3, %4}], [%5];" ::"r"(dst),
+      "l"(reinterpret_cast<uint64_t>(map)), "r"(x), "r"(y), "r"(z), "r"(bar)
+      : "memory");
+}
+__device__ __forceinline__ bool mbar_try_wait(uint32_t bar, uint32_t parity) {
+  uint32_t ok;
+  asm volatile(
+      "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n"
+      " selp.u32 %0, 1, 0, p;\n}"
+      : "=r"(ok)
+      : "r"(bar), "r"(parity)
+      : "memory");
+  return ok != 0;
+}
+__device__ __forceinline__ uint64_t global_ns() {
+  uint64_t t;
+  asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+  return t;
+}
+// Wait for the given phase parity; false when limit_ns of wall time passed.
+__device__ __forceinline__ bool mbar_wait_bounded(uint32_t bar, uint32_t parity,
+                                                  uint64_t limit_ns) {
+  if (mbar_try_wait(bar, parity)) return true;
+  const uint64_t t0 = global_ns();
+  while (!mbar_try_wait(bar, parity)) {
+    if (global_ns() - t0 > limit_ns) return false;
+  }
+  return true;
+}
+
+static constexpr uint64_t kWaitLimitNs = 500000000ull;  // 0.5 s; a plane lands in microseconds
+
+template <int FMT, bool COEF7>
+__global__ void __launch_bounds__(256, COEF7 ? 2 : 3)
+k_newton_tma(const __grid_constant__ NewtonMaps M, const StencilDev g, const NewtonScalars s,
+             void* __restrict__ w_out_, void* __restrict__ p_, double* partials, DevCtl* ctl,
+             int zc) {
+  using C = TmaCfg<FMT, COEF7>;
+  using T = typename C::T;
+  using P = typename C::P;
+  if (*(volatile int*)&ctl->done != 0) return;
+  extern __shared__ __align__(128) unsigned char smem_raw[];
+  // stage tiles start on 128-byte boundaries whatever the static shared memory
+  const uint32_t raw = smem_u32(smem_raw);
+  const uint32_t sbase = (raw + 127u) & ~127u;
+  unsigned char* smem = smem_raw + (sbase - raw);
+  const uint32_t bar0 = sbase + C::NST * C::STAGE;
+  const int tx = threadIdx.x, ty = threadIdx.y, tid = ty * C::TX + tx;
+  const int x0 = blockIdx.x * C::TX, y0 = blockIdx.y * C::TY;
+  const int z0 = blockIdx.z * zc;
+  const int z1 = min(z0 + zc, g.nz);
+  const int nplanes = z1 - z0 + 2;  // z0-1 .. z1
+  const bool needp = s.j > 0;
+  const uint32_t tx_halo = C::W_BYTES + (COEF7 ? 0 : C::W_BYTES);
+  const uint32_t tx_full = tx_halo + C::N_CT * C::C_BYTES + (needp ? C::P_BYTES : 0);
+
+  if (tid == 0) {
+    for (int i = 0; i < C::NST; ++i) mbar_init(bar0 + 8 * i, 1);
+    fence_mbar_init();
+  }
+  __syncthreads();
+
+  int last_issued = -1;  // meaningful in thread 0
+  auto issue = [&](int q) {
+    const int stg = q & (C::NST - 1);
+    const uint32_t base = sbase + stg * C::STAGE;
+    const uint32_t bar = bar0 + 8 * stg;
+    const int z = z0 - 1 + q;
+    const bool halo = (q == 0) || (q == nplanes - 1);
+    mbar_expect_tx(bar, halo ? tx_halo : tx_full);
+    tma_load_3d(base + C::OFF_W, &M.w, x0 - C::HX, y0 - 1, z, bar);
+    if (!COEF7) tma_load_3d(base + C::OFF_D, &M.c[0], x0 - C::HX, y0 - 1, z, bar);
+    if (!halo) {
+#pragma unroll
+      for (int k = 0; k < C::N_CT; ++k)
+        tma_load_3d(base + C::OFF_CT + k * C::C_BYTES, &M.c[COEF7 ? k : k + 1], x0, y0, z, bar);
+      if (needp) tma_load_3d(base + C::OFF_P, &M.p, x0, y0, z, bar);
+    }
+    last_issued = q;
+  };
+  int waited_ok = -1;  // last plane whose copies this thread saw complete
+  auto wait = [&](int q) {
+    const bool ok =
+        mbar_wait_bounded(bar0 + 8 * (q & (C::NST - 1)), (q / C::NST) & 1, kWaitLimitNs);
+    if (ok) waited_ok = q;
+    return ok;
+  };
+
+  if (tid == 0) {
+    issue(0);
+    issue(1);
+    if (nplanes > 2) issue(2);
+  }
+
+  const T invg = from_d<T>(s.inv_gamma);
+  const T nshift = from_d<T>(-s.shift);
+  const P dn = from_d<P>(s.d_next);
+  const P d0 = from_d<P>(s.d0);
+  T aw = zero<T>();
+  P ap = zero<P>();
+  T* __restrict__ w_out = static_cast<T*>(w_out_);
+  P* __restrict__ p = static_cast<P*>(p_);
+  const int x = x0 + tx, y = y0 + ty;
+  const bool inside = (x < g.nx) && (y < g.ny);
+  const int wi = (ty + 1) * C::WX + tx + C::HX;
+  const int ci = ty * C::TX + tx;
+  constexpr int TT = C::TX * C::TY;
+  bool bad = false;
+
+  for (int q = 1; q <= nplanes - 2; ++q) {
+    if (tid == 0 && q + 2 < nplanes) {
+      fence_proxy_async();
+      issue(q + 2);
+    }
+    if (q == 1) {
+      if (!bad) bad = !wait(0);
+      if (!bad) bad = !wait(1);
+    }
+    if (!bad) bad = !wait(q + 1);
+    if (!bad && inside) {
+      const int z = z0 - 1 + q;
+      const unsigned char* sm = smem + (q & (C::NST - 1)) * C::STAGE;
+      const unsigned char* smm = smem + ((q - 1) & (C::NST - 1)) * C::STAGE;
+      const unsigned char* smp = smem + ((q + 1) & (C::NST - 1)) * C::STAGE;
+      const T* Wc = reinterpret_cast<const T*>(sm + C::OFF_W);
+      const T* Wm = reinterpret_cast<const T*>(smm + C::OFF_W);
+      const T* Wp = reinterpret_cast<const T*>(smp + C::OFF_W);
+      const T* Ct = reinterpret_cast<const T*>(sm + C::OFF_CT);
+      const T wc = Wc[wi];
+      T acc;
+      if constexpr (COEF7) {
+        acc = mul(Ct[6 * TT + ci], wc);
+        acc = mac(acc, Ct[0 * TT + ci], Wc[wi - 1]);
+        acc = mac(acc, Ct[1 * TT + ci], Wc[wi + 1]);
+        acc = mac(acc, Ct[2 * TT + ci], Wc[wi - C::WX]);
+        acc = mac(acc, Ct[3 * TT + ci], Wc[wi + C::WX]);
+        acc = mac(acc, Ct[4 * TT + ci], Wm[wi]);
+        acc = mac(acc, Ct[5 * TT + ci], Wp[wi]);
+      } else {
+        // flux form: ghost w is 0 (Dirichlet, from the zero fill) or w_c
+        // (Neumann); ghost D is D_c
+        const T* Dt = reinterpret_cast<const T*>(sm + C::OFF_D);
+        const T* Dm_ = reinterpret_cast<const T*>(smm + C::OFF_D);
+        const T* Dp_ = reinterpret_cast<const T*>(smp + C::OFF_D);
+        const T Dc = Dt[wi];
+        const T wxm = (x == 0 && g.bc[0]) ? wc : Wc[wi - 1];
+        const T wxp = (x == g.nx - 1 && g.bc[1]) ? wc : Wc[wi + 1];
+        const T wym = (y == 0 && g.bc[2]) ? wc : Wc[wi - C::WX];
+        const T wyp = (y == g.ny - 1 && g.bc[3]) ? wc : Wc[wi + C::WX];
+        const T Dxm = x > 0 ? Dt[wi - 1] : Dc;
+        const T Dxp = x < g.nx - 1 ? Dt[wi + 1] : Dc;
+        const T Dym = y > 0 ? Dt[wi - C::WX] : Dc;
+        const T Dyp = y < g.ny - 1 ? Dt[wi + C::WX] : Dc;
+        acc = mul(add(Dc, Dxp), sub(wxp, wc));
+        acc = mac(acc, add(Dc, Dxm), sub(wxm, wc));
+        acc = mac(acc, Ct[0 * TT + ci], sub(wxp, wxm));
+        T ay = mul(add(Dc, Dyp), sub(wyp, wc));
+        ay = mac(ay, add(Dc, Dym), sub(wym, wc));
+        acc = g.uniform ? add(acc, ay) : mac(acc, from_d<T>(g.ratio[1]), ay);
+        acc = mac(acc, Ct[1 * TT + ci], sub(wyp, wym));
+        if (g.dim == 3) {
+          const T wzm = (z == 0 && g.bc[4]) ? wc : Wm[wi];
+          const T wzp = (z == g.nz - 1 && g.bc[5]) ? wc : Wp[wi];
+          const T Dzm = z > 0 ? Dm_[wi] : Dc;
+          const T Dzp = z < g.nz - 1 ? Dp_[wi] : Dc;
+          T az = mul(add(Dc, Dzp), sub(wzp, wc));
+          az = mac(az, add(Dc, Dzm), sub(wzm, wc));
+          acc = g.uniform ? add(acc, az) : mac(acc, from_d<T>(g.ratio[2]), az);
+          acc = mac(acc, Ct[2 * TT + ci], sub(wzp, wzm));
+        }
+        acc = mac(acc, Ct[3 * TT + ci], wc);
+      }
+      const T wn = mac(mul(acc, invg), nshift, wc);
+      const P* Pt = reinterpret_cast<const P*>(sm + C::OFF_P);
+      const P pold = needp ? Pt[ci] : mul(d0, to_p(wc));
+      const P pn = mac(pold, dn, to_p(wn));
+      const int64_t idx = ((int64_t)z * g.ny + y) * g.pitch + x;
+      st(w_out, idx, wn);
+      st(p, idx, pn);
+      aw = mac(aw, wn, wn);
+      ap = mac(ap, pn, pn);
+    }
+    if (__syncthreads_or(bad)) {
+      bad = true;
+      break;
+    }
+  }
+  if (bad && tid == 0) {
+    atomicOr(&ctl->err, 1);
+    // let this block's copies in flight land before its shared memory goes away
+    for (int q = waited_ok + 1; q <= last_issued; ++q)
+      mbar_wait_bounded(bar0 + 8 * (q & (C::NST - 1)), (q / C::NST) & 1, kWaitLimitNs / 8);
+  }
+
+  double nw2 = to_d(aw), np2 = to_d(ap);
+  if (last_block_reduce2<RED_SUM>(nw2, np2, partials, ctl)) {
+    if (tid == 0) {
+      ctl->nw2 = nw2;
+      ctl->np2 = np2;
+      if (*(volatile int*)&ctl->err) {
+        ctl->done = 5;
+        ctl->degree = s.j + 1;
+      } else if (!finite_d(nw2) || !finite_d(np2)) {
+        ctl->done = 4;
+        ctl->degree = s.j + 1;
+      } else if (s.j == 0 && np2 == 0.0) {  // zero input: p = 0 at degree 0
+        ctl->done = 1;
+        ctl->degree = 0;
+      } else if (fabs(s.d_next) * sqrt(nw2) <= s.tol * sqrt(np2)) {
+        ctl->done = 1;
+        ctl->degree = s.j + 1;
+      } else if (s.j + 1 >= s.m_max) {
+        ctl->done = 2;
+        ctl->degree = s.j + 1;
+      }
+    }
+  }
+}
+
+// ---- host side ----------------------------------------------------------------
+typedef CUresult (*EncodeTiledFn)(CUtensorMap*, CUtensorMapDataType, cuuint32_t, void*,
+                                  const cuuint64_t*, const cuuint64_t*, const cuuint32_t*,
+                                  const cuuint32_t*, CUtensorMapInterleave, CUtensorMapSwizzle,
+                                  CUtensorMapL2promotion, CUtensorMapFloatOOBfill);
+
+static EncodeTiledFn encode_fn() {
+  static EncodeTiledFn fn = nullptr;
+  static bool tried = false;
+  if (!tried) {
+    tried = true;
+    void* p = nullptr;
+    cudaDriverEntryPointQueryResult q;
+    if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault,
+                                         &q) == cudaSuccess &&
+        q == cudaDriverEntryPointSuccess)
+      fn = reinterpret_cast<EncodeTiledFn>(p);
+    else
+      cudaGetLastError();
+  }
+  return fn;
+}
+
+bool encode_map(CUtensorMap* m, const void* base, int elem_bytes, const StencilDev& g, int halo) {
+  EncodeTiledFn fn = encode_fn();
+  if (!fn) return false;
+  const int hx = 16 / elem_bytes;
+  cuuint64_t dims[3] = {(cuuint64_t)g.nx, (cuuint64_t)g.ny, (cuuint64_t)g.nz};
+  cuuint64_t strides[2] = {(cuuint64_t)g.pitch * elem_bytes,
+                           (cuuint64_t)g.pitch * g.ny * elem_bytes};
+  cuuint32_t box[3] = {(cuuint32_t)(32 + (halo ? 2 * hx : 0)), (cuuint32_t)(8 + (halo ? 2 : 0)),
+                       1};
+  cuuint32_t estr[3] = {1, 1, 1};
+  CUresult r = fn(m, elem_bytes == 8 ? CU_TENSOR_MAP_DATA_TYPE_FLOAT64 : CU_TENSOR_MAP_DATA_TYPE_FLOAT32,
+                  3, const_cast<void*>(base), dims, strides, box, estr,
+                  CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE,
+                  CU_TENSOR_MAP_L2_PROMOTION_L2_128B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+  return r == CUDA_SUCCESS;
+}
+
+static int tma_zchunk(const StencilDev& g) {
+  const int bxy = ((g.nx + 31) / 32) * ((g.ny + 7) / 8);
+  int zc = 32;
+  while (zc > 4 && (int64_t)bxy * ((g.nz + zc - 1) / zc) < 1216) zc /= 2;
+  if (zc > g.nz) zc = g.nz;
+  if (zc < 1) zc = 1;
+  while ((g.nz + zc - 1) / zc > 65535) zc *= 2;
+  return zc;
+}
+
+int newton_tma_blocks(const StencilDev& g) {
+  const int zc = tma_zchunk(g);
+  return ((g.nx + 31) / 32) * ((g.ny + 7) / 8) * ((g.nz + zc - 1) / zc);
+}
+
+template <int FMT, bool COEF7>
+static cudaError_t launch_one(const StencilDev& g, const NewtonMaps& M, void* w_out, void* p,
+                              const NewtonScalars& s, double* partials, DevCtl* ctl,
+                              cudaStream_t st) {
+  using C = TmaCfg<FMT, COEF7>;
+  static bool attr = false;
+  if (!attr) {
+    cudaError_t e = cudaFuncSetAttribute(k_newton_tma<FMT, COEF7>,
+                                         cudaFuncAttributeMaxDynamicSharedMemorySize, C::SMEM);
+    if (e != cudaSuccess) return e;
+    attr = true;
+  }
+  const int zc = tma_zchunk(g);
+  dim3 grid((g.nx + 31) / 32, (g.ny + 7) / 8, (g.nz + zc - 1) / zc), block(32, 8, 1);
+  k_newton_tma<FMT, COEF7><<<grid, block, C::SMEM, st>>>(M, g, s, w_out, p, partials, ctl, zc);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_newton_tma(const StencilDev& g, const NewtonMaps& M, void* w_out, void* p,
+                              const NewtonScalars& s, int fmt, double* partials, DevCtl* ctl,
+                              cudaStream_t st) {
+  if (fmt == VF_DF) return launch_one<VF_DF, true>(g, M, w_out, p, s, partials, ctl, st);
+  if (fmt == VF_F64) return launch_one<VF_F64, true>(g, M, w_out, p, s, partials, ctl, st);
+  return launch_one<VF_F32, false>(g, M, w_out, p, s, partials, ctl, st);
+}
+
+}  // namespace ei

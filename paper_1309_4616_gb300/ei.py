@@ -32,14 +32,15 @@ EXPORTS = [
 
 class Options(C.Structure):
     _fields_ = [("m_max", C.c_int), ("arith", C.c_int), ("fixed_s", C.c_int),
-                ("reserved", C.c_int * 5)]
+                ("profile", C.c_int), ("reserved", C.c_int * 4)]
 
 
 class Stats(C.Structure):
     _fields_ = [("alpha", C.c_double), ("beta", C.c_double), ("s", C.c_int),
                 ("restarts", C.c_int), ("matvecs", C.c_int), ("degree_sum", C.c_int),
                 ("degree_max", C.c_int), ("m_sched", C.c_int),
-                ("degrees", C.c_int * STATS_MAX_SUBSTEPS)]
+                ("degrees", C.c_int * STATS_MAX_SUBSTEPS), ("launches", C.c_int),
+                ("newton_timed", C.c_int), ("newton_ms", C.c_double)]
 
     def degree_list(self):
         return [int(self.degrees[i]) for i in range(min(self.s, STATS_MAX_SUBSTEPS))]
@@ -48,7 +49,8 @@ class Stats(C.Structure):
         return {"alpha": self.alpha, "beta": self.beta, "s": self.s, "restarts": self.restarts,
                 "matvecs": self.matvecs, "degree_sum": self.degree_sum,
                 "degree_max": self.degree_max, "m_sched": self.m_sched,
-                "degrees": self.degree_list()}
+                "degrees": self.degree_list(), "launches": self.launches,
+                "newton_timed": self.newton_timed, "newton_ms": self.newton_ms}
 
 
 class EIError(RuntimeError):
@@ -228,18 +230,22 @@ class Context:
             setattr(o, k, v)
         return C.byref(o)
 
+    def _n(self):
+        # before set_operator the library itself reports EI_ERR_STATE
+        return self.n if self.n > 0 else None
+
     def phi_apply(self, k, h, v, out, tol, options=None):
         dt = self._dtype(self.prec)
         st = Stats()
-        _check(lib().ei_phi_apply(self._h, k, h, _dev_ptr(v, dt, self.n, "v"),
-                                  _dev_ptr(out, dt, self.n, "out"), tol, self._opts(options),
+        _check(lib().ei_phi_apply(self._h, k, h, _dev_ptr(v, dt, self._n(), "v"),
+                                  _dev_ptr(out, dt, self._n(), "out"), tol, self._opts(options),
                                   C.byref(st)), "ei_phi_apply")
         return st
 
     def step(self, method, h, u, nonlin, tol, options=None):
         dt = self._dtype(self.prec)
         st = Stats()
-        _check(lib().ei_step(self._h, method, h, _dev_ptr(u, dt, self.n, "u"), nonlin, tol,
+        _check(lib().ei_step(self._h, method, h, _dev_ptr(u, dt, self._n(), "u"), nonlin, tol,
                              self._opts(options), C.byref(st)), "ei_step")
         return st
 
