@@ -143,6 +143,35 @@ ei_status ei_set_operator_csr(ei_ctx* ctx, int64_t n, int64_t nnz, const int64_t
  * method.  Host outputs. */
 ei_status ei_estimate_spectrum(ei_ctx* ctx, double* alpha, double* beta);
 
+/* Gershgorin interval of a stencil operator, computed with no device memory
+ * allocation at all.  (The paper has no counterpart: this entry exists for
+ * callers that must not allocate.)  Callers that cannot call cudaMalloc:
+ * code running while its stream is captured into a CUDA graph, real-time or
+ * budgeted code that reserves all device memory up front, and hosts whose
+ * framework owns the GPU's memory.  The arguments describe the operator
+ * exactly as for ei_set_operator_stencil (device arrays or constants); the
+ * result equals the ei_estimate_spectrum interval of that operator.  No
+ * context is needed.
+ *   device, cuda_stream: where the reduction runs; the caller's current device
+ *     is restored before returning.  The call synchronises the stream.
+ *   alpha, beta: host outputs.
+ * Scratch: a fixed ~256 KB array inside the library, one per GPU that loads
+ * the library, held until the process exits.  It bounds the operator to
+ * n0*n1*n2 <= 2^27 points (512^3); larger operators return
+ * EI_ERR_INVALID_ARG.  The first call on a device looks the array up
+ * (cudaGetSymbolAddress) and so should come before any stream capture.
+ * Every call shares the array and the call clears its arrival counter first:
+ * calls that overlap on the GPU (other streams, other host threads) race and
+ * must be serialised by the caller.
+ * Errors: EI_ERR_INVALID_ARG (bad arguments, too many points), EI_ERR_CUDA,
+ * EI_ERR_NONFINITE (NaN/Inf in the coefficients). */
+ei_status ei_estimate_spectrum_stencil_noalloc(int device, void* cuda_stream, int dim,
+                                               const int64_t n[3], const double dx[3],
+                                               const void* D, double D_const,
+                                               const void* const b[3], const double b_const[3],
+                                               const void* c, double c_const, const int bc[6],
+                                               int prec, double* alpha, double* beta);
+
 /* out = phi_k(hA) v  (Eq. (2) for k = 1; phi_0 = exp).  v, out: device
  * vectors of the operator's size and precision; they may alias.
  * k = 1: substepped ODE form; k = 0: (e^{(h/s)A})^s v; k >= 2: one substep

@@ -11,6 +11,9 @@
 #include <math.h>
 #include <stdint.h>
 
+#include <mutex>
+
+#include "ei.h"
 #include "ei_device.cuh"
 
 namespace ei {
@@ -798,3 +801,145 @@ cudaError_t launch_zero(void* x, int fmt, int64_t n, cudaStream_t stm) {
 }
 
 }  // namespace ei
+
+// ===========================================================================
+// Spectral interval without device allocation
+// ===========================================================================
+// Some callers may not allocate device memory at all: code that runs while a
+// stream is being captured into a CUDA graph (an allocation there breaks the
+// capture), real-time loops and device-memory budgets in which every byte is
+// reserved up front, and hosts whose framework owns all of the GPU's memory.
+// ei_estimate_spectrum_stencil_noalloc serves them: it computes the Gershgorin
+// interval of a stencil operator straight from the caller's coefficient
+// arrays, with its reduction scratch (one pair of doubles per block and the
+// arrival counter) in the fixed array below instead of memory from
+// cudaMalloc.  The array exists once per GPU that loads the library and stays
+// there until the process exits.
+namespace ei {
+
+static constexpr int kNoallocChunk = 8192;       // grid points per block (256 threads x 32)
+static constexpr int kNoallocMaxBlocks = 16384;  // so at most 2^27 = 512^3 points
+static constexpr int kNoallocMaxDevices = 64;
+static constexpr size_t kNoallocBytes = 256 + sizeof(double) * 2 * kNoallocMaxBlocks;
+
+static __device__ __align__(256) unsigned char g_noalloc_scratch[kNoallocBytes];
+
+// The Gershgorin row kernel with a fixed chunk of points per block; the
+// control block sits at the start of the scratch, the block partials after it.
+template <class U>
+__global__ void __launch_bounds__(EI_TPB) k_stencil_gershgorin_chunk(UserCoef u, unsigned char* scratch) {
+  DevCtl* ctl = reinterpret_cast<DevCtl*>(scratch);
+  double* partials = reinterpret_cast<double*>(scratch + 256);
+  const int64_t n = (int64_t)u.nx * u.ny * u.nz;
+  const int64_t i0 = (int64_t)blockIdx.x * kNoallocChunk;
+  const int64_t i1 = i0 + kNoallocChunk < n ? i0 + kNoallocChunk : n;
+  double mn = INFINITY, mx = -INFINITY;
+  for (int64_t i = i0 + threadIdx.x; i < i1; i += blockDim.x) {
+    const int x = (int)(i % u.nx);
+    const int y = (int)((i / u.nx) % u.ny);
+    const int z = (int)(i / ((int64_t)u.nx * u.ny));
+    double a[6], diag, rad;
+    stencil_row<U>(u, i, x, y, z, a, diag, rad);
+    mn = fmin(mn, diag - rad);
+    mx = fmax(mx, diag + rad);
+  }
+  if (last_block_reduce2<RED_MINMAX>(mn, mx, partials, ctl)) {
+    if (threadIdx.x == 0) {
+      ctl->mn = mn;
+      ctl->mx = mx;
+    }
+  }
+}
+
+// Device address of the scratch array, looked up once per device (with that
+// device current) and cached.
+static void* noalloc_scratch(int device, cudaError_t* err) {
+  static std::mutex mu;
+  static void* addr[kNoallocMaxDevices] = {nullptr};
+  std::lock_guard<std::mutex> lock(mu);
+  if (!addr[device]) {
+    void* p = nullptr;
+    *err = cudaGetSymbolAddress(&p, g_noalloc_scratch);
+    if (*err != cudaSuccess) return nullptr;
+    addr[device] = p;
+  }
+  *err = cudaSuccess;
+  return addr[device];
+}
+
+}  // namespace ei
+
+extern "C" ei_status ei_estimate_spectrum_stencil_noalloc(
+    int device, void* cuda_stream, int dim, const int64_t n[3], const double dx[3], const void* D,
+    double D_const, const void* const b[3], const double b_const[3], const void* c,
+    double c_const, const int bc[6], int prec, double* alpha, double* beta) {
+  using namespace ei;
+  if (!n || !dx || !bc || !alpha || !beta || (dim != 2 && dim != 3) ||
+      (prec != EI_PREC_F64 && prec != EI_PREC_F32) || device < 0 || device >= kNoallocMaxDevices)
+    return EI_ERR_INVALID_ARG;
+  const int64_t ext[3] = {n[0], n[1], dim == 3 ? n[2] : 1};
+  for (int e = 0; e < 3; ++e)
+    if (ext[e] < 1 || ext[e] > ((int64_t)1 << 30)) return EI_ERR_INVALID_ARG;
+  for (int e = 0; e < dim; ++e)
+    if (!(dx[e] > 0) || !isfinite(dx[e])) return EI_ERR_INVALID_ARG;
+  for (int f = 0; f < 2 * dim; ++f)
+    if (bc[f] != EI_BC_DIRICHLET0 && bc[f] != EI_BC_NEUMANN0) return EI_ERR_INVALID_ARG;
+  const int64_t npts = ext[0] * ext[1] * ext[2];
+  if ((double)ext[0] * ext[1] * ext[2] > (double)kNoallocMaxBlocks * kNoallocChunk)
+    return EI_ERR_INVALID_ARG;  // more points than the fixed scratch can reduce
+  int prev = 0;
+  if (cudaGetDevice(&prev) != cudaSuccess) return EI_ERR_CUDA;
+  if (cudaSetDevice(device) != cudaSuccess) {
+    cudaGetLastError();
+    return EI_ERR_CUDA;
+  }
+  ei_status rc = EI_OK;
+  cudaError_t e = cudaSuccess;
+  unsigned char* scratch = static_cast<unsigned char*>(noalloc_scratch(device, &e));
+  if (!scratch) {
+    rc = EI_ERR_CUDA;
+  } else {
+    UserCoef u;
+    u.dim = dim;
+    u.nx = (int)ext[0];
+    u.ny = (int)ext[1];
+    u.nz = (int)ext[2];
+    for (int f = 0; f < 6; ++f) u.bc[f] = (f < 2 * dim) ? bc[f] : EI_BC_NEUMANN0;
+    for (int k = 0; k < 3; ++k) {
+      u.dx[k] = k < dim ? dx[k] : 1.0;
+      u.b[k] = (b && k < dim) ? b[k] : nullptr;
+      u.bc_[k] = (b_const && k < dim) ? b_const[k] : 0.0;
+    }
+    u.D = D;
+    u.Dc = D_const;
+    u.c = c;
+    u.cc = c_const;
+    cudaStream_t st = (cudaStream_t)cuda_stream;
+    const int blocks = (int)((npts + kNoallocChunk - 1) / kNoallocChunk);
+    double out[2] = {0.0, 0.0};
+    // the arrival counter must start at zero; the rest is written before it is read
+    e = cudaMemsetAsync(scratch, 0, sizeof(DevCtl), st);
+    if (e == cudaSuccess) {
+      if (prec == EI_PREC_F64)
+        k_stencil_gershgorin_chunk<double><<<blocks, EI_TPB, 0, st>>>(u, scratch);
+      else
+        k_stencil_gershgorin_chunk<float><<<blocks, EI_TPB, 0, st>>>(u, scratch);
+      e = cudaGetLastError();
+    }
+    if (e == cudaSuccess)
+      e = cudaMemcpyAsync(out, scratch + offsetof(DevCtl, mn), sizeof(out),
+                          cudaMemcpyDeviceToHost, st);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+    if (e != cudaSuccess) {
+      cudaGetLastError();
+      rc = EI_ERR_CUDA;
+    } else if (!isfinite(out[0]) || !isfinite(out[1])) {
+      rc = EI_ERR_NONFINITE;
+    } else {
+      *alpha = out[0];
+      *beta = out[1];
+    }
+  }
+  cudaSetDevice(prev);
+  return rc;
+}

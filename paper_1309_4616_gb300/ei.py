@@ -26,7 +26,7 @@ EXPORTS = [
     "ei_create", "ei_destroy", "ei_set_stream", "ei_set_operator_stencil",
     "ei_set_operator_csr", "ei_estimate_spectrum", "ei_phi_apply", "ei_step",
     "ei_step_host", "ei_leja_points", "ei_divided_differences", "ei_schedule",
-    "ei_status_string",
+    "ei_status_string", "ei_estimate_spectrum_stencil_noalloc",
 ]
 
 
@@ -85,6 +85,9 @@ def lib():
                                              C.c_int, dp]
         L.ei_schedule.argtypes = [C.c_int, C.c_double, C.c_double, C.c_double, C.c_double,
                                   C.c_int, ip, ip]
+        L.ei_estimate_spectrum_stencil_noalloc.argtypes = [
+            C.c_int, vp, C.c_int, i64p, dp, vp, C.c_double, C.POINTER(C.c_void_p), dp, vp,
+            C.c_double, ip, C.c_int, dp, dp]
         L.ei_status_string.argtypes = [C.c_int]
         L.ei_status_string.restype = C.c_char_p
         for name in EXPORTS:
