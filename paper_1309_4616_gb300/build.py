@@ -60,7 +60,7 @@ def build(force: bool = False, verbose: bool = False) -> str:
     for f in CPP_SOURCES:
         o = os.path.join(BUILD, f + ".o")
         objs.append(o)
-        jobs.append(["g++", "-std=c++17", "-O2", "-fPIC", "-Wall", "-I" + INCLUDE, "-I" + CSRC,
+        jobs.append(["g++", "-std=c++17", "-O3", "-fPIC", "-Wall", "-I" + INCLUDE, "-I" + CSRC,
                      "-I" + os.path.join(CUDA_HOME, "include"), "-c", os.path.join(CSRC, f),
                      "-o", o])
     with ThreadPoolExecutor(max_workers=len(jobs)) as ex:

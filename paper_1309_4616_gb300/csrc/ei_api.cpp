@@ -22,7 +22,7 @@ namespace ei {
 const double* leja_table();
 void divided_differences(int k, double tau, double c, double gamma, int m, double* out);
 int schedule(int k, double h, double c, double gamma, double tol, int m_max, int* s_out,
-             int* m_out);
+             int* m_out, double* d_out);
 double phi_scalar(int k, double z);
 }  // namespace ei
 
@@ -390,17 +390,21 @@ static ei_status phi1_substeps(ei_ctx* c, Prepared& P, const void* qc, double h,
   interval(alpha, beta, &cc, &gamma);
   const int m_max = (opt && opt->m_max > 0 && opt->m_max <= 100) ? opt->m_max : 100;
   int s = 1, m_pred = 0;
+  std::vector<double> d(m_max + 1);
+  bool have_d = false;  // the schedule hands back the divided differences of its s
   if (opt && opt->fixed_s > 0) {
     s = opt->fixed_s;
-  } else if (schedule(1, h, cc, gamma, tol, m_max, &s, &m_pred) != 0) {
+  } else if (schedule(1, h, cc, gamma, tol, m_max, &s, &m_pred, d.data()) != 0) {
     return EI_ERR_NOT_CONVERGED;
+  } else {
+    have_d = true;
   }
   if (st) st->m_sched = m_pred;
-  std::vector<double> d(m_max + 1);
   int restarts = 0, matvecs = 0;
   while (s <= (1 << 20)) {
     const double tau = h / s;
-    divided_differences(1, tau, cc, gamma, m_max, d.data());
+    if (!have_d) divided_differences(1, tau, cc, gamma, m_max, d.data());
+    have_d = false;
     if (s > 1) EI_LAUNCH(launch_zero(P.y, P.fmt, P.n_alloc, c->stream));
     bool ok_all = true;
     int dsum = 0, dmax = 0;
@@ -705,7 +709,8 @@ static ei_status phi_apply_impl(ei_ctx* c, int k, double h, const void* v, void*
     const int m_max = (opt && opt->m_max > 0 && opt->m_max <= 100) ? opt->m_max : 100;
     int s = 1, m_pred = 0;
     if (opt && opt->fixed_s > 0) s = opt->fixed_s;
-    else if (schedule(k, h, cc, gamma, tol, m_max, &s, &m_pred) != 0) return EI_ERR_NOT_CONVERGED;
+    else if (schedule(k, h, cc, gamma, tol, m_max, &s, &m_pred, nullptr) != 0)
+      return EI_ERR_NOT_CONVERGED;
     if (st) st->m_sched = m_pred;
     std::vector<double> d(m_max + 1);
     int restarts = 0;

@@ -91,8 +91,9 @@ const double* leja_table() {
 // (nonnegative off the diagonal), so exp(N) = e^{-sigma} exp(N + sigma I) with
 // N + sigma I >= 0 entrywise: Taylor terms and squarings add only
 // nonnegative numbers, which keeps every entry relatively accurate.
-// Scaling: entries <= 1 after 2^-q, q >= 5; Taylor degree 64 (per-factor
-// truncation is negligible for the band offsets that matter).
+// Scaling: entries <= 4 after 2^-q, q >= 5; Taylor degree 64 (all terms are
+// nonnegative, so the series has no cancellation; its per-factor truncation
+// is negligible for the band offsets that reach the result).
 // ---------------------------------------------------------------------------
 static void expm_bidiag_col0(int n, const double* dg, const double* sd, double* out) {
   double sigma = 0.0, mx = 0.0;
@@ -100,7 +101,7 @@ static void expm_bidiag_col0(int n, const double* dg, const double* sd, double* 
   for (int i = 0; i < n; ++i) mx = std::max(mx, dg[i] + sigma);
   for (int i = 0; i + 1 < n; ++i) mx = std::max(mx, sd[i]);
   int q = 5;
-  while (ldexp(1.0, q) < mx) ++q;
+  while (ldexp(4.0, q) < mx) ++q;  // entries of X at most 4
   const double sc = ldexp(1.0, -q);
   std::vector<double> xd(n), xs(n > 1 ? n - 1 : 1);
   for (int i = 0; i < n; ++i) xd[i] = (dg[i] + sigma) * sc;
@@ -127,15 +128,25 @@ static void expm_bidiag_col0(int n, const double* dg, const double* sd, double* 
   const double es = exp(-sigma * sc);
   for (int r = 0; r < n; ++r)
     for (int c = 0; c <= r; ++c) T[(size_t)r * n + c] *= es;
-  // square q times (the last squaring only for column 0)
+  // square q times (the last squaring only for column 0); row r of T*T is
+  // accumulated as sum_l T[r][l] * (row l of T), l increasing, so every entry
+  // sums its terms in the same order as the dot-product form
   for (int sq = 0; sq < q; ++sq) {
     const bool last = (sq == q - 1);
     for (int r = 0; r < n; ++r) {
-      const int cmax = last ? 0 : r;
-      for (int c = 0; c <= cmax; ++c) {
-        double s = 0.0;
-        for (int l = c; l <= r; ++l) s += T[(size_t)r * n + l] * T[(size_t)l * n + c];
-        U[(size_t)r * n + c] = s;
+      double* Ur = &U[(size_t)r * n];
+      const double* Tr = &T[(size_t)r * n];
+      if (last) {
+        double s0 = 0.0;
+        for (int l = 0; l <= r; ++l) s0 += Tr[l] * T[(size_t)l * n];
+        Ur[0] = s0;
+        continue;
+      }
+      for (int c = 0; c <= r; ++c) Ur[c] = 0.0;
+      for (int l = 0; l <= r; ++l) {
+        const double t = Tr[l];
+        const double* Tl = &T[(size_t)l * n];
+        for (int c = 0; c <= l; ++c) Ur[c] += t * Tl[c];
       }
     }
     std::swap(T, U);
@@ -188,7 +199,7 @@ double phi_scalar(int k, double z) {
 static const int kGrid = 2001;
 
 int schedule(int k, double h, double c, double gamma, double tol, int m_max, int* s_out,
-             int* m_out) {
+             int* m_out, double* d_out) {
   const double* xi = leja_table();
   std::vector<double> g(kGrid), f(kGrid), p(kGrid), om(kGrid), d(m_max + 1);
   const double step = 4.0 / (kGrid - 1);  // the same points as numpy.linspace(-2, 2, 2001)
@@ -215,6 +226,8 @@ int schedule(int k, double h, double c, double gamma, double tol, int m_max, int
       if (err <= tol * fmax) {
         *s_out = s;
         *m_out = j;
+        if (d_out)
+          for (int i = 0; i <= m_max; ++i) d_out[i] = d[i];
         return 0;
       }
     }
@@ -245,5 +258,6 @@ extern "C" ei_status ei_schedule(int k, double h, double c, double gamma, double
   if (k < 0 || k > 8 || !(h > 0) || !(tol > 0) || m_max < 1 || m_max > ei::kMaxM || !s_out ||
       !m_out || !(gamma > 0) || !isfinite(c) || !isfinite(gamma))
     return EI_ERR_INVALID_ARG;
-  return ei::schedule(k, h, c, gamma, tol, m_max, s_out, m_out) ? EI_ERR_NOT_CONVERGED : EI_OK;
+  return ei::schedule(k, h, c, gamma, tol, m_max, s_out, m_out, nullptr) ? EI_ERR_NOT_CONVERGED
+                                                                          : EI_OK;
 }

@@ -12,9 +12,10 @@
 // over the third index; here the slice is fed by TMA).  Per plane, one thread
 // issues cp.async.bulk.tensor loads of the w tile with its x/y halo (x start
 // rounded down to a 16-byte boundary), the coefficient tiles and the p tile
-// into a 4-stage ring; an mbarrier per stage carries the transaction bytes.
-// Planes z-1, z, z+1 are resident while plane z is computed and plane z+2 is
-// in flight.  Halo columns and planes outside the grid arrive as zeros (TMA
+// into two rings: the w tiles (planes z-1, z, z+1 are read while plane z is
+// computed) and the coefficient and p tiles (plane z only).  Four planes are in
+// flight ahead of the one being computed; an mbarrier per plane carries the
+// transaction bytes of all its copies.  Halo columns and planes outside the grid arrive as zeros (TMA
 // out-of-bounds fill); with the explicit-coefficient layout every coefficient
 // that would touch them is zero, so no boundary branches are needed.
 //
@@ -33,7 +34,11 @@ template <int FMT, bool COEF7>
 struct TmaCfg {
   using T = typename VT<FMT>::T;
   using P = typename VT<FMT>::P;
-  static constexpr int TX = 32, TY = 8, NST = 4;
+  static constexpr int TX = 32, TY = 8;
+  static constexpr int PF = 4;          // planes in flight ahead of the one computed
+  static constexpr int NW = PF + 2;     // w ring: planes z-1, z, z+1 resident + PF in flight
+  static constexpr int NC = PF + 1;     // coefficient/p ring: plane z resident + PF in flight
+  static constexpr int NBAR = 8;        // one mbarrier per plane, reused every 8 planes
   static constexpr int HX = 16 / (int)sizeof(T);  // x halo, rounded to 16 bytes
   static constexpr int WX = TX + 2 * HX, WY = TY + 2;
   static constexpr int al(int b) { return (b + 127) / 128 * 128; }
@@ -41,12 +46,17 @@ struct TmaCfg {
   static constexpr int C_BYTES = TX * TY * (int)sizeof(T);
   static constexpr int P_BYTES = TX * TY * (int)sizeof(P);
   static constexpr int N_CT = COEF7 ? 7 : 4;      // interior coefficient tiles
+  // w-ring slot: w halo tile (+ D halo tile in the flux form)
   static constexpr int OFF_W = 0;
-  static constexpr int OFF_D = al(W_BYTES);       // flux form: D halo tile
-  static constexpr int OFF_CT = COEF7 ? al(W_BYTES) : al(W_BYTES) + al(W_BYTES);
-  static constexpr int OFF_P = OFF_CT + N_CT * C_BYTES;
-  static constexpr int STAGE = al(OFF_P + P_BYTES);
-  static constexpr int SMEM = NST * STAGE + 128 + 128;  // + mbarriers + alignment slack
+  static constexpr int OFF_D = al(W_BYTES);
+  static constexpr int WSTAGE = COEF7 ? al(W_BYTES) : 2 * al(W_BYTES);
+  // coefficient-ring slot: interior coefficient tiles, then the p tile
+  static constexpr int OFF_CT = 0;
+  static constexpr int OFF_P = N_CT * C_BYTES;
+  static constexpr int CSTAGE = al(OFF_P + P_BYTES);
+  static constexpr int CRING = NW * WSTAGE;
+  static constexpr int BARS = CRING + NC * CSTAGE;
+  static constexpr int SMEM = BARS + 8 * NBAR + 128;  // + alignment slack
 };
 
 // ---- PTX wrappers ------------------------------------------------------------
@@ -103,7 +113,7 @@ __device__ __forceinline__ bool mbar_wait_bounded(uint32_t bar, uint32_t parity,
 static constexpr uint64_t kWaitLimitNs = 500000000ull;  // 0.5 s; a plane lands in microseconds
 
 template <int FMT, bool COEF7>
-__global__ void __launch_bounds__(256, COEF7 ? 2 : 3)
+__global__ void __launch_bounds__(256, COEF7 ? 2 : 4)
 k_newton_tma(const __grid_constant__ NewtonMaps M, const StencilDev g, const NewtonScalars s,
              void* __restrict__ w_out_, void* __restrict__ p_, double* partials, DevCtl* ctl,
              int zc) {
@@ -116,7 +126,7 @@ k_newton_tma(const __grid_constant__ NewtonMaps M, const StencilDev g, const New
   const uint32_t raw = smem_u32(smem_raw);
   const uint32_t sbase = (raw + 127u) & ~127u;
   unsigned char* smem = smem_raw + (sbase - raw);
-  const uint32_t bar0 = sbase + C::NST * C::STAGE;
+  const uint32_t bar0 = sbase + C::BARS;
   const int tx = threadIdx.x, ty = threadIdx.y, tid = ty * C::TX + tx;
   const int x0 = blockIdx.x * C::TX, y0 = blockIdx.y * C::TY;
   const int z0 = blockIdx.z * zc;
@@ -127,41 +137,39 @@ k_newton_tma(const __grid_constant__ NewtonMaps M, const StencilDev g, const New
   const uint32_t tx_full = tx_halo + C::N_CT * C::C_BYTES + (needp ? C::P_BYTES : 0);
 
   if (tid == 0) {
-    for (int i = 0; i < C::NST; ++i) mbar_init(bar0 + 8 * i, 1);
+    for (int i = 0; i < C::NBAR; ++i) mbar_init(bar0 + 8 * i, 1);
     fence_mbar_init();
   }
   __syncthreads();
 
   int last_issued = -1;  // meaningful in thread 0
   auto issue = [&](int q) {
-    const int stg = q & (C::NST - 1);
-    const uint32_t base = sbase + stg * C::STAGE;
-    const uint32_t bar = bar0 + 8 * stg;
+    const uint32_t wb = sbase + (q % C::NW) * C::WSTAGE;
+    const uint32_t cb = sbase + C::CRING + (q % C::NC) * C::CSTAGE;
+    const uint32_t bar = bar0 + 8 * (q % C::NBAR);
     const int z = z0 - 1 + q;
     const bool halo = (q == 0) || (q == nplanes - 1);
     mbar_expect_tx(bar, halo ? tx_halo : tx_full);
-    tma_load_3d(base + C::OFF_W, &M.w, x0 - C::HX, y0 - 1, z, bar);
-    if (!COEF7) tma_load_3d(base + C::OFF_D, &M.c[0], x0 - C::HX, y0 - 1, z, bar);
+    tma_load_3d(wb + C::OFF_W, &M.w, x0 - C::HX, y0 - 1, z, bar);
+    if (!COEF7) tma_load_3d(wb + C::OFF_D, &M.c[0], x0 - C::HX, y0 - 1, z, bar);
     if (!halo) {
 #pragma unroll
       for (int k = 0; k < C::N_CT; ++k)
-        tma_load_3d(base + C::OFF_CT + k * C::C_BYTES, &M.c[COEF7 ? k : k + 1], x0, y0, z, bar);
-      if (needp) tma_load_3d(base + C::OFF_P, &M.p, x0, y0, z, bar);
+        tma_load_3d(cb + C::OFF_CT + k * C::C_BYTES, &M.c[COEF7 ? k : k + 1], x0, y0, z, bar);
+      if (needp) tma_load_3d(cb + C::OFF_P, &M.p, x0, y0, z, bar);
     }
     last_issued = q;
   };
   int waited_ok = -1;  // last plane whose copies this thread saw complete
   auto wait = [&](int q) {
     const bool ok =
-        mbar_wait_bounded(bar0 + 8 * (q & (C::NST - 1)), (q / C::NST) & 1, kWaitLimitNs);
+        mbar_wait_bounded(bar0 + 8 * (q % C::NBAR), (q / C::NBAR) & 1, kWaitLimitNs);
     if (ok) waited_ok = q;
     return ok;
   };
 
   if (tid == 0) {
-    issue(0);
-    issue(1);
-    if (nplanes > 2) issue(2);
+    for (int q = 0; q <= C::PF && q < nplanes; ++q) issue(q);
   }
 
   const T invg = from_d<T>(s.inv_gamma);
@@ -180,9 +188,9 @@ k_newton_tma(const __grid_constant__ NewtonMaps M, const StencilDev g, const New
   bool bad = false;
 
   for (int q = 1; q <= nplanes - 2; ++q) {
-    if (tid == 0 && q + 2 < nplanes) {
+    if (tid == 0 && q + C::PF < nplanes) {
       fence_proxy_async();
-      issue(q + 2);
+      issue(q + C::PF);  // into the w slot of plane q-2 and the coefficient slot of q-1
     }
     if (q == 1) {
       if (!bad) bad = !wait(0);
@@ -191,13 +199,14 @@ k_newton_tma(const __grid_constant__ NewtonMaps M, const StencilDev g, const New
     if (!bad) bad = !wait(q + 1);
     if (!bad && inside) {
       const int z = z0 - 1 + q;
-      const unsigned char* sm = smem + (q & (C::NST - 1)) * C::STAGE;
-      const unsigned char* smm = smem + ((q - 1) & (C::NST - 1)) * C::STAGE;
-      const unsigned char* smp = smem + ((q + 1) & (C::NST - 1)) * C::STAGE;
+      const unsigned char* sm = smem + (q % C::NW) * C::WSTAGE;
+      const unsigned char* smm = smem + ((q - 1) % C::NW) * C::WSTAGE;
+      const unsigned char* smp = smem + ((q + 1) % C::NW) * C::WSTAGE;
+      const unsigned char* scq = smem + C::CRING + (q % C::NC) * C::CSTAGE;
       const T* Wc = reinterpret_cast<const T*>(sm + C::OFF_W);
       const T* Wm = reinterpret_cast<const T*>(smm + C::OFF_W);
       const T* Wp = reinterpret_cast<const T*>(smp + C::OFF_W);
-      const T* Ct = reinterpret_cast<const T*>(sm + C::OFF_CT);
+      const T* Ct = reinterpret_cast<const T*>(scq + C::OFF_CT);
       const T wc = Wc[wi];
       T acc;
       if constexpr (COEF7) {
@@ -243,7 +252,7 @@ k_newton_tma(const __grid_constant__ NewtonMaps M, const StencilDev g, const New
         acc = mac(acc, Ct[3 * TT + ci], wc);
       }
       const T wn = mac(mul(acc, invg), nshift, wc);
-      const P* Pt = reinterpret_cast<const P*>(sm + C::OFF_P);
+      const P* Pt = reinterpret_cast<const P*>(scq + C::OFF_P);
       const P pold = needp ? Pt[ci] : mul(d0, to_p(wc));
       const P pn = mac(pold, dn, to_p(wn));
       const int64_t idx = ((int64_t)z * g.ny + y) * g.pitch + x;
@@ -261,7 +270,7 @@ k_newton_tma(const __grid_constant__ NewtonMaps M, const StencilDev g, const New
     atomicOr(&ctl->err, 1);
     // let this block's copies in flight land before its shared memory goes away
     for (int q = waited_ok + 1; q <= last_issued; ++q)
-      mbar_wait_bounded(bar0 + 8 * (q & (C::NST - 1)), (q / C::NST) & 1, kWaitLimitNs / 8);
+      mbar_wait_bounded(bar0 + 8 * (q % C::NBAR), (q / C::NBAR) & 1, kWaitLimitNs / 8);
   }
 
   double nw2 = to_d(aw), np2 = to_d(ap);
