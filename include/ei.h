@@ -81,7 +81,9 @@ typedef struct {
   int fixed_s;    /* > 0: use this substep count instead of the a-priori rule */
   int profile;    /* 1: time every Newton-iteration launch with CUDA events on the
                      context's stream (stats.newton_ms / newton_timed) */
-  int reserved[4];
+  int single_iter; /* 1: one Newton iteration per kernel launch (by default stencils
+                      in the F64 formats fuse two iterations per launch) */
+  int reserved[3];
 } ei_options;
 
 #define EI_STATS_MAX_SUBSTEPS 64
@@ -96,6 +98,7 @@ typedef struct {
   int degrees[EI_STATS_MAX_SUBSTEPS]; /* per substep, first 64 substeps */
   int launches;         /* kernels this call launched */
   int newton_timed;     /* Newton-iteration launches timed (options.profile) */
+  int newton_fused;     /* Newton iterations per timed launch (1 or 2) */
   double newton_ms;     /* their summed device time (launches that did work) */
 } ei_stats;
 

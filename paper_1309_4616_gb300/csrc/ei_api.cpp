@@ -51,6 +51,7 @@ struct Prepared {
   int64_t n_alloc = 0;     // elements per vector including row padding
   // TMA descriptors of the stencil Newton kernel
   CUtensorMap map_in[4];   // w-input candidates: v, r, w[0], w[1] (halo box)
+  CUtensorMap map_in2[4];  // the same with a two-point halo (two-iteration kernel)
   CUtensorMap map_c[6];    // coef7: a[0..5]; flux: D (halo), B[0..2]
   CUtensorMap map_diagA, map_cbase, map_qc, map_p;
 };
@@ -92,6 +93,8 @@ struct ei_ctx {
   bool profile = false;
   int newton_timed = 0;
   double newton_ms = 0.0;
+  int newton_fused = 1;
+  bool fuse2 = true;       // two Newton iterations per launch where the kernel allows
   std::vector<cudaEvent_t> ev;
 };
 
@@ -226,6 +229,8 @@ static ei_status prepare(ei_ctx* c, int fmt) {
     const void* ins[4] = {P.v, P.r, P.w[0], P.w[1]};
     bool ok = true;
     for (int i = 0; i < 4; ++i) ok = ok && encode_map(&P.map_in[i], ins[i], eb, c->sd, 1);
+    if (P.coef7)
+      for (int i = 0; i < 4; ++i) ok = ok && encode_map(&P.map_in2[i], ins[i], eb, c->sd, 2);
     if (P.coef7) {
       for (int k = 0; k < 6; ++k) ok = ok && encode_map(&P.map_c[k], P.a[k], eb, c->sd, 0);
       ok = ok && encode_map(&P.map_diagA, P.diagA, eb, c->sd, 0);
@@ -277,7 +282,7 @@ static ei_status read_ctl(ei_ctx* c) {
 }
 
 static ei_status reset_done(ei_ctx* c) {
-  EI_TRY_CUDA(cudaMemsetAsync(&c->ctl->done, 0, 3 * sizeof(int), c->stream));  // done, degree, err
+  EI_TRY_CUDA(cudaMemsetAsync(&c->ctl->done, 0, 4 * sizeof(int), c->stream));  // done, degree, err, fixup
   return EI_OK;
 }
 
@@ -316,6 +321,23 @@ static cudaError_t op_newton(ei_ctx* c, Prepared& P, const void* qc, const void*
                            c->stream);
 }
 
+static cudaError_t op_newton2(ei_ctx* c, Prepared& P, const void* qc, const void* w_in,
+                              void* w_out, const NewtonScalars& s) {
+  ++c->launches;
+  NewtonMaps M;
+  const void* ins[4] = {P.v, P.r, P.w[0], P.w[1]};
+  int wi = -1;
+  for (int i = 0; i < 4; ++i)
+    if (ins[i] == w_in) wi = i;
+  if (wi < 0) return cudaErrorInvalidValue;
+  M.w = P.map_in2[wi];
+  for (int k = 0; k < 6; ++k) M.c[k] = P.map_c[k];
+  M.c[6] = (qc == P.qc) ? P.map_qc : P.map_diagA;
+  M.p = P.map_p;
+  return launch_newton2_tma(stencil_view(c, P, qc), M, w_out, P.p, s, P.fmt, c->partials, c->ctl,
+                            c->stream);
+}
+
 // One Newton loop on w_0 = r into P.p.  Returns the degree in *deg; *ok = 0
 // when m_max was reached without meeting tol.
 static ei_status newton_loop(ei_ctx* c, Prepared& P, const void* qc, const void* r,
@@ -335,31 +357,57 @@ static ei_status newton_loop(ei_ctx* c, Prepared& P, const void* qc, const void*
       c->ev.push_back(e);
     }
   }
-  int j = 0;
+  // explicit-coefficient stencils take two iterations per launch
+  const bool pair = (c->kind == KIND_STENCIL) && P.coef7 && c->fuse2;
+  int lj[128];          // first iteration index of each launch
+  bool l2[128];         // whether that launch did two iterations
+  int j = 0, nl = 0;
   int batch = m_pred > 0 ? m_pred : 8;
   while (true) {
     const int jend = (j + batch < m_max) ? j + batch : m_max;
-    for (; j < jend; ++j) {
+    while (j < jend) {
+      const bool two = pair && (j + 2 <= m_max);
       s.j = j;
       s.d_next = d[j + 1];
       s.shift = cc / gamma + xi[j];
-      const void* w_in = (j == 0) ? r : P.w[(j - 1) & 1];
-      if (c->profile) EI_TRY_CUDA(cudaEventRecord(c->ev[2 * j], c->stream));
-      EI_TRY_CUDA(op_newton(c, P, qc, w_in, P.w[j & 1], s));
-      if (c->profile) EI_TRY_CUDA(cudaEventRecord(c->ev[2 * j + 1], c->stream));
+      if (two) {
+        s.d_next2 = d[j + 2];
+        s.shift2 = cc / gamma + xi[j + 1];
+      }
+      const void* w_in = (nl == 0) ? r : P.w[(nl - 1) & 1];
+      void* w_out = P.w[nl & 1];
+      if (c->profile) EI_TRY_CUDA(cudaEventRecord(c->ev[2 * nl], c->stream));
+      if (two) {
+        EI_TRY_CUDA(op_newton2(c, P, qc, w_in, w_out, s));
+      } else {
+        EI_TRY_CUDA(op_newton(c, P, qc, w_in, w_out, s));
+      }
+      if (c->profile) EI_TRY_CUDA(cudaEventRecord(c->ev[2 * nl + 1], c->stream));
+      lj[nl] = j;
+      l2[nl] = two;
+      ++nl;
+      j += two ? 2 : 1;
     }
     EI_TRY(read_ctl(c));
     const int done = c->h_ctl->done;
     if (done == 1 || done == 2) {
       *deg = c->h_ctl->degree;
       *ok = (done == 1);
-      if (c->profile) {  // launches j < degree did the work; later ones exited at once
-        for (int i = 0; i < *deg && i < j; ++i) {
+      if (c->h_ctl->fixup) {
+        // stopped at the first of a launch's two iterations: p holds p_{deg+1}
+        for (int i = 0; i < nl; ++i)
+          if (l2[i] && lj[i] == *deg - 1)
+            EI_LAUNCH(launch_p_fixup(P.p, P.w[i & 1], P.fmt, P.n_alloc, d[*deg + 1], c->stream));
+      }
+      if (c->profile) {  // launches that started below the degree did the work
+        for (int i = 0; i < nl; ++i) {
+          if (lj[i] >= *deg && !(i == 0 && *deg == 0)) continue;
           float ms = 0.f;
           EI_TRY_CUDA(cudaEventElapsedTime(&ms, c->ev[2 * i], c->ev[2 * i + 1]));
           c->newton_ms += ms;
           ++c->newton_timed;
         }
+        c->newton_fused = pair ? 2 : 1;
       }
       return EI_OK;
     }
@@ -577,7 +625,7 @@ ei_status ei_set_operator_stencil(ei_ctx* c, int dim, const int64_t n[3], const 
   if (nb < reduction_capacity()) nb = reduction_capacity();
   c->max_blocks = nb;
   ei_status st;
-  if ((st = alloc((void**)&c->partials, sizeof(double) * 2 * nb)) != EI_OK) { free_operator(c); return st; }
+  if ((st = alloc((void**)&c->partials, sizeof(double) * 4 * nb)) != EI_OK) { free_operator(c); return st; }
   if ((st = alloc((void**)&c->ger_lo, sizeof(double) * c->n)) != EI_OK) { free_operator(c); return st; }
   if ((st = alloc((void**)&c->ger_hi, sizeof(double) * c->n)) != EI_OK) { free_operator(c); return st; }
   const void* bptr[3] = {c->bu[0], c->bu[1], c->bu[2]};
@@ -641,7 +689,9 @@ static void acct_begin(ei_ctx* c, const ei_options* opt) {
   c->launches = 0;
   c->newton_timed = 0;
   c->newton_ms = 0.0;
+  c->newton_fused = 1;
   c->profile = opt && opt->profile;
+  c->fuse2 = !(opt && opt->single_iter);
 }
 
 static void acct_end(ei_ctx* c, ei_stats* st) {
@@ -649,6 +699,7 @@ static void acct_end(ei_ctx* c, ei_stats* st) {
   st->launches = c->launches;
   st->newton_timed = c->newton_timed;
   st->newton_ms = c->newton_ms;
+  st->newton_fused = c->newton_fused;
 }
 
 static ei_status phi_apply_impl(ei_ctx* c, int k, double h, const void* v, void* out, double tol,

@@ -72,6 +72,58 @@ __device__ __forceinline__ void st(df* p, int64_t i, df v) {
 __device__ __forceinline__ void st(double* p, int64_t i, double v) { p[i] = v; }
 __device__ __forceinline__ void st(float* p, int64_t i, float v) { p[i] = v; }
 
+// 7-point sum diag*wc + sum_k a_k*w_k and the Newton update
+// w' = (A w)*inv_gamma - shift*wc.  Float-float: two lazily normalised
+// accumulators (independent chains for instruction-level parallelism);
+// double/float: plain FMAs in the same order.
+__device__ __forceinline__ df stencil7(df dg, df wc, df a0, df w0, df a1, df w1, df a2, df w2,
+                                       df a3, df w3, df a4, df w4, df a5, df w5) {
+  dfacc s1 = dfa_mul(dg, wc);
+  dfacc s2 = dfa_mul(a3, w3);
+  s1 = dfa_mac(s1, a0, w0);
+  s2 = dfa_mac(s2, a4, w4);
+  s1 = dfa_mac(s1, a1, w1);
+  s2 = dfa_mac(s2, a5, w5);
+  s1 = dfa_mac(s1, a2, w2);
+  return dfa_norm(dfa_add(s1, s2));
+}
+__device__ __forceinline__ double stencil7(double dg, double wc, double a0, double w0, double a1,
+                                           double w1, double a2, double w2, double a3, double w3,
+                                           double a4, double w4, double a5, double w5) {
+  double s1 = dg * wc, s2 = a3 * w3;
+  s1 = fma(a0, w0, s1);
+  s2 = fma(a4, w4, s2);
+  s1 = fma(a1, w1, s1);
+  s2 = fma(a5, w5, s2);
+  s1 = fma(a2, w2, s1);
+  return s1 + s2;
+}
+__device__ __forceinline__ df newton_update(df Aw, df invg, df nshift, df wc) {
+  return dfa_norm(dfa_mac(dfa_mul(Aw, invg), nshift, wc));
+}
+__device__ __forceinline__ double newton_update(double Aw, double invg, double nshift,
+                                                double wc) {
+  return fma(nshift, wc, Aw * invg);
+}
+__device__ __forceinline__ float newton_update(float Aw, float invg, float nshift, float wc) {
+  return fmaf(nshift, wc, Aw * invg);
+}
+// squared-norm accumulators: lazily normalised pairs for float-float values
+template <class T> struct Acc {
+  using type = T;
+  static __device__ __forceinline__ T zero() { return T(0); }
+};
+template <> struct Acc<df> {
+  using type = dfacc;
+  static __device__ __forceinline__ dfacc zero() { return dfacc{0.0f, 0.0f}; }
+};
+__device__ __forceinline__ double acc_sq(double a, double x) { return fma(x, x, a); }
+__device__ __forceinline__ float acc_sq(float a, float x) { return fmaf(x, x, a); }
+__device__ __forceinline__ dfacc acc_sq(dfacc a, df x) { return dfa_mac(a, x, x); }
+__device__ __forceinline__ double acc_d(double a) { return a; }
+__device__ __forceinline__ double acc_d(float a) { return (double)a; }
+__device__ __forceinline__ double acc_d(dfacc a) { return (double)a.s + (double)a.t; }
+
 template <int FMT> struct VT;
 template <> struct VT<VF_DF> { using T = df; using P = df; };
 template <> struct VT<VF_F64> { using T = double; using P = double; };
@@ -167,5 +219,39 @@ __device__ bool last_block_reduce2(double& a, double& b, double* partials, DevCt
   return true;
 }
 
+
+// Four sums: every block publishes its four partial sums; the last block to
+// arrive adds them in block order.  Returns true (in all its threads) there.
+__device__ inline bool last_block_reduce4(double v[4], double* partials, DevCtl* ctl) {
+  __shared__ bool am_last4;
+  __shared__ double f4[4];
+  const int tid = threadIdx.x + blockDim.x * (threadIdx.y + blockDim.y * threadIdx.z);
+  const int nthr = blockDim.x * blockDim.y * blockDim.z;
+  const unsigned nblk = gridDim.x * gridDim.y * gridDim.z;
+  const unsigned bid = blockIdx.x + gridDim.x * (blockIdx.y + gridDim.y * blockIdx.z);
+  block_reduce2<RED_SUM>(v[0], v[1]);
+  block_reduce2<RED_SUM>(v[2], v[3]);
+  if (tid == 0) {
+    for (int k = 0; k < 4; ++k) partials[4 * bid + k] = v[k];
+    __threadfence();
+    unsigned t = atomicAdd(&ctl->count, 1u);
+    am_last4 = (t == nblk - 1);
+  }
+  __syncthreads();
+  if (!am_last4) return false;
+  __threadfence();
+  double r[4] = {0.0, 0.0, 0.0, 0.0};
+  for (unsigned i = tid; i < nblk; i += nthr)
+    for (int k = 0; k < 4; ++k) r[k] += __ldcg(partials + 4 * i + k);
+  block_reduce2<RED_SUM>(r[0], r[1]);
+  block_reduce2<RED_SUM>(r[2], r[3]);
+  if (tid == 0) {
+    for (int k = 0; k < 4; ++k) f4[k] = r[k];
+    ctl->count = 0;
+  }
+  __syncthreads();
+  for (int k = 0; k < 4; ++k) v[k] = f4[k];
+  return true;
+}
 
 }  // namespace ei

@@ -18,6 +18,9 @@ struct DevCtl {
                        //         4 non-finite, 5 a bounded device wait ran out
   int degree;          // Newton degree at stop
   int err;             // set by a block whose bounded wait ran out
+  int fixup;           // two-iteration kernel stopped at its first iteration: p holds
+                       // p_{j+2}; subtract d_{j+2} w_{j+2} to get p_{j+1}
+  int pad2[3];
   double sum0, sum1;   // import / F / residual: squared norm, finiteness flag (1 = finite)
   double mn, mx;       // Gershgorin reductions: min_i (a_ii - r_i), max_i (a_ii + r_i)
   double nw2, np2;     // squared norms of the last Newton iterate / sum
@@ -58,6 +61,8 @@ struct NewtonScalars {
   double tol;
   int j;
   int m_max;
+  double d_next2;      // two-iteration kernel: d_{j+2}
+  double shift2;       // two-iteration kernel: c/gamma + xi_{j+1}
 };
 
 // Tensor maps of the TMA-staged Newton kernel (3D maps over the padded
@@ -75,7 +80,8 @@ int reduction_capacity();        // block bound of the grid-stride kernels
 int newton_tma_blocks(const StencilDev& op);
 
 // tensor maps: encode one 3D map over a padded array (elem 4 or 8 bytes);
-// halo = 1 widens the box by the 16-byte aligned x halo and one row in y.
+// halo = 1 widens the box by the 16-byte aligned x halo and one row in y,
+// halo = 2 by two columns and two rows (8-byte elements).
 bool encode_map(CUtensorMap* m, const void* base, int elem_bytes, const StencilDev& g, int halo);
 
 // Coefficients of the stencil operator in the vector format (coef7 layout),
@@ -139,6 +145,15 @@ cudaError_t launch_csr_residual(const CsrDev& op, const void* y, const void* v, 
 cudaError_t launch_newton_tma(const StencilDev& op, const NewtonMaps& M, void* w_out, void* p,
                               const NewtonScalars& s, int fmt, double* partials, DevCtl* ctl,
                               cudaStream_t st);
+// Two Newton iterations j+1 and j+2 in one pass (explicit-coefficient stencil,
+// 8-byte formats): w_{j+1} is formed on chip over the tile and a one-point
+// halo; only w_{j+2} and p_{j+2} are written.  M.w must be a halo-2 map.
+cudaError_t launch_newton2_tma(const StencilDev& op, const NewtonMaps& M, void* w_out, void* p,
+                               const NewtonScalars& s, int fmt, double* partials, DevCtl* ctl,
+                               cudaStream_t st);
+// p -= d * w (elementwise, Newton-sum format p, vector format w)
+cudaError_t launch_p_fixup(void* p, const void* w, int fmt, int64_t n_alloc, double d,
+                           cudaStream_t st);
 cudaError_t launch_csr_newton(const CsrDev& op, const void* w_in, void* w_out, void* p,
                               const NewtonScalars& s, int fmt, double* partials, DevCtl* ctl,
                               cudaStream_t st);

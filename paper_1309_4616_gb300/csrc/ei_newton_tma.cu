@@ -176,8 +176,8 @@ k_newton_tma(const __grid_constant__ NewtonMaps M, const StencilDev g, const New
   const T nshift = from_d<T>(-s.shift);
   const P dn = from_d<P>(s.d_next);
   const P d0 = from_d<P>(s.d0);
-  T aw = zero<T>();
-  P ap = zero<P>();
+  typename Acc<T>::type aw = Acc<T>::zero();
+  typename Acc<P>::type ap = Acc<P>::zero();
   T* __restrict__ w_out = static_cast<T*>(w_out_);
   P* __restrict__ p = static_cast<P*>(p_);
   const int x = x0 + tx, y = y0 + ty;
@@ -210,13 +210,9 @@ k_newton_tma(const __grid_constant__ NewtonMaps M, const StencilDev g, const New
       const T wc = Wc[wi];
       T acc;
       if constexpr (COEF7) {
-        acc = mul(Ct[6 * TT + ci], wc);
-        acc = mac(acc, Ct[0 * TT + ci], Wc[wi - 1]);
-        acc = mac(acc, Ct[1 * TT + ci], Wc[wi + 1]);
-        acc = mac(acc, Ct[2 * TT + ci], Wc[wi - C::WX]);
-        acc = mac(acc, Ct[3 * TT + ci], Wc[wi + C::WX]);
-        acc = mac(acc, Ct[4 * TT + ci], Wm[wi]);
-        acc = mac(acc, Ct[5 * TT + ci], Wp[wi]);
+        acc = stencil7(Ct[6 * TT + ci], wc, Ct[0 * TT + ci], Wc[wi - 1], Ct[1 * TT + ci],
+                       Wc[wi + 1], Ct[2 * TT + ci], Wc[wi - C::WX], Ct[3 * TT + ci],
+                       Wc[wi + C::WX], Ct[4 * TT + ci], Wm[wi], Ct[5 * TT + ci], Wp[wi]);
       } else {
         // flux form: ghost w is 0 (Dirichlet, from the zero fill) or w_c
         // (Neumann); ghost D is D_c
@@ -251,15 +247,15 @@ k_newton_tma(const __grid_constant__ NewtonMaps M, const StencilDev g, const New
         }
         acc = mac(acc, Ct[3 * TT + ci], wc);
       }
-      const T wn = mac(mul(acc, invg), nshift, wc);
+      const T wn = newton_update(acc, invg, nshift, wc);
       const P* Pt = reinterpret_cast<const P*>(scq + C::OFF_P);
       const P pold = needp ? Pt[ci] : mul(d0, to_p(wc));
       const P pn = mac(pold, dn, to_p(wn));
       const int64_t idx = ((int64_t)z * g.ny + y) * g.pitch + x;
       st(w_out, idx, wn);
       st(p, idx, pn);
-      aw = mac(aw, wn, wn);
-      ap = mac(ap, pn, pn);
+      aw = acc_sq(aw, wn);
+      ap = acc_sq(ap, pn);
     }
     if (__syncthreads_or(bad)) {
       bad = true;
@@ -273,7 +269,7 @@ k_newton_tma(const __grid_constant__ NewtonMaps M, const StencilDev g, const New
       mbar_wait_bounded(bar0 + 8 * (q % C::NBAR), (q / C::NBAR) & 1, kWaitLimitNs / 8);
   }
 
-  double nw2 = to_d(aw), np2 = to_d(ap);
+  double nw2 = acc_d(aw), np2 = acc_d(ap);
   if (last_block_reduce2<RED_SUM>(nw2, np2, partials, ctl)) {
     if (tid == 0) {
       ctl->nw2 = nw2;
@@ -296,6 +292,296 @@ k_newton_tma(const __grid_constant__ NewtonMaps M, const StencilDev g, const New
       }
     }
   }
+}
+
+
+// ===========================================================================
+// Two Newton iterations per pass (temporal blocking), explicit coefficients.
+//
+// The pass reads w_j with a two-point halo, the coefficient and p tiles of
+// each plane once, forms w_{j+1} on chip over the tile plus a one-point halo
+// (the halo points' coefficients come from global memory, where they are the
+// neighbouring tiles' interior), and writes only w_{j+2} and p_{j+2}:
+// 88 bytes per point for two iterations instead of 176.  w_{j+1} and p_{j+1}
+// are bit-identical to the one-iteration kernel's, so the stop test is taken
+// at both degrees; when it already holds at j+1 the host subtracts
+// d_{j+2} w_{j+2} from p.
+//
+// z-march step m computes w_{j+1} on plane zc = z0-1+m and, from m = 2 on,
+// w_{j+2} on plane zc-1.  It reads w_j planes zc-1..zc+1 and the coefficients
+// of planes zc (w_{j+1}) and zc-1 (w_{j+2}).  Only the x/y neighbours of
+// w_{j+1} cross threads: they come from the plane finished in the previous
+// step (a ring of 2 in shared memory); the centre and z neighbours are the
+// thread's own values in registers, so a step needs a single barrier.
+// ===========================================================================
+template <int FMT>
+struct TmaCfg2 {
+  using T = typename VT<FMT>::T;
+  using P = typename VT<FMT>::P;
+  static_assert(sizeof(T) == 8, "two-iteration kernel: 8-byte formats");
+  static constexpr int TX = 32, TY = 8;
+  static constexpr int PF = 2;                 // planes in flight ahead
+  static constexpr int NW = PF + 3, NC = PF + 3, NBAR = 8;
+  static constexpr int WJX = TX + 4, WJY = TY + 4;   // w_j box, two-point halo
+  static constexpr int W1X = TX + 2, W1Y = TY + 2;   // w_{j+1} region, one-point halo
+  static constexpr int NHALO = W1X * W1Y - TX * TY;  // 84
+  static constexpr int al(int b) { return (b + 127) / 128 * 128; }
+  static constexpr int WJ_BYTES = WJX * WJY * (int)sizeof(T);
+  static constexpr int C_BYTES = TX * TY * (int)sizeof(T);
+  static constexpr int P_BYTES = TX * TY * (int)sizeof(P);
+  static constexpr int WSTAGE = al(WJ_BYTES);
+  static constexpr int OFF_P = 7 * C_BYTES;
+  static constexpr int CSTAGE = al(OFF_P + P_BYTES);
+  static constexpr int W1STAGE = al(W1X * W1Y * (int)sizeof(T));
+  static constexpr int CRING = NW * WSTAGE;
+  static constexpr int W1RING = CRING + NC * CSTAGE;
+  static constexpr int BARS = W1RING + 2 * W1STAGE;
+  static constexpr int SMEM = BARS + 8 * NBAR + 128;
+};
+
+template <int FMT>
+__global__ void __launch_bounds__(256, 2)
+k_newton2_tma(const __grid_constant__ NewtonMaps M, const StencilDev g, const NewtonScalars s,
+              void* __restrict__ w_out_, void* __restrict__ p_, double* partials, DevCtl* ctl,
+              int zc_len) {
+  using C = TmaCfg2<FMT>;
+  using T = typename C::T;
+  using P = typename C::P;
+  if (*(volatile int*)&ctl->done != 0) return;
+  extern __shared__ __align__(128) unsigned char smem_raw[];
+  const uint32_t raw = smem_u32(smem_raw);
+  const uint32_t sbase = (raw + 127u) & ~127u;
+  unsigned char* smem = smem_raw + (sbase - raw);
+  const uint32_t bar0 = sbase + C::BARS;
+  const int tx = threadIdx.x, ty = threadIdx.y, tid = ty * C::TX + tx;
+  const int x0 = blockIdx.x * C::TX, y0 = blockIdx.y * C::TY;
+  const int z0 = blockIdx.z * zc_len;
+  const int z1 = min(z0 + zc_len, g.nz);
+  const int nzc = z1 - z0;
+  const int nq = nzc + 4;  // w_j planes z0-2 .. z1+1
+  const bool needp = s.j > 0;
+
+  if (tid == 0) {
+    for (int i = 0; i < C::NBAR; ++i) mbar_init(bar0 + 8 * i, 1);
+    fence_mbar_init();
+  }
+  __syncthreads();
+
+  int last_issued = -1;
+  auto issue = [&](int q) {
+    const uint32_t wb = sbase + (q % C::NW) * C::WSTAGE;
+    const uint32_t cb = sbase + C::CRING + (q % C::NC) * C::CSTAGE;
+    const uint32_t bar = bar0 + 8 * (q % C::NBAR);
+    const int z = z0 - 2 + q;
+    const bool hasc = (q >= 1) && (q <= nzc + 2);  // coefficient planes z0-1 .. z1
+    const bool hasp = needp && (q >= 2) && (q <= nzc + 1);
+    mbar_expect_tx(bar, C::WJ_BYTES + (hasc ? 7 * C::C_BYTES : 0) + (hasp ? C::P_BYTES : 0));
+    tma_load_3d(wb, &M.w, x0 - 2, y0 - 2, z, bar);
+    if (hasc) {
+#pragma unroll
+      for (int k = 0; k < 7; ++k) tma_load_3d(cb + k * C::C_BYTES, &M.c[k], x0, y0, z, bar);
+    }
+    if (hasp) tma_load_3d(cb + C::OFF_P, &M.p, x0, y0, z, bar);
+    last_issued = q;
+  };
+  int waited_ok = -1;
+  auto wait = [&](int q) {
+    const bool ok = mbar_wait_bounded(bar0 + 8 * (q % C::NBAR), (q / C::NBAR) & 1, kWaitLimitNs);
+    if (ok) waited_ok = q;
+    return ok;
+  };
+  if (tid == 0) {
+    for (int q = 0; q <= 2 + C::PF && q < nq; ++q) issue(q);
+  }
+
+  const T invg = from_d<T>(s.inv_gamma);
+  const T nsh1 = from_d<T>(-s.shift);
+  const T nsh2 = from_d<T>(-s.shift2);
+  const P d1 = from_d<P>(s.d_next);
+  const P d2 = from_d<P>(s.d_next2);
+  const P d0 = from_d<P>(s.d0);
+  double acc4[4] = {0.0, 0.0, 0.0, 0.0};
+  typename Acc<T>::type aw1 = Acc<T>::zero(), aw2 = Acc<T>::zero();
+  typename Acc<P>::type ap1 = Acc<P>::zero(), ap2 = Acc<P>::zero();
+  T* __restrict__ w_out = static_cast<T*>(w_out_);
+  P* __restrict__ p = static_cast<P*>(p_);
+  constexpr int TT = C::TX * C::TY;
+  // every thread owns one of the 32 x 8 interior points; threads 0-83 (the
+  // first three warps) also one of the 84 halo points of the 34 x 10 region
+  const bool interior = true;
+  int hlx = -1, hly = -1;
+  if (tid < C::NHALO) {
+    const int h = tid;
+    if (h < C::W1X) { hlx = h; hly = 0; }
+    else if (h < 2 * C::W1X) { hlx = h - C::W1X; hly = C::W1Y - 1; }
+    else if (h < 2 * C::W1X + C::TY) { hlx = 0; hly = 1 + h - 2 * C::W1X; }
+    else { hlx = C::W1X - 1; hly = 1 + h - 2 * C::W1X - C::TY; }
+  }
+  const int hx = x0 - 1 + hlx, hy = y0 - 1 + hly;
+  const bool hxy = hlx >= 0 && hx >= 0 && hx < g.nx && hy >= 0 && hy < g.ny;
+  // halo coefficients come from global memory one step ahead of their use
+  auto load_halo = [&](int zz, T* a) {
+    if (hxy && zz >= 0 && zz < g.nz) {
+      const int64_t gi = ((int64_t)zz * g.ny + hy) * g.pitch + hx;
+#pragma unroll
+      for (int k = 0; k < 6; ++k) a[k] = ldg(static_cast<const T*>(g.a[k]), gi);
+      a[6] = ldg(static_cast<const T*>(g.diag), gi);
+    } else {
+#pragma unroll
+      for (int k = 0; k < 7; ++k) a[k] = zero<T>();
+    }
+  };
+  T hcur[7], hnxt[7];
+  load_halo(z0 - 1, hcur);
+  bool bad = false;
+
+  // this thread's own w_{j+1} values on planes zc-2 and zc-1 (registers)
+  T w1_m2 = zero<T>(), w1_m1 = zero<T>();
+  const int xi_ = x0 + tx, yi_ = y0 + ty;
+  const bool own_xy = interior && (xi_ < g.nx) && (yi_ < g.ny);
+  const int wi_own = (ty + 2) * C::WJX + tx + 2;   // own point in the w_j box
+  const int vi_own = (ty + 1) * C::W1X + tx + 1;   // own point in the w_{j+1} region
+  const int ci = ty * C::TX + tx;
+  int sw = 0, sc = 0;  // ring slots of plane m (w_j ring, coefficient ring)
+
+  for (int m = 0; m <= nzc + 1; ++m) {
+    if (tid == 0 && m >= 1 && m + 2 + C::PF < nq) {
+      fence_proxy_async();
+      issue(m + 2 + C::PF);  // into the slots of plane m-1
+    }
+    if (m == 0) {
+      if (!bad) bad = !wait(0);
+      if (!bad) bad = !wait(1);
+    }
+    if (!bad) bad = !wait(m + 2);
+    const int zc = z0 - 1 + m;
+    if (hlx >= 0) load_halo(zc + 1, hnxt);  // in flight while this step computes
+    const int sw1 = (sw + 1 == C::NW) ? 0 : sw + 1, sw2 = (sw1 + 1 == C::NW) ? 0 : sw1 + 1;
+    const int sc1 = (sc + 1 == C::NC) ? 0 : sc + 1;
+    T w1own = zero<T>();
+    if (!bad) {
+      const T* Wm = reinterpret_cast<const T*>(smem + sw * C::WSTAGE);
+      const T* Wc = reinterpret_cast<const T*>(smem + sw1 * C::WSTAGE);
+      const T* Wp = reinterpret_cast<const T*>(smem + sw2 * C::WSTAGE);
+      T* W1 = reinterpret_cast<T*>(smem + C::W1RING + (m & 1) * C::W1STAGE);
+      const bool zin = (zc >= 0) && (zc < g.nz);
+      // ---- w_{j+1}(zc) at the own point
+      if (interior && zin && own_xy) {
+        const T* Ct = reinterpret_cast<const T*>(smem + C::CRING + sc1 * C::CSTAGE);
+        const T wc = Wc[wi_own];
+        const T acc = stencil7(Ct[6 * TT + ci], wc, Ct[0 * TT + ci], Wc[wi_own - 1],
+                               Ct[1 * TT + ci], Wc[wi_own + 1], Ct[2 * TT + ci],
+                               Wc[wi_own - C::WJX], Ct[3 * TT + ci], Wc[wi_own + C::WJX],
+                               Ct[4 * TT + ci], Wm[wi_own], Ct[5 * TT + ci], Wp[wi_own]);
+        w1own = newton_update(acc, invg, nsh1, wc);
+      }
+      if (interior) W1[vi_own] = w1own;
+      // ---- w_{j+1}(zc) at this thread's halo point (first three warps)
+      if (hlx >= 0) {
+        T w1 = zero<T>();
+        if (zin && hxy) {
+          const int wi = (hly + 1) * C::WJX + hlx + 1;
+          const T wc = Wc[wi];
+          const T acc = stencil7(hcur[6], wc, hcur[0], Wc[wi - 1], hcur[1], Wc[wi + 1], hcur[2],
+                                 Wc[wi - C::WJX], hcur[3], Wc[wi + C::WJX], hcur[4], Wm[wi],
+                                 hcur[5], Wp[wi]);
+          w1 = newton_update(acc, invg, nsh1, wc);
+        }
+        W1[hly * C::W1X + hlx] = w1;
+      }
+      // ---- w_{j+2}(zc - 1) at the own point: its x/y neighbours come from the
+      // w_{j+1} plane finished in the previous step, its z neighbours and centre
+      // are this thread's own values
+      if (m >= 2 && own_xy) {
+        const int z = zc - 1;
+        const T* V1 = reinterpret_cast<const T*>(smem + C::W1RING + ((m - 1) & 1) * C::W1STAGE);
+        const unsigned char* cs = smem + C::CRING + sc * C::CSTAGE;
+        const T* Ct = reinterpret_cast<const T*>(cs);
+        const P* Pt = reinterpret_cast<const P*>(cs + C::OFF_P);
+        const T w1c = w1_m1;
+        const T acc = stencil7(Ct[6 * TT + ci], w1c, Ct[0 * TT + ci], V1[vi_own - 1],
+                               Ct[1 * TT + ci], V1[vi_own + 1], Ct[2 * TT + ci],
+                               V1[vi_own - C::W1X], Ct[3 * TT + ci], V1[vi_own + C::W1X],
+                               Ct[4 * TT + ci], w1_m2, Ct[5 * TT + ci], w1own);
+        const T w2 = newton_update(acc, invg, nsh2, w1c);
+        const P pj = needp ? Pt[ci] : mul(d0, to_p(Wm[wi_own]));
+        const P p1 = mac(pj, d1, to_p(w1c));
+        const P p2 = mac(p1, d2, to_p(w2));
+        const int64_t idx = ((int64_t)z * g.ny + yi_) * g.pitch + xi_;
+        st(w_out, idx, w2);
+        st(p, idx, p2);
+        aw1 = acc_sq(aw1, w1c);
+        ap1 = acc_sq(ap1, p1);
+        aw2 = acc_sq(aw2, w2);
+        ap2 = acc_sq(ap2, p2);
+      }
+    }
+    w1_m2 = w1_m1;
+    w1_m1 = w1own;
+    if (hlx >= 0) {
+#pragma unroll
+      for (int k = 0; k < 7; ++k) hcur[k] = hnxt[k];
+    }
+    sw = sw1;
+    sc = sc1;
+    if (__syncthreads_or(bad)) {
+      bad = true;
+      break;
+    }
+  }
+  if (bad && tid == 0) {
+    atomicOr(&ctl->err, 1);
+    for (int q = waited_ok + 1; q <= last_issued; ++q)
+      mbar_wait_bounded(bar0 + 8 * (q % C::NBAR), (q / C::NBAR) & 1, kWaitLimitNs / 8);
+  }
+  acc4[0] = acc_d(aw1);
+  acc4[1] = acc_d(ap1);
+  acc4[2] = acc_d(aw2);
+  acc4[3] = acc_d(ap2);
+  if (last_block_reduce4(acc4, partials, ctl)) {
+    if (tid == 0) {
+      const double nw1 = acc4[0], np1 = acc4[1], nw2 = acc4[2], np2 = acc4[3];
+      ctl->nw2 = nw2;
+      ctl->np2 = np2;
+      const bool fin = finite_d(nw1) && finite_d(np1) && finite_d(nw2) && finite_d(np2);
+      if (*(volatile int*)&ctl->err) {
+        ctl->done = 5;
+        ctl->degree = s.j + 1;
+      } else if (!fin) {
+        ctl->done = 4;
+        ctl->degree = s.j + 1;
+      } else if (s.j == 0 && np1 == 0.0) {  // zero input: p = 0 at degree 0
+        ctl->done = 1;
+        ctl->degree = 0;
+      } else if (fabs(s.d_next) * sqrt(nw1) <= s.tol * sqrt(np1)) {
+        ctl->done = 1;
+        ctl->degree = s.j + 1;
+        ctl->fixup = 1;
+      } else if (s.j + 1 >= s.m_max) {
+        ctl->done = 2;
+        ctl->degree = s.j + 1;
+        ctl->fixup = 1;
+      } else if (fabs(s.d_next2) * sqrt(nw2) <= s.tol * sqrt(np2)) {
+        ctl->done = 1;
+        ctl->degree = s.j + 2;
+      } else if (s.j + 2 >= s.m_max) {
+        ctl->done = 2;
+        ctl->degree = s.j + 2;
+      }
+    }
+  }
+}
+
+template <int FMT>
+__global__ void k_p_fixup(void* p_, const void* w_, int64_t n, double d) {
+  using T = typename VT<FMT>::T;
+  using P = typename VT<FMT>::P;
+  P* p = static_cast<P*>(p_);
+  const T* w = static_cast<const T*>(w_);
+  const P nd = from_d<P>(-d);
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;
+       i += (int64_t)gridDim.x * blockDim.x)
+    st(p, i, mac(ld(p, i), nd, to_p(ldg(w, i))));
 }
 
 // ---- host side ----------------------------------------------------------------
@@ -328,8 +614,8 @@ bool encode_map(CUtensorMap* m, const void* base, int elem_bytes, const StencilD
   cuuint64_t dims[3] = {(cuuint64_t)g.nx, (cuuint64_t)g.ny, (cuuint64_t)g.nz};
   cuuint64_t strides[2] = {(cuuint64_t)g.pitch * elem_bytes,
                            (cuuint64_t)g.pitch * g.ny * elem_bytes};
-  cuuint32_t box[3] = {(cuuint32_t)(32 + (halo ? 2 * hx : 0)), (cuuint32_t)(8 + (halo ? 2 : 0)),
-                       1};
+  cuuint32_t box[3] = {(cuuint32_t)(32 + (halo ? 2 * hx : 0)), (cuuint32_t)(8 + 2 * halo), 1};
+  if (halo == 2 && elem_bytes != 8) return false;
   cuuint32_t estr[3] = {1, 1, 1};
   CUresult r = fn(m, elem_bytes == 8 ? CU_TENSOR_MAP_DATA_TYPE_FLOAT64 : CU_TENSOR_MAP_DATA_TYPE_FLOAT32,
                   3, const_cast<void*>(base), dims, strides, box, estr,
@@ -377,6 +663,46 @@ cudaError_t launch_newton_tma(const StencilDev& g, const NewtonMaps& M, void* w_
   if (fmt == VF_DF) return launch_one<VF_DF, true>(g, M, w_out, p, s, partials, ctl, st);
   if (fmt == VF_F64) return launch_one<VF_F64, true>(g, M, w_out, p, s, partials, ctl, st);
   return launch_one<VF_F32, false>(g, M, w_out, p, s, partials, ctl, st);
+}
+
+cudaError_t launch_newton2_tma(const StencilDev& g, const NewtonMaps& M, void* w_out, void* p,
+                               const NewtonScalars& s, int fmt, double* partials, DevCtl* ctl,
+                               cudaStream_t st) {
+  const int zc = tma_zchunk(g);
+  dim3 grid((g.nx + 31) / 32, (g.ny + 7) / 8, (g.nz + zc - 1) / zc), block(32, 8, 1);
+  if (fmt == VF_DF) {
+    using C = TmaCfg2<VF_DF>;
+    static bool attr = false;
+    if (!attr) {
+      cudaError_t e = cudaFuncSetAttribute(k_newton2_tma<VF_DF>,
+                                           cudaFuncAttributeMaxDynamicSharedMemorySize, C::SMEM);
+      if (e != cudaSuccess) return e;
+      attr = true;
+    }
+    k_newton2_tma<VF_DF><<<grid, block, C::SMEM, st>>>(M, g, s, w_out, p, partials, ctl, zc);
+  } else if (fmt == VF_F64) {
+    using C = TmaCfg2<VF_F64>;
+    static bool attr = false;
+    if (!attr) {
+      cudaError_t e = cudaFuncSetAttribute(k_newton2_tma<VF_F64>,
+                                           cudaFuncAttributeMaxDynamicSharedMemorySize, C::SMEM);
+      if (e != cudaSuccess) return e;
+      attr = true;
+    }
+    k_newton2_tma<VF_F64><<<grid, block, C::SMEM, st>>>(M, g, s, w_out, p, partials, ctl, zc);
+  } else {
+    return cudaErrorInvalidValue;
+  }
+  return cudaGetLastError();
+}
+
+cudaError_t launch_p_fixup(void* p, const void* w, int fmt, int64_t n, double d,
+                           cudaStream_t st) {
+  const int nb = 152 * 8;
+  if (fmt == VF_DF) k_p_fixup<VF_DF><<<nb, 256, 0, st>>>(p, w, n, d);
+  else if (fmt == VF_F64) k_p_fixup<VF_F64><<<nb, 256, 0, st>>>(p, w, n, d);
+  else k_p_fixup<VF_F32><<<nb, 256, 0, st>>>(p, w, n, d);
+  return cudaGetLastError();
 }
 
 }  // namespace ei

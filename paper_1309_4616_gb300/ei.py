@@ -32,7 +32,7 @@ EXPORTS = [
 
 class Options(C.Structure):
     _fields_ = [("m_max", C.c_int), ("arith", C.c_int), ("fixed_s", C.c_int),
-                ("profile", C.c_int), ("reserved", C.c_int * 4)]
+                ("profile", C.c_int), ("single_iter", C.c_int), ("reserved", C.c_int * 3)]
 
 
 class Stats(C.Structure):
@@ -40,7 +40,8 @@ class Stats(C.Structure):
                 ("restarts", C.c_int), ("matvecs", C.c_int), ("degree_sum", C.c_int),
                 ("degree_max", C.c_int), ("m_sched", C.c_int),
                 ("degrees", C.c_int * STATS_MAX_SUBSTEPS), ("launches", C.c_int),
-                ("newton_timed", C.c_int), ("newton_ms", C.c_double)]
+                ("newton_timed", C.c_int), ("newton_fused", C.c_int),
+                ("newton_ms", C.c_double)]
 
     def degree_list(self):
         return [int(self.degrees[i]) for i in range(min(self.s, STATS_MAX_SUBSTEPS))]
@@ -50,7 +51,8 @@ class Stats(C.Structure):
                 "matvecs": self.matvecs, "degree_sum": self.degree_sum,
                 "degree_max": self.degree_max, "m_sched": self.m_sched,
                 "degrees": self.degree_list(), "launches": self.launches,
-                "newton_timed": self.newton_timed, "newton_ms": self.newton_ms}
+                "newton_timed": self.newton_timed, "newton_fused": self.newton_fused,
+                "newton_ms": self.newton_ms}
 
 
 class EIError(RuntimeError):

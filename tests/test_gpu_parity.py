@@ -43,7 +43,8 @@ def _check_stats(st, ost):
 # 2D advection-diffusion on 64 x 64, the small configuration in full
 # --------------------------------------------------------------------------
 @pytest.mark.parametrize("arith", [0, 1])
-def test_adv_diff_2d_phi1(env, xi, arith):
+@pytest.mark.parametrize("single", [0, 1])
+def test_adv_diff_2d_phi1(env, xi, arith, single):
     torch, ei = env
     w = W.adv_diff_2d()
     op = O.StencilOperator(w.n, w.dx, w.D, w.b, bc=w.bc)
@@ -53,7 +54,7 @@ def test_adv_diff_2d_phi1(env, xi, arith):
     assert a == pytest.approx(-3380.0, rel=1e-13) and abs(b) < 1e-9
     v = dev(torch, w.v)
     out = torch.empty_like(v)
-    st = ctx.phi_apply(1, w.h, v, out, w.tol, {"arith": arith})
+    st = ctx.phi_apply(1, w.h, v, out, w.tol, {"arith": arith, "single_iter": single})
     assert rel_err(out.cpu().numpy(), ref) <= FP64_TOL
     _check_stats(st, ost)
 
@@ -68,9 +69,9 @@ def _fields_3d(rng, n):
     return D, b
 
 
-@pytest.mark.parametrize("method", [Nw.NONLIN_LOGISTIC])
+@pytest.mark.parametrize("single", [0, 1])
 @pytest.mark.parametrize("arith", [0, 1])
-def test_rosenbrock_3d_neumann(env, xi, method, arith):
+def test_rosenbrock_3d_neumann(env, xi, single, arith):
     torch, ei = env
     rng = np.random.default_rng(21)
     n = (37, 29, 21)
@@ -82,7 +83,8 @@ def test_rosenbrock_3d_neumann(env, xi, method, arith):
     ref, ost = Nw.exp_rosenbrock_step(op, u0, h, tol, xi=xi)
     ctx = stencil_context(torch, ei, n, dx, D, b, 0.0, (1,) * 6)
     u = dev(torch, u0)
-    st = ctx.step(ei.EXP_ROSENBROCK, h, u, ei.NONLIN_LOGISTIC, tol, {"arith": arith})
+    st = ctx.step(ei.EXP_ROSENBROCK, h, u, ei.NONLIN_LOGISTIC, tol,
+                  {"arith": arith, "single_iter": single})
     got = u.cpu().numpy()
     assert rel_err(got - u0, ref - u0) <= FP64_TOL
     assert rel_err(got, ref) <= FP64_TOL
@@ -109,7 +111,8 @@ def test_exp_euler_3d_mixed_bc_with_c(env, xi):
     _check_stats(st, ost)
 
 
-def test_substeps_2d_mixed(env, xi):
+@pytest.mark.parametrize("m_max", [100, 15])
+def test_substeps_2d_mixed(env, xi, m_max):
     # a large h makes the a-priori rule ask for several substeps
     torch, ei = env
     rng = np.random.default_rng(23)
@@ -121,12 +124,12 @@ def test_substeps_2d_mixed(env, xi):
     v0 = rng.standard_normal((43, 70))
     op = O.StencilOperator(n, dx, D, b, bc=bc)
     h, tol = 0.02, 1e-10
-    ref, ost = Nw.phi_apply(op, 1, h, v0, tol, xi=xi)
+    ref, ost = Nw.phi_apply(op, 1, h, v0, tol, m_max=m_max, xi=xi)
     assert ost.s > 1
     ctx = stencil_context(torch, ei, n, dx, D, b, 0.0, bc)
     v = dev(torch, v0)
     out = torch.empty_like(v)
-    st = ctx.phi_apply(1, h, v, out, tol)
+    st = ctx.phi_apply(1, h, v, out, tol, {"m_max": m_max})
     assert rel_err(out.cpu().numpy(), ref) <= FP64_TOL
     _check_stats(st, ost)
 
