@@ -48,7 +48,10 @@ def parse():
     ap.add_argument("--steps", type=int, default=20)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--n", type=int, default=N_SIDE, help=argparse.SUPPRESS)
+    ap.add_argument("--n", type=int, default=None, help=argparse.SUPPRESS)
+    ap.add_argument("--workload", default="adr3d", choices=["adr3d", "adr3d_fp32", "rgg_csr"],
+                    help="adr3d (default, the headline): 256^3 FP64 Rosenbrock-Euler; "
+                         "adr3d_fp32: 512^3 FP32 exponential Euler; rgg_csr: 2^20-node CSR phi_1")
     ap.add_argument("--no-cpu", action="store_true", help="skip the CPU baseline sample")
     return ap.parse_args()
 
@@ -163,7 +166,7 @@ def run_reference(args):
     if rank != 0:
         return
     from paper_1309_4616_gb300 import workloads as W
-    w = W.adr_3d(n=args.n)
+    w = W.adr_3d(n=args.n if args.n is not None else N_SIDE)
     u = w.u0.copy()
     op, xi = oracle_setup(w)
     for _ in range(args.warmup):
@@ -182,7 +185,7 @@ def run_reference(args):
         "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
         "ms_per_step": est * 1e3, "higher_is_better": True, "scaling": "weak",
         "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-        "config": {"workload": WORKLOAD, "grid": [args.n] * 3, "h": w.h, "tol": w.tol,
+        "config": {"workload": WORKLOAD, "grid": list(w.n), "h": w.h, "tol": w.tol,
                    "bc": "neumann", "sample_wall_s": wall},
         "cpu_baseline": {"value": value, "unit": "steps/s", "cores": 1, "kind": "oracle",
                          "sample": desc},
@@ -195,6 +198,126 @@ def run_reference(args):
 # --------------------------------------------------------------------------
 # the GPU arm
 # --------------------------------------------------------------------------
+class Workload:
+    """One benchmark configuration: set-up, one step, its bytes per point."""
+    name = ""
+    method = ""
+    dtype = ""
+
+    def state_reset(self):
+        self.state.copy_(self.state0)
+
+
+class Adr3d(Workload):
+    """256^3 (or --n) FP64 exponential Rosenbrock-Euler, Neumann, logistic g."""
+
+    def __init__(self, torch, ei, W, dev, ctx, n):
+        self.name, self.method = WORKLOAD, "exp_rosenbrock_euler"
+        self.dtype = "f64 (float-float pairs on the FP32 pipes)"
+        self.ei, self.w = ei, W.adr_3d(n=n)
+        w = self.w
+        self.npts = n ** 3
+        self.keep = [torch.from_numpy(w.D).to(dev)] + [torch.from_numpy(x).to(dev) for x in w.b]
+        ctx.set_operator_stencil(w.n, w.dx, self.keep[0], self.keep[1:], 0.0, list(w.bc),
+                                 ei.PREC_F64)
+        self.state0 = torch.from_numpy(w.u0).to(dev)
+        self.state = self.state0.clone()
+        self.host0 = w.u0
+        self.bytes_per_point = BYTES_PER_POINT
+        self.config = {"grid": [n] * 3, "h": w.h, "tol": w.tol, "bc": "neumann",
+                       "method": self.method}
+
+    def step(self, ctx, opts=None):
+        return ctx.step(self.ei.EXP_ROSENBROCK, self.w.h, self.state, self.ei.NONLIN_LOGISTIC,
+                        self.w.tol, opts)
+
+    def step_host(self, ctx, host):
+        return ctx.step_host(self.ei.EXP_ROSENBROCK, self.w.h, host, self.ei.NONLIN_LOGISTIC,
+                             self.w.tol)
+
+    def kernel(self, fused):
+        return ("k_newton2_tma<float-float> (two Newton iterations per launch)"
+                if fused == 2 else "k_newton_tma<float-float>")
+
+
+class Adr3dFp32(Adr3d):
+    """512^3 reduced-precision form: FP32 vectors and stencil, exponential Euler."""
+
+    def __init__(self, torch, ei, W, dev, ctx, n):
+        self.name, self.method = f"adr3d_{n}_fp32_exp_euler", "exp_euler"
+        self.dtype = "f32 (float-float Newton sum)"
+        self.ei, self.w = ei, W.adr_3d_fp32(n=n)
+        w = self.w
+        self.npts = n ** 3
+        f32 = torch.float32
+        self.keep = [torch.from_numpy(w.D).to(dev, f32)] + \
+            [torch.from_numpy(x).to(dev, f32) for x in w.b]
+        ctx.set_operator_stencil(w.n, w.dx, self.keep[0], self.keep[1:], 0.0, list(w.bc),
+                                 ei.PREC_F32)
+        self.state0 = torch.from_numpy(w.u0).to(dev, f32)
+        self.state = self.state0.clone()
+        self.host0 = w.u0.astype(np.float32)
+        # w 4 + w' 4 + p 8+8 + D 4 + b 12 + c 4
+        self.bytes_per_point = 44
+        self.config = {"grid": [n] * 3, "h": w.h, "tol": w.tol, "bc": "neumann",
+                       "method": self.method}
+
+    def step(self, ctx, opts=None):
+        return ctx.step(self.ei.EXP_EULER, self.w.h, self.state, self.ei.NONLIN_LOGISTIC,
+                        self.w.tol, opts)
+
+    def step_host(self, ctx, host):
+        return ctx.step_host(self.ei.EXP_EULER, self.w.h, host, self.ei.NONLIN_LOGISTIC,
+                             self.w.tol)
+
+    def kernel(self, fused):
+        return "k_newton_tma<float, flux form>"
+
+
+class RggCsr(Workload):
+    """phi_1(hA)v for A = -(graph Laplacian) of the 2^20-node random geometric
+    graph, h*rho(A) = 100, tol 1e-10, FP64."""
+
+    def __init__(self, torch, ei, W, dev, ctx, n):
+        self.name, self.method = "rgg_2^20_csr_phi1", "phi1"
+        self.dtype = "f64 (float-float pairs on the FP32 pipes)"
+        self.ei = ei
+        g = W.rgg_graph(n=n)
+        self.npts = g.n
+        self.keep = [torch.from_numpy(g.rowptr).to(dev), torch.from_numpy(g.col).to(dev),
+                     torch.from_numpy(g.val).to(dev), torch.from_numpy(-g.deg_w).to(dev)]
+        ctx.set_operator_csr(g.n, *self.keep)
+        self.h = 100.0 / (2.0 * g.deg_w.max())
+        self.tol = 1e-10
+        v = W.random_vector(g.n, 5)
+        self.host0 = v
+        self.state0 = torch.from_numpy(v).to(dev)
+        self.state = self.state0.clone()
+        self.out = torch.empty_like(self.state)
+        nnz = g.col.size
+        # val 8 + col 4 per entry, rowptr 8 + diag 8 + w 8 + w' 8 + p 16 per row
+        self.bytes_per_point = 12.0 * nnz / g.n + 48.0
+        self.config = {"nodes": g.n, "nnz": int(nnz), "mean_degree": nnz / g.n,
+                       "h_rho": 100.0, "tol": self.tol, "method": self.method}
+
+    def step(self, ctx, opts=None):
+        return ctx.phi_apply(1, self.h, self.state, self.out, self.tol, opts)
+
+    def step_host(self, ctx, host):
+        import torch
+        d = host.to(self.state.device, non_blocking=True)
+        st = ctx.phi_apply(1, self.h, d, self.out, self.tol)
+        host.copy_(self.out, non_blocking=False)
+        return st
+
+    def kernel(self, fused):
+        return "k_csr_newton<float-float> (4 lanes per row)"
+
+
+WORKLOADS = {"adr3d": Adr3d, "adr3d_fp32": Adr3dFp32, "rgg_csr": RggCsr}
+DEFAULT_N = {"adr3d": N_SIDE, "adr3d_fp32": 512, "rgg_csr": 1 << 20}
+
+
 def run_ours(args):
     import torch
     from paper_1309_4616_gb300 import build, ei
@@ -214,21 +337,16 @@ def run_ours(args):
     if dist is not None:
         dist.barrier()
     dev = torch.device("cuda", local)
-
-    w = W.adr_3d(n=args.n)
-    npts = args.n ** 3
     stream = torch.cuda.current_stream(dev)
     ctx = ei.Context(local, stream)
-    D = torch.from_numpy(w.D).to(dev)
-    b = [torch.from_numpy(x).to(dev) for x in w.b]
-    ctx.set_operator_stencil(w.n, w.dx, D, b, 0.0, list(w.bc), ei.PREC_F64)
-    u0 = torch.from_numpy(w.u0).to(dev)
+    n = args.n if args.n is not None else DEFAULT_N[args.workload]
+    wl = WORKLOADS[args.workload](torch, ei, W, dev, ctx, n)
+    npts = wl.npts
 
-    # warm-up on a copy, then the timed steps from u0
-    u = u0.clone()
+    # warm-up on a copy, then the timed steps from the initial state
     for _ in range(args.warmup):
-        ctx.step(ei.EXP_ROSENBROCK, w.h, u, ei.NONLIN_LOGISTIC, w.tol)
-    u.copy_(u0)
+        wl.step(ctx)
+    wl.state_reset()
     torch.cuda.synchronize(dev)
     if dist is not None:
         dist.barrier()
@@ -243,7 +361,7 @@ def run_ours(args):
     torch.cuda.synchronize(dev)
     e0.record(stream)
     for _ in range(args.steps):
-        st = ctx.step(ei.EXP_ROSENBROCK, w.h, u, ei.NONLIN_LOGISTIC, w.tol)
+        st = wl.step(ctx)
         launches += st.launches
         matvecs.append(st.matvecs)
         degrees.append(st.degree_list())
@@ -259,26 +377,26 @@ def run_ours(args):
 
     # roofline of the dominant kernel: per-launch CUDA events around every Newton
     # launch of two further steps (profile option), same stream, same sizes
-    u_prof = u0.clone()
+    wl.state_reset()
     prof_ms, prof_n, fused = 0.0, 0, 1
     for _ in range(2):
-        st = ctx.step(ei.EXP_ROSENBROCK, w.h, u_prof, ei.NONLIN_LOGISTIC, w.tol, {"profile": 1})
+        st = wl.step(ctx, {"profile": 1})
         prof_ms += st.newton_ms
         prof_n += st.newton_timed
         fused = st.newton_fused
     avg_launch_s = prof_ms / max(prof_n, 1) * 1e-3
     hbm, peak_kind = peaks()
-    achieved = BYTES_PER_POINT * npts / avg_launch_s / 1e9
+    achieved = wl.bytes_per_point * npts / avg_launch_s / 1e9
 
-    # e2e through the public API with host buffers: H2D of u, the step, D2H of u
-    u_host = torch.from_numpy(w.u0.copy()).pin_memory()
+    # e2e through the public API with host buffers: H2D of the state, the step, D2H
+    u_host = torch.from_numpy(np.ascontiguousarray(wl.host0).copy()).pin_memory()
     k_e2e = max(1, min(args.steps, 10))
-    ctx.step_host(ei.EXP_ROSENBROCK, w.h, u_host, ei.NONLIN_LOGISTIC, w.tol)  # warm
-    u_host.copy_(torch.from_numpy(w.u0))
+    wl.step_host(ctx, u_host)  # warm
+    u_host.copy_(torch.from_numpy(np.ascontiguousarray(wl.host0)))
     torch.cuda.synchronize(dev)
     t0 = time.perf_counter()
     for _ in range(k_e2e):
-        ctx.step_host(ei.EXP_ROSENBROCK, w.h, u_host, ei.NONLIN_LOGISTIC, w.tol)
+        wl.step_host(ctx, u_host)
     torch.cuda.synchronize(dev)
     e2e_s = time.perf_counter() - t0
     if dist is not None:
@@ -287,30 +405,28 @@ def run_ours(args):
         e2e_s = float(t.item())
 
     cpu = None
-    if rank == 0 and not args.no_cpu:
-        op, xi = oracle_setup(w)
-        per_step, desc = oracle_step_sample(w, w.u0.copy(), op, xi)
+    if rank == 0 and not args.no_cpu and args.workload == "adr3d":
+        op, xi = oracle_setup(wl.w)
+        per_step, desc = oracle_step_sample(wl.w, wl.w.u0.copy(), op, xi)
         cpu = {"value": 1.0 / per_step, "unit": "steps/s", "cores": 1, "kind": "oracle",
                "sample": desc}
 
     if rank == 0:
         steps_total = args.steps * world
         value = steps_total / (ms * 1e-3)
+        esz = u_host.element_size()
+        config = {"workload": wl.name, **wl.config, "parallelism": f"replicas x{world}",
+                  "l2": "inputs larger than L2 (each vector >= 8 MB and the step's working "
+                        "set >= 0.3 GB; 256^3: 134 MB per vector)",
+                  "matvecs_per_step": matvecs, "degrees": degrees[:3]}
         line = {
             "metric": METRIC, "value": value, "unit": "steps/s", "n_gpus": world,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms / args.steps,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
-            "dtype": "f64 (float-float pairs on the FP32 pipes)", "data": "synthetic",
-            "config": {"workload": WORKLOAD, "grid": [args.n] * 3, "h": w.h, "tol": w.tol,
-                       "bc": "neumann", "method": "exp_rosenbrock_euler",
-                       "parallelism": f"replicas x{world}",
-                       "l2": "inputs larger than L2 (each vector 134 MB, ~1.3 GB per step)",
-                       "matvecs_per_step": matvecs, "degrees": degrees[:3]},
+            "dtype": wl.dtype, "data": "synthetic", "config": config,
             "roofline": {"bound": "hbm", "achieved": achieved, "peak": hbm, "unit": "GB/s",
-                         "frac": achieved / hbm, "traffic": None,
-                         "kernel": ("k_newton2_tma<float-float> (two Newton iterations per launch)"
-                                    if fused == 2 else "k_newton_tma<float-float>"),
-                         "bytes_per_launch": BYTES_PER_POINT * npts,
+                         "frac": achieved / hbm, "traffic": None, "kernel": wl.kernel(fused),
+                         "bytes_per_launch": wl.bytes_per_point * npts,
                          "avg_launch_us": avg_launch_s * 1e6, "launches_timed": prof_n,
                          "iterations_per_launch": fused,
                          "us_per_iteration": avg_launch_s * 1e6 / fused,
@@ -318,7 +434,7 @@ def run_ours(args):
                          "paper_gflops": FLOPS_PER_POINT_PAPER * npts * fused / avg_launch_s / 1e9},
             "cpu_baseline": cpu,
             "e2e": {"value": k_e2e * world / e2e_s, "unit": "steps/s",
-                    "h2d_bytes_per_step": npts * 8, "d2h_bytes_per_step": npts * 8},
+                    "h2d_bytes_per_step": npts * esz, "d2h_bytes_per_step": npts * esz},
             "gpu_launches": launches,
             "clocks": clocks,
         }

@@ -1,0 +1,119 @@
+"""Full-size parity: the configurations the benchmarks run, checked against the
+oracle on the same seeded inputs where the oracle finishes in about a minute,
+and through properties that hold at any size where it does not.
+
+  * 256^3 FP64 exponential Rosenbrock-Euler, one step: the full field against
+    the oracle (1e-9), identical Leja degree and substep count.
+  * 2^20-node CSR phi_1 (h*rho = 100): the full vector against the oracle
+    (1e-9), identical degree; phi_1(hA)1 = 1 and 1^T phi_1(hA)v = 1^T v.
+  * 512^3 FP32 form, 10 exponential-Euler steps: against the FP64 path on the
+    64^3 restriction (every 8th point, offset 4), within 1e-5; the FP64 path
+    itself is held to the oracle by the other tests.  The same FP32 form on a
+    64^3 grid against the oracle directly.
+"""
+import numpy as np
+import pytest
+
+from oracle import leja as L
+from oracle import newton as Nw
+from oracle import operators as O
+from paper_1309_4616_gb300 import workloads as W
+
+from gpu_helpers import dev, rel_err, require_gpu
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def env():
+    return require_gpu()
+
+
+@pytest.fixture(scope="module")
+def xi():
+    return L.leja_points(100)
+
+
+def test_adr3d_256_rosenbrock_step(env, xi):
+    torch, ei = env
+    w = W.adr_3d(n=256)
+    op = O.StencilOperator(w.n, w.dx, w.D, w.b, bc=w.bc)
+    ref, ost = Nw.exp_rosenbrock_step(op, w.u0, w.h, w.tol, xi=xi)
+    ctx = ei.Context()
+    ctx.set_operator_stencil(w.n, w.dx, dev(torch, w.D), [dev(torch, x) for x in w.b], 0.0,
+                             list(w.bc), ei.PREC_F64)
+    u = dev(torch, w.u0)
+    st = ctx.step(ei.EXP_ROSENBROCK, w.h, u, ei.NONLIN_LOGISTIC, w.tol)
+    got = u.cpu().numpy()
+    assert rel_err(got - w.u0, ref - w.u0) <= 1e-9
+    assert st.s == ost.s and st.degree_list() == list(ost.degrees)
+    assert st.alpha == pytest.approx(ost.alpha, rel=1e-13)
+    assert st.beta == pytest.approx(ost.beta, rel=1e-13, abs=1e-9)
+
+
+def test_csr_2e20_phi1(env, xi):
+    torch, ei = env
+    g = W.rgg_graph()
+    assert g.col.size == 12 * g.n          # mean degree exactly 12
+    op = O.CsrOperator(g.n, g.rowptr, g.col, g.val, -g.deg_w)
+    h = 100.0 / (2.0 * g.deg_w.max())
+    v0 = W.random_vector(g.n, 5)
+    ref, ost = Nw.phi_apply(op, 1, h, v0, 1e-10, xi=xi)
+    ctx = ei.Context()
+    ctx.set_operator_csr(g.n, dev(torch, g.rowptr), dev(torch, g.col), dev(torch, g.val),
+                         dev(torch, -g.deg_w))
+    v = dev(torch, v0)
+    out = torch.empty_like(v)
+    st = ctx.phi_apply(1, h, v, out, 1e-10)
+    got = out.cpu().numpy()
+    assert rel_err(got, ref) <= 1e-9
+    assert st.s == ost.s and st.degree_list() == list(ost.degrees)
+    # conservation: 1^T A = 0 and A 1 = 0
+    assert abs(got.sum() - v0.sum()) <= 1e-9 * np.abs(v0).sum()
+    ones = torch.ones_like(v)
+    ctx.phi_apply(1, h, ones, out, 1e-10)
+    assert np.abs(out.cpu().numpy() - 1.0).max() <= 1e-9
+
+
+def _fp32_run(torch, ei, w, steps):
+    f32 = torch.float32
+    ctx = ei.Context()
+    ctx.set_operator_stencil(w.n, w.dx, dev(torch, w.D, f32), [dev(torch, x, f32) for x in w.b],
+                             0.0, list(w.bc), ei.PREC_F32)
+    u = dev(torch, w.u0, f32)
+    for _ in range(steps):
+        ctx.step(ei.EXP_EULER, w.h, u, ei.NONLIN_LOGISTIC, w.tol)
+    out = u.cpu().numpy().astype(np.float64)
+    ctx.close()
+    return out
+
+
+def test_fp32_form_64cube_vs_oracle(env, xi):
+    torch, ei = env
+    w = W.adr_3d_fp32(n=64)
+    # the oracle runs on the FP32-rounded inputs the FP32 form receives
+    D = w.D.astype(np.float32).astype(np.float64)
+    b = [x.astype(np.float32).astype(np.float64) for x in w.b]
+    u = w.u0.astype(np.float32).astype(np.float64)
+    op = O.StencilOperator(w.n, w.dx, D, b, bc=w.bc)
+    for _ in range(w.steps):
+        u, _ = Nw.exp_euler_step(op, u, w.h, w.tol, Nw.NONLIN_LOGISTIC, xi=xi)
+    got = _fp32_run(torch, ei, w, w.steps)
+    assert rel_err(got, u) <= 1e-5
+
+
+def test_fp32_form_512cube_restriction(env):
+    torch, ei = env
+    w = W.adr_3d_fp32(n=512)
+    got = _fp32_run(torch, ei, w, w.steps)[4::8, 4::8, 4::8]
+    ctx = ei.Context()
+    ctx.set_operator_stencil(w.n, w.dx, dev(torch, w.D), [dev(torch, x) for x in w.b], 0.0,
+                             list(w.bc), ei.PREC_F64)
+    u = dev(torch, w.u0)
+    for _ in range(w.steps):
+        ctx.step(ei.EXP_EULER, w.h, u, ei.NONLIN_LOGISTIC, w.tol)
+    ref = u.cpu().numpy()[4::8, 4::8, 4::8]
+    ctx.close()
+    err = rel_err(got, ref)
+    print(f"512^3 FP32 form vs FP64 path on the 64^3 restriction: {err:.3e}")
+    assert err <= 1e-5
