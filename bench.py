@@ -311,7 +311,7 @@ class RggCsr(Workload):
         return st
 
     def kernel(self, fused):
-        return "k_csr_newton<float-float> (4 lanes per row)"
+        return "k_csr_newton<float-float> (one thread per row)"
 
 
 WORKLOADS = {"adr3d": Adr3d, "adr3d_fp32": Adr3dFp32, "rgg_csr": RggCsr}

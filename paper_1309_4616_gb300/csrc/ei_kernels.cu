@@ -260,37 +260,39 @@ k_stencil_F(StencilDev g, const void* __restrict__ u_, void* __restrict__ F_,
 }
 
 // ---------------------------------------------------------------------------
-// CSR operator (Sec. III-D): a group of EI_LPR lanes per row.  The paper found
-// four threads per row best for its matrix; rows of the random geometric graph
-// carry ~12 entries, so a 4-lane group reads three entries per lane.
+// CSR operator (Sec. III-D): one thread per row.  The paper's C2075 code gave
+// each row four threads; rows of the random geometric graph carry ~12
+// entries, and on sm_103a one thread per row issues all of a row's column,
+// value and gather loads together (four at a time, two independent
+// accumulators) and keeps every lane busy in the Newton update.
 // ---------------------------------------------------------------------------
-#define EI_LPR 4
+__device__ __forceinline__ dfacc lmac(dfacc c, df a, df b) { return dfa_mac(c, a, b); }
+__device__ __forceinline__ double lmac(double c, double a, double b) { return fma(a, b, c); }
+__device__ __forceinline__ float lmac(float c, float a, float b) { return fmaf(a, b, c); }
+__device__ __forceinline__ df lsum(dfacc a, dfacc b) { return dfa_norm(dfa_add(a, b)); }
+__device__ __forceinline__ double lsum(double a, double b) { return a + b; }
+__device__ __forceinline__ float lsum(float a, float b) { return a + b; }
 
+// (W x)_row
 template <class T>
-__device__ __forceinline__ T shfl_xor_T(T v, int m);
-template <> __device__ __forceinline__ double shfl_xor_T<double>(double v, int m) {
-  return __shfl_xor_sync(0xffffffffu, v, m);
-}
-template <> __device__ __forceinline__ float shfl_xor_T<float>(float v, int m) {
-  return __shfl_xor_sync(0xffffffffu, v, m);
-}
-template <> __device__ __forceinline__ df shfl_xor_T<df>(df v, int m) {
-  return df{__shfl_xor_sync(0xffffffffu, v.hi, m), __shfl_xor_sync(0xffffffffu, v.lo, m)};
-}
-
-// (W x)_row over the lane group; every lane of the group gets the full sum
-template <class T>
-__device__ __forceinline__ T csr_row(const CsrDev& op, const T* __restrict__ x, int64_t row,
-                                     bool valid, int lane) {
-  T acc = zero<T>();
-  if (valid) {
-    const T* __restrict__ val = static_cast<const T*>(op.val);
-    const int64_t b = __ldg(op.rowptr + row), e = __ldg(op.rowptr + row + 1);
-    for (int64_t k = b + lane; k < e; k += EI_LPR) acc = mac(acc, ldg(val, k), ldg(x, __ldg(op.col + k)));
+__device__ __forceinline__ T csr_row(const CsrDev& op, const T* __restrict__ x, int64_t row) {
+  const T* __restrict__ val = static_cast<const T*>(op.val);
+  const int32_t* __restrict__ col = op.col;
+  const int64_t b = __ldg(op.rowptr + row), e = __ldg(op.rowptr + row + 1);
+  typename Acc<T>::type s1 = Acc<T>::zero(), s2 = Acc<T>::zero();
+  int64_t k = b;
+  for (; k + 4 <= e; k += 4) {
+    const int c0 = __ldg(col + k), c1 = __ldg(col + k + 1);
+    const int c2 = __ldg(col + k + 2), c3 = __ldg(col + k + 3);
+    const T v0 = ldg(val, k), v1 = ldg(val, k + 1), v2 = ldg(val, k + 2), v3 = ldg(val, k + 3);
+    const T x0 = ldg(x, c0), x1 = ldg(x, c1), x2 = ldg(x, c2), x3 = ldg(x, c3);
+    s1 = lmac(s1, v0, x0);
+    s2 = lmac(s2, v1, x1);
+    s1 = lmac(s1, v2, x2);
+    s2 = lmac(s2, v3, x3);
   }
-#pragma unroll
-  for (int m = EI_LPR / 2; m > 0; m >>= 1) acc = add(acc, shfl_xor_T(acc, m));
-  return acc;
+  for (; k < e; ++k) s1 = lmac(s1, ldg(val, k), ldg(x, __ldg(col + k)));
+  return lsum(s1, s2);
 }
 
 template <int FMT>
@@ -304,31 +306,25 @@ k_csr_newton(CsrDev op, const void* __restrict__ w_in_, void* __restrict__ w_out
   T* __restrict__ w_out = static_cast<T*>(w_out_);
   P* __restrict__ p = static_cast<P*>(p_);
   const T* __restrict__ qc = static_cast<const T*>(op.qc);
-  const int lane = threadIdx.x % EI_LPR;
-  const int64_t rows_per_iter = (int64_t)gridDim.x * (EI_TPB / EI_LPR);
   const T invg = from_d<T>(s.inv_gamma);
   const T nshift = from_d<T>(-s.shift);
   const P dn = from_d<P>(s.d_next);
   const P d0 = from_d<P>(s.d0);
-  T aw = zero<T>();
-  P ap = zero<P>();
-  for (int64_t base = (int64_t)blockIdx.x * (EI_TPB / EI_LPR); base < op.n; base += rows_per_iter) {
-    const int64_t row = base + threadIdx.x / EI_LPR;
-    const bool valid = row < op.n;
-    const T Wx = csr_row<T>(op, w_in, row, valid, lane);
-    if (valid && lane == 0) {
-      const T wc = ldg(w_in, row);
-      const T Aw = mac(Wx, ldg(qc, row), wc);
-      const T wn = mac(mul(Aw, invg), nshift, wc);
-      const P pold = (s.j == 0) ? mul(d0, to_p(wc)) : ld(p, row);
-      const P pn = mac(pold, dn, to_p(wn));
-      st(w_out, row, wn);
-      st(p, row, pn);
-      aw = mac(aw, wn, wn);
-      ap = mac(ap, pn, pn);
-    }
+  typename Acc<T>::type aw = Acc<T>::zero();
+  typename Acc<P>::type ap = Acc<P>::zero();
+  const int64_t row = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (row < op.n) {
+    const T wc = ldg(w_in, row);
+    const T Aw = mac(csr_row<T>(op, w_in, row), ldg(qc, row), wc);
+    const T wn = newton_update(Aw, invg, nshift, wc);
+    const P pold = (s.j == 0) ? mul(d0, to_p(wc)) : ld(p, row);
+    const P pn = mac(pold, dn, to_p(wn));
+    st(w_out, row, wn);
+    st(p, row, pn);
+    aw = acc_sq(aw, wn);
+    ap = acc_sq(ap, pn);
   }
-  double nw2 = to_d(aw), np2 = to_d(ap);
+  double nw2 = acc_d(aw), np2 = acc_d(ap);
   if (last_block_reduce2<RED_SUM>(nw2, np2, partials, ctl)) {
     if (threadIdx.x == 0) {
       ctl->nw2 = nw2;
@@ -359,20 +355,14 @@ k_csr_residual(CsrDev op, const void* __restrict__ y_, const void* __restrict__ 
   const T* __restrict__ v = static_cast<const T*>(v_);
   T* __restrict__ r = static_cast<T*>(r_);
   const T* __restrict__ qc = static_cast<const T*>(op.qc);
-  const int lane = threadIdx.x % EI_LPR;
-  const int64_t rows_per_iter = (int64_t)gridDim.x * (EI_TPB / EI_LPR);
-  T ar = zero<T>();
-  for (int64_t base = (int64_t)blockIdx.x * (EI_TPB / EI_LPR); base < op.n; base += rows_per_iter) {
-    const int64_t row = base + threadIdx.x / EI_LPR;
-    const bool valid = row < op.n;
-    const T Wy = csr_row<T>(op, yv, row, valid, lane);
-    if (valid && lane == 0) {
-      const T rv = add(mac(Wy, ldg(qc, row), ldg(yv, row)), ldg(v, row));
-      st(r, row, rv);
-      ar = mac(ar, rv, rv);
-    }
+  typename Acc<T>::type ar = Acc<T>::zero();
+  const int64_t row = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (row < op.n) {
+    const T rv = add(mac(csr_row<T>(op, yv, row), ldg(qc, row), ldg(yv, row)), ldg(v, row));
+    st(r, row, rv);
+    ar = acc_sq(ar, rv);
   }
-  double a = to_d(ar), b = 0.0;
+  double a = acc_d(ar), b = 0.0;
   if (last_block_reduce2<RED_SUM>(a, b, partials, ctl)) {
     if (threadIdx.x == 0) ctl->sum0 = a;
   }
@@ -388,28 +378,22 @@ k_csr_F(CsrDev op, const void* __restrict__ u_, void* __restrict__ F_, void* __r
   const T* __restrict__ cb = static_cast<const T*>(cb_);
   T* __restrict__ F = static_cast<T*>(F_);
   T* __restrict__ qo = static_cast<T*>(qo_);
-  const int lane = threadIdx.x % EI_LPR;
-  const int64_t rows_per_iter = (int64_t)gridDim.x * (EI_TPB / EI_LPR);
   const T one = from_d<T>(1.0);
-  T af = zero<T>();
-  for (int64_t base = (int64_t)blockIdx.x * (EI_TPB / EI_LPR); base < op.n; base += rows_per_iter) {
-    const int64_t row = base + threadIdx.x / EI_LPR;
-    const bool valid = row < op.n;
-    const T Wu = csr_row<T>(op, u, row, valid, lane);
-    if (valid && lane == 0) {
-      const T uc = ldg(u, row);
-      T Fv = mac(Wu, ldg(cb, row), uc);
-      if (nonlin) Fv = mac(Fv, uc, sub(one, uc));
-      st(F, row, Fv);
-      if (rosenbrock) {
-        T q = ldg(cb, row);
-        if (nonlin) q = add(q, mac(one, from_d<T>(-2.0), uc));
-        st(qo, row, q);
-      }
-      af = mac(af, Fv, Fv);
+  typename Acc<T>::type af = Acc<T>::zero();
+  const int64_t row = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (row < op.n) {
+    const T uc = ldg(u, row);
+    T Fv = mac(csr_row<T>(op, u, row), ldg(cb, row), uc);
+    if (nonlin) Fv = mac(Fv, uc, sub(one, uc));
+    st(F, row, Fv);
+    if (rosenbrock) {
+      T q = ldg(cb, row);
+      if (nonlin) q = add(q, mac(one, from_d<T>(-2.0), uc));
+      st(qo, row, q);
     }
+    af = acc_sq(af, Fv);
   }
-  double a = to_d(af), b = 0.0;
+  double a = acc_d(af), b = 0.0;
   if (last_block_reduce2<RED_SUM>(a, b, partials, ctl)) {
     if (threadIdx.x == 0) {
       ctl->sum0 = a;
@@ -588,12 +572,9 @@ static int ew_blocks(int64_t n) {
 
 int reduction_capacity() { return num_sms() * 8; }
 
-int csr_blocks(int64_t n) {
-  int64_t b = (n + (EI_TPB / EI_LPR) - 1) / (EI_TPB / EI_LPR);
-  int64_t cap = (int64_t)num_sms() * 8;
-  if (b > cap) b = cap;
-  if (b < 1) b = 1;
-  return (int)b;
+int csr_blocks(int64_t n) {  // one thread per row
+  int64_t b = (n + EI_TPB - 1) / EI_TPB;
+  return b < 1 ? 1 : (int)b;
 }
 
 #define EI_DISPATCH_FMT(fmt, KERNEL_CALL)                           \
