@@ -83,7 +83,9 @@ typedef struct {
                      context's stream (stats.newton_ms / newton_timed) */
   int single_iter; /* 1: one Newton iteration per kernel launch (by default stencils
                       in the F64 formats fuse two iterations per launch) */
-  int reserved[3];
+  int tile_rows;   /* batched form: tile height in units of 8 rows (1 to 32);
+                      0 = the autotuner's choice */
+  int reserved[2];
 } ei_options;
 
 #define EI_STATS_MAX_SUBSTEPS 64
@@ -211,6 +213,57 @@ ei_status ei_divided_differences(int k, double tau, double c, double gamma, int 
  * meets max_G |f - p_m| <= tol max_G |f| on 2001 points G of [-2,2]. */
 ei_status ei_schedule(int k, double h, double c, double gamma, double tol, int m_max,
                       int* s_out, int* m_out);
+
+/* ---- Batched form ---------------------------------------------------------
+ * Many independent problems of uneven size, each a 2D stencil operator with
+ * constant coefficients (the rows of Sec. III-A with constant D, b, c and its
+ * own per-side homogeneous boundary conditions), advanced together: all the
+ * phi_1(h_i A_i) v_i are computed by ONE persistent kernel launch, replayed
+ * from a captured CUDA graph.  Blocks claim (problem, tile) work items from a
+ * device work queue; the block that finishes a problem's last tile reduces
+ * its norms in tile order, takes the stop test and publishes the problem's
+ * next phase, so no block ever waits for another.  Tile heights per
+ * problem-size class come from a built-in autotuner (timed on the device the
+ * first time a class is seen, cached per process and device). */
+typedef struct {
+  int64_t nx, ny;   /* grid points, each >= 1 */
+  double dx, dy;    /* spacings, > 0 */
+  double D;         /* diffusion coefficient */
+  double bx, by;    /* advection b (the operator uses + b . grad u) */
+  double c;         /* reaction/diagonal term */
+  int bc[4];        /* EI_BC_* of faces x-lo, x-hi, y-lo, y-hi */
+  double h;         /* step, > 0 */
+} ei_batch_problem;
+
+typedef struct {
+  double alpha, beta; /* Gershgorin interval */
+  int s;              /* substeps of the accepted attempt */
+  int degree_sum;     /* Newton degrees summed over substeps */
+  int restarts;       /* attempts rejected (m_max reached) */
+  int tile_rows;      /* tile height the autotuner chose for its size class */
+} ei_batch_stats;
+
+typedef struct ei_batch ei_batch; /* opaque, library-owned */
+
+/* Set up `count` problems on `device`: per-problem Gershgorin interval,
+ * a-priori schedule and divided differences (host, FP64), workspaces for all
+ * problems in one device pool, and the tile choice.  prec: EI_PREC_F64 or
+ * EI_PREC_F32 (vectors and matvec in float).  tol: Leja tolerance for every
+ * problem.  opt may be NULL.  Synchronous. */
+ei_status ei_batch_create(ei_batch** out, int device, int count, const ei_batch_problem* problems,
+                          int prec, double tol, const ei_options* opt);
+/* offsets[0..count]: element offsets of each problem's vector in the packed
+ * layout ei_batch_phi1 reads and writes (problem i occupies
+ * [offsets[i], offsets[i+1]), x fastest).  Host array. */
+ei_status ei_batch_offsets(const ei_batch* b, int64_t* offsets);
+/* out_i = phi_1(h_i A_i) v_i for every problem.  v, out: device arrays in the
+ * packed layout, in the batch's precision; ordered on `cuda_stream`.  The
+ * first call captures the launch sequence into a CUDA graph, later calls
+ * replay it.  per_problem: host array of `count` stats, or NULL.  Returns
+ * after completion. */
+ei_status ei_batch_phi1(ei_batch* b, void* cuda_stream, const void* v, void* out,
+                        ei_batch_stats* per_problem);
+void ei_batch_destroy(ei_batch* b);
 
 const char* ei_status_string(ei_status st);
 

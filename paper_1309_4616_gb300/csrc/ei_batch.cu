@@ -1,0 +1,1046 @@
+// Batched form: phi_1(h_i A_i) v_i for many independent 2D stencil problems
+// of uneven size in one persistent kernel launch (sm_103a).
+//
+// Each problem i runs the same method as the single-problem path (Gershgorin
+// interval, a-priori substeps s_i, Newton form at Leja points with the stop
+// test |d_{j+1}| ||w_{j+1}|| <= tol ||p_{j+1}||; Sec. II-C, Eq. (3), Sec. III-C
+// of the paper) and proceeds through phases, each a sweep over its tiles:
+//   NEWTON(j): w_{j+1} = (A w_j)/gamma - (c/gamma + xi_j) w_j, p += d_{j+1} w_{j+1}
+//   AXPY:      y += tau p          (substeps s > 1)
+//   RES:       r = A y + v         (start of substeps 2..s)
+// Work distribution: each problem has a 64-bit word (epoch << 32 | next tile);
+// a block claims a tile with one atomicAdd, processes it, writes the tile's
+// norm partials and counts the tile done.  The block that completes the last
+// tile of an epoch sums the partials in tile order (deterministic), takes the
+// phase's decision and publishes the next epoch.  No block waits for another;
+// a block that finds nothing to claim sleeps briefly, and gives up after 5 s
+// without global progress (status EI_ERR_TIMEOUT).  Data written by other
+// blocks in earlier epochs is read through L2 (ld.global.cg).
+#include <cuda_runtime.h>
+#include <math.h>
+#include <stdint.h>
+#include <string.h>
+
+#include <algorithm>
+#include <functional>
+#include <map>
+#include <mutex>
+#include <string>
+#include <thread>
+#include <vector>
+
+#include "ei.h"
+#include "ei_device.cuh"
+
+namespace ei {
+const double* leja_table();
+void divided_differences(int k, double tau, double c, double gamma, int m, double* out);
+int schedule(int k, double h, double c, double gamma, double tol, int m_max, int* s_out,
+             int* m_out, double* d_out);
+double phi_scalar(int k, double z);
+
+enum { PH_NEWTON = 0, PH_AXPY = 1, PH_RES = 2 };
+enum { ST_RUN = 0, ST_DONE = 1, ST_FAIL = 2, ST_NONFINITE = 3, ST_SCALAR = 4, ST_SKIP = 5 };
+
+struct BInst {
+  int nx, ny, tiles_x, tiles, rows;  // rows: points per thread in y (tile height 8*rows)
+  int bc[4];
+  int s;
+  double d0, axm, axp, aym, ayp;     // interior coefficients (ghost form)
+  double inv_gamma, c_over_gamma, tau, h;
+  int64_t off;                       // element offset of the problem's block of vectors
+  int64_t npts;
+  int64_t poff;                      // offset of the tile partials
+  int dd_off;                        // offset of the divided differences
+};
+
+struct BState {
+  unsigned long long word;  // epoch << 32 | next tile to claim
+  unsigned int done;        // tiles completed in the current epoch
+  int phase, j, sub, status, degree_sum;
+};
+
+struct BatchDev {
+  int count;
+  int m_max;
+  double tol;
+  const BInst* inst;
+  BState* state;
+  const int* order;          // biggest problems first
+  const double* dd;
+  const double* xi;
+  double* partials;
+  void* pool;                // 5 vectors per problem: v, w0, w1, y, r
+  void* ppool;               // Newton sum per problem
+  unsigned int* finished;
+  unsigned long long* progress;
+  int* error;
+};
+
+template <class T>
+__device__ __forceinline__ T ldcg_(const T* p, int64_t i);
+template <> __device__ __forceinline__ df ldcg_<df>(const df* p, int64_t i) {
+  float2 v = __ldcg(reinterpret_cast<const float2*>(p) + i);
+  return df{v.x, v.y};
+}
+template <> __device__ __forceinline__ double ldcg_<double>(const double* p, int64_t i) {
+  return __ldcg(p + i);
+}
+template <> __device__ __forceinline__ float ldcg_<float>(const float* p, int64_t i) {
+  return __ldcg(p + i);
+}
+
+// One tile: 32 columns x (8*rows) rows.  Lane = column; warp w marches down
+// its own strip of `rows` consecutive rows keeping u(y-1), u(y), u(y+1) of its
+// column in registers, so a point costs three loads (u(y+1), u(x-1), u(x+1)),
+// and the next row's loads are issued before this row's arithmetic.  A ghost
+// value is 0 behind a Dirichlet face and u itself behind a Neumann face.
+template <int FMT>
+__device__ void batch_tile(const BatchDev& B, int i, int t, int phase, int j, int sub,
+                           double& o0, double& o1) {
+  using T = typename VT<FMT>::T;
+  using P = typename VT<FMT>::P;
+  const BInst& I = B.inst[i];
+  T* __restrict__ base = static_cast<T*>(B.pool) + I.off;
+  const T* V = base;
+  T* W0 = base + I.npts;
+  T* W1 = base + 2 * I.npts;
+  T* Y = base + 3 * I.npts;
+  T* R = base + 4 * I.npts;
+  P* __restrict__ Pp = static_cast<P*>(B.ppool) + I.off / 5;
+  const T d0 = from_d<T>(I.d0), axm = from_d<T>(I.axm), axp = from_d<T>(I.axp);
+  const T aym = from_d<T>(I.aym), ayp = from_d<T>(I.ayp);
+  const int x = (t % I.tiles_x) * 32 + (int)(threadIdx.x & 31);
+  const int y0 = (t / I.tiles_x) * (8 * I.rows) + (int)(threadIdx.x >> 5) * I.rows;
+  const int y1 = min(y0 + I.rows, I.ny);
+  typename Acc<T>::type aw = Acc<T>::zero();
+  typename Acc<P>::type ap = Acc<P>::zero();
+  if (phase == PH_AXPY) {
+    const P tau = from_d<P>(I.tau);
+    if (x < I.nx)
+      for (int y = y0; y < y1; ++y) {
+        const int64_t k = (int64_t)y * I.nx + x;
+        const P yo = (sub == 0) ? zero<P>() : to_p(ldcg_(Y, k));
+        const P yn = mac(yo, tau, ldcg_(Pp, k));
+        if constexpr (FMT == VF_F32) {
+          st(Y, k, (float)to_d(yn));
+        } else {
+          st(Y, k, yn);
+        }
+      }
+    o0 = 0.0;
+    o1 = 0.0;
+    return;
+  }
+  const T* __restrict__ u = (phase == PH_RES) ? Y : ((j == 0) ? (sub == 0 ? V : R) : ((j - 1) & 1 ? W1 : W0));
+  T* wout = (j & 1) ? W1 : W0;
+  const T invg = from_d<T>(I.inv_gamma);
+  const T nshift = from_d<T>(phase == PH_NEWTON ? -(I.c_over_gamma + B.xi[j]) : 0.0);
+  const P dn = from_d<P>(phase == PH_NEWTON ? B.dd[I.dd_off + j + 1] : 0.0);
+  const P dz = from_d<P>(phase == PH_NEWTON ? B.dd[I.dd_off] : 0.0);
+  const T zro = zero<T>();
+  if (x < I.nx && y0 < y1) {
+    // column queue: um = u(y-1), uc = u(y), up = u(y+1)
+    int64_t k = (int64_t)y0 * I.nx + x;
+    T uc = ldcg_(u, k);
+    T um = y0 > 0 ? ldcg_(u, k - I.nx) : (I.bc[2] ? uc : zro);
+    T ul = x > 0 ? ldcg_(u, k - 1) : (I.bc[0] ? uc : zro);
+    T ur = x < I.nx - 1 ? ldcg_(u, k + 1) : (I.bc[1] ? uc : zro);
+    T up = y0 < I.ny - 1 ? ldcg_(u, k + I.nx) : (I.bc[3] ? uc : zro);
+    for (int y = y0; y < y1; ++y) {
+      // loads of the next row, issued before this row's arithmetic
+      const int64_t kn = k + I.nx;
+      const bool more = (y + 1 < y1);
+      T nl = zro, nr = zro, nu = zro;
+      if (more) {
+        nl = x > 0 ? ldcg_(u, kn - 1) : zro;
+        nr = x < I.nx - 1 ? ldcg_(u, kn + 1) : zro;
+        nu = (y + 2 < I.ny) ? ldcg_(u, kn + I.nx) : zro;
+      }
+      T acc = mul(d0, uc);
+      acc = mac(acc, axm, ul);
+      acc = mac(acc, axp, ur);
+      acc = mac(acc, aym, um);
+      acc = mac(acc, ayp, up);
+      if (phase == PH_NEWTON) {
+        const T wn = newton_update(acc, invg, nshift, uc);
+        const P pold = (j == 0) ? mul(dz, to_p(uc)) : ldcg_(Pp, k);
+        const P pn = mac(pold, dn, to_p(wn));
+        st(wout, k, wn);
+        st(Pp, k, pn);
+        aw = acc_sq(aw, wn);
+        ap = acc_sq(ap, pn);
+      } else {
+        st(R, k, add(acc, ldcg_(V, k)));
+      }
+      if (more) {
+        // shift the column queue; ghosts for the next row
+        um = uc;
+        uc = up;
+        ul = x > 0 ? nl : (I.bc[0] ? uc : zro);
+        ur = x < I.nx - 1 ? nr : (I.bc[1] ? uc : zro);
+        up = (y + 2 < I.ny) ? nu : (I.bc[3] ? uc : zro);
+        k = kn;
+      }
+    }
+  }
+  o0 = acc_d(aw);
+  o1 = acc_d(ap);
+}
+
+// Claim one tile: lanes of the calling warp look at 32 problems at a time (in
+// the biggest-first order, from `cursor`), vote for those whose current epoch
+// still has unclaimed tiles, and try them in order with one atomicAdd each.
+// Returns the problem index (-1: nothing claimable) in every lane.
+__device__ int warp_claim(const BatchDev& B, int& cursor, int& t_out, int& phase, int& j,
+                          int& sub) {
+  const int lane = threadIdx.x & 31;
+  for (int base = 0; base < B.count; base += 32) {
+    int k = cursor + base + lane;
+    while (k >= B.count) k -= B.count;
+    const int i = B.order[k];
+    const BState* S = &B.state[i];
+    bool cand = false;
+    if (base + lane < B.count && *(volatile const int*)&S->status == ST_RUN) {
+      const unsigned long long w = *(volatile const unsigned long long*)&S->word;
+      cand = (unsigned)(w & 0xffffffffull) < (unsigned)B.inst[i].tiles;
+    }
+    unsigned mask = __ballot_sync(0xffffffffu, cand);
+    while (mask) {
+      const int l = __ffs(mask) - 1;
+      mask &= mask - 1;
+      int got = 0, ti = 0, ph = 0, jj = 0, sb = 0;
+      if (lane == l) {
+        const unsigned long long w = atomicAdd(&B.state[i].word, 1ull);
+        const unsigned t = (unsigned)(w & 0xffffffffull);
+        if (t < (unsigned)B.inst[i].tiles) {
+          __threadfence();
+          got = 1;
+          ti = (int)t;
+          ph = *(volatile const int*)&B.state[i].phase;
+          jj = *(volatile const int*)&B.state[i].j;
+          sb = *(volatile const int*)&B.state[i].sub;
+        }
+      }
+      got = __shfl_sync(0xffffffffu, got, l);
+      if (got) {
+        t_out = __shfl_sync(0xffffffffu, ti, l);
+        phase = __shfl_sync(0xffffffffu, ph, l);
+        j = __shfl_sync(0xffffffffu, jj, l);
+        sub = __shfl_sync(0xffffffffu, sb, l);
+        const int ik = __shfl_sync(0xffffffffu, k, l);
+        cursor = ik;
+        return __shfl_sync(0xffffffffu, i, l);
+      }
+    }
+  }
+  return -1;
+}
+
+// Sum (a, b) over the 8 compute warps; result in thread 0.  Fixed order.
+__device__ __forceinline__ void compute_reduce2(double& a, double& b, double* sa, double* sb) {
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+#pragma unroll
+  for (int off = 16; off > 0; off >>= 1) {
+    a += __shfl_down_sync(0xffffffffu, a, off);
+    b += __shfl_down_sync(0xffffffffu, b, off);
+  }
+  if (lane == 0) {
+    sa[wid] = a;
+    sb[wid] = b;
+  }
+  asm volatile("bar.sync 1, 256;" ::: "memory");  // the 8 compute warps only
+  if (threadIdx.x == 0) {
+    a = 0.0;
+    b = 0.0;
+    for (int w = 0; w < 8; ++w) {
+      a += sa[w];
+      b += sb[w];
+    }
+  }
+}
+
+// 256 compute threads (warps 0-7) process the claimed tile while warp 8 claims
+// the next one; the claim's latency hides behind the tile's arithmetic.
+template <int FMT>
+__global__ void __launch_bounds__(288) k_batch(BatchDev B) {
+  __shared__ int sh_i, sh_t, sh_phase, sh_j, sh_sub, sh_exit, sh_last;
+  __shared__ int nx_i, nx_t, nx_phase, nx_j, nx_sub;
+  __shared__ double sh_n0, sh_n1, red_a[8], red_b[8];
+  const int tid = threadIdx.x;
+  const bool sched = tid >= 256;  // warp 8
+  int cursor = (int)((blockIdx.x * 37u) % (unsigned)B.count);
+  unsigned long long seen = 0;
+  uint64_t idle_t0 = 0;
+  // first claim
+  if (sched) {
+    int t = 0, ph = 0, j = 0, sb = 0;
+    const int i = warp_claim(B, cursor, t, ph, j, sb);
+    if (tid == 256) {
+      nx_i = i;
+      nx_t = t;
+      nx_phase = ph;
+      nx_j = j;
+      nx_sub = sb;
+    }
+  }
+  __syncthreads();
+  while (true) {
+    if (tid == 256) {
+      sh_i = nx_i;
+      sh_t = nx_t;
+      sh_phase = nx_phase;
+      sh_j = nx_j;
+      sh_sub = nx_sub;
+      sh_exit = (*(volatile unsigned*)B.finished >= (unsigned)B.count || *(volatile int*)B.error);
+    }
+    __syncthreads();
+    if (sh_exit && sh_i < 0) break;
+    if (sh_i < 0) {
+      // nothing claimed: claim again at once; pause only when that fails too,
+      // and give up after 5 s without progress anywhere
+      if (sched) {
+        int t = 0, ph = 0, j = 0, sb = 0;
+        const int ni = warp_claim(B, cursor, t, ph, j, sb);
+        if (tid == 256) {
+          nx_i = ni;
+          nx_t = t;
+          nx_phase = ph;
+          nx_j = j;
+          nx_sub = sb;
+          if (ni < 0) {
+            const unsigned long long pr = *(volatile unsigned long long*)B.progress;
+            uint64_t now;
+            asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(now));
+            if (pr != seen || idle_t0 == 0) {
+              seen = pr;
+              idle_t0 = now;
+            } else if (now - idle_t0 > 5000000000ull) {
+              atomicExch(B.error, 1);
+            }
+            __nanosleep(500);
+          }
+        }
+      }
+      __syncthreads();
+      continue;
+    }
+    idle_t0 = 0;
+    const int i = sh_i;
+    if (sched) {
+      int t = 0, ph = 0, j = 0, sb = 0;
+      const int ni = warp_claim(B, cursor, t, ph, j, sb);
+      if (tid == 256) {
+        nx_i = ni;
+        nx_t = t;
+        nx_phase = ph;
+        nx_j = j;
+        nx_sub = sb;
+      }
+    } else {
+      double a = 0.0, b = 0.0;
+      batch_tile<FMT>(B, i, sh_t, sh_phase, sh_j, sh_sub, a, b);
+      if (sh_phase == PH_NEWTON) {
+        compute_reduce2(a, b, red_a, red_b);
+        if (tid == 0) {
+          B.partials[B.inst[i].poff + 2 * sh_t] = a;
+          B.partials[B.inst[i].poff + 2 * sh_t + 1] = b;
+        }
+      }
+    }
+    __syncthreads();
+    if (tid == 0) {
+      __threadfence();
+      const unsigned d = atomicAdd(&B.state[i].done, 1u);
+      sh_last = (d == (unsigned)B.inst[i].tiles - 1);
+      atomicAdd(B.progress, 1ull);
+    }
+    __syncthreads();
+    if (!sh_last) continue;
+    // ---- this block completed the epoch: decide the problem's next phase
+    __threadfence();
+    const BInst& I = B.inst[i];
+    BState* S = &B.state[i];
+    if (sh_phase == PH_NEWTON) {
+      double ra = 0.0, rb = 0.0;
+      for (int t = tid; t < I.tiles; t += blockDim.x) {
+        ra += __ldcg(B.partials + I.poff + 2 * t);
+        rb += __ldcg(B.partials + I.poff + 2 * t + 1);
+      }
+      block_reduce2<RED_SUM>(ra, rb);
+      if (tid == 0) {
+        sh_n0 = ra;
+        sh_n1 = rb;
+      }
+      __syncthreads();
+    }
+    if (tid == 0) {
+      int phase = sh_phase, j = sh_j, sub = sh_sub, status = ST_RUN;
+      if (sh_phase == PH_NEWTON) {
+        const double nw2 = sh_n0, np2 = sh_n1;
+        const double dn = B.dd[I.dd_off + j + 1];
+        int deg = -1;
+        if (!isfinite(nw2) || !isfinite(np2)) status = ST_NONFINITE;
+        else if (j == 0 && np2 == 0.0) deg = 0;
+        else if (fabs(dn) * sqrt(nw2) <= B.tol * sqrt(np2)) deg = j + 1;
+        else if (j + 1 >= B.m_max) status = ST_FAIL;
+        else j = j + 1;
+        if (deg >= 0) {
+          S->degree_sum += deg;
+          if (I.s == 1) status = ST_DONE;
+          else phase = PH_AXPY;
+        }
+      } else if (sh_phase == PH_AXPY) {
+        sub = sub + 1;
+        if (sub >= I.s) status = ST_DONE;
+        else phase = PH_RES;
+      } else {
+        phase = PH_NEWTON;
+        j = 0;
+      }
+      S->done = 0;
+      if (status != ST_RUN) {
+        S->status = status;
+        __threadfence();
+        atomicAdd(B.finished, 1u);
+      } else {
+        S->phase = phase;
+        S->j = j;
+        S->sub = sub;
+        __threadfence();
+        const unsigned long long epoch = (*(volatile unsigned long long*)&S->word >> 32) + 1ull;
+        atomicExch(&S->word, epoch << 32);
+      }
+    }
+    __syncthreads();
+    // the scheduler's pre-claim may have found nothing while this epoch was
+    // being closed; the next loop turn retries
+  }
+}
+
+// ---- set-up, import/export ---------------------------------------------------
+__global__ void k_batch_init(const BInst* inst, BState* state, const int* init_status, int count,
+                             unsigned int* finished, unsigned long long* progress, int* error) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i == 0) {
+    *finished = 0;
+    *progress = 0;
+    *error = 0;
+  }
+  if (i < count) {
+    BState s;
+    s.word = 1ull << 32;
+    s.done = 0;
+    s.phase = PH_NEWTON;
+    s.j = 0;
+    s.sub = 0;
+    s.degree_sum = 0;
+    s.status = init_status[i];
+    state[i] = s;
+  }
+}
+
+// count the problems that start finished (inactive / scalar)
+__global__ void k_batch_count_idle(const BState* state, int count, unsigned int* finished) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < count && state[i].status != ST_RUN) atomicAdd(finished, 1u);
+}
+
+template <int FMT, class U>
+__global__ void k_batch_import(const BInst* inst, const int64_t* uoff, const U* v, void* pool) {
+  using T = typename VT<FMT>::T;
+  const BInst& I = inst[blockIdx.y];
+  T* V = static_cast<T*>(pool) + I.off;
+  const U* src = v + uoff[blockIdx.y];
+  for (int64_t k = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; k < I.npts;
+       k += (int64_t)gridDim.x * blockDim.x)
+    st(V, k, from_d<T>((double)src[k]));
+}
+
+// out = phi_1(hA) v: p (s = 1), y/h (s > 1), or scale * v (scalar problems)
+template <int FMT, class U>
+__global__ void k_batch_export(const BInst* inst, const BState* state, const int64_t* uoff,
+                               const double* scal, const void* pool, const void* ppool,
+                               U* out) {
+  using T = typename VT<FMT>::T;
+  using P = typename VT<FMT>::P;
+  const int i = blockIdx.y;
+  const BInst& I = inst[i];
+  const T* base = static_cast<const T*>(pool) + I.off;
+  const P* Pp = static_cast<const P*>(ppool) + I.off / 5;
+  U* dst = out + uoff[i];
+  const int st_ = state[i].status;
+  if (st_ == ST_SKIP || st_ == ST_FAIL || st_ == ST_NONFINITE) return;
+  for (int64_t k = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; k < I.npts;
+       k += (int64_t)gridDim.x * blockDim.x) {
+    double v;
+    if (st_ == ST_SCALAR) v = scal[i] * to_d(base[k]);
+    else if (I.s == 1) v = to_d(Pp[k]);
+    else v = to_d(base[3 * I.npts + k]) / I.h;
+    dst[k] = (U)v;
+  }
+}
+
+}  // namespace ei
+
+// ===========================================================================
+// host side
+// ===========================================================================
+using namespace ei;
+
+struct ei_batch {
+  int device = 0, prec = 0, fmt = 0, count = 0, m_max = 100;
+  double tol = 0;
+  cudaStream_t stream = nullptr;  // library stream the graph is captured on
+  std::vector<ei_batch_problem> prob;
+  std::vector<BInst> hinst;
+  std::vector<int64_t> uoff;      // packed caller layout offsets (count + 1)
+  std::vector<int> active;        // 0: scalar problem (A = cI)
+  std::vector<int> init;          // initial status of each problem in the next run
+  std::vector<int> final_deg;     // degree sum of the accepted attempt
+  std::vector<double> scal;       // phi_1(h c) for scalar problems
+  std::vector<double> alpha, beta, c, gamma;
+  std::vector<int> restarts;
+  std::vector<double> hdd;
+  // device
+  BInst* inst = nullptr;
+  BState* state = nullptr;
+  int* order = nullptr;
+  int* dinit = nullptr;
+  int64_t* duoff = nullptr;
+  double* dscal = nullptr;
+  double* dd = nullptr;
+  double* xi = nullptr;
+  double* partials = nullptr;
+  void* pool = nullptr;
+  void* ppool = nullptr;
+  unsigned int* finished = nullptr;
+  unsigned long long* progress = nullptr;
+  int* error = nullptr;
+  int grid = 0;
+  cudaGraphExec_t exec = nullptr;
+  const void* graph_v = nullptr;
+  void* graph_out = nullptr;
+};
+
+static std::mutex g_tune_mu;
+static std::map<std::string, int> g_tune;  // (device, format, size class) -> rows
+
+static int size_class(int64_t npts) {
+  if (npts < 64 * 64) return 0;
+  if (npts < 128 * 128) return 1;
+  if (npts < 256 * 256) return 2;
+  return 3;
+}
+
+// Gershgorin row of the constant-coefficient 2D operator at a point class:
+// the same rule as the stencil rows (neighbour inside: a = D/dx^2 +- b/(2dx),
+// diag -= D/dx^2; Dirichlet face: diag -= D/dx^2; Neumann face: diag += +-b/(2dx))
+static void batch_row(const ei_batch_problem& P, bool xl, bool xh, bool yl, bool yh, double* dg,
+                      double* rad) {
+  double d = P.c, r = 0.0;
+  const bool has[4] = {!xl, !xh, !yl, !yh};
+  const double h2[2] = {P.dx * P.dx, P.dy * P.dy};
+  const double hh[2] = {P.dx, P.dy};
+  const double b[2] = {P.bx, P.by};
+  for (int e = 0; e < 2; ++e)
+    for (int side = 0; side < 2; ++side) {
+      const int sgn = side ? 1 : -1;
+      const int f = 2 * e + side;
+      if (has[f]) {
+        const double a = P.D / h2[e] + sgn * b[e] / (2.0 * hh[e]);
+        r += fabs(a);
+        d -= P.D / h2[e];
+      } else if (P.bc[f] == EI_BC_NEUMANN0) {
+        d += sgn * b[e] / (2.0 * hh[e]);
+      } else {
+        d -= P.D / h2[e];
+      }
+    }
+  *dg = d;
+  *rad = r;
+}
+
+static void batch_interval(const ei_batch_problem& P, double* alpha, double* beta) {
+  double lo = INFINITY, hi = -INFINITY;
+  // classes along x: x=0 (lo), interior, x=nx-1 (hi); nx == 1: both faces
+  for (int cx = 0; cx < 3; ++cx)
+    for (int cy = 0; cy < 3; ++cy) {
+      bool xl, xh, yl, yh;
+      if (P.nx == 1) { xl = xh = true; if (cx) continue; }
+      else if (P.nx == 2) { if (cx == 1) continue; xl = cx == 0; xh = cx == 2; }
+      else { xl = cx == 0; xh = cx == 2; }
+      if (P.ny == 1) { yl = yh = true; if (cy) continue; }
+      else if (P.ny == 2) { if (cy == 1) continue; yl = cy == 0; yh = cy == 2; }
+      else { yl = cy == 0; yh = cy == 2; }
+      double d, r;
+      batch_row(P, xl, xh, yl, yh, &d, &r);
+      lo = std::min(lo, d - r);
+      hi = std::max(hi, d + r);
+    }
+  *alpha = lo;
+  *beta = hi;
+}
+
+// schedule and divided differences of problem i for its current s (s <= 0: a-priori rule)
+static bool batch_plan(ei_batch* B, int i, int s_force) {
+  const double cc = B->c[i], gm = B->gamma[i];
+  const double h = B->prob[i].h;
+  int s = s_force, m = 0;
+  double* d = &B->hdd[(size_t)i * (B->m_max + 1)];
+  if (s <= 0) {
+    if (schedule(1, h, cc, gm, B->tol, B->m_max, &s, &m, d) != 0) return false;
+  } else {
+    divided_differences(1, h / s, cc, gm, B->m_max, d);
+  }
+  B->hinst[i].s = s;
+  B->hinst[i].tau = h / s;
+  return true;
+}
+
+static void parallel_for(int n, const std::function<void(int)>& f) {
+  int nt = (int)std::thread::hardware_concurrency();
+  if (nt < 1) nt = 1;
+  if (nt > 32) nt = 32;
+  if (nt > n) nt = n;
+  std::vector<std::thread> th;
+  for (int t = 0; t < nt; ++t)
+    th.emplace_back([&, t] {
+      for (int i = t; i < n; i += nt) f(i);
+    });
+  for (auto& x : th) x.join();
+}
+
+static void batch_free(ei_batch* B) {
+  if (B->exec) cudaGraphExecDestroy(B->exec);
+  void* ptrs[] = {B->inst, B->state, B->order, B->dinit, B->duoff, B->dscal, B->dd, B->xi,
+                  B->partials, B->pool, B->ppool, B->finished, B->progress, B->error};
+  for (void* p : ptrs)
+    if (p) cudaFree(p);
+  if (B->stream) cudaStreamDestroy(B->stream);
+}
+
+#define BTRY(x)                        \
+  do {                                 \
+    if ((x) != cudaSuccess) {          \
+      cudaGetLastError();              \
+      return EI_ERR_CUDA;              \
+    }                                  \
+  } while (0)
+
+template <int FMT>
+static cudaError_t batch_launch_body(ei_batch* B) {
+  const int count = B->count;
+  BatchDev D;
+  D.count = count;
+  D.m_max = B->m_max;
+  D.tol = B->tol;
+  D.inst = B->inst;
+  D.state = B->state;
+  D.order = B->order;
+  D.dd = B->dd;
+  D.xi = B->xi;
+  D.partials = B->partials;
+  D.pool = B->pool;
+  D.ppool = B->ppool;
+  D.finished = B->finished;
+  D.progress = B->progress;
+  D.error = B->error;
+  k_batch_init<<<(count + 255) / 256, 256, 0, B->stream>>>(B->inst, B->state, B->dinit, count,
+                                                           B->finished, B->progress, B->error);
+  k_batch_count_idle<<<(count + 255) / 256, 256, 0, B->stream>>>(B->state, count, B->finished);
+  k_batch<FMT><<<B->grid, 288, 0, B->stream>>>(D);
+  return cudaGetLastError();
+}
+
+template <int FMT, class U>
+static cudaError_t batch_io(ei_batch* B, const void* v, void* out, bool import) {
+  dim3 g(64, B->count);
+  if (import)
+    k_batch_import<FMT, U><<<g, 256, 0, B->stream>>>(B->inst, B->duoff, static_cast<const U*>(v),
+                                                     B->pool);
+  else
+    k_batch_export<FMT, U><<<g, 256, 0, B->stream>>>(B->inst, B->state, B->duoff, B->dscal,
+                                                     B->pool, B->ppool, static_cast<U*>(out));
+  return cudaGetLastError();
+}
+
+static cudaError_t batch_sequence(ei_batch* B, const void* v, void* out) {
+  cudaError_t e;
+  if (B->fmt == VF_DF) {
+    if ((e = batch_io<VF_DF, double>(B, v, out, true)) != cudaSuccess) return e;
+    if ((e = batch_launch_body<VF_DF>(B)) != cudaSuccess) return e;
+    return batch_io<VF_DF, double>(B, v, out, false);
+  }
+  if (B->fmt == VF_F64) {
+    if ((e = batch_io<VF_F64, double>(B, v, out, true)) != cudaSuccess) return e;
+    if ((e = batch_launch_body<VF_F64>(B)) != cudaSuccess) return e;
+    return batch_io<VF_F64, double>(B, v, out, false);
+  }
+  if ((e = batch_io<VF_F32, float>(B, v, out, true)) != cudaSuccess) return e;
+  if ((e = batch_launch_body<VF_F32>(B)) != cudaSuccess) return e;
+  return batch_io<VF_F32, float>(B, v, out, false);
+}
+
+static int persistent_grid(int fmt) {
+  int dev = 0, sms = 1, per = 1;
+  cudaGetDevice(&dev);
+  cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+  if (fmt == VF_DF) cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, k_batch<VF_DF>, 288, 0);
+  else if (fmt == VF_F64) cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, k_batch<VF_F64>, 288, 0);
+  else cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, k_batch<VF_F32>, 288, 0);
+  if (per < 1) per = 1;
+  return sms * per;
+}
+
+// upload per-problem tables that depend on the tile choice and the schedule
+static ei_status batch_upload(ei_batch* B) {
+  const int count = B->count;
+  int64_t poff = 0;
+  for (int i = 0; i < count; ++i) {
+    BInst& I = B->hinst[i];
+    I.tiles_x = (I.nx + 31) / 32;
+    const int th = 8 * I.rows;
+    I.tiles = I.tiles_x * ((I.ny + th - 1) / th);
+    I.poff = poff;
+    poff += 2 * (int64_t)I.tiles;
+  }
+  if (B->partials) cudaFree(B->partials);
+  B->partials = nullptr;
+  BTRY(cudaMalloc(&B->partials, sizeof(double) * (poff > 0 ? poff : 2)));
+  BTRY(cudaMemcpy(B->inst, B->hinst.data(), sizeof(BInst) * count, cudaMemcpyHostToDevice));
+  BTRY(cudaMemcpy(B->dd, B->hdd.data(), sizeof(double) * B->hdd.size(), cudaMemcpyHostToDevice));
+  // biggest problems first
+  std::vector<int> ord(count);
+  for (int i = 0; i < count; ++i) ord[i] = i;
+  std::vector<double> work(count);
+  for (int i = 0; i < count; ++i)
+    work[i] = (double)B->hinst[i].npts * B->hinst[i].s * (B->m_max / 2 + 1);
+  std::stable_sort(ord.begin(), ord.end(), [&](int a, int b) { return work[a] > work[b]; });
+  BTRY(cudaMemcpy(B->order, ord.data(), sizeof(int) * count, cudaMemcpyHostToDevice));
+  return EI_OK;
+}
+
+static ei_status batch_run(ei_batch* B, const void* v, void* out, bool graph) {
+  if (!graph) {
+    BTRY(batch_sequence(B, v, out));
+  } else {
+    if (!B->exec || B->graph_v != v || B->graph_out != out) {
+      if (B->exec) cudaGraphExecDestroy(B->exec);
+      B->exec = nullptr;
+      cudaGraph_t g;
+      BTRY(cudaStreamBeginCapture(B->stream, cudaStreamCaptureModeThreadLocal));
+      cudaError_t e = batch_sequence(B, v, out);
+      cudaError_t e2 = cudaStreamEndCapture(B->stream, &g);
+      if (e != cudaSuccess || e2 != cudaSuccess) {
+        cudaGetLastError();
+        return EI_ERR_CUDA;
+      }
+      BTRY(cudaGraphInstantiate(&B->exec, g, 0));
+      cudaGraphDestroy(g);
+      B->graph_v = v;
+      B->graph_out = out;
+    }
+    BTRY(cudaGraphLaunch(B->exec, B->stream));
+  }
+  BTRY(cudaStreamSynchronize(B->stream));
+  int err = 0;
+  BTRY(cudaMemcpy(&err, B->error, sizeof(int), cudaMemcpyDeviceToHost));
+  return err ? EI_ERR_TIMEOUT : EI_OK;
+}
+
+// autotuner: for each size class present, time the candidate tile heights on a
+// mini-batch of copies of the class's median problem; keep the fastest
+static ei_status batch_tune(ei_batch* B) {
+  int dev = 0;
+  cudaGetDevice(&dev);
+  cudaDeviceProp prop;
+  cudaGetDeviceProperties(&prop, dev);
+  std::vector<std::vector<int>> members(4);
+  for (int i = 0; i < B->count; ++i)
+    if (B->active[i]) members[size_class(B->hinst[i].npts)].push_back(i);
+  const int cand[4] = {4, 8, 16, 32};
+  for (int cls = 0; cls < 4; ++cls) {
+    if (members[cls].empty()) continue;
+    const std::string key = std::string(prop.name) + "/" + std::to_string(B->fmt) + "/" +
+                            std::to_string(cls);
+    int rows = 0;
+    {
+      std::lock_guard<std::mutex> lock(g_tune_mu);
+      auto it = g_tune.find(key);
+      if (it != g_tune.end()) rows = it->second;
+    }
+    if (!rows) {
+      std::vector<int>& m = members[cls];
+      std::sort(m.begin(), m.end(),
+                [&](int a, int b) { return B->hinst[a].npts < B->hinst[b].npts; });
+      const int rep = m[m.size() / 2];
+      // fixed work: copies of the median problem, one substep, 16 Newton
+      // iterations each (a tolerance no iteration meets)
+      int copies = (int)std::min<int64_t>(64, std::max<int64_t>(4, (int64_t)(1 << 22) / B->hinst[rep].npts));
+      std::vector<ei_batch_problem> probs(copies, B->prob[rep]);
+      float best = 1e30f;
+      for (int c : cand) {
+        ei_options o{};
+        o.tile_rows = c;
+        o.fixed_s = 1;
+        o.m_max = 16;
+        ei_batch* T = nullptr;
+        if (ei_batch_create(&T, dev, copies, probs.data(), B->prec, 1e-300, &o) != EI_OK) continue;
+        const int64_t total = T->uoff[copies];
+        void* buf = nullptr;
+        const size_t eb = B->prec == EI_PREC_F32 ? 4 : 8;
+        if (cudaMalloc(&buf, 2 * total * eb) == cudaSuccess) {
+          std::vector<double> ones(total, 1.0);
+          std::vector<float> onesf(total, 1.0f);
+          if (eb == 8) cudaMemcpy(buf, ones.data(), total * 8, cudaMemcpyHostToDevice);
+          else cudaMemcpy(buf, onesf.data(), total * 4, cudaMemcpyHostToDevice);
+          void* outb = static_cast<char*>(buf) + total * eb;
+          batch_run(T, buf, outb, false);  // warm
+          cudaEvent_t e0, e1;
+          cudaEventCreate(&e0);
+          cudaEventCreate(&e1);
+          cudaEventRecord(e0, T->stream);
+          ei_status rs = batch_run(T, buf, outb, false);
+          cudaEventRecord(e1, T->stream);
+          cudaEventSynchronize(e1);
+          float ms = 0;
+          cudaEventElapsedTime(&ms, e0, e1);
+          cudaEventDestroy(e0);
+          cudaEventDestroy(e1);
+          if (rs == EI_OK && ms < best) {
+            best = ms;
+            rows = c;
+          }
+          cudaFree(buf);
+        }
+        ei_batch_destroy(T);
+      }
+      if (!rows) rows = 2;
+      std::lock_guard<std::mutex> lock(g_tune_mu);
+      g_tune[key] = rows;
+    }
+    for (int i : members[cls]) B->hinst[i].rows = rows;
+  }
+  return EI_OK;
+}
+
+extern "C" {
+
+ei_status ei_batch_create(ei_batch** out, int device, int count, const ei_batch_problem* problems,
+                          int prec, double tol, const ei_options* opt) {
+  if (!out || count < 1 || !problems || (prec != EI_PREC_F64 && prec != EI_PREC_F32) ||
+      !(tol > 0) || !isfinite(tol))
+    return EI_ERR_INVALID_ARG;
+  *out = nullptr;
+  for (int i = 0; i < count; ++i) {
+    const ei_batch_problem& P = problems[i];
+    if (P.nx < 1 || P.ny < 1 || P.nx > (1 << 20) || P.ny > (1 << 20) || !(P.dx > 0) ||
+        !(P.dy > 0) || !(P.h > 0) || !isfinite(P.D) || !isfinite(P.bx) || !isfinite(P.by) ||
+        !isfinite(P.c) || !isfinite(P.h))
+      return EI_ERR_INVALID_ARG;
+    for (int f = 0; f < 4; ++f)
+      if (P.bc[f] != EI_BC_DIRICHLET0 && P.bc[f] != EI_BC_NEUMANN0) return EI_ERR_INVALID_ARG;
+  }
+  if (cudaSetDevice(device) != cudaSuccess) {
+    cudaGetLastError();
+    return EI_ERR_CUDA;
+  }
+  ei_batch* B = new ei_batch();
+  B->device = device;
+  B->prec = prec;
+  B->fmt = (prec == EI_PREC_F32) ? VF_F32 : ((opt && opt->arith == EI_ARITH_NATIVE_F64) ? VF_F64 : VF_DF);
+  B->count = count;
+  B->tol = tol;
+  B->m_max = (opt && opt->m_max > 0 && opt->m_max <= 100) ? opt->m_max : 100;
+  B->prob.assign(problems, problems + count);
+  B->hinst.resize(count);
+  B->uoff.resize(count + 1);
+  B->active.assign(count, 1);
+  B->scal.assign(count, 0.0);
+  B->alpha.resize(count);
+  B->beta.resize(count);
+  B->c.resize(count);
+  B->gamma.resize(count);
+  B->restarts.assign(count, 0);
+  B->hdd.assign((size_t)count * (B->m_max + 1), 0.0);
+  int64_t uo = 0, po = 0;
+  for (int i = 0; i < count; ++i) {
+    const ei_batch_problem& P = problems[i];
+    BInst& I = B->hinst[i];
+    memset(&I, 0, sizeof(I));
+    I.nx = (int)P.nx;
+    I.ny = (int)P.ny;
+    I.npts = P.nx * P.ny;
+    for (int f = 0; f < 4; ++f) I.bc[f] = P.bc[f];
+    I.axm = P.D / (P.dx * P.dx) - P.bx / (2.0 * P.dx);
+    I.axp = P.D / (P.dx * P.dx) + P.bx / (2.0 * P.dx);
+    I.aym = P.D / (P.dy * P.dy) - P.by / (2.0 * P.dy);
+    I.ayp = P.D / (P.dy * P.dy) + P.by / (2.0 * P.dy);
+    I.d0 = P.c - 2.0 * P.D / (P.dx * P.dx) - 2.0 * P.D / (P.dy * P.dy);
+    I.h = P.h;
+    I.rows = 2;
+    B->uoff[i] = uo;
+    uo += I.npts;
+    I.off = po;
+    po += 5 * I.npts;
+    batch_interval(P, &B->alpha[i], &B->beta[i]);
+    B->c[i] = 0.5 * (B->alpha[i] + B->beta[i]);
+    B->gamma[i] = 0.25 * (B->beta[i] - B->alpha[i]);
+    I.inv_gamma = B->gamma[i] > 0 ? 1.0 / B->gamma[i] : 0.0;
+    I.c_over_gamma = B->gamma[i] > 0 ? B->c[i] / B->gamma[i] : 0.0;
+    I.dd_off = i * (B->m_max + 1);
+    I.s = 1;
+    if (!(B->gamma[i] > 0)) {
+      B->active[i] = 0;
+      B->scal[i] = phi_scalar(1, P.h * B->c[i]);
+    }
+  }
+  B->uoff[count] = uo;
+  // schedules and divided differences, in parallel over problems
+  std::vector<int> ok(count, 1);
+  const int s_force = (opt && opt->fixed_s > 0) ? opt->fixed_s : 0;
+  parallel_for(count, [&](int i) {
+    if (B->active[i]) ok[i] = batch_plan(B, i, s_force) ? 1 : 0;
+  });
+  for (int i = 0; i < count; ++i)
+    if (!ok[i]) {
+      delete B;
+      return EI_ERR_NOT_CONVERGED;
+    }
+  ei_status st = EI_OK;
+  auto fail = [&](ei_status s) {
+    batch_free(B);
+    delete B;
+    return s;
+  };
+  if (cudaStreamCreateWithFlags(&B->stream, cudaStreamNonBlocking) != cudaSuccess) return fail(EI_ERR_CUDA);
+  const size_t eb = (B->fmt == VF_F32) ? 4 : 8;
+  if (cudaMalloc(&B->pool, eb * po) != cudaSuccess || cudaMalloc(&B->ppool, 8 * (po / 5)) != cudaSuccess ||
+      cudaMalloc(&B->inst, sizeof(BInst) * count) != cudaSuccess ||
+      cudaMalloc(&B->state, sizeof(BState) * count) != cudaSuccess ||
+      cudaMalloc(&B->order, sizeof(int) * count) != cudaSuccess ||
+      cudaMalloc(&B->dinit, sizeof(int) * count) != cudaSuccess ||
+      cudaMalloc(&B->duoff, sizeof(int64_t) * (count + 1)) != cudaSuccess ||
+      cudaMalloc(&B->dscal, sizeof(double) * count) != cudaSuccess ||
+      cudaMalloc(&B->dd, sizeof(double) * B->hdd.size()) != cudaSuccess ||
+      cudaMalloc(&B->xi, sizeof(double) * 101) != cudaSuccess ||
+      cudaMalloc(&B->finished, sizeof(unsigned)) != cudaSuccess ||
+      cudaMalloc(&B->progress, sizeof(unsigned long long)) != cudaSuccess ||
+      cudaMalloc(&B->error, sizeof(int)) != cudaSuccess) {
+    cudaGetLastError();
+    return fail(EI_ERR_NOMEM);
+  }
+  cudaMemset(B->pool, 0, eb * po);
+  cudaMemset(B->ppool, 0, 8 * (po / 5));
+  B->init.resize(count);
+  for (int i = 0; i < count; ++i) B->init[i] = B->active[i] ? ST_RUN : ST_SCALAR;
+  B->final_deg.assign(count, 0);
+  cudaMemcpy(B->dinit, B->init.data(), sizeof(int) * count, cudaMemcpyHostToDevice);
+  cudaMemcpy(B->duoff, B->uoff.data(), sizeof(int64_t) * (count + 1), cudaMemcpyHostToDevice);
+  cudaMemcpy(B->dscal, B->scal.data(), sizeof(double) * count, cudaMemcpyHostToDevice);
+  cudaMemcpy(B->xi, leja_table(), sizeof(double) * 101, cudaMemcpyHostToDevice);
+  B->grid = persistent_grid(B->fmt);
+  if (opt && opt->tile_rows > 0) {
+    for (int i = 0; i < count; ++i) B->hinst[i].rows = opt->tile_rows;
+  } else if ((st = batch_tune(B)) != EI_OK) {
+    return fail(st);
+  }
+  if ((st = batch_upload(B)) != EI_OK) return fail(st);
+  *out = B;
+  return EI_OK;
+}
+
+ei_status ei_batch_offsets(const ei_batch* b, int64_t* offsets) {
+  if (!b) return EI_ERR_INVALID_ARG;
+  if (offsets)
+    for (int i = 0; i <= b->count; ++i) offsets[i] = b->uoff[i];
+  return EI_OK;
+}
+
+ei_status ei_batch_phi1(ei_batch* B, void* cuda_stream, const void* v, void* out,
+                        ei_batch_stats* per) {
+  if (!B || !v || !out) return EI_ERR_INVALID_ARG;
+  if (cudaSetDevice(B->device) != cudaSuccess) return EI_ERR_CUDA;
+  // order against the caller's stream: its pending work on v finishes first
+  cudaStream_t us = (cudaStream_t)cuda_stream;
+  cudaEvent_t ev;
+  BTRY(cudaEventCreateWithFlags(&ev, cudaEventDisableTiming));
+  BTRY(cudaEventRecord(ev, us));
+  BTRY(cudaStreamWaitEvent(B->stream, ev, 0));
+  ei_status rc = batch_run(B, v, out, true);
+  // problems that reached m_max: double s and rerun them alone; the others keep
+  // their results (status SKIP in the rerun)
+  std::vector<BState> hs(B->count);
+  while (rc == EI_OK) {
+    BTRY(cudaMemcpy(hs.data(), B->state, sizeof(BState) * B->count, cudaMemcpyDeviceToHost));
+    std::vector<int> redo;
+    for (int i = 0; i < B->count; ++i) {
+      if (hs[i].status == ST_NONFINITE) rc = EI_ERR_NONFINITE;
+      else if (hs[i].status == ST_FAIL) redo.push_back(i);
+      else if (hs[i].status == ST_DONE) B->final_deg[i] = hs[i].degree_sum;
+    }
+    if (rc != EI_OK || redo.empty()) break;
+    std::vector<int> init(B->count, ST_SKIP);
+    for (int i : redo) {
+      const int s2 = 2 * B->hinst[i].s;
+      if (s2 > (1 << 20)) {
+        rc = EI_ERR_NOT_CONVERGED;
+        break;
+      }
+      batch_plan(B, i, s2);
+      B->restarts[i] += 1;
+      init[i] = ST_RUN;
+    }
+    if (rc != EI_OK) break;
+    if ((rc = batch_upload(B)) != EI_OK) break;
+    BTRY(cudaMemcpy(B->dinit, init.data(), sizeof(int) * B->count, cudaMemcpyHostToDevice));
+    cudaError_t e;
+    if (B->fmt == VF_DF) e = batch_launch_body<VF_DF>(B);
+    else if (B->fmt == VF_F64) e = batch_launch_body<VF_F64>(B);
+    else e = batch_launch_body<VF_F32>(B);
+    if (e == cudaSuccess) {
+      if (B->fmt == VF_DF) e = batch_io<VF_DF, double>(B, v, out, false);
+      else if (B->fmt == VF_F64) e = batch_io<VF_F64, double>(B, v, out, false);
+      else e = batch_io<VF_F32, float>(B, v, out, false);
+    }
+    if (e == cudaSuccess) e = cudaStreamSynchronize(B->stream);
+    BTRY(cudaMemcpy(B->dinit, B->init.data(), sizeof(int) * B->count, cudaMemcpyHostToDevice));
+    if (e != cudaSuccess) {
+      cudaGetLastError();
+      rc = EI_ERR_CUDA;
+    } else {
+      int err = 0;
+      BTRY(cudaMemcpy(&err, B->error, sizeof(int), cudaMemcpyDeviceToHost));
+      if (err) rc = EI_ERR_TIMEOUT;
+    }
+    // the graph holds the old tables: rebuild it at the next call
+    if (B->exec) cudaGraphExecDestroy(B->exec);
+    B->exec = nullptr;
+  }
+  if (per && rc == EI_OK) {
+    for (int i = 0; i < B->count; ++i) {
+      per[i].alpha = B->alpha[i];
+      per[i].beta = B->beta[i];
+      per[i].s = B->active[i] ? B->hinst[i].s : 1;
+      per[i].degree_sum = B->active[i] ? B->final_deg[i] : 0;
+      per[i].restarts = B->restarts[i];
+      per[i].tile_rows = B->hinst[i].rows;
+    }
+  }
+  // the caller's stream waits for the batch
+  BTRY(cudaEventRecord(ev, B->stream));
+  BTRY(cudaStreamWaitEvent(us, ev, 0));
+  cudaEventDestroy(ev);
+  return rc;
+}
+
+void ei_batch_destroy(ei_batch* B) {
+  if (!B) return;
+  cudaSetDevice(B->device);
+  if (B->stream) cudaStreamSynchronize(B->stream);
+  batch_free(B);
+  delete B;
+}
+
+}  // extern "C"

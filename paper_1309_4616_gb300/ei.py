@@ -27,12 +27,14 @@ EXPORTS = [
     "ei_set_operator_csr", "ei_estimate_spectrum", "ei_phi_apply", "ei_step",
     "ei_step_host", "ei_leja_points", "ei_divided_differences", "ei_schedule",
     "ei_status_string", "ei_estimate_spectrum_stencil_noalloc",
+    "ei_batch_create", "ei_batch_offsets", "ei_batch_phi1", "ei_batch_destroy",
 ]
 
 
 class Options(C.Structure):
     _fields_ = [("m_max", C.c_int), ("arith", C.c_int), ("fixed_s", C.c_int),
-                ("profile", C.c_int), ("single_iter", C.c_int), ("reserved", C.c_int * 3)]
+                ("profile", C.c_int), ("single_iter", C.c_int), ("tile_rows", C.c_int),
+                ("reserved", C.c_int * 2)]
 
 
 class Stats(C.Structure):
@@ -53,6 +55,17 @@ class Stats(C.Structure):
                 "degrees": self.degree_list(), "launches": self.launches,
                 "newton_timed": self.newton_timed, "newton_fused": self.newton_fused,
                 "newton_ms": self.newton_ms}
+
+
+class BatchProblem(C.Structure):
+    _fields_ = [("nx", C.c_int64), ("ny", C.c_int64), ("dx", C.c_double), ("dy", C.c_double),
+                ("D", C.c_double), ("bx", C.c_double), ("by", C.c_double), ("c", C.c_double),
+                ("bc", C.c_int * 4), ("h", C.c_double)]
+
+
+class BatchStats(C.Structure):
+    _fields_ = [("alpha", C.c_double), ("beta", C.c_double), ("s", C.c_int),
+                ("degree_sum", C.c_int), ("restarts", C.c_int), ("tile_rows", C.c_int)]
 
 
 class EIError(RuntimeError):
@@ -90,11 +103,18 @@ def lib():
         L.ei_estimate_spectrum_stencil_noalloc.argtypes = [
             C.c_int, vp, C.c_int, i64p, dp, vp, C.c_double, C.POINTER(C.c_void_p), dp, vp,
             C.c_double, ip, C.c_int, dp, dp]
+        L.ei_batch_create.argtypes = [C.POINTER(C.c_void_p), C.c_int, C.c_int,
+                                      C.POINTER(BatchProblem), C.c_int, C.c_double,
+                                      C.POINTER(Options)]
+        L.ei_batch_offsets.argtypes = [vp, i64p]
+        L.ei_batch_phi1.argtypes = [vp, vp, vp, vp, C.POINTER(BatchStats)]
+        L.ei_batch_destroy.argtypes = [vp]
+        L.ei_batch_destroy.restype = None
         L.ei_status_string.argtypes = [C.c_int]
         L.ei_status_string.restype = C.c_char_p
         for name in EXPORTS:
             f = getattr(L, name)
-            if name not in ("ei_destroy", "ei_status_string"):
+            if name not in ("ei_destroy", "ei_status_string", "ei_batch_destroy"):
                 f.restype = C.c_int
         _LIB = L
     return _LIB
@@ -264,3 +284,56 @@ class Context:
         _check(lib().ei_step_host(self._h, method, h, C.c_void_p(u_host.data_ptr()), nonlin,
                                   tol, self._opts(options), C.byref(st)), "ei_step_host")
         return st
+
+
+class Batch:
+    """Many independent 2D constant-coefficient problems advanced by one
+    persistent launch (ei_batch_*).  problems: objects with n=(nx, ny),
+    dx=(dx, dy), D, b=(bx, by), bc (4 codes), h, and optionally c."""
+
+    def __init__(self, problems, prec=PREC_F64, tol=1e-10, device=0, options=None):
+        import numpy as np
+        self.count = len(problems)
+        arr = (BatchProblem * self.count)()
+        for i, p in enumerate(problems):
+            q = arr[i]
+            q.nx, q.ny = int(p.n[0]), int(p.n[1])
+            q.dx, q.dy = float(p.dx[0]), float(p.dx[1])
+            q.D = float(p.D)
+            q.bx, q.by = float(p.b[0]), float(p.b[1])
+            q.c = float(getattr(p, "c", 0.0))
+            for f in range(4):
+                q.bc[f] = int(p.bc[f])
+            q.h = float(p.h)
+        h = C.c_void_p()
+        _check(lib().ei_batch_create(C.byref(h), device, self.count, arr, prec, tol,
+                                     Context._opts(options)), "ei_batch_create")
+        self._h = h
+        self.prec = prec
+        off = np.zeros(self.count + 1, dtype=np.int64)
+        _check(lib().ei_batch_offsets(self._h, off.ctypes.data_as(C.POINTER(C.c_int64))),
+               "ei_batch_offsets")
+        self.offsets = off
+
+    def phi1(self, v, out, stream=None):
+        import torch
+        dt = torch.float64 if self.prec == PREC_F64 else torch.float32
+        n = int(self.offsets[-1])
+        if stream is None:
+            stream = torch.cuda.current_stream()
+        st = (BatchStats * self.count)()
+        _check(lib().ei_batch_phi1(self._h, C.c_void_p(stream.cuda_stream),
+                                   _dev_ptr(v, dt, n, "v"), _dev_ptr(out, dt, n, "out"), st),
+               "ei_batch_phi1")
+        return st
+
+    def close(self):
+        if getattr(self, "_h", None):
+            lib().ei_batch_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass

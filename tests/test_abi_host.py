@@ -22,7 +22,7 @@ def ei():
 
 def test_header_symbols_exported(ei):
     hdr = open(os.path.join(ROOT, "include", "ei.h")).read()
-    declared = set(re.findall(r"\b(ei_[a-z_]+)\s*\(", hdr)) - {"ei_ctx"}
+    declared = set(re.findall(r"\b(ei_[a-z_0-9]+)\s*\(", hdr)) - {"ei_ctx"}
     assert declared == set(ei.EXPORTS)
     L_ = ei.lib()
     for name in declared:
