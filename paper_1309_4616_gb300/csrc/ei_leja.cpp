@@ -110,48 +110,71 @@ static void expm_bidiag_col0(int n, const double* dg, const double* sd, double* 
   const int K = 64;
   std::vector<double> T((size_t)n * n, 0.0), U((size_t)n * n, 0.0);
   for (int i = 0; i < n; ++i) T[(size_t)i * n + i] = 1.0;
+  // After i Horner steps T - I has band width i (X is bidiagonal), so row r
+  // only needs columns c >= r - i; the rest of the lower triangle is still 0.
   for (int it = K; it >= 1; --it) {
     const double inv = 1.0 / it;
+    const int band = K - it + 1;
     // U = I + (X T)/it ;  (X T)[r][c] = xd[r] T[r][c] + xs[r-1] T[r-1][c]
-    for (int r = 0; r < n; ++r) {
-      double* Ur = &U[(size_t)r * n];
-      const double* Tr = &T[(size_t)r * n];
-      const double* Tm = r > 0 ? &T[(size_t)(r - 1) * n] : nullptr;
-      for (int c = 0; c <= r; ++c) {
-        double v = xd[r] * Tr[c];
-        if (r > 0 && c <= r - 1) v += xs[r - 1] * Tm[c];
-        Ur[c] = v * inv + (r == c ? 1.0 : 0.0);
-      }
+    U[0] = xd[0] * T[0] * inv + 1.0;
+    for (int r = 1; r < n; ++r) {
+      double* __restrict__ Ur = &U[(size_t)r * n];
+      const double* __restrict__ Tr = &T[(size_t)r * n];
+      const double* __restrict__ Tm = &T[(size_t)(r - 1) * n];
+      const double a = xd[r], b = xs[r - 1];
+      const int c0 = r - band > 0 ? r - band : 0;
+      for (int c = c0; c < r; ++c) Ur[c] = (a * Tr[c] + b * Tm[c]) * inv;
+      Ur[r] = a * Tr[r] * inv + 1.0;
     }
     std::swap(T, U);
   }
   const double es = exp(-sigma * sc);
   for (int r = 0; r < n; ++r)
     for (int c = 0; c <= r; ++c) T[(size_t)r * n + c] *= es;
-  // square q times (the last squaring only for column 0); row r of T*T is
-  // accumulated as sum_l T[r][l] * (row l of T), l increasing, so every entry
-  // sums its terms in the same order as the dot-product form
-  for (int sq = 0; sq < q; ++sq) {
-    const bool last = (sq == q - 1);
+  // exp(N) e_0 = T^(2^q) e_0.  Square T `sq` times (n^3/6 multiply-adds
+  // each), then apply the result 2^(q-sq) times to e_0 as a triangular
+  // matrix-vector product (n^2/2 each); sq minimises the total.  Every term
+  // is nonnegative.  Row r of T*T is accumulated as sum_l T[r][l] * (row l of T).
+  int sq = 0;
+  {
+    double best = 0.0;
+    for (int j = 0; j <= q; ++j) {
+      const double cost = j * (double)n * n * n / 6.0 + ldexp((double)n * n / 2.0, q - j);
+      if (j == 0 || cost < best) { best = cost; sq = j; }
+    }
+  }
+  for (int it = 0; it < sq; ++it) {
     for (int r = 0; r < n; ++r) {
-      double* Ur = &U[(size_t)r * n];
-      const double* Tr = &T[(size_t)r * n];
-      if (last) {
-        double s0 = 0.0;
-        for (int l = 0; l <= r; ++l) s0 += Tr[l] * T[(size_t)l * n];
-        Ur[0] = s0;
-        continue;
-      }
+      double* __restrict__ Ur = &U[(size_t)r * n];
+      const double* __restrict__ Tr = &T[(size_t)r * n];
       for (int c = 0; c <= r; ++c) Ur[c] = 0.0;
       for (int l = 0; l <= r; ++l) {
         const double t = Tr[l];
-        const double* Tl = &T[(size_t)l * n];
+        const double* __restrict__ Tl = &T[(size_t)l * n];
         for (int c = 0; c <= l; ++c) Ur[c] += t * Tl[c];
       }
     }
     std::swap(T, U);
   }
-  for (int r = 0; r < n; ++r) out[r] = T[(size_t)r * n];
+  std::vector<double> y(n), z(n);
+  for (int r = 0; r < n; ++r) y[r] = T[(size_t)r * n];
+  for (long rep = 1; rep < (1L << (q - sq)); ++rep) {
+    for (int r = 0; r < n; ++r) {
+      const double* __restrict__ Tr = &T[(size_t)r * n];
+      double a0 = 0.0, a1 = 0.0, a2 = 0.0, a3 = 0.0;  // four independent chains
+      int l = 0;
+      for (; l + 3 <= r; l += 4) {
+        a0 += Tr[l] * y[l];
+        a1 += Tr[l + 1] * y[l + 1];
+        a2 += Tr[l + 2] * y[l + 2];
+        a3 += Tr[l + 3] * y[l + 3];
+      }
+      for (; l <= r; ++l) a0 += Tr[l] * y[l];
+      z[r] = (a0 + a1) + (a2 + a3);
+    }
+    std::swap(y, z);
+  }
+  for (int r = 0; r < n; ++r) out[r] = y[r];
 }
 
 void divided_differences(int k, double tau, double c, double gamma, int m, double* out) {
@@ -216,14 +239,18 @@ int schedule(int k, double h, double c, double gamma, double tol, int m_max, int
       p[i] = 0.0;
       om[i] = 1.0;
     }
+    const double bound = tol * fmax;
     for (int j = 0; j <= m_max; ++j) {
-      double err = 0.0;
+      const double dj = d[j], xj = xi[j];
       for (int i = 0; i < kGrid; ++i) {
-        p[i] += d[j] * om[i];
-        err = std::max(err, fabs(f[i] - p[i]));
-        om[i] *= (g[i] - xi[j]);
+        p[i] += dj * om[i];
+        om[i] *= (g[i] - xj);
       }
-      if (err <= tol * fmax) {
+      // max_G |f - p| <= bound  <=>  no grid point exceeds the bound
+      bool pass = true;
+      for (int i = 0; i < kGrid; ++i)
+        if (!(fabs(f[i] - p[i]) <= bound)) { pass = false; break; }
+      if (pass) {
         *s_out = s;
         *m_out = j;
         if (d_out)
