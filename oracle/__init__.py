@@ -12,7 +12,11 @@ Modules
   operators  Row assembly of the stencil operators and the CSR graph operator,
              Gershgorin interval (Sec. III-A, III-B).
   newton     The Newton-form Leja iteration, phi_k(hA)v with substeps,
-             exponential Euler (Eq. (2)) and exponential Rosenbrock-Euler.
+             exponential Euler (Eq. (2)) and exponential Rosenbrock-Euler;
+             the fixed-count form and the no-restart driver.
+  mlp        The schedule network: forward, loss, backward, Adam (FP64).
+  learned    Features, decision rule and phi_1 under the learned schedule,
+             with the plain method as fallback.
   dense      phi_k(hA)v by definition: expm of an augmented matrix.
   closed     Closed forms: sine / cosine eigenbases of constant-coefficient
              operators, the analytic Gaussian.

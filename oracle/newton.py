@@ -112,6 +112,72 @@ def h_phi1_substeps(op, h, v, tol, stats, m_max=L.M_MAX, xi=None):
     raise NotConverged("phi_1: no s <= S_MAX converged")
 
 
+def newton_phi_fixed(op, r, d, xi, c, gamma, tol, m, stats):
+    """Exactly m Newton steps with no test in between; then the estimate of
+    the last step decides: ok = |d_m| ||w_m|| <= tol ||p_m||.  Returns (p, ok).
+    The iterates are those of newton_phi; only the stopping differs."""
+    if _norm(r) == 0.0:
+        return np.zeros_like(r), True
+    w = r.copy()
+    p = d[0] * w
+    for j in range(m):
+        shift = c / gamma + xi[j]
+        w = op.matvec(w) / gamma - shift * w
+        stats.matvecs += 1
+        p = p + d[j + 1] * w
+    ok = abs(d[m]) * _norm(w) <= tol * _norm(p)
+    return p, ok
+
+
+def h_phi1_fixed(op, h, v, tol, s, m, stats, xi=None):
+    """y ~= h phi_1(hA) v with a given substep count s and exactly m Newton
+    steps in every substep; ok = every substep's final estimate passed.
+    Returns (y, ok).  gamma > 0 and ||v|| > 0 are the caller's to check."""
+    alpha, beta, c, gamma = _interval(op)
+    stats.alpha, stats.beta = alpha, beta
+    v = np.asarray(v, dtype=np.float64).reshape(op.shape)
+    if xi is None:
+        xi = L.leja_points(L.M_MAX)
+    tau = h / s
+    d = L.divided_differences(1, tau, c, gamma, xi[: m + 1])
+    y = np.zeros_like(v)
+    ok_all = True
+    for i in range(s):
+        if i == 0:
+            r = v.copy()
+        else:
+            r = op.matvec(y) + v
+            stats.matvecs += 1
+        p, ok = newton_phi_fixed(op, r, d, xi, c, gamma, tol, m, stats)
+        ok_all = ok_all and ok
+        y = y + tau * p
+    stats.s, stats.degrees = s, [m] * s
+    return y, ok_all
+
+
+def h_phi1_at(op, h, v, tol, s, m_max=L.M_MAX, xi=None):
+    """The a posteriori iteration at a given s with no restart: returns
+    (y, degrees, converged) where converged says every substep met the
+    tolerance within m_max steps (degrees then lists them)."""
+    stats = Stats()
+    alpha, beta, c, gamma = _interval(op)
+    v = np.asarray(v, dtype=np.float64).reshape(op.shape)
+    if xi is None:
+        xi = L.leja_points(m_max)
+    tau = h / s
+    d = L.divided_differences(1, tau, c, gamma, xi[: m_max + 1])
+    y = np.zeros_like(v)
+    degrees = []
+    for i in range(s):
+        r = v.copy() if i == 0 else op.matvec(y) + v
+        p, deg, conv = newton_phi(op, r, d, xi, c, gamma, tol, m_max, stats)
+        degrees.append(deg)
+        if not conv:
+            return y, degrees, False
+        y = y + tau * p
+    return y, degrees, True
+
+
 def phi_apply(op, k, h, v, tol, m_max=L.M_MAX, xi=None):
     """phi_k(hA) v.  k = 1: substepped ODE form; k = 0: (e^{tau A})^s v;
     k >= 2: a single step (s = 1) or NotConverged.  Returns (result, Stats)."""
