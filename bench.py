@@ -468,8 +468,10 @@ def run_ours(args):
         avg_launch_s = ms * 1e-3 / args.steps
         achieved = wl.bytes_per_point * st.point_iters / avg_launch_s / 1e9
     else:
+        # unit: one point-iteration; a two-iteration launch processes two per point
+        # (its DRAM traffic is about half of that: w_{j+1} stays on chip)
         avg_launch_s = prof_ms / max(prof_n, 1) * 1e-3
-        achieved = wl.bytes_per_point * npts / avg_launch_s / 1e9
+        achieved = wl.bytes_per_point * npts * fused / avg_launch_s / 1e9
 
     # e2e through the public API with host buffers: H2D of the state, the step, D2H
     u_host = torch.from_numpy(np.ascontiguousarray(wl.host0).copy()).pin_memory()
@@ -509,7 +511,7 @@ def run_ours(args):
             "dtype": wl.dtype, "data": "synthetic", "config": config,
             "roofline": {"bound": "hbm", "achieved": achieved, "peak": hbm, "unit": "GB/s",
                          "frac": achieved / hbm, "traffic": None, "kernel": wl.kernel(fused),
-                         "bytes_per_launch": wl.bytes_per_point * npts,
+                         "bytes_per_launch": wl.bytes_per_point * npts * fused,
                          "avg_launch_us": avg_launch_s * 1e6, "launches_timed": prof_n,
                          "iterations_per_launch": fused,
                          "us_per_iteration": avg_launch_s * 1e6 / fused,

@@ -85,7 +85,12 @@ typedef struct {
                       in the F64 formats fuse two iterations per launch) */
   int tile_rows;   /* batched form: tile height in units of 8 rows (1 to 32);
                       0 = the autotuner's choice */
-  int reserved[2];
+  int learned;     /* phi_1 schedule: 0 the plain a-priori rule; 1 the learned
+                      schedule of the model set by ei_set_schedule_model (plain
+                      fallback); 2 the plain rule, reporting stats.features */
+  int no_restart;  /* with fixed_s: an attempt that reaches m_max returns
+                      EI_ERR_NOT_CONVERGED instead of doubling s (stats keep the
+                      degrees reached; u and out are left unmodified) */
 } ei_options;
 
 #define EI_STATS_MAX_SUBSTEPS 64
@@ -102,6 +107,14 @@ typedef struct {
   int newton_timed;     /* Newton-iteration launches timed (options.profile) */
   int newton_fused;     /* Newton iterations per timed launch (1 or 2) */
   double newton_ms;     /* their summed device time (launches that did work) */
+  int learned;          /* 0 plain rule; 1 learned proposal accepted; 2 proposal
+                           failed its check (plain fallback); 3 no q accepted
+                           (plain); 4 features only (options.learned = 2) */
+  int learned_s;        /* the proposal (learned = 1 or 2) */
+  int learned_m;
+  int learned_pad;
+  double features[12];  /* features of the call at the substep count used
+                           (options.learned != 0); see ei_mlp below */
 } ei_stats;
 
 /* Create a context on CUDA device `device`, ordering work on `cuda_stream`
@@ -213,6 +226,73 @@ ei_status ei_divided_differences(int k, double tau, double c, double gamma, int 
  * meets max_G |f - p_m| <= tol max_G |f| on 2001 points G of [-2,2]. */
 ei_status ei_schedule(int k, double h, double c, double gamma, double tol, int m_max,
                       int* s_out, int* m_out);
+
+/* ---- Learned schedule ------------------------------------------------------
+ * A small network proposes the substep count and the Leja degree of a phi_1
+ * call instead of the conservative a priori rule (Sec. III-C); the a
+ * posteriori estimate still accepts or rejects the proposal.  Network:
+ * EI_MLP_INPUTS inputs, three hidden layers of 64 with ReLU, EI_MLP_OUTPUTS
+ * linear outputs, FP32, parameters one flat vector (per layer W, out x in,
+ * row major, then b).  For candidate q = 0..q_max (s = 2^q) output 0 is the
+ * degree the estimate will need as a fraction of m_max and output 1 the logit
+ * of meeting it within m_max.  The call takes the smallest q with
+ * o1 >= z_min and need = m_max o0 (1 + rho_m) + delta_m <= m_max, runs
+ * m = clamp(ceil(need), 1, m_max) Newton steps in each of the s substeps with
+ * no test in between, then checks |d_m| ||w_m|| <= tol ||p_m|| once per
+ * substep.  Any failed check, or no accepted q, redoes the call by the plain
+ * method.
+ * Features of a call with interval [alpha, beta], c = (alpha+beta)/2,
+ * gamma = (beta-alpha)/4, tau = h/s, rho = max(|alpha|, |beta|):
+ *   0 log10(tau gamma)        1 clip(c/gamma, -8, 8)/4   2 log10(tol)/10
+ *   3 log2(s)/10              4 log10(h rho)/3           5 k (1)
+ *   6 1 for CSR, else 0       7 dim/3 (CSR: 0)
+ *   8 coefficient ratio: stencil mean(D)/max(D); CSR mean|diag|/max|diag|
+ *   9 log10(1 + min(Pe, 1e30)), Pe = max over points and axes of
+ *     |b_e| dx_e / (2 D) (stencil), 0 (CSR)
+ *  10 clip(log10(||v||_2 / sqrt(n)), -30, 30)/10    11 log10(n)/8
+ * (v is the vector phi_1 acts on: the input of ei_phi_apply, F_n of ei_step). */
+#define EI_MLP_INPUTS 12
+#define EI_MLP_OUTPUTS 2
+#define EI_MLP_PARAMS 9282
+#define EI_MLP_MAX_Q 12
+
+typedef struct ei_mlp ei_mlp; /* opaque, library-owned: parameters and Adam state */
+
+typedef struct {
+  double z_min;    /* acceptance threshold on output 1 (a logit) */
+  double rho_m;    /* relative margin on the predicted degree, >= 0 */
+  double delta_m;  /* absolute margin on the predicted degree */
+  int q_max;       /* largest candidate q, 0..EI_MLP_MAX_Q */
+  int pad;
+} ei_mlp_decision;
+
+/* Create a network on `device` (parameters zero; decision z_min 0, rho_m 0.05,
+ * delta_m 2, q_max EI_MLP_MAX_Q), ordering its work on `cuda_stream`. */
+ei_status ei_mlp_create(ei_mlp** out, int device, void* cuda_stream);
+void ei_mlp_destroy(ei_mlp* m);
+/* Parameters from / to a host array of EI_MLP_PARAMS floats.  Setting them
+ * clears the Adam state.  Non-finite values: EI_ERR_NONFINITE. */
+ei_status ei_mlp_set_params(ei_mlp* m, const float* theta);
+ei_status ei_mlp_get_params(ei_mlp* m, float* theta);
+ei_status ei_mlp_set_decision(ei_mlp* m, const ei_mlp_decision* d);
+ei_status ei_mlp_get_decision(const ei_mlp* m, ei_mlp_decision* d);
+/* out (device, rows x EI_MLP_OUTPUTS) = network(x) for x (device,
+ * rows x EI_MLP_INPUTS, row major).  Asynchronous on the model's stream. */
+ei_status ei_mlp_forward(ei_mlp* m, const float* x, int64_t rows, float* out);
+/* Loss of a batch and its gradient: x as above, y (device, rows x 2: target
+ * degree fraction, converged 0/1), mask (device, rows: 1 where y[.,0] is
+ * defined).  loss = mean over rows of mask k(e) e^2 + lam (softplus(o1) - y1 o1),
+ * e = o0 - y0, k = kappa if e < 0 else 1.  grad: device, EI_MLP_PARAMS floats.
+ * *loss (host, may be NULL) is written after a stream synchronisation. */
+ei_status ei_mlp_loss_grad(ei_mlp* m, const float* x, const float* y, const float* mask,
+                           int64_t rows, double lam, double kappa, double* loss, float* grad);
+/* One Adam step (b1 0.9, b2 0.999, eps 1e-8, learning rate lr) on the batch's
+ * gradient.  *loss (may be NULL) receives the batch loss before the step. */
+ei_status ei_mlp_train_step(ei_mlp* m, const float* x, const float* y, const float* mask,
+                            int64_t rows, double lam, double kappa, double lr, double* loss);
+/* Use `model` (NULL: none) for calls with ei_options.learned = 1.  The
+ * context keeps the pointer; the caller keeps the model alive meanwhile. */
+ei_status ei_set_schedule_model(ei_ctx* ctx, const ei_mlp* model);
 
 /* ---- Batched form ---------------------------------------------------------
  * Many independent problems of uneven size, each a 2D stencil operator with

@@ -20,7 +20,7 @@ rho = max(|alpha|, |beta|):
   x0  log10(tau gamma)               x6  1 for a CSR operator, else 0
   x1  clip(c/gamma, -8, 8) / 4       x7  grid dimension / 3 (0 for CSR)
   x2  log10(tol) / 10                x8  coefficient ratio (below)
-  x3  q / 10                         x9  log10(1 + Peclet) (below)
+  x3  q / 10 (= log2(s)/10)          x9  log10(1 + min(Peclet, 1e30))
   x4  log10(h rho) / 3               x10 clip(log10(||v||_2/sqrt(n)), -30, 30) / 10
   x5  k (the phi index; 1 here)      x11 log10(n) / 8
 
@@ -95,7 +95,7 @@ def features(q, h, alpha, beta, tol, k, kind, dim, n, ratio, peclet, v_norm):
         1.0 if kind == KIND_CSR else 0.0,
         (dim / 3.0) if kind == KIND_STENCIL else 0.0,
         ratio,
-        math.log10(1.0 + peclet),
+        math.log10(1.0 + min(peclet, 1e30)),
         lr / 10.0,
         math.log10(n) / 8.0,
     ])

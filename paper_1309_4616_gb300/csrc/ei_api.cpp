@@ -13,6 +13,7 @@
 #include <stdlib.h>
 #include <string.h>
 
+#include <algorithm>
 #include <vector>
 
 #include "ei.h"
@@ -96,6 +97,12 @@ struct ei_ctx {
   int newton_fused = 1;
   bool fuse2 = true;       // two Newton iterations per launch where the kernel allows
   std::vector<cudaEvent_t> ev;
+  // learned schedule: the model (caller-owned), the operator's coefficient
+  // statistics (computed on first use) and ||v||^2 of the current phi_1 call
+  const ei_mlp* model = nullptr;
+  bool cs_valid = false;
+  double cs_ratio = 1.0, cs_pe = 0.0;
+  double vnorm2 = 0.0;
 };
 
 #define EI_TRY_CUDA(expr)                        \
@@ -164,6 +171,7 @@ static void free_operator(ei_ctx* c) {
   c->host_stage = nullptr;
   c->max_blocks = 0;
   c->kind = KIND_NONE;
+  c->cs_valid = false;
 }
 
 static ei_status alloc(void** p, size_t bytes) {
@@ -428,6 +436,192 @@ static void stats_reset(ei_stats* st) {
   if (st) memset(st, 0, sizeof(*st));
 }
 
+// ===========================================================================
+// Learned schedule: a network proposes (s, m); s substeps of exactly m Newton
+// steps run with one check of the a posteriori estimate per substep and a
+// single synchronisation; a failed check falls back to the plain method.
+// ===========================================================================
+
+// Coefficient statistics of the operator's inputs (computed once per operator).
+static ei_status coef_stats(ei_ctx* c, double* ratio, double* pe) {
+  if (!c->cs_valid) {
+    double r = 1.0, p = 0.0;
+    if (c->kind == KIND_STENCIL) {
+      const int dim = c->sd.dim;
+      bool arrays = c->Du != nullptr;
+      for (int e = 0; e < dim; ++e) arrays = arrays || c->bu[e] != nullptr;
+      if (!arrays) {
+        for (int e = 0; e < dim; ++e)
+          p = std::max(p, fabs(c->bcst[e]) * c->dx[e] / (2.0 * c->Dc));
+      } else {
+        const void* bptr[3] = {c->bu[0], c->bu[1], c->bu[2]};
+        EI_TRY_CUDA(launch_coef_stats(c->n, 0, c->prec, dim, c->Du, c->Dc, bptr, c->bcst, c->dx,
+                                      c->partials, c->ctl, c->stream));
+        EI_TRY(read_ctl(c));
+        r = c->h_ctl->cs_sum / ((double)c->n * c->h_ctl->cs_max);
+        p = c->h_ctl->cs_pe;
+      }
+    } else if (c->diag_u) {
+      const void* none[3] = {nullptr, nullptr, nullptr};
+      const double zero[3] = {0, 0, 0}, one[3] = {1, 1, 1};
+      EI_TRY_CUDA(launch_coef_stats(c->n, 1, c->prec, 1, c->diag_u, 0.0, none, zero, one,
+                                    c->partials, c->ctl, c->stream));
+      EI_TRY(read_ctl(c));
+      r = c->h_ctl->cs_max > 0 ? c->h_ctl->cs_sum / ((double)c->n * c->h_ctl->cs_max) : 1.0;
+    }
+    c->cs_ratio = isfinite(r) ? r : 1.0;
+    c->cs_pe = p;
+    c->cs_valid = true;
+  }
+  *ratio = c->cs_ratio;
+  *pe = c->cs_pe;
+  return EI_OK;
+}
+
+// The twelve features of a phi_1 call at substep count s (see ei.h).
+static void learned_features(double* f, double s, double h, double alpha, double beta,
+                             double tol, int kind, int dim, int64_t n, double ratio, double pe,
+                             double vnorm) {
+  const double cc = 0.5 * (alpha + beta), gamma = 0.25 * (beta - alpha);
+  const double tau = h / s;
+  const double rho = std::max(fabs(alpha), fabs(beta));
+  const double rms = vnorm / sqrt((double)n);
+  const double lr = rms > 0 ? std::min(30.0, std::max(-30.0, log10(rms))) : -30.0;
+  f[0] = log10(tau * gamma);
+  f[1] = std::max(-8.0, std::min(8.0, cc / gamma)) / 4.0;
+  f[2] = log10(tol) / 10.0;
+  f[3] = log2(s) / 10.0;
+  f[4] = log10(h * rho) / 3.0;
+  f[5] = 1.0;  // k
+  f[6] = kind == KIND_CSR ? 1.0 : 0.0;
+  f[7] = kind == KIND_STENCIL ? dim / 3.0 : 0.0;
+  f[8] = ratio;
+  f[9] = log10(1.0 + std::min(pe, 1e30));
+  f[10] = lr / 10.0;
+  f[11] = log10((double)n) / 8.0;
+}
+
+static ei_status fill_features(ei_ctx* c, ei_stats* st, int s, double h, double alpha,
+                               double beta, double tol) {
+  if (!st) return EI_OK;
+  double ratio, pe;
+  EI_TRY(coef_stats(c, &ratio, &pe));
+  learned_features(st->features, (double)s, h, alpha, beta, tol, c->kind, c->sd.dim, c->n, ratio,
+                   pe, sqrt(c->vnorm2));
+  return EI_OK;
+}
+
+// The smallest accepted q: output 1 >= z_min and the predicted degree with
+// its margins within m_max.
+static bool learned_decide(const float* o, int rows, const ei_mlp_decision& D, int m_max, int* s,
+                           int* m) {
+  const int qn = std::min(D.q_max, rows - 1);
+  for (int q = 0; q <= qn; ++q) {
+    const double o0 = o[EI_MLP_OUTPUTS * q], o1 = o[EI_MLP_OUTPUTS * q + 1];
+    const double need = m_max * o0 * (1.0 + D.rho_m) + D.delta_m;
+    if (o1 >= D.z_min && need <= m_max) {
+      *s = 1 << q;
+      *m = std::max(1, std::min(m_max, (int)ceil(need)));
+      return true;
+    }
+  }
+  return false;
+}
+
+// Exactly m Newton steps on r with no test in between: the kernels judge only
+// degree m and count a failed check into ctl->fixfail.  Launches only.  With
+// two-step launches an odd count starts with one single step, so the last
+// launch ends at degree m.  timed: record events around each launch.
+static ei_status newton_fixed(ei_ctx* c, Prepared& P, const void* qc, const void* r,
+                              const std::vector<double>& d, double cc, double gamma, double tol,
+                              int m, bool timed, int* n_launched) {
+  const double* xi = leja_table();
+  EI_TRY(reset_done(c));
+  NewtonScalars s{};
+  s.d0 = d[0];
+  s.inv_gamma = 1.0 / gamma;
+  s.tol = tol;
+  s.m_max = m;
+  s.fixed = 1;
+  const bool pair = (c->kind == KIND_STENCIL) && P.coef7 && c->fuse2;
+  if (timed)
+    while (c->ev.size() < (size_t)(2 * m + 2)) {
+      cudaEvent_t e;
+      EI_TRY_CUDA(cudaEventCreate(&e));
+      c->ev.push_back(e);
+    }
+  int j = 0, nl = 0;
+  while (j < m) {
+    const bool two = pair && ((m - j) % 2 == 0);
+    s.j = j;
+    s.d_next = d[j + 1];
+    s.shift = cc / gamma + xi[j];
+    if (two) {
+      s.d_next2 = d[j + 2];
+      s.shift2 = cc / gamma + xi[j + 1];
+    }
+    const void* w_in = (nl == 0) ? r : P.w[(nl - 1) & 1];
+    void* w_out = P.w[nl & 1];
+    if (timed) EI_TRY_CUDA(cudaEventRecord(c->ev[2 * nl], c->stream));
+    if (two) {
+      EI_TRY_CUDA(op_newton2(c, P, qc, w_in, w_out, s));
+    } else {
+      EI_TRY_CUDA(op_newton(c, P, qc, w_in, w_out, s));
+    }
+    if (timed) EI_TRY_CUDA(cudaEventRecord(c->ev[2 * nl + 1], c->stream));
+    ++nl;
+    j += two ? 2 : 1;
+  }
+  *n_launched = nl;
+  return EI_OK;
+}
+
+// h phi_1(hJ) v by s substeps of exactly m Newton steps, then one
+// synchronisation: *ok says every substep passed its check.
+static ei_status phi1_fixed(ei_ctx* c, Prepared& P, const void* qc, double h, double cc,
+                            double gamma, double tol, int s, int m, bool* ok,
+                            const void** result, int* result_is_p, double* result_scale) {
+  const double tau = h / s;
+  std::vector<double> d(m + 1);
+  divided_differences(1, tau, cc, gamma, m, d.data());
+  EI_TRY_CUDA(cudaMemsetAsync(&c->ctl->fixfail, 0, sizeof(int), c->stream));
+  if (s > 1) EI_LAUNCH(launch_zero(P.y, P.fmt, P.n_alloc, c->stream));
+  int timed_launches = 0;
+  for (int i = 0; i < s; ++i) {
+    const void* r = P.v;
+    if (i > 0) {
+      EI_TRY_CUDA(op_residual(c, P, qc, P.y, P.v, P.r));
+      r = P.r;
+    }
+    int nl = 0;
+    const bool timed = c->profile && i == 0;  // the first substep's launches
+    EI_TRY(newton_fixed(c, P, qc, r, d, cc, gamma, tol, m, timed, &nl));
+    if (timed) timed_launches = nl;
+    if (s > 1) EI_LAUNCH(launch_axpy(P.y, P.p, P.fmt, P.n_alloc, tau, c->stream));
+  }
+  EI_TRY(read_ctl(c));
+  *ok = c->h_ctl->fixfail == 0;
+  if (timed_launches) {
+    for (int i = 0; i < timed_launches; ++i) {
+      float ms = 0.f;
+      EI_TRY_CUDA(cudaEventElapsedTime(&ms, c->ev[2 * i], c->ev[2 * i + 1]));
+      c->newton_ms += ms;
+      ++c->newton_timed;
+    }
+    c->newton_fused = (c->kind == KIND_STENCIL && P.coef7 && c->fuse2) ? 2 : 1;
+  }
+  if (s == 1) {
+    *result = P.p;
+    *result_is_p = 1;
+    *result_scale = h;
+  } else {
+    *result = P.y;
+    *result_is_p = 0;
+    *result_scale = 1.0;
+  }
+  return EI_OK;
+}
+
 // Integrate y' = J y + v from 0 over h by s substeps: returns y_s in the
 // buffer *result (vector format if *result_is_p == 0, Newton-sum format if 1).
 // k = 1 only.  v: imported vector (P.v); qc: J's diagonal array.
@@ -437,6 +631,51 @@ static ei_status phi1_substeps(ei_ctx* c, Prepared& P, const void* qc, double h,
   double cc, gamma;
   interval(alpha, beta, &cc, &gamma);
   const int m_max = (opt && opt->m_max > 0 && opt->m_max <= 100) ? opt->m_max : 100;
+  const int learned = opt ? opt->learned : 0;
+  int wasted = 0;  // operator applications of a rejected learned proposal
+  if (learned == 1 && c->model && !(opt && opt->fixed_s > 0)) {
+    double ratio, pe;
+    EI_TRY(coef_stats(c, &ratio, &pe));
+    const ei_mlp_decision& D = mlp_decision(c->model);
+    const int rows = D.q_max + 1;
+    double feat[(EI_MLP_MAX_Q + 1) * EI_MLP_INPUTS];
+    for (int q = 0; q < rows; ++q)
+      learned_features(feat + EI_MLP_INPUTS * q, (double)(1 << q), h, alpha, beta, tol, c->kind,
+                       c->sd.dim, c->n, ratio, pe, sqrt(c->vnorm2));
+    float outs[(EI_MLP_MAX_Q + 1) * EI_MLP_OUTPUTS];
+    EI_TRY(mlp_infer_host(c->model, feat, rows, outs));
+    int s_l = 0, m_l = 0;
+    if (learned_decide(outs, rows, D, m_max, &s_l, &m_l)) {
+      bool ok = false;
+      EI_TRY(phi1_fixed(c, P, qc, h, cc, gamma, tol, s_l, m_l, &ok, result, result_is_p,
+                        result_scale));
+      int q_l = 0;
+      while ((1 << q_l) < s_l) ++q_l;
+      if (st) {
+        st->learned_s = s_l;
+        st->learned_m = m_l;
+        memcpy(st->features, feat + EI_MLP_INPUTS * q_l, sizeof(st->features));
+      }
+      if (ok) {
+        if (st) {
+          st->learned = 1;
+          st->s = s_l;
+          st->restarts = 0;
+          st->matvecs += s_l * m_l + (s_l - 1);
+          st->degree_sum = s_l * m_l;
+          st->degree_max = m_l;
+          for (int i = 0; i < s_l && i < EI_STATS_MAX_SUBSTEPS; ++i) st->degrees[i] = m_l;
+          st->alpha = alpha;
+          st->beta = beta;
+        }
+        return EI_OK;
+      }
+      if (st) st->learned = 2;
+      wasted = s_l * m_l + (s_l - 1);
+    } else if (st) {
+      st->learned = 3;
+    }
+  }
   int s = 1, m_pred = 0;
   std::vector<double> d(m_max + 1);
   bool have_d = false;  // the schedule hands back the divided differences of its s
@@ -472,15 +711,34 @@ static ei_status phi1_substeps(ei_ctx* c, Prepared& P, const void* qc, double h,
       if (deg > dmax) dmax = deg;
       if (s > 1) EI_LAUNCH(launch_axpy(P.y, P.p, P.fmt, P.n_alloc, tau, c->stream));
     }
-    if (ok_all) {
+    if (!ok_all && opt && opt->no_restart && opt->fixed_s > 0) {
       if (st) {
         st->s = s;
-        st->restarts = restarts;
-        st->matvecs += matvecs;
+        st->matvecs += matvecs + wasted;
         st->degree_sum = dsum;
         st->degree_max = dmax;
         st->alpha = alpha;
         st->beta = beta;
+        if (learned == 2) {
+          st->learned = 4;
+          EI_TRY(fill_features(c, st, s, h, alpha, beta, tol));
+        }
+      }
+      return EI_ERR_NOT_CONVERGED;
+    }
+    if (ok_all) {
+      if (st) {
+        st->s = s;
+        st->restarts = restarts;
+        st->matvecs += matvecs + wasted;
+        st->degree_sum = dsum;
+        st->degree_max = dmax;
+        st->alpha = alpha;
+        st->beta = beta;
+        if (learned == 2) {
+          st->learned = 4;
+          EI_TRY(fill_features(c, st, s, h, alpha, beta, tol));
+        }
       }
       if (s == 1) {  // y_1 = tau * p
         *result = P.p;
@@ -663,7 +921,7 @@ ei_status ei_set_operator_csr(ei_ctx* c, int64_t n, int64_t nnz, const int64_t* 
   if (nb < reduction_capacity()) nb = reduction_capacity();
   c->max_blocks = nb;
   ei_status st;
-  if ((st = alloc((void**)&c->partials, sizeof(double) * 2 * nb)) != EI_OK) { free_operator(c); return st; }
+  if ((st = alloc((void**)&c->partials, sizeof(double) * 4 * nb)) != EI_OK) { free_operator(c); return st; }
   if ((st = alloc((void**)&c->ger_lo, sizeof(double) * n)) != EI_OK) { free_operator(c); return st; }
   if ((st = alloc((void**)&c->ger_hi, sizeof(double) * n)) != EI_OK) { free_operator(c); return st; }
   cudaError_t e = launch_csr_gershgorin(c->cd, prec, val, diag, c->ger_lo, c->ger_hi, c->partials,
@@ -674,6 +932,12 @@ ei_status ei_set_operator_csr(ei_ctx* c, int64_t n, int64_t nnz, const int64_t* 
   c->alphaA = c->h_ctl->mn;
   c->betaA = c->h_ctl->mx;
   if (!isfinite(c->alphaA) || !isfinite(c->betaA)) { free_operator(c); return EI_ERR_NONFINITE; }
+  return EI_OK;
+}
+
+ei_status ei_set_schedule_model(ei_ctx* c, const ei_mlp* model) {
+  if (!c) return EI_ERR_INVALID_ARG;
+  c->model = model;
   return EI_OK;
 }
 
@@ -751,6 +1015,7 @@ static ei_status phi_apply_impl(ei_ctx* c, int k, double h, const void* v, void*
     const void* res = nullptr;
     int is_p = 0;
     double scale = 1.0;
+    c->vnorm2 = vnorm2;
     rc = phi1_substeps(c, P, base_diag(P), h, alpha, beta, tol, opt, st, &res, &is_p, &scale);
     if (rc == EI_OK) {
       EI_LAUNCH(launch_export(out, c->prec, res, fmt, is_p, n, geo_nx(c), c->kind == KIND_STENCIL ? c->sd.ny : 1, geo_pitch(c), scale / h, c->stream));
@@ -842,6 +1107,7 @@ static ei_status step_impl(ei_ctx* c, int method, double h, void* u, int nonlin,
   const void* res = nullptr;
   int is_p = 0;
   double scale = 1.0;
+  c->vnorm2 = fnorm2;
   EI_TRY(phi1_substeps(c, P, qc, h, alpha, beta, tol, opt, st, &res, &is_p, &scale));
   EI_LAUNCH(launch_add_export(u, c->prec, res, fmt, is_p, n, geo_nx(c), c->kind == KIND_STENCIL ? c->sd.ny : 1, geo_pitch(c), scale, c->stream));
   EI_TRY_CUDA(cudaStreamSynchronize(c->stream));

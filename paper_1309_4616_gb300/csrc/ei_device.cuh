@@ -53,6 +53,49 @@ __device__ __forceinline__ double to_p(double x) { return x; }
 
 __device__ __forceinline__ bool finite_d(double x) { return isfinite(x); }
 
+// Verdict after the Newton step reaching degree `deg`, with squared norms nw2
+// of w_deg and np2 of p_deg and coefficient d = d_deg.  Adaptive mode: stop
+// at the first degree whose estimate |d| ||w|| <= tol ||p|| holds (done = 1),
+// or at m_max (done = 2).  Fixed-count mode: only deg == m_max is judged, and
+// a failed check also counts into ctl->fixfail.  Non-finite norms stop with
+// done = 4 in both modes, and a bounded device wait that ran out (ctl->err)
+// with done = 5.  Returns true when the iteration stops at `deg`.  Called by
+// one thread after the grid-wide reduction.
+__device__ __forceinline__ bool newton_verdict(DevCtl* ctl, const NewtonScalars& s, int deg,
+                                               double d, double nw2, double np2) {
+  const bool last = deg >= s.m_max;
+  if (*(volatile int*)&ctl->err) {
+    ctl->done = 5;
+    ctl->degree = deg;
+    if (s.fixed) atomicAdd(&ctl->fixfail, 1);
+    return true;
+  }
+  if (!finite_d(nw2) || !finite_d(np2)) {
+    ctl->done = 4;
+    ctl->degree = deg;
+    if (s.fixed) atomicAdd(&ctl->fixfail, 1);
+    return true;
+  }
+  if (deg == 1 && s.j == 0 && np2 == 0.0 && nw2 == 0.0) {  // zero input: p = 0 at degree 0
+    ctl->done = 1;
+    ctl->degree = 0;
+    return true;
+  }
+  if (s.fixed && !last) return false;
+  if (fabs(d) * sqrt(nw2) <= s.tol * sqrt(np2)) {
+    ctl->done = 1;
+    ctl->degree = deg;
+    return true;
+  }
+  if (last) {
+    ctl->done = 2;
+    ctl->degree = deg;
+    if (s.fixed) atomicAdd(&ctl->fixfail, 1);
+    return true;
+  }
+  return false;
+}
+
 // loads / stores (read-only path for data the kernel does not write)
 __device__ __forceinline__ df ldg(const df* p, int64_t i) {
   float2 v = __ldg(reinterpret_cast<const float2*>(p) + i);

@@ -5,6 +5,8 @@
 #include <cuda_runtime.h>
 #include <stdint.h>
 
+#include "ei.h"
+
 namespace ei {
 
 // Vector element formats inside the library.
@@ -20,10 +22,13 @@ struct DevCtl {
   int err;             // set by a block whose bounded wait ran out
   int fixup;           // two-iteration kernel stopped at its first iteration: p holds
                        // p_{j+2}; subtract d_{j+2} w_{j+2} to get p_{j+1}
-  int pad2[3];
+  int fixfail;         // fixed-count mode: substeps whose final check failed (sticky
+                       // across substeps; reset by the host once per call)
+  int pad2[2];
   double sum0, sum1;   // import / F / residual: squared norm, finiteness flag (1 = finite)
   double mn, mx;       // Gershgorin reductions: min_i (a_ii - r_i), max_i (a_ii + r_i)
   double nw2, np2;     // squared norms of the last Newton iterate / sum
+  double cs_sum, cs_max, cs_pe;  // coefficient statistics (launch_coef_stats)
 };
 
 // Grid geometry of the stencil operator.  Library-owned arrays are stored
@@ -63,6 +68,8 @@ struct NewtonScalars {
   int m_max;
   double d_next2;      // two-iteration kernel: d_{j+2}
   double shift2;       // two-iteration kernel: c/gamma + xi_{j+1}
+  int fixed;           // 1: fixed-count mode, m_max steps exactly; only degree m_max
+                       //    is tested and a failure counts into ctl->fixfail
 };
 
 // Tensor maps of the TMA-staged Newton kernel (3D maps over the padded
@@ -103,6 +110,15 @@ cudaError_t launch_csr_gershgorin(const CsrDev& op, int prec, const void* val_us
 cudaError_t launch_shifted_minmax(int64_t n, const double* lo, const double* hi, const void* u,
                                   int prec, int nonlin, double* partials, DevCtl* ctl,
                                   cudaStream_t st);
+
+// Coefficient statistics of the caller's operator inputs, for the learned
+// schedule's features.  Stencil (csr = 0): over the n grid points, sum and max
+// of D and max over axes e < dim of |b_e| dx_e / (2 D) (arrays in `prec`, or
+// the constants where a pointer is NULL).  CSR (csr = 1): sum and max of
+// |diag|.  Into ctl->cs_sum, cs_max, cs_pe.
+cudaError_t launch_coef_stats(int64_t n, int csr, int prec, int dim, const void* D, double Dc,
+                              const void* const b[3], const double bcst[3], const double dx[3],
+                              double* partials, DevCtl* ctl, cudaStream_t st);
 
 // dst (vector format, padded by (nx, ny, pitch)) = scale * (src or cst)
 cudaError_t launch_fill_coef(void* dst, int fmt, int64_t n, int nx, int ny, int pitch,
@@ -157,6 +173,11 @@ cudaError_t launch_p_fixup(void* p, const void* w, int fmt, int64_t n_alloc, dou
 cudaError_t launch_csr_newton(const CsrDev& op, const void* w_in, void* w_out, void* p,
                               const NewtonScalars& s, int fmt, double* partials, DevCtl* ctl,
                               cudaStream_t st);
+
+// The schedule network (ei_mlp.cu): outputs (rows x EI_MLP_OUTPUTS, FP32
+// rounding) for host feature rows (FP64); synchronises the model's stream.
+ei_status mlp_infer_host(const ei_mlp* model, const double* features, int rows, float* out);
+const ei_mlp_decision& mlp_decision(const ei_mlp* model);
 
 // size in bytes of one vector element / of one Newton-sum element
 inline size_t vec_elem_bytes(int fmt) { return fmt == VF_F32 ? 4 : 8; }

@@ -329,19 +329,7 @@ k_csr_newton(CsrDev op, const void* __restrict__ w_in_, void* __restrict__ w_out
     if (threadIdx.x == 0) {
       ctl->nw2 = nw2;
       ctl->np2 = np2;
-      if (!finite_d(nw2) || !finite_d(np2)) {
-        ctl->done = 4;
-        ctl->degree = s.j + 1;
-      } else if (s.j == 0 && np2 == 0.0) {
-        ctl->done = 1;
-        ctl->degree = 0;
-      } else if (fabs(s.d_next) * sqrt(nw2) <= s.tol * sqrt(np2)) {
-        ctl->done = 1;
-        ctl->degree = s.j + 1;
-      } else if (s.j + 1 >= s.m_max) {
-        ctl->done = 2;
-        ctl->degree = s.j + 1;
-      }
+      newton_verdict(ctl, s, s.j + 1, s.d_next, nw2, np2);
     }
   }
 }
@@ -679,6 +667,69 @@ cudaError_t launch_csr_gershgorin(const CsrDev& op, int prec, const void* val_us
   else
     k_csr_gershgorin<float><<<nb, EI_TPB, 0, stm>>>(op.n, op.rowptr, op.col,
         static_cast<const float*>(val_user), static_cast<const float*>(diag_user), lo, hi, partials, ctl);
+  return cudaGetLastError();
+}
+
+// Coefficient statistics (see launch_coef_stats).  Per block: the sum in a
+// fixed order and the two maxima; the last block combines the blocks in
+// block order.
+template <class U>
+__global__ void __launch_bounds__(EI_TPB)
+    k_coef_stats(int64_t n, int csr, int dim, const void* D, double Dc, const void* b0,
+                 const void* b1, const void* b2, double bc0, double bc1, double bc2, double dx0,
+                 double dx1, double dx2, double* partials, DevCtl* ctl) {
+  double sum = 0.0, mx = 0.0, pe = 0.0;
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n;
+       i += (int64_t)gridDim.x * blockDim.x) {
+    double Di = uval<U>(D, Dc, i);
+    if (csr) Di = fabs(Di);
+    sum += Di;
+    mx = fmax(mx, Di);
+    if (!csr) {
+      pe = fmax(pe, fabs(uval<U>(b0, bc0, i)) * dx0 / (2.0 * Di));
+      if (dim > 1) pe = fmax(pe, fabs(uval<U>(b1, bc1, i)) * dx1 / (2.0 * Di));
+      if (dim > 2) pe = fmax(pe, fabs(uval<U>(b2, bc2, i)) * dx2 / (2.0 * Di));
+    }
+  }
+  double zero = 0.0, npe = -pe;
+  block_reduce2<RED_SUM>(sum, zero);
+  block_reduce2<RED_MINMAX>(npe, mx);
+  __shared__ bool am_last;
+  const unsigned nblk = gridDim.x;
+  if (threadIdx.x == 0) {
+    partials[4 * blockIdx.x] = sum;
+    partials[4 * blockIdx.x + 1] = mx;
+    partials[4 * blockIdx.x + 2] = -npe;
+    __threadfence();
+    am_last = (atomicAdd(&ctl->count, 1u) == nblk - 1);
+  }
+  __syncthreads();
+  if (!am_last || threadIdx.x != 0) return;
+  __threadfence();
+  double s = 0.0, m = 0.0, p = 0.0;
+  for (unsigned k = 0; k < nblk; ++k) {
+    s += __ldcg(partials + 4 * k);
+    m = fmax(m, __ldcg(partials + 4 * k + 1));
+    p = fmax(p, __ldcg(partials + 4 * k + 2));
+  }
+  ctl->cs_sum = s;
+  ctl->cs_max = m;
+  ctl->cs_pe = p;
+  ctl->count = 0;
+}
+
+cudaError_t launch_coef_stats(int64_t n, int csr, int prec, int dim, const void* D, double Dc,
+                              const void* const b[3], const double bcst[3], const double dx[3],
+                              double* partials, DevCtl* ctl, cudaStream_t stm) {
+  const int nb = ew_blocks(n);
+  if (prec == 0)
+    k_coef_stats<double><<<nb, EI_TPB, 0, stm>>>(n, csr, dim, D, Dc, b[0], b[1], b[2], bcst[0],
+                                                  bcst[1], bcst[2], dx[0], dx[1], dx[2],
+                                                  partials, ctl);
+  else
+    k_coef_stats<float><<<nb, EI_TPB, 0, stm>>>(n, csr, dim, D, Dc, b[0], b[1], b[2], bcst[0],
+                                                 bcst[1], bcst[2], dx[0], dx[1], dx[2],
+                                                 partials, ctl);
   return cudaGetLastError();
 }
 

@@ -274,22 +274,7 @@ k_newton_tma(const __grid_constant__ NewtonMaps M, const StencilDev g, const New
     if (tid == 0) {
       ctl->nw2 = nw2;
       ctl->np2 = np2;
-      if (*(volatile int*)&ctl->err) {
-        ctl->done = 5;
-        ctl->degree = s.j + 1;
-      } else if (!finite_d(nw2) || !finite_d(np2)) {
-        ctl->done = 4;
-        ctl->degree = s.j + 1;
-      } else if (s.j == 0 && np2 == 0.0) {  // zero input: p = 0 at degree 0
-        ctl->done = 1;
-        ctl->degree = 0;
-      } else if (fabs(s.d_next) * sqrt(nw2) <= s.tol * sqrt(np2)) {
-        ctl->done = 1;
-        ctl->degree = s.j + 1;
-      } else if (s.j + 1 >= s.m_max) {
-        ctl->done = 2;
-        ctl->degree = s.j + 1;
-      }
+      newton_verdict(ctl, s, s.j + 1, s.d_next, nw2, np2);
     }
   }
 }
@@ -543,30 +528,13 @@ k_newton2_tma(const __grid_constant__ NewtonMaps M, const StencilDev g, const Ne
       const double nw1 = acc4[0], np1 = acc4[1], nw2 = acc4[2], np2 = acc4[3];
       ctl->nw2 = nw2;
       ctl->np2 = np2;
-      const bool fin = finite_d(nw1) && finite_d(np1) && finite_d(nw2) && finite_d(np2);
-      if (*(volatile int*)&ctl->err) {
-        ctl->done = 5;
-        ctl->degree = s.j + 1;
-      } else if (!fin) {
-        ctl->done = 4;
-        ctl->degree = s.j + 1;
-      } else if (s.j == 0 && np1 == 0.0) {  // zero input: p = 0 at degree 0
-        ctl->done = 1;
-        ctl->degree = 0;
-      } else if (fabs(s.d_next) * sqrt(nw1) <= s.tol * sqrt(np1)) {
-        ctl->done = 1;
-        ctl->degree = s.j + 1;
-        ctl->fixup = 1;
-      } else if (s.j + 1 >= s.m_max) {
-        ctl->done = 2;
-        ctl->degree = s.j + 1;
-        ctl->fixup = 1;
-      } else if (fabs(s.d_next2) * sqrt(nw2) <= s.tol * sqrt(np2)) {
-        ctl->done = 1;
-        ctl->degree = s.j + 2;
-      } else if (s.j + 2 >= s.m_max) {
-        ctl->done = 2;
-        ctl->degree = s.j + 2;
+      if (!finite_d(nw2) || !finite_d(np2)) {
+        newton_verdict(ctl, s, s.j + 1, s.d_next, nw2, np2);  // stops: non-finite
+      } else if (newton_verdict(ctl, s, s.j + 1, s.d_next, nw1, np1)) {
+        // stopped at j+1 (not at degree 0): p holds p_{j+2}; the host fixes it
+        if (ctl->done <= 2 && ctl->degree == s.j + 1) ctl->fixup = 1;
+      } else {
+        newton_verdict(ctl, s, s.j + 2, s.d_next2, nw2, np2);
       }
     }
   }

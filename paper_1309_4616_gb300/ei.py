@@ -20,6 +20,7 @@ ARITH_DF, ARITH_NATIVE_F64 = 0, 1
 EXP_EULER, EXP_ROSENBROCK = 0, 1
 NONLIN_NONE, NONLIN_LOGISTIC = 0, 1
 STATS_MAX_SUBSTEPS = 64
+MLP_INPUTS, MLP_OUTPUTS, MLP_PARAMS, MLP_MAX_Q = 12, 2, 9282, 12
 
 # every symbol include/ei.h declares
 EXPORTS = [
@@ -28,13 +29,16 @@ EXPORTS = [
     "ei_step_host", "ei_leja_points", "ei_divided_differences", "ei_schedule",
     "ei_status_string", "ei_estimate_spectrum_stencil_noalloc",
     "ei_batch_create", "ei_batch_offsets", "ei_batch_phi1", "ei_batch_destroy",
+    "ei_mlp_create", "ei_mlp_destroy", "ei_mlp_set_params", "ei_mlp_get_params",
+    "ei_mlp_set_decision", "ei_mlp_get_decision", "ei_mlp_forward", "ei_mlp_loss_grad",
+    "ei_mlp_train_step", "ei_set_schedule_model",
 ]
 
 
 class Options(C.Structure):
     _fields_ = [("m_max", C.c_int), ("arith", C.c_int), ("fixed_s", C.c_int),
                 ("profile", C.c_int), ("single_iter", C.c_int), ("tile_rows", C.c_int),
-                ("reserved", C.c_int * 2)]
+                ("learned", C.c_int), ("no_restart", C.c_int)]
 
 
 class Stats(C.Structure):
@@ -43,7 +47,9 @@ class Stats(C.Structure):
                 ("degree_max", C.c_int), ("m_sched", C.c_int),
                 ("degrees", C.c_int * STATS_MAX_SUBSTEPS), ("launches", C.c_int),
                 ("newton_timed", C.c_int), ("newton_fused", C.c_int),
-                ("newton_ms", C.c_double)]
+                ("newton_ms", C.c_double), ("learned", C.c_int), ("learned_s", C.c_int),
+                ("learned_m", C.c_int), ("learned_pad", C.c_int),
+                ("features", C.c_double * MLP_INPUTS)]
 
     def degree_list(self):
         return [int(self.degrees[i]) for i in range(min(self.s, STATS_MAX_SUBSTEPS))]
@@ -54,7 +60,16 @@ class Stats(C.Structure):
                 "degree_max": self.degree_max, "m_sched": self.m_sched,
                 "degrees": self.degree_list(), "launches": self.launches,
                 "newton_timed": self.newton_timed, "newton_fused": self.newton_fused,
-                "newton_ms": self.newton_ms}
+                "newton_ms": self.newton_ms, "learned": self.learned,
+                "learned_s": self.learned_s, "learned_m": self.learned_m}
+
+    def feature_list(self):
+        return [float(self.features[i]) for i in range(MLP_INPUTS)]
+
+
+class MlpDecision(C.Structure):
+    _fields_ = [("z_min", C.c_double), ("rho_m", C.c_double), ("delta_m", C.c_double),
+                ("q_max", C.c_int), ("pad", C.c_int)]
 
 
 class BatchProblem(C.Structure):
@@ -110,11 +125,26 @@ def lib():
         L.ei_batch_phi1.argtypes = [vp, vp, vp, vp, C.POINTER(BatchStats)]
         L.ei_batch_destroy.argtypes = [vp]
         L.ei_batch_destroy.restype = None
+        fp = C.POINTER(C.c_float)
+        L.ei_mlp_create.argtypes = [C.POINTER(C.c_void_p), C.c_int, vp]
+        L.ei_mlp_destroy.argtypes = [vp]
+        L.ei_mlp_destroy.restype = None
+        L.ei_mlp_set_params.argtypes = [vp, fp]
+        L.ei_mlp_get_params.argtypes = [vp, fp]
+        L.ei_mlp_set_decision.argtypes = [vp, C.POINTER(MlpDecision)]
+        L.ei_mlp_get_decision.argtypes = [vp, C.POINTER(MlpDecision)]
+        L.ei_mlp_forward.argtypes = [vp, vp, C.c_int64, vp]
+        L.ei_mlp_loss_grad.argtypes = [vp, vp, vp, vp, C.c_int64, C.c_double, C.c_double, dp,
+                                       vp]
+        L.ei_mlp_train_step.argtypes = [vp, vp, vp, vp, C.c_int64, C.c_double, C.c_double,
+                                        C.c_double, dp]
+        L.ei_set_schedule_model.argtypes = [vp, vp]
         L.ei_status_string.argtypes = [C.c_int]
         L.ei_status_string.restype = C.c_char_p
         for name in EXPORTS:
             f = getattr(L, name)
-            if name not in ("ei_destroy", "ei_status_string", "ei_batch_destroy"):
+            if name not in ("ei_destroy", "ei_status_string", "ei_batch_destroy",
+                            "ei_mlp_destroy"):
                 f.restype = C.c_int
         _LIB = L
     return _LIB
@@ -274,6 +304,12 @@ class Context:
                              self._opts(options), C.byref(st)), "ei_step")
         return st
 
+    def set_schedule_model(self, model):
+        """Use `model` (an Mlp, or None) for calls with options learned = 1."""
+        self._model = model
+        _check(lib().ei_set_schedule_model(self._h, model._h if model is not None else None),
+               "ei_set_schedule_model")
+
     def step_host(self, method, h, u_host, nonlin, tol, options=None):
         """u_host: a CPU tensor (pinned for asynchronous copies)."""
         dt = self._dtype(self.prec)
@@ -330,6 +366,84 @@ class Batch:
     def close(self):
         if getattr(self, "_h", None):
             lib().ei_batch_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+class Mlp:
+    """The schedule network (ei_mlp_*): parameters and Adam state on the device."""
+
+    def __init__(self, device=0, stream=None):
+        import torch
+        if stream is None:
+            stream = torch.cuda.current_stream(device)
+        self.stream = stream
+        h = C.c_void_p()
+        _check(lib().ei_mlp_create(C.byref(h), device, C.c_void_p(stream.cuda_stream)),
+               "ei_mlp_create")
+        self._h = h
+
+    def set_params(self, theta):
+        import numpy as np
+        t = np.ascontiguousarray(theta, dtype=np.float32)
+        if t.size != MLP_PARAMS:
+            raise ValueError(f"expected {MLP_PARAMS} parameters, got {t.size}")
+        _check(lib().ei_mlp_set_params(self._h, t.ctypes.data_as(C.POINTER(C.c_float))),
+               "ei_mlp_set_params")
+
+    def get_params(self):
+        import numpy as np
+        t = np.zeros(MLP_PARAMS, dtype=np.float32)
+        _check(lib().ei_mlp_get_params(self._h, t.ctypes.data_as(C.POINTER(C.c_float))),
+               "ei_mlp_get_params")
+        return t
+
+    def set_decision(self, z_min=0.0, rho_m=0.05, delta_m=2.0, q_max=MLP_MAX_Q):
+        d = MlpDecision(z_min=z_min, rho_m=rho_m, delta_m=delta_m, q_max=q_max)
+        _check(lib().ei_mlp_set_decision(self._h, C.byref(d)), "ei_mlp_set_decision")
+
+    def get_decision(self):
+        d = MlpDecision()
+        _check(lib().ei_mlp_get_decision(self._h, C.byref(d)), "ei_mlp_get_decision")
+        return {"z_min": d.z_min, "rho_m": d.rho_m, "delta_m": d.delta_m, "q_max": d.q_max}
+
+    def forward(self, x, out):
+        import torch
+        rows = x.shape[0]
+        _check(lib().ei_mlp_forward(self._h, _dev_ptr(x, torch.float32, rows * MLP_INPUTS, "x"),
+                                    rows, _dev_ptr(out, torch.float32, rows * MLP_OUTPUTS,
+                                                   "out")), "ei_mlp_forward")
+
+    def loss_grad(self, x, y, mask, grad, lam=0.1, kappa=4.0):
+        import torch
+        rows = x.shape[0]
+        loss = C.c_double()
+        _check(lib().ei_mlp_loss_grad(
+            self._h, _dev_ptr(x, torch.float32, rows * MLP_INPUTS, "x"),
+            _dev_ptr(y, torch.float32, rows * MLP_OUTPUTS, "y"),
+            _dev_ptr(mask, torch.float32, rows, "mask"), rows, lam, kappa, C.byref(loss),
+            _dev_ptr(grad, torch.float32, MLP_PARAMS, "grad")), "ei_mlp_loss_grad")
+        return loss.value
+
+    def train_step(self, x, y, mask, lr, lam=0.1, kappa=4.0, want_loss=True):
+        import torch
+        rows = x.shape[0]
+        loss = C.c_double()
+        _check(lib().ei_mlp_train_step(
+            self._h, _dev_ptr(x, torch.float32, rows * MLP_INPUTS, "x"),
+            _dev_ptr(y, torch.float32, rows * MLP_OUTPUTS, "y"),
+            _dev_ptr(mask, torch.float32, rows, "mask"), rows, lam, kappa, lr,
+            C.byref(loss) if want_loss else None), "ei_mlp_train_step")
+        return loss.value if want_loss else None
+
+    def close(self):
+        if getattr(self, "_h", None):
+            lib().ei_mlp_destroy(self._h)
             self._h = None
 
     def __del__(self):
