@@ -235,11 +235,12 @@ ei_status ei_schedule(int k, double h, double c, double gamma, double tol, int m
  * linear outputs, FP32, parameters one flat vector (per layer W, out x in,
  * row major, then b).  For candidate q = 0..q_max (s = 2^q) output 0 is the
  * degree the estimate will need as a fraction of m_max and output 1 the logit
- * of meeting it within m_max.  The call takes the smallest q with
- * o1 >= z_min and need = m_max o0 (1 + rho_m) + delta_m <= m_max, runs
- * m = clamp(ceil(need), 1, m_max) Newton steps in each of the s substeps with
- * no test in between, then checks |d_m| ||w_m|| <= tol ||p_m|| once per
- * substep.  Any failed check, or no accepted q, redoes the call by the plain
+ * of meeting it within m_max.  A candidate q is accepted when o1 >= z_min and
+ * need = m_max o0 (1 + rho_m) + delta_m <= m_max, with
+ * m_q = clamp(ceil(need), 1, m_max); the call takes the accepted q with the
+ * fewest operator applications 2^q (m_q + 1) - 1 (ties: the smaller q), runs
+ * m_q Newton steps in each of the s = 2^q substeps with no test in between,
+ * then checks |d_m| ||w_m|| <= tol ||p_m|| once per substep.  Any failed check, or no accepted q, redoes the call by the plain
  * method.
  * Features of a call with interval [alpha, beta], c = (alpha+beta)/2,
  * gamma = (beta-alpha)/4, tau = h/s, rho = max(|alpha|, |beta|):

@@ -7,7 +7,7 @@ on the spectral interval (Sec. III-C) and ends each substep's Newton
 iteration by the a posteriori estimate |d_{j+1}| ||w_{j+1}|| <= tol ||p||.
 The learned schedule asks a small network instead, for each candidate
 s = 2^q (q = 0..Q), for the degree the estimate will need and whether it
-will be met within m_max.  It takes the smallest q the network accepts,
+will be met within m_max.  It takes the cheapest q the network accepts,
 runs exactly m Newton steps in every substep with no test in between, and
 applies the estimate once at the end of each substep.  If any substep fails
 that check, or the network accepts no q, the call is redone by the plain
@@ -30,9 +30,11 @@ max over points and axes of |b_e(x)| dx_e / (2 D(x)); a CSR operator's
 ratio is mean|diag|/max|diag| and its Peclet number is 0.
 
 Decision, from the network outputs o_q = (o_q0, o_q1): the predicted degree
-is mhat_q = m_max * o_q0 and q is accepted when o_q1 >= z_min and
-mhat_q (1 + rho_m) + delta_m <= m_max; then s = 2^q and
-m = clamp(ceil(mhat_q (1 + rho_m) + delta_m), 1, m_max).
+is mhat_q = m_max * o_q0, need_q = mhat_q (1 + rho_m) + delta_m, and q is
+accepted when o_q1 >= z_min and need_q <= m_max, with
+m_q = clamp(ceil(need_q), 1, m_max).  Of the accepted q the one with the
+fewest operator applications 2^q (m_q + 1) - 1 is taken (ties: the smaller
+q); then s = 2^q and m = m_q.
 """
 from __future__ import annotations
 
@@ -108,13 +110,16 @@ def feature_table(h, alpha, beta, tol, k, kind, dim, n, ratio, peclet, v_norm, q
 
 def decide(outputs, meta: Meta):
     """(s, m) from the network outputs for q = 0..q_max, or None."""
+    best = None
     for q in range(min(meta.q_max, len(outputs) - 1) + 1):
         o0, o1 = float(outputs[q][0]), float(outputs[q][1])
         need = meta.m_max * o0 * (1.0 + meta.rho_m) + meta.delta_m
         if o1 >= meta.z_min and need <= meta.m_max:
-            m = int(math.ceil(need))
-            return 1 << q, max(1, min(meta.m_max, m))
-    return None
+            m = max(1, min(meta.m_max, int(math.ceil(need))))
+            cost = (1 << q) * (m + 1) - 1
+            if best is None or cost < best[0]:
+                best = (cost, 1 << q, m)
+    return None if best is None else (best[1], best[2])
 
 
 @dataclass

@@ -158,6 +158,8 @@ static void free_prepared(Prepared& p) {
     *a = nullptr;
   }
   p.ready = false;
+  p.coef7 = false;  // a later operator of another kind must not inherit the layout
+  p.n_alloc = 0;
 }
 
 static void free_operator(ei_ctx* c) {
@@ -251,6 +253,7 @@ static ei_status prepare(ei_ctx* c, int fmt) {
     ok = ok && encode_map(&P.map_p, P.p, 8, c->sd, 0);
     if (!ok) { free_prepared(P); return EI_ERR_CUDA; }
   } else {
+    P.coef7 = false;
     if ((s = alloc(&P.csr_val, vec_elem_bytes(fmt) * (size_t)c->nnz)) != EI_OK) { free_prepared(P); return s; }
     EI_LAUNCH(launch_fill_coef(P.csr_val, fmt, c->nnz, (int)c->nnz, 1, (int)c->nnz, c->val_u,
                                c->prec, 0.0, 1.0, c->stream));
@@ -511,21 +514,29 @@ static ei_status fill_features(ei_ctx* c, ei_stats* st, int s, double h, double 
   return EI_OK;
 }
 
-// The smallest accepted q: output 1 >= z_min and the predicted degree with
-// its margins within m_max.
+// Of the accepted q (output 1 >= z_min, the predicted degree with its
+// margins within m_max) the one with the fewest operator applications
+// 2^q (m_q + 1) - 1; ties go to the smaller q.
 static bool learned_decide(const float* o, int rows, const ei_mlp_decision& D, int m_max, int* s,
                            int* m) {
   const int qn = std::min(D.q_max, rows - 1);
+  bool found = false;
+  double best = 0.0;
   for (int q = 0; q <= qn; ++q) {
     const double o0 = o[EI_MLP_OUTPUTS * q], o1 = o[EI_MLP_OUTPUTS * q + 1];
     const double need = m_max * o0 * (1.0 + D.rho_m) + D.delta_m;
     if (o1 >= D.z_min && need <= m_max) {
-      *s = 1 << q;
-      *m = std::max(1, std::min(m_max, (int)ceil(need)));
-      return true;
+      const int mq = std::max(1, std::min(m_max, (int)ceil(need)));
+      const double cost = ldexp((double)(mq + 1), q) - 1.0;
+      if (!found || cost < best) {
+        found = true;
+        best = cost;
+        *s = 1 << q;
+        *m = mq;
+      }
     }
   }
-  return false;
+  return found;
 }
 
 // Exactly m Newton steps on r with no test in between: the kernels judge only

@@ -289,19 +289,27 @@ class Context:
         # before set_operator the library itself reports EI_ERR_STATE
         return self.n if self.n > 0 else None
 
-    def phi_apply(self, k, h, v, out, tol, options=None):
+    def phi_apply(self, k, h, v, out, tol, options=None, check=True):
+        """Stats of the call; with check=False returns (status, stats) instead
+        of raising on an error status."""
         dt = self._dtype(self.prec)
         st = Stats()
-        _check(lib().ei_phi_apply(self._h, k, h, _dev_ptr(v, dt, self._n(), "v"),
-                                  _dev_ptr(out, dt, self._n(), "out"), tol, self._opts(options),
-                                  C.byref(st)), "ei_phi_apply")
+        rc = lib().ei_phi_apply(self._h, k, h, _dev_ptr(v, dt, self._n(), "v"),
+                                _dev_ptr(out, dt, self._n(), "out"), tol, self._opts(options),
+                                C.byref(st))
+        if not check:
+            return rc, st
+        _check(rc, "ei_phi_apply")
         return st
 
-    def step(self, method, h, u, nonlin, tol, options=None):
+    def step(self, method, h, u, nonlin, tol, options=None, check=True):
         dt = self._dtype(self.prec)
         st = Stats()
-        _check(lib().ei_step(self._h, method, h, _dev_ptr(u, dt, self._n(), "u"), nonlin, tol,
-                             self._opts(options), C.byref(st)), "ei_step")
+        rc = lib().ei_step(self._h, method, h, _dev_ptr(u, dt, self._n(), "u"), nonlin, tol,
+                           self._opts(options), C.byref(st))
+        if not check:
+            return rc, st
+        _check(rc, "ei_step")
         return st
 
     def set_schedule_model(self, model):

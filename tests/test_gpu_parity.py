@@ -305,3 +305,46 @@ def test_step_host_equals_step(env, xi):
     uh = torch.from_numpy(u0.copy()).pin_memory()
     ctx.step_host(ei.EXP_ROSENBROCK, 1e-4, uh, ei.NONLIN_LOGISTIC, 1e-10)
     assert torch.equal(uh, ud.cpu())
+
+
+def test_context_reuse_across_operator_kinds(env, xi):
+    """One context takes a 3D stencil, a CSR graph, then a constant-coefficient
+    2D stencil that needs several substeps; every call matches the oracle
+    (nothing of one operator's layout carries over to the next)."""
+    torch, ei = env
+    ctx = ei.Context()
+    w = W.adr_3d(n=18, h=2e-3)
+    op = O.StencilOperator(w.n, w.dx, w.D, w.b, bc=w.bc)
+    ref, ost = Nw.exp_rosenbrock_step(op, w.u0, w.h, w.tol, xi=xi)
+    ctx.set_operator_stencil(w.n, w.dx, dev(torch, w.D), [dev(torch, x) for x in w.b], 0.0,
+                             list(w.bc), ei.PREC_F64)
+    u = dev(torch, w.u0)
+    st = ctx.step(ei.EXP_ROSENBROCK, w.h, u, ei.NONLIN_LOGISTIC, w.tol)
+    assert rel_err(u.cpu().numpy() - w.u0, ref - w.u0) <= FP64_TOL
+    _check_stats(st, ost)
+
+    g = W.rgg_graph(n=3000, seed=8)
+    gop = O.CsrOperator(g.n, g.rowptr, g.col, g.val, -g.deg_w)
+    h = 30.0 / (2.0 * g.deg_w.max())
+    v0 = W.random_vector(g.n, 2)
+    ref, ost = Nw.phi_apply(gop, 1, h, v0, 1e-10, xi=xi)
+    ctx.set_operator_csr(g.n, dev(torch, g.rowptr), dev(torch, g.col), dev(torch, g.val),
+                         dev(torch, -g.deg_w))
+    v = dev(torch, v0)
+    out = torch.empty_like(v)
+    st = ctx.phi_apply(1, h, v, out, 1e-10)
+    assert rel_err(out.cpu().numpy(), ref) <= FP64_TOL
+    _check_stats(st, ost)
+
+    n, dx = (48, 48), (1 / 49, 1 / 49)
+    sop = O.StencilOperator(n, dx, 0.2, (0.4, 0.9), bc=(0, 0, 0, 0))
+    v0 = np.random.default_rng(4).standard_normal((48, 48))
+    ref, ost = Nw.phi_apply(sop, 1, 0.25, v0, 1e-8, xi=xi)
+    assert ost.s > 1
+    ctx.set_operator_stencil(n, dx, 0.2, [0.4, 0.9], 0.0, [0, 0, 0, 0], ei.PREC_F64)
+    v = dev(torch, v0)
+    out = torch.empty_like(v)
+    st = ctx.phi_apply(1, 0.25, v, out, 1e-8)
+    assert rel_err(out.cpu().numpy(), ref) <= FP64_TOL
+    _check_stats(st, ost)
+    ctx.close()

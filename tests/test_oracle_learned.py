@@ -87,9 +87,16 @@ def test_no_restart_driver_agrees_with_plain(xi):
 
 def test_decision_rule_truth_table():
     meta = Lr.Meta(z_min=0.0, rho_m=0.05, delta_m=2.0, m_max=100, q_max=3)
-    # q=0 rejected by the classifier, q=1 by the degree, q=2 accepted
+    # q=0 rejected by the classifier, q=1 by the degree; q=2 (m 44, cost
+    # 4*45-1 = 179) and q=3 (m 13, cost 8*14-1 = 111) accepted: q=3 is cheaper
     outs = [(0.2, -1.0), (0.97, 3.0), (0.40, 0.5), (0.1, 5.0)]
-    assert Lr.decide(outs, meta) == (4, math.ceil(100 * 0.40 * 1.05 + 2.0))
+    assert Lr.decide(outs, meta) == (8, 13)
+    # with q=3 at m 30 (cost 247) q=2 is the cheaper
+    outs[3] = (0.27, 5.0)
+    assert Lr.decide(outs, meta) == (4, 44)
+    # equal cost: the smaller q (q=0: m 19, cost 19; q=1: m 9, cost 19)
+    tie = [((19 - 2) / 105, 1.0), ((9 - 2) / 105, 1.0)]
+    assert Lr.decide(tie, Lr.Meta(rho_m=0.05, delta_m=2.0, q_max=1)) == (1, 19)
     assert Lr.decide([(0.1, -0.1)] * 4, meta) is None
     # the degree is clamped to [1, m_max]
     assert Lr.decide([(-0.5, 1.0)], meta) == (1, 1)
