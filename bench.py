@@ -52,7 +52,8 @@ def parse():
     # batch workloads: fixed tile height instead of the autotuner (profiling)
     ap.add_argument("--tile-rows", type=int, default=0, help=argparse.SUPPRESS)
     ap.add_argument("--workload", default="adr3d",
-                    choices=["adr3d", "adr3d_fp32", "rgg_csr", "batch", "batch_fp32"],
+                    choices=["adr3d", "adr3d_fp32", "rgg_csr", "batch", "batch_fp32",
+                             "adr3d_learned", "adr3d_fp32_learned", "rgg_csr_learned"],
                     help="adr3d (default, the headline): 256^3 FP64 Rosenbrock-Euler; "
                          "adr3d_fp32: 512^3 FP32 exponential Euler; rgg_csr: 2^20-node CSR phi_1")
     ap.add_argument("--no-cpu", action="store_true", help="skip the CPU baseline sample")
@@ -234,9 +235,9 @@ class Adr3d(Workload):
         return ctx.step(self.ei.EXP_ROSENBROCK, self.w.h, self.state, self.ei.NONLIN_LOGISTIC,
                         self.w.tol, opts)
 
-    def step_host(self, ctx, host):
+    def step_host(self, ctx, host, opts=None):
         return ctx.step_host(self.ei.EXP_ROSENBROCK, self.w.h, host, self.ei.NONLIN_LOGISTIC,
-                             self.w.tol)
+                             self.w.tol, opts)
 
     def kernel(self, fused):
         return ("k_newton2_tma<float-float> (two Newton iterations per launch)"
@@ -269,9 +270,9 @@ class Adr3dFp32(Adr3d):
         return ctx.step(self.ei.EXP_EULER, self.w.h, self.state, self.ei.NONLIN_LOGISTIC,
                         self.w.tol, opts)
 
-    def step_host(self, ctx, host):
+    def step_host(self, ctx, host, opts=None):
         return ctx.step_host(self.ei.EXP_EULER, self.w.h, host, self.ei.NONLIN_LOGISTIC,
-                             self.w.tol)
+                             self.w.tol, opts)
 
     def kernel(self, fused):
         return "k_newton_tma<float, flux form>"
@@ -306,10 +307,9 @@ class RggCsr(Workload):
     def step(self, ctx, opts=None):
         return ctx.phi_apply(1, self.h, self.state, self.out, self.tol, opts)
 
-    def step_host(self, ctx, host):
-        import torch
+    def step_host(self, ctx, host, opts=None):
         d = host.to(self.state.device, non_blocking=True)
-        st = ctx.phi_apply(1, self.h, d, self.out, self.tol)
+        st = ctx.phi_apply(1, self.h, d, self.out, self.tol, opts)
         host.copy_(self.out, non_blocking=False)
         return st
 
@@ -387,10 +387,56 @@ class BatchStepStats:
         return [int(s.degree_sum) for s in self._st[:3]]
 
 
+class Learned:
+    """The same workload with phi_1 under the learned schedule: the committed
+    network (paper_1309_4616_gb300/schedule_mlp.npz) proposes s and m, the a
+    posteriori estimate accepts or rejects, the plain method is the fallback."""
+
+    def setup_learned(self, ctx):
+        from paper_1309_4616_gb300 import learned
+        self.model = learned.load()
+        ctx.set_schedule_model(self.model)
+        self.name += "_learned"
+        self.method += " (learned schedule)"
+        self.config["schedule"] = "learned (network proposal, a posteriori check)"
+
+    @staticmethod
+    def _opts(opts):
+        o = {"learned": 1}
+        o.update(opts or {})
+        return o
+
+    def step(self, ctx, opts=None):
+        return super().step(ctx, self._opts(opts))
+
+    def step_host(self, ctx, host, opts=None):
+        return super().step_host(ctx, host, self._opts(opts))
+
+
+class Adr3dLearned(Learned, Adr3d):
+    def __init__(self, torch, ei, W, dev, ctx, n):
+        Adr3d.__init__(self, torch, ei, W, dev, ctx, n)
+        self.setup_learned(ctx)
+
+
+class Adr3dFp32Learned(Learned, Adr3dFp32):
+    def __init__(self, torch, ei, W, dev, ctx, n):
+        Adr3dFp32.__init__(self, torch, ei, W, dev, ctx, n)
+        self.setup_learned(ctx)
+
+
+class RggCsrLearned(Learned, RggCsr):
+    def __init__(self, torch, ei, W, dev, ctx, n):
+        RggCsr.__init__(self, torch, ei, W, dev, ctx, n)
+        self.setup_learned(ctx)
+
+
 WORKLOADS = {"adr3d": Adr3d, "adr3d_fp32": Adr3dFp32, "rgg_csr": RggCsr, "batch": Batch2d,
-             "batch_fp32": Batch2dFp32}
+             "batch_fp32": Batch2dFp32, "adr3d_learned": Adr3dLearned,
+             "adr3d_fp32_learned": Adr3dFp32Learned, "rgg_csr_learned": RggCsrLearned}
 DEFAULT_N = {"adr3d": N_SIDE, "adr3d_fp32": 512, "rgg_csr": 1 << 20, "batch": 1024,
-             "batch_fp32": 1024}
+             "batch_fp32": 1024, "adr3d_learned": N_SIDE, "adr3d_fp32_learned": 512,
+             "rgg_csr_learned": 1 << 20}
 
 
 def run_ours(args):
@@ -435,6 +481,7 @@ def run_ours(args):
     launches = 0
     matvecs = []
     degrees = []
+    learned_flags = []
     torch.cuda.synchronize(dev)
     e0.record(stream)
     for _ in range(args.steps):
@@ -442,6 +489,7 @@ def run_ours(args):
         launches += st.launches
         matvecs.append(st.matvecs)
         degrees.append(st.degree_list())
+        learned_flags.append(int(getattr(st, "learned", 0)))
     e1.record(stream)
     torch.cuda.synchronize(dev)
     clocks = sampler.stop()
@@ -504,6 +552,8 @@ def run_ours(args):
                   "l2": "inputs larger than L2 (each vector >= 8 MB and the step's working "
                         "set >= 0.3 GB; 256^3: 134 MB per vector)",
                   "matvecs_per_step": matvecs, "degrees": degrees[:3]}
+        if any(learned_flags):
+            config["learned_accepted_steps"] = sum(1 for f in learned_flags if f == 1)
         line = {
             "metric": METRIC, "value": value, "unit": "steps/s", "n_gpus": world,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms / args.steps,

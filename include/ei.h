@@ -86,8 +86,12 @@ typedef struct {
   int tile_rows;   /* batched form: tile height in units of 8 rows (1 to 32);
                       0 = the autotuner's choice */
   int learned;     /* phi_1 schedule: 0 the plain a-priori rule; 1 the learned
-                      schedule of the model set by ei_set_schedule_model (plain
-                      fallback); 2 the plain rule, reporting stats.features */
+                      schedule of the model set by ei_set_schedule_model, adaptive
+                      (the proposal's s, the per-substep a posteriori stop; m sets
+                      the launches issued before the first look); 3 the learned
+                      schedule with a fixed count of m steps per substep; both fall
+                      back to the plain rule; 2 the plain rule, reporting
+                      stats.features */
   int no_restart;  /* with fixed_s: an attempt that reaches m_max returns
                       EI_ERR_NOT_CONVERGED instead of doubling s (stats keep the
                       degrees reached; u and out are left unmodified) */
@@ -239,9 +243,13 @@ ei_status ei_schedule(int k, double h, double c, double gamma, double tol, int m
  * need = m_max o0 (1 + rho_m) + delta_m <= m_max, with
  * m_q = clamp(ceil(need), 1, m_max); the call takes the accepted q with the
  * fewest operator applications 2^q (m_q + 1) - 1 (ties: the smaller q), runs
- * m_q Newton steps in each of the s = 2^q substeps with no test in between,
- * then checks |d_m| ||w_m|| <= tol ||p_m|| once per substep.  Any failed check, or no accepted q, redoes the call by the plain
- * method.
+ * s = 2^q substeps.  Adaptive mode (ei_options.learned = 1) ends every
+ * substep at the first degree whose estimate |d_j| ||w_j|| <= tol ||p_j||
+ * passes, as the plain method does, after issuing m_q steps before the first
+ * look; a substep reaching m_max sends the call to the plain method.  Fixed
+ * count (learned = 3) runs exactly m_q Newton steps in each substep with no
+ * test in between and checks the estimate once per substep.  Any failed
+ * check, or no accepted q, redoes the call by the plain method.
  * Features of a call with interval [alpha, beta], c = (alpha+beta)/2,
  * gamma = (beta-alpha)/4, tau = h/s, rho = max(|alpha|, |beta|):
  *   0 log10(tau gamma)        1 clip(c/gamma, -8, 8)/4   2 log10(tol)/10

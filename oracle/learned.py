@@ -7,11 +7,20 @@ on the spectral interval (Sec. III-C) and ends each substep's Newton
 iteration by the a posteriori estimate |d_{j+1}| ||w_{j+1}|| <= tol ||p||.
 The learned schedule asks a small network instead, for each candidate
 s = 2^q (q = 0..Q), for the degree the estimate will need and whether it
-will be met within m_max.  It takes the cheapest q the network accepts,
-runs exactly m Newton steps in every substep with no test in between, and
-applies the estimate once at the end of each substep.  If any substep fails
-that check, or the network accepts no q, the call is redone by the plain
-method.  So an accepted result meets the same tolerance test as the plain one.
+will be met within m_max.  It takes the cheapest q the network accepts and
+runs s = 2^q substeps in one of two ways:
+
+  adaptive (the default): every substep ends, as in the plain method, at the
+      first degree whose a posteriori estimate passes; m only sets how many
+      Newton steps are issued before the first look at the estimate.  A
+      substep that reaches m_max without passing sends the call to the plain
+      method.
+  fixed count: exactly m Newton steps in every substep with no test in
+      between, and the estimate applied once at the end of each substep; any
+      failed check sends the call to the plain method.
+
+If the network accepts no q the plain method runs.  So an accepted result
+meets the same tolerance test as the plain one.
 
 Features of a call at candidate q (all cheap scalars the library already
 has): with c = (alpha+beta)/2, gamma = (beta-alpha)/4, tau = h/2^q and
@@ -129,13 +138,14 @@ class LearnedStats:
     accepted: bool = False      # the proposal passed every substep's check
     proposed: bool = False      # the network accepted some q
     plain: object = None        # Stats of the plain fallback, when taken
+    degrees: list = None        # per substep, of the proposal's attempt
 
 
 def phi1_learned(op, h, v, tol, theta, meta: Meta, kind, dim, ratio, peclet, xi=None,
-                 sizes=M.SIZES):
-    """h phi_1(hA) v under the learned schedule; falls back to the plain
-    method.  The network is evaluated in FP32, the precision of the library's
-    inference kernel.  Returns (y, LearnedStats)."""
+                 sizes=M.SIZES, fixed=False):
+    """h phi_1(hA) v under the learned schedule (adaptive, or fixed count);
+    falls back to the plain method.  The network is evaluated in FP32, the
+    precision of the library's inference kernel.  Returns (y, LearnedStats)."""
     ls = LearnedStats()
     v = np.asarray(v, dtype=np.float64).reshape(op.shape)
     alpha, beta = op.gershgorin()
@@ -149,8 +159,11 @@ def phi1_learned(op, h, v, tol, theta, meta: Meta, kind, dim, ratio, peclet, xi=
         if sm is not None:
             ls.proposed = True
             ls.s, ls.m = sm
-            st = Nw.Stats()
-            y, ok = Nw.h_phi1_fixed(op, h, v, tol, ls.s, ls.m, st, xi)
+            if fixed:
+                y, ok = Nw.h_phi1_fixed(op, h, v, tol, ls.s, ls.m, Nw.Stats(), xi)
+                ls.degrees = [ls.m] * ls.s
+            else:
+                y, ls.degrees, ok = Nw.h_phi1_at(op, h, v, tol, ls.s, meta.m_max, xi)
             if ok:
                 ls.accepted = True
                 return y, ls
@@ -161,12 +174,12 @@ def phi1_learned(op, h, v, tol, theta, meta: Meta, kind, dim, ratio, peclet, xi=
 
 
 def exp_step_learned(op, u, h, tol, theta, meta, kind, dim, ratio, peclet, rosenbrock=True,
-                     nonlin=Nw.NONLIN_LOGISTIC, xi=None):
+                     nonlin=Nw.NONLIN_LOGISTIC, xi=None, fixed=False):
     """One exponential Euler (rosenbrock=False) or Rosenbrock-Euler step with
     phi_1 under the learned schedule."""
     u = np.asarray(u, dtype=np.float64).reshape(op.shape)
     g, dg = Nw.nonlinearity(u, nonlin)
     F = op.matvec(u) + g
     J = ShiftedOperator(op, dg) if rosenbrock else op
-    y, ls = phi1_learned(J, h, F, tol, theta, meta, kind, dim, ratio, peclet, xi)
+    y, ls = phi1_learned(J, h, F, tol, theta, meta, kind, dim, ratio, peclet, xi, fixed=fixed)
     return u + y, ls

@@ -636,6 +636,53 @@ static ei_status phi1_fixed(ei_ctx* c, Prepared& P, const void* qc, double h, do
 // Integrate y' = J y + v from 0 over h by s substeps: returns y_s in the
 // buffer *result (vector format if *result_is_p == 0, Newton-sum format if 1).
 // k = 1 only.  v: imported vector (P.v); qc: J's diagonal array.
+// One attempt at s substeps with the per-substep a posteriori stop: d holds
+// the divided differences of tau = h/s, m_pred the degree launched before the
+// first look at the estimate.  *ok = every substep converged within m_max.
+// Substep degrees go to st->degrees (first EI_STATS_MAX_SUBSTEPS).
+static ei_status substep_attempt(ei_ctx* c, Prepared& P, const void* qc, double h, double cc,
+                                 double gamma, double tol, int m_max, int s, int m_pred,
+                                 const std::vector<double>& d, ei_stats* st, bool* ok_all,
+                                 int* matvecs, int* dsum, int* dmax) {
+  const double tau = h / s;
+  if (s > 1) EI_LAUNCH(launch_zero(P.y, P.fmt, P.n_alloc, c->stream));
+  *ok_all = true;
+  *matvecs = *dsum = *dmax = 0;
+  for (int i = 0; i < s; ++i) {
+    const void* r = P.v;
+    if (i > 0) {
+      EI_TRY_CUDA(op_residual(c, P, qc, P.y, P.v, P.r));
+      r = P.r;
+      ++*matvecs;
+    }
+    int deg = 0, ok = 0;
+    EI_TRY(newton_loop(c, P, qc, r, d, cc, gamma, tol, m_max, m_pred, &deg, &ok));
+    *matvecs += deg;
+    if (!ok) {
+      *ok_all = false;
+      return EI_OK;
+    }
+    if (st && i < EI_STATS_MAX_SUBSTEPS) st->degrees[i] = deg;
+    *dsum += deg;
+    if (deg > *dmax) *dmax = deg;
+    if (s > 1) EI_LAUNCH(launch_axpy(P.y, P.p, P.fmt, P.n_alloc, tau, c->stream));
+  }
+  return EI_OK;
+}
+
+static void set_result(Prepared& P, int s, double h, const void** result, int* is_p,
+                       double* scale) {
+  if (s == 1) {  // y_1 = tau * p
+    *result = P.p;
+    *is_p = 1;
+    *scale = h;
+  } else {
+    *result = P.y;
+    *is_p = 0;
+    *scale = 1.0;
+  }
+}
+
 static ei_status phi1_substeps(ei_ctx* c, Prepared& P, const void* qc, double h, double alpha,
                                double beta, double tol, const ei_options* opt, ei_stats* st,
                                const void** result, int* result_is_p, double* result_scale) {
@@ -644,7 +691,7 @@ static ei_status phi1_substeps(ei_ctx* c, Prepared& P, const void* qc, double h,
   const int m_max = (opt && opt->m_max > 0 && opt->m_max <= 100) ? opt->m_max : 100;
   const int learned = opt ? opt->learned : 0;
   int wasted = 0;  // operator applications of a rejected learned proposal
-  if (learned == 1 && c->model && !(opt && opt->fixed_s > 0)) {
+  if ((learned == 1 || learned == 3) && c->model && !(opt && opt->fixed_s > 0)) {
     double ratio, pe;
     EI_TRY(coef_stats(c, &ratio, &pe));
     const ei_mlp_decision& D = mlp_decision(c->model);
@@ -657,9 +704,6 @@ static ei_status phi1_substeps(ei_ctx* c, Prepared& P, const void* qc, double h,
     EI_TRY(mlp_infer_host(c->model, feat, rows, outs));
     int s_l = 0, m_l = 0;
     if (learned_decide(outs, rows, D, m_max, &s_l, &m_l)) {
-      bool ok = false;
-      EI_TRY(phi1_fixed(c, P, qc, h, cc, gamma, tol, s_l, m_l, &ok, result, result_is_p,
-                        result_scale));
       int q_l = 0;
       while ((1 << q_l) < s_l) ++q_l;
       if (st) {
@@ -667,22 +711,41 @@ static ei_status phi1_substeps(ei_ctx* c, Prepared& P, const void* qc, double h,
         st->learned_m = m_l;
         memcpy(st->features, feat + EI_MLP_INPUTS * q_l, sizeof(st->features));
       }
+      bool ok = false;
+      int mv = 0, dsum = 0, dmax = 0;
+      if (learned == 3) {  // fixed count
+        EI_TRY(phi1_fixed(c, P, qc, h, cc, gamma, tol, s_l, m_l, &ok, result, result_is_p,
+                          result_scale));
+        mv = s_l * m_l + (s_l - 1);
+        dsum = s_l * m_l;
+        dmax = m_l;
+        if (ok && st)
+          for (int i = 0; i < s_l && i < EI_STATS_MAX_SUBSTEPS; ++i) st->degrees[i] = m_l;
+      } else {  // adaptive: the proposal's s, the a posteriori stop in every substep
+        std::vector<double> d(m_max + 1);
+        divided_differences(1, h / s_l, cc, gamma, m_max, d.data());
+        EI_TRY(substep_attempt(c, P, qc, h, cc, gamma, tol, m_max, s_l, m_l, d, st, &ok, &mv,
+                               &dsum, &dmax));
+        if (ok) set_result(P, s_l, h, result, result_is_p, result_scale);
+      }
       if (ok) {
         if (st) {
           st->learned = 1;
           st->s = s_l;
           st->restarts = 0;
-          st->matvecs += s_l * m_l + (s_l - 1);
-          st->degree_sum = s_l * m_l;
-          st->degree_max = m_l;
-          for (int i = 0; i < s_l && i < EI_STATS_MAX_SUBSTEPS; ++i) st->degrees[i] = m_l;
+          st->matvecs += mv;
+          st->degree_sum = dsum;
+          st->degree_max = dmax;
           st->alpha = alpha;
           st->beta = beta;
         }
         return EI_OK;
       }
-      if (st) st->learned = 2;
-      wasted = s_l * m_l + (s_l - 1);
+      if (st) {
+        st->learned = 2;
+        memset(st->degrees, 0, sizeof(st->degrees));
+      }
+      wasted = mv;
     } else if (st) {
       st->learned = 3;
     }
@@ -700,44 +763,14 @@ static ei_status phi1_substeps(ei_ctx* c, Prepared& P, const void* qc, double h,
   if (st) st->m_sched = m_pred;
   int restarts = 0, matvecs = 0;
   while (s <= (1 << 20)) {
-    const double tau = h / s;
-    if (!have_d) divided_differences(1, tau, cc, gamma, m_max, d.data());
+    if (!have_d) divided_differences(1, h / s, cc, gamma, m_max, d.data());
     have_d = false;
-    if (s > 1) EI_LAUNCH(launch_zero(P.y, P.fmt, P.n_alloc, c->stream));
     bool ok_all = true;
-    int dsum = 0, dmax = 0;
-    for (int i = 0; i < s; ++i) {
-      const void* r = P.v;
-      if (i > 0) {
-        EI_TRY_CUDA(op_residual(c, P, qc, P.y, P.v, P.r));
-        r = P.r;
-        ++matvecs;
-      }
-      int deg = 0, ok = 0;
-      EI_TRY(newton_loop(c, P, qc, r, d, cc, gamma, tol, m_max, m_pred, &deg, &ok));
-      matvecs += deg;
-      if (!ok) { ok_all = false; break; }
-      if (st && i < EI_STATS_MAX_SUBSTEPS) st->degrees[i] = deg;
-      dsum += deg;
-      if (deg > dmax) dmax = deg;
-      if (s > 1) EI_LAUNCH(launch_axpy(P.y, P.p, P.fmt, P.n_alloc, tau, c->stream));
-    }
-    if (!ok_all && opt && opt->no_restart && opt->fixed_s > 0) {
-      if (st) {
-        st->s = s;
-        st->matvecs += matvecs + wasted;
-        st->degree_sum = dsum;
-        st->degree_max = dmax;
-        st->alpha = alpha;
-        st->beta = beta;
-        if (learned == 2) {
-          st->learned = 4;
-          EI_TRY(fill_features(c, st, s, h, alpha, beta, tol));
-        }
-      }
-      return EI_ERR_NOT_CONVERGED;
-    }
-    if (ok_all) {
+    int mv = 0, dsum = 0, dmax = 0;
+    EI_TRY(substep_attempt(c, P, qc, h, cc, gamma, tol, m_max, s, m_pred, d, st, &ok_all, &mv,
+                           &dsum, &dmax));
+    matvecs += mv;
+    if (ok_all || (opt && opt->no_restart && opt->fixed_s > 0)) {
       if (st) {
         st->s = s;
         st->restarts = restarts;
@@ -751,15 +784,8 @@ static ei_status phi1_substeps(ei_ctx* c, Prepared& P, const void* qc, double h,
           EI_TRY(fill_features(c, st, s, h, alpha, beta, tol));
         }
       }
-      if (s == 1) {  // y_1 = tau * p
-        *result = P.p;
-        *result_is_p = 1;
-        *result_scale = h;
-      } else {
-        *result = P.y;
-        *result_is_p = 0;
-        *result_scale = 1.0;
-      }
+      if (!ok_all) return EI_ERR_NOT_CONVERGED;
+      set_result(P, s, h, result, result_is_p, result_scale);
       return EI_OK;
     }
     ++restarts;

@@ -279,10 +279,10 @@ def predict(net, X):
 def calibrate(net, X, Y, mask, pid, cost):
     """Margins (z_min, rho_m, delta_m) that minimise the operator applications
     of the held-out problems under the decision rule (the cheapest accepted
-    q).  A proposal (q, m) is taken as accepted when the plain method
-    converged at that q with largest degree <= m; a rejected one costs its own
-    s (m + 1) - 1 plus the plain call.  Only the q values that have traces are
-    candidates here."""
+    q) in adaptive mode: a proposal at q is accepted when the plain method
+    converged at that q and then costs what it cost there; a rejected one
+    costs the work it did before reaching m_max plus the plain call.  Only
+    the q values that have traces are candidates here."""
     O = predict(net, X)
     groups = {}
     for i, p in enumerate(pid):
@@ -311,12 +311,12 @@ def calibrate(net, X, Y, mask, pid, cost):
                     if chosen is None:
                         total += plain_cost
                         continue
-                    q, i, m, own = chosen
-                    if mask[i] > 0 and Y[i, 0] * M_MAX <= m:
-                        total += own
+                    q, i, m, _ = chosen
+                    if mask[i] > 0:
+                        total += cost[i]
                         acc += 1
                     else:
-                        total += own + plain_cost
+                        total += cost[i] + plain_cost
                 if best is None or total < best[0]:
                     best = (total, z_min, rho_m, delta_m, acc / max(len(groups), 1),
                             total / plain)
@@ -417,6 +417,7 @@ def main():
     ap.add_argument("--seed", type=int, default=0)
     ap.add_argument("--out", default=MODEL_PATH)
     ap.add_argument("--save-traces", default=None)
+    ap.add_argument("--load-traces", default=None, help="traces saved by an earlier run")
     ap.add_argument("--budget-s", type=float, default=None, help="wall-clock limit of generation")
     ap.add_argument("--evaluate", type=int, default=0, help="held-out problems to compare on")
     args = ap.parse_args()
@@ -424,7 +425,11 @@ def main():
     build.build()
     log = lambda m: print(m, flush=True)  # noqa: E731
     t0 = time.time()
-    X, Y, M, P, Cst = generate(args.traces, args.seed, log=log, budget_s=args.budget_s)
+    if args.load_traces:
+        z = np.load(args.load_traces)
+        X, Y, M, P, Cst = z["X"], z["Y"], z["M"], z["P"], z["C"]
+    else:
+        X, Y, M, P, Cst = generate(args.traces, args.seed, log=log, budget_s=args.budget_s)
     t_gen = time.time() - t0
     if args.save_traces:
         np.savez(args.save_traces, X=X, Y=Y, M=M, P=P, C=Cst)

@@ -1,9 +1,10 @@
 """The learned schedule through the C ABI against the oracle
-(oracle/learned.py): the same network, evaluated in FP32 on both sides,
-makes the same proposal (s, m); an accepted proposal gives the fixed-count
-result within 1e-9, a rejected one the plain result (same degrees) within
-1e-9.  Hand-built networks make the proposal known in advance; the features
-the library reports match the oracle's definition."""
+(oracle/learned.py), in both modes (adaptive: options.learned = 1; fixed
+count: 3): the same network, evaluated in FP32 on both sides, makes the
+same proposal (s, m); an accepted proposal gives the oracle's result for it
+within 1e-9 (same degrees), a rejected one the plain result within 1e-9.
+Hand-built networks make the proposal known in advance; the features the
+library reports match the oracle's definition."""
 import math
 
 import numpy as np
@@ -60,48 +61,53 @@ def _field2d(n, seed):
     return D, b
 
 
-@pytest.mark.parametrize("q_accept,o0,expect_ok", [(1, 0.75, True), (0, 0.0625, False),
-                                                    (99, 0.5, None)])
-def test_learned_phi1_stencil(env, xi, q_accept, o0, expect_ok):
+@pytest.mark.parametrize("mode,q_accept,o0,h,expect", [
+    # fixed count (options.learned = 3)
+    (3, 1, 0.75, 6e-3, 1), (3, 0, 0.0625, 6e-3, 2), (3, 99, 0.5, 6e-3, 3),
+    # adaptive (options.learned = 1): m only batches the launches; at h = 0.03
+    # s = 1 reaches m_max (the plain rule needs s = 2) and the call falls back
+    (1, 1, 0.75, 6e-3, 1), (1, 0, 0.0625, 6e-3, 1), (1, 0, 0.5, 0.03, 2), (1, 99, 0.5, 6e-3, 3)])
+def test_learned_phi1_stencil(env, xi, mode, q_accept, o0, h, expect):
     torch, ei = env
     n, dx, bc = (45, 38), (1 / 46, 1 / 39), (0, 1, 1, 0)
     D, b = _field2d(n, 1)
     v0 = np.random.default_rng(2).standard_normal((n[1], n[0]))
-    h, tol = 6e-3, 1e-10
+    tol = 1e-10
     op = O.StencilOperator(n, dx, D, b, bc=bc)
     ratio, pe = Lr.stencil_stats(D, b, dx)
     theta = net_from(q_accept, o0)
     y, ls = Lr.phi1_learned(op, h, v0, tol, theta.astype(np.float64), Lr.Meta(), Lr.KIND_STENCIL,
-                            2, ratio, pe, xi)
+                            2, ratio, pe, xi, fixed=(mode == 3))
+    assert (1 if ls.accepted else 2 if ls.proposed else 3) == expect
     ctx = stencil_context(torch, ei, n, dx, D, b, 0.0, bc)
     net = _model(ei, theta)
     ctx.set_schedule_model(net)
     v = dev(torch, v0)
     out = torch.empty_like(v)
-    st = ctx.phi_apply(1, h, v, out, tol, {"learned": 1})
+    st = ctx.phi_apply(1, h, v, out, tol, {"learned": mode})
     got = out.cpu().numpy()
     assert rel_err(got, y / h) <= 1e-9
-    if expect_ok is None:
-        assert st.learned == 3 and not ls.proposed
-    else:
-        assert ls.proposed and (st.learned_s, st.learned_m) == (ls.s, ls.m)
+    assert st.learned == expect
+    if expect != 3:
+        assert (st.learned_s, st.learned_m) == (ls.s, ls.m)
         assert ls.s == 2 ** max(q_accept, 0)
-        assert st.learned == (1 if expect_ok else 2) and ls.accepted == expect_ok
     if st.learned == 1:
-        assert st.s == ls.s and st.degree_list() == [ls.m] * ls.s
+        assert st.s == ls.s and st.degree_list() == list(ls.degrees)
     else:  # the plain method's degrees
         assert st.s == ls.plain.s and st.degree_list() == list(ls.plain.degrees)
     ctx.close()
 
 
-def test_learned_rosenbrock_3d(env, xi):
+@pytest.mark.parametrize("mode", [1, 3])
+def test_learned_rosenbrock_3d(env, xi, mode):
     torch, ei = env
     w = W.adr_3d(n=20, h=4e-3)
     op = O.StencilOperator(w.n, w.dx, w.D, w.b, bc=w.bc)
     ratio, pe = Lr.stencil_stats(w.D, w.b, w.dx)
     theta = net_from(0, 0.5)
     ref, ls = Lr.exp_step_learned(op, w.u0, w.h, w.tol, theta.astype(np.float64), Lr.Meta(),
-                                  Lr.KIND_STENCIL, 3, ratio, pe, rosenbrock=True, xi=xi)
+                                  Lr.KIND_STENCIL, 3, ratio, pe, rosenbrock=True, xi=xi,
+                                  fixed=(mode == 3))
     assert ls.accepted
     ctx = ei.Context()
     ctx.set_operator_stencil(w.n, w.dx, dev(torch, w.D), [dev(torch, x) for x in w.b], 0.0,
@@ -109,13 +115,15 @@ def test_learned_rosenbrock_3d(env, xi):
     net = _model(ei, theta)
     ctx.set_schedule_model(net)
     u = dev(torch, w.u0)
-    st = ctx.step(ei.EXP_ROSENBROCK, w.h, u, ei.NONLIN_LOGISTIC, w.tol, {"learned": 1})
+    st = ctx.step(ei.EXP_ROSENBROCK, w.h, u, ei.NONLIN_LOGISTIC, w.tol, {"learned": mode})
     assert st.learned == 1 and (st.s, st.learned_m) == (ls.s, ls.m)
+    assert st.degree_list() == list(ls.degrees)
     assert rel_err(u.cpu().numpy() - w.u0, ref - w.u0) <= 1e-9
     ctx.close()
 
 
-def test_learned_csr(env, xi):
+@pytest.mark.parametrize("mode", [1, 3])
+def test_learned_csr(env, xi, mode):
     torch, ei = env
     g = W.rgg_graph(n=6000, seed=11)
     op = O.CsrOperator(g.n, g.rowptr, g.col, g.val, -g.deg_w)
@@ -124,7 +132,7 @@ def test_learned_csr(env, xi):
     v0 = W.random_vector(g.n, 4)
     theta = net_from(0, 0.5)
     y, ls = Lr.phi1_learned(op, h, v0, 1e-10, theta.astype(np.float64), Lr.Meta(), Lr.KIND_CSR,
-                            0, ratio, pe, xi)
+                            0, ratio, pe, xi, fixed=(mode == 3))
     ctx = ei.Context()
     ctx.set_operator_csr(g.n, dev(torch, g.rowptr), dev(torch, g.col), dev(torch, g.val),
                          dev(torch, -g.deg_w))
@@ -132,13 +140,14 @@ def test_learned_csr(env, xi):
     ctx.set_schedule_model(net)
     v = dev(torch, v0)
     out = torch.empty_like(v)
-    st = ctx.phi_apply(1, h, v, out, 1e-10, {"learned": 1})
+    st = ctx.phi_apply(1, h, v, out, 1e-10, {"learned": mode})
     assert st.learned == (1 if ls.accepted else 2)
     assert rel_err(out.cpu().numpy(), y / h) <= 1e-9
     ctx.close()
 
 
-def test_learned_fp32_form(env, xi):
+@pytest.mark.parametrize("mode", [1, 3])
+def test_learned_fp32_form(env, xi, mode):
     """The FP32 form under an accepted proposal, against the oracle on the
     FP32-rounded inputs (1e-5)."""
     torch, ei = env
@@ -152,14 +161,14 @@ def test_learned_fp32_form(env, xi):
     ratio, pe = Lr.stencil_stats(D32, b32, dx)
     theta = net_from(0, 0.5)
     y, ls = Lr.phi1_learned(op, h, v0.astype(np.float64), tol, theta.astype(np.float64),
-                            Lr.Meta(), Lr.KIND_STENCIL, 2, ratio, pe, xi)
+                            Lr.Meta(), Lr.KIND_STENCIL, 2, ratio, pe, xi, fixed=(mode == 3))
     assert ls.accepted
     ctx = stencil_context(torch, ei, n, dx, D, b, 0.0, bc, prec=1)
     net = _model(ei, theta)
     ctx.set_schedule_model(net)
     v = dev(torch, v0)
     out = torch.empty_like(v)
-    st = ctx.phi_apply(1, h, v, out, tol, {"learned": 1})
+    st = ctx.phi_apply(1, h, v, out, tol, {"learned": mode})
     assert st.learned == 1 and (st.s, st.learned_m) == (ls.s, ls.m)
     assert rel_err(out.cpu().numpy(), y / h) <= 1e-5
     ctx.close()

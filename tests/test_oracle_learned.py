@@ -134,7 +134,7 @@ def _constant_network(o0, o1, sizes=M.SIZES):
     return theta
 
 
-def test_learned_phi1_accepts_and_falls_back(xi):
+def test_learned_phi1_fixed_count_accepts_and_falls_back(xi):
     op, D, b, dx = _op2d()
     ratio, pe = Lr.stencil_stats(D, b, dx)
     v = np.random.default_rng(3).standard_normal(op.shape)
@@ -144,12 +144,12 @@ def test_learned_phi1_accepts_and_falls_back(xi):
     # outputs exactly representable in FP32, so the degree is exact
     # proposal (s = 1, m = 50): enough; accepted without the plain method
     y, ls = Lr.phi1_learned(op, h, v, tol, _constant_network(0.5, 1.0), meta,
-                            Lr.KIND_STENCIL, 2, ratio, pe, xi)
+                            Lr.KIND_STENCIL, 2, ratio, pe, xi, fixed=True)
     assert ls.proposed and ls.accepted and (ls.s, ls.m) == (1, 50) and ls.plain is None
     assert np.linalg.norm(y - ref) <= 1e-9 * np.linalg.norm(ref)
     # proposal (s = 1, m = 4): its check fails; the plain result is returned
     y2, ls2 = Lr.phi1_learned(op, h, v, tol, _constant_network(1.0 / 32, 1.0), meta,
-                              Lr.KIND_STENCIL, 2, ratio, pe, xi)
+                              Lr.KIND_STENCIL, 2, ratio, pe, xi, fixed=True)
     assert ls2.proposed and not ls2.accepted and ls2.plain is not None
     st = Nw.Stats()
     np.testing.assert_array_equal(y2, Nw.h_phi1_substeps(op, h, v, tol, st, xi=xi))
@@ -157,3 +157,31 @@ def test_learned_phi1_accepts_and_falls_back(xi):
     _, ls3 = Lr.phi1_learned(op, h, v, tol, _constant_network(0.5, -1.0), meta,
                              Lr.KIND_STENCIL, 2, ratio, pe, xi)
     assert not ls3.proposed and ls3.plain is not None
+
+
+def test_learned_phi1_adaptive(xi):
+    """Adaptive mode: the proposal's s with the plain method's per-substep
+    stop, so an accepted call equals the plain method at that s exactly; a
+    substep that reaches m_max sends the call to the plain method."""
+    op, D, b, dx = _op2d()
+    ratio, pe = Lr.stencil_stats(D, b, dx)
+    v = np.random.default_rng(3).standard_normal(op.shape)
+    meta = Lr.Meta(rho_m=0.0, delta_m=0.0)
+    tol = 1e-10
+    # h = 0.1: the plain rule takes s = 1 (degree 58); the proposal s = 1, m = 4
+    # is accepted and its m only batches the launches
+    st = Nw.Stats()
+    ref = Nw.h_phi1_substeps(op, 0.1, v, tol, st, xi=xi)
+    assert st.s == 1
+    y, ls = Lr.phi1_learned(op, 0.1, v, tol, _constant_network(1.0 / 32, 1.0), meta,
+                            Lr.KIND_STENCIL, 2, ratio, pe, xi)
+    assert ls.accepted and ls.s == 1 and ls.degrees == list(st.degrees)
+    np.testing.assert_array_equal(y, ref)
+    # h = 0.4: s = 1 reaches m_max (the plain rule needs s = 2): fallback
+    st = Nw.Stats()
+    ref = Nw.h_phi1_substeps(op, 0.4, v, tol, st, xi=xi)
+    assert st.s == 2
+    y, ls = Lr.phi1_learned(op, 0.4, v, tol, _constant_network(0.5, 1.0), meta,
+                            Lr.KIND_STENCIL, 2, ratio, pe, xi)
+    assert ls.proposed and not ls.accepted and ls.degrees == [100]
+    np.testing.assert_array_equal(y, ref)
