@@ -53,7 +53,8 @@ def parse():
     ap.add_argument("--tile-rows", type=int, default=0, help=argparse.SUPPRESS)
     ap.add_argument("--workload", default="adr3d",
                     choices=["adr3d", "adr3d_fp32", "rgg_csr", "batch", "batch_fp32",
-                             "adr3d_learned", "adr3d_fp32_learned", "rgg_csr_learned"],
+                             "adr3d_learned", "adr3d_fp32_learned", "rgg_csr_learned",
+                             "batch_learned_fp32", "batch_plain_fp64_loop"],
                     help="adr3d (default, the headline): 256^3 FP64 Rosenbrock-Euler; "
                          "adr3d_fp32: 512^3 FP32 exponential Euler; rgg_csr: 2^20-node CSR phi_1")
     ap.add_argument("--no-cpu", action="store_true", help="skip the CPU baseline sample")
@@ -328,7 +329,7 @@ class Batch2d(Workload):
 
     prec = 0
 
-    def __init__(self, torch, ei, W, dev, ctx, n):
+    def __init__(self, torch, ei, W, dev, ctx, n, learned_opt=False):
         self.name = "batch_1024_2d" + ("_fp32" if self.prec else "_fp64")
         self.method = "phi1 (batched, persistent kernel)"
         self.dtype = "f32 (float-float Newton sum)" if self.prec else \
@@ -337,8 +338,10 @@ class Batch2d(Workload):
         probs = W.batch_2d(count=n)
         self.tol = 1e-6 if self.prec else 1e-10
         t0 = time.perf_counter()
-        opts = {"tile_rows": TILE_ROWS} if TILE_ROWS else None
-        self.batch = ei.Batch(probs, prec=self.prec, tol=self.tol, options=opts)
+        opts = {"tile_rows": TILE_ROWS} if TILE_ROWS else {}
+        if learned_opt:
+            opts["learned"] = 1  # plans come from the network at each pass
+        self.batch = ei.Batch(probs, prec=self.prec, tol=self.tol, options=opts or None)
         self.setup_s = time.perf_counter() - t0
         dt = torch.float32 if self.prec else torch.float64
         flat = np.concatenate([p.v.ravel() for p in probs])
@@ -370,6 +373,102 @@ class Batch2dFp32(Batch2d):
     prec = 1
 
 
+class Batch2dLearnedFp32(Batch2d):
+    """The learned + FP32 + batched form: the 1024 problems in FP32 (tol 1e-6),
+    one persistent launch per pass, every problem's substep count from the
+    committed schedule network (adaptive; the a-priori rule where a proposal
+    reaches m_max).  The plan is made inside every pass."""
+
+    prec = 1
+
+    def __init__(self, torch, ei, W, dev, ctx, n):
+        from paper_1309_4616_gb300 import learned
+        self.model = learned.load()
+        Batch2d.__init__(self, torch, ei, W, dev, ctx, n, learned_opt=True)
+        self.batch.set_schedule_model(self.model)
+        self.name = "batch_1024_2d_fp32_learned"
+        self.method = "phi1 (batched, persistent kernel, learned schedule)"
+        self.config["schedule"] = "learned (network proposal, a posteriori stop)"
+
+
+class Batch2dPlainLoop(Workload):
+    """The plain FP64 GPU method on the same 1024 problems: one context per
+    problem, ei_phi_apply with the a-priori schedule, one problem after the
+    other (tol 1e-6, the accuracy the FP32 form states).  A step is one pass
+    over all problems."""
+
+    def __init__(self, torch, ei, W, dev, ctx, n):
+        self.name = "batch_1024_2d_fp64_plain_loop"
+        self.method = "phi1 (one ei_phi_apply per problem, a-priori schedule)"
+        self.dtype = "f64 (float-float pairs on the FP32 pipes)"
+        self.ei = ei
+        probs = W.batch_2d(count=n)
+        self.tol = 1e-6
+        t0 = time.perf_counter()
+        self.ctxs = []
+        for p in probs:
+            c = ei.Context(ctx.device, ctx.stream)
+            c.set_operator_stencil(p.n, p.dx, float(p.D), [float(x) for x in p.b], 0.0,
+                                   list(p.bc), ei.PREC_F64)
+            self.ctxs.append(c)
+        self.setup_s = time.perf_counter() - t0
+        flat = np.concatenate([p.v.ravel() for p in probs])
+        self.offsets = np.concatenate([[0], np.cumsum([p.v.size for p in probs])])
+        self.host0 = flat
+        self.state0 = torch.from_numpy(flat).to(dev)
+        self.state = self.state0.clone()
+        self.out = torch.empty_like(self.state)
+        self.npts = int(flat.size)
+        self.probs = probs
+        self.bytes_per_point = 72  # 2D explicit coefficients: w 8 + w' 8 + p 16 + 5 x 8
+        self.config = {"problems": len(probs), "points": self.npts, "tol": self.tol,
+                       "method": self.method, "setup_s": self.setup_s}
+
+    def _run(self, v, opts):
+        agg = LoopStepStats()
+        for i, (c, p) in enumerate(zip(self.ctxs, self.probs)):
+            a, b = int(self.offsets[i]), int(self.offsets[i + 1])
+            st = c.phi_apply(1, p.h, v[a:b], self.out[a:b], self.tol, opts)
+            agg.add(st, self.bytes_per_point * (b - a))
+        return agg
+
+    def step(self, ctx, opts=None):
+        return self._run(self.state, opts)
+
+    def step_host(self, ctx, host, opts=None):
+        d = host.to(self.state.device, non_blocking=True)
+        st = self._run(d, opts)
+        host.copy_(self.out, non_blocking=False)
+        return st
+
+    def kernel(self, fused):
+        return "k_newton2_tma<float-float> (per-problem launches)"
+
+
+class LoopStepStats:
+    """ei_stats-like sum over the calls of one pass."""
+
+    def __init__(self):
+        self.launches = self.matvecs = self.newton_timed = 0
+        self.newton_ms = 0.0
+        self.newton_fused = 1
+        self.timed_bytes = 0.0
+        self._degs = []
+
+    def add(self, st, bytes_per_iteration_sweep):
+        self.launches += st.launches
+        self.matvecs += st.matvecs
+        self.newton_timed += st.newton_timed
+        self.newton_ms += st.newton_ms
+        self.newton_fused = st.newton_fused or 1
+        self.timed_bytes += bytes_per_iteration_sweep * st.newton_fused * st.newton_timed
+        if len(self._degs) < 3:
+            self._degs.append(int(st.degree_sum))
+
+    def degree_list(self):
+        return self._degs
+
+
 class BatchStepStats:
     """ei_stats-like view of a batch pass."""
 
@@ -381,6 +480,8 @@ class BatchStepStats:
         self.newton_ms = 0.0
         self.newton_timed = 0
         self.newton_fused = 1
+        self.learned = 1 if any(s.learned == 1 for s in st) else 0
+        self.learned_kept = sum(1 for s in st if s.learned == 1)
         self._st = st
 
     def degree_list(self):
@@ -433,10 +534,12 @@ class RggCsrLearned(Learned, RggCsr):
 
 WORKLOADS = {"adr3d": Adr3d, "adr3d_fp32": Adr3dFp32, "rgg_csr": RggCsr, "batch": Batch2d,
              "batch_fp32": Batch2dFp32, "adr3d_learned": Adr3dLearned,
-             "adr3d_fp32_learned": Adr3dFp32Learned, "rgg_csr_learned": RggCsrLearned}
+             "adr3d_fp32_learned": Adr3dFp32Learned, "rgg_csr_learned": RggCsrLearned,
+             "batch_learned_fp32": Batch2dLearnedFp32, "batch_plain_fp64_loop": Batch2dPlainLoop}
 DEFAULT_N = {"adr3d": N_SIDE, "adr3d_fp32": 512, "rgg_csr": 1 << 20, "batch": 1024,
              "batch_fp32": 1024, "adr3d_learned": N_SIDE, "adr3d_fp32_learned": 512,
-             "rgg_csr_learned": 1 << 20}
+             "rgg_csr_learned": 1 << 20, "batch_learned_fp32": 1024,
+             "batch_plain_fp64_loop": 1024}
 
 
 def run_ours(args):
@@ -482,6 +585,7 @@ def run_ours(args):
     matvecs = []
     degrees = []
     learned_flags = []
+    learned_kept = None
     torch.cuda.synchronize(dev)
     e0.record(stream)
     for _ in range(args.steps):
@@ -490,6 +594,8 @@ def run_ours(args):
         matvecs.append(st.matvecs)
         degrees.append(st.degree_list())
         learned_flags.append(int(getattr(st, "learned", 0)))
+        if hasattr(st, "learned_kept"):
+            learned_kept = st.learned_kept
     e1.record(stream)
     torch.cuda.synchronize(dev)
     clocks = sampler.stop()
@@ -503,18 +609,24 @@ def run_ours(args):
     # roofline of the dominant kernel: per-launch CUDA events around every Newton
     # launch of two further steps (profile option), same stream, same sizes
     wl.state_reset()
-    prof_ms, prof_n, fused = 0.0, 0, 1
+    prof_ms, prof_n, fused, prof_bytes = 0.0, 0, 1, 0.0
     for _ in range(2):
         st = wl.step(ctx, {"profile": 1})
         prof_ms += st.newton_ms
         prof_n += st.newton_timed
         fused = st.newton_fused
+        prof_bytes += getattr(st, "timed_bytes", 0.0)
     hbm, peak_kind = peaks()
     if prof_n == 0 and hasattr(st, "point_iters"):
         # batched pass: one persistent launch; algorithmic bytes of all its sweeps
         # over the measured time per pass
         avg_launch_s = ms * 1e-3 / args.steps
         achieved = wl.bytes_per_point * st.point_iters / avg_launch_s / 1e9
+    elif hasattr(st, "timed_bytes"):
+        # many problems, one launch sequence each: bytes of all timed launches
+        # over their summed time
+        avg_launch_s = prof_ms / max(prof_n, 1) * 1e-3
+        achieved = prof_bytes / max(prof_ms * 1e-3, 1e-12) / 1e9
     else:
         # unit: one point-iteration; a two-iteration launch processes two per point
         # (its DRAM traffic is about half of that: w_{j+1} stays on chip)
@@ -552,7 +664,9 @@ def run_ours(args):
                   "l2": "inputs larger than L2 (each vector >= 8 MB and the step's working "
                         "set >= 0.3 GB; 256^3: 134 MB per vector)",
                   "matvecs_per_step": matvecs, "degrees": degrees[:3]}
-        if any(learned_flags):
+        if learned_kept is not None and getattr(wl, "model", None) is not None:
+            config["learned_problems_kept_per_pass"] = learned_kept
+        elif any(learned_flags):
             config["learned_accepted_steps"] = sum(1 for f in learned_flags if f == 1)
         line = {
             "metric": METRIC, "value": value, "unit": "steps/s", "n_gpus": world,
@@ -561,7 +675,8 @@ def run_ours(args):
             "dtype": wl.dtype, "data": "synthetic", "config": config,
             "roofline": {"bound": "hbm", "achieved": achieved, "peak": hbm, "unit": "GB/s",
                          "frac": achieved / hbm, "traffic": None, "kernel": wl.kernel(fused),
-                         "bytes_per_launch": wl.bytes_per_point * npts * fused,
+                         "bytes_per_launch": (prof_bytes / max(prof_n, 1)) if prof_bytes
+                         else wl.bytes_per_point * npts * fused,
                          "avg_launch_us": avg_launch_s * 1e6, "launches_timed": prof_n,
                          "iterations_per_launch": fused,
                          "us_per_iteration": avg_launch_s * 1e6 / fused,

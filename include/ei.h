@@ -330,6 +330,9 @@ typedef struct {
   int degree_sum;     /* Newton degrees summed over substeps */
   int restarts;       /* attempts rejected (m_max reached) */
   int tile_rows;      /* tile height the autotuner chose for its size class */
+  int learned;        /* with a schedule model: 1 the network's s kept, 2 it reached
+                         m_max and the a-priori rule took over, 0 no q accepted */
+  int pad;
 } ei_batch_stats;
 
 typedef struct ei_batch ei_batch; /* opaque, library-owned */
@@ -352,6 +355,14 @@ ei_status ei_batch_offsets(const ei_batch* b, int64_t* offsets);
  * after completion. */
 ei_status ei_batch_phi1(ei_batch* b, void* cuda_stream, const void* v, void* out,
                         ei_batch_stats* per_problem);
+/* Plan every later ei_batch_phi1 call with the schedule network `model`
+ * (NULL: the a-priori rule), in the adaptive mode of ei_options.learned = 1:
+ * per problem the network's substep count with the per-substep a posteriori
+ * stop; a problem whose proposal reaches m_max is redone with the a-priori
+ * rule.  The plan is made at each call (it depends on ||v_i||); divided
+ * differences are kept per problem and substep count.  A batch created with
+ * ei_options.learned = 1 skips the a-priori plans at creation. */
+ei_status ei_batch_set_schedule_model(ei_batch* b, const ei_mlp* model);
 void ei_batch_destroy(ei_batch* b);
 
 const char* ei_status_string(ei_status st);

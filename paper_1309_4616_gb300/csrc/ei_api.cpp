@@ -482,9 +482,8 @@ static ei_status coef_stats(ei_ctx* c, double* ratio, double* pe) {
 }
 
 // The twelve features of a phi_1 call at substep count s (see ei.h).
-static void learned_features(double* f, double s, double h, double alpha, double beta,
-                             double tol, int kind, int dim, int64_t n, double ratio, double pe,
-                             double vnorm) {
+void ei::learned_features(double* f, double s, double h, double alpha, double beta, double tol,
+                      int csr, int dim, int64_t n, double ratio, double pe, double vnorm) {
   const double cc = 0.5 * (alpha + beta), gamma = 0.25 * (beta - alpha);
   const double tau = h / s;
   const double rho = std::max(fabs(alpha), fabs(beta));
@@ -496,8 +495,8 @@ static void learned_features(double* f, double s, double h, double alpha, double
   f[3] = log2(s) / 10.0;
   f[4] = log10(h * rho) / 3.0;
   f[5] = 1.0;  // k
-  f[6] = kind == KIND_CSR ? 1.0 : 0.0;
-  f[7] = kind == KIND_STENCIL ? dim / 3.0 : 0.0;
+  f[6] = csr ? 1.0 : 0.0;
+  f[7] = csr ? 0.0 : dim / 3.0;
   f[8] = ratio;
   f[9] = log10(1.0 + std::min(pe, 1e30));
   f[10] = lr / 10.0;
@@ -509,16 +508,16 @@ static ei_status fill_features(ei_ctx* c, ei_stats* st, int s, double h, double 
   if (!st) return EI_OK;
   double ratio, pe;
   EI_TRY(coef_stats(c, &ratio, &pe));
-  learned_features(st->features, (double)s, h, alpha, beta, tol, c->kind, c->sd.dim, c->n, ratio,
-                   pe, sqrt(c->vnorm2));
+  learned_features(st->features, (double)s, h, alpha, beta, tol, c->kind == KIND_CSR, c->sd.dim,
+                   c->n, ratio, pe, sqrt(c->vnorm2));
   return EI_OK;
 }
 
 // Of the accepted q (output 1 >= z_min, the predicted degree with its
 // margins within m_max) the one with the fewest operator applications
 // 2^q (m_q + 1) - 1; ties go to the smaller q.
-static bool learned_decide(const float* o, int rows, const ei_mlp_decision& D, int m_max, int* s,
-                           int* m) {
+bool ei::learned_decide(const float* o, int rows, const ei_mlp_decision& D, int m_max, int* s,
+                    int* m) {
   const int qn = std::min(D.q_max, rows - 1);
   bool found = false;
   double best = 0.0;
@@ -698,8 +697,8 @@ static ei_status phi1_substeps(ei_ctx* c, Prepared& P, const void* qc, double h,
     const int rows = D.q_max + 1;
     double feat[(EI_MLP_MAX_Q + 1) * EI_MLP_INPUTS];
     for (int q = 0; q < rows; ++q)
-      learned_features(feat + EI_MLP_INPUTS * q, (double)(1 << q), h, alpha, beta, tol, c->kind,
-                       c->sd.dim, c->n, ratio, pe, sqrt(c->vnorm2));
+      learned_features(feat + EI_MLP_INPUTS * q, (double)(1 << q), h, alpha, beta, tol,
+                       c->kind == KIND_CSR, c->sd.dim, c->n, ratio, pe, sqrt(c->vnorm2));
     float outs[(EI_MLP_MAX_Q + 1) * EI_MLP_OUTPUTS];
     EI_TRY(mlp_infer_host(c->model, feat, rows, outs));
     int s_l = 0, m_l = 0;

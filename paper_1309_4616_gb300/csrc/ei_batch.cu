@@ -521,6 +521,15 @@ struct ei_batch {
   cudaGraphExec_t exec = nullptr;
   const void* graph_v = nullptr;
   void* graph_out = nullptr;
+  int64_t parts_cap = 0;           // partials allocated (doubles)
+  // learned schedule
+  const ei_mlp* model = nullptr;
+  bool deferred = false;           // plain plans not made yet (created with learned = 1)
+  std::vector<int> dd_s;           // the s whose divided differences hdd holds (0: none)
+  std::vector<int> plain_s;        // the a-priori rule's s (0: not computed)
+  std::vector<int> learned;        // 0 plain plan, 1 learned proposal kept, 2 fell back
+  double* vn2 = nullptr;           // device: ||v_i||^2
+  std::vector<double> hvn2;
 };
 
 static std::mutex g_tune_mu;
@@ -590,9 +599,11 @@ static bool batch_plan(ei_batch* B, int i, int s_force) {
   double* d = &B->hdd[(size_t)i * (B->m_max + 1)];
   if (s <= 0) {
     if (schedule(1, h, cc, gm, B->tol, B->m_max, &s, &m, d) != 0) return false;
-  } else {
+    B->plain_s[i] = s;
+  } else if (B->dd_s[i] != s) {
     divided_differences(1, h / s, cc, gm, B->m_max, d);
   }
+  B->dd_s[i] = s;
   B->hinst[i].s = s;
   B->hinst[i].tau = h / s;
   return true;
@@ -614,7 +625,7 @@ static void parallel_for(int n, const std::function<void(int)>& f) {
 static void batch_free(ei_batch* B) {
   if (B->exec) cudaGraphExecDestroy(B->exec);
   void* ptrs[] = {B->inst, B->state, B->order, B->dinit, B->duoff, B->dscal, B->dd, B->xi,
-                  B->partials, B->pool, B->ppool, B->finished, B->progress, B->error};
+                  B->partials, B->pool, B->ppool, B->finished, B->progress, B->error, B->vn2};
   for (void* p : ptrs)
     if (p) cudaFree(p);
   if (B->stream) cudaStreamDestroy(B->stream);
@@ -705,9 +716,16 @@ static ei_status batch_upload(ei_batch* B) {
     I.poff = poff;
     poff += 2 * (int64_t)I.tiles;
   }
-  if (B->partials) cudaFree(B->partials);
-  B->partials = nullptr;
-  BTRY(cudaMalloc(&B->partials, sizeof(double) * (poff > 0 ? poff : 2)));
+  const int64_t need = poff > 0 ? poff : 2;
+  if (need > B->parts_cap) {  // the captured graph holds the old pointer
+    if (B->partials) cudaFree(B->partials);
+    B->partials = nullptr;
+    B->parts_cap = 0;
+    BTRY(cudaMalloc(&B->partials, sizeof(double) * need));
+    B->parts_cap = need;
+    if (B->exec) cudaGraphExecDestroy(B->exec);
+    B->exec = nullptr;
+  }
   BTRY(cudaMemcpy(B->inst, B->hinst.data(), sizeof(BInst) * count, cudaMemcpyHostToDevice));
   BTRY(cudaMemcpy(B->dd, B->hdd.data(), sizeof(double) * B->hdd.size(), cudaMemcpyHostToDevice));
   // biggest problems first
@@ -747,6 +765,74 @@ static ei_status batch_run(ei_batch* B, const void* v, void* out, bool graph) {
   int err = 0;
   BTRY(cudaMemcpy(&err, B->error, sizeof(int), cudaMemcpyDeviceToHost));
   return err ? EI_ERR_TIMEOUT : EI_OK;
+}
+
+// ||v_i||^2 of every problem from the caller's packed v (one block per problem,
+// fixed summation order)
+template <class U>
+__global__ void k_batch_vnorm(const int64_t* uoff, const U* v, int count, double* vn2) {
+  const int i = blockIdx.x;
+  if (i >= count) return;
+  const int64_t a = uoff[i], b = uoff[i + 1];
+  double acc = 0.0, zero = 0.0;
+  for (int64_t k = a + threadIdx.x; k < b; k += blockDim.x) {
+    const double x = (double)v[k];
+    acc += x * x;
+  }
+  block_reduce2<RED_SUM>(acc, zero);
+  if (threadIdx.x == 0) vn2[i] = acc;
+}
+
+// Plans of this call from the schedule network: per problem the features of
+// s = 2^q, q = 0..q_max (constant D: coefficient ratio 1; Peclet number
+// max(|b_x| dx, |b_y| dy) / (2 D)), one batched inference, the cheapest
+// accepted q; a problem with no accepted q takes the a-priori rule.
+static ei_status batch_learned_plan(ei_batch* B, const void* v) {
+  const int count = B->count;
+  if (!B->vn2) {
+    BTRY(cudaMalloc(&B->vn2, sizeof(double) * count));
+    B->hvn2.assign(count, 0.0);
+  }
+  if (B->prec == EI_PREC_F32)
+    k_batch_vnorm<float><<<count, 256, 0, B->stream>>>(B->duoff, static_cast<const float*>(v),
+                                                       count, B->vn2);
+  else
+    k_batch_vnorm<double><<<count, 256, 0, B->stream>>>(B->duoff, static_cast<const double*>(v),
+                                                        count, B->vn2);
+  BTRY(cudaGetLastError());
+  BTRY(cudaMemcpyAsync(B->hvn2.data(), B->vn2, sizeof(double) * count, cudaMemcpyDeviceToHost,
+                       B->stream));
+  BTRY(cudaStreamSynchronize(B->stream));
+  const ei_mlp_decision& D = mlp_decision(B->model);
+  const int rows = D.q_max + 1;
+  std::vector<double> feat((size_t)count * rows * EI_MLP_INPUTS, 0.0);
+  for (int i = 0; i < count; ++i) {
+    if (!B->active[i]) continue;
+    const ei_batch_problem& P = B->prob[i];
+    const double pe = std::max(fabs(P.bx) * P.dx, fabs(P.by) * P.dy) / (2.0 * P.D);
+    for (int q = 0; q < rows; ++q)
+      learned_features(&feat[((size_t)i * rows + q) * EI_MLP_INPUTS], (double)(1 << q), P.h,
+                       B->alpha[i], B->beta[i], B->tol, 0, 2, B->hinst[i].npts, 1.0, pe,
+                       sqrt(B->hvn2[i]));
+  }
+  std::vector<float> outs((size_t)count * rows * EI_MLP_OUTPUTS);
+  ei_status st = mlp_infer_rows(B->model, feat.data(), (int64_t)count * rows, outs.data());
+  if (st != EI_OK) return st;
+  std::vector<int> ok(count, 1);
+  parallel_for(count, [&](int i) {
+    if (!B->active[i]) return;
+    int s = 0, m = 0;
+    if (learned_decide(&outs[(size_t)i * rows * EI_MLP_OUTPUTS], rows, D, B->m_max, &s, &m)) {
+      B->learned[i] = 1;
+      ok[i] = batch_plan(B, i, s) ? 1 : 0;
+    } else {
+      B->learned[i] = 0;
+      ok[i] = batch_plan(B, i, B->plain_s[i] > 0 ? B->plain_s[i] : 0) ? 1 : 0;
+    }
+  });
+  for (int i = 0; i < count; ++i)
+    if (!ok[i]) return EI_ERR_NOT_CONVERGED;
+  return batch_upload(B);
 }
 
 // autotuner: for each size class present, time the candidate tile heights on a
@@ -864,6 +950,10 @@ ei_status ei_batch_create(ei_batch** out, int device, int count, const ei_batch_
   B->gamma.resize(count);
   B->restarts.assign(count, 0);
   B->hdd.assign((size_t)count * (B->m_max + 1), 0.0);
+  B->dd_s.assign(count, 0);
+  B->plain_s.assign(count, 0);
+  B->learned.assign(count, 0);
+  B->deferred = opt && opt->learned == 1;
   int64_t uo = 0, po = 0;
   for (int i = 0; i < count; ++i) {
     const ei_batch_problem& P = problems[i];
@@ -900,9 +990,10 @@ ei_status ei_batch_create(ei_batch** out, int device, int count, const ei_batch_
   // schedules and divided differences, in parallel over problems
   std::vector<int> ok(count, 1);
   const int s_force = (opt && opt->fixed_s > 0) ? opt->fixed_s : 0;
-  parallel_for(count, [&](int i) {
-    if (B->active[i]) ok[i] = batch_plan(B, i, s_force) ? 1 : 0;
-  });
+  if (!B->deferred)
+    parallel_for(count, [&](int i) {
+      if (B->active[i]) ok[i] = batch_plan(B, i, s_force) ? 1 : 0;
+    });
   for (int i = 0; i < count; ++i)
     if (!ok[i]) {
       delete B;
@@ -968,7 +1059,20 @@ ei_status ei_batch_phi1(ei_batch* B, void* cuda_stream, const void* v, void* out
   BTRY(cudaEventCreateWithFlags(&ev, cudaEventDisableTiming));
   BTRY(cudaEventRecord(ev, us));
   BTRY(cudaStreamWaitEvent(B->stream, ev, 0));
-  ei_status rc = batch_run(B, v, out, true);
+  ei_status rc = EI_OK;
+  if (B->model) {
+    rc = batch_learned_plan(B, v);
+  } else if (B->deferred) {  // created for the learned schedule, used without a model
+    std::vector<int> ok(B->count, 1);
+    parallel_for(B->count, [&](int i) {
+      if (B->active[i]) ok[i] = batch_plan(B, i, 0) ? 1 : 0;
+    });
+    for (int i = 0; i < B->count; ++i)
+      if (!ok[i]) rc = EI_ERR_NOT_CONVERGED;
+    if (rc == EI_OK) rc = batch_upload(B);
+    B->deferred = false;
+  }
+  if (rc == EI_OK) rc = batch_run(B, v, out, true);
   // problems that reached m_max: double s and rerun them alone; the others keep
   // their results (status SKIP in the rerun)
   std::vector<BState> hs(B->count);
@@ -983,12 +1087,20 @@ ei_status ei_batch_phi1(ei_batch* B, void* cuda_stream, const void* v, void* out
     if (rc != EI_OK || redo.empty()) break;
     std::vector<int> init(B->count, ST_SKIP);
     for (int i : redo) {
-      const int s2 = 2 * B->hinst[i].s;
-      if (s2 > (1 << 20)) {
-        rc = EI_ERR_NOT_CONVERGED;
-        break;
+      if (B->learned[i] == 1) {  // the proposal reached m_max: the a-priori rule
+        B->learned[i] = 2;
+        if (!batch_plan(B, i, B->plain_s[i] > 0 ? B->plain_s[i] : 0)) {
+          rc = EI_ERR_NOT_CONVERGED;
+          break;
+        }
+      } else {
+        const int s2 = 2 * B->hinst[i].s;
+        if (s2 > (1 << 20)) {
+          rc = EI_ERR_NOT_CONVERGED;
+          break;
+        }
+        batch_plan(B, i, s2);
       }
-      batch_plan(B, i, s2);
       B->restarts[i] += 1;
       init[i] = ST_RUN;
     }
@@ -1026,6 +1138,7 @@ ei_status ei_batch_phi1(ei_batch* B, void* cuda_stream, const void* v, void* out
       per[i].degree_sum = B->active[i] ? B->final_deg[i] : 0;
       per[i].restarts = B->restarts[i];
       per[i].tile_rows = B->hinst[i].rows;
+      per[i].learned = B->model ? B->learned[i] : 0;
     }
   }
   // the caller's stream waits for the batch
@@ -1033,6 +1146,12 @@ ei_status ei_batch_phi1(ei_batch* B, void* cuda_stream, const void* v, void* out
   BTRY(cudaStreamWaitEvent(us, ev, 0));
   cudaEventDestroy(ev);
   return rc;
+}
+
+ei_status ei_batch_set_schedule_model(ei_batch* B, const ei_mlp* model) {
+  if (!B) return EI_ERR_INVALID_ARG;
+  B->model = model;
+  return EI_OK;
 }
 
 void ei_batch_destroy(ei_batch* B) {

@@ -178,6 +178,14 @@ cudaError_t launch_csr_newton(const CsrDev& op, const void* w_in, void* w_out, v
 // rounding) for host feature rows (FP64); synchronises the model's stream.
 ei_status mlp_infer_host(const ei_mlp* model, const double* features, int rows, float* out);
 const ei_mlp_decision& mlp_decision(const ei_mlp* model);
+// The twelve features of a phi_1 call at substep count s (definition in ei.h)
+// and the decision rule over the outputs of q = 0..rows-1 (ei_api.cpp).
+void learned_features(double* f, double s, double h, double alpha, double beta, double tol,
+                      int csr, int dim, int64_t n, double ratio, double pe, double vnorm);
+bool learned_decide(const float* outputs, int rows, const ei_mlp_decision& D, int m_max, int* s,
+                    int* m);
+// the same for any number of rows (staging grows as needed)
+ei_status mlp_infer_rows(const ei_mlp* model, const double* features, int64_t rows, float* out);
 
 // size in bytes of one vector element / of one Newton-sum element
 inline size_t vec_elem_bytes(int fmt) { return fmt == VF_F32 ? 4 : 8; }

@@ -315,6 +315,10 @@ struct ei_mlp {
   float* h_xo = nullptr;     // pinned: inputs then outputs
   int64_t t = 0;             // Adam step count
   ei_mlp_decision dec{};
+  float* big_x = nullptr;    // staging of many-row inference (mlp_infer_rows)
+  float* big_o = nullptr;
+  float* big_h = nullptr;    // pinned
+  int64_t big_rows = 0;
 };
 
 namespace {
@@ -377,6 +381,38 @@ ei_status mlp_infer_host(const ei_mlp* Mc, const double* feat, int rows, float* 
   return EI_OK;
 }
 const ei_mlp_decision& mlp_decision(const ei_mlp* M) { return M->dec; }
+
+// Any number of rows: staging buffers grow as needed (pinned host, device).
+ei_status mlp_infer_rows(const ei_mlp* Mc, const double* feat, int64_t rows, float* out) {
+  ei_mlp* M = const_cast<ei_mlp*>(Mc);
+  if (rows < 1) return EI_ERR_INVALID_ARG;
+  if (rows > M->big_rows) {
+    cudaFree(M->big_x);
+    cudaFree(M->big_o);
+    cudaFreeHost(M->big_h);
+    M->big_x = M->big_o = M->big_h = nullptr;
+    M->big_rows = 0;
+    if (cudaMalloc(&M->big_x, sizeof(float) * rows * kIn) != cudaSuccess ||
+        cudaMalloc(&M->big_o, sizeof(float) * rows * kOut) != cudaSuccess ||
+        cudaMallocHost(&M->big_h, sizeof(float) * rows * (kIn + kOut)) != cudaSuccess) {
+      cudaGetLastError();
+      return EI_ERR_NOMEM;
+    }
+    M->big_rows = rows;
+  }
+  for (int64_t i = 0; i < rows * kIn; ++i) M->big_h[i] = (float)feat[i];
+  float* ho = M->big_h + rows * kIn;
+  if (cudaMemcpyAsync(M->big_x, M->big_h, sizeof(float) * rows * kIn, cudaMemcpyHostToDevice,
+                      M->stream) != cudaSuccess)
+    return EI_ERR_CUDA;
+  if (ei_mlp_forward(M, M->big_x, rows, M->big_o) != EI_OK) return EI_ERR_CUDA;
+  if (cudaMemcpyAsync(ho, M->big_o, sizeof(float) * rows * kOut, cudaMemcpyDeviceToHost,
+                      M->stream) != cudaSuccess ||
+      cudaStreamSynchronize(M->stream) != cudaSuccess)
+    return EI_ERR_CUDA;
+  memcpy(out, ho, sizeof(float) * rows * kOut);
+  return EI_OK;
+}
 }  // namespace ei
 
 extern "C" {
@@ -434,6 +470,9 @@ void ei_mlp_destroy(ei_mlp* M) {
   cudaFree(M->d_o);
   cudaFreeHost(M->h_loss);
   cudaFreeHost(M->h_xo);
+  cudaFree(M->big_x);
+  cudaFree(M->big_o);
+  cudaFreeHost(M->big_h);
   delete M;
 }
 

@@ -31,7 +31,7 @@ EXPORTS = [
     "ei_batch_create", "ei_batch_offsets", "ei_batch_phi1", "ei_batch_destroy",
     "ei_mlp_create", "ei_mlp_destroy", "ei_mlp_set_params", "ei_mlp_get_params",
     "ei_mlp_set_decision", "ei_mlp_get_decision", "ei_mlp_forward", "ei_mlp_loss_grad",
-    "ei_mlp_train_step", "ei_set_schedule_model",
+    "ei_mlp_train_step", "ei_set_schedule_model", "ei_batch_set_schedule_model",
 ]
 
 
@@ -80,7 +80,8 @@ class BatchProblem(C.Structure):
 
 class BatchStats(C.Structure):
     _fields_ = [("alpha", C.c_double), ("beta", C.c_double), ("s", C.c_int),
-                ("degree_sum", C.c_int), ("restarts", C.c_int), ("tile_rows", C.c_int)]
+                ("degree_sum", C.c_int), ("restarts", C.c_int), ("tile_rows", C.c_int),
+                ("learned", C.c_int), ("pad", C.c_int)]
 
 
 class EIError(RuntimeError):
@@ -139,6 +140,7 @@ def lib():
         L.ei_mlp_train_step.argtypes = [vp, vp, vp, vp, C.c_int64, C.c_double, C.c_double,
                                         C.c_double, dp]
         L.ei_set_schedule_model.argtypes = [vp, vp]
+        L.ei_batch_set_schedule_model.argtypes = [vp, vp]
         L.ei_status_string.argtypes = [C.c_int]
         L.ei_status_string.restype = C.c_char_p
         for name in EXPORTS:
@@ -358,6 +360,12 @@ class Batch:
         _check(lib().ei_batch_offsets(self._h, off.ctypes.data_as(C.POINTER(C.c_int64))),
                "ei_batch_offsets")
         self.offsets = off
+
+    def set_schedule_model(self, model):
+        """Plan later passes with `model` (an Mlp, or None: the a-priori rule)."""
+        self._model = model
+        _check(lib().ei_batch_set_schedule_model(self._h, model._h if model is not None
+                                                 else None), "ei_batch_set_schedule_model")
 
     def phi1(self, v, out, stream=None):
         import torch

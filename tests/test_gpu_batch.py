@@ -125,3 +125,94 @@ def test_batch_full_workload_sampled(env, xi):
         assert rel_err(_unpack(got, b.offsets, i), ref) <= 1e-9
         assert st[i].s == ost.s and st[i].degree_sum == sum(ost.degrees)
     b.close()
+
+
+def _net_from(q_accept, o0):
+    """Output 0 = o0; output 1 = 10 x3 - q_accept + 0.5 (x3 = q/10): every
+    problem is offered s = 2^q_accept with the same degree."""
+    from oracle import mlp as M
+    th = np.zeros(M.n_params())
+    (W0, _), (W1, _), (W2, _), (W3, b3) = M.unpack(th)
+    W0[0, 3] = 1.0
+    W1[0, 0] = 1.0
+    W2[0, 0] = 1.0
+    W3[1, 0] = 10.0
+    b3[:] = [o0, -q_accept + 0.5]
+    return th.astype(np.float32)
+
+
+@pytest.mark.parametrize("prec", [0, 1])
+def test_batch_learned_vs_oracle(env, xi, prec):
+    """The learned schedule in the batch (adaptive): every problem gets the
+    network's s = 1; a third of the problems have a 40x larger h, and where
+    s = 1 reaches m_max the a-priori rule takes over.  Each problem against
+    oracle/learned.py."""
+    from oracle import learned as Lr
+    torch, ei = env
+    probs = _small_batch(21 + prec, 40, nmax=64)
+    for p in probs[2::3]:
+        p.h *= 40
+    tol = 1e-10 if prec == 0 else 1e-6
+    theta = _net_from(0, 0.5)
+    b = ei.Batch(probs, prec=prec, tol=tol, options={"learned": 1})
+    net = ei.Mlp()
+    net.set_params(theta)
+    net.set_decision(0.0, 0.05, 2.0, 12)
+    b.set_schedule_model(net)
+    dt = torch.float64 if prec == 0 else torch.float32
+    v = _pack(torch, probs, dt)
+    out = torch.empty_like(v)
+    st = b.phi1(v, out)
+    got = out.cpu().numpy().astype(np.float64)
+    kinds = {1: 0, 2: 0}
+    for i, p in enumerate(probs):
+        op = O.StencilOperator(p.n, p.dx, p.D, p.b, bc=p.bc)
+        pe = max(abs(p.b[0]) * p.dx[0], abs(p.b[1]) * p.dx[1]) / (2.0 * p.D)
+        y, ls = Lr.phi1_learned(op, p.h, p.v, tol, theta.astype(np.float64), Lr.Meta(),
+                                Lr.KIND_STENCIL, 2, 1.0, pe, xi)
+        g = _unpack(got, b.offsets, i)
+        ref = y / p.h
+        assert rel_err(g, ref) <= (1e-9 if prec == 0 else 1e-5), (i, p.n, rel_err(g, ref))
+        if prec == 0 and ls.proposed:
+            want = 1 if ls.accepted else 2
+            assert st[i].learned == want, (i, st[i].learned, want)
+            assert st[i].s == (ls.s if ls.accepted else ls.plain.s)
+            kinds[want] += 1
+    if prec == 0:
+        assert kinds[1] > 0 and kinds[2] > 0  # both outcomes covered
+
+
+def test_batch_learned_fp32_matches_plain_fp64(env):
+    """The same stated accuracy: at one tolerance (1e-6) the learned + FP32 +
+    batched form is as accurate as the plain FP64 method.  On 128 problems,
+    against a tol 1e-10 FP64 reference, every problem's error is at most 1.5x
+    the plain FP64 method's at tol 1e-6 plus 2e-6 (FP32 rounding); most
+    proposals are kept.  (At tol 1e-6 the a posteriori estimate itself lets
+    errors reach a few 1e-5 on the largest h*gamma; the FP32 form adds nothing
+    to that.)"""
+    torch, ei = env
+    from paper_1309_4616_gb300 import learned
+    probs = W.batch_2d(count=128, seed=77, nmax=160)
+
+    def run(prec, tol, model=None):
+        b = ei.Batch(probs, prec=prec, tol=tol, options={"learned": 1} if model else None)
+        if model is not None:
+            b.set_schedule_model(model)
+        v = _pack(torch, probs, torch.float64 if prec == 0 else torch.float32)
+        out = torch.empty_like(v)
+        st = b.phi1(v, out)
+        return out.cpu().numpy().astype(np.float64), st, b.offsets
+
+    ref, _, off = run(0, 1e-10)
+    p64, _, _ = run(0, 1e-6)
+    l32, st, _ = run(1, 1e-6, learned.load())
+    worst = 0.0
+    for i in range(len(probs)):
+        r = _unpack(ref, off, i)
+        e_plain = rel_err(_unpack(p64, off, i), r)
+        e_learn = rel_err(_unpack(l32, off, i), r)
+        worst = max(worst, e_learn)
+        assert e_learn <= 1.5 * e_plain + 2e-6, (i, probs[i].n, e_learn, e_plain)
+    kept = sum(1 for s in st if s.learned == 1)
+    print(f"worst relative error {worst:.2e}; proposals kept {kept}/{len(probs)}")
+    assert kept >= 0.8 * len(probs)
