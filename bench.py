@@ -39,6 +39,11 @@ N_SIDE = 256
 # w read 8 + w' write 8 + p read 8 + p write 8 + 7 coefficients x 8.  The
 # two-iteration kernel moves the same 88 bytes per launch for two iterations.
 BYTES_PER_POINT = 88
+# DRAM bytes per grid point of one launch of the two-iteration float-float
+# kernel, from ncu dram__bytes_read.sum + dram__bytes_write.sum on 192^3
+# (profiles/launches_adr3d_256_rosenbrock.md); traffic scales with the points.
+# Valid for the kernel as captured: retake it when the kernel changes.
+PAIR_DRAM_BYTES_PER_POINT = 86.9
 FLOPS_PER_POINT_PAPER = 10  # the paper's count for (alpha A + beta I)x, Sec. III-A
 
 
@@ -674,7 +679,10 @@ def run_ours(args):
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
             "dtype": wl.dtype, "data": "synthetic", "config": config,
             "roofline": {"bound": "hbm", "achieved": achieved, "peak": hbm, "unit": "GB/s",
-                         "frac": achieved / hbm, "traffic": None, "kernel": wl.kernel(fused),
+                         "frac": achieved / hbm,
+                         "traffic": (PAIR_DRAM_BYTES_PER_POINT * npts
+                                     if isinstance(wl, Adr3d) and fused == 2 else None),
+                         "kernel": wl.kernel(fused),
                          "bytes_per_launch": (prof_bytes / max(prof_n, 1)) if prof_bytes
                          else wl.bytes_per_point * npts * fused,
                          "avg_launch_us": avg_launch_s * 1e6, "launches_timed": prof_n,

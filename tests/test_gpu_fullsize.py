@@ -117,3 +117,34 @@ def test_fp32_form_512cube_restriction(env):
     err = rel_err(got, ref)
     print(f"512^3 FP32 form vs FP64 path on the 64^3 restriction: {err:.3e}")
     assert err <= 1e-5
+
+
+def test_paper_table4_matvec_count(env):
+    """Sec. III-D, Table 4 (tests/golden/paper_table4_step.txt): a step of the
+    256^3 homogeneous-Dirichlet problem with h = 1e-4 and tol = 1e-4 took 40
+    matrix-vector products.  One exponential Euler step of the Laplacian from
+    smooth data through the library takes the same order: within a factor of
+    2.5 either way (a range check: the paper's schedule is not given)."""
+    import os
+    torch, ei = env
+    g = {}
+    for line in open(os.path.join(os.path.dirname(__file__), "golden", "paper_table4_step.txt")):
+        line = line.strip()
+        if line and not line.startswith("#"):
+            k, v = line.split()
+            g[k] = float(v)
+    n = int(g["grid_points_per_axis"])
+    dx = 1.0 / (n + 1)
+    ctx = ei.Context()
+    ctx.set_operator_stencil((n, n, n), (dx, dx, dx), 1.0, [0.0, 0.0, 0.0], 0.0, [0] * 6,
+                             ei.PREC_F64)
+    x = (np.arange(n) + 1) * dx
+    s = np.sin(np.pi * x)
+    u0 = np.ascontiguousarray(s[:, None, None] * s[None, :, None] * s[None, None, :] +
+                              0.3 * np.sin(5 * np.pi * x)[None, None, :])
+    u = dev(torch, u0)
+    st = ctx.step(ei.EXP_EULER, g["h"], u, ei.NONLIN_NONE, g["tol"])
+    mv = g["matvecs_per_step"]
+    print(f"matvecs per step: {st.matvecs} (paper: {mv:.0f})")
+    assert mv / 2.5 <= st.matvecs <= mv * 2.5
+    ctx.close()
