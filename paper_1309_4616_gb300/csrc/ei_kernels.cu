@@ -281,6 +281,23 @@ __device__ __forceinline__ T csr_row(const CsrDev& op, const T* __restrict__ x, 
   const int64_t b = __ldg(op.rowptr + row), e = __ldg(op.rowptr + row + 1);
   typename Acc<T>::type s1 = Acc<T>::zero(), s2 = Acc<T>::zero();
   int64_t k = b;
+  // batches of 8 entries: all column and value loads of a batch, then all its
+  // gathers, so a row of ~12 entries needs two dependent rounds
+  for (; k + 8 <= e; k += 8) {
+    int c[8];
+    T v[8], xv[8];
+#pragma unroll
+    for (int i = 0; i < 8; ++i) c[i] = __ldg(col + k + i);
+#pragma unroll
+    for (int i = 0; i < 8; ++i) v[i] = ldg(val, k + i);
+#pragma unroll
+    for (int i = 0; i < 8; ++i) xv[i] = ldg(x, c[i]);
+#pragma unroll
+    for (int i = 0; i < 8; i += 2) {
+      s1 = lmac(s1, v[i], xv[i]);
+      s2 = lmac(s2, v[i + 1], xv[i + 1]);
+    }
+  }
   for (; k + 4 <= e; k += 4) {
     const int c0 = __ldg(col + k), c1 = __ldg(col + k + 1);
     const int c2 = __ldg(col + k + 2), c3 = __ldg(col + k + 3);
