@@ -53,7 +53,9 @@ def parse():
     ap.add_argument("--steps", type=int, default=20)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--n", type=int, default=None, help=argparse.SUPPRESS)
+    # problem size (grid side, nodes or problem count); --n is kept as an alias
+    # (torchrun reads an abbreviated --n as one of its own options: use --size there)
+    ap.add_argument("--size", "--n", dest="n", type=int, default=None, help=argparse.SUPPRESS)
     # batch workloads: fixed tile height instead of the autotuner (profiling)
     ap.add_argument("--tile-rows", type=int, default=0, help=argparse.SUPPRESS)
     ap.add_argument("--workload", default="adr3d",
@@ -547,6 +549,26 @@ DEFAULT_N = {"adr3d": N_SIDE, "adr3d_fp32": 512, "rgg_csr": 1 << 20, "batch": 10
              "batch_plain_fp64_loop": 1024}
 
 
+def replica_group(world, backend):
+    """The process group of N replicas (None for one process).  Ranks share no
+    data: only a barrier and the slowest replica's times."""
+    if world <= 1:
+        return None
+    import torch.distributed as dist
+    dist.init_process_group(backend)
+    return dist
+
+
+def max_over_ranks(value, dist, device):
+    """The largest value over all ranks (every rank receives it)."""
+    if dist is None:
+        return value
+    import torch
+    t = torch.tensor([float(value)], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
 def run_ours(args):
     import torch
     from paper_1309_4616_gb300 import build, ei
@@ -555,12 +577,8 @@ def run_ours(args):
     world = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))
     local = int(os.environ.get("LOCAL_RANK", "0"))
-    dist = None
-    if world > 1:
-        import torch.distributed as dist
-        torch.cuda.set_device(local)
-        dist.init_process_group("nccl")
     torch.cuda.set_device(local)
+    dist = replica_group(world, "nccl")
     if rank == 0 or world == 1:
         build.build()
     if dist is not None:
@@ -604,11 +622,8 @@ def run_ours(args):
     e1.record(stream)
     torch.cuda.synchronize(dev)
     clocks = sampler.stop()
-    ms = e0.elapsed_time(e1)
+    ms = max_over_ranks(e0.elapsed_time(e1), dist, dev)
     if dist is not None:
-        t = torch.tensor([ms], device=dev)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        ms = float(t.item())
         dist.barrier()
 
     # roofline of the dominant kernel: per-launch CUDA events around every Newton
@@ -648,11 +663,7 @@ def run_ours(args):
     for _ in range(k_e2e):
         wl.step_host(ctx, u_host)
     torch.cuda.synchronize(dev)
-    e2e_s = time.perf_counter() - t0
-    if dist is not None:
-        t = torch.tensor([e2e_s], device=dev)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        e2e_s = float(t.item())
+    e2e_s = max_over_ranks(time.perf_counter() - t0, dist, dev)
 
     cpu = None
     if rank == 0 and not args.no_cpu and args.workload == "adr3d":
