@@ -92,9 +92,10 @@ template <> __device__ __forceinline__ float ldcg_<float>(const float* p, int64_
 
 // One tile: 32 columns x (8*rows) rows.  Lane = column; warp w marches down
 // its own strip of `rows` consecutive rows keeping u(y-1), u(y), u(y+1) of its
-// column in registers, so a point costs three loads (u(y+1), u(x-1), u(x+1)),
-// and the next row's loads are issued before this row's arithmetic.  A ghost
-// value is 0 behind a Dirichlet face and u itself behind a Neumann face.
+// column in registers, so a point costs three loads (u(y+1), u(x-1), u(x+1))
+// plus its Newton sum; the loads of a row are issued two rows ahead of its
+// arithmetic.  A ghost value is 0 behind a Dirichlet face and u itself behind
+// a Neumann face.
 template <int FMT>
 __device__ void batch_tile(const BatchDev& B, int i, int t, int phase, int j, int sub,
                            double& o0, double& o1) {
@@ -140,47 +141,66 @@ __device__ void batch_tile(const BatchDev& B, int i, int t, int phase, int j, in
   const P dz = from_d<P>(phase == PH_NEWTON ? B.dd[I.dd_off] : 0.0);
   const T zro = zero<T>();
   if (x < I.nx && y0 < y1) {
-    // column queue: um = u(y-1), uc = u(y), up = u(y+1)
+    const bool newton = (phase == PH_NEWTON);
+    const bool needp = newton && j > 0;
+    // column queue of row y: um = u(y-1), uc = u(y), up = u(y+1), ul, ur, and
+    // the row's Newton sum pc (NEWTON, j > 0) or v (RES)
     int64_t k = (int64_t)y0 * I.nx + x;
     T uc = ldcg_(u, k);
     T um = y0 > 0 ? ldcg_(u, k - I.nx) : (I.bc[2] ? uc : zro);
     T ul = x > 0 ? ldcg_(u, k - 1) : (I.bc[0] ? uc : zro);
     T ur = x < I.nx - 1 ? ldcg_(u, k + 1) : (I.bc[1] ? uc : zro);
     T up = y0 < I.ny - 1 ? ldcg_(u, k + I.nx) : (I.bc[3] ? uc : zro);
+    P pc = needp ? ldcg_(Pp, k) : zero<P>();
+    T vc = newton ? zro : ldcg_(V, k);
+    // raw loads of a later row yy at element kk: left, right, the point above
+    // (u(yy+1)), its p or v; ghosts are applied when the row becomes current
+    auto fetch = [&](int64_t kk, int yy, T& l, T& r, T& a, P& pq, T& vq) {
+      l = x > 0 ? ldcg_(u, kk - 1) : zro;
+      r = x < I.nx - 1 ? ldcg_(u, kk + 1) : zro;
+      a = (yy + 1 < I.ny) ? ldcg_(u, kk + I.nx) : zro;
+      pq = needp ? ldcg_(Pp, kk) : zero<P>();
+      vq = newton ? zro : ldcg_(V, kk);
+    };
+    // row y+1 is one row ahead, row y+2 two rows ahead
+    T al = zro, ar = zro, au = zro, av = zro;
+    P apn = zero<P>();
+    if (y0 + 1 < y1) fetch(k + I.nx, y0 + 1, al, ar, au, apn, av);
     for (int y = y0; y < y1; ++y) {
-      // loads of the next row, issued before this row's arithmetic
-      const int64_t kn = k + I.nx;
-      const bool more = (y + 1 < y1);
-      T nl = zro, nr = zro, nu = zro;
-      if (more) {
-        nl = x > 0 ? ldcg_(u, kn - 1) : zro;
-        nr = x < I.nx - 1 ? ldcg_(u, kn + 1) : zro;
-        nu = (y + 2 < I.ny) ? ldcg_(u, kn + I.nx) : zro;
-      }
+      T bl = zro, br = zro, bu = zro, bv = zro;
+      P bpn = zero<P>();
+      if (y + 2 < y1) fetch(k + 2 * (int64_t)I.nx, y + 2, bl, br, bu, bpn, bv);
       T acc = mul(d0, uc);
       acc = mac(acc, axm, ul);
       acc = mac(acc, axp, ur);
       acc = mac(acc, aym, um);
       acc = mac(acc, ayp, up);
-      if (phase == PH_NEWTON) {
+      if (newton) {
         const T wn = newton_update(acc, invg, nshift, uc);
-        const P pold = (j == 0) ? mul(dz, to_p(uc)) : ldcg_(Pp, k);
+        const P pold = (j == 0) ? mul(dz, to_p(uc)) : pc;
         const P pn = mac(pold, dn, to_p(wn));
         st(wout, k, wn);
         st(Pp, k, pn);
         aw = acc_sq(aw, wn);
         ap = acc_sq(ap, pn);
       } else {
-        st(R, k, add(acc, ldcg_(V, k)));
+        st(R, k, add(acc, vc));
       }
-      if (more) {
-        // shift the column queue; ghosts for the next row
+      if (y + 1 < y1) {
+        // shift the queue; ghosts of row y+1 (u(y+1) = up is a real point)
         um = uc;
         uc = up;
-        ul = x > 0 ? nl : (I.bc[0] ? uc : zro);
-        ur = x < I.nx - 1 ? nr : (I.bc[1] ? uc : zro);
-        up = (y + 2 < I.ny) ? nu : (I.bc[3] ? uc : zro);
-        k = kn;
+        ul = x > 0 ? al : (I.bc[0] ? uc : zro);
+        ur = x < I.nx - 1 ? ar : (I.bc[1] ? uc : zro);
+        up = (y + 2 < I.ny) ? au : (I.bc[3] ? uc : zro);
+        pc = apn;
+        vc = av;
+        al = bl;
+        ar = br;
+        au = bu;
+        apn = bpn;
+        av = bv;
+        k += I.nx;
       }
     }
   }
