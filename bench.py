@@ -269,8 +269,8 @@ class Adr3dFp32(Adr3d):
         self.state0 = torch.from_numpy(w.u0).to(dev, f32)
         self.state = self.state0.clone()
         self.host0 = w.u0.astype(np.float32)
-        # w 4 + w' 4 + p 8+8 + D 4 + b 12 + c 4
-        self.bytes_per_point = 44
+        # w 4 + w' 4 + p 8+8 + 7 coefficients x 4
+        self.bytes_per_point = 52
         self.config = {"grid": [n] * 3, "h": w.h, "tol": w.tol, "bc": "neumann",
                        "method": self.method}
 
@@ -283,7 +283,8 @@ class Adr3dFp32(Adr3d):
                              self.w.tol, opts)
 
     def kernel(self, fused):
-        return "k_newton_tma<float, flux form>"
+        return ("k_newton2_tma<float> (two Newton iterations per launch)"
+                if fused == 2 else "k_newton_tma<float>")
 
 
 class RggCsr(Workload):

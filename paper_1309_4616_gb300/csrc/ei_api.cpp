@@ -187,10 +187,10 @@ static ei_status alloc(void** p, size_t bytes) {
   return EI_OK;
 }
 
-// Build the operator arrays and workspaces of one vector format.  Stencil
-// formats with 8-byte elements use explicit coefficients (7 arrays; the
-// Newton kernel then needs no boundary logic and little arithmetic per point);
-// the float format keeps the flux form (D, b, c), which moves fewer bytes.
+// Build the operator arrays and workspaces of one vector format.  Stencils use
+// explicit coefficients (7 arrays with the boundary conditions folded in): the
+// Newton kernel then needs no boundary logic, little arithmetic per point, and
+// can fuse two iterations per pass.
 static ei_status prepare(ei_ctx* c, int fmt) {
   Prepared& P = c->prep[fmt];
   if (P.ready) return EI_OK;
@@ -211,7 +211,7 @@ static ei_status prepare(ei_ctx* c, int fmt) {
     if ((s = take(a, vb)) != EI_OK) { free_prepared(P); return s; }
   if ((s = take(&P.p, pb)) != EI_OK) { free_prepared(P); return s; }
   if (c->kind == KIND_STENCIL) {
-    P.coef7 = (fmt != VF_F32);
+    P.coef7 = true;
     if (P.coef7) {
       for (int k = 0; k < 6; ++k)
         if ((s = take(&P.a[k], vb)) != EI_OK) { free_prepared(P); return s; }

@@ -141,6 +141,17 @@ __device__ __forceinline__ double stencil7(double dg, double wc, double a0, doub
   s1 = fma(a2, w2, s1);
   return s1 + s2;
 }
+__device__ __forceinline__ float stencil7(float dg, float wc, float a0, float w0, float a1,
+                                          float w1, float a2, float w2, float a3, float w3,
+                                          float a4, float w4, float a5, float w5) {
+  float s1 = dg * wc, s2 = a3 * w3;
+  s1 = fmaf(a0, w0, s1);
+  s2 = fmaf(a4, w4, s2);
+  s1 = fmaf(a1, w1, s1);
+  s2 = fmaf(a5, w5, s2);
+  s1 = fmaf(a2, w2, s1);
+  return s1 + s2;
+}
 __device__ __forceinline__ df newton_update(df Aw, df invg, df nshift, df wc) {
   return dfa_norm(dfa_mac(dfa_mul(Aw, invg), nshift, wc));
 }

@@ -87,8 +87,9 @@ int reduction_capacity();        // block bound of the grid-stride kernels
 int newton_tma_blocks(const StencilDev& op);
 
 // tensor maps: encode one 3D map over a padded array (elem 4 or 8 bytes);
-// halo = 1 widens the box by the 16-byte aligned x halo and one row in y,
-// halo = 2 by two columns and two rows (8-byte elements).
+// halo = 1 widens the box by the 16-byte aligned x halo (16/elem_bytes
+// columns each side) and one row in y, halo = 2 by the same x halo and two
+// rows.
 bool encode_map(CUtensorMap* m, const void* base, int elem_bytes, const StencilDev& g, int halo);
 
 // Coefficients of the stencil operator in the vector format (coef7 layout),
@@ -162,7 +163,7 @@ cudaError_t launch_newton_tma(const StencilDev& op, const NewtonMaps& M, void* w
                               const NewtonScalars& s, int fmt, double* partials, DevCtl* ctl,
                               cudaStream_t st);
 // Two Newton iterations j+1 and j+2 in one pass (explicit-coefficient stencil,
-// 8-byte formats): w_{j+1} is formed on chip over the tile and a one-point
+// all formats): w_{j+1} is formed on chip over the tile and a one-point
 // halo; only w_{j+2} and p_{j+2} are written.  M.w must be a halo-2 map.
 cudaError_t launch_newton2_tma(const StencilDev& op, const NewtonMaps& M, void* w_out, void* p,
                                const NewtonScalars& s, int fmt, double* partials, DevCtl* ctl,

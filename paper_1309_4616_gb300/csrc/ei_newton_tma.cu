@@ -303,11 +303,13 @@ template <int FMT>
 struct TmaCfg2 {
   using T = typename VT<FMT>::T;
   using P = typename VT<FMT>::P;
-  static_assert(sizeof(T) == 8, "two-iteration kernel: 8-byte formats");
   static constexpr int TX = 32, TY = 8;
   static constexpr int PF = 2;                 // planes in flight ahead
   static constexpr int NW = PF + 3, NC = PF + 3, NBAR = 8;
-  static constexpr int WJX = TX + 4, WJY = TY + 4;   // w_j box, two-point halo
+  // w_j box: two-point halo in y; in x the halo is widened to 16 bytes (2
+  // elements of 8 bytes, 4 of 4 bytes) so the box starts on a TMA boundary
+  static constexpr int XH = 16 / (int)sizeof(T);
+  static constexpr int WJX = TX + 2 * XH, WJY = TY + 4;
   static constexpr int W1X = TX + 2, W1Y = TY + 2;   // w_{j+1} region, one-point halo
   static constexpr int NHALO = W1X * W1Y - TX * TY;  // 84
   static constexpr int al(int b) { return (b + 127) / 128 * 128; }
@@ -361,7 +363,7 @@ k_newton2_tma(const __grid_constant__ NewtonMaps M, const StencilDev g, const Ne
     const bool hasc = (q >= 1) && (q <= nzc + 2);  // coefficient planes z0-1 .. z1
     const bool hasp = needp && (q >= 2) && (q <= nzc + 1);
     mbar_expect_tx(bar, C::WJ_BYTES + (hasc ? 7 * C::C_BYTES : 0) + (hasp ? C::P_BYTES : 0));
-    tma_load_3d(wb, &M.w, x0 - 2, y0 - 2, z, bar);
+    tma_load_3d(wb, &M.w, x0 - C::XH, y0 - 2, z, bar);
     if (hasc) {
 #pragma unroll
       for (int k = 0; k < 7; ++k) tma_load_3d(cb + k * C::C_BYTES, &M.c[k], x0, y0, z, bar);
@@ -424,7 +426,7 @@ k_newton2_tma(const __grid_constant__ NewtonMaps M, const StencilDev g, const Ne
   T w1_m2 = zero<T>(), w1_m1 = zero<T>();
   const int xi_ = x0 + tx, yi_ = y0 + ty;
   const bool own_xy = interior && (xi_ < g.nx) && (yi_ < g.ny);
-  const int wi_own = (ty + 2) * C::WJX + tx + 2;   // own point in the w_j box
+  const int wi_own = (ty + 2) * C::WJX + tx + C::XH;  // own point in the w_j box
   const int vi_own = (ty + 1) * C::W1X + tx + 1;   // own point in the w_{j+1} region
   const int ci = ty * C::TX + tx;
   int sw = 0, sc = 0;  // ring slots of plane m (w_j ring, coefficient ring)
@@ -465,7 +467,7 @@ k_newton2_tma(const __grid_constant__ NewtonMaps M, const StencilDev g, const Ne
       if (hlx >= 0) {
         T w1 = zero<T>();
         if (zin && hxy) {
-          const int wi = (hly + 1) * C::WJX + hlx + 1;
+          const int wi = (hly + 1) * C::WJX + hlx + C::XH - 1;
           const T wc = Wc[wi];
           const T acc = stencil7(hcur[6], wc, hcur[0], Wc[wi - 1], hcur[1], Wc[wi + 1], hcur[2],
                                  Wc[wi - C::WJX], hcur[3], Wc[wi + C::WJX], hcur[4], Wm[wi],
@@ -583,7 +585,6 @@ bool encode_map(CUtensorMap* m, const void* base, int elem_bytes, const StencilD
   cuuint64_t strides[2] = {(cuuint64_t)g.pitch * elem_bytes,
                            (cuuint64_t)g.pitch * g.ny * elem_bytes};
   cuuint32_t box[3] = {(cuuint32_t)(32 + (halo ? 2 * hx : 0)), (cuuint32_t)(8 + 2 * halo), 1};
-  if (halo == 2 && elem_bytes != 8) return false;
   cuuint32_t estr[3] = {1, 1, 1};
   CUresult r = fn(m, elem_bytes == 8 ? CU_TENSOR_MAP_DATA_TYPE_FLOAT64 : CU_TENSOR_MAP_DATA_TYPE_FLOAT32,
                   3, const_cast<void*>(base), dims, strides, box, estr,
@@ -630,6 +631,7 @@ cudaError_t launch_newton_tma(const StencilDev& g, const NewtonMaps& M, void* w_
                               cudaStream_t st) {
   if (fmt == VF_DF) return launch_one<VF_DF, true>(g, M, w_out, p, s, partials, ctl, st);
   if (fmt == VF_F64) return launch_one<VF_F64, true>(g, M, w_out, p, s, partials, ctl, st);
+  if (g.coef7) return launch_one<VF_F32, true>(g, M, w_out, p, s, partials, ctl, st);
   return launch_one<VF_F32, false>(g, M, w_out, p, s, partials, ctl, st);
 }
 
@@ -659,7 +661,15 @@ cudaError_t launch_newton2_tma(const StencilDev& g, const NewtonMaps& M, void* w
     }
     k_newton2_tma<VF_F64><<<grid, block, C::SMEM, st>>>(M, g, s, w_out, p, partials, ctl, zc);
   } else {
-    return cudaErrorInvalidValue;
+    using C = TmaCfg2<VF_F32>;
+    static bool attr = false;
+    if (!attr) {
+      cudaError_t e = cudaFuncSetAttribute(k_newton2_tma<VF_F32>,
+                                           cudaFuncAttributeMaxDynamicSharedMemorySize, C::SMEM);
+      if (e != cudaSuccess) return e;
+      attr = true;
+    }
+    k_newton2_tma<VF_F32><<<grid, block, C::SMEM, st>>>(M, g, s, w_out, p, partials, ctl, zc);
   }
   return cudaGetLastError();
 }
