@@ -35,8 +35,6 @@ enum { KIND_NONE = 0, KIND_STENCIL = 1, KIND_CSR = 2 };
 struct Prepared {
   bool ready = false;
   int fmt = VF_DF;
-  void* D = nullptr;       // stencil: D / (2 dx_x^2)
-  void* B[3] = {nullptr, nullptr, nullptr};  // stencil: b_e / (2 dx_e)
   void* cbase = nullptr;   // the fixed diagonal c_i (stencil) / diag (CSR)
   void* qc = nullptr;      // per-step diagonal c_i + g'(u_i)
   void* w[2] = {nullptr, nullptr};
@@ -48,13 +46,13 @@ struct Prepared {
   void* csr_val = nullptr; // CSR values in the matvec precision
   void* a[6] = {nullptr, nullptr, nullptr, nullptr, nullptr, nullptr};  // stencil coefficients
   void* diagA = nullptr;   // stencil: diagonal of A (coefficient layout)
-  bool coef7 = false;      // stencil layout of this format: explicit coefficients or flux form
+  bool coef7 = false;      // explicit stencil coefficients present (stencil operators)
   int64_t n_alloc = 0;     // elements per vector including row padding
   // TMA descriptors of the stencil Newton kernel
   CUtensorMap map_in[4];   // w-input candidates: v, r, w[0], w[1] (halo box)
   CUtensorMap map_in2[4];  // the same with a two-point halo (two-iteration kernel)
-  CUtensorMap map_c[6];    // coef7: a[0..5]; flux: D (halo), B[0..2]
-  CUtensorMap map_diagA, map_cbase, map_qc, map_p;
+  CUtensorMap map_c[6];    // a[0..5]
+  CUtensorMap map_diagA, map_qc, map_p;
 };
 
 struct ei_ctx {
@@ -150,9 +148,9 @@ static int vec_fmt_for(const ei_ctx* c, const ei_options* opt) {
 }
 
 static void free_prepared(Prepared& p) {
-  void** arrs[] = {&p.D,    &p.B[0], &p.B[1], &p.B[2], &p.cbase, &p.qc,   &p.w[0],
-                   &p.w[1], &p.p,    &p.y,    &p.r,    &p.v,     &p.u,    &p.csr_val,
-                   &p.a[0], &p.a[1], &p.a[2], &p.a[3], &p.a[4],  &p.a[5], &p.diagA};
+  void** arrs[] = {&p.cbase, &p.qc,   &p.w[0], &p.w[1], &p.p,    &p.y,    &p.r,
+                   &p.v,     &p.u,    &p.csr_val, &p.a[0], &p.a[1], &p.a[2], &p.a[3],
+                   &p.a[4],  &p.a[5], &p.diagA};
   for (void** a : arrs) {
     if (*a) cudaFree(*a);
     *a = nullptr;
@@ -212,43 +210,20 @@ static ei_status prepare(ei_ctx* c, int fmt) {
   if ((s = take(&P.p, pb)) != EI_OK) { free_prepared(P); return s; }
   if (c->kind == KIND_STENCIL) {
     P.coef7 = true;
-    if (P.coef7) {
-      for (int k = 0; k < 6; ++k)
-        if ((s = take(&P.a[k], vb)) != EI_OK) { free_prepared(P); return s; }
-      if ((s = take(&P.diagA, vb)) != EI_OK) { free_prepared(P); return s; }
-      const void* bptr[3] = {c->bu[0], c->bu[1], c->bu[2]};
-      EI_LAUNCH(launch_stencil_coef(c->sd, c->prec, c->dx, c->Du, c->Dc, bptr, c->bcst, c->cu,
-                                    c->cc, P.a, P.diagA, fmt, c->stream));
-    } else {
-      if ((s = take(&P.D, vb)) != EI_OK) { free_prepared(P); return s; }
-      for (int e = 0; e < 3; ++e)
-        if ((s = take(&P.B[e], vb)) != EI_OK) { free_prepared(P); return s; }
-      const double kx = 1.0 / (2.0 * c->dx[0] * c->dx[0]);
-      EI_LAUNCH(launch_fill_coef(P.D, fmt, n, nx, ny, pitch, c->Du, c->prec, c->Dc, kx, c->stream));
-      for (int e = 0; e < 3; ++e) {
-        const bool active = e < c->sd.dim;
-        EI_LAUNCH(launch_fill_coef(P.B[e], fmt, n, nx, ny, pitch, active ? c->bu[e] : nullptr,
-                                   c->prec, active ? c->bcst[e] : 0.0, 1.0 / (2.0 * c->dx[e]),
-                                   c->stream));
-      }
-      EI_LAUNCH(launch_fill_coef(P.cbase, fmt, n, nx, ny, pitch, c->cu, c->prec, c->cc, 1.0,
-                                 c->stream));
-    }
+    for (int k = 0; k < 6; ++k)
+      if ((s = take(&P.a[k], vb)) != EI_OK) { free_prepared(P); return s; }
+    if ((s = take(&P.diagA, vb)) != EI_OK) { free_prepared(P); return s; }
+    const void* bptr[3] = {c->bu[0], c->bu[1], c->bu[2]};
+    EI_LAUNCH(launch_stencil_coef(c->sd, c->prec, c->dx, c->Du, c->Dc, bptr, c->bcst, c->cu,
+                                  c->cc, P.a, P.diagA, fmt, c->stream));
     // tensor maps over the padded arrays
     const int eb = (int)vec_elem_bytes(fmt);
     const void* ins[4] = {P.v, P.r, P.w[0], P.w[1]};
     bool ok = true;
     for (int i = 0; i < 4; ++i) ok = ok && encode_map(&P.map_in[i], ins[i], eb, c->sd, 1);
-    if (P.coef7)
-      for (int i = 0; i < 4; ++i) ok = ok && encode_map(&P.map_in2[i], ins[i], eb, c->sd, 2);
-    if (P.coef7) {
-      for (int k = 0; k < 6; ++k) ok = ok && encode_map(&P.map_c[k], P.a[k], eb, c->sd, 0);
-      ok = ok && encode_map(&P.map_diagA, P.diagA, eb, c->sd, 0);
-    } else {
-      ok = ok && encode_map(&P.map_c[0], P.D, eb, c->sd, 1);
-      for (int e = 0; e < 3; ++e) ok = ok && encode_map(&P.map_c[1 + e], P.B[e], eb, c->sd, 0);
-      ok = ok && encode_map(&P.map_cbase, P.cbase, eb, c->sd, 0);
-    }
+    for (int i = 0; i < 4; ++i) ok = ok && encode_map(&P.map_in2[i], ins[i], eb, c->sd, 2);
+    for (int k = 0; k < 6; ++k) ok = ok && encode_map(&P.map_c[k], P.a[k], eb, c->sd, 0);
+    ok = ok && encode_map(&P.map_diagA, P.diagA, eb, c->sd, 0);
     ok = ok && encode_map(&P.map_qc, P.qc, eb, c->sd, 0);
     ok = ok && encode_map(&P.map_p, P.p, 8, c->sd, 0);
     if (!ok) { free_prepared(P); return EI_ERR_CUDA; }
@@ -264,18 +239,13 @@ static ei_status prepare(ei_ctx* c, int fmt) {
   return EI_OK;
 }
 
-// the fixed diagonal of A in this format's layout (stencil coef7: diagA; flux
-// form and CSR: c / diag)
+// the fixed diagonal of A in this format's layout (stencil: diagA; CSR: diag)
 static void* base_diag(Prepared& P) { return P.coef7 ? P.diagA : P.cbase; }
 
 static StencilDev stencil_view(const ei_ctx* c, const Prepared& P, const void* diag) {
   StencilDev s = c->sd;
-  s.coef7 = P.coef7 ? 1 : 0;
   for (int k = 0; k < 6; ++k) s.a[k] = P.a[k];
   s.diag = diag;
-  s.D = P.D;
-  for (int e = 0; e < 3; ++e) s.B[e] = P.B[e];
-  s.qc = diag;
   return s;
 }
 
@@ -318,12 +288,7 @@ static cudaError_t op_newton(ei_ctx* c, Prepared& P, const void* qc, const void*
     if (wi < 0) return cudaErrorInvalidValue;
     M.w = P.map_in[wi];
     for (int k = 0; k < 6; ++k) M.c[k] = P.map_c[k];
-    const CUtensorMap& md = (qc == P.qc) ? P.map_qc : (P.coef7 ? P.map_diagA : P.map_cbase);
-    if (P.coef7) {
-      M.c[6] = md;
-    } else {
-      M.c[4] = md;  // flux form: D, B0, B1, B2, diagonal term
-    }
+    M.c[6] = (qc == P.qc) ? P.map_qc : P.map_diagA;
     M.p = P.map_p;
     return launch_newton_tma(stencil_view(c, P, qc), M, w_out, P.p, s, P.fmt, c->partials,
                              c->ctl, c->stream);
@@ -901,11 +866,6 @@ ei_status ei_set_operator_stencil(ei_ctx* c, int dim, const int64_t n[3], const 
   s.pitch = (int)((ext[0] + 3) / 4 * 4);  // rows start on 16-byte boundaries
   for (int f = 0; f < 6; ++f) s.bc[f] = (f < 2 * dim) ? bc[f] : EI_BC_NEUMANN0;
   for (int e = 0; e < 3; ++e) c->dx[e] = (e < dim) ? dx[e] : 1.0;
-  s.uniform = 1;
-  for (int e = 0; e < 3; ++e) {
-    s.ratio[e] = (c->dx[0] * c->dx[0]) / (c->dx[e] * c->dx[e]);
-    if (e < dim && s.ratio[e] != 1.0) s.uniform = 0;
-  }
   c->Du = D;
   c->Dc = D_const;
   for (int e = 0; e < 3; ++e) {

@@ -39,14 +39,8 @@ struct StencilDev {
   int dim;
   int nx, ny, nz, pitch;
   int bc[6];
-  int coef7;           // 1: explicit coefficients a[6] + diag; 0: flux form D, B, qc
-  const void* a[6];    // coef7: neighbour coefficients x-, x+, y-, y+, z-, z+ (0 at a boundary)
-  const void* diag;    // coef7: diagonal of the operator in use (A, or J = A + diag g'(u))
-  const void* D;       // flux form: D / (2 dx_x^2)
-  const void* B[3];    // flux form: b_e / (2 dx_e)
-  const void* qc;      // flux form: diagonal term c_i (+ g'(u_i))
-  double ratio[3];     // flux form: k_e / k_x with k_e = 1/(2 dx_e^2)
-  int uniform;         // flux form: all ratios == 1
+  const void* a[6];    // neighbour coefficients x-, x+, y-, y+, z-, z+ (0 at a boundary)
+  const void* diag;    // diagonal of the operator in use (A, or J = A + diag g'(u))
 };
 
 // CSR operator: y = W x + diag .* x.
@@ -77,7 +71,7 @@ struct NewtonScalars {
 // as zeros).
 struct NewtonMaps {
   CUtensorMap w;       // w_in, halo box
-  CUtensorMap c[7];    // coef7: a[0..5], diag (interior box); flux: D (halo box), B0..2, qc
+  CUtensorMap c[7];    // a[0..5], diag (interior box)
   CUtensorMap p;       // Newton sum, interior box
 };
 
@@ -141,8 +135,8 @@ cudaError_t launch_axpy(void* y, const void* p, int fmt, int64_t n_alloc, double
                         cudaStream_t st);
 cudaError_t launch_zero(void* x, int fmt, int64_t n_alloc, cudaStream_t st);
 
-// Step start: F = A u + g(u), with A's diagonal from `diag_base` (coef7: the
-// operator's diagonal; flux: c), and diag_out = diag_base + g'(u) (Rosenbrock).
+// Step start: F = A u + g(u), with A's diagonal from `diag_base`, and
+// diag_out = diag_base + g'(u) (Rosenbrock).
 // u in vector format.  ||F||^2 into ctl->sum0, finiteness into ctl->sum1.
 cudaError_t launch_stencil_F(const StencilDev& op, const void* u, void* F, const void* diag_base,
                              void* diag_out, int nonlin, int rosenbrock, int fmt,

@@ -150,44 +150,7 @@ __device__ __forceinline__ T apply_coef7(const StencilDev& g, const T* __restric
   return acc;
 }
 
-// flux form: sum_e r_e [(D_i + D_{i+e})(w_{i+e} - w_i) + (D_i + D_{i-e})(w_{i-e} - w_i)]
-//            + sum_e B_e (w_{i+e} - w_{i-e}) + qc_i w_i, ghosts as in the row rule
-template <class T>
-__device__ __forceinline__ T apply_flux(const StencilDev& g, const T* __restrict__ w,
-                                        const T* __restrict__ qc, int x, int y, int z,
-                                        int64_t idx, T& wc) {
-  const T* __restrict__ D = static_cast<const T*>(g.D);
-  wc = ldg(w, idx);
-  const T Dc = ldg(D, idx);
-  const T zro = zero<T>();
-  const int crd[3] = {x, y, z};
-  const int ext[3] = {g.nx, g.ny, g.nz};
-  const int64_t str[3] = {1, g.pitch, (int64_t)g.pitch * g.ny};
-  T acc = zero<T>();
-#pragma unroll
-  for (int e = 0; e < 3; ++e) {
-    if (e >= g.dim) break;
-    const bool hm = crd[e] > 0, hp = crd[e] < ext[e] - 1;
-    const T wm = hm ? ldg(w, idx - str[e]) : (g.bc[2 * e] ? wc : zro);
-    const T wp = hp ? ldg(w, idx + str[e]) : (g.bc[2 * e + 1] ? wc : zro);
-    const T Dm = hm ? ldg(D, idx - str[e]) : Dc;
-    const T Dp = hp ? ldg(D, idx + str[e]) : Dc;
-    T ae = mul(add(Dc, Dp), sub(wp, wc));
-    ae = mac(ae, add(Dc, Dm), sub(wm, wc));
-    acc = (e == 0 || g.uniform) ? add(acc, ae) : mac(acc, from_d<T>(g.ratio[e]), ae);
-    acc = mac(acc, ldg(static_cast<const T*>(g.B[e]), idx), sub(wp, wm));
-  }
-  return mac(acc, ldg(qc, idx), wc);
-}
-
-template <class T>
-__device__ __forceinline__ T apply_stencil(const StencilDev& g, const T* w, const T* diag_or_qc,
-                                           int x, int y, int z, int64_t idx, T& wc) {
-  return g.coef7 ? apply_coef7<T>(g, w, diag_or_qc, x, y, z, idx, wc)
-                 : apply_flux<T>(g, w, diag_or_qc, x, y, z, idx, wc);
-}
-
-// r = J y + v, ||r||^2 (J's diagonal: g.diag (coef7) or g.qc (flux))
+// r = J y + v, ||r||^2 (J's diagonal: g.diag)
 template <int FMT>
 __global__ void __launch_bounds__(EI_TPB)
 k_stencil_residual(StencilDev g, const void* __restrict__ y_, const void* __restrict__ v_,
@@ -196,7 +159,7 @@ k_stencil_residual(StencilDev g, const void* __restrict__ y_, const void* __rest
   const T* __restrict__ yv = static_cast<const T*>(y_);
   const T* __restrict__ v = static_cast<const T*>(v_);
   T* __restrict__ r = static_cast<T*>(r_);
-  const T* dg = static_cast<const T*>(g.coef7 ? g.diag : g.qc);
+  const T* dg = static_cast<const T*>(g.diag);
   const int64_t n = (int64_t)g.nx * g.ny * g.nz;
   T ar = zero<T>();
   for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;
@@ -207,7 +170,7 @@ k_stencil_residual(StencilDev g, const void* __restrict__ y_, const void* __rest
     const int z = (int)(t / g.ny);
     const int64_t idx = t * g.pitch + x;
     T yc;
-    const T Ay = apply_stencil<T>(g, yv, dg, x, y, z, idx, yc);
+    const T Ay = apply_coef7<T>(g, yv, dg, x, y, z, idx, yc);
     const T rv = add(Ay, ldg(v, idx));
     st(r, idx, rv);
     ar = mac(ar, rv, rv);
@@ -240,7 +203,7 @@ k_stencil_F(StencilDev g, const void* __restrict__ u_, void* __restrict__ F_,
     const int z = (int)(t / g.ny);
     const int64_t idx = t * g.pitch + x;
     T uc;
-    T Fv = apply_stencil<T>(g, u, db, x, y, z, idx, uc);
+    T Fv = apply_coef7<T>(g, u, db, x, y, z, idx, uc);
     if (nonlin) Fv = mac(Fv, uc, sub(one, uc));  // g(u) = u(1-u)
     st(F, idx, Fv);
     if (rosenbrock) {
@@ -262,8 +225,8 @@ k_stencil_F(StencilDev g, const void* __restrict__ u_, void* __restrict__ F_,
 // ---------------------------------------------------------------------------
 // CSR operator (Sec. III-D): one thread per row.  The paper's C2075 code gave
 // each row four threads; rows of the random geometric graph carry ~12
-// entries, and on sm_103a one thread per row issues all of a row's column,
-// value and gather loads together (four at a time, two independent
+// entries, and on sm_103a one thread per row issues a row's column, value
+// and gather loads in batches (eight, then four at a time; two independent
 // accumulators) and keeps every lane busy in the Newton update.
 // ---------------------------------------------------------------------------
 __device__ __forceinline__ dfacc lmac(dfacc c, df a, df b) { return dfa_mac(c, a, b); }

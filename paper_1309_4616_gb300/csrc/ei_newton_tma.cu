@@ -30,7 +30,7 @@
 
 namespace ei {
 
-template <int FMT, bool COEF7>
+template <int FMT>
 struct TmaCfg {
   using T = typename VT<FMT>::T;
   using P = typename VT<FMT>::P;
@@ -45,11 +45,10 @@ struct TmaCfg {
   static constexpr int W_BYTES = WX * WY * (int)sizeof(T);
   static constexpr int C_BYTES = TX * TY * (int)sizeof(T);
   static constexpr int P_BYTES = TX * TY * (int)sizeof(P);
-  static constexpr int N_CT = COEF7 ? 7 : 4;      // interior coefficient tiles
-  // w-ring slot: w halo tile (+ D halo tile in the flux form)
+  static constexpr int N_CT = 7;        // interior coefficient tiles: a[0..5], diagonal
+  // w-ring slot: the w halo tile
   static constexpr int OFF_W = 0;
-  static constexpr int OFF_D = al(W_BYTES);
-  static constexpr int WSTAGE = COEF7 ? al(W_BYTES) : 2 * al(W_BYTES);
+  static constexpr int WSTAGE = al(W_BYTES);
   // coefficient-ring slot: interior coefficient tiles, then the p tile
   static constexpr int OFF_CT = 0;
   static constexpr int OFF_P = N_CT * C_BYTES;
@@ -112,12 +111,12 @@ __device__ __forceinline__ bool mbar_wait_bounded(uint32_t bar, uint32_t parity,
 
 static constexpr uint64_t kWaitLimitNs = 500000000ull;  // 0.5 s; a plane lands in microseconds
 
-template <int FMT, bool COEF7>
-__global__ void __launch_bounds__(256, COEF7 ? 2 : 4)
+template <int FMT>
+__global__ void __launch_bounds__(256, 2)
 k_newton_tma(const __grid_constant__ NewtonMaps M, const StencilDev g, const NewtonScalars s,
              void* __restrict__ w_out_, void* __restrict__ p_, double* partials, DevCtl* ctl,
              int zc) {
-  using C = TmaCfg<FMT, COEF7>;
+  using C = TmaCfg<FMT>;
   using T = typename C::T;
   using P = typename C::P;
   if (*(volatile int*)&ctl->done != 0) return;
@@ -133,7 +132,7 @@ k_newton_tma(const __grid_constant__ NewtonMaps M, const StencilDev g, const New
   const int z1 = min(z0 + zc, g.nz);
   const int nplanes = z1 - z0 + 2;  // z0-1 .. z1
   const bool needp = s.j > 0;
-  const uint32_t tx_halo = C::W_BYTES + (COEF7 ? 0 : C::W_BYTES);
+  const uint32_t tx_halo = C::W_BYTES;
   const uint32_t tx_full = tx_halo + C::N_CT * C::C_BYTES + (needp ? C::P_BYTES : 0);
 
   if (tid == 0) {
@@ -151,11 +150,10 @@ k_newton_tma(const __grid_constant__ NewtonMaps M, const StencilDev g, const New
     const bool halo = (q == 0) || (q == nplanes - 1);
     mbar_expect_tx(bar, halo ? tx_halo : tx_full);
     tma_load_3d(wb + C::OFF_W, &M.w, x0 - C::HX, y0 - 1, z, bar);
-    if (!COEF7) tma_load_3d(wb + C::OFF_D, &M.c[0], x0 - C::HX, y0 - 1, z, bar);
     if (!halo) {
 #pragma unroll
       for (int k = 0; k < C::N_CT; ++k)
-        tma_load_3d(cb + C::OFF_CT + k * C::C_BYTES, &M.c[COEF7 ? k : k + 1], x0, y0, z, bar);
+        tma_load_3d(cb + C::OFF_CT + k * C::C_BYTES, &M.c[k], x0, y0, z, bar);
       if (needp) tma_load_3d(cb + C::OFF_P, &M.p, x0, y0, z, bar);
     }
     last_issued = q;
@@ -208,45 +206,9 @@ k_newton_tma(const __grid_constant__ NewtonMaps M, const StencilDev g, const New
       const T* Wp = reinterpret_cast<const T*>(smp + C::OFF_W);
       const T* Ct = reinterpret_cast<const T*>(scq + C::OFF_CT);
       const T wc = Wc[wi];
-      T acc;
-      if constexpr (COEF7) {
-        acc = stencil7(Ct[6 * TT + ci], wc, Ct[0 * TT + ci], Wc[wi - 1], Ct[1 * TT + ci],
-                       Wc[wi + 1], Ct[2 * TT + ci], Wc[wi - C::WX], Ct[3 * TT + ci],
-                       Wc[wi + C::WX], Ct[4 * TT + ci], Wm[wi], Ct[5 * TT + ci], Wp[wi]);
-      } else {
-        // flux form: ghost w is 0 (Dirichlet, from the zero fill) or w_c
-        // (Neumann); ghost D is D_c
-        const T* Dt = reinterpret_cast<const T*>(sm + C::OFF_D);
-        const T* Dm_ = reinterpret_cast<const T*>(smm + C::OFF_D);
-        const T* Dp_ = reinterpret_cast<const T*>(smp + C::OFF_D);
-        const T Dc = Dt[wi];
-        const T wxm = (x == 0 && g.bc[0]) ? wc : Wc[wi - 1];
-        const T wxp = (x == g.nx - 1 && g.bc[1]) ? wc : Wc[wi + 1];
-        const T wym = (y == 0 && g.bc[2]) ? wc : Wc[wi - C::WX];
-        const T wyp = (y == g.ny - 1 && g.bc[3]) ? wc : Wc[wi + C::WX];
-        const T Dxm = x > 0 ? Dt[wi - 1] : Dc;
-        const T Dxp = x < g.nx - 1 ? Dt[wi + 1] : Dc;
-        const T Dym = y > 0 ? Dt[wi - C::WX] : Dc;
-        const T Dyp = y < g.ny - 1 ? Dt[wi + C::WX] : Dc;
-        acc = mul(add(Dc, Dxp), sub(wxp, wc));
-        acc = mac(acc, add(Dc, Dxm), sub(wxm, wc));
-        acc = mac(acc, Ct[0 * TT + ci], sub(wxp, wxm));
-        T ay = mul(add(Dc, Dyp), sub(wyp, wc));
-        ay = mac(ay, add(Dc, Dym), sub(wym, wc));
-        acc = g.uniform ? add(acc, ay) : mac(acc, from_d<T>(g.ratio[1]), ay);
-        acc = mac(acc, Ct[1 * TT + ci], sub(wyp, wym));
-        if (g.dim == 3) {
-          const T wzm = (z == 0 && g.bc[4]) ? wc : Wm[wi];
-          const T wzp = (z == g.nz - 1 && g.bc[5]) ? wc : Wp[wi];
-          const T Dzm = z > 0 ? Dm_[wi] : Dc;
-          const T Dzp = z < g.nz - 1 ? Dp_[wi] : Dc;
-          T az = mul(add(Dc, Dzp), sub(wzp, wc));
-          az = mac(az, add(Dc, Dzm), sub(wzm, wc));
-          acc = g.uniform ? add(acc, az) : mac(acc, from_d<T>(g.ratio[2]), az);
-          acc = mac(acc, Ct[2 * TT + ci], sub(wzp, wzm));
-        }
-        acc = mac(acc, Ct[3 * TT + ci], wc);
-      }
+      const T acc = stencil7(Ct[6 * TT + ci], wc, Ct[0 * TT + ci], Wc[wi - 1], Ct[1 * TT + ci],
+                             Wc[wi + 1], Ct[2 * TT + ci], Wc[wi - C::WX], Ct[3 * TT + ci],
+                             Wc[wi + C::WX], Ct[4 * TT + ci], Wm[wi], Ct[5 * TT + ci], Wp[wi]);
       const T wn = newton_update(acc, invg, nshift, wc);
       const P* Pt = reinterpret_cast<const P*>(scq + C::OFF_P);
       const P pold = needp ? Pt[ci] : mul(d0, to_p(wc));
@@ -608,31 +570,30 @@ int newton_tma_blocks(const StencilDev& g) {
   return ((g.nx + 31) / 32) * ((g.ny + 7) / 8) * ((g.nz + zc - 1) / zc);
 }
 
-template <int FMT, bool COEF7>
+template <int FMT>
 static cudaError_t launch_one(const StencilDev& g, const NewtonMaps& M, void* w_out, void* p,
                               const NewtonScalars& s, double* partials, DevCtl* ctl,
                               cudaStream_t st) {
-  using C = TmaCfg<FMT, COEF7>;
+  using C = TmaCfg<FMT>;
   static bool attr = false;
   if (!attr) {
-    cudaError_t e = cudaFuncSetAttribute(k_newton_tma<FMT, COEF7>,
+    cudaError_t e = cudaFuncSetAttribute(k_newton_tma<FMT>,
                                          cudaFuncAttributeMaxDynamicSharedMemorySize, C::SMEM);
     if (e != cudaSuccess) return e;
     attr = true;
   }
   const int zc = tma_zchunk(g);
   dim3 grid((g.nx + 31) / 32, (g.ny + 7) / 8, (g.nz + zc - 1) / zc), block(32, 8, 1);
-  k_newton_tma<FMT, COEF7><<<grid, block, C::SMEM, st>>>(M, g, s, w_out, p, partials, ctl, zc);
+  k_newton_tma<FMT><<<grid, block, C::SMEM, st>>>(M, g, s, w_out, p, partials, ctl, zc);
   return cudaGetLastError();
 }
 
 cudaError_t launch_newton_tma(const StencilDev& g, const NewtonMaps& M, void* w_out, void* p,
                               const NewtonScalars& s, int fmt, double* partials, DevCtl* ctl,
                               cudaStream_t st) {
-  if (fmt == VF_DF) return launch_one<VF_DF, true>(g, M, w_out, p, s, partials, ctl, st);
-  if (fmt == VF_F64) return launch_one<VF_F64, true>(g, M, w_out, p, s, partials, ctl, st);
-  if (g.coef7) return launch_one<VF_F32, true>(g, M, w_out, p, s, partials, ctl, st);
-  return launch_one<VF_F32, false>(g, M, w_out, p, s, partials, ctl, st);
+  if (fmt == VF_DF) return launch_one<VF_DF>(g, M, w_out, p, s, partials, ctl, st);
+  if (fmt == VF_F64) return launch_one<VF_F64>(g, M, w_out, p, s, partials, ctl, st);
+  return launch_one<VF_F32>(g, M, w_out, p, s, partials, ctl, st);
 }
 
 cudaError_t launch_newton2_tma(const StencilDev& g, const NewtonMaps& M, void* w_out, void* p,
