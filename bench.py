@@ -41,7 +41,8 @@ N_SIDE = 256
 BYTES_PER_POINT = 88
 # DRAM bytes per grid point of one launch of the two-iteration float-float
 # kernel, from ncu dram__bytes_read.sum + dram__bytes_write.sum on 192^3
-# (profiles/launches_adr3d_256_rosenbrock.md); traffic scales with the points.
+# (profiles/launches_adr3d_256_rosenbrock.md, taken on the current kernel);
+# traffic scales with the points.
 # Valid for the kernel as captured: retake it when the kernel changes.
 PAIR_DRAM_BYTES_PER_POINT = 86.9
 FLOPS_PER_POINT_PAPER = 10  # the paper's count for (alpha A + beta I)x, Sec. III-A

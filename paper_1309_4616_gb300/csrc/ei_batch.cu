@@ -8,14 +8,19 @@
 //   NEWTON(j): w_{j+1} = (A w_j)/gamma - (c/gamma + xi_j) w_j, p += d_{j+1} w_{j+1}
 //   AXPY:      y += tau p          (substeps s > 1)
 //   RES:       r = A y + v         (start of substeps 2..s)
-// Work distribution: each problem has a 64-bit word (epoch << 32 | next tile);
-// a block claims a tile with one atomicAdd, processes it, writes the tile's
-// norm partials and counts the tile done.  The block that completes the last
-// tile of an epoch sums the partials in tile order (deterministic), takes the
-// phase's decision and publishes the next epoch.  No block waits for another;
-// a block that finds nothing to claim sleeps briefly, and gives up after 5 s
-// without global progress (status EI_ERR_TIMEOUT).  Data written by other
-// blocks in earlier epochs is read through L2 (ld.global.cg).
+// Work distribution: a claim queue in claim order (biggest problems first)
+// holds one 64-bit word per problem, descriptor << 32 | next tile, where the
+// descriptor names the current epoch (phase, Newton index j, substep).  A
+// block claims a tile with one atomicAdd, whose result is the tile and its
+// epoch at once.  Each block runs 8 compute warps and one scheduler warp: while
+// the compute warps process tile n, the scheduler warp accounts for tile n-1
+// (counts it done; the block that completes the last tile of an epoch sums the
+// tile partials in tile order, deterministic, takes the phase's decision and
+// publishes the next epoch) and claims tile n+1, so the compute warps meet one
+// barrier per tile.  No block waits for another; a block that finds nothing
+// to claim sleeps briefly, and gives up after 5 s without global progress
+// (status EI_ERR_TIMEOUT).  Data written by other blocks in earlier epochs is
+// read through L2 (ld.global.cg).
 #include <cuda_runtime.h>
 #include <math.h>
 #include <stdint.h>
@@ -46,6 +51,7 @@ struct BInst {
   int nx, ny, tiles_x, tiles, rows;  // rows: points per thread in y (tile height 8*rows)
   int bc[4];
   int s;
+  int pos;                           // position in the claim queue
   double d0, axm, axp, aym, ayp;     // interior coefficients (ghost form)
   double inv_gamma, c_over_gamma, tau, h;
   int64_t off;                       // element offset of the problem's block of vectors
@@ -55,10 +61,20 @@ struct BInst {
 };
 
 struct BState {
-  unsigned long long word;  // epoch << 32 | next tile to claim
   unsigned int done;        // tiles completed in the current epoch
-  int phase, j, sub, status, degree_sum;
+  int status, degree_sum, pad;
 };
+
+// Epoch descriptor (high half of a claim word): Newton index j in bits 0-6
+// (j < m_max <= 100), phase in bits 7-8, substep in bits 9-30 (s <= 2^20).
+__host__ __device__ __forceinline__ unsigned make_desc(int phase, int j, int sub) {
+  return (unsigned)j | ((unsigned)phase << 7) | ((unsigned)sub << 9);
+}
+__device__ __forceinline__ int desc_j(unsigned d) { return (int)(d & 127u); }
+__device__ __forceinline__ int desc_phase(unsigned d) { return (int)((d >> 7) & 3u); }
+__device__ __forceinline__ int desc_sub(unsigned d) { return (int)(d >> 9); }
+// low half of the word of a problem that is not running: above any tile count
+constexpr unsigned long long IDLE_WORD = 0x40000000ull;
 
 struct BatchDev {
   int count;
@@ -66,7 +82,9 @@ struct BatchDev {
   double tol;
   const BInst* inst;
   BState* state;
-  const int* order;          // biggest problems first
+  unsigned long long* qword;  // claim word per queue position
+  const int* qtiles;          // tile count per queue position
+  const int* order;           // problem at each queue position
   const double* dd;
   const double* xi;
   double* partials;
@@ -208,49 +226,36 @@ __device__ void batch_tile(const BatchDev& B, int i, int t, int phase, int j, in
   o1 = acc_d(ap);
 }
 
-// Claim one tile: lanes of the calling warp look at 32 problems at a time (in
-// the biggest-first order, from `cursor`), vote for those whose current epoch
-// still has unclaimed tiles, and try them in order with one atomicAdd each.
-// Returns the problem index (-1: nothing claimable) in every lane.
-__device__ int warp_claim(const BatchDev& B, int& cursor, int& t_out, int& phase, int& j,
-                          int& sub) {
+// Claim one tile: lanes of the calling warp look at 32 queue positions at a
+// time (from `cursor`), vote for those whose current epoch still has unclaimed
+// tiles, and try them in order with one atomicAdd each.  Returns the queue
+// position (-1: nothing claimable) in every lane, with the tile and the
+// epoch descriptor.
+__device__ int warp_claim(const BatchDev& B, int& cursor, int& t_out, unsigned& desc_out) {
   const int lane = threadIdx.x & 31;
   for (int base = 0; base < B.count; base += 32) {
     int k = cursor + base + lane;
     while (k >= B.count) k -= B.count;
-    const int i = B.order[k];
-    const BState* S = &B.state[i];
     bool cand = false;
-    if (base + lane < B.count && *(volatile const int*)&S->status == ST_RUN) {
-      const unsigned long long w = *(volatile const unsigned long long*)&S->word;
-      cand = (unsigned)(w & 0xffffffffull) < (unsigned)B.inst[i].tiles;
+    if (base + lane < B.count) {
+      const unsigned long long w = *(volatile const unsigned long long*)(B.qword + k);
+      cand = (unsigned)(w & 0xffffffffull) < (unsigned)__ldg(B.qtiles + k);
     }
     unsigned mask = __ballot_sync(0xffffffffu, cand);
     while (mask) {
       const int l = __ffs(mask) - 1;
       mask &= mask - 1;
-      int got = 0, ti = 0, ph = 0, jj = 0, sb = 0;
-      if (lane == l) {
-        const unsigned long long w = atomicAdd(&B.state[i].word, 1ull);
-        const unsigned t = (unsigned)(w & 0xffffffffull);
-        if (t < (unsigned)B.inst[i].tiles) {
-          __threadfence();
-          got = 1;
-          ti = (int)t;
-          ph = *(volatile const int*)&B.state[i].phase;
-          jj = *(volatile const int*)&B.state[i].j;
-          sb = *(volatile const int*)&B.state[i].sub;
-        }
-      }
-      got = __shfl_sync(0xffffffffu, got, l);
-      if (got) {
-        t_out = __shfl_sync(0xffffffffu, ti, l);
-        phase = __shfl_sync(0xffffffffu, ph, l);
-        j = __shfl_sync(0xffffffffu, jj, l);
-        sub = __shfl_sync(0xffffffffu, sb, l);
-        const int ik = __shfl_sync(0xffffffffu, k, l);
-        cursor = ik;
-        return __shfl_sync(0xffffffffu, i, l);
+      unsigned long long w = 0;
+      if (lane == l) w = atomicAdd(B.qword + k, 1ull);
+      w = __shfl_sync(0xffffffffu, w, l);
+      const int kk = __shfl_sync(0xffffffffu, k, l);
+      const unsigned t = (unsigned)(w & 0xffffffffull);
+      if (t < (unsigned)__ldg(B.qtiles + kk)) {
+        __threadfence();  // the epoch's data is read after the claim
+        t_out = (int)t;
+        desc_out = (unsigned)(w >> 32);
+        cursor = kk;
+        return kk;
       }
     }
   }
@@ -280,55 +285,131 @@ __device__ __forceinline__ void compute_reduce2(double& a, double& b, double* sa
   }
 }
 
-// 256 compute threads (warps 0-7) process the claimed tile while warp 8 claims
-// the next one; the claim's latency hides behind the tile's arithmetic.
+// Scheduler warp: count tile t of problem i (epoch descriptor d) done.  The
+// compute warps' stores of the tile precede this call through a block barrier.
+// The warp that completes the epoch sums the tile partials (lane-strided,
+// then a fixed shuffle tree), decides and publishes the next epoch.
+__device__ void account_tile(const BatchDev& B, int i, unsigned d) {
+  const int lane = threadIdx.x & 31;
+  const BInst& I = B.inst[i];
+  BState* S = &B.state[i];
+  int last = 0;
+  if (lane == 0) {
+    __threadfence();
+    const unsigned dn = atomicAdd(&S->done, 1u);
+    last = (dn == (unsigned)I.tiles - 1);
+    atomicAdd(B.progress, 1ull);
+  }
+  last = __shfl_sync(0xffffffffu, last, 0);
+  if (!last) return;
+  __threadfence();
+  const int phase0 = desc_phase(d), j0 = desc_j(d), sub0 = desc_sub(d);
+  double nw2 = 0.0, np2 = 0.0;
+  if (phase0 == PH_NEWTON) {
+    for (int t = lane; t < I.tiles; t += 32) {
+      nw2 += __ldcg(B.partials + I.poff + 2 * t);
+      np2 += __ldcg(B.partials + I.poff + 2 * t + 1);
+    }
+#pragma unroll
+    for (int off = 16; off > 0; off >>= 1) {
+      nw2 += __shfl_xor_sync(0xffffffffu, nw2, off);
+      np2 += __shfl_xor_sync(0xffffffffu, np2, off);
+    }
+  }
+  if (lane != 0) return;
+  int phase = phase0, j = j0, sub = sub0, status = ST_RUN;
+  if (phase0 == PH_NEWTON) {
+    const double dn = B.dd[I.dd_off + j + 1];
+    int deg = -1;
+    if (!isfinite(nw2) || !isfinite(np2)) status = ST_NONFINITE;
+    else if (j == 0 && np2 == 0.0) deg = 0;
+    else if (fabs(dn) * sqrt(nw2) <= B.tol * sqrt(np2)) deg = j + 1;
+    else if (j + 1 >= B.m_max) status = ST_FAIL;
+    else j = j + 1;
+    if (deg >= 0) {
+      volatile int* ds = &S->degree_sum;
+      *ds = *ds + deg;
+      if (I.s == 1) status = ST_DONE;
+      else phase = PH_AXPY;
+    }
+  } else if (phase0 == PH_AXPY) {
+    sub = sub + 1;
+    if (sub >= I.s) status = ST_DONE;
+    else phase = PH_RES;
+  } else {
+    phase = PH_NEWTON;
+    j = 0;
+  }
+  *(volatile unsigned*)&S->done = 0u;
+  if (status != ST_RUN) {
+    *(volatile int*)&S->status = status;
+    __threadfence();
+    atomicExch(B.qword + I.pos, IDLE_WORD);
+    atomicAdd(B.finished, 1u);
+  } else {
+    __threadfence();
+    atomicExch(B.qword + I.pos, (unsigned long long)make_desc(phase, j, sub) << 32);
+  }
+}
+
+// 256 compute threads (warps 0-7) process tile n while warp 8 accounts for
+// tile n-1 and claims tile n+1; the hand-over goes through two shared slots
+// (tile n in slot n mod 2) and one block barrier per tile.
+// Three blocks per SM for FP32, two for the 8-byte formats (register budget).
 template <int FMT>
-__global__ void __launch_bounds__(288) k_batch(BatchDev B) {
-  __shared__ int sh_i, sh_t, sh_phase, sh_j, sh_sub, sh_exit, sh_last;
-  __shared__ int nx_i, nx_t, nx_phase, nx_j, nx_sub;
-  __shared__ double sh_n0, sh_n1, red_a[8], red_b[8];
+__global__ void __launch_bounds__(288, FMT == VF_F32 ? 3 : 2) k_batch(BatchDev B) {
+  __shared__ int sl_i[2], sl_t[2], sl_exit[2];
+  __shared__ unsigned sl_d[2];
+  __shared__ volatile int tile_fin;  // last iteration whose tile the compute warps finished
+  __shared__ double red_a[8], red_b[8];
   const int tid = threadIdx.x;
+  const int lane = tid & 31;
   const bool sched = tid >= 256;  // warp 8
   int cursor = (int)((blockIdx.x * 37u) % (unsigned)B.count);
   unsigned long long seen = 0;
   uint64_t idle_t0 = 0;
-  // first claim
+  int prev_i = -1;
+  unsigned prev_d = 0;
   if (sched) {
-    int t = 0, ph = 0, j = 0, sb = 0;
-    const int i = warp_claim(B, cursor, t, ph, j, sb);
-    if (tid == 256) {
-      nx_i = i;
-      nx_t = t;
-      nx_phase = ph;
-      nx_j = j;
-      nx_sub = sb;
+    int t = 0;
+    unsigned dsc = 0;
+    const int k = warp_claim(B, cursor, t, dsc);
+    if (lane == 0) {
+      sl_i[0] = k >= 0 ? __ldg(B.order + k) : -1;
+      sl_t[0] = t;
+      sl_d[0] = dsc;
+      sl_exit[0] = 0;
+      tile_fin = -1;
     }
   }
   __syncthreads();
-  while (true) {
-    if (tid == 256) {
-      sh_i = nx_i;
-      sh_t = nx_t;
-      sh_phase = nx_phase;
-      sh_j = nx_j;
-      sh_sub = nx_sub;
-      sh_exit = (*(volatile unsigned*)B.finished >= (unsigned)B.count || *(volatile int*)B.error);
-    }
-    __syncthreads();
-    if (sh_exit && sh_i < 0) break;
-    if (sh_i < 0) {
-      // nothing claimed: claim again at once; pause only when that fails too,
-      // and give up after 5 s without progress anywhere
-      if (sched) {
-        int t = 0, ph = 0, j = 0, sb = 0;
-        const int ni = warp_claim(B, cursor, t, ph, j, sb);
-        if (tid == 256) {
-          nx_i = ni;
-          nx_t = t;
-          nx_phase = ph;
-          nx_j = j;
-          nx_sub = sb;
-          if (ni < 0) {
+  for (int n = 0;; ++n) {
+    const int cur = n & 1, nxt = cur ^ 1;
+    const int i = sl_i[cur];
+    if (sl_exit[cur]) break;
+    if (sched) {
+      // account for tile n-1, then claim tile n+1; while tile n runs, retry a
+      // claim that finds nothing (another block may publish an epoch); the
+      // retries are a hint only and stop after a bounded number of turns
+      if (prev_i >= 0) account_tile(B, prev_i, prev_d);
+      int t = 0, k = -1;
+      unsigned dsc = 0;
+      for (int r = 0; r < 100000; ++r) {
+        k = warp_claim(B, cursor, t, dsc);
+        if (k >= 0 || i < 0) break;
+        int fin = 0;
+        if (lane == 0) fin = (tile_fin == n);
+        if (__shfl_sync(0xffffffffu, fin, 0)) break;
+        __nanosleep(200);
+      }
+      int ex = 0;
+      if (k < 0 && i < 0) {
+        // nothing in flight here and nothing claimable: finished, failed, or
+        // waiting for another block's epoch; give up after 5 s without progress
+        if (lane == 0) {
+          if (*(volatile unsigned*)B.finished >= (unsigned)B.count || *(volatile int*)B.error) {
+            ex = 1;
+          } else {
             const unsigned long long pr = *(volatile unsigned long long*)B.progress;
             uint64_t now;
             asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(now));
@@ -341,122 +422,57 @@ __global__ void __launch_bounds__(288) k_batch(BatchDev B) {
             __nanosleep(500);
           }
         }
+        ex = __shfl_sync(0xffffffffu, ex, 0);
+      } else {
+        idle_t0 = 0;
       }
-      __syncthreads();
-      continue;
-    }
-    idle_t0 = 0;
-    const int i = sh_i;
-    if (sched) {
-      int t = 0, ph = 0, j = 0, sb = 0;
-      const int ni = warp_claim(B, cursor, t, ph, j, sb);
-      if (tid == 256) {
-        nx_i = ni;
-        nx_t = t;
-        nx_phase = ph;
-        nx_j = j;
-        nx_sub = sb;
+      if (lane == 0) {
+        sl_i[nxt] = k >= 0 ? __ldg(B.order + k) : -1;
+        sl_t[nxt] = t;
+        sl_d[nxt] = dsc;
+        sl_exit[nxt] = ex;
       }
-    } else {
+      prev_i = i;
+      prev_d = sl_d[cur];
+    } else if (i >= 0) {
+      const unsigned d = sl_d[cur];
+      const int t = sl_t[cur];
       double a = 0.0, b = 0.0;
-      batch_tile<FMT>(B, i, sh_t, sh_phase, sh_j, sh_sub, a, b);
-      if (sh_phase == PH_NEWTON) {
+      batch_tile<FMT>(B, i, t, desc_phase(d), desc_j(d), desc_sub(d), a, b);
+      if (desc_phase(d) == PH_NEWTON) {
         compute_reduce2(a, b, red_a, red_b);
         if (tid == 0) {
-          B.partials[B.inst[i].poff + 2 * sh_t] = a;
-          B.partials[B.inst[i].poff + 2 * sh_t + 1] = b;
+          B.partials[B.inst[i].poff + 2 * t] = a;
+          B.partials[B.inst[i].poff + 2 * t + 1] = b;
         }
       }
+      if (tid == 0) tile_fin = n;
     }
     __syncthreads();
-    if (tid == 0) {
-      __threadfence();
-      const unsigned d = atomicAdd(&B.state[i].done, 1u);
-      sh_last = (d == (unsigned)B.inst[i].tiles - 1);
-      atomicAdd(B.progress, 1ull);
-    }
-    __syncthreads();
-    if (!sh_last) continue;
-    // ---- this block completed the epoch: decide the problem's next phase
-    __threadfence();
-    const BInst& I = B.inst[i];
-    BState* S = &B.state[i];
-    if (sh_phase == PH_NEWTON) {
-      double ra = 0.0, rb = 0.0;
-      for (int t = tid; t < I.tiles; t += blockDim.x) {
-        ra += __ldcg(B.partials + I.poff + 2 * t);
-        rb += __ldcg(B.partials + I.poff + 2 * t + 1);
-      }
-      block_reduce2<RED_SUM>(ra, rb);
-      if (tid == 0) {
-        sh_n0 = ra;
-        sh_n1 = rb;
-      }
-      __syncthreads();
-    }
-    if (tid == 0) {
-      int phase = sh_phase, j = sh_j, sub = sh_sub, status = ST_RUN;
-      if (sh_phase == PH_NEWTON) {
-        const double nw2 = sh_n0, np2 = sh_n1;
-        const double dn = B.dd[I.dd_off + j + 1];
-        int deg = -1;
-        if (!isfinite(nw2) || !isfinite(np2)) status = ST_NONFINITE;
-        else if (j == 0 && np2 == 0.0) deg = 0;
-        else if (fabs(dn) * sqrt(nw2) <= B.tol * sqrt(np2)) deg = j + 1;
-        else if (j + 1 >= B.m_max) status = ST_FAIL;
-        else j = j + 1;
-        if (deg >= 0) {
-          S->degree_sum += deg;
-          if (I.s == 1) status = ST_DONE;
-          else phase = PH_AXPY;
-        }
-      } else if (sh_phase == PH_AXPY) {
-        sub = sub + 1;
-        if (sub >= I.s) status = ST_DONE;
-        else phase = PH_RES;
-      } else {
-        phase = PH_NEWTON;
-        j = 0;
-      }
-      S->done = 0;
-      if (status != ST_RUN) {
-        S->status = status;
-        __threadfence();
-        atomicAdd(B.finished, 1u);
-      } else {
-        S->phase = phase;
-        S->j = j;
-        S->sub = sub;
-        __threadfence();
-        const unsigned long long epoch = (*(volatile unsigned long long*)&S->word >> 32) + 1ull;
-        atomicExch(&S->word, epoch << 32);
-      }
-    }
-    __syncthreads();
-    // the scheduler's pre-claim may have found nothing while this epoch was
-    // being closed; the next loop turn retries
   }
 }
 
 // ---- set-up, import/export ---------------------------------------------------
-__global__ void k_batch_init(const BInst* inst, BState* state, const int* init_status, int count,
-                             unsigned int* finished, unsigned long long* progress, int* error) {
-  const int i = blockIdx.x * blockDim.x + threadIdx.x;
-  if (i == 0) {
+__global__ void k_batch_init(const int* order, BState* state, unsigned long long* qword,
+                             const int* init_status, int count, unsigned int* finished,
+                             unsigned long long* progress, int* error) {
+  const int k = blockIdx.x * blockDim.x + threadIdx.x;
+  if (k == 0) {
     *finished = 0;
     *progress = 0;
     *error = 0;
   }
-  if (i < count) {
+  if (k < count) {
+    const int i = order[k];
     BState s;
-    s.word = 1ull << 32;
     s.done = 0;
-    s.phase = PH_NEWTON;
-    s.j = 0;
-    s.sub = 0;
-    s.degree_sum = 0;
     s.status = init_status[i];
+    s.degree_sum = 0;
+    s.pad = 0;
     state[i] = s;
+    // the first epoch of a running problem: Newton, j = 0, substep 0
+    qword[k] = s.status == ST_RUN ? ((unsigned long long)make_desc(PH_NEWTON, 0, 0) << 32)
+                                  : IDLE_WORD;
   }
 }
 
@@ -525,6 +541,8 @@ struct ei_batch {
   // device
   BInst* inst = nullptr;
   BState* state = nullptr;
+  unsigned long long* qword = nullptr;
+  int* qtiles = nullptr;
   int* order = nullptr;
   int* dinit = nullptr;
   int64_t* duoff = nullptr;
@@ -644,7 +662,7 @@ static void parallel_for(int n, const std::function<void(int)>& f) {
 
 static void batch_free(ei_batch* B) {
   if (B->exec) cudaGraphExecDestroy(B->exec);
-  void* ptrs[] = {B->inst, B->state, B->order, B->dinit, B->duoff, B->dscal, B->dd, B->xi,
+  void* ptrs[] = {B->inst, B->state, B->qword, B->qtiles, B->order, B->dinit, B->duoff, B->dscal, B->dd, B->xi,
                   B->partials, B->pool, B->ppool, B->finished, B->progress, B->error, B->vn2};
   for (void* p : ptrs)
     if (p) cudaFree(p);
@@ -668,6 +686,8 @@ static cudaError_t batch_launch_body(ei_batch* B) {
   D.tol = B->tol;
   D.inst = B->inst;
   D.state = B->state;
+  D.qword = B->qword;
+  D.qtiles = B->qtiles;
   D.order = B->order;
   D.dd = B->dd;
   D.xi = B->xi;
@@ -677,8 +697,9 @@ static cudaError_t batch_launch_body(ei_batch* B) {
   D.finished = B->finished;
   D.progress = B->progress;
   D.error = B->error;
-  k_batch_init<<<(count + 255) / 256, 256, 0, B->stream>>>(B->inst, B->state, B->dinit, count,
-                                                           B->finished, B->progress, B->error);
+  k_batch_init<<<(count + 255) / 256, 256, 0, B->stream>>>(B->order, B->state, B->qword,
+                                                           B->dinit, count, B->finished,
+                                                           B->progress, B->error);
   k_batch_count_idle<<<(count + 255) / 256, 256, 0, B->stream>>>(B->state, count, B->finished);
   k_batch<FMT><<<B->grid, 288, 0, B->stream>>>(D);
   return cudaGetLastError();
@@ -731,8 +752,10 @@ static ei_status batch_upload(ei_batch* B) {
   for (int i = 0; i < count; ++i) {
     BInst& I = B->hinst[i];
     I.tiles_x = (I.nx + 31) / 32;
-    const int th = 8 * I.rows;
-    I.tiles = I.tiles_x * ((I.ny + th - 1) / th);
+    const int64_t th = 8 * (int64_t)I.rows;
+    const int64_t tiles = (int64_t)I.tiles_x * ((I.ny + th - 1) / th);
+    if (tiles >= (int64_t)IDLE_WORD) return EI_ERR_INVALID_ARG;  // the claim word's range
+    I.tiles = (int)tiles;
     I.poff = poff;
     poff += 2 * (int64_t)I.tiles;
   }
@@ -746,16 +769,22 @@ static ei_status batch_upload(ei_batch* B) {
     if (B->exec) cudaGraphExecDestroy(B->exec);
     B->exec = nullptr;
   }
-  BTRY(cudaMemcpy(B->inst, B->hinst.data(), sizeof(BInst) * count, cudaMemcpyHostToDevice));
-  BTRY(cudaMemcpy(B->dd, B->hdd.data(), sizeof(double) * B->hdd.size(), cudaMemcpyHostToDevice));
-  // biggest problems first
+  // claim queue: biggest problems first
   std::vector<int> ord(count);
   for (int i = 0; i < count; ++i) ord[i] = i;
   std::vector<double> work(count);
   for (int i = 0; i < count; ++i)
     work[i] = (double)B->hinst[i].npts * B->hinst[i].s * (B->m_max / 2 + 1);
   std::stable_sort(ord.begin(), ord.end(), [&](int a, int b) { return work[a] > work[b]; });
+  std::vector<int> qt(count);
+  for (int k = 0; k < count; ++k) {
+    B->hinst[ord[k]].pos = k;
+    qt[k] = B->hinst[ord[k]].tiles;
+  }
+  BTRY(cudaMemcpy(B->inst, B->hinst.data(), sizeof(BInst) * count, cudaMemcpyHostToDevice));
+  BTRY(cudaMemcpy(B->dd, B->hdd.data(), sizeof(double) * B->hdd.size(), cudaMemcpyHostToDevice));
   BTRY(cudaMemcpy(B->order, ord.data(), sizeof(int) * count, cudaMemcpyHostToDevice));
+  BTRY(cudaMemcpy(B->qtiles, qt.data(), sizeof(int) * count, cudaMemcpyHostToDevice));
   return EI_OK;
 }
 
@@ -1030,6 +1059,8 @@ ei_status ei_batch_create(ei_batch** out, int device, int count, const ei_batch_
   if (cudaMalloc(&B->pool, eb * po) != cudaSuccess || cudaMalloc(&B->ppool, 8 * (po / 5)) != cudaSuccess ||
       cudaMalloc(&B->inst, sizeof(BInst) * count) != cudaSuccess ||
       cudaMalloc(&B->state, sizeof(BState) * count) != cudaSuccess ||
+      cudaMalloc(&B->qword, sizeof(unsigned long long) * count) != cudaSuccess ||
+      cudaMalloc(&B->qtiles, sizeof(int) * count) != cudaSuccess ||
       cudaMalloc(&B->order, sizeof(int) * count) != cudaSuccess ||
       cudaMalloc(&B->dinit, sizeof(int) * count) != cudaSuccess ||
       cudaMalloc(&B->duoff, sizeof(int64_t) * (count + 1)) != cudaSuccess ||
