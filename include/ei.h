@@ -83,8 +83,9 @@ typedef struct {
                      context's stream (stats.newton_ms / newton_timed) */
   int single_iter; /* 1: one Newton iteration per kernel launch (by default stencils
                       in the F64 formats fuse two iterations per launch) */
-  int tile_rows;   /* batched form: tile height in units of 8 rows (1 to 32);
-                      0 = the autotuner's choice */
+  int tile_rows;   /* batched form: height in rows (1 to 1024) of a strip, the
+                      32-column unit of work of one warp; 0 = the autotuner's
+                      choice */
   int learned;     /* phi_1 schedule: 0 the plain a-priori rule; 1 the learned
                       schedule of the model set by ei_set_schedule_model, adaptive
                       (the proposal's s, the per-substep a posteriori stop; m sets
@@ -329,7 +330,7 @@ typedef struct {
   int s;              /* substeps of the accepted attempt */
   int degree_sum;     /* Newton degrees summed over substeps */
   int restarts;       /* attempts rejected (m_max reached) */
-  int tile_rows;      /* tile height the autotuner chose for its size class */
+  int tile_rows;      /* strip height (rows) the autotuner chose for its size class */
   int learned;        /* with a schedule model: 1 the network's s kept, 2 it reached
                          m_max and the a-priori rule took over, 0 no q accepted */
   int pad;

@@ -8,19 +8,25 @@
 //   NEWTON(j): w_{j+1} = (A w_j)/gamma - (c/gamma + xi_j) w_j, p += d_{j+1} w_{j+1}
 //   AXPY:      y += tau p          (substeps s > 1)
 //   RES:       r = A y + v         (start of substeps 2..s)
-// Work distribution: a claim queue in claim order (biggest problems first)
-// holds one 64-bit word per problem, descriptor << 32 | next tile, where the
-// descriptor names the current epoch (phase, Newton index j, substep).  A
-// block claims a tile with one atomicAdd, whose result is the tile and its
-// epoch at once.  Each block runs 8 compute warps and one scheduler warp: while
-// the compute warps process tile n, the scheduler warp accounts for tile n-1
-// (counts it done; the block that completes the last tile of an epoch sums the
-// tile partials in tile order, deterministic, takes the phase's decision and
-// publishes the next epoch) and claims tile n+1, so the compute warps meet one
-// barrier per tile.  No block waits for another; a block that finds nothing
-// to claim sleeps briefly, and gives up after 5 s without global progress
-// (status EI_ERR_TIMEOUT).  Data written by other blocks in earlier epochs is
-// read through L2 (ld.global.cg).
+// Work distribution: the unit of work is a strip, 32 columns x `rows` rows of
+// one problem, processed by one warp; no block-level synchronisation.  A claim
+// queue in claim order (biggest problems first) holds one 64-bit word per
+// problem, descriptor << 32 | next strip, where the descriptor names the
+// current epoch (phase, Newton index j, substep), and a bitmap marks the
+// positions whose epoch has unclaimed strips (set when an epoch is published,
+// cleared by the claimer of its last strip).  A warp looking for work reads the
+// bitmap (one L2 round trip per 1024 problems) and claims from the biggest
+// problems first, so their chains of epochs start at once instead of forming a
+// tail.  It claims a strip with one atomicAdd, whose result is the strip and
+// its epoch at once, and claims the next strip of the same epoch before the
+// current one's arithmetic (the epoch cannot close while the warp holds an
+// unfinished strip), so the claim's latency hides behind the strip.  After a strip the warp writes its norm
+// partials and counts it done; the warp that completes the last strip of an
+// epoch sums the partials in strip order (deterministic), takes the phase's
+// decision and publishes the next epoch.  No warp waits for another; a warp
+// that finds nothing to claim sleeps briefly, and gives up after 5 s without
+// global progress (status EI_ERR_TIMEOUT).  Data written by other warps in
+// earlier epochs is read through L2 (ld.global.cg).
 #include <cuda_runtime.h>
 #include <math.h>
 #include <stdint.h>
@@ -48,7 +54,7 @@ enum { PH_NEWTON = 0, PH_AXPY = 1, PH_RES = 2 };
 enum { ST_RUN = 0, ST_DONE = 1, ST_FAIL = 2, ST_NONFINITE = 3, ST_SCALAR = 4, ST_SKIP = 5 };
 
 struct BInst {
-  int nx, ny, tiles_x, tiles, rows;  // rows: points per thread in y (tile height 8*rows)
+  int nx, ny, tiles_x, tiles, rows;  // tiles: strips of 32 columns x rows rows
   int bc[4];
   int s;
   int pos;                           // position in the claim queue
@@ -84,6 +90,8 @@ struct BatchDev {
   BState* state;
   unsigned long long* qword;  // claim word per queue position
   const int* qtiles;          // tile count per queue position
+  unsigned* avail;            // bit k: position k's epoch has unclaimed strips
+  int nwords;                 // words of the bitmap
   const int* order;           // problem at each queue position
   const double* dd;
   const double* xi;
@@ -108,9 +116,29 @@ template <> __device__ __forceinline__ float ldcg_<float>(const float* p, int64_
   return __ldcg(p + i);
 }
 
-// One tile: 32 columns x (8*rows) rows.  Lane = column; warp w marches down
-// its own strip of `rows` consecutive rows keeping u(y-1), u(y), u(y+1) of its
-// column in registers, so a point costs three loads (u(y+1), u(x-1), u(x+1))
+// 5-point sum dg*uc + sum_k a_k*u_k.  Float-float: two lazily normalised
+// accumulators (independent chains); double/float: two FMA chains.
+__device__ __forceinline__ df stencil5(df dg, df uc, df a0, df u0, df a1, df u1, df a2, df u2,
+                                       df a3, df u3) {
+  dfacc s1 = dfa_mul(dg, uc);
+  dfacc s2 = dfa_mul(a2, u2);
+  s1 = dfa_mac(s1, a0, u0);
+  s2 = dfa_mac(s2, a3, u3);
+  s1 = dfa_mac(s1, a1, u1);
+  return dfa_norm(dfa_add(s1, s2));
+}
+template <class R>
+__device__ __forceinline__ R stencil5(R dg, R uc, R a0, R u0, R a1, R u1, R a2, R u2, R a3,
+                                      R u3) {
+  R s1 = dg * uc, s2 = a2 * u2;
+  s1 = fma(a0, u0, s1);
+  s2 = fma(a3, u3, s2);
+  s1 = fma(a1, u1, s1);
+  return s1 + s2;
+}
+
+// One strip: 32 columns x `rows` rows.  Lane = column; the warp marches down
+// the strip keeping u(y-1), u(y), u(y+1) of its column in registers, so a point costs three loads (u(y+1), u(x-1), u(x+1))
 // plus its Newton sum; the loads of a row are issued two rows ahead of its
 // arithmetic.  A ghost value is 0 behind a Dirichlet face and u itself behind
 // a Neumann face.
@@ -127,10 +155,8 @@ __device__ void batch_tile(const BatchDev& B, int i, int t, int phase, int j, in
   T* Y = base + 3 * I.npts;
   T* R = base + 4 * I.npts;
   P* __restrict__ Pp = static_cast<P*>(B.ppool) + I.off / 5;
-  const T d0 = from_d<T>(I.d0), axm = from_d<T>(I.axm), axp = from_d<T>(I.axp);
-  const T aym = from_d<T>(I.aym), ayp = from_d<T>(I.ayp);
   const int x = (t % I.tiles_x) * 32 + (int)(threadIdx.x & 31);
-  const int y0 = (t / I.tiles_x) * (8 * I.rows) + (int)(threadIdx.x >> 5) * I.rows;
+  const int y0 = (t / I.tiles_x) * I.rows;
   const int y1 = min(y0 + I.rows, I.ny);
   typename Acc<T>::type aw = Acc<T>::zero();
   typename Acc<P>::type ap = Acc<P>::zero();
@@ -153,13 +179,18 @@ __device__ void batch_tile(const BatchDev& B, int i, int t, int phase, int j, in
   }
   const T* __restrict__ u = (phase == PH_RES) ? Y : ((j == 0) ? (sub == 0 ? V : R) : ((j - 1) & 1 ? W1 : W0));
   T* wout = (j & 1) ? W1 : W0;
-  const T invg = from_d<T>(I.inv_gamma);
-  const T nshift = from_d<T>(phase == PH_NEWTON ? -(I.c_over_gamma + B.xi[j]) : 0.0);
+  // NEWTON: w' = (A u)/gamma - (c/gamma + xi_j) u as one 5-point sum with
+  // coefficients a/gamma and centre d0/gamma - c/gamma - xi_j (formed in
+  // double); RES: A y with the plain coefficients
+  const bool newton = (phase == PH_NEWTON);
+  const double sg = newton ? I.inv_gamma : 1.0;
+  const T cdg = from_d<T>(newton ? I.d0 * sg - I.c_over_gamma - B.xi[j] : I.d0);
+  const T axm = from_d<T>(I.axm * sg), axp = from_d<T>(I.axp * sg);
+  const T aym = from_d<T>(I.aym * sg), ayp = from_d<T>(I.ayp * sg);
   const P dn = from_d<P>(phase == PH_NEWTON ? B.dd[I.dd_off + j + 1] : 0.0);
   const P dz = from_d<P>(phase == PH_NEWTON ? B.dd[I.dd_off] : 0.0);
   const T zro = zero<T>();
   if (x < I.nx && y0 < y1) {
-    const bool newton = (phase == PH_NEWTON);
     const bool needp = newton && j > 0;
     // column queue of row y: um = u(y-1), uc = u(y), up = u(y+1), ul, ur, and
     // the row's Newton sum pc (NEWTON, j > 0) or v (RES)
@@ -188,13 +219,9 @@ __device__ void batch_tile(const BatchDev& B, int i, int t, int phase, int j, in
       T bl = zro, br = zro, bu = zro, bv = zro;
       P bpn = zero<P>();
       if (y + 2 < y1) fetch(k + 2 * (int64_t)I.nx, y + 2, bl, br, bu, bpn, bv);
-      T acc = mul(d0, uc);
-      acc = mac(acc, axm, ul);
-      acc = mac(acc, axp, ur);
-      acc = mac(acc, aym, um);
-      acc = mac(acc, ayp, up);
+      const T acc = stencil5(cdg, uc, axm, ul, axp, ur, aym, um, ayp, up);
       if (newton) {
-        const T wn = newton_update(acc, invg, nshift, uc);
+        const T wn = acc;
         const P pold = (j == 0) ? mul(dz, to_p(uc)) : pc;
         const P pn = mac(pold, dn, to_p(wn));
         st(wout, k, wn);
@@ -226,74 +253,78 @@ __device__ void batch_tile(const BatchDev& B, int i, int t, int phase, int j, in
   o1 = acc_d(ap);
 }
 
-// Claim one tile: lanes of the calling warp look at 32 queue positions at a
-// time (from `cursor`), vote for those whose current epoch still has unclaimed
-// tiles, and try them in order with one atomicAdd each.  Returns the queue
-// position (-1: nothing claimable) in every lane, with the tile and the
-// epoch descriptor.
-__device__ int warp_claim(const BatchDev& B, int& cursor, int& t_out, unsigned& desc_out) {
+// After a claim that returned strip t of position k: the claimer of the last
+// strip clears the position's bit (it holds an unfinished strip of the epoch,
+// so the epoch cannot be closed and republished before the clear).
+__device__ __forceinline__ void claimed_strip(const BatchDev& B, int k, unsigned t,
+                                              unsigned tiles) {
+  if (t == tiles - 1) atomicAnd(B.avail + (k >> 5), ~(1u << (k & 31)));
+}
+
+// A claim at position k found its epoch exhausted while the bit was set: clear
+// the bit, then look at the word again and set the bit back if an epoch with
+// unclaimed strips was published meanwhile.  The publisher writes the word,
+// fences and sets the bit; this side clears, fences and reads the word; with
+// both fences either the read sees the new word or the set follows the clear,
+// so a published epoch never loses its bit.
+__device__ __forceinline__ void stale_bit(const BatchDev& B, int k, unsigned tiles) {
+  atomicAnd(B.avail + (k >> 5), ~(1u << (k & 31)));
+  __threadfence();
+  const unsigned long long w = *(volatile const unsigned long long*)(B.qword + k);
+  if ((unsigned)(w & 0xffffffffull) < tiles) atomicOr(B.avail + (k >> 5), 1u << (k & 31));
+}
+
+// Claim one strip: the lanes read 32 bitmap words (1024 positions) at a time;
+// the first word with set bits holds the biggest problems with unclaimed
+// strips.  The warp tries its set bits with one atomicAdd each, starting at a
+// bit chosen by the warp index to spread warps over those problems.  Returns
+// the queue position (-1: nothing claimable) in every lane, with the strip and
+// the epoch descriptor.
+__device__ int warp_claim(const BatchDev& B, unsigned gw, int& t_out, unsigned& desc_out) {
   const int lane = threadIdx.x & 31;
-  for (int base = 0; base < B.count; base += 32) {
-    int k = cursor + base + lane;
-    while (k >= B.count) k -= B.count;
-    bool cand = false;
-    if (base + lane < B.count) {
-      const unsigned long long w = *(volatile const unsigned long long*)(B.qword + k);
-      cand = (unsigned)(w & 0xffffffffull) < (unsigned)__ldg(B.qtiles + k);
-    }
-    unsigned mask = __ballot_sync(0xffffffffu, cand);
-    while (mask) {
-      const int l = __ffs(mask) - 1;
-      mask &= mask - 1;
-      unsigned long long w = 0;
-      if (lane == l) w = atomicAdd(B.qword + k, 1ull);
-      w = __shfl_sync(0xffffffffu, w, l);
-      const int kk = __shfl_sync(0xffffffffu, k, l);
-      const unsigned t = (unsigned)(w & 0xffffffffull);
-      if (t < (unsigned)__ldg(B.qtiles + kk)) {
-        __threadfence();  // the epoch's data is read after the claim
-        t_out = (int)t;
-        desc_out = (unsigned)(w >> 32);
-        cursor = kk;
-        return kk;
+  for (int base = 0; base < B.nwords; base += 32) {
+    const int wi = base + lane;
+    const unsigned m = wi < B.nwords ? *(volatile const unsigned*)(B.avail + wi) : 0u;
+    unsigned lanes = __ballot_sync(0xffffffffu, m != 0u);
+    while (lanes) {
+      const int l = __ffs(lanes) - 1;
+      lanes &= lanes - 1;
+      const unsigned bits = __shfl_sync(0xffffffffu, m, l);
+      const int nb = __popc(bits);
+      for (int r = 0; r < nb; ++r) {
+        // the ((gw + r) mod nb)-th set bit
+        unsigned rest = bits;
+        for (int q = (int)((gw + (unsigned)r) % (unsigned)nb); q > 0; --q) rest &= rest - 1;
+        const int k = (base + l) * 32 + __ffs(rest) - 1;
+        unsigned long long w = 0;
+        if (lane == 0) w = atomicAdd(B.qword + k, 1ull);
+        w = __shfl_sync(0xffffffffu, w, 0);
+        const unsigned t = (unsigned)(w & 0xffffffffull);
+        const unsigned tiles = (unsigned)__ldg(B.qtiles + k);
+        if (t < tiles) {
+          if (lane == 0) claimed_strip(B, k, t, tiles);
+          __threadfence();  // the epoch's data is read after the claim
+          t_out = (int)t;
+          desc_out = (unsigned)(w >> 32);
+          return k;
+        }
+        if (lane == 0) stale_bit(B, k, tiles);
       }
     }
   }
   return -1;
 }
 
-// Sum (a, b) over the 8 compute warps; result in thread 0.  Fixed order.
-__device__ __forceinline__ void compute_reduce2(double& a, double& b, double* sa, double* sb) {
-  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
-#pragma unroll
-  for (int off = 16; off > 0; off >>= 1) {
-    a += __shfl_down_sync(0xffffffffu, a, off);
-    b += __shfl_down_sync(0xffffffffu, b, off);
-  }
-  if (lane == 0) {
-    sa[wid] = a;
-    sb[wid] = b;
-  }
-  asm volatile("bar.sync 1, 256;" ::: "memory");  // the 8 compute warps only
-  if (threadIdx.x == 0) {
-    a = 0.0;
-    b = 0.0;
-    for (int w = 0; w < 8; ++w) {
-      a += sa[w];
-      b += sb[w];
-    }
-  }
-}
-
-// Scheduler warp: count tile t of problem i (epoch descriptor d) done.  The
-// compute warps' stores of the tile precede this call through a block barrier.
-// The warp that completes the epoch sums the tile partials (lane-strided,
-// then a fixed shuffle tree), decides and publishes the next epoch.
-__device__ void account_tile(const BatchDev& B, int i, unsigned d) {
+// Count a strip of problem i (epoch descriptor d) done; called by the whole
+// warp after its stores of the strip.  The warp that completes the epoch sums
+// the strip partials (lane-strided, then a fixed shuffle tree), decides and
+// publishes the next epoch.
+__device__ void account_strip(const BatchDev& B, int i, unsigned d) {
   const int lane = threadIdx.x & 31;
   const BInst& I = B.inst[i];
   BState* S = &B.state[i];
   int last = 0;
+  __syncwarp();
   if (lane == 0) {
     __threadfence();
     const unsigned dn = atomicAdd(&S->done, 1u);
@@ -349,119 +380,92 @@ __device__ void account_tile(const BatchDev& B, int i, unsigned d) {
   } else {
     __threadfence();
     atomicExch(B.qword + I.pos, (unsigned long long)make_desc(phase, j, sub) << 32);
+    __threadfence();
+    atomicOr(B.avail + (I.pos >> 5), 1u << (I.pos & 31));
   }
 }
 
-// 256 compute threads (warps 0-7) process tile n while warp 8 accounts for
-// tile n-1 and claims tile n+1; the hand-over goes through two shared slots
-// (tile n in slot n mod 2) and one block barrier per tile.
-// Three blocks per SM for FP32, two for the 8-byte formats (register budget).
+// Every warp is an independent worker: claim a strip, process it, count it
+// done.  Up to 7 blocks of 4 warps per SM for FP32, 5 for the 8-byte formats
+// (register budget).
+constexpr int BATCH_THREADS = 128;
 template <int FMT>
-__global__ void __launch_bounds__(288, FMT == VF_F32 ? 3 : 2) k_batch(BatchDev B) {
-  __shared__ int sl_i[2], sl_t[2], sl_exit[2];
-  __shared__ unsigned sl_d[2];
-  __shared__ volatile int tile_fin;  // last iteration whose tile the compute warps finished
-  __shared__ double red_a[8], red_b[8];
-  const int tid = threadIdx.x;
-  const int lane = tid & 31;
-  const bool sched = tid >= 256;  // warp 8
-  int cursor = (int)((blockIdx.x * 37u) % (unsigned)B.count);
+__global__ void __launch_bounds__(BATCH_THREADS, FMT == VF_F32 ? 7 : 5) k_batch(BatchDev B) {
+  const int lane = threadIdx.x & 31;
+  const unsigned gw = blockIdx.x * (BATCH_THREADS / 32) + (threadIdx.x >> 5);
   unsigned long long seen = 0;
   uint64_t idle_t0 = 0;
-  int prev_i = -1;
-  unsigned prev_d = 0;
-  if (sched) {
-    int t = 0;
-    unsigned dsc = 0;
-    const int k = warp_claim(B, cursor, t, dsc);
-    if (lane == 0) {
-      sl_i[0] = k >= 0 ? __ldg(B.order + k) : -1;
-      sl_t[0] = t;
-      sl_d[0] = dsc;
-      sl_exit[0] = 0;
-      tile_fin = -1;
-    }
-  }
-  __syncthreads();
-  for (int n = 0;; ++n) {
-    const int cur = n & 1, nxt = cur ^ 1;
-    const int i = sl_i[cur];
-    if (sl_exit[cur]) break;
-    if (sched) {
-      // account for tile n-1, then claim tile n+1; while tile n runs, retry a
-      // claim that finds nothing (another block may publish an epoch); the
-      // retries are a hint only and stop after a bounded number of turns
-      if (prev_i >= 0) account_tile(B, prev_i, prev_d);
-      int t = 0, k = -1;
-      unsigned dsc = 0;
-      for (int r = 0; r < 100000; ++r) {
-        k = warp_claim(B, cursor, t, dsc);
-        if (k >= 0 || i < 0) break;
-        int fin = 0;
-        if (lane == 0) fin = (tile_fin == n);
-        if (__shfl_sync(0xffffffffu, fin, 0)) break;
-        __nanosleep(200);
-      }
+  int k = -1, t = 0;
+  unsigned d = 0;
+  while (true) {
+    if (k < 0) k = warp_claim(B, gw, t, d);
+    if (k < 0) {
+      // nothing claimable: finished, failed, or waiting for another warp's
+      // epoch; give up after 5 s without progress anywhere
       int ex = 0;
-      if (k < 0 && i < 0) {
-        // nothing in flight here and nothing claimable: finished, failed, or
-        // waiting for another block's epoch; give up after 5 s without progress
-        if (lane == 0) {
-          if (*(volatile unsigned*)B.finished >= (unsigned)B.count || *(volatile int*)B.error) {
-            ex = 1;
-          } else {
-            const unsigned long long pr = *(volatile unsigned long long*)B.progress;
-            uint64_t now;
-            asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(now));
-            if (pr != seen || idle_t0 == 0) {
-              seen = pr;
-              idle_t0 = now;
-            } else if (now - idle_t0 > 5000000000ull) {
-              atomicExch(B.error, 1);
-            }
-            __nanosleep(500);
+      if (lane == 0) {
+        if (*(volatile unsigned*)B.finished >= (unsigned)B.count || *(volatile int*)B.error) {
+          ex = 1;
+        } else {
+          const unsigned long long pr = *(volatile unsigned long long*)B.progress;
+          uint64_t now;
+          asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(now));
+          if (pr != seen || idle_t0 == 0) {
+            seen = pr;
+            idle_t0 = now;
+          } else if (now - idle_t0 > 5000000000ull) {
+            atomicExch(B.error, 1);
           }
+          __nanosleep(256);
         }
-        ex = __shfl_sync(0xffffffffu, ex, 0);
-      } else {
-        idle_t0 = 0;
+      }
+      if (__shfl_sync(0xffffffffu, ex, 0)) break;
+      continue;
+    }
+    idle_t0 = 0;
+    const int i = __ldg(B.order + k);
+    // the next strip of this epoch, claimed ahead
+    unsigned long long wn = 0;
+    if (lane == 0) wn = atomicAdd(B.qword + k, 1ull);
+    const int phase = desc_phase(d);
+    double a = 0.0, b = 0.0;
+    batch_tile<FMT>(B, i, t, phase, desc_j(d), desc_sub(d), a, b);
+    if (phase == PH_NEWTON) {
+#pragma unroll
+      for (int off = 16; off > 0; off >>= 1) {
+        a += __shfl_xor_sync(0xffffffffu, a, off);
+        b += __shfl_xor_sync(0xffffffffu, b, off);
       }
       if (lane == 0) {
-        sl_i[nxt] = k >= 0 ? __ldg(B.order + k) : -1;
-        sl_t[nxt] = t;
-        sl_d[nxt] = dsc;
-        sl_exit[nxt] = ex;
+        B.partials[B.inst[i].poff + 2 * t] = a;
+        B.partials[B.inst[i].poff + 2 * t + 1] = b;
       }
-      prev_i = i;
-      prev_d = sl_d[cur];
-    } else if (i >= 0) {
-      const unsigned d = sl_d[cur];
-      const int t = sl_t[cur];
-      double a = 0.0, b = 0.0;
-      batch_tile<FMT>(B, i, t, desc_phase(d), desc_j(d), desc_sub(d), a, b);
-      if (desc_phase(d) == PH_NEWTON) {
-        compute_reduce2(a, b, red_a, red_b);
-        if (tid == 0) {
-          B.partials[B.inst[i].poff + 2 * t] = a;
-          B.partials[B.inst[i].poff + 2 * t + 1] = b;
-        }
-      }
-      if (tid == 0) tile_fin = n;
     }
-    __syncthreads();
+    account_strip(B, i, d);
+    wn = __shfl_sync(0xffffffffu, wn, 0);
+    const unsigned tn = (unsigned)(wn & 0xffffffffull);
+    const unsigned tiles = (unsigned)__ldg(B.qtiles + k);
+    if (tn < tiles) {
+      if (lane == 0) claimed_strip(B, k, tn, tiles);
+      t = (int)tn;
+      d = (unsigned)(wn >> 32);
+    } else {
+      k = -1;
+    }
   }
 }
 
 // ---- set-up, import/export ---------------------------------------------------
 __global__ void k_batch_init(const int* order, BState* state, unsigned long long* qword,
-                             const int* init_status, int count, unsigned int* finished,
-                             unsigned long long* progress, int* error) {
-  const int k = blockIdx.x * blockDim.x + threadIdx.x;
+                             unsigned* avail, const int* init_status, int count,
+                             unsigned int* finished, unsigned long long* progress, int* error) {
+  const int k = blockIdx.x * blockDim.x + threadIdx.x;  // a warp covers one bitmap word
   if (k == 0) {
     *finished = 0;
     *progress = 0;
     *error = 0;
   }
+  bool run = false;
   if (k < count) {
     const int i = order[k];
     BState s;
@@ -470,10 +474,12 @@ __global__ void k_batch_init(const int* order, BState* state, unsigned long long
     s.degree_sum = 0;
     s.pad = 0;
     state[i] = s;
+    run = s.status == ST_RUN;
     // the first epoch of a running problem: Newton, j = 0, substep 0
-    qword[k] = s.status == ST_RUN ? ((unsigned long long)make_desc(PH_NEWTON, 0, 0) << 32)
-                                  : IDLE_WORD;
+    qword[k] = run ? ((unsigned long long)make_desc(PH_NEWTON, 0, 0) << 32) : IDLE_WORD;
   }
+  const unsigned bits = __ballot_sync(0xffffffffu, run);
+  if ((threadIdx.x & 31) == 0 && k < count) avail[k >> 5] = bits;
 }
 
 // count the problems that start finished (inactive / scalar)
@@ -543,6 +549,7 @@ struct ei_batch {
   BState* state = nullptr;
   unsigned long long* qword = nullptr;
   int* qtiles = nullptr;
+  unsigned* avail = nullptr;
   int* order = nullptr;
   int* dinit = nullptr;
   int64_t* duoff = nullptr;
@@ -662,7 +669,7 @@ static void parallel_for(int n, const std::function<void(int)>& f) {
 
 static void batch_free(ei_batch* B) {
   if (B->exec) cudaGraphExecDestroy(B->exec);
-  void* ptrs[] = {B->inst, B->state, B->qword, B->qtiles, B->order, B->dinit, B->duoff, B->dscal, B->dd, B->xi,
+  void* ptrs[] = {B->inst, B->state, B->qword, B->qtiles, B->avail, B->order, B->dinit, B->duoff, B->dscal, B->dd, B->xi,
                   B->partials, B->pool, B->ppool, B->finished, B->progress, B->error, B->vn2};
   for (void* p : ptrs)
     if (p) cudaFree(p);
@@ -688,6 +695,8 @@ static cudaError_t batch_launch_body(ei_batch* B) {
   D.state = B->state;
   D.qword = B->qword;
   D.qtiles = B->qtiles;
+  D.avail = B->avail;
+  D.nwords = (count + 31) / 32;
   D.order = B->order;
   D.dd = B->dd;
   D.xi = B->xi;
@@ -698,10 +707,10 @@ static cudaError_t batch_launch_body(ei_batch* B) {
   D.progress = B->progress;
   D.error = B->error;
   k_batch_init<<<(count + 255) / 256, 256, 0, B->stream>>>(B->order, B->state, B->qword,
-                                                           B->dinit, count, B->finished,
-                                                           B->progress, B->error);
+                                                           B->avail, B->dinit, count,
+                                                           B->finished, B->progress, B->error);
   k_batch_count_idle<<<(count + 255) / 256, 256, 0, B->stream>>>(B->state, count, B->finished);
-  k_batch<FMT><<<B->grid, 288, 0, B->stream>>>(D);
+  k_batch<FMT><<<B->grid, BATCH_THREADS, 0, B->stream>>>(D);
   return cudaGetLastError();
 }
 
@@ -738,9 +747,9 @@ static int persistent_grid(int fmt) {
   int dev = 0, sms = 1, per = 1;
   cudaGetDevice(&dev);
   cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-  if (fmt == VF_DF) cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, k_batch<VF_DF>, 288, 0);
-  else if (fmt == VF_F64) cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, k_batch<VF_F64>, 288, 0);
-  else cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, k_batch<VF_F32>, 288, 0);
+  if (fmt == VF_DF) cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, k_batch<VF_DF>, BATCH_THREADS, 0);
+  else if (fmt == VF_F64) cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, k_batch<VF_F64>, BATCH_THREADS, 0);
+  else cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, k_batch<VF_F32>, BATCH_THREADS, 0);
   if (per < 1) per = 1;
   return sms * per;
 }
@@ -752,7 +761,7 @@ static ei_status batch_upload(ei_batch* B) {
   for (int i = 0; i < count; ++i) {
     BInst& I = B->hinst[i];
     I.tiles_x = (I.nx + 31) / 32;
-    const int64_t th = 8 * (int64_t)I.rows;
+    const int64_t th = I.rows;
     const int64_t tiles = (int64_t)I.tiles_x * ((I.ny + th - 1) / th);
     if (tiles >= (int64_t)IDLE_WORD) return EI_ERR_INVALID_ARG;  // the claim word's range
     I.tiles = (int)tiles;
@@ -894,7 +903,7 @@ static ei_status batch_tune(ei_batch* B) {
   std::vector<std::vector<int>> members(4);
   for (int i = 0; i < B->count; ++i)
     if (B->active[i]) members[size_class(B->hinst[i].npts)].push_back(i);
-  const int cand[4] = {4, 8, 16, 32};
+  const int cand[4] = {8, 16, 32, 64};
   for (int cls = 0; cls < 4; ++cls) {
     if (members[cls].empty()) continue;
     const std::string key = std::string(prop.name) + "/" + std::to_string(B->fmt) + "/" +
@@ -911,8 +920,11 @@ static ei_status batch_tune(ei_batch* B) {
                 [&](int a, int b) { return B->hinst[a].npts < B->hinst[b].npts; });
       const int rep = m[m.size() / 2];
       // fixed work: copies of the median problem, one substep, 16 Newton
-      // iterations each (a tolerance no iteration meets)
-      int copies = (int)std::min<int64_t>(64, std::max<int64_t>(4, (int64_t)(1 << 22) / B->hinst[rep].npts));
+      // iterations each (a tolerance no iteration meets); enough copies that
+      // every resident warp could hold a 64-row strip, as in a full batch
+      const int64_t target = (int64_t)B->grid * (BATCH_THREADS / 32) * 64 * 32;
+      int copies = (int)std::min<int64_t>(
+          2048, std::max<int64_t>(4, (target + B->hinst[rep].npts - 1) / B->hinst[rep].npts));
       std::vector<ei_batch_problem> probs(copies, B->prob[rep]);
       float best = 1e30f;
       for (int c : cand) {
@@ -951,7 +963,7 @@ static ei_status batch_tune(ei_batch* B) {
         }
         ei_batch_destroy(T);
       }
-      if (!rows) rows = 2;
+      if (!rows) rows = 16;
       std::lock_guard<std::mutex> lock(g_tune_mu);
       g_tune[key] = rows;
     }
@@ -1018,7 +1030,7 @@ ei_status ei_batch_create(ei_batch** out, int device, int count, const ei_batch_
     I.ayp = P.D / (P.dy * P.dy) + P.by / (2.0 * P.dy);
     I.d0 = P.c - 2.0 * P.D / (P.dx * P.dx) - 2.0 * P.D / (P.dy * P.dy);
     I.h = P.h;
-    I.rows = 2;
+    I.rows = 16;
     B->uoff[i] = uo;
     uo += I.npts;
     I.off = po;
@@ -1061,6 +1073,7 @@ ei_status ei_batch_create(ei_batch** out, int device, int count, const ei_batch_
       cudaMalloc(&B->state, sizeof(BState) * count) != cudaSuccess ||
       cudaMalloc(&B->qword, sizeof(unsigned long long) * count) != cudaSuccess ||
       cudaMalloc(&B->qtiles, sizeof(int) * count) != cudaSuccess ||
+      cudaMalloc(&B->avail, sizeof(unsigned) * ((count + 31) / 32)) != cudaSuccess ||
       cudaMalloc(&B->order, sizeof(int) * count) != cudaSuccess ||
       cudaMalloc(&B->dinit, sizeof(int) * count) != cudaSuccess ||
       cudaMalloc(&B->duoff, sizeof(int64_t) * (count + 1)) != cudaSuccess ||
@@ -1083,6 +1096,7 @@ ei_status ei_batch_create(ei_batch** out, int device, int count, const ei_batch_
   cudaMemcpy(B->dscal, B->scal.data(), sizeof(double) * count, cudaMemcpyHostToDevice);
   cudaMemcpy(B->xi, leja_table(), sizeof(double) * 101, cudaMemcpyHostToDevice);
   B->grid = persistent_grid(B->fmt);
+  if (opt && opt->tile_rows > 1024) return fail(EI_ERR_INVALID_ARG);
   if (opt && opt->tile_rows > 0) {
     for (int i = 0; i < count; ++i) B->hinst[i].rows = opt->tile_rows;
   } else if ((st = batch_tune(B)) != EI_OK) {
