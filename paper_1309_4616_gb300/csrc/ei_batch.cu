@@ -9,24 +9,30 @@
 //   AXPY:      y += tau p          (substeps s > 1)
 //   RES:       r = A y + v         (start of substeps 2..s)
 // Work distribution: the unit of work is a strip, 32 columns x `rows` rows of
-// one problem, processed by one warp; no block-level synchronisation.  A claim
-// queue in claim order (biggest problems first) holds one 64-bit word per
-// problem, descriptor << 32 | next strip, where the descriptor names the
-// current epoch (phase, Newton index j, substep), and a bitmap marks the
-// positions whose epoch has unclaimed strips (set when an epoch is published,
-// cleared by the claimer of its last strip).  A warp looking for work reads the
-// bitmap (one L2 round trip per 1024 problems) and claims from the biggest
-// problems first, so their chains of epochs start at once instead of forming a
-// tail.  It claims a strip with one atomicAdd, whose result is the strip and
-// its epoch at once, and claims the next strip of the same epoch before the
-// current one's arithmetic (the epoch cannot close while the warp holds an
-// unfinished strip), so the claim's latency hides behind the strip.  After a strip the warp writes its norm
-// partials and counts it done; the warp that completes the last strip of an
-// epoch sums the partials in strip order (deterministic), takes the phase's
-// decision and publishes the next epoch.  No warp waits for another; a warp
-// that finds nothing to claim sleeps briefly, and gives up after 5 s without
-// global progress (status EI_ERR_TIMEOUT).  Data written by other warps in
-// earlier epochs is read through L2 (ld.global.cg).
+// one problem, processed by one warp; no block-level synchronisation.
+// - Claim queue: one 64-bit word per problem, descriptor << 32 | next strip,
+//   where the descriptor names the current epoch (phase, Newton index j,
+//   substep).  Queue order puts the longest expected chains of epochs first
+//   (critical path first; then the bigger problem).
+// - Availability bitmap: a bit per queue position whose epoch has unclaimed
+//   strips, set when an epoch is published and cleared by the claimer of its
+//   last strip.  A warp looking for work reads it (one L2 round trip per 1024
+//   problems) and claims from the front of the queue, so the long chains start
+//   at once instead of forming a tail.
+// - Claims: one atomicAdd returns the strip and its epoch at once.  Outside
+//   the first 32 queue positions the next strip of the same epoch is claimed
+//   before the current one's arithmetic (the epoch cannot close while the warp
+//   holds an unfinished strip), so the claim's latency hides behind the strip;
+//   at the front, where the chains of epochs are longest, a held-back strip
+//   would delay its epoch by a whole strip, so each strip goes to a free warp.
+// - Epochs: after a strip the warp writes its norm partials and counts it
+//   done; the warp that completes the last strip of an epoch sums the partials
+//   in strip order (deterministic), takes the phase's decision and publishes
+//   the next epoch.
+// No warp waits for another; a warp that finds nothing to claim sleeps
+// briefly, and gives up after 5 s without global progress (status
+// EI_ERR_TIMEOUT).  Data written by other warps in earlier epochs is read
+// through L2 (ld.global.cg).
 #include <cuda_runtime.h>
 #include <math.h>
 #include <stdint.h>
@@ -275,7 +281,7 @@ __device__ __forceinline__ void stale_bit(const BatchDev& B, int k, unsigned til
 }
 
 // Claim one strip: the lanes read 32 bitmap words (1024 positions) at a time;
-// the first word with set bits holds the biggest problems with unclaimed
+// the first word with set bits holds the front-most problems with unclaimed
 // strips.  The warp tries its set bits with one atomicAdd each, starting at a
 // bit chosen by the warp index to spread warps over those problems.  Returns
 // the queue position (-1: nothing claimable) in every lane, with the strip and
@@ -424,9 +430,12 @@ __global__ void __launch_bounds__(BATCH_THREADS, FMT == VF_F32 ? 7 : 5) k_batch(
     }
     idle_t0 = 0;
     const int i = __ldg(B.order + k);
-    // the next strip of this epoch, claimed ahead
-    unsigned long long wn = 0;
-    if (lane == 0) wn = atomicAdd(B.qword + k, 1ull);
+    // the next strip of this epoch, claimed ahead; not for the front of the
+    // queue (the longest chains), whose epochs end sooner when each of their
+    // strips goes to a warp that is free now
+    const bool ahead = k >= 32;
+    unsigned long long wn = IDLE_WORD;
+    if (lane == 0 && ahead) wn = atomicAdd(B.qword + k, 1ull);
     const int phase = desc_phase(d);
     double a = 0.0, b = 0.0;
     batch_tile<FMT>(B, i, t, phase, desc_j(d), desc_sub(d), a, b);
@@ -572,6 +581,8 @@ struct ei_batch {
   bool deferred = false;           // plain plans not made yet (created with learned = 1)
   std::vector<int> dd_s;           // the s whose divided differences hdd holds (0: none)
   std::vector<int> plain_s;        // the a-priori rule's s (0: not computed)
+  std::vector<int> plain_m;        // and its degree estimate
+  std::vector<int> est_m;          // expected degree per substep of the current plan
   std::vector<int> learned;        // 0 plain plan, 1 learned proposal kept, 2 fell back
   double* vn2 = nullptr;           // device: ||v_i||^2
   std::vector<double> hvn2;
@@ -636,8 +647,10 @@ static void batch_interval(const ei_batch_problem& P, double* alpha, double* bet
   *beta = hi;
 }
 
-// schedule and divided differences of problem i for its current s (s <= 0: a-priori rule)
-static bool batch_plan(ei_batch* B, int i, int s_force) {
+// schedule and divided differences of problem i for its current s (s <= 0:
+// a-priori rule); m_hint > 0 is the degree the plan expects per substep (the
+// a-priori rule gives its own), used to order the claim queue
+static bool batch_plan(ei_batch* B, int i, int s_force, int m_hint = 0) {
   const double cc = B->c[i], gm = B->gamma[i];
   const double h = B->prob[i].h;
   int s = s_force, m = 0;
@@ -645,8 +658,12 @@ static bool batch_plan(ei_batch* B, int i, int s_force) {
   if (s <= 0) {
     if (schedule(1, h, cc, gm, B->tol, B->m_max, &s, &m, d) != 0) return false;
     B->plain_s[i] = s;
-  } else if (B->dd_s[i] != s) {
-    divided_differences(1, h / s, cc, gm, B->m_max, d);
+    B->plain_m[i] = m;
+    B->est_m[i] = m;
+  } else {
+    if (B->dd_s[i] != s) divided_differences(1, h / s, cc, gm, B->m_max, d);
+    B->est_m[i] = m_hint > 0 ? m_hint
+                             : (s == B->plain_s[i] && B->plain_m[i] > 0 ? B->plain_m[i] : B->m_max / 2);
   }
   B->dd_s[i] = s;
   B->hinst[i].s = s;
@@ -778,13 +795,19 @@ static ei_status batch_upload(ei_batch* B) {
     if (B->exec) cudaGraphExecDestroy(B->exec);
     B->exec = nullptr;
   }
-  // claim queue: biggest problems first
+  // claim queue: longest expected chain of epochs first (critical path first:
+  // a problem's epochs run one after the other, its strips in parallel), then
+  // the bigger problem
   std::vector<int> ord(count);
   for (int i = 0; i < count; ++i) ord[i] = i;
-  std::vector<double> work(count);
-  for (int i = 0; i < count; ++i)
-    work[i] = (double)B->hinst[i].npts * B->hinst[i].s * (B->m_max / 2 + 1);
-  std::stable_sort(ord.begin(), ord.end(), [&](int a, int b) { return work[a] > work[b]; });
+  std::vector<int64_t> chain(count);
+  for (int i = 0; i < count; ++i) {
+    const int64_t sv = B->hinst[i].s;
+    chain[i] = sv * (B->est_m[i] + 1) + (sv > 1 ? 2 * sv - 1 : 0);
+  }
+  std::stable_sort(ord.begin(), ord.end(), [&](int a, int b) {
+    return chain[a] != chain[b] ? chain[a] > chain[b] : B->hinst[a].npts > B->hinst[b].npts;
+  });
   std::vector<int> qt(count);
   for (int k = 0; k < count; ++k) {
     B->hinst[ord[k]].pos = k;
@@ -882,7 +905,7 @@ static ei_status batch_learned_plan(ei_batch* B, const void* v) {
     int s = 0, m = 0;
     if (learned_decide(&outs[(size_t)i * rows * EI_MLP_OUTPUTS], rows, D, B->m_max, &s, &m)) {
       B->learned[i] = 1;
-      ok[i] = batch_plan(B, i, s) ? 1 : 0;
+      ok[i] = batch_plan(B, i, s, m) ? 1 : 0;
     } else {
       B->learned[i] = 0;
       ok[i] = batch_plan(B, i, B->plain_s[i] > 0 ? B->plain_s[i] : 0) ? 1 : 0;
@@ -1013,6 +1036,8 @@ ei_status ei_batch_create(ei_batch** out, int device, int count, const ei_batch_
   B->hdd.assign((size_t)count * (B->m_max + 1), 0.0);
   B->dd_s.assign(count, 0);
   B->plain_s.assign(count, 0);
+  B->plain_m.assign(count, 0);
+  B->est_m.assign(count, B->m_max / 2);
   B->learned.assign(count, 0);
   B->deferred = opt && opt->learned == 1;
   int64_t uo = 0, po = 0;
