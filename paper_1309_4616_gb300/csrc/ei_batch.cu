@@ -143,10 +143,29 @@ __device__ __forceinline__ R stencil5(R dg, R uc, R a0, R u0, R a1, R u1, R a2, 
   return s1 + s2;
 }
 
+// a lane's value from the lane below / above (lane 0 / 31 get their own)
+__device__ __forceinline__ float shfl_up1(float v) { return __shfl_up_sync(0xffffffffu, v, 1); }
+__device__ __forceinline__ float shfl_down1(float v) { return __shfl_down_sync(0xffffffffu, v, 1); }
+__device__ __forceinline__ double shfl_up1(double v) { return __shfl_up_sync(0xffffffffu, v, 1); }
+__device__ __forceinline__ double shfl_down1(double v) {
+  return __shfl_down_sync(0xffffffffu, v, 1);
+}
+__device__ __forceinline__ df shfl_up1(df v) {
+  return df{__shfl_up_sync(0xffffffffu, v.hi, 1), __shfl_up_sync(0xffffffffu, v.lo, 1)};
+}
+__device__ __forceinline__ df shfl_down1(df v) {
+  return df{__shfl_down_sync(0xffffffffu, v.hi, 1), __shfl_down_sync(0xffffffffu, v.lo, 1)};
+}
+// a vector value carried in the Newton sum's type, back to the vector type
+__device__ __forceinline__ float narrow_to(df a, float) { return a.hi; }
+__device__ __forceinline__ df narrow_to(df a, df) { return a; }
+__device__ __forceinline__ double narrow_to(double a, double) { return a; }
+
 // One strip: 32 columns x `rows` rows.  Lane = column; the warp marches down
-// the strip keeping u(y-1), u(y), u(y+1) of its column in registers, so a point costs three loads (u(y+1), u(x-1), u(x+1))
-// plus its Newton sum; the loads of a row are issued two rows ahead of its
-// arithmetic.  A ghost value is 0 behind a Dirichlet face and u itself behind
+// the strip keeping u(y-1), u(y), u(y+1) of its column in registers and takes
+// u(x-1), u(x+1) from the adjacent lanes, so a point costs one load of u plus
+// its Newton sum (and the two edge lanes one halo value); the loads of a row
+// are issued three rows ahead of its arithmetic.  A ghost value is 0 behind a Dirichlet face and u itself behind
 // a Neumann face.
 template <int FMT>
 __device__ void batch_tile(const BatchDev& B, int i, int t, int phase, int j, int sub,
@@ -196,63 +215,74 @@ __device__ void batch_tile(const BatchDev& B, int i, int t, int phase, int j, in
   const P dn = from_d<P>(phase == PH_NEWTON ? B.dd[I.dd_off + j + 1] : 0.0);
   const P dz = from_d<P>(phase == PH_NEWTON ? B.dd[I.dd_off] : 0.0);
   const T zro = zero<T>();
-  if (x < I.nx && y0 < y1) {
+  if (y0 < y1) {  // the whole warp takes part (lane shuffles)
+    const int lane = (int)(threadIdx.x & 31);
+    const int nx = I.nx, ny = I.ny;
+    const bool g0 = I.bc[0], g1 = I.bc[1], g2 = I.bc[2], g3 = I.bc[3];
+    const bool xin = x < nx;
     const bool needp = newton && j > 0;
-    // column queue of row y: um = u(y-1), uc = u(y), up = u(y+1), ul, ur, and
-    // the row's Newton sum pc (NEWTON, j > 0) or v (RES)
-    int64_t k = (int64_t)y0 * I.nx + x;
-    T uc = ldcg_(u, k);
-    T um = y0 > 0 ? ldcg_(u, k - I.nx) : (I.bc[2] ? uc : zro);
-    T ul = x > 0 ? ldcg_(u, k - 1) : (I.bc[0] ? uc : zro);
-    T ur = x < I.nx - 1 ? ldcg_(u, k + 1) : (I.bc[1] ? uc : zro);
-    T up = y0 < I.ny - 1 ? ldcg_(u, k + I.nx) : (I.bc[3] ? uc : zro);
-    P pc = needp ? ldcg_(Pp, k) : zero<P>();
-    T vc = newton ? zro : ldcg_(V, k);
-    // raw loads of a later row yy at element kk: left, right, the point above
-    // (u(yy+1)), its p or v; ghosts are applied when the row becomes current
-    auto fetch = [&](int64_t kk, int yy, T& l, T& r, T& a, P& pq, T& vq) {
-      l = x > 0 ? ldcg_(u, kk - 1) : zro;
-      r = x < I.nx - 1 ? ldcg_(u, kk + 1) : zro;
-      a = (yy + 1 < I.ny) ? ldcg_(u, kk + I.nx) : zro;
-      pq = needp ? ldcg_(Pp, kk) : zero<P>();
-      vq = newton ? zro : ldcg_(V, kk);
+    const bool needa = needp || !newton;
+    // lane 0 holds u(x0-1) and lane 31 u(x0+32) of each row (the strip's halo);
+    // the other horizontal neighbours come from the adjacent lanes
+    const int hx = lane == 0 ? x - 1 : x + 1;
+    const bool hld = (lane == 0 && x > 0) || (lane == 31 && x + 1 < nx);
+    // raw loads of a row: the centre u, the halo value, and the row's Newton
+    // sum (NEWTON, j > 0) or v (RES) widened to the sum's type.  `ok`: the row
+    // lies in the grid.  `ro` is the element offset of row y, advanced by nx.
+    int64_t ro = (int64_t)y0 * nx;
+    const int ylast = ny - 1;
+    auto ldrow = [&](int yy, int64_t off, T& c, T& h, P& a) {
+      const bool in = yy <= ylast;
+      const int64_t kk = ro + off;
+      c = (in && xin) ? ldcg_(u, kk + x) : zro;
+      h = (in && hld) ? ldcg_(u, kk + hx) : zro;
+      a = zero<P>();
+      if (in && xin && needa) a = needp ? ldcg_(Pp, kk + x) : to_p(ldcg_(V, kk + x));
     };
-    // row y+1 is one row ahead, row y+2 two rows ahead
-    T al = zro, ar = zro, au = zro, av = zro;
-    P apn = zero<P>();
-    if (y0 + 1 < y1) fetch(k + I.nx, y0 + 1, al, ar, au, apn, av);
+    // queue: row y (uc, hc, ac), rows y+1 and y+2 in flight; the loads of row
+    // y+3 are issued before row y's arithmetic (the centre of a row is used one
+    // row early, as the point above)
+    T uc, hc, c1, h1, c2, h2;
+    P ac, a1, a2;
+    ldrow(y0, 0, uc, hc, ac);
+    T um = (y0 > 0 && xin) ? ldcg_(u, ro - nx + x) : zro;
+    ldrow(y0 + 1, nx, c1, h1, a1);
+    ldrow(y0 + 2, 2 * (int64_t)nx, c2, h2, a2);
+    if (y0 == 0) um = g2 ? uc : zro;
+    const int64_t off3 = 3 * (int64_t)nx;
     for (int y = y0; y < y1; ++y) {
-      T bl = zro, br = zro, bu = zro, bv = zro;
-      P bpn = zero<P>();
-      if (y + 2 < y1) fetch(k + 2 * (int64_t)I.nx, y + 2, bl, br, bu, bpn, bv);
+      T c3 = zro, h3 = zro;
+      P a3 = zero<P>();
+      if (y + 3 <= y1) ldrow(y + 3, off3, c3, h3, a3);
+      const T up = (y < ylast) ? c1 : (g3 ? uc : zro);
+      const T sl = shfl_up1(uc), sr = shfl_down1(uc);
+      const T ul = x > 0 ? (lane == 0 ? hc : sl) : (g0 ? uc : zro);
+      const T ur = x < nx - 1 ? (lane == 31 ? hc : sr) : (g1 ? uc : zro);
       const T acc = stencil5(cdg, uc, axm, ul, axp, ur, aym, um, ayp, up);
-      if (newton) {
-        const T wn = acc;
-        const P pold = (j == 0) ? mul(dz, to_p(uc)) : pc;
-        const P pn = mac(pold, dn, to_p(wn));
-        st(wout, k, wn);
-        st(Pp, k, pn);
-        aw = acc_sq(aw, wn);
-        ap = acc_sq(ap, pn);
-      } else {
-        st(R, k, add(acc, vc));
+      if (xin) {
+        if (newton) {
+          const T wn = acc;
+          const P pold = (j == 0) ? mul(dz, to_p(uc)) : ac;
+          const P pn = mac(pold, dn, to_p(wn));
+          st(wout, ro + x, wn);
+          st(Pp, ro + x, pn);
+          aw = acc_sq(aw, wn);
+          ap = acc_sq(ap, pn);
+        } else {
+          st(R, ro + x, add(acc, narrow_to(ac, zro)));
+        }
       }
-      if (y + 1 < y1) {
-        // shift the queue; ghosts of row y+1 (u(y+1) = up is a real point)
-        um = uc;
-        uc = up;
-        ul = x > 0 ? al : (I.bc[0] ? uc : zro);
-        ur = x < I.nx - 1 ? ar : (I.bc[1] ? uc : zro);
-        up = (y + 2 < I.ny) ? au : (I.bc[3] ? uc : zro);
-        pc = apn;
-        vc = av;
-        al = bl;
-        ar = br;
-        au = bu;
-        apn = bpn;
-        av = bv;
-        k += I.nx;
-      }
+      ro += nx;
+      um = uc;
+      uc = c1;
+      hc = h1;
+      ac = a1;
+      c1 = c2;
+      h1 = h2;
+      a1 = a2;
+      c2 = c3;
+      h2 = h3;
+      a2 = a3;
     }
   }
   o0 = acc_d(aw);
