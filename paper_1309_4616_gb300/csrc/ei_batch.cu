@@ -289,6 +289,23 @@ __device__ void batch_tile(const BatchDev& B, int i, int t, int phase, int j, in
   o1 = acc_d(ap);
 }
 
+// Atomic adds with acquire / acquire-release semantics at GPU scope: a claim
+// must see the data of the epoch it claims (acquire only: the warp's own
+// earlier stores need not drain first); counting a strip done releases the
+// strip's stores and, for the warp that completes the epoch, acquires the
+// other warps' partials.
+__device__ __forceinline__ unsigned long long atom_add_acquire(unsigned long long* p,
+                                                               unsigned long long v) {
+  unsigned long long r;
+  asm volatile("atom.acquire.gpu.global.add.u64 %0, [%1], %2;" : "=l"(r) : "l"(p), "l"(v) : "memory");
+  return r;
+}
+__device__ __forceinline__ unsigned atom_add_acq_rel(unsigned* p, unsigned v) {
+  unsigned r;
+  asm volatile("atom.acq_rel.gpu.global.add.u32 %0, [%1], %2;" : "=r"(r) : "l"(p), "r"(v) : "memory");
+  return r;
+}
+
 // After a claim that returned strip t of position k: the claimer of the last
 // strip clears the position's bit (it holds an unfinished strip of the epoch,
 // so the epoch cannot be closed and republished before the clear).
@@ -333,13 +350,13 @@ __device__ int warp_claim(const BatchDev& B, unsigned gw, int& t_out, unsigned& 
         for (int q = (int)((gw + (unsigned)r) % (unsigned)nb); q > 0; --q) rest &= rest - 1;
         const int k = (base + l) * 32 + __ffs(rest) - 1;
         unsigned long long w = 0;
-        if (lane == 0) w = atomicAdd(B.qword + k, 1ull);
+        if (lane == 0) w = atom_add_acquire(B.qword + k, 1ull);
         w = __shfl_sync(0xffffffffu, w, 0);
         const unsigned t = (unsigned)(w & 0xffffffffull);
         const unsigned tiles = (unsigned)__ldg(B.qtiles + k);
         if (t < tiles) {
           if (lane == 0) claimed_strip(B, k, t, tiles);
-          __threadfence();  // the epoch's data is read after the claim
+          __syncwarp();  // the lanes read the epoch's data after lane 0's acquire
           t_out = (int)t;
           desc_out = (unsigned)(w >> 32);
           return k;
@@ -360,16 +377,15 @@ __device__ void account_strip(const BatchDev& B, int i, unsigned d) {
   const BInst& I = B.inst[i];
   BState* S = &B.state[i];
   int last = 0;
-  __syncwarp();
+  __syncwarp();  // the lanes' stores of the strip precede lane 0's release
   if (lane == 0) {
-    __threadfence();
-    const unsigned dn = atomicAdd(&S->done, 1u);
+    const unsigned dn = atom_add_acq_rel(&S->done, 1u);
     last = (dn == (unsigned)I.tiles - 1);
     atomicAdd(B.progress, 1ull);
   }
   last = __shfl_sync(0xffffffffu, last, 0);
   if (!last) return;
-  __threadfence();
+  __syncwarp();  // the lanes read the partials after lane 0's acquire
   const int phase0 = desc_phase(d), j0 = desc_j(d), sub0 = desc_sub(d);
   double nw2 = 0.0, np2 = 0.0;
   if (phase0 == PH_NEWTON) {
