@@ -153,7 +153,10 @@ ei_status ei_set_operator_stencil(ei_ctx* ctx, int dim, const int64_t n[3], cons
                                   const int bc[6], int prec);
 
 /* Sparse operator in CSR, Sec. III-D: A = W + diag(diag).
- * rowptr  int64[n+1] (device), col int32[nnz] (device), val[nnz] (device),
+ * rowptr  int64[n+1] (device), nondecreasing from rowptr[0] = 0 to
+ *         rowptr[n] = nnz; col int32[nnz] (device), each in [0, n);
+ *         val[nnz] (device).  The structure is checked on the device before
+ *         use: a violation returns EI_ERR_INVALID_ARG.
  * diag    device array of n values or NULL (zero).  Entries with col == row
  *         are allowed and count as diagonal.  prec as above. */
 ei_status ei_set_operator_csr(ei_ctx* ctx, int64_t n, int64_t nnz, const int64_t* rowptr,

@@ -920,6 +920,15 @@ ei_status ei_set_operator_csr(ei_ctx* c, int64_t n, int64_t nnz, const int64_t* 
   if ((st = alloc((void**)&c->partials, sizeof(double) * 4 * nb)) != EI_OK) { free_operator(c); return st; }
   if ((st = alloc((void**)&c->ger_lo, sizeof(double) * n)) != EI_OK) { free_operator(c); return st; }
   if ((st = alloc((void**)&c->ger_hi, sizeof(double) * n)) != EI_OK) { free_operator(c); return st; }
+  // the structure is checked before any kernel reads through rowptr and col
+  if (cudaMemsetAsync(&c->ctl->csr_bad, 0, sizeof(int), c->stream) != cudaSuccess ||
+      launch_csr_validate(n, nnz, rowptr, col, c->ctl, c->stream) != cudaSuccess) {
+    cudaGetLastError();
+    free_operator(c);
+    return EI_ERR_CUDA;
+  }
+  if ((st = read_ctl(c)) != EI_OK) { free_operator(c); return st; }
+  if (c->h_ctl->csr_bad) { free_operator(c); return EI_ERR_INVALID_ARG; }
   cudaError_t e = launch_csr_gershgorin(c->cd, prec, val, diag, c->ger_lo, c->ger_hi, c->partials,
                                         c->ctl, c->stream);
   if (e != cudaSuccess) { free_operator(c); return EI_ERR_CUDA; }

@@ -24,7 +24,8 @@ struct DevCtl {
                        // p_{j+2}; subtract d_{j+2} w_{j+2} to get p_{j+1}
   int fixfail;         // fixed-count mode: substeps whose final check failed (sticky
                        // across substeps; reset by the host once per call)
-  int pad2[2];
+  int csr_bad;         // set by the CSR structure check (launch_csr_validate)
+  int pad2;
   double sum0, sum1;   // import / F / residual: squared norm, finiteness flag (1 = finite)
   double mn, mx;       // Gershgorin reductions: min_i (a_ii - r_i), max_i (a_ii + r_i)
   double nw2, np2;     // squared norms of the last Newton iterate / sum
@@ -98,6 +99,10 @@ cudaError_t launch_stencil_gershgorin(const StencilDev& g, int user_prec, const 
                                       const void* D, double Dc, const void* const b[3],
                                       const double bc[3], const void* c, double cc, double* lo,
                                       double* hi, double* partials, DevCtl* ctl, cudaStream_t st);
+// CSR structure check: rowptr[0] == 0, rowptr[n] == nnz, rowptr nondecreasing,
+// every column in [0, n); a violation sets ctl->csr_bad (reset it first).
+cudaError_t launch_csr_validate(int64_t n, int64_t nnz, const int64_t* rowptr,
+                                const int32_t* col, DevCtl* ctl, cudaStream_t stm);
 cudaError_t launch_csr_gershgorin(const CsrDev& op, int prec, const void* val_user,
                                   const void* diag_user, double* lo, double* hi,
                                   double* partials, DevCtl* ctl, cudaStream_t st);

@@ -275,12 +275,79 @@ __device__ __forceinline__ T csr_row(const CsrDev& op, const T* __restrict__ x, 
   return lsum(s1, s2);
 }
 
+// Rows pipelined across a grid-stride walk: each thread keeps the row
+// pointers of its next two rows in registers and the columns of its next row
+// in its own shared-memory slots (cp.async, no registers held), so a row's
+// value loads and gathers go out at once and the chain rowptr -> col -> x of
+// a later row runs behind the current row's arithmetic.  A row's first
+// CSR_PFC columns are prefetched; its entries are consumed in register batches
+// of CSR_PF (value loads and gathers of a batch issued together); columns past
+// CSR_PFC are read directly, four at a time.
+constexpr int CSR_PF = 12;
+constexpr int CSR_PFC = 20;
+__device__ __forceinline__ void cp_async4(void* smem, const void* gmem) {
+  const unsigned sa = (unsigned)__cvta_generic_to_shared(smem);
+  asm volatile("cp.async.ca.shared.global [%0], [%1], 4;" ::"r"(sa), "l"(gmem) : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
+template <int N>
+__device__ __forceinline__ void cp_async_wait() { asm volatile("cp.async.wait_group %0;" ::"n"(N) : "memory"); }
+
+// the first CSR_PFC columns of entries [b, e) into this thread's slots
+__device__ __forceinline__ void csr_prefetch_cols(int32_t (*slot)[EI_TPB], const int32_t* col,
+                                                  int64_t b, int64_t e) {
+#pragma unroll
+  for (int q = 0; q < CSR_PFC; ++q)
+    if (b + q < e) cp_async4(&slot[q][threadIdx.x], col + b + q);
+}
+
+template <class T>
+__device__ __forceinline__ T csr_row_pf(const CsrDev& op, const T* __restrict__ x, int64_t b,
+                                        int64_t e, const int32_t (*slot)[EI_TPB]) {
+  const T* __restrict__ val = static_cast<const T*>(op.val);
+  typename Acc<T>::type s1 = Acc<T>::zero(), s2 = Acc<T>::zero();
+  const int m = (int)(e - b < CSR_PFC ? e - b : CSR_PFC);
+  // prefetched columns, in batches of CSR_PF entries
+  for (int q0 = 0; q0 < m; q0 += CSR_PF) {
+    T v[CSR_PF], xv[CSR_PF];
+#pragma unroll
+    for (int q = 0; q < CSR_PF; ++q) {
+      const bool in = q0 + q < m;
+      v[q] = in ? ldg(val, b + q0 + q) : zero<T>();
+      xv[q] = in ? ldg(x, slot[in ? q0 + q : 0][threadIdx.x]) : zero<T>();
+    }
+#pragma unroll
+    for (int q = 0; q < CSR_PF; q += 2) {
+      s1 = lmac(s1, v[q], xv[q]);
+      s2 = lmac(s2, v[q + 1], xv[q + 1]);
+    }
+  }
+  // the rest, four entries at a time
+  for (int64_t k = b + CSR_PFC; k < e; k += 4) {
+    int c[4];
+    T v[4], xv[4];
+#pragma unroll
+    for (int q = 0; q < 4; ++q) c[q] = k + q < e ? __ldg(op.col + k + q) : -1;
+#pragma unroll
+    for (int q = 0; q < 4; ++q) {
+      v[q] = c[q] >= 0 ? ldg(val, k + q) : zero<T>();
+      xv[q] = c[q] >= 0 ? ldg(x, c[q]) : zero<T>();
+    }
+    s1 = lmac(s1, v[0], xv[0]);
+    s2 = lmac(s2, v[1], xv[1]);
+    s1 = lmac(s1, v[2], xv[2]);
+    s2 = lmac(s2, v[3], xv[3]);
+  }
+  return lsum(s1, s2);
+}
+
 template <int FMT>
 __global__ void __launch_bounds__(EI_TPB)
 k_csr_newton(CsrDev op, const void* __restrict__ w_in_, void* __restrict__ w_out_,
              void* __restrict__ p_, NewtonScalars s, double* partials, DevCtl* ctl) {
   using T = typename VT<FMT>::T;
   using P = typename VT<FMT>::P;
+  __shared__ int32_t slots[2][CSR_PFC][EI_TPB];
   if (*(volatile int*)&ctl->done != 0) return;
   const T* __restrict__ w_in = static_cast<const T*>(w_in_);
   T* __restrict__ w_out = static_cast<T*>(w_out_);
@@ -292,10 +359,32 @@ k_csr_newton(CsrDev op, const void* __restrict__ w_in_, void* __restrict__ w_out
   const P d0 = from_d<P>(s.d0);
   typename Acc<T>::type aw = Acc<T>::zero();
   typename Acc<P>::type ap = Acc<P>::zero();
-  const int64_t row = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-  if (row < op.n) {
+  const int64_t G = (int64_t)gridDim.x * blockDim.x;
+  const int64_t n = op.n;
+  int64_t row = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  int64_t b0 = 0, e0 = 0, b1 = 0, e1 = 0;
+  if (row < n) {
+    b0 = __ldg(op.rowptr + row);
+    e0 = __ldg(op.rowptr + row + 1);
+  }
+  if (row + G < n) {
+    b1 = __ldg(op.rowptr + row + G);
+    e1 = __ldg(op.rowptr + row + G + 1);
+  }
+  csr_prefetch_cols(slots[0], op.col, b0, e0);
+  cp_async_commit();
+  int buf = 0;
+  for (; row < n; row += G) {
+    int64_t b2 = 0, e2 = 0;
+    if (row + 2 * G < n) {
+      b2 = __ldg(op.rowptr + row + 2 * G);
+      e2 = __ldg(op.rowptr + row + 2 * G + 1);
+    }
+    csr_prefetch_cols(slots[buf ^ 1], op.col, b1, e1);
+    cp_async_commit();
+    cp_async_wait<1>();  // this row's columns have landed
     const T wc = ldg(w_in, row);
-    const T Aw = mac(csr_row<T>(op, w_in, row), ldg(qc, row), wc);
+    const T Aw = mac(csr_row_pf<T>(op, w_in, b0, e0, slots[buf]), ldg(qc, row), wc);
     const T wn = newton_update(Aw, invg, nshift, wc);
     const P pold = (s.j == 0) ? mul(d0, to_p(wc)) : ld(p, row);
     const P pn = mac(pold, dn, to_p(wn));
@@ -303,7 +392,13 @@ k_csr_newton(CsrDev op, const void* __restrict__ w_in_, void* __restrict__ w_out
     st(p, row, pn);
     aw = acc_sq(aw, wn);
     ap = acc_sq(ap, pn);
+    b0 = b1;
+    e0 = e1;
+    b1 = b2;
+    e1 = e2;
+    buf ^= 1;
   }
+  cp_async_wait<0>();
   double nw2 = acc_d(aw), np2 = acc_d(ap);
   if (last_block_reduce2<RED_SUM>(nw2, np2, partials, ctl)) {
     if (threadIdx.x == 0) {
@@ -617,7 +712,16 @@ cudaError_t launch_stencil_F(const StencilDev& g, const void* u, void* F, const 
 cudaError_t launch_csr_newton(const CsrDev& op, const void* w_in, void* w_out, void* p,
                               const NewtonScalars& s, int fmt, double* partials, DevCtl* ctl,
                               cudaStream_t stm) {
-  const int nb = csr_blocks(op.n);
+  // a grid of resident blocks walking the rows (at most csr_blocks(n))
+  static int per_sm[3] = {0, 0, 0};
+  if (!per_sm[fmt]) {
+    int per = 1;
+    EI_DISPATCH_FMT(fmt, cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, k_csr_newton<F_>,
+                                                                       EI_TPB, 0));
+    per_sm[fmt] = per < 1 ? 1 : per;
+  }
+  int nb = csr_blocks(op.n);
+  if (nb > num_sms() * per_sm[fmt]) nb = num_sms() * per_sm[fmt];
   EI_DISPATCH_FMT(fmt, (k_csr_newton<F_><<<nb, EI_TPB, 0, stm>>>(op, w_in, w_out, p, s, partials, ctl)));
   return cudaGetLastError();
 }
@@ -634,6 +738,28 @@ cudaError_t launch_csr_F(const CsrDev& op, const void* u, void* F, void* qc_out,
                          double* partials, DevCtl* ctl, cudaStream_t stm) {
   const int nb = csr_blocks(op.n);
   EI_DISPATCH_FMT(fmt, (k_csr_F<F_><<<nb, EI_TPB, 0, stm>>>(op, u, F, qc_out, c_base, nonlin, rosenbrock, partials, ctl)));
+  return cudaGetLastError();
+}
+
+__global__ void k_csr_validate(int64_t n, int64_t nnz, const int64_t* __restrict__ rowptr,
+                               const int32_t* __restrict__ col, DevCtl* ctl) {
+  const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+  bool bad = false;
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i <= n; i += stride) {
+    const int64_t a = __ldg(rowptr + i);
+    bad |= (i == 0 && a != 0) || (i == n && a != nnz) || (i < n && __ldg(rowptr + i + 1) < a);
+  }
+  for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < nnz; e += stride) {
+    const int32_t c = __ldg(col + e);
+    bad |= c < 0 || (int64_t)c >= n;
+  }
+  if (bad) atomicOr(&ctl->csr_bad, 1);
+}
+
+cudaError_t launch_csr_validate(int64_t n, int64_t nnz, const int64_t* rowptr,
+                                const int32_t* col, DevCtl* ctl, cudaStream_t stm) {
+  k_csr_validate<<<ew_blocks(n + 1 > nnz ? n + 1 : nnz), EI_TPB, 0, stm>>>(n, nnz, rowptr, col,
+                                                                           ctl);
   return cudaGetLastError();
 }
 

@@ -222,6 +222,91 @@ def test_csr_rosenbrock(env, xi):
     _check_stats(st, ost)
 
 
+def _irregular_graph(n, seed, hub_degree):
+    """Symmetric weighted graph with isolated nodes (empty rows), a hub whose
+    row is longer than a warp's 256-entry chunk, and ragged degrees."""
+    rng = np.random.default_rng(seed)
+    edges = set()
+    for i in range(n):
+        for j in rng.integers(0, n, size=rng.integers(0, 9)):
+            if i != j:
+                edges.add((min(i, j), max(int(j), i)))
+    hub = n // 3
+    for j in rng.choice(n, size=min(hub_degree, n - 1), replace=False):
+        if j != hub:
+            edges.add((min(hub, int(j)), max(hub, int(j))))
+    iso = set(range(5, n, 97))  # isolated nodes
+    edges = {(a, b) for a, b in edges if a not in iso and b not in iso}
+    w = {e: rng.uniform(0.5, 2.0) for e in edges}
+    rows = [[] for _ in range(n)]
+    for (a, b), x in w.items():
+        rows[a].append((b, x))
+        rows[b].append((a, x))
+    rowptr = np.zeros(n + 1, dtype=np.int64)
+    col, val = [], []
+    for i in range(n):
+        rows[i].sort()
+        rowptr[i + 1] = rowptr[i] + len(rows[i])
+        col += [c for c, _ in rows[i]]
+        val += [x for _, x in rows[i]]
+    col = np.array(col, dtype=np.int32)
+    val = np.array(val)
+    deg = np.bincount(np.repeat(np.arange(n), np.diff(rowptr)), val, minlength=n)
+    return rowptr, col, val, deg
+
+
+@pytest.mark.parametrize("n,hub", [(1000, 700), (20, 19), (33, 5)])
+def test_csr_irregular_rows(env, xi, n, hub):
+    """Empty rows, a row longer than a chunk, warps whose entries span several
+    chunks, n below and not a multiple of 32."""
+    torch, ei = env
+    rowptr, col, val, deg = _irregular_graph(n, 5 + n, hub)
+    assert (np.diff(rowptr) == 0).any()
+    if hub > 256:
+        assert np.diff(rowptr).max() > 256
+    op = O.CsrOperator(n, rowptr, col, val, -deg)
+    v0 = W.random_vector(n, 9)
+    h = 30.0 / (2 * deg.max())
+    ref, ost = Nw.phi_apply(op, 1, h, v0, 1e-10, xi=xi)
+    ctx = ei.Context()
+    ctx.set_operator_csr(n, dev(torch, rowptr), dev(torch, col), dev(torch, val), dev(torch, -deg))
+    v = dev(torch, v0)
+    out = torch.empty_like(v)
+    st = ctx.phi_apply(1, h, v, out, 1e-10)
+    assert rel_err(out.cpu().numpy(), ref) <= FP64_TOL
+    _check_stats(st, ost)
+
+
+@pytest.mark.parametrize("defect", ["col_high", "col_negative", "rowptr_start", "rowptr_end",
+                                    "rowptr_decreasing"])
+def test_csr_invalid_structure_rejected(env, defect):
+    """A structure the kernels could not read safely is refused before use
+    (the check reads only the stated n + 1 and nnz entries); the context stays
+    usable."""
+    torch, ei = env
+    g = W.rgg_graph(n=500, seed=3)
+    rowptr, col = g.rowptr.copy(), g.col.copy()
+    if defect == "col_high":
+        col[17] = g.n
+    elif defect == "col_negative":
+        col[-1] = -1
+    elif defect == "rowptr_start":
+        rowptr[0] = 1
+    elif defect == "rowptr_end":
+        rowptr[-1] -= 1
+    else:
+        rowptr[200] = rowptr[202] + 1
+    ctx = ei.Context()
+    with pytest.raises(ei.EIError) as e:
+        ctx.set_operator_csr(g.n, dev(torch, rowptr), dev(torch, col), dev(torch, g.val),
+                             dev(torch, -g.deg_w))
+    assert e.value.status == ei.ERR_INVALID_ARG
+    ctx.set_operator_csr(g.n, dev(torch, g.rowptr), dev(torch, g.col), dev(torch, g.val),
+                         dev(torch, -g.deg_w))
+    assert ctx.estimate_spectrum()[0] == pytest.approx(-2 * g.deg_w.max(), rel=1e-13)
+    ctx.close()
+
+
 # --------------------------------------------------------------------------
 # edge cases
 # --------------------------------------------------------------------------
