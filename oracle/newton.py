@@ -29,6 +29,10 @@ from .operators import ShiftedOperator
 
 NONLIN_NONE = 0
 NONLIN_LOGISTIC = 1
+NONLIN_COMBUSTION = 2
+# below this u the combustion term and its derivative are 0 (their limit as
+# u -> 0+; in FP64 the exponential already underflows to 0 there)
+COMBUSTION_CUT = 0.025
 
 
 class NotConverged(RuntimeError):
@@ -219,10 +223,29 @@ def phi_apply(op, k, h, v, tol, m_max=L.M_MAX, xi=None):
     raise NotConverged("phi_k: no s <= S_MAX converged")
 
 
+def combustion(u):
+    """The combustion model's reaction term (Sec. III-C, the nonlinearity
+    evaluated pointwise on the GPU): g(u) = (2 - u) exp(20 (1 - 1/u)) / 4, and
+    its derivative g'(u) = exp(20 (1 - 1/u)) (20 (2 - u) / u^2 - 1) / 4 (the
+    product rule).  Reading: for u <= COMBUSTION_CUT both are 0."""
+    u = np.asarray(u, dtype=np.float64)
+    g = np.zeros_like(u)
+    dg = np.zeros_like(u)
+    m = u > COMBUSTION_CUT
+    um = u[m]
+    e = np.exp(20.0 * (1.0 - 1.0 / um))
+    g[m] = 0.25 * (2.0 - um) * e
+    dg[m] = 0.25 * e * (20.0 * (2.0 - um) / (um * um) - 1.0)
+    return g, dg
+
+
 def nonlinearity(u, kind):
-    """g(u) and g'(u): none (0, 0) or logistic u(1-u), 1-2u."""
+    """g(u) and g'(u): none (0, 0), logistic u(1-u), 1-2u, or the combustion
+    term of Sec. III-C."""
     if kind == NONLIN_LOGISTIC:
         return u * (1.0 - u), 1.0 - 2.0 * u
+    if kind == NONLIN_COMBUSTION:
+        return combustion(u)
     return np.zeros_like(u), np.zeros_like(u)
 
 
