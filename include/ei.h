@@ -73,7 +73,11 @@ enum { EI_PREC_F64 = 0, EI_PREC_F32 = 1 };
 enum { EI_ARITH_DF = 0, EI_ARITH_NATIVE_F64 = 1 };
 
 enum { EI_EXP_EULER = 0, EI_EXP_ROSENBROCK = 1 };
-enum { EI_NONLIN_NONE = 0, EI_NONLIN_LOGISTIC = 1 }; /* g = 0 | g = u(1-u) */
+/* g = 0 | g = u(1-u) | the combustion term of Sec. III-C,
+ * g = (2-u) e^{20(1-1/u)}/4, at the format's precision | the same with FP32
+ * hardware approximations of exp and division (the paper's fast math) */
+enum { EI_NONLIN_NONE = 0, EI_NONLIN_LOGISTIC = 1, EI_NONLIN_COMBUSTION = 2,
+       EI_NONLIN_COMBUSTION_FAST = 3 };
 
 typedef struct {
   int m_max;      /* largest Newton degree per substep; 0 -> 100 (max 100) */
@@ -211,7 +215,10 @@ ei_status ei_phi_apply(ei_ctx* ctx, int k, double h, const void* v, void* out, d
 /* One step of size h of u' = A u + g(u), in place on the device vector u.
  * method EI_EXP_EULER:      u <- u + h phi_1(hA)(A u + g(u))          (Eq. (2))
  * method EI_EXP_ROSENBROCK: u <- u + h phi_1(hJ)(A u + g(u)), J = A + diag(g'(u))
- * nonlin EI_NONLIN_NONE (g = 0) or EI_NONLIN_LOGISTIC (g = u(1-u)). */
+ * nonlin EI_NONLIN_*: g = 0, u(1-u), or the combustion term of Sec. III-C
+ *        (g and g' fused into the kernel that forms A u + g(u); the full form
+ *        at the format's precision, float-float for EI_ARITH_DF; the fast form
+ *        in FP32 with __expf / __fdividef). */
 ei_status ei_step(ei_ctx* ctx, int method, double h, void* u, int nonlin, double tol,
                   const ei_options* opt, ei_stats* stats);
 
@@ -220,6 +227,20 @@ ei_status ei_step(ei_ctx* ctx, int method, double h, void* u, int nonlin, double
  * Returns after the copy back completed. */
 ei_status ei_step_host(ei_ctx* ctx, int method, double h, void* u_host, int nonlin, double tol,
                        const ei_options* opt, ei_stats* stats);
+
+/* Pointwise nonlinearity, Sec. III-C (the paper's Table 3 times exactly this
+ * evaluation): g[i] = g(u[i]) and, when dg is not NULL, dg[i] = g'(u[i]),
+ * for 0 <= i < n.
+ *   nonlin  EI_NONLIN_* (NONE gives zeros).
+ *   prec    EI_PREC_F64 (double arrays) or EI_PREC_F32 (float arrays).
+ *   arith   FP64 arrays only: EI_ARITH_DF evaluates in float-float on the
+ *           FP32 pipes, EI_ARITH_NATIVE_F64 with the FP64 math library.
+ *   u, g, dg  device arrays of n elements, caller-owned; g or dg may alias u.
+ *   cuda_stream  the kernel is queued there; the call does not synchronise.
+ * Errors: EI_ERR_INVALID_ARG for an unknown nonlin, prec or arith, n < 0, or
+ * a NULL u or g with n > 0; EI_ERR_CUDA if the launch fails. */
+ei_status ei_nonlinearity(int nonlin, int prec, int arith, int64_t n, const void* u, void* g,
+                          void* dg, void* cuda_stream);
 
 /* Host-side pieces of the method, exported for inspection and tests. */
 /* Leja points xi_0..xi_m on [-2,2]: xi_0 = 2, xi_j maximises prod_{i<j}|x - xi_i|,

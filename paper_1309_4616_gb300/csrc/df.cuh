@@ -11,6 +11,7 @@
 // can neither contract nor reassociate them.
 #pragma once
 #include <cuda_runtime.h>
+#include <math.h>
 
 struct __align__(8) df {
   float hi, lo;
@@ -123,4 +124,59 @@ __device__ __forceinline__ df dfa_norm(dfacc c) {
   df r;
   two_sum(c.s, c.t, r.hi, r.lo);
   return r;
+}
+
+// ---- reciprocal and exponential -------------------------------------------
+// 1/a: Newton-Raphson from the float reciprocal, q = q0 + q0 (1 - a q0), one
+// step doubling the 24 correct bits of q0 to the format's 48.
+__device__ __forceinline__ df df_recip(df a) {
+  const float q0 = 1.0f / a.hi;
+  const df e = df_add(df{1.0f, 0.0f}, df_neg(df_mul(a, df{q0, 0.0f})));
+  return df_mac(df{q0, 0.0f}, df{q0, 0.0f}, e);
+}
+
+// e^x, written from the mathematics:
+// - Cody-Waite argument reduction x = k ln2 + r, k = rint(x / ln2), with ln 2
+//   split in three floats.  The first carries 16 significant bits, so k*L1 is
+//   exact for |k| < 256, and k*L2 is formed exactly by an FMA.
+// - The Taylor series of e^r for |r| <= ln2/2 to degree 12 in Horner form.
+//   Truncation is below 2e-16 relative.
+// - 2^k applied to both halves.
+// The split constants are ln 2 to 60 digits cut into floats:
+//   L1 = 0x1.62e4p-1, L2 = 0x1.7f7d1cp-20, L3 = 0x1.ef357ap-45.
+// The residual of the split is 1.3e-21.  The coefficients are 1/i!, rounded
+// from double.  The float exponent range limits the result: +inf above
+// x = 88, 0 below x = -87.
+struct df_fact_inv {
+  static constexpr __host__ __device__ double v(int i) { return i <= 1 ? 1.0 : v(i - 1) / i; }
+  // 1/i! as a float-float pair, formed at compile time
+  static constexpr __host__ __device__ float hi(int i) { return (float)v(i); }
+  static constexpr __host__ __device__ float lo(int i) { return (float)(v(i) - (double)(float)v(i)); }
+};
+__device__ __forceinline__ df df_exp(df x) {
+  if (x.hi > 88.0f) return df{INFINITY, 0.0f};
+  if (!(x.hi >= -87.0f)) return x.hi != x.hi ? x : df{0.0f, 0.0f};  // NaN passes through
+  constexpr float L1 = 0x1.62e4p-1f, L2 = 0x1.7f7d1cp-20f, L3 = 0x1.ef357ap-45f;
+  const float k = rintf(x.hi * 1.44269504088896341f);
+  df r = df_add(x, df{-k * L1, 0.0f});
+  const float p2 = k * L2;
+  r = df_add(r, df{-p2, -__fmaf_rn(k, L2, -p2)});
+  r = df_add(r, df{-k * L3, 0.0f});
+#define EI_DF_C(i) df{df_fact_inv::hi(i), df_fact_inv::lo(i)}
+  df p = EI_DF_C(12);
+  p = df_mac(EI_DF_C(11), p, r);
+  p = df_mac(EI_DF_C(10), p, r);
+  p = df_mac(EI_DF_C(9), p, r);
+  p = df_mac(EI_DF_C(8), p, r);
+  p = df_mac(EI_DF_C(7), p, r);
+  p = df_mac(EI_DF_C(6), p, r);
+  p = df_mac(EI_DF_C(5), p, r);
+  p = df_mac(EI_DF_C(4), p, r);
+  p = df_mac(EI_DF_C(3), p, r);
+  p = df_mac(EI_DF_C(2), p, r);
+  p = df_mac(df{1.0f, 0.0f}, p, r);
+  p = df_mac(df{1.0f, 0.0f}, p, r);
+#undef EI_DF_C
+  const int ki = (int)k;
+  return df{ldexpf(p.hi, ki), ldexpf(p.lo, ki)};
 }

@@ -940,6 +940,21 @@ ei_status ei_set_operator_csr(ei_ctx* c, int64_t n, int64_t nnz, const int64_t* 
   return EI_OK;
 }
 
+ei_status ei_nonlinearity(int nonlin, int prec, int arith, int64_t n, const void* u, void* g,
+                          void* dg, void* cuda_stream) {
+  if (nonlin < EI_NONLIN_NONE || nonlin > EI_NONLIN_COMBUSTION_FAST ||
+      (prec != EI_PREC_F64 && prec != EI_PREC_F32) ||
+      (arith != EI_ARITH_DF && arith != EI_ARITH_NATIVE_F64) || n < 0 || (n > 0 && (!u || !g)))
+    return EI_ERR_INVALID_ARG;
+  if (n == 0) return EI_OK;
+  if (launch_nonlinearity(nonlin, prec, arith, n, u, g, dg, (cudaStream_t)cuda_stream) !=
+      cudaSuccess) {
+    cudaGetLastError();
+    return EI_ERR_CUDA;
+  }
+  return EI_OK;
+}
+
 ei_status ei_set_schedule_model(ei_ctx* c, const ei_mlp* model) {
   if (!c) return EI_ERR_INVALID_ARG;
   c->model = model;
@@ -1125,7 +1140,7 @@ ei_status ei_step(ei_ctx* c, int method, double h, void* u, int nonlin, double t
   if (!c || !u) return EI_ERR_INVALID_ARG;
   if (c->kind == KIND_NONE) return EI_ERR_STATE;
   if ((method != EI_EXP_EULER && method != EI_EXP_ROSENBROCK) ||
-      (nonlin != EI_NONLIN_NONE && nonlin != EI_NONLIN_LOGISTIC) || !(h > 0) || !isfinite(h) ||
+      nonlin < EI_NONLIN_NONE || nonlin > EI_NONLIN_COMBUSTION_FAST || !(h > 0) || !isfinite(h) ||
       !(tol > 0) || !isfinite(tol))
     return EI_ERR_INVALID_ARG;
   EI_TRY_CUDA(cudaSetDevice(c->device));

@@ -162,6 +162,80 @@ __device__ __forceinline__ double newton_update(double Aw, double invg, double n
 __device__ __forceinline__ float newton_update(float Aw, float invg, float nshift, float wc) {
   return fmaf(nshift, wc, Aw * invg);
 }
+// ---------------------------------------------------------------------------
+// The combustion term of Sec. III-C, g(u) = (2 - u) e^{20 (1 - 1/u)} / 4, and
+// g'(u) = e^{20 (1 - 1/u)} (20 (2 - u) / u^2 - 1) / 4; both 0 for u <= 0.025
+// (their limit as u -> 0+).  A NaN u gives NaN.
+// - float-float: the format's own reciprocal and exponential (df.cuh);
+// - double (the native FP64 format): the math library's exp and IEEE division;
+// - float: expf and IEEE division;
+// - fast (any format): __expf and __fdividef in FP32, the hardware
+//   approximations (the paper's "fast math" variant).
+// ---------------------------------------------------------------------------
+constexpr float COMBUSTION_CUT = 0.025f;
+__device__ __forceinline__ void combustion_eval(df u, df& g, df& dg) {
+  if (u.hi <= COMBUSTION_CUT) {
+    g = df{0.0f, 0.0f};
+    dg = df{0.0f, 0.0f};
+    return;
+  }
+  const df q = df_recip(u);
+  const df e4 = df_mul(df{0.25f, 0.0f}, df_exp(df_mul(df{20.0f, 0.0f}, df_add(df{1.0f, 0.0f}, df_neg(q)))));
+  const df tm = df_add(df{2.0f, 0.0f}, df_neg(u));
+  g = df_mul(e4, tm);
+  const df t = df_mul(df_mul(df{20.0f, 0.0f}, tm), df_mul(q, q));
+  dg = df_mul(e4, df_add(t, df{-1.0f, 0.0f}));
+}
+__device__ __forceinline__ void combustion_eval(double u, double& g, double& dg) {
+  if (u <= (double)COMBUSTION_CUT) {
+    g = 0.0;
+    dg = 0.0;
+    return;
+  }
+  const double q = 1.0 / u;
+  const double e4 = 0.25 * exp(20.0 * (1.0 - q));
+  g = e4 * (2.0 - u);
+  dg = e4 * (20.0 * (2.0 - u) * q * q - 1.0);
+}
+__device__ __forceinline__ void combustion_eval(float u, float& g, float& dg) {
+  if (u <= COMBUSTION_CUT) {
+    g = 0.0f;
+    dg = 0.0f;
+    return;
+  }
+  const float q = 1.0f / u;
+  const float e4 = 0.25f * expf(20.0f * (1.0f - q));
+  g = e4 * (2.0f - u);
+  dg = e4 * (20.0f * (2.0f - u) * q * q - 1.0f);
+}
+__device__ __forceinline__ void combustion_fast(float u, float& g, float& dg) {
+  if (u <= COMBUSTION_CUT) {
+    g = 0.0f;
+    dg = 0.0f;
+    return;
+  }
+  const float q = __fdividef(1.0f, u);
+  const float e4 = 0.25f * __expf(20.0f * (1.0f - q));
+  g = e4 * (2.0f - u);
+  dg = e4 * (20.0f * (2.0f - u) * q * q - 1.0f);
+}
+__device__ __forceinline__ float to_f(float x) { return x; }
+__device__ __forceinline__ float to_f(double x) { return (float)x; }
+__device__ __forceinline__ float to_f(df x) { return x.hi; }
+// g(u) and g'(u) of a combustion nonlinearity (EI_NONLIN_COMBUSTION or
+// EI_NONLIN_COMBUSTION_FAST) in the vector format T
+template <class T>
+__device__ __forceinline__ void combustion_term(int nonlin, T u, T& g, T& dg) {
+  if (nonlin == EI_NONLIN_COMBUSTION_FAST) {
+    float gf, dgf;
+    combustion_fast(to_f(u), gf, dgf);
+    g = from_d<T>((double)gf);
+    dg = from_d<T>((double)dgf);
+  } else {
+    combustion_eval(u, g, dg);
+  }
+}
+
 // squared-norm accumulators: lazily normalised pairs for float-float values
 template <class T> struct Acc {
   using type = T;

@@ -99,6 +99,9 @@ cudaError_t launch_stencil_gershgorin(const StencilDev& g, int user_prec, const 
                                       const void* D, double Dc, const void* const b[3],
                                       const double bc[3], const void* c, double cc, double* lo,
                                       double* hi, double* partials, DevCtl* ctl, cudaStream_t st);
+// pointwise nonlinearity over n elements (ei_nonlinearity)
+cudaError_t launch_nonlinearity(int nonlin, int prec, int arith, int64_t n, const void* u,
+                                void* g, void* dg, cudaStream_t stm);
 // CSR structure check: rowptr[0] == 0, rowptr[n] == nnz, rowptr nondecreasing,
 // every column in [0, n); a violation sets ctl->csr_bad (reset it first).
 cudaError_t launch_csr_validate(int64_t n, int64_t nnz, const int64_t* rowptr,

@@ -204,13 +204,17 @@ k_stencil_F(StencilDev g, const void* __restrict__ u_, void* __restrict__ F_,
     const int64_t idx = t * g.pitch + x;
     T uc;
     T Fv = apply_coef7<T>(g, u, db, x, y, z, idx, uc);
-    if (nonlin) Fv = mac(Fv, uc, sub(one, uc));  // g(u) = u(1-u)
-    st(F, idx, Fv);
-    if (rosenbrock) {
-      T q = ldg(db, idx);
-      if (nonlin) q = add(q, mac(one, mtwo, uc));  // g'(u) = 1 - 2u
-      st(dout, idx, q);
+    T gq = zero<T>();
+    if (nonlin == EI_NONLIN_LOGISTIC) {
+      Fv = mac(Fv, uc, sub(one, uc));  // g(u) = u(1-u)
+      gq = mac(one, mtwo, uc);         // g'(u) = 1 - 2u
+    } else if (nonlin != EI_NONLIN_NONE) {
+      T gv;
+      combustion_term(nonlin, uc, gv, gq);
+      Fv = add(Fv, gv);
     }
+    st(F, idx, Fv);
+    if (rosenbrock) st(dout, idx, nonlin ? add(ldg(db, idx), gq) : ldg(db, idx));
     af = mac(af, Fv, Fv);
   }
   double a = to_d(af), b = 0.0;
@@ -447,13 +451,17 @@ k_csr_F(CsrDev op, const void* __restrict__ u_, void* __restrict__ F_, void* __r
   if (row < op.n) {
     const T uc = ldg(u, row);
     T Fv = mac(csr_row<T>(op, u, row), ldg(cb, row), uc);
-    if (nonlin) Fv = mac(Fv, uc, sub(one, uc));
-    st(F, row, Fv);
-    if (rosenbrock) {
-      T q = ldg(cb, row);
-      if (nonlin) q = add(q, mac(one, from_d<T>(-2.0), uc));
-      st(qo, row, q);
+    T gq = zero<T>();
+    if (nonlin == EI_NONLIN_LOGISTIC) {
+      Fv = mac(Fv, uc, sub(one, uc));
+      gq = mac(one, from_d<T>(-2.0), uc);
+    } else if (nonlin != EI_NONLIN_NONE) {
+      T gv;
+      combustion_term(nonlin, uc, gv, gq);
+      Fv = add(Fv, gv);
     }
+    st(F, row, Fv);
+    if (rosenbrock) st(qo, row, nonlin ? add(ldg(cb, row), gq) : ldg(cb, row));
     af = acc_sq(af, Fv);
   }
   double a = acc_d(af), b = 0.0;
@@ -492,7 +500,24 @@ k_csr_gershgorin(int64_t n, const int64_t* __restrict__ rowptr, const int32_t* _
   }
 }
 
-// min/max of (lo + q), (hi + q), q = g'(u) = 1 - 2u for the logistic g
+// g'(u) of the caller's u for the Rosenbrock interval: FP64 arrays in
+// float-float (the FP64 pipes are slow), FP32 arrays in float
+__device__ __forceinline__ double nonlin_slope(int nonlin, double u) {
+  if (nonlin == EI_NONLIN_LOGISTIC) return 1.0 - 2.0 * u;
+  if (nonlin == EI_NONLIN_NONE) return 0.0;
+  df gv, dq;
+  combustion_term(nonlin, df_from_double(u), gv, dq);
+  return to_d(dq);
+}
+__device__ __forceinline__ double nonlin_slope(int nonlin, float u) {
+  if (nonlin == EI_NONLIN_LOGISTIC) return 1.0 - 2.0 * (double)u;
+  if (nonlin == EI_NONLIN_NONE) return 0.0;
+  float gv, dq;
+  combustion_term(nonlin, u, gv, dq);
+  return (double)dq;
+}
+
+// min/max of (lo + q), (hi + q), q = g'(u)
 template <class U>
 __global__ void __launch_bounds__(EI_TPB)
 k_shifted_minmax(int64_t n, const double* __restrict__ lo, const double* __restrict__ hi,
@@ -500,7 +525,7 @@ k_shifted_minmax(int64_t n, const double* __restrict__ lo, const double* __restr
   double mn = INFINITY, mx = -INFINITY;
   for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;
        i += (int64_t)gridDim.x * blockDim.x) {
-    const double q = nonlin ? 1.0 - 2.0 * (double)u[i] : 0.0;
+    const double q = nonlin_slope(nonlin, u[i]);
     mn = fmin(mn, lo[i] + q);
     mx = fmax(mx, hi[i] + q);
   }
@@ -738,6 +763,46 @@ cudaError_t launch_csr_F(const CsrDev& op, const void* u, void* F, void* qc_out,
                          double* partials, DevCtl* ctl, cudaStream_t stm) {
   const int nb = csr_blocks(op.n);
   EI_DISPATCH_FMT(fmt, (k_csr_F<F_><<<nb, EI_TPB, 0, stm>>>(op, u, F, qc_out, c_base, nonlin, rosenbrock, partials, ctl)));
+  return cudaGetLastError();
+}
+
+// Pointwise g(u) and g'(u) (Sec. III-C; Table 3 times this evaluation): U is
+// the array type, T the format the arithmetic runs in.
+template <class T, class U>
+__global__ void __launch_bounds__(EI_TPB)
+k_nonlin_eval(int nonlin, int64_t n, const U* u, U* g, U* dg) {
+  const T one = from_d<T>(1.0), mtwo = from_d<T>(-2.0);
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;
+       i += (int64_t)gridDim.x * blockDim.x) {
+    const T uc = from_d<T>((double)u[i]);
+    T gv = zero<T>(), dq = zero<T>();
+    if (nonlin == EI_NONLIN_LOGISTIC) {
+      gv = mul(uc, sub(one, uc));
+      dq = mac(one, mtwo, uc);
+    } else if (nonlin != EI_NONLIN_NONE) {
+      combustion_term(nonlin, uc, gv, dq);
+    }
+    g[i] = (U)to_d(gv);
+    if (dg) dg[i] = (U)to_d(dq);
+  }
+}
+
+cudaError_t launch_nonlinearity(int nonlin, int prec, int arith, int64_t n, const void* u,
+                                void* g, void* dg, cudaStream_t stm) {
+  const int nb = ew_blocks(n);
+  if (prec == EI_PREC_F32)
+    k_nonlin_eval<float, float><<<nb, EI_TPB, 0, stm>>>(nonlin, n, static_cast<const float*>(u),
+                                                        static_cast<float*>(g),
+                                                        static_cast<float*>(dg));
+  else if (arith == EI_ARITH_NATIVE_F64)
+    k_nonlin_eval<double, double><<<nb, EI_TPB, 0, stm>>>(nonlin, n,
+                                                          static_cast<const double*>(u),
+                                                          static_cast<double*>(g),
+                                                          static_cast<double*>(dg));
+  else
+    k_nonlin_eval<df, double><<<nb, EI_TPB, 0, stm>>>(nonlin, n, static_cast<const double*>(u),
+                                                      static_cast<double*>(g),
+                                                      static_cast<double*>(dg));
   return cudaGetLastError();
 }
 

@@ -18,7 +18,7 @@ BC_DIRICHLET0, BC_NEUMANN0 = 0, 1
 PREC_F64, PREC_F32 = 0, 1
 ARITH_DF, ARITH_NATIVE_F64 = 0, 1
 EXP_EULER, EXP_ROSENBROCK = 0, 1
-NONLIN_NONE, NONLIN_LOGISTIC = 0, 1
+NONLIN_NONE, NONLIN_LOGISTIC, NONLIN_COMBUSTION, NONLIN_COMBUSTION_FAST = 0, 1, 2, 3
 STATS_MAX_SUBSTEPS = 64
 MLP_INPUTS, MLP_OUTPUTS, MLP_PARAMS, MLP_MAX_Q = 12, 2, 9282, 12
 
@@ -32,6 +32,7 @@ EXPORTS = [
     "ei_mlp_create", "ei_mlp_destroy", "ei_mlp_set_params", "ei_mlp_get_params",
     "ei_mlp_set_decision", "ei_mlp_get_decision", "ei_mlp_forward", "ei_mlp_loss_grad",
     "ei_mlp_train_step", "ei_set_schedule_model", "ei_batch_set_schedule_model",
+    "ei_nonlinearity",
 ]
 
 
@@ -141,6 +142,7 @@ def lib():
                                         C.c_double, dp]
         L.ei_set_schedule_model.argtypes = [vp, vp]
         L.ei_batch_set_schedule_model.argtypes = [vp, vp]
+        L.ei_nonlinearity.argtypes = [C.c_int, C.c_int, C.c_int, C.c_int64, vp, vp, vp, vp]
         L.ei_status_string.argtypes = [C.c_int]
         L.ei_status_string.restype = C.c_char_p
         for name in EXPORTS:
@@ -182,6 +184,23 @@ def schedule(k, h, c, gamma, tol, m_max=100):
     s, m = C.c_int(0), C.c_int(0)
     _check(lib().ei_schedule(k, h, c, gamma, tol, m_max, C.byref(s), C.byref(m)), "ei_schedule")
     return s.value, m.value
+
+
+def nonlinearity(kind, u, g, dg=None, arith=ARITH_DF, stream=None):
+    """g = g(u) and, if dg is given, dg = g'(u), pointwise on the device
+    (ei_nonlinearity); u, g, dg contiguous CUDA float64 or float32 tensors of
+    one size.  Queued on `stream` (default: the current stream)."""
+    import torch
+    dt = u.dtype
+    if dt not in (torch.float64, torch.float32):
+        raise ValueError("u: float64 or float32 expected")
+    prec = PREC_F64 if dt == torch.float64 else PREC_F32
+    n = u.numel()
+    if stream is None:
+        stream = torch.cuda.current_stream(u.device)
+    _check(lib().ei_nonlinearity(kind, prec, arith, n, _dev_ptr(u, dt, n, "u"),
+                                 _dev_ptr(g, dt, n, "g"), _dev_ptr(dg, dt, n, "dg"),
+                                 C.c_void_p(stream.cuda_stream)), "ei_nonlinearity")
 
 
 # ---- context ---------------------------------------------------------------
