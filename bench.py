@@ -62,7 +62,8 @@ def parse():
     ap.add_argument("--workload", default="adr3d",
                     choices=["adr3d", "adr3d_fp32", "rgg_csr", "batch", "batch_fp32",
                              "adr3d_learned", "adr3d_fp32_learned", "rgg_csr_learned",
-                             "batch_learned_fp32", "batch_plain_fp64_loop"],
+                             "batch_learned_fp32", "batch_plain_fp64_loop", "combustion",
+                             "combustion_fast", "combustion_nonlin"],
                     help="adr3d (default, the headline): 256^3 FP64 Rosenbrock-Euler; "
                          "adr3d_fp32: 512^3 FP32 exponential Euler; rgg_csr: 2^20-node CSR phi_1")
     ap.add_argument("--no-cpu", action="store_true", help="skip the CPU baseline sample")
@@ -286,6 +287,126 @@ class Adr3dFp32(Adr3d):
     def kernel(self, fused):
         return ("k_newton2_tma<float> (two Newton iterations per launch)"
                 if fused == 2 else "k_newton_tma<float>")
+
+
+class Combustion3d(Adr3d):
+    """The combustion model of Sec. III-C with the step of Table 4: 256^3
+    interior points, Laplacian, homogeneous Dirichlet, u0 = 1, h = tol = 1e-4;
+    exponential Euler (Eq. (2)) with the combustion term fused into the F
+    kernel, at full precision (float-float) or with FP32 fast math."""
+
+    fast = False
+
+    def __init__(self, torch, ei, W, dev, ctx, n):
+        kind = "fast" if self.fast else "full"
+        self.name, self.method = f"combustion_{n}_fp64_exp_euler_{kind}", "exp_euler"
+        self.dtype = "f64 (float-float pairs on the FP32 pipes)"
+        self.ei, self.w = ei, W.combustion_3d(n=n)
+        w = self.w
+        self.npts = n ** 3
+        self.keep = []
+        ctx.set_operator_stencil(w.n, w.dx, w.D, list(w.b), 0.0, list(w.bc), ei.PREC_F64)
+        self.state0 = torch.from_numpy(w.u0).to(dev)
+        self.state = self.state0.clone()
+        self.host0 = w.u0
+        self.bytes_per_point = BYTES_PER_POINT
+        self.nonlin = ei.NONLIN_COMBUSTION_FAST if self.fast else ei.NONLIN_COMBUSTION
+        self.config = {"grid": [n] * 3, "h": w.h, "tol": w.tol, "bc": "dirichlet0",
+                       "method": self.method, "u0": 1.0,
+                       "nonlinearity": "combustion (2-u) e^{20(1-1/u)}/4, " +
+                       ("FP32 __expf/__fdividef" if self.fast else "float-float")}
+
+    def step(self, ctx, opts=None):
+        return ctx.step(self.ei.EXP_EULER, self.w.h, self.state, self.nonlin, self.w.tol, opts)
+
+    def step_host(self, ctx, host, opts=None):
+        return ctx.step_host(self.ei.EXP_EULER, self.w.h, host, self.nonlin, self.w.tol, opts)
+
+
+class Combustion3dFast(Combustion3d):
+    fast = True
+
+
+class NonlinStats:
+    """ei_stats-like record of one pointwise evaluation."""
+
+    def __init__(self, ms=0.0, timed=0):
+        self.launches = 1
+        self.matvecs = 0
+        self.newton_ms = ms
+        self.newton_timed = timed
+        self.newton_fused = 1
+
+    def degree_list(self):
+        return []
+
+
+class NonlinEval(Workload):
+    """Table 3 of the paper: one evaluation of the combustion term g(u) of
+    Sec. III-C at every point of an n^3 grid (u ~ U[1, 2]), FP64 arrays
+    evaluated in float-float (ei_nonlinearity).  The other variants (native
+    FP64, FP32, and FP32 fast math on FP64 and FP32 arrays) are timed once at
+    set-up and listed in the config."""
+
+    def __init__(self, torch, ei, W, dev, ctx, n):
+        self.name, self.method = f"combustion_nonlinearity_{n}", "g(u) pointwise"
+        self.dtype = "f64 (float-float on the FP32 pipes)"
+        self.ei, self.torch = ei, torch
+        u = W.combustion_field(n)
+        self.npts = n ** 3
+        self.host0 = u
+        self.state0 = torch.from_numpy(u).to(dev)
+        self.state = self.state0.clone()
+        self.g = torch.empty_like(self.state)
+        self.stream = ctx.stream
+        # read u 8 + write g 8
+        self.bytes_per_point = 16
+        u32 = self.state.to(torch.float32)
+        g32 = torch.empty_like(u32)
+        variants = {
+            "f64_float_float": (ei.NONLIN_COMBUSTION, self.state, self.g, ei.ARITH_DF),
+            "f64_native": (ei.NONLIN_COMBUSTION, self.state, self.g, ei.ARITH_NATIVE_F64),
+            "f64_fast_math": (ei.NONLIN_COMBUSTION_FAST, self.state, self.g, ei.ARITH_DF),
+            "f32_full": (ei.NONLIN_COMBUSTION, u32, g32, ei.ARITH_DF),
+            "f32_fast_math": (ei.NONLIN_COMBUSTION_FAST, u32, g32, ei.ARITH_DF),
+        }
+        ms = {}
+        for name, (kind, uu, gg, ar) in variants.items():
+            ms[name] = round(self._time(kind, uu, gg, ar), 4)
+        self.config = {"grid": [n] * 3, "u": "uniform [1, 2]", "variants_ms": ms,
+                       "l2_note": "one evaluation reads u and writes g once"}
+
+    def _run(self, kind, u, g, arith):
+        self.ei.nonlinearity(kind, u, g, None, arith=arith, stream=self.stream)
+
+    def _time(self, kind, u, g, arith, reps=10):
+        torch = self.torch
+        for _ in range(3):
+            self._run(kind, u, g, arith)
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(self.stream)
+        for _ in range(reps):
+            self._run(kind, u, g, arith)
+        e1.record(self.stream)
+        e1.synchronize()
+        return e0.elapsed_time(e1) / reps
+
+    def step(self, ctx, opts=None):
+        if opts and opts.get("profile"):
+            return NonlinStats(self._time(self.ei.NONLIN_COMBUSTION, self.state, self.g,
+                                          self.ei.ARITH_DF, reps=1), 1)
+        self._run(self.ei.NONLIN_COMBUSTION, self.state, self.g, self.ei.ARITH_DF)
+        return NonlinStats()
+
+    def step_host(self, ctx, host, opts=None):
+        d = host.to(self.state.device, non_blocking=True)
+        self._run(self.ei.NONLIN_COMBUSTION, d, self.g, self.ei.ARITH_DF)
+        pinned_like(self, host).copy_(self.g, non_blocking=False)
+        return NonlinStats()
+
+    def kernel(self, fused):
+        return "k_nonlin_eval<float-float> (combustion g(u), Table 3)"
 
 
 class RggCsr(Workload):
@@ -559,11 +680,14 @@ class RggCsrLearned(Learned, RggCsr):
 WORKLOADS = {"adr3d": Adr3d, "adr3d_fp32": Adr3dFp32, "rgg_csr": RggCsr, "batch": Batch2d,
              "batch_fp32": Batch2dFp32, "adr3d_learned": Adr3dLearned,
              "adr3d_fp32_learned": Adr3dFp32Learned, "rgg_csr_learned": RggCsrLearned,
-             "batch_learned_fp32": Batch2dLearnedFp32, "batch_plain_fp64_loop": Batch2dPlainLoop}
+             "batch_learned_fp32": Batch2dLearnedFp32, "batch_plain_fp64_loop": Batch2dPlainLoop,
+             "combustion": Combustion3d, "combustion_fast": Combustion3dFast,
+             "combustion_nonlin": NonlinEval}
 DEFAULT_N = {"adr3d": N_SIDE, "adr3d_fp32": 512, "rgg_csr": 1 << 20, "batch": 1024,
              "batch_fp32": 1024, "adr3d_learned": N_SIDE, "adr3d_fp32_learned": 512,
              "rgg_csr_learned": 1 << 20, "batch_learned_fp32": 1024,
-             "batch_plain_fp64_loop": 1024}
+             "batch_plain_fp64_loop": 1024, "combustion": N_SIDE, "combustion_fast": N_SIDE,
+             "combustion_nonlin": N_SIDE}
 
 
 def replica_group(world, backend):

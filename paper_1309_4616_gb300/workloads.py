@@ -15,6 +15,9 @@ Workloads (sizes as the paper's experiments use them, Sec. III-A to III-D):
                   u_0 a sum of 4 Gaussians (sigma = 0.05) scaled into [0, 1].
   batch_2d        1024 independent 2D advection-diffusion problems with
                   log-uniform sides in [32, 512] and per-side Dirichlet/Neumann.
+  combustion_3d   Sec. III-C combustion model, Table 4 step: 256^3 interior,
+                  Laplacian, homogeneous Dirichlet, u0 = 1, h = tol = 1e-4.
+  combustion_field  u ~ U[1, 2] on n^3 points (Table 3's evaluation).
   rgg_graph       -(graph Laplacian) of a random geometric graph in the unit
                   cube: 2^20 nodes, mean degree 12, edge weights U[0.5, 2].
 """
@@ -133,6 +136,23 @@ def adr_3d(n: int = 256, seed: int = SEED_BASE + 1, h: float = 1e-4,
 def adr_3d_fp32(n: int = 512, seed: int = SEED_BASE + 2) -> Stencil3D:
     """The reduced-precision workload: same fields on 512^3, h = 5e-5, tol 1e-6."""
     return adr_3d(n=n, seed=seed, h=5e-5, tol=1e-6, steps=10)
+
+
+def combustion_3d(n: int = 256, h: float = 1e-4, tol: float = 1e-4, steps: int = 1) -> Stencil3D:
+    """The combustion model of Sec. III-C, u_t = Laplace(u) + g(u) with
+    g(u) = (2 - u) e^{20 (1 - 1/u)} / 4, with the step of Table 4: n^3
+    interior points of the unit cube (dx = 1/(n+1)), homogeneous Dirichlet
+    boundaries, u0 = 1, h = tol = 1e-4.  D and b are constants (1 and 0),
+    given as scalars."""
+    dx = 1.0 / (n + 1)
+    return Stencil3D(n=(n, n, n), dx=(dx, dx, dx), D=1.0, b=(0.0, 0.0, 0.0),
+                     bc=(DIRICHLET0,) * 6, u0=np.ones((n, n, n)), h=h, tol=tol, steps=steps)
+
+
+def combustion_field(n: int, seed: int = SEED_BASE + 5) -> np.ndarray:
+    """u uniform in [1, 2] (the combustion model's range) on n^3 points: the
+    input of the pointwise evaluation timed in Table 3."""
+    return np.random.default_rng(seed).uniform(1.0, 2.0, (n, n, n))
 
 
 # --------------------------------------------------------------------------
