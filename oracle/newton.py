@@ -249,24 +249,31 @@ def nonlinearity(u, kind):
     return np.zeros_like(u), np.zeros_like(u)
 
 
-def exp_euler_step(op, u, h, tol, nonlin=NONLIN_NONE, xi=None):
+def exp_euler_step(op, u, h, tol, nonlin=NONLIN_NONE, xi=None, bvec=None):
     """Eq. (2) with A -> -A:  u_{n+1} = e^{hA}u_n + h phi_1(hA) g(u_n)
-    = u_n + h phi_1(hA)(A u_n + g(u_n))."""
+    = u_n + h phi_1(hA)(A u_n + g(u_n)).  bvec: the constant forcing b_D of
+    inhomogeneous Dirichlet data (StencilOperator.boundary_vector), added to
+    A u_n + g(u_n)."""
     stats = Stats()
     u = np.asarray(u, dtype=np.float64).reshape(op.shape)
     g, _ = nonlinearity(u, nonlin)
     F = op.matvec(u) + g
+    if bvec is not None:
+        F = F + np.asarray(bvec, dtype=np.float64).reshape(op.shape)
     stats.matvecs += 1
     return u + h_phi1_substeps(op, h, F, tol, stats, xi=xi), stats
 
 
-def exp_rosenbrock_step(op, u, h, tol, nonlin=NONLIN_LOGISTIC, xi=None):
+def exp_rosenbrock_step(op, u, h, tol, nonlin=NONLIN_LOGISTIC, xi=None, bvec=None):
     """Exponential Rosenbrock-Euler: J_n = A + diag(g'(u_n)),
-    u_{n+1} = u_n + h phi_1(h J_n)(A u_n + g(u_n))."""
+    u_{n+1} = u_n + h phi_1(h J_n)(A u_n + b_D + g(u_n)); bvec = b_D as in
+    exp_euler_step (a constant forcing: J_n is unchanged)."""
     stats = Stats()
     u = np.asarray(u, dtype=np.float64).reshape(op.shape)
     g, dg = nonlinearity(u, nonlin)
     F = op.matvec(u) + g
+    if bvec is not None:
+        F = F + np.asarray(bvec, dtype=np.float64).reshape(op.shape)
     stats.matvecs += 1
     J = ShiftedOperator(op, dg)
     return u + h_phi1_substeps(J, h, F, tol, stats, xi=xi), stats

@@ -42,6 +42,7 @@ class StencilOperator:
         if bc is None:
             bc = (DIRICHLET0,) * (2 * self.dim)
         self.bc = tuple(bc)
+        self._D, self._b = D, b
         Darr = np.broadcast_to(np.asarray(D, dtype=np.float64), self.shape)
         diag = np.zeros(self.shape)
         self.off = {}
@@ -76,6 +77,35 @@ class StencilOperator:
         if c is not None:
             diag = diag + np.broadcast_to(np.asarray(c, dtype=np.float64), self.shape)
         self.diag = diag
+
+    def face_shape(self, face):
+        """Shape of face `face` (2 ax + side): the grid without axis ax."""
+        npax = self.dim - 1 - face // 2
+        return tuple(v for k, v in enumerate(self.shape) if k != npax)
+
+    def boundary_vector(self, faces) -> np.ndarray:
+        """Inhomogeneous Dirichlet data (the paper's boundary functions f of
+        Sec. III-A): at a DIRICHLET0 face the ghost value is the prescribed
+        value instead of 0, so each row next to that face gains its face
+        coefficient, D_i/dx^2 + sgn b_i/(2 dx) (the ghost D is D_i), times the
+        value.  faces: one array of face_shape(f) per face, or None (zero).
+        Returns b_D, with A u + b_D the operator applied to u and its data."""
+        out = np.zeros(self.shape)
+        for face, vals in enumerate(faces[: 2 * self.dim]):
+            if vals is None:
+                continue
+            if self.bc[face] != DIRICHLET0:
+                raise ValueError(f"face {face}: boundary values need a Dirichlet face")
+            ax, sgn = face // 2, (-1 if face % 2 == 0 else 1)
+            npax = self.dim - 1 - ax
+            vals = np.asarray(vals, dtype=np.float64).reshape(self.face_shape(face))
+            sl = [slice(None)] * self.dim
+            sl[npax] = 0 if sgn < 0 else self.shape[npax] - 1
+            Dx = np.broadcast_to(np.asarray(self._D, dtype=np.float64), self.shape)[tuple(sl)]
+            bx = np.broadcast_to(np.asarray(self._b[ax], dtype=np.float64), self.shape)[tuple(sl)]
+            h = self.dx[ax]
+            out[tuple(sl)] += (Dx / (h * h) + sgn * bx / (2.0 * h)) * vals
+        return out
 
     # (A u)_i = diag_i u_i + sum_nb coef_nb,i u_nb
     def matvec(self, u: np.ndarray) -> np.ndarray:
