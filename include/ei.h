@@ -228,6 +228,23 @@ ei_status ei_step(ei_ctx* ctx, int method, double h, void* u, int nonlin, double
 ei_status ei_step_host(ei_ctx* ctx, int method, double h, void* u_host, int nonlin, double tol,
                        const ei_options* opt, ei_stats* stats);
 
+/* Inhomogeneous Dirichlet data (Sec. III-A: boundary functions f on the
+ * faces of the domain).  faces[f], f < 2*dim (f = 2*axis + side, side 0 the
+ * lower face): NULL (homogeneous: ghost value 0) or a device array of the
+ * prescribed values at the face's ghost points, in the operator's precision:
+ *   faces 0, 1 (x = lower, upper): ny*nz values, index z*ny + y;
+ *   faces 2, 3 (y): nx*nz values, index z*nx + x;
+ *   faces 4, 5 (z, 3D only): nx*ny values, index y*nx + x.
+ * The arrays are read before the call returns (the library keeps its own
+ * FP64 face terms: face coefficient D_i/dx^2 +- b_i/(2dx) x value).
+ * Effect: ei_step forms A u + b_D + g(u), b_D the face terms at the rows next
+ * to each face; b_D is a constant forcing, so the Newton loop, the Rosenbrock
+ * Jacobian and ei_phi_apply use the linear A.  faces == NULL (or all NULL)
+ * clears the data; ei_set_operator_* clears it too.
+ * Errors: EI_ERR_STATE without a stencil operator; EI_ERR_INVALID_ARG for
+ * data on a Neumann face or on a face beyond 2*dim. */
+ei_status ei_set_dirichlet_values(ei_ctx* ctx, const void* const faces[6]);
+
 /* Pointwise nonlinearity, Sec. III-C (the paper's Table 3 times exactly this
  * evaluation): g[i] = g(u[i]) and, when dg is not NULL, dg[i] = g'(u[i]),
  * for 0 <= i < n.

@@ -64,6 +64,7 @@ struct ei_ctx {
   // stencil description (caller's arrays are referenced, not copied)
   StencilDev sd{};
   double dx[3] = {1, 1, 1};
+  double* face_term[6] = {nullptr, nullptr, nullptr, nullptr, nullptr, nullptr};  // b_D by face
   const void* Du = nullptr;
   double Dc = 0;
   const void* bu[3] = {nullptr, nullptr, nullptr};
@@ -160,7 +161,15 @@ static void free_prepared(Prepared& p) {
   p.n_alloc = 0;
 }
 
+static void free_faces(ei_ctx* c) {
+  for (auto& f : c->face_term) {
+    if (f) cudaFree(f);
+    f = nullptr;
+  }
+}
+
 static void free_operator(ei_ctx* c) {
+  free_faces(c);
   for (auto& p : c->prep) free_prepared(p);
   if (c->ger_lo) cudaFree(c->ger_lo);
   if (c->ger_hi) cudaFree(c->ger_hi);
@@ -940,6 +949,35 @@ ei_status ei_set_operator_csr(ei_ctx* c, int64_t n, int64_t nnz, const int64_t* 
   return EI_OK;
 }
 
+ei_status ei_set_dirichlet_values(ei_ctx* c, const void* const faces[6]) {
+  if (!c) return EI_ERR_INVALID_ARG;
+  if (c->kind != KIND_STENCIL) return EI_ERR_STATE;
+  const StencilDev& s = c->sd;
+  for (int f = 0; f < 6 && faces; ++f)
+    if (faces[f] && (f >= 2 * s.dim || s.bc[f] != EI_BC_DIRICHLET0)) return EI_ERR_INVALID_ARG;
+  EI_TRY_CUDA(cudaSetDevice(c->device));
+  cudaStreamSynchronize(c->stream);
+  free_faces(c);
+  if (!faces) return EI_OK;
+  for (int f = 0; f < 2 * s.dim; ++f) {
+    if (!faces[f]) continue;
+    const int ax = f / 2;
+    const int64_t m = ax == 0 ? (int64_t)s.ny * s.nz : ax == 1 ? (int64_t)s.nx * s.nz
+                                                              : (int64_t)s.nx * s.ny;
+    ei_status st = alloc((void**)&c->face_term[f], sizeof(double) * m);
+    if (st != EI_OK) { free_faces(c); return st; }
+    if (launch_face_term(s, f, c->prec, c->dx, c->Du, c->Dc, c->bu[ax], c->bcst[ax], faces[f],
+                         c->face_term[f], c->stream) != cudaSuccess) {
+      cudaGetLastError();
+      free_faces(c);
+      return EI_ERR_CUDA;
+    }
+  }
+  // the caller's arrays are read before the call returns
+  EI_TRY_CUDA(cudaStreamSynchronize(c->stream));
+  return EI_OK;
+}
+
 ei_status ei_nonlinearity(int nonlin, int prec, int arith, int64_t n, const void* u, void* g,
                           void* dg, void* cuda_stream) {
   if (nonlin < EI_NONLIN_NONE || nonlin > EI_NONLIN_COMBUSTION_FAST ||
@@ -1098,8 +1136,10 @@ static ei_status step_impl(ei_ctx* c, int method, double h, void* u, int nonlin,
   EI_LAUNCH(launch_import(P.u, fmt, u, c->prec, n, geo_nx(c), c->kind == KIND_STENCIL ? c->sd.ny : 1, geo_pitch(c), c->partials, c->ctl,
                          c->stream));
   if (c->kind == KIND_STENCIL) {
+    BndFaces bnd;
+    for (int f = 0; f < 6; ++f) bnd.c[f] = c->face_term[f];
     EI_LAUNCH(launch_stencil_F(stencil_view(c, P, base_diag(P)), P.u, P.v, base_diag(P), P.qc,
-                               nonlin, rosen, fmt, c->partials, c->ctl, c->stream));
+                               nonlin, rosen, bnd, fmt, c->partials, c->ctl, c->stream));
   } else {
     EI_LAUNCH(launch_csr_F(csr_view(c, P, P.cbase), P.u, P.v, P.qc, P.cbase, nonlin, rosen,
                              fmt, c->partials, c->ctl, c->stream));

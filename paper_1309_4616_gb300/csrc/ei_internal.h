@@ -146,9 +146,18 @@ cudaError_t launch_zero(void* x, int fmt, int64_t n_alloc, cudaStream_t st);
 // Step start: F = A u + g(u), with A's diagonal from `diag_base`, and
 // diag_out = diag_base + g'(u) (Rosenbrock).
 // u in vector format.  ||F||^2 into ctl->sum0, finiteness into ctl->sum1.
+// inhomogeneous Dirichlet data: per face the FP64 term (face coefficient x
+// prescribed value) added to A u at the rows next to that face; NULL: none
+struct BndFaces {
+  const double* c[6];
+};
+// face term of face f from the caller's values (operator precision prec)
+cudaError_t launch_face_term(const StencilDev& g, int face, int prec, const double dx[3],
+                             const void* D, double D_const, const void* b_axis,
+                             double b_const, const void* vals, double* out, cudaStream_t stm);
 cudaError_t launch_stencil_F(const StencilDev& op, const void* u, void* F, const void* diag_base,
-                             void* diag_out, int nonlin, int rosenbrock, int fmt,
-                             double* partials, DevCtl* ctl, cudaStream_t st);
+                             void* diag_out, int nonlin, int rosenbrock, const BndFaces& bnd,
+                             int fmt, double* partials, DevCtl* ctl, cudaStream_t st);
 cudaError_t launch_csr_F(const CsrDev& op, const void* u, void* F, void* qc_out,
                          const void* c_base, int nonlin, int rosenbrock, int fmt,
                          double* partials, DevCtl* ctl, cudaStream_t st);

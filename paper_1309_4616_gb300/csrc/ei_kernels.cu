@@ -181,12 +181,14 @@ k_stencil_residual(StencilDev g, const void* __restrict__ y_, const void* __rest
   }
 }
 
-// F = A u + g(u); diag_out = diag_base + g'(u) (Rosenbrock)
+// F = A u + b_D + g(u); diag_out = diag_base + g'(u) (Rosenbrock).  b_D, the
+// inhomogeneous Dirichlet data, is read only at the rows next to a face that
+// has it (BndFaces).
 template <int FMT>
 __global__ void __launch_bounds__(EI_TPB)
 k_stencil_F(StencilDev g, const void* __restrict__ u_, void* __restrict__ F_,
             const void* __restrict__ db_, void* __restrict__ dout_, int nonlin, int rosenbrock,
-            double* partials, DevCtl* ctl) {
+            BndFaces bnd, double* partials, DevCtl* ctl) {
   using T = typename VT<FMT>::T;
   const T* __restrict__ u = static_cast<const T*>(u_);
   const T* __restrict__ db = static_cast<const T*>(db_);
@@ -204,6 +206,16 @@ k_stencil_F(StencilDev g, const void* __restrict__ u_, void* __restrict__ F_,
     const int64_t idx = t * g.pitch + x;
     T uc;
     T Fv = apply_coef7<T>(g, u, db, x, y, z, idx, uc);
+    if (x == 0 || x == g.nx - 1 || y == 0 || y == g.ny - 1 || z == 0 || z == g.nz - 1) {
+      double bd = 0.0;
+      if (x == 0 && bnd.c[0]) bd += bnd.c[0][(int64_t)z * g.ny + y];
+      if (x == g.nx - 1 && bnd.c[1]) bd += bnd.c[1][(int64_t)z * g.ny + y];
+      if (y == 0 && bnd.c[2]) bd += bnd.c[2][(int64_t)z * g.nx + x];
+      if (y == g.ny - 1 && bnd.c[3]) bd += bnd.c[3][(int64_t)z * g.nx + x];
+      if (z == 0 && bnd.c[4]) bd += bnd.c[4][(int64_t)y * g.nx + x];
+      if (z == g.nz - 1 && bnd.c[5]) bd += bnd.c[5][(int64_t)y * g.nx + x];
+      if (bd != 0.0) Fv = add(Fv, from_d<T>(bd));
+    }
     T gq = zero<T>();
     if (nonlin == EI_NONLIN_LOGISTIC) {
       Fv = mac(Fv, uc, sub(one, uc));  // g(u) = u(1-u)
@@ -728,10 +740,54 @@ cudaError_t launch_stencil_residual(const StencilDev& g, const void* y, const vo
 }
 
 cudaError_t launch_stencil_F(const StencilDev& g, const void* u, void* F, const void* diag_base,
-                             void* diag_out, int nonlin, int rosenbrock, int fmt,
-                             double* partials, DevCtl* ctl, cudaStream_t stm) {
+                             void* diag_out, int nonlin, int rosenbrock, const BndFaces& bnd,
+                             int fmt, double* partials, DevCtl* ctl, cudaStream_t stm) {
   const int nb = ew_blocks((int64_t)g.nx * g.ny * g.nz);
-  EI_DISPATCH_FMT(fmt, (k_stencil_F<F_><<<nb, EI_TPB, 0, stm>>>(g, u, F, diag_base, diag_out, nonlin, rosenbrock, partials, ctl)));
+  EI_DISPATCH_FMT(fmt, (k_stencil_F<F_><<<nb, EI_TPB, 0, stm>>>(g, u, F, diag_base, diag_out, nonlin, rosenbrock, bnd, partials, ctl)));
+  return cudaGetLastError();
+}
+
+// Face term of face f (2 ax + side): at each boundary row next to the face,
+// (D_i/dx^2 + sgn b_i/(2 dx)) x the prescribed ghost value (the ghost D is D_i),
+// in FP64 from the caller's arrays (contiguous, x fastest) or constants.
+// Face layout: faces 0/1 [z][y], 2/3 [z][x], 4/5 [y][x].
+template <class U>
+__global__ void __launch_bounds__(EI_TPB)
+k_face_term(StencilDev g, int face, double h, const U* D, double Dc, const U* b, double bc,
+            const U* vals, double* out) {
+  const int ax = face / 2;
+  const double sgn = (face & 1) ? 1.0 : -1.0;
+  const int64_t m0 = ax == 0 ? g.ny : g.nx;           // fastest index of the face
+  const int64_t m1 = ax == 2 ? g.ny : g.nz;
+  for (int64_t j = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; j < m0 * m1;
+       j += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t a0 = j % m0, a1 = j / m0;
+    int64_t x, y, z;
+    if (ax == 0) { x = (face & 1) ? g.nx - 1 : 0; y = a0; z = a1; }
+    else if (ax == 1) { x = a0; y = (face & 1) ? g.ny - 1 : 0; z = a1; }
+    else { x = a0; y = a1; z = (face & 1) ? g.nz - 1 : 0; }
+    const int64_t i = (z * g.ny + y) * g.nx + x;
+    const double Di = D ? (double)D[i] : Dc;
+    const double bi = b ? (double)b[i] : bc;
+    out[j] = (Di / (h * h) + sgn * bi / (2.0 * h)) * (double)vals[j];
+  }
+}
+
+cudaError_t launch_face_term(const StencilDev& g, int face, int prec, const double dx[3],
+                             const void* D, double D_const, const void* b_axis,
+                             double b_const, const void* vals, double* out, cudaStream_t stm) {
+  const int ax = face / 2;
+  const int64_t m = (ax == 0 ? (int64_t)g.ny * g.nz : ax == 1 ? (int64_t)g.nx * g.nz
+                                                               : (int64_t)g.nx * g.ny);
+  const int nb = ew_blocks(m);
+  if (prec == EI_PREC_F32)
+    k_face_term<float><<<nb, EI_TPB, 0, stm>>>(g, face, dx[ax], static_cast<const float*>(D),
+                                                D_const, static_cast<const float*>(b_axis),
+                                                b_const, static_cast<const float*>(vals), out);
+  else
+    k_face_term<double><<<nb, EI_TPB, 0, stm>>>(g, face, dx[ax], static_cast<const double*>(D),
+                                                 D_const, static_cast<const double*>(b_axis),
+                                                 b_const, static_cast<const double*>(vals), out);
   return cudaGetLastError();
 }
 cudaError_t launch_csr_newton(const CsrDev& op, const void* w_in, void* w_out, void* p,

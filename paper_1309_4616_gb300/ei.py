@@ -32,7 +32,7 @@ EXPORTS = [
     "ei_mlp_create", "ei_mlp_destroy", "ei_mlp_set_params", "ei_mlp_get_params",
     "ei_mlp_set_decision", "ei_mlp_get_decision", "ei_mlp_forward", "ei_mlp_loss_grad",
     "ei_mlp_train_step", "ei_set_schedule_model", "ei_batch_set_schedule_model",
-    "ei_nonlinearity",
+    "ei_nonlinearity", "ei_set_dirichlet_values",
 ]
 
 
@@ -143,6 +143,7 @@ def lib():
         L.ei_set_schedule_model.argtypes = [vp, vp]
         L.ei_batch_set_schedule_model.argtypes = [vp, vp]
         L.ei_nonlinearity.argtypes = [C.c_int, C.c_int, C.c_int, C.c_int64, vp, vp, vp, vp]
+        L.ei_set_dirichlet_values.argtypes = [vp, C.POINTER(vp)]
         L.ei_status_string.argtypes = [C.c_int]
         L.ei_status_string.restype = C.c_char_p
         for name in EXPORTS:
@@ -230,6 +231,7 @@ class Context:
         self._keep = []
         self.prec = PREC_F64
         self.n = 0
+        self._grid = (0, 0, 0)
 
     def close(self):
         if getattr(self, "_h", None):
@@ -253,6 +255,7 @@ class Context:
         for v in n:
             npts *= int(v)
         dt = self._dtype(prec)
+        self._grid = tuple(int(v) for v in (list(n) + [1] * (3 - dim)))
         n3 = (C.c_int64 * 3)(*(list(n) + [1] * (3 - dim)))
         dx3 = (C.c_double * 3)(*(list(dx) + [1.0] * (3 - dim)))
         bc = bc if bc is not None else [BC_DIRICHLET0] * (2 * dim)
@@ -289,6 +292,22 @@ class Context:
             _dev_ptr(diag, dt, int(n), "diag"), prec), "ei_set_operator_csr")
         self.prec = prec
         self.n = int(n)
+
+    def set_dirichlet_values(self, faces):
+        """Inhomogeneous Dirichlet data (ei_set_dirichlet_values): a list of up
+        to six device tensors (or None) in the operator's precision, face f of
+        the size and index order include/ei.h gives; None clears all."""
+        if faces is None:
+            _check(lib().ei_set_dirichlet_values(self._h, None), "ei_set_dirichlet_values")
+            return
+        dt = self._dtype(self.prec)
+        nx, ny, nz = self._grid
+        size = [ny * nz, ny * nz, nx * nz, nx * nz, nx * ny, nx * ny]
+        arr = (C.c_void_p * 6)()
+        for f in range(6):
+            t = faces[f] if f < len(faces) else None
+            arr[f] = _dev_ptr(t, dt, size[f], f"face {f}")
+        _check(lib().ei_set_dirichlet_values(self._h, arr), "ei_set_dirichlet_values")
 
     def estimate_spectrum(self):
         a, b = C.c_double(), C.c_double()
