@@ -63,7 +63,8 @@ def parse():
                     choices=["adr3d", "adr3d_fp32", "rgg_csr", "batch", "batch_fp32",
                              "adr3d_learned", "adr3d_fp32_learned", "rgg_csr_learned",
                              "batch_learned_fp32", "batch_plain_fp64_loop", "combustion",
-                             "combustion_fast", "combustion_nonlin"],
+                             "combustion_fast", "combustion_nonlin", "heat_dirichlet_data",
+                             "heat_dirichlet_hom"],
                     help="adr3d (default, the headline): 256^3 FP64 Rosenbrock-Euler; "
                          "adr3d_fp32: 512^3 FP32 exponential Euler; rgg_csr: 2^20-node CSR phi_1")
     ap.add_argument("--no-cpu", action="store_true", help="skip the CPU baseline sample")
@@ -325,6 +326,57 @@ class Combustion3d(Adr3d):
 
 class Combustion3dFast(Combustion3d):
     fast = True
+
+
+class HeatDirichlet(Adr3d):
+    """The boundary conditions of Sec. III-A on the Table 4 grid: u_t = Laplace(u)
+    on 256^3 interior points (dx = 1/257), Dirichlet faces,
+    u0 = sin(pi x) sin(pi y) sin(pi z), one exponential Euler step
+    (h = tol = 1e-4).  With data: the paper's boundary
+    function sin(pi z) exp(-xy) on all six faces (ei_set_dirichlet_values);
+    without: homogeneous."""
+
+    data = True
+
+    def __init__(self, torch, ei, W, dev, ctx, n):
+        kind = "sin(pi z)exp(-xy)" if self.data else "homogeneous"
+        self.name = f"heat_{n}_dirichlet_{'data' if self.data else 'hom'}_exp_euler"
+        self.method = "exp_euler"
+        self.dtype = "f64 (float-float pairs on the FP32 pipes)"
+        self.ei, self.w = ei, W.combustion_3d(n=n)
+        w = self.w
+        self.npts = n ** 3
+        self.keep = []
+        ctx.set_operator_stencil(w.n, w.dx, 1.0, [0.0, 0.0, 0.0], 0.0, list(w.bc), ei.PREC_F64)
+        if self.data:
+            ax = np.arange(1, n + 1) / (n + 1)
+            P, Q = np.meshgrid(ax, ax, indexing="ij")  # [slow, fast]
+            f = lambda x, y, z: np.sin(np.pi * z) * np.exp(-x * y)
+            faces = [f(0 * P, Q, P), f(1 + 0 * P, Q, P), f(Q, 0 * P, P), f(Q, 1 + 0 * P, P),
+                     f(Q, P, 0 * P), f(Q, P, 1 + 0 * P)]
+            self.keep = [torch.from_numpy(np.ascontiguousarray(x)).to(dev) for x in faces]
+            ctx.set_dirichlet_values(self.keep)
+        s1 = np.sin(np.pi * np.arange(1, n + 1) / (n + 1))
+        u0 = s1[:, None, None] * s1[None, :, None] * s1[None, None, :]
+        self.state0 = torch.from_numpy(u0).to(dev)
+        self.state = self.state0.clone()
+        self.host0 = u0
+        self.bytes_per_point = BYTES_PER_POINT
+        self.config = {"grid": [n] * 3, "h": w.h, "tol": w.tol, "bc": "dirichlet",
+                       "boundary_data": kind, "method": self.method,
+                       "u0": "sin(pi x) sin(pi y) sin(pi z)"}
+
+    def step(self, ctx, opts=None):
+        return ctx.step(self.ei.EXP_EULER, self.w.h, self.state, self.ei.NONLIN_NONE, self.w.tol,
+                        opts)
+
+    def step_host(self, ctx, host, opts=None):
+        return ctx.step_host(self.ei.EXP_EULER, self.w.h, host, self.ei.NONLIN_NONE, self.w.tol,
+                             opts)
+
+
+class HeatDirichletHom(HeatDirichlet):
+    data = False
 
 
 class NonlinStats:
@@ -682,12 +734,14 @@ WORKLOADS = {"adr3d": Adr3d, "adr3d_fp32": Adr3dFp32, "rgg_csr": RggCsr, "batch"
              "adr3d_fp32_learned": Adr3dFp32Learned, "rgg_csr_learned": RggCsrLearned,
              "batch_learned_fp32": Batch2dLearnedFp32, "batch_plain_fp64_loop": Batch2dPlainLoop,
              "combustion": Combustion3d, "combustion_fast": Combustion3dFast,
-             "combustion_nonlin": NonlinEval}
+             "combustion_nonlin": NonlinEval, "heat_dirichlet_data": HeatDirichlet,
+             "heat_dirichlet_hom": HeatDirichletHom}
 DEFAULT_N = {"adr3d": N_SIDE, "adr3d_fp32": 512, "rgg_csr": 1 << 20, "batch": 1024,
              "batch_fp32": 1024, "adr3d_learned": N_SIDE, "adr3d_fp32_learned": 512,
              "rgg_csr_learned": 1 << 20, "batch_learned_fp32": 1024,
              "batch_plain_fp64_loop": 1024, "combustion": N_SIDE, "combustion_fast": N_SIDE,
-             "combustion_nonlin": N_SIDE}
+             "combustion_nonlin": N_SIDE, "heat_dirichlet_data": N_SIDE,
+             "heat_dirichlet_hom": N_SIDE}
 
 
 def replica_group(world, backend):
