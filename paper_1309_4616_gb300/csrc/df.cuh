@@ -180,3 +180,34 @@ __device__ __forceinline__ df df_exp(df x) {
   const int ki = (int)k;
   return df{ldexpf(p.hi, ki), ldexpf(p.lo, ki)};
 }
+
+// ---- double -> float-float without the FP64 pipe ----------------------------
+// From the IEEE-754 fields: hi = sign, exponent and the top 23 fraction bits
+// (x cut to 24 significant bits, exact as a float); lo = the remaining 29
+// fraction bits as an integer converted to float and scaled by 2^(e - 52),
+// exact up to its single rounding; a fast two-sum renormalises the pair
+// (|lo| < ulp(hi)).  Zeros, and magnitudes below 2^-150 (zero in the format's
+// range), give signed zeros; the few others outside [2^-96, 2^128) -- float
+// subnormal range, huge, infinite, NaN -- take df_from_double.  The result agrees with df_from_double
+// to the format's precision (both keep 48 of the 53 bits).
+__device__ __forceinline__ float df_pow2f(int k) {  // 2^k as a float, k >= -149
+  return k >= -126 ? __uint_as_float((unsigned)(k + 127) << 23)
+                   : __uint_as_float(1u << (k + 149));
+}
+__device__ __forceinline__ df df_split_double(double x) {
+  const unsigned long long b = (unsigned long long)__double_as_longlong(x);
+  const unsigned hw = (unsigned)(b >> 32), lw = (unsigned)b;
+  if ((b << 1) == 0ull) return df{__uint_as_float(hw & 0x80000000u), 0.0f};  // +-0
+  const int e = (int)((hw >> 20) & 0x7ffu) - 1023;
+  // below 2^-150 the float-float value is a signed zero (the format's range)
+  if (e < -150) return df{__uint_as_float(hw & 0x80000000u), 0.0f};
+  if (e < -96 || e > 127) return df_from_double(x);
+  const unsigned sgn = hw & 0x80000000u;
+  const float hi = __uint_as_float(sgn | ((unsigned)(e + 127) << 23) |
+                                   ((hw & 0xfffffu) << 3) | (lw >> 29));
+  float lo = __uint2float_rn(lw & 0x1fffffffu) * df_pow2f(e - 52);
+  lo = sgn ? -lo : lo;
+  df r;
+  fast_two_sum(hi, lo, r.hi, r.lo);
+  return r;
+}

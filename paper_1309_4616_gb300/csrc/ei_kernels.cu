@@ -24,6 +24,47 @@ __device__ __forceinline__ int64_t pidx(int64_t i, int nx, int pitch) {
   return t * pitch + (i - t * nx);
 }
 
+// (x, y, z) and the row t = z*ny + y of logical point i; 32-bit division
+// when the grid has fewer than 2^31 points (the usual case)
+__device__ __forceinline__ void grid_coords(const StencilDev& g, int64_t n, int64_t i, int& x,
+                                            int& y, int& z, int64_t& t) {
+  if (n < ((int64_t)1 << 31)) {
+    const unsigned ui = (unsigned)i, tt = ui / (unsigned)g.nx;
+    x = (int)(ui - tt * (unsigned)g.nx);
+    y = (int)(tt % (unsigned)g.ny);
+    z = (int)(tt / (unsigned)g.ny);
+    t = tt;
+  } else {
+    t = i / g.nx;
+    x = (int)(i - t * g.nx);
+    y = (int)(t % g.ny);
+    z = (int)(t / g.ny);
+  }
+}
+
+// Walk of the rows (y, z) of a grid by warps, grid-stride: a warp takes one
+// row at a time and its lanes stride along x, so a point costs no division
+// and the loads of a warp are contiguous.
+#define EI_FOR_ROWS(nrows, row)                                                        \
+  for (int64_t row = blockIdx.x * (int64_t)(blockDim.x >> 5) + (threadIdx.x >> 5);    \
+       row < (nrows); row += (int64_t)gridDim.x * (blockDim.x >> 5))
+#define EI_FOR_X(nx, x) for (int x = (int)(threadIdx.x & 31); x < (nx); x += 32)
+// f(i, j) for every logical point i (contiguous, x fastest) and its padded
+// index j: a flat walk when there is no padding (pitch == nx, e.g. CSR
+// vectors), the row walk otherwise.
+template <class Fn>
+__device__ __forceinline__ void for_points(int64_t n, int nx, int pitch, Fn f) {
+  if (pitch == nx) {
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;
+         i += (int64_t)gridDim.x * blockDim.x)
+      f(i, i);
+  } else {
+    EI_FOR_ROWS(n / nx, row) {
+      EI_FOR_X(nx, x) f(row * nx + x, row * pitch + x);
+    }
+  }
+}
+
 // ---------------------------------------------------------------------------
 // one row of the stencil operator in FP64 (shared by the Gershgorin bounds and
 // the coefficient arrays): for each axis e and side s,
@@ -164,10 +205,9 @@ k_stencil_residual(StencilDev g, const void* __restrict__ y_, const void* __rest
   T ar = zero<T>();
   for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;
        i += (int64_t)gridDim.x * blockDim.x) {
-    const int x = (int)(i % g.nx);
-    const int64_t t = i / g.nx;
-    const int y = (int)(t % g.ny);
-    const int z = (int)(t / g.ny);
+    int x, y, z;
+    int64_t t;
+    grid_coords(g, n, i, x, y, z, t);
     const int64_t idx = t * g.pitch + x;
     T yc;
     const T Ay = apply_coef7<T>(g, yv, dg, x, y, z, idx, yc);
@@ -183,9 +223,10 @@ k_stencil_residual(StencilDev g, const void* __restrict__ y_, const void* __rest
 
 // F = A u + b_D + g(u); diag_out = diag_base + g'(u) (Rosenbrock).  b_D, the
 // inhomogeneous Dirichlet data, is read only at the rows next to a face that
-// has it (BndFaces).
-template <int FMT>
-__global__ void __launch_bounds__(EI_TPB)
+// has it (BndFaces).  COMB: the combustion forms are compiled in (a separate
+// instantiation, so the common path keeps its few registers).
+template <int FMT, bool COMB>
+__global__ void __launch_bounds__(EI_TPB, COMB ? 1 : 6)
 k_stencil_F(StencilDev g, const void* __restrict__ u_, void* __restrict__ F_,
             const void* __restrict__ db_, void* __restrict__ dout_, int nonlin, int rosenbrock,
             BndFaces bnd, double* partials, DevCtl* ctl) {
@@ -199,10 +240,9 @@ k_stencil_F(StencilDev g, const void* __restrict__ u_, void* __restrict__ F_,
   T af = zero<T>();
   for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;
        i += (int64_t)gridDim.x * blockDim.x) {
-    const int x = (int)(i % g.nx);
-    const int64_t t = i / g.nx;
-    const int y = (int)(t % g.ny);
-    const int z = (int)(t / g.ny);
+    int x, y, z;
+    int64_t t;
+    grid_coords(g, n, i, x, y, z, t);
     const int64_t idx = t * g.pitch + x;
     T uc;
     T Fv = apply_coef7<T>(g, u, db, x, y, z, idx, uc);
@@ -217,13 +257,13 @@ k_stencil_F(StencilDev g, const void* __restrict__ u_, void* __restrict__ F_,
       if (bd != 0.0) Fv = add(Fv, from_d<T>(bd));
     }
     T gq = zero<T>();
-    if (nonlin == EI_NONLIN_LOGISTIC) {
-      Fv = mac(Fv, uc, sub(one, uc));  // g(u) = u(1-u)
-      gq = mac(one, mtwo, uc);         // g'(u) = 1 - 2u
-    } else if (nonlin != EI_NONLIN_NONE) {
+    if constexpr (COMB) {
       T gv;
       combustion_term(nonlin, uc, gv, gq);
       Fv = add(Fv, gv);
+    } else if (nonlin == EI_NONLIN_LOGISTIC) {
+      Fv = mac(Fv, uc, sub(one, uc));  // g(u) = u(1-u)
+      gq = mac(one, mtwo, uc);         // g'(u) = 1 - 2u
     }
     st(F, idx, Fv);
     if (rosenbrock) st(dout, idx, nonlin ? add(ldg(db, idx), gq) : ldg(db, idx));
@@ -447,7 +487,7 @@ k_csr_residual(CsrDev op, const void* __restrict__ y_, const void* __restrict__ 
   }
 }
 
-template <int FMT>
+template <int FMT, bool COMB>
 __global__ void __launch_bounds__(EI_TPB)
 k_csr_F(CsrDev op, const void* __restrict__ u_, void* __restrict__ F_, void* __restrict__ qo_,
         const void* __restrict__ cb_, int nonlin, int rosenbrock, double* partials,
@@ -464,13 +504,13 @@ k_csr_F(CsrDev op, const void* __restrict__ u_, void* __restrict__ F_, void* __r
     const T uc = ldg(u, row);
     T Fv = mac(csr_row<T>(op, u, row), ldg(cb, row), uc);
     T gq = zero<T>();
-    if (nonlin == EI_NONLIN_LOGISTIC) {
-      Fv = mac(Fv, uc, sub(one, uc));
-      gq = mac(one, from_d<T>(-2.0), uc);
-    } else if (nonlin != EI_NONLIN_NONE) {
+    if constexpr (COMB) {
       T gv;
       combustion_term(nonlin, uc, gv, gq);
       Fv = add(Fv, gv);
+    } else if (nonlin == EI_NONLIN_LOGISTIC) {
+      Fv = mac(Fv, uc, sub(one, uc));
+      gq = mac(one, from_d<T>(-2.0), uc);
     }
     st(F, row, Fv);
     if (rosenbrock) st(qo, row, nonlin ? add(ldg(cb, row), gq) : ldg(cb, row));
@@ -572,11 +612,21 @@ k_import(void* dst_, const U* __restrict__ src, int64_t n, int nx, int pitch, do
   using T = typename VT<FMT>::T;
   T* dst = static_cast<T*>(dst_);
   double a = 0.0, b = 0.0;
-  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;
-       i += (int64_t)gridDim.x * blockDim.x) {
-    const double v = (double)src[i];
-    st(dst, pidx(i, nx, pitch), from_d<T>(v));
-    a = fma(v, v, a);
+  if constexpr (FMT == VF_DF) {
+    // the split and the squared norm on the FP32 pipes (the FP64 pipe is slow)
+    dfacc acc{0.0f, 0.0f};
+    for_points(n, nx, pitch, [&](int64_t i, int64_t j) {
+      const df v = df_split_double((double)src[i]);
+      st(dst, j, v);
+      acc = dfa_mac(acc, v, v);
+    });
+    a = acc_d(acc);
+  } else {
+    for_points(n, nx, pitch, [&](int64_t i, int64_t j) {
+      const double v = (double)src[i];
+      st(dst, j, from_d<T>(v));
+      a = fma(v, v, a);
+    });
   }
   if (last_block_reduce2<RED_SUM>(a, b, partials, ctl)) {
     if (threadIdx.x == 0) {
@@ -589,19 +639,16 @@ k_import(void* dst_, const U* __restrict__ src, int64_t n, int nx, int pitch, do
 template <class S, class U>
 __global__ void k_export(U* dst, const S* __restrict__ src, int64_t n, int nx, int pitch,
                          double scale) {
-  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;
-       i += (int64_t)gridDim.x * blockDim.x) {
-    dst[i] = (U)(to_d(ldg(src, pidx(i, nx, pitch))) * scale);
-  }
+  for_points(n, nx, pitch,
+             [&](int64_t i, int64_t j) { dst[i] = (U)(to_d(ldg(src, j)) * scale); });
 }
 
 template <class S, class U>
 __global__ void k_add_export(U* u, const S* __restrict__ y, int64_t n, int nx, int pitch,
                              double scale) {
-  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;
-       i += (int64_t)gridDim.x * blockDim.x) {
-    u[i] = (U)fma(to_d(ldg(y, pidx(i, nx, pitch))), scale, (double)u[i]);
-  }
+  for_points(n, nx, pitch, [&](int64_t i, int64_t j) {
+    u[i] = (U)fma(to_d(ldg(y, j)), scale, (double)u[i]);
+  });
 }
 
 template <int FMT>
@@ -743,7 +790,11 @@ cudaError_t launch_stencil_F(const StencilDev& g, const void* u, void* F, const 
                              void* diag_out, int nonlin, int rosenbrock, const BndFaces& bnd,
                              int fmt, double* partials, DevCtl* ctl, cudaStream_t stm) {
   const int nb = ew_blocks((int64_t)g.nx * g.ny * g.nz);
-  EI_DISPATCH_FMT(fmt, (k_stencil_F<F_><<<nb, EI_TPB, 0, stm>>>(g, u, F, diag_base, diag_out, nonlin, rosenbrock, bnd, partials, ctl)));
+  if (nonlin >= EI_NONLIN_COMBUSTION) {
+    EI_DISPATCH_FMT(fmt, (k_stencil_F<F_, true><<<nb, EI_TPB, 0, stm>>>(g, u, F, diag_base, diag_out, nonlin, rosenbrock, bnd, partials, ctl)));
+  } else {
+    EI_DISPATCH_FMT(fmt, (k_stencil_F<F_, false><<<nb, EI_TPB, 0, stm>>>(g, u, F, diag_base, diag_out, nonlin, rosenbrock, bnd, partials, ctl)));
+  }
   return cudaGetLastError();
 }
 
@@ -818,7 +869,11 @@ cudaError_t launch_csr_F(const CsrDev& op, const void* u, void* F, void* qc_out,
                          const void* c_base, int nonlin, int rosenbrock, int fmt,
                          double* partials, DevCtl* ctl, cudaStream_t stm) {
   const int nb = csr_blocks(op.n);
-  EI_DISPATCH_FMT(fmt, (k_csr_F<F_><<<nb, EI_TPB, 0, stm>>>(op, u, F, qc_out, c_base, nonlin, rosenbrock, partials, ctl)));
+  if (nonlin >= EI_NONLIN_COMBUSTION) {
+    EI_DISPATCH_FMT(fmt, (k_csr_F<F_, true><<<nb, EI_TPB, 0, stm>>>(op, u, F, qc_out, c_base, nonlin, rosenbrock, partials, ctl)));
+  } else {
+    EI_DISPATCH_FMT(fmt, (k_csr_F<F_, false><<<nb, EI_TPB, 0, stm>>>(op, u, F, qc_out, c_base, nonlin, rosenbrock, partials, ctl)));
+  }
   return cudaGetLastError();
 }
 
