@@ -13,13 +13,15 @@ writes out the Newton form of that interpolant:
     stop when |d_{j+1}| * ||w_{j+1}||_2 <= tol * ||p_{j+1}||_2,
 
 and, where s > 1 substeps are needed, integrates y' = A y + v from y = 0
-(y(h) = h phi_1(hA) v exactly):  y_{i+1} = y_i + tau * phi_1(tau A)(A y_i + v).
+(y(h) = h phi_1(hA) v exactly):  y_{i+1} = y_i + tau * phi_1(tau A)(A y_i + v);
+for k >= 2 the same with the forcing t^{k-1}/(k-1)! v (h_phik_substeps).
 Readings where the paper is silent: the tolerance applies per substep and is
 relative to ||p||; a substep that reaches m_max without meeting it doubles s
 and restarts; ||v|| = 0 returns 0; gamma = 0 (A = cI) returns phi_k(hc) v.
 """
 from __future__ import annotations
 
+import math
 from dataclasses import dataclass, field
 
 import numpy as np
@@ -182,9 +184,68 @@ def h_phi1_at(op, h, v, tol, s, m_max=L.M_MAX, xi=None):
     return y, degrees, True
 
 
-def phi_apply(op, k, h, v, tol, m_max=L.M_MAX, xi=None):
+def h_phik_substeps(op, k, h, v, tol, stats, m_max=L.M_MAX, xi=None, fixed_s=None):
+    """y_s ~= h^k phi_k(hA) v, k >= 1, by s substeps of y' = A y + t^{k-1}/(k-1)! v
+    from y = 0 (y(t) = t^k phi_k(tA) v).  A substep of length tau from t_i is
+    exactly  y_{i+1} = sum_{j=0..k} tau^j phi_j(tau A) b_j  with b_0 = y_i and
+    b_j = t_i^{k-j}/(k-j)! v (variation of constants on the polynomial
+    forcing); the recurrence phi_j(Z) = Z phi_{j+1}(Z) + I/j! turns it into
+        c_0 = y_i,  c_l = A c_{l-1} + b_l  (l = 1..k),
+        y_{i+1} = sum_{l=0..k-1} tau^l/l! c_l + tau^k phi_k(tau A) c_k,
+    k products with A and one Newton run per substep (the first substep, y_0 = 0,
+    reduces to tau^k phi_k(tau A) v).  k = 1 is h_phi1_substeps.  Reading: the
+    a-priori rule of phi_k at h picks s; a substep reaching m_max doubles s."""
+    alpha, beta, c, gamma = _interval(op)
+    stats.alpha, stats.beta = alpha, beta
+    v = np.asarray(v, dtype=np.float64).reshape(op.shape)
+    if xi is None:
+        xi = L.leja_points(m_max)
+    if fixed_s:
+        s = int(fixed_s)
+    else:
+        s, stats.m_sched, _ = L.plain_schedule(k, h, c, gamma, tol, xi, m_max)
+    while s <= L.S_MAX:
+        tau = h / s
+        d = L.divided_differences(k, tau, c, gamma, xi[: m_max + 1])
+        y = np.zeros_like(v)
+        degrees = []
+        ok = True
+        p_first = None
+        for i in range(s):
+            if i == 0:
+                ck = v
+            else:
+                ti = i * tau
+                cl = [y]
+                for l in range(1, k + 1):
+                    b = (ti ** (k - l) / math.factorial(k - l)) * v
+                    cl.append(op.matvec(cl[-1]) + b)
+                    stats.matvecs += 1
+                ck = cl[k]
+            p, deg, conv = newton_phi(op, ck, d, xi, c, gamma, tol, m_max, stats)
+            degrees.append(deg)
+            if not conv:
+                ok = False
+                break
+            if i == 0:
+                p_first = p
+                y = tau ** k * p
+            else:
+                y = sum(tau ** l / math.factorial(l) * cl[l] for l in range(k)) + tau ** k * p
+        if ok:
+            stats.s, stats.degrees = s, degrees
+            return y, p_first
+        if fixed_s:
+            raise NotConverged("phi_k: the fixed s did not converge")
+        stats.restarts += 1
+        s *= 2
+    raise NotConverged("phi_k: no s <= S_MAX converged")
+
+
+def phi_apply(op, k, h, v, tol, m_max=L.M_MAX, xi=None, fixed_s=None):
     """phi_k(hA) v.  k = 1: substepped ODE form; k = 0: (e^{tau A})^s v;
-    k >= 2: a single step (s = 1) or NotConverged.  Returns (result, Stats)."""
+    k >= 2: h_phik_substeps (with s = 1 the Newton sum itself).  fixed_s
+    (k >= 2): run that s, no schedule.  Returns (result, Stats)."""
     stats = Stats()
     v = np.asarray(v, dtype=np.float64).reshape(op.shape)
     if k == 1:
@@ -200,10 +261,11 @@ def phi_apply(op, k, h, v, tol, m_max=L.M_MAX, xi=None):
         return L.phi_scalar(k, h * c) * v, stats
     if xi is None:
         xi = L.leja_points(m_max)
+    if k >= 2:
+        y, p1 = h_phik_substeps(op, k, h, v, tol, stats, m_max, xi, fixed_s)
+        return (p1 if stats.s == 1 else y / h ** k), stats
     s, stats.m_sched, _ = L.plain_schedule(k, h, c, gamma, tol, xi, m_max)
     while s <= L.S_MAX:
-        if k >= 2 and s > 1:
-            raise NotConverged("phi_k, k >= 2, needs more than one substep")
         tau = h / s
         d = L.divided_differences(k, tau, c, gamma, xi[: m_max + 1])
         y = v.copy()

@@ -273,3 +273,50 @@ def test_exp_rosenbrock_second_order(xi):
         errs.append(np.abs(u.ravel() - ref).max())
     assert 3.3 < errs[0] / errs[1] < 4.7
     assert 3.3 < errs[1] / errs[2] < 4.7
+
+
+@pytest.mark.parametrize("k", [2, 3, 4])
+@pytest.mark.parametrize("s", [2, 4, 8])
+def test_phik_substeps_vs_dense(xi, k, s):
+    """phi_k, k >= 2, by s substeps of the polynomial-forcing ODE (the phi
+    recurrence turning each substep into k products and one phi_k run)
+    against the augmented-matrix definition."""
+    rng = np.random.default_rng(40 + 10 * k + s)
+    n = (11, 9)
+    op = O.StencilOperator(n, (1 / 12, 1 / 10), 0.2, (0.4, -0.3), bc=(0, 1, 0, 0))
+    v = rng.standard_normal((9, 11))
+    h = 0.05
+    y, st = Nw.phi_apply(op, k, h, v, 1e-12, xi=xi, fixed_s=s)
+    assert st.s == s and len(st.degrees) == s
+    ex = Dn.phi_dense(op.dense(), k, h, v)
+    assert np.linalg.norm(y.ravel() - ex) / np.linalg.norm(ex) <= 1e-9
+
+
+@pytest.mark.parametrize("k", [2, 3])
+def test_phik_schedule_picks_substeps(xi, k):
+    """h rho large enough that the a-priori rule needs s > 1 for phi_k."""
+    rng = np.random.default_rng(77 + k)
+    n = (10, 10)
+    op = O.StencilOperator(n, (0.1, 0.1), 1.0, (0.5, -0.5), bc=(0, 1, 0, 1))
+    v = rng.standard_normal((10, 10))
+    y, st = Nw.phi_apply(op, k, 5.0, v, 1e-10, xi=xi)
+    assert st.s > 1
+    ex = Dn.phi_dense(op.dense(), k, 5.0, v)
+    assert np.linalg.norm(y.ravel() - ex) / np.linalg.norm(ex) <= 1e-7
+
+
+def test_phik_substeps_diagonal_closed_form(xi):
+    """A diagonal: phi_k(h lam) = (e^z - sum_{j<k} z^j/j!)/z^k, z = h lam,
+    pointwise, through 4 substeps."""
+    n = 30
+    lam = -np.linspace(1.0, 300.0, n)
+    op = O.CsrOperator(n, np.zeros(n + 1, dtype=np.int64), np.zeros(0, np.int64),
+                       np.zeros(0), lam)
+    v = np.random.default_rng(3).standard_normal(n)
+    h = 0.02
+    for k in (2, 3):
+        y, st = Nw.phi_apply(op, k, h, v, 1e-13, xi=xi, fixed_s=4)
+        z = h * lam
+        ex = np.array([(math.exp(t) - sum(t ** j / math.factorial(j) for j in range(k))) / t ** k
+                       for t in z]) * v
+        assert np.linalg.norm(y - ex) / np.linalg.norm(ex) <= 1e-9
