@@ -64,7 +64,7 @@ def parse():
                              "adr3d_learned", "adr3d_fp32_learned", "rgg_csr_learned",
                              "batch_learned_fp32", "batch_plain_fp64_loop", "combustion",
                              "combustion_fast", "combustion_nonlin", "heat_dirichlet_data",
-                             "heat_dirichlet_hom"],
+                             "heat_dirichlet_hom", "phi2_adr3d"],
                     help="adr3d (default, the headline): 256^3 FP64 Rosenbrock-Euler; "
                          "adr3d_fp32: 512^3 FP32 exponential Euler; rgg_csr: 2^20-node CSR phi_1")
     ap.add_argument("--no-cpu", action="store_true", help="skip the CPU baseline sample")
@@ -491,13 +491,39 @@ class RggCsr(Workload):
         return ctx.phi_apply(1, self.h, self.state, self.out, self.tol, opts)
 
     def step_host(self, ctx, host, opts=None):
+        # phi_1(hA)v of the same v every call: the result goes to its own buffer
         d = host.to(self.state.device, non_blocking=True)
         st = ctx.phi_apply(1, self.h, d, self.out, self.tol, opts)
-        host.copy_(self.out, non_blocking=False)
+        pinned_like(self, host).copy_(self.out, non_blocking=False)
         return st
 
     def kernel(self, fused):
-        return "k_csr_newton<float-float> (one thread per row)"
+        return "k_csr_newton<float-float> (rows pipelined across a grid-stride walk)"
+
+
+class PhiKAdr3d(Adr3d):
+    """phi_2(hA)v on the 256^3 advection-diffusion operator of the headline
+    workload, h = 5e-4 (h rho ~ 600: the a-priori rule takes several substeps,
+    each an e^{tau A} run on the state and a psi run on v), tol 1e-10, FP64."""
+
+    k = 2
+
+    def __init__(self, torch, ei, W, dev, ctx, n):
+        Adr3d.__init__(self, torch, ei, W, dev, ctx, n)
+        self.name, self.method = f"adr3d_{n}_phi{self.k}_substeps", f"phi_{self.k}(hA)v"
+        self.h = 5e-4
+        self.out = torch.empty_like(self.state)
+        self.config = {"grid": [n] * 3, "h": self.h, "tol": self.w.tol, "k": self.k,
+                       "bc": "neumann", "method": self.method}
+
+    def step(self, ctx, opts=None):
+        return ctx.phi_apply(self.k, self.h, self.state, self.out, self.w.tol, opts)
+
+    def step_host(self, ctx, host, opts=None):
+        d = host.to(self.state.device, non_blocking=True)
+        st = ctx.phi_apply(self.k, self.h, d, self.out, self.w.tol, opts)
+        pinned_like(self, host).copy_(self.out, non_blocking=False)
+        return st
 
 
 TILE_ROWS = 0
@@ -735,13 +761,13 @@ WORKLOADS = {"adr3d": Adr3d, "adr3d_fp32": Adr3dFp32, "rgg_csr": RggCsr, "batch"
              "batch_learned_fp32": Batch2dLearnedFp32, "batch_plain_fp64_loop": Batch2dPlainLoop,
              "combustion": Combustion3d, "combustion_fast": Combustion3dFast,
              "combustion_nonlin": NonlinEval, "heat_dirichlet_data": HeatDirichlet,
-             "heat_dirichlet_hom": HeatDirichletHom}
+             "heat_dirichlet_hom": HeatDirichletHom, "phi2_adr3d": PhiKAdr3d}
 DEFAULT_N = {"adr3d": N_SIDE, "adr3d_fp32": 512, "rgg_csr": 1 << 20, "batch": 1024,
              "batch_fp32": 1024, "adr3d_learned": N_SIDE, "adr3d_fp32_learned": 512,
              "rgg_csr_learned": 1 << 20, "batch_learned_fp32": 1024,
              "batch_plain_fp64_loop": 1024, "combustion": N_SIDE, "combustion_fast": N_SIDE,
              "combustion_nonlin": N_SIDE, "heat_dirichlet_data": N_SIDE,
-             "heat_dirichlet_hom": N_SIDE}
+             "heat_dirichlet_hom": N_SIDE, "phi2_adr3d": N_SIDE}
 
 
 def replica_group(world, backend):

@@ -47,7 +47,7 @@ typedef enum {
   EI_OK = 0,
   EI_ERR_INVALID_ARG = 1,   /* bad size, null pointer, k < 0, h <= 0, tol <= 0 ... */
   EI_ERR_NONFINITE = 2,     /* NaN/Inf met in the input vector or the iteration */
-  EI_ERR_NOT_CONVERGED = 3, /* no substep count s <= 2^20 met tol (k >= 2: s > 1) */
+  EI_ERR_NOT_CONVERGED = 3, /* no substep count s <= 2^20 met tol */
   EI_ERR_TIMEOUT = 4,       /* a bounded device wait ran out */
   EI_ERR_CUDA = 5,          /* a CUDA runtime call failed */
   EI_ERR_NOMEM = 6,         /* workspace allocation failed */
@@ -204,8 +204,10 @@ ei_status ei_estimate_spectrum_stencil_noalloc(int device, void* cuda_stream, in
 
 /* out = phi_k(hA) v  (Eq. (2) for k = 1; phi_0 = exp).  v, out: device
  * vectors of the operator's size and precision; they may alias.
- * k = 1: substepped ODE form; k = 0: (e^{(h/s)A})^s v; k >= 2: one substep
- * only (EI_ERR_NOT_CONVERGED if the a-priori rule asks for more).
+ * k = 1: substepped ODE form; k = 0: (e^{(h/s)A})^s v; k >= 2 (k <= 8): s
+ * substeps of y' = A y + t^{k-1}/(k-1)! v from 0, each
+ * y_{i+1} = e^{tau A} y_i + psi_i(tau A) v with psi_i a positive combination
+ * of tau^j phi_j (two Newton runs; stats.degrees sums them per substep).
  * tol: relative stop tolerance of the a-posteriori estimate
  *   |d_{j+1}| ||w_{j+1}||_2 <= tol ||p_{j+1}||_2, per substep.
  * opt may be NULL (defaults).  stats may be NULL. */

@@ -14,7 +14,8 @@ writes out the Newton form of that interpolant:
 
 and, where s > 1 substeps are needed, integrates y' = A y + v from y = 0
 (y(h) = h phi_1(hA) v exactly):  y_{i+1} = y_i + tau * phi_1(tau A)(A y_i + v);
-for k >= 2 the same with the forcing t^{k-1}/(k-1)! v (h_phik_substeps).
+for k >= 2 the forcing t^{k-1}/(k-1)! v, two Newton runs per substep
+(h_phik_substeps).
 Readings where the paper is silent: the tolerance applies per substep and is
 relative to ||p||; a substep that reaches m_max without meeting it doubles s
 and restarts; ||v|| = 0 returns 0; gamma = 0 (A = cI) returns phi_k(hc) v.
@@ -185,16 +186,19 @@ def h_phi1_at(op, h, v, tol, s, m_max=L.M_MAX, xi=None):
 
 
 def h_phik_substeps(op, k, h, v, tol, stats, m_max=L.M_MAX, xi=None, fixed_s=None):
-    """y_s ~= h^k phi_k(hA) v, k >= 1, by s substeps of y' = A y + t^{k-1}/(k-1)! v
+    """y_s ~= h^k phi_k(hA) v, k >= 2, by s substeps of y' = A y + t^{k-1}/(k-1)! v
     from y = 0 (y(t) = t^k phi_k(tA) v).  A substep of length tau from t_i is
-    exactly  y_{i+1} = sum_{j=0..k} tau^j phi_j(tau A) b_j  with b_0 = y_i and
-    b_j = t_i^{k-j}/(k-j)! v (variation of constants on the polynomial
-    forcing); the recurrence phi_j(Z) = Z phi_{j+1}(Z) + I/j! turns it into
-        c_0 = y_i,  c_l = A c_{l-1} + b_l  (l = 1..k),
-        y_{i+1} = sum_{l=0..k-1} tau^l/l! c_l + tau^k phi_k(tau A) c_k,
-    k products with A and one Newton run per substep (the first substep, y_0 = 0,
-    reduces to tau^k phi_k(tau A) v).  k = 1 is h_phi1_substeps.  Reading: the
-    a-priori rule of phi_k at h picks s; a substep reaching m_max doubles s."""
+    exactly (variation of constants on the polynomial forcing)
+        y_{i+1} = e^{tau A} y_i + psi_i(tau A) v,
+        psi_i(z) = sum_{j=1..k} t_i^{k-j}/(k-j)! tau^j phi_j(z),
+    a sum of positive multiples of phi_j, so one Newton run with the divided
+    differences of psi_i (the same combination of the phi_j tables) gives the
+    second term, and one run of phi_0 = exp the first: two runs per substep, no
+    products with A outside the Newton loop (an expansion of phi_j in powers of
+    A would amplify rounding by (tau rho)^k).  The first substep is psi_0 =
+    tau^k phi_k alone.  Reading: the a-priori rule of phi_k at h picks s; a run
+    reaching m_max doubles s.  stats.degrees holds the two runs' degrees summed
+    per substep."""
     alpha, beta, c, gamma = _interval(op)
     stats.alpha, stats.beta = alpha, beta
     v = np.asarray(v, dtype=np.float64).reshape(op.shape)
@@ -206,32 +210,33 @@ def h_phik_substeps(op, k, h, v, tol, stats, m_max=L.M_MAX, xi=None, fixed_s=Non
         s, stats.m_sched, _ = L.plain_schedule(k, h, c, gamma, tol, xi, m_max)
     while s <= L.S_MAX:
         tau = h / s
-        d = L.divided_differences(k, tau, c, gamma, xi[: m_max + 1])
+        dj = [L.divided_differences(j, tau, c, gamma, xi[: m_max + 1]) for j in range(k + 1)]
         y = np.zeros_like(v)
         degrees = []
         ok = True
         p_first = None
         for i in range(s):
-            if i == 0:
-                ck = v
-            else:
-                ti = i * tau
-                cl = [y]
-                for l in range(1, k + 1):
-                    b = (ti ** (k - l) / math.factorial(k - l)) * v
-                    cl.append(op.matvec(cl[-1]) + b)
-                    stats.matvecs += 1
-                ck = cl[k]
-            p, deg, conv = newton_phi(op, ck, d, xi, c, gamma, tol, m_max, stats)
+            ti = i * tau
+            dpsi = sum((ti ** (k - j) / math.factorial(k - j)) * tau ** j * dj[j]
+                       for j in range(1, k + 1))
+            deg = 0
+            if i > 0:
+                e, d0, conv = newton_phi(op, y, dj[0], xi, c, gamma, tol, m_max, stats)
+                deg += d0
+                if not conv:
+                    ok = False
+                    break
+            q, d1, conv = newton_phi(op, v, dpsi, xi, c, gamma, tol, m_max, stats)
+            deg += d1
             degrees.append(deg)
             if not conv:
                 ok = False
                 break
             if i == 0:
-                p_first = p
-                y = tau ** k * p
+                p_first = q
+                y = q
             else:
-                y = sum(tau ** l / math.factorial(l) * cl[l] for l in range(k)) + tau ** k * p
+                y = e + q
         if ok:
             stats.s, stats.degrees = s, degrees
             return y, p_first
@@ -263,7 +268,7 @@ def phi_apply(op, k, h, v, tol, m_max=L.M_MAX, xi=None, fixed_s=None):
         xi = L.leja_points(m_max)
     if k >= 2:
         y, p1 = h_phik_substeps(op, k, h, v, tol, stats, m_max, xi, fixed_s)
-        return (p1 if stats.s == 1 else y / h ** k), stats
+        return (p1 / h ** k if stats.s == 1 else y / h ** k), stats
     s, stats.m_sched, _ = L.plain_schedule(k, h, c, gamma, tol, xi, m_max)
     while s <= L.S_MAX:
         tau = h / s

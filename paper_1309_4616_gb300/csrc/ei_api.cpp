@@ -1038,6 +1038,89 @@ ei_status ei_phi_apply(ei_ctx* c, int k, double h, const void* v, void* out, dou
   return rc;
 }
 
+// phi_k(hA) v for k >= 2 by s substeps of y' = A y + t^{k-1}/(k-1)! v from 0
+// (y(t) = t^k phi_k(tA) v).  A substep of length tau from t_i is
+//   y_{i+1} = e^{tau A} y_i + psi_i(tau A) v,
+//   psi_i(z) = sum_{j=1..k} t_i^{k-j}/(k-j)! tau^j phi_j(z)
+// (variation of constants on the polynomial forcing): a Newton run of
+// phi_0 = exp on y_i and one with the divided differences of psi_i (the same
+// combination of the phi_j tables) on v.  psi_i is a positive combination,
+// so nothing cancels.  The first substep is psi_0 = tau^k phi_k alone.  y_i
+// is copied to P.r, a Newton input with a tensor map.  st->degrees holds the
+// two runs' degrees summed per substep.
+static ei_status phik_substeps(ei_ctx* c, Prepared& P, int k, double h, double cc,
+                               double gamma, double tol, const ei_options* opt, ei_stats* st,
+                               void* out) {
+  const int fmt = P.fmt;
+  const int64_t n = c->n;
+  const int m_max = (opt && opt->m_max > 0 && opt->m_max <= 100) ? opt->m_max : 100;
+  int s = 1, m_pred = 0;
+  const bool fixed = opt && opt->fixed_s > 0;
+  if (fixed) s = opt->fixed_s;
+  else if (schedule(k, h, cc, gamma, tol, m_max, &s, &m_pred, nullptr) != 0)
+    return EI_ERR_NOT_CONVERGED;
+  if (st) st->m_sched = m_pred;
+  const void* qc = base_diag(P);
+  const size_t vbytes = vec_elem_bytes(fmt) * (size_t)P.n_alloc;
+  std::vector<std::vector<double>> dj(k + 1, std::vector<double>(m_max + 1));
+  std::vector<double> dpsi(m_max + 1);
+  int restarts = 0;
+  while (s <= (1 << 20)) {
+    const double tau = h / s;
+    for (int j = 0; j <= k; ++j) divided_differences(j, tau, cc, gamma, m_max, dj[j].data());
+    bool ok_all = true;
+    int dsum = 0, dmax = 0;
+    for (int i = 0; i < s; ++i) {
+      const double ti = i * tau;
+      for (int q = 0; q <= m_max; ++q) dpsi[q] = 0.0;
+      double fact = 1.0;  // (k-j)!, from j = k down
+      for (int j = k; j >= 1; --j) {
+        if (j < k) fact *= (k - j);
+        const double bj = pow(ti, k - j) / fact * pow(tau, j);
+        for (int q = 0; q <= m_max; ++q) dpsi[q] += bj * dj[j][q];
+      }
+      int deg = 0, d1 = 0, ok = 0;
+      if (i > 0) {  // e^{tau A} y_i
+        EI_TRY_CUDA(cudaMemcpyAsync(P.r, P.y, vbytes, cudaMemcpyDeviceToDevice, c->stream));
+        EI_TRY(newton_loop(c, P, qc, P.r, dj[0], cc, gamma, tol, m_max, 0, &d1, &ok));
+        deg += d1;
+        if (!ok) { ok_all = false; break; }
+        EI_LAUNCH(launch_p_to_vec(P.y, P.p, fmt, P.n_alloc, c->stream));
+      }
+      EI_TRY(newton_loop(c, P, qc, P.v, dpsi, cc, gamma, tol, m_max, m_pred, &d1, &ok));
+      deg += d1;
+      if (!ok) { ok_all = false; break; }
+      if (i == 0) {
+        if (s > 1) EI_LAUNCH(launch_p_to_vec(P.y, P.p, fmt, P.n_alloc, c->stream));
+      } else {
+        EI_LAUNCH(launch_axpy(P.y, P.p, fmt, P.n_alloc, 1.0, c->stream));
+      }
+      if (st) st->matvecs += deg;
+      if (st && i < EI_STATS_MAX_SUBSTEPS) st->degrees[i] = deg;
+      dsum += deg;
+      if (deg > dmax) dmax = deg;
+    }
+    if (ok_all) {
+      if (st) {
+        st->s = s; st->restarts = restarts; st->degree_sum = dsum; st->degree_max = dmax;
+      }
+      const int geo_ny = c->kind == KIND_STENCIL ? c->sd.ny : 1;
+      if (s == 1)
+        EI_LAUNCH(launch_export(out, c->prec, P.p, fmt, 1, n, geo_nx(c), geo_ny, geo_pitch(c),
+                                1.0 / pow(h, k), c->stream));
+      else
+        EI_LAUNCH(launch_export(out, c->prec, P.y, fmt, 0, n, geo_nx(c), geo_ny, geo_pitch(c),
+                                1.0 / pow(h, k), c->stream));
+      EI_TRY_CUDA(cudaStreamSynchronize(c->stream));
+      return EI_OK;
+    }
+    if (fixed) return EI_ERR_NOT_CONVERGED;
+    ++restarts;
+    s *= 2;
+  }
+  return EI_ERR_NOT_CONVERGED;
+}
+
 static ei_status phi_apply_impl(ei_ctx* c, int k, double h, const void* v, void* out, double tol,
                                 const ei_options* opt, ei_stats* st) {
   if (c->kind == KIND_NONE) return EI_ERR_STATE;
@@ -1079,6 +1162,8 @@ static ei_status phi_apply_impl(ei_ctx* c, int k, double h, const void* v, void*
       EI_LAUNCH(launch_export(out, c->prec, res, fmt, is_p, n, geo_nx(c), c->kind == KIND_STENCIL ? c->sd.ny : 1, geo_pitch(c), scale / h, c->stream));
       EI_TRY_CUDA(cudaStreamSynchronize(c->stream));
     }
+  } else if (k >= 2) {
+    rc = phik_substeps(c, P, k, h, cc, gamma, tol, opt, st, out);
   } else {
     const int m_max = (opt && opt->m_max > 0 && opt->m_max <= 100) ? opt->m_max : 100;
     int s = 1, m_pred = 0;
@@ -1089,8 +1174,7 @@ static ei_status phi_apply_impl(ei_ctx* c, int k, double h, const void* v, void*
     std::vector<double> d(m_max + 1);
     int restarts = 0;
     rc = EI_ERR_NOT_CONVERGED;
-    while (s <= (1 << 20)) {
-      if (k >= 2 && s > 1) { rc = EI_ERR_NOT_CONVERGED; break; }
+    while (s <= (1 << 20)) {  // k = 0: (e^{tau A})^s v
       const double tau = h / s;
       divided_differences(k, tau, cc, gamma, m_max, d.data());
       bool ok_all = true;
