@@ -224,9 +224,12 @@ ei_status ei_phi_apply(ei_ctx* ctx, int k, double h, const void* v, void* out, d
 ei_status ei_step(ei_ctx* ctx, int method, double h, void* u, int nonlin, double tol,
                   const ei_options* opt, ei_stats* stats);
 
-/* ei_step on a HOST vector: copies u to the device, steps, copies it back,
- * all on the context's stream (pinned host memory gives asynchronous copies).
- * Returns after the copy back completed. */
+/* ei_step on a HOST vector of the operator's size and precision, on the
+ * context's stream.  Pinned host memory with a device mapping (cudaHostAlloc,
+ * cudaHostRegister, torch pin_memory) is read by the import kernel and written
+ * by the final update directly (over NVLink-C2C on GB300), with a device copy
+ * of u_n kept for the step; other host memory is copied in and out.  Either
+ * way u_host holds u_{n+1} when the call returns, and is unchanged on error. */
 ei_status ei_step_host(ei_ctx* ctx, int method, double h, void* u_host, int nonlin, double tol,
                        const ei_options* opt, ei_stats* stats);
 

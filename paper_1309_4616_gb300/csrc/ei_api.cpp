@@ -1209,16 +1209,21 @@ static ei_status phi_apply_impl(ei_ctx* c, int k, double h, const void* v, void*
   return rc;
 }
 
+// One step on the device vector u.  src/dst (optional): the step reads u_n
+// from src, keeping a copy in u, and writes u_{n+1} to dst instead of u (a
+// mapped host buffer: no separate copies).
 static ei_status step_impl(ei_ctx* c, int method, double h, void* u, int nonlin, double tol,
-                           const ei_options* opt, ei_stats* st) {
+                           const ei_options* opt, ei_stats* st, const void* src = nullptr,
+                           void* dst = nullptr) {
   const int fmt = vec_fmt_for(c, opt);
   EI_TRY(prepare(c, fmt));
   Prepared& P = c->prep[fmt];
   const int64_t n = c->n;
   const int rosen = (method == EI_EXP_ROSENBROCK);
   // import u; F = A u + g(u); J's diagonal; the interval of J
-  EI_LAUNCH(launch_import(P.u, fmt, u, c->prec, n, geo_nx(c), c->kind == KIND_STENCIL ? c->sd.ny : 1, geo_pitch(c), c->partials, c->ctl,
-                         c->stream));
+  EI_LAUNCH(launch_import(P.u, fmt, src ? src : u, c->prec, n, geo_nx(c),
+                          c->kind == KIND_STENCIL ? c->sd.ny : 1, geo_pitch(c), c->partials,
+                          c->ctl, c->stream, src ? u : nullptr));
   if (c->kind == KIND_STENCIL) {
     BndFaces bnd;
     for (int f = 0; f < 6; ++f) bnd.c[f] = c->face_term[f];
@@ -1244,7 +1249,7 @@ static ei_status step_impl(ei_ctx* c, int method, double h, void* u, int nonlin,
   const void* qc = rosen ? P.qc : base_diag(P);
   if (gamma == 0.0) {  // J = cI: z(h) = h phi_1(hc) F
     EI_LAUNCH(launch_add_export(u, c->prec, P.v, fmt, 0, n, geo_nx(c), c->kind == KIND_STENCIL ? c->sd.ny : 1, geo_pitch(c),
-                            h * phi_scalar(1, h * cc), c->stream));
+                            h * phi_scalar(1, h * cc), c->stream, dst));
     EI_TRY_CUDA(cudaStreamSynchronize(c->stream));
     return EI_OK;
   }
@@ -1253,7 +1258,7 @@ static ei_status step_impl(ei_ctx* c, int method, double h, void* u, int nonlin,
   double scale = 1.0;
   c->vnorm2 = fnorm2;
   EI_TRY(phi1_substeps(c, P, qc, h, alpha, beta, tol, opt, st, &res, &is_p, &scale));
-  EI_LAUNCH(launch_add_export(u, c->prec, res, fmt, is_p, n, geo_nx(c), c->kind == KIND_STENCIL ? c->sd.ny : 1, geo_pitch(c), scale, c->stream));
+  EI_LAUNCH(launch_add_export(u, c->prec, res, fmt, is_p, n, geo_nx(c), c->kind == KIND_STENCIL ? c->sd.ny : 1, geo_pitch(c), scale, c->stream, dst));
   EI_TRY_CUDA(cudaStreamSynchronize(c->stream));
   return EI_OK;
 }
@@ -1285,6 +1290,25 @@ ei_status ei_step_host(ei_ctx* c, int method, double h, void* u_host, int nonlin
   if (!c->host_stage) {
     ei_status s = alloc(&c->host_stage, bytes);
     if (s != EI_OK) return s;
+  }
+  // pinned host memory with a device mapping (GB300's host memory is
+  // reachable over NVLink-C2C): the import kernel reads it and the final
+  // update writes it directly; other host memory goes through copies
+  cudaPointerAttributes attr{};
+  const bool mapped = cudaPointerGetAttributes(&attr, u_host) == cudaSuccess &&
+                      attr.type == cudaMemoryTypeHost && attr.devicePointer != nullptr;
+  if (!mapped) cudaGetLastError();
+  if (mapped) {
+    if ((method != EI_EXP_EULER && method != EI_EXP_ROSENBROCK) ||
+        nonlin < EI_NONLIN_NONE || nonlin > EI_NONLIN_COMBUSTION_FAST || !(h > 0) ||
+        !isfinite(h) || !(tol > 0) || !isfinite(tol))
+      return EI_ERR_INVALID_ARG;
+    acct_begin(c, opt);
+    ei_status rc = step_impl(c, method, h, c->host_stage, nonlin, tol, opt, st,
+                             attr.devicePointer, attr.devicePointer);
+    acct_end(c, st);
+    log_stats("step_host", st, rc);
+    return rc;
   }
   EI_TRY_CUDA(cudaMemcpyAsync(c->host_stage, u_host, bytes, cudaMemcpyHostToDevice, c->stream));
   ei_status rc = ei_step(c, method, h, c->host_stage, nonlin, tol, opt, st);

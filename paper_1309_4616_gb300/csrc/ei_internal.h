@@ -129,14 +129,18 @@ cudaError_t launch_fill_coef(void* dst, int fmt, int64_t n, int nx, int ny, int 
                              cudaStream_t st);
 // dst (vector format, padded) = src (caller precision, contiguous); squared
 // norm into ctl->sum0, finiteness flag into ctl->sum1.
+// raw (optional): also copy src there, in the caller's precision
 cudaError_t launch_import(void* dst, int fmt, const void* src, int src_prec, int64_t n, int nx,
-                          int ny, int pitch, double* partials, DevCtl* ctl, cudaStream_t st);
+                          int ny, int pitch, double* partials, DevCtl* ctl, cudaStream_t st,
+                          void* raw = nullptr);
 // dst (caller precision, contiguous) = scale * src (vector or Newton-sum format)
 cudaError_t launch_export(void* dst, int dst_prec, const void* src, int fmt, int src_is_p,
                           int64_t n, int nx, int ny, int pitch, double scale, cudaStream_t st);
-// u (caller precision, contiguous) += scale * y (vector or Newton-sum format)
+// u (caller precision, contiguous) += scale * y (vector or Newton-sum format);
+// out (optional): write the sum there instead of into u
 cudaError_t launch_add_export(void* u, int prec, const void* y, int fmt, int src_is_p, int64_t n,
-                              int nx, int ny, int pitch, double scale, cudaStream_t st);
+                              int nx, int ny, int pitch, double scale, cudaStream_t st,
+                              void* out = nullptr);
 // elementwise over whole (padded) arrays of n_alloc elements
 cudaError_t launch_p_to_vec(void* dst, const void* p, int fmt, int64_t n_alloc, cudaStream_t st);
 cudaError_t launch_axpy(void* y, const void* p, int fmt, int64_t n_alloc, double tau,

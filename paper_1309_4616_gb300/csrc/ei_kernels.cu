@@ -607,8 +607,8 @@ __global__ void k_fill_coef(void* dst_, int64_t n, int nx, int pitch, const U* s
 
 template <int FMT, class U>
 __global__ void __launch_bounds__(EI_TPB)
-k_import(void* dst_, const U* __restrict__ src, int64_t n, int nx, int pitch, double* partials,
-         DevCtl* ctl) {
+k_import(void* dst_, const U* __restrict__ src, int64_t n, int nx, int pitch, U* raw,
+         double* partials, DevCtl* ctl) {
   using T = typename VT<FMT>::T;
   T* dst = static_cast<T*>(dst_);
   double a = 0.0, b = 0.0;
@@ -616,14 +616,18 @@ k_import(void* dst_, const U* __restrict__ src, int64_t n, int nx, int pitch, do
     // the split and the squared norm on the FP32 pipes (the FP64 pipe is slow)
     dfacc acc{0.0f, 0.0f};
     for_points(n, nx, pitch, [&](int64_t i, int64_t j) {
-      const df v = df_split_double((double)src[i]);
+      const U x = src[i];
+      if (raw) raw[i] = x;
+      const df v = df_split_double((double)x);
       st(dst, j, v);
       acc = dfa_mac(acc, v, v);
     });
     a = acc_d(acc);
   } else {
     for_points(n, nx, pitch, [&](int64_t i, int64_t j) {
-      const double v = (double)src[i];
+      const U x = src[i];
+      if (raw) raw[i] = x;
+      const double v = (double)x;
       st(dst, j, from_d<T>(v));
       a = fma(v, v, a);
     });
@@ -643,11 +647,12 @@ __global__ void k_export(U* dst, const S* __restrict__ src, int64_t n, int nx, i
              [&](int64_t i, int64_t j) { dst[i] = (U)(to_d(ldg(src, j)) * scale); });
 }
 
+// out = u + scale * y (out may be u, or a mapped host buffer)
 template <class S, class U>
-__global__ void k_add_export(U* u, const S* __restrict__ y, int64_t n, int nx, int pitch,
-                             double scale) {
+__global__ void k_add_export(U* out, const U* u, const S* __restrict__ y, int64_t n, int nx,
+                             int pitch, double scale) {
   for_points(n, nx, pitch, [&](int64_t i, int64_t j) {
-    u[i] = (U)fma(to_d(ldg(y, j)), scale, (double)u[i]);
+    out[i] = (U)fma(to_d(ldg(y, j)), scale, (double)u[i]);
   });
 }
 
@@ -1043,34 +1048,37 @@ cudaError_t launch_fill_coef(void* dst, int fmt, int64_t n, int nx, int ny, int 
 }
 
 cudaError_t launch_import(void* dst, int fmt, const void* src, int src_prec, int64_t n, int nx,
-                          int ny, int pitch, double* partials, DevCtl* ctl, cudaStream_t stm) {
+                          int ny, int pitch, double* partials, DevCtl* ctl, cudaStream_t stm,
+                          void* raw) {
   (void)ny;
   const int nb = ew_blocks(n);
   if (src_prec == 0) {
-    EI_DISPATCH_FMT(fmt, (k_import<F_, double><<<nb, EI_TPB, 0, stm>>>(dst, static_cast<const double*>(src), n, nx, pitch, partials, ctl)));
+    EI_DISPATCH_FMT(fmt, (k_import<F_, double><<<nb, EI_TPB, 0, stm>>>(dst, static_cast<const double*>(src), n, nx, pitch, static_cast<double*>(raw), partials, ctl)));
   } else {
-    EI_DISPATCH_FMT(fmt, (k_import<F_, float><<<nb, EI_TPB, 0, stm>>>(dst, static_cast<const float*>(src), n, nx, pitch, partials, ctl)));
+    EI_DISPATCH_FMT(fmt, (k_import<F_, float><<<nb, EI_TPB, 0, stm>>>(dst, static_cast<const float*>(src), n, nx, pitch, static_cast<float*>(raw), partials, ctl)));
   }
   return cudaGetLastError();
 }
 
 template <class U>
 static void export_dispatch(U* dst, const void* src, int fmt, int src_is_p, int64_t n, int nx,
-                            int pitch, double scale, bool add, cudaStream_t stm) {
+                            int pitch, double scale, bool add, cudaStream_t stm,
+                            U* add_out = nullptr) {
+  U* out = add_out ? add_out : dst;
   const int nb = ew_blocks(n);
   // source element type: df for the float-float format and for the Newton
   // sum of every format but the double one
   if (fmt == VF_F64) {
     const double* s = static_cast<const double*>(src);
-    if (add) k_add_export<double, U><<<nb, EI_TPB, 0, stm>>>(dst, s, n, nx, pitch, scale);
+    if (add) k_add_export<double, U><<<nb, EI_TPB, 0, stm>>>(out, dst, s, n, nx, pitch, scale);
     else k_export<double, U><<<nb, EI_TPB, 0, stm>>>(dst, s, n, nx, pitch, scale);
   } else if (fmt == VF_DF || src_is_p) {
     const df* s = static_cast<const df*>(src);
-    if (add) k_add_export<df, U><<<nb, EI_TPB, 0, stm>>>(dst, s, n, nx, pitch, scale);
+    if (add) k_add_export<df, U><<<nb, EI_TPB, 0, stm>>>(out, dst, s, n, nx, pitch, scale);
     else k_export<df, U><<<nb, EI_TPB, 0, stm>>>(dst, s, n, nx, pitch, scale);
   } else {
     const float* s = static_cast<const float*>(src);
-    if (add) k_add_export<float, U><<<nb, EI_TPB, 0, stm>>>(dst, s, n, nx, pitch, scale);
+    if (add) k_add_export<float, U><<<nb, EI_TPB, 0, stm>>>(out, dst, s, n, nx, pitch, scale);
     else k_export<float, U><<<nb, EI_TPB, 0, stm>>>(dst, s, n, nx, pitch, scale);
   }
 }
@@ -1086,12 +1094,15 @@ cudaError_t launch_export(void* dst, int dst_prec, const void* src, int fmt, int
 }
 
 cudaError_t launch_add_export(void* u, int prec, const void* y, int fmt, int src_is_p, int64_t n,
-                              int nx, int ny, int pitch, double scale, cudaStream_t stm) {
+                              int nx, int ny, int pitch, double scale, cudaStream_t stm,
+                              void* out) {
   (void)ny;
   if (prec == 0)
-    export_dispatch(static_cast<double*>(u), y, fmt, src_is_p, n, nx, pitch, scale, true, stm);
+    export_dispatch(static_cast<double*>(u), y, fmt, src_is_p, n, nx, pitch, scale, true, stm,
+                    static_cast<double*>(out));
   else
-    export_dispatch(static_cast<float*>(u), y, fmt, src_is_p, n, nx, pitch, scale, true, stm);
+    export_dispatch(static_cast<float*>(u), y, fmt, src_is_p, n, nx, pitch, scale, true, stm,
+                    static_cast<float*>(out));
   return cudaGetLastError();
 }
 

@@ -359,7 +359,8 @@ class Context:
                "ei_set_schedule_model")
 
     def step_host(self, method, h, u_host, nonlin, tol, options=None):
-        """u_host: a CPU tensor (pinned for asynchronous copies)."""
+        """u_host: a CPU tensor; pinned memory is read and written by the
+        kernels directly, other memory is copied."""
         dt = self._dtype(self.prec)
         if u_host.is_cuda or not u_host.is_contiguous() or u_host.dtype != dt or \
                 u_host.numel() != self.n:

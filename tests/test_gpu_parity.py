@@ -433,3 +433,26 @@ def test_context_reuse_across_operator_kinds(env, xi):
     assert rel_err(out.cpu().numpy(), ref) <= FP64_TOL
     _check_stats(st, ost)
     ctx.close()
+
+
+@pytest.mark.parametrize("method", ["euler", "rosenbrock"])
+def test_step_host_paths_match_device(env, method):
+    """ei_step_host on pinned (mapped: read and written by the kernels) and on
+    pageable host memory (copied) gives the device step's result bit for bit."""
+    torch, ei = env
+    rng = np.random.default_rng(61)
+    n = (41, 23, 17)
+    dx = (1 / 41, 1 / 41, 1 / 41)
+    D, b = _fields_3d(rng, n)
+    u0 = rng.uniform(0, 1, (17, 23, 41))
+    m = ei.EXP_EULER if method == "euler" else ei.EXP_ROSENBROCK
+    ctx = stencil_context(torch, ei, n, dx, D, b, 0.0, (1,) * 6)
+    ud = dev(torch, u0)
+    ctx.step(m, 3e-4, ud, ei.NONLIN_LOGISTIC, 1e-10)
+    ref = ud.cpu().numpy()
+    pinned = torch.from_numpy(u0.copy()).pin_memory()
+    ctx.step_host(m, 3e-4, pinned, ei.NONLIN_LOGISTIC, 1e-10)
+    pageable = torch.from_numpy(u0.copy())
+    ctx.step_host(m, 3e-4, pageable, ei.NONLIN_LOGISTIC, 1e-10)
+    assert np.array_equal(pinned.numpy(), ref) and np.array_equal(pageable.numpy(), ref)
+    ctx.close()
