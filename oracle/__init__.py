@@ -18,6 +18,8 @@ Modules
   learned    Features, decision rule and phi_1 under the learned schedule,
              with the plain method as fallback.
   dense      phi_k(hA)v by definition: expm of an augmented matrix.
+  skew       phi_k(-i h H)v for a real symmetric H (complex products, K = C):
+             complex divided differences at the real Leja points.
   closed     Closed forms: sine / cosine eigenbases of constant-coefficient
              operators, the analytic Gaussian.
 """
