@@ -64,7 +64,7 @@ def parse():
                              "adr3d_learned", "adr3d_fp32_learned", "rgg_csr_learned",
                              "batch_learned_fp32", "batch_plain_fp64_loop", "combustion",
                              "combustion_fast", "combustion_nonlin", "heat_dirichlet_data",
-                             "heat_dirichlet_hom", "phi2_adr3d"],
+                             "heat_dirichlet_hom", "phi2_adr3d", "spin_bath", "spin_bath_fp32"],
                     help="adr3d (default, the headline): 256^3 FP64 Rosenbrock-Euler; "
                          "adr3d_fp32: 512^3 FP32 exponential Euler; rgg_csr: 2^20-node CSR phi_1")
     ap.add_argument("--no-cpu", action="store_true", help="skip the CPU baseline sample")
@@ -526,6 +526,59 @@ class PhiKAdr3d(Adr3d):
         return st
 
 
+class SpinBath(Workload):
+    """e^{-i t H} psi for the spin-bath Hamiltonian of Sec. III-D (two central
+    spins and a bath, 21 spins: 2^21 complex states, 40 entries a row),
+    t = 10, tol 1e-5: Table 5's integration as one propagation call, FP64."""
+    prec = 0
+
+    def __init__(self, torch, ei, W, dev, ctx, n):
+        single = self.prec == 1
+        self.name = f"spin_bath_{n}_propagator" + ("_fp32" if single else "")
+        self.method = "exp(-i t H) psi"
+        self.dtype = ("f32 (Newton sum float-float)" if single
+                      else "f64 (float-float pairs on the FP32 pipes)")
+        g = W.spin_bath(n)
+        self.npts = g.n
+        dt = torch.float32 if single else torch.float64
+        self.keep = [torch.from_numpy(g.rowptr).to(dev), torch.from_numpy(g.col).to(dev),
+                     torch.from_numpy(g.val).to(dt).to(dev), torch.from_numpy(g.diag).to(dt).to(dev)]
+        ctx.set_operator_csr(g.n, *self.keep, prec=self.prec)
+        self.h, self.tol = 10.0, 1e-5
+        v = W.spin_state(g.n, 5)
+        if single:
+            v = v.astype(np.complex64)
+        self.host0 = v
+        self.state0 = torch.from_numpy(v).to(dev)
+        self.state = self.state0.clone()
+        self.out = torch.empty_like(self.state)
+        nnz = g.col.size
+        # per row: val + col per entry, rowptr 8, diagonal, w in + w out, p read + write
+        ev = 4 if single else 8
+        self.bytes_per_point = (ev + 4.0) * nnz / g.n + 8 + ev + 4 * ev + 32
+        self.config = {"spins": n, "states": g.n, "nnz_offdiag": int(nnz),
+                       "entries_per_row": nnz / g.n + 1, "t": self.h, "tol": self.tol,
+                       "method": self.method}
+
+    def step(self, ctx, opts=None):
+        return ctx.phi_apply_imag(0, self.h, self.state, self.out, self.tol, opts)
+
+    def step_host(self, ctx, host, opts=None):
+        d = host.to(self.state.device, non_blocking=True)
+        st = ctx.phi_apply_imag(0, self.h, d, self.out, self.tol, opts)
+        pinned_like(self, host).copy_(self.out, non_blocking=False)
+        return st
+
+    def kernel(self, fused):
+        fmt = "float" if self.prec == 1 else "float-float"
+        return (f"k_csr_newton_cg<{fmt}, 4 lanes a row> (complex w and p interleaved, "
+                f"real H)")
+
+
+class SpinBathFp32(SpinBath):
+    prec = 1
+
+
 TILE_ROWS = 0
 
 
@@ -761,13 +814,15 @@ WORKLOADS = {"adr3d": Adr3d, "adr3d_fp32": Adr3dFp32, "rgg_csr": RggCsr, "batch"
              "batch_learned_fp32": Batch2dLearnedFp32, "batch_plain_fp64_loop": Batch2dPlainLoop,
              "combustion": Combustion3d, "combustion_fast": Combustion3dFast,
              "combustion_nonlin": NonlinEval, "heat_dirichlet_data": HeatDirichlet,
-             "heat_dirichlet_hom": HeatDirichletHom, "phi2_adr3d": PhiKAdr3d}
+             "heat_dirichlet_hom": HeatDirichletHom, "phi2_adr3d": PhiKAdr3d,
+             "spin_bath": SpinBath, "spin_bath_fp32": SpinBathFp32}
 DEFAULT_N = {"adr3d": N_SIDE, "adr3d_fp32": 512, "rgg_csr": 1 << 20, "batch": 1024,
              "batch_fp32": 1024, "adr3d_learned": N_SIDE, "adr3d_fp32_learned": 512,
              "rgg_csr_learned": 1 << 20, "batch_learned_fp32": 1024,
              "batch_plain_fp64_loop": 1024, "combustion": N_SIDE, "combustion_fast": N_SIDE,
              "combustion_nonlin": N_SIDE, "heat_dirichlet_data": N_SIDE,
-             "heat_dirichlet_hom": N_SIDE, "phi2_adr3d": N_SIDE}
+             "heat_dirichlet_hom": N_SIDE, "phi2_adr3d": N_SIDE, "spin_bath": 21,
+             "spin_bath_fp32": 21}
 
 
 def replica_group(world, backend):

@@ -100,6 +100,10 @@ typedef struct {
   int no_restart;  /* with fixed_s: an attempt that reaches m_max returns
                       EI_ERR_NOT_CONVERGED instead of doubling s (stats keep the
                       degrees reached; u and out are left unmodified) */
+  int csr_lanes;   /* ei_phi_apply_imag on CSR: lanes of a warp per row in the
+                      Newton kernel, 1, 2, 4, 8, 16 or 32; 0 (or any other
+                      value) chooses by the mean row length: 1 below 16
+                      entries, 4 below 96, else 8 */
 } ei_options;
 
 #define EI_STATS_MAX_SUBSTEPS 64
@@ -214,6 +218,32 @@ ei_status ei_estimate_spectrum_stencil_noalloc(int device, void* cuda_stream, in
 ei_status ei_phi_apply(ei_ctx* ctx, int k, double h, const void* v, void* out, double tol,
                        const ei_options* opt, ei_stats* stats);
 
+/* out = phi_k(-i h H) v for the context's CSR operator H, read as a real
+ * symmetric (Hermitian) matrix: the products (alpha A + beta I) x of Eq. (3)
+ * with K = C (Sec. II-C), for psi' = -i H psi (the spin system of
+ * Sec. III-D).  The interpolation runs on H's Gershgorin interval
+ * [alpha, beta] with the real Leja points; the divided differences of
+ * f(xi) = phi_k(-i tau (c + gamma xi)) are complex (ei_divided_differences_imag)
+ * and the Newton basis is H's real recurrence applied to complex vectors.
+ *   v, out: device arrays of n complex numbers, interleaved (re, im): double
+ *     pairs for EI_PREC_F64 (16-byte aligned), float pairs for EI_PREC_F32
+ *     (8-byte aligned); they may alias.  Read and written on the context's
+ *     stream; the call synchronises it.
+ *   k = 0: (e^{-i (h/s) H})^s v, s from ei_schedule_imag (or opt->fixed_s);
+ *     k >= 1 (k <= 8): one substep, s = 1.
+ *   tol: per-substep stop rule |d_{j+1}| ||w_{j+1}||_2 <= tol ||p_{j+1}||_2
+ *     with |d| the complex modulus and 2-norms over both parts.
+ * Only the operator's symmetry is assumed, not checked: for a non-symmetric
+ * operator the interval does not bound the spectrum and the result is not
+ * phi_k(-i h H) v.
+ * Errors: EI_ERR_STATE (no operator, or a stencil operator),
+ * EI_ERR_INVALID_ARG (k, h, tol; opt->fixed_s > 1 with k >= 1),
+ * EI_ERR_NONFINITE (NaN/Inf in v or in the iteration), EI_ERR_NOT_CONVERGED
+ * (k >= 1 needing s > 1, or no s <= 2^20), EI_ERR_NOMEM (the five complex
+ * workspaces, allocated on first use per format), EI_ERR_CUDA. */
+ei_status ei_phi_apply_imag(ei_ctx* ctx, int k, double h, const void* v, void* out, double tol,
+                            const ei_options* opt, ei_stats* stats);
+
 /* One step of size h of u' = A u + g(u), in place on the device vector u.
  * method EI_EXP_EULER:      u <- u + h phi_1(hA)(A u + g(u))          (Eq. (2))
  * method EI_EXP_ROSENBROCK: u <- u + h phi_1(hJ)(A u + g(u)), J = A + diag(g'(u))
@@ -277,6 +307,16 @@ ei_status ei_divided_differences(int k, double tau, double c, double gamma, int 
  * meets max_G |f - p_m| <= tol max_G |f| on 2001 points G of [-2,2]. */
 ei_status ei_schedule(int k, double h, double c, double gamma, double tol, int m_max,
                       int* s_out, int* m_out);
+/* The skew case of ei_phi_apply_imag: d_j of f(xi) = phi_k(-i tau (c + gamma xi)),
+ * complex, j = 0..m (m <= 100), from Opitz's matrix with complex entries
+ * (scaling, a Taylor polynomial and squaring).  out: host array of 2(m+1)
+ * doubles, interleaved (Re d_j, Im d_j). */
+ei_status ei_divided_differences_imag(int k, double tau, double c, double gamma, int m,
+                                      double* out);
+/* The a-priori rule of ei_schedule with that complex f (max_G |f - p_m| with
+ * the complex modulus). */
+ei_status ei_schedule_imag(int k, double h, double c, double gamma, double tol, int m_max,
+                           int* s_out, int* m_out);
 
 /* ---- Learned schedule ------------------------------------------------------
  * A small network proposes the substep count and the Leja degree of a phi_1

@@ -19,7 +19,7 @@ ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 CUDA_HOME = os.environ.get("CUDA_HOME", "/usr/local/cuda")
 NVCC = os.path.join(CUDA_HOME, "bin", "nvcc")
 
-CU_SOURCES = ["ei_kernels.cu", "ei_newton_tma.cu", "ei_batch.cu", "ei_mlp.cu"]
+CU_SOURCES = ["ei_kernels.cu", "ei_newton_tma.cu", "ei_batch.cu", "ei_mlp.cu", "ei_complex.cu"]
 CPP_SOURCES = ["ei_api.cpp", "ei_leja.cpp"]
 HEADERS = ["df.cuh", "ei_internal.h", "ei_device.cuh"]
 

@@ -25,6 +25,10 @@ void divided_differences(int k, double tau, double c, double gamma, int m, doubl
 int schedule(int k, double h, double c, double gamma, double tol, int m_max, int* s_out,
              int* m_out, double* d_out);
 double phi_scalar(int k, double z);
+void divided_differences_imag(int k, double tau, double c, double gamma, int m, double* out);
+int schedule_imag(int k, double h, double c, double gamma, double tol, int m_max, int* s_out,
+                  int* m_out, double* d_out);
+void phi_imag(int k, double y, double* re, double* im);
 }  // namespace ei
 
 using namespace ei;
@@ -88,6 +92,9 @@ struct ei_ctx {
   Prepared prep[3];
   // staging for ei_step_host
   void* host_stage = nullptr;
+  // complex workspaces of ei_phi_apply_imag (v, r, w0, w1, p), format cx_fmt
+  void* cx[5] = {nullptr, nullptr, nullptr, nullptr, nullptr};
+  int cx_fmt = -1;
   // launch accounting and optional per-launch timing of the Newton kernel
   int launches = 0;
   bool profile = false;
@@ -178,6 +185,11 @@ static void free_operator(ei_ctx* c) {
   c->ger_lo = c->ger_hi = nullptr;
   c->partials = nullptr;
   c->host_stage = nullptr;
+  for (auto& a : c->cx) {
+    if (a) cudaFree(a);
+    a = nullptr;
+  }
+  c->cx_fmt = -1;
   c->max_blocks = 0;
   c->kind = KIND_NONE;
   c->cs_valid = false;
@@ -325,13 +337,26 @@ static cudaError_t op_newton2(ei_ctx* c, Prepared& P, const void* qc, const void
 
 // One Newton loop on w_0 = r into P.p.  Returns the degree in *deg; *ok = 0
 // when m_max was reached without meeting tol.
+// With cx (complex run, CSR only): d and cx->d_im are the real and imaginary
+// parts of d_j, and the complex workspaces cx->w, cx->p take the place of
+// P.w, P.p.
+struct CxRun {
+  const double* d_im;
+  void* w[2];
+  void* p;
+  int lanes;  // lanes per row of the CSR kernel (ei_options.csr_lanes)
+};
+
 static ei_status newton_loop(ei_ctx* c, Prepared& P, const void* qc, const void* r,
                              const std::vector<double>& d, double cc, double gamma, double tol,
-                             int m_max, int m_pred, int* deg, int* ok) {
+                             int m_max, int m_pred, int* deg, int* ok,
+                             const CxRun* cx = nullptr) {
   const double* xi = leja_table();
   EI_TRY(reset_done(c));
   NewtonScalars s{};
   s.d0 = d[0];
+  if (cx) s.d0_im = cx->d_im[0];
+  void* const wbuf[2] = {cx ? cx->w[0] : P.w[0], cx ? cx->w[1] : P.w[1]};
   s.inv_gamma = 1.0 / gamma;
   s.tol = tol;
   s.m_max = m_max;
@@ -359,10 +384,15 @@ static ei_status newton_loop(ei_ctx* c, Prepared& P, const void* qc, const void*
         s.d_next2 = d[j + 2];
         s.shift2 = cc / gamma + xi[j + 1];
       }
-      const void* w_in = (nl == 0) ? r : P.w[(nl - 1) & 1];
-      void* w_out = P.w[nl & 1];
+      const void* w_in = (nl == 0) ? r : wbuf[(nl - 1) & 1];
+      void* w_out = wbuf[nl & 1];
       if (c->profile) EI_TRY_CUDA(cudaEventRecord(c->ev[2 * nl], c->stream));
-      if (two) {
+      if (cx) {
+        s.d_next_im = cx->d_im[j + 1];
+        ++c->launches;
+        EI_TRY_CUDA(launch_csr_newton_c(csr_view(c, P, qc), c->nnz, cx->lanes, w_in, w_out,
+                                        cx->p, s, P.fmt, c->partials, c->ctl, c->stream));
+      } else if (two) {
         EI_TRY_CUDA(op_newton2(c, P, qc, w_in, w_out, s));
       } else {
         EI_TRY_CUDA(op_newton(c, P, qc, w_in, w_out, s));
@@ -1206,6 +1236,124 @@ static ei_status phi_apply_impl(ei_ctx* c, int k, double h, const void* v, void*
       s *= 2;
     }
   }
+  return rc;
+}
+
+// phi_k(-i h H) v, H the context's CSR operator (real symmetric), v complex
+// (Sec. II-C with K = C).  The interval [alpha, beta] of H and the real Leja
+// points are those of the real path; the divided differences of
+// f(xi) = phi_k(-i tau (c + gamma xi)) are complex.  k = 0 applies
+// e^{-i tau H} s times; k >= 1 takes one substep (s = 1).
+static ei_status phi_imag_impl(ei_ctx* c, int k, double h, const void* v, void* out, double tol,
+                               const ei_options* opt, ei_stats* st) {
+  if (c->kind == KIND_NONE) return EI_ERR_STATE;
+  if (c->kind != KIND_CSR) return EI_ERR_STATE;
+  if (k < 0 || k > 8 || !(h > 0) || !isfinite(h) || !(tol > 0) || !isfinite(tol))
+    return EI_ERR_INVALID_ARG;
+  if (opt && opt->fixed_s > 1 && k >= 1) return EI_ERR_INVALID_ARG;
+  EI_TRY_CUDA(cudaSetDevice(c->device));
+  const int fmt = vec_fmt_for(c, opt);
+  EI_TRY(prepare(c, fmt));
+  Prepared& P = c->prep[fmt];
+  const int64_t n = c->n;
+  if (c->cx_fmt != fmt) {
+    for (auto& a : c->cx) {
+      if (a) cudaFree(a);
+      a = nullptr;
+    }
+    c->cx_fmt = -1;
+    const size_t vb = 2 * vec_elem_bytes(fmt) * (size_t)n, pb = 2 * p_elem_bytes(fmt) * (size_t)n;
+    for (int i = 0; i < 5; ++i) {
+      ei_status r = alloc(&c->cx[i], i == 4 ? pb : vb);
+      if (r != EI_OK) {
+        for (auto& a : c->cx) {
+          if (a) cudaFree(a);
+          a = nullptr;
+        }
+        return r;
+      }
+    }
+    c->cx_fmt = fmt;
+  }
+  void* cv = c->cx[0];
+  void* cr = c->cx[1];
+  CxRun run{nullptr, {c->cx[2], c->cx[3]}, c->cx[4], opt ? opt->csr_lanes : 0};
+  // a complex vector of n is a real vector of 2n in the same format
+  EI_LAUNCH(launch_import(cv, fmt, v, c->prec, 2 * n, (int)(2 * n), 1, (int)(2 * n), c->partials,
+                          c->ctl, c->stream));
+  EI_TRY(read_ctl(c));
+  if (c->h_ctl->sum1 != 1.0) return EI_ERR_NONFINITE;
+  const double vnorm2 = c->h_ctl->sum0;
+  const double alpha = c->alphaA, beta = c->betaA;
+  double cc, gamma;
+  interval(alpha, beta, &cc, &gamma);
+  if (st) { st->alpha = alpha; st->beta = beta; st->s = 1; }
+  if (vnorm2 == 0.0 || gamma == 0.0) {  // 0, or H = cI: phi_k(-i h c) v
+    double fr = 0.0, fi = 0.0;
+    if (vnorm2 != 0.0) phi_imag(k, -h * cc, &fr, &fi);
+    EI_LAUNCH(launch_cexport(out, c->prec, cv, fmt, 0, n, fr, fi, c->stream));
+    EI_TRY_CUDA(cudaStreamSynchronize(c->stream));
+    return EI_OK;
+  }
+  const int m_max = (opt && opt->m_max > 0 && opt->m_max <= 100) ? opt->m_max : 100;
+  int s = 1, m_pred = 0;
+  const bool fixed = opt && opt->fixed_s > 0;
+  if (fixed) s = opt->fixed_s;
+  else if (schedule_imag(k, h, cc, gamma, tol, m_max, &s, &m_pred, nullptr) != 0)
+    return EI_ERR_NOT_CONVERGED;
+  if (st) st->m_sched = m_pred;
+  std::vector<double> dd(2 * (m_max + 1)), d(m_max + 1), di(m_max + 1);
+  int restarts = 0;
+  while (s <= (1 << 20)) {
+    if (k >= 1 && s > 1) return EI_ERR_NOT_CONVERGED;  // one substep only for k >= 1
+    const double tau = h / s;
+    divided_differences_imag(k, tau, cc, gamma, m_max, dd.data());
+    for (int j = 0; j <= m_max; ++j) {
+      d[j] = dd[2 * j];
+      di[j] = dd[2 * j + 1];
+    }
+    run.d_im = di.data();
+    bool ok_all = true;
+    int dsum = 0, dmax = 0;
+    const void* cur = cv;
+    for (int i = 0; i < s; ++i) {
+      if (i > 0) {
+        EI_LAUNCH(launch_p_to_vec(cr, run.p, fmt, 2 * n, c->stream));
+        cur = cr;
+      }
+      int deg = 0, ok = 0;
+      EI_TRY(newton_loop(c, P, base_diag(P), cur, d, cc, gamma, tol, m_max, m_pred, &deg, &ok,
+                         &run));
+      if (st) st->matvecs += deg;
+      if (!ok) { ok_all = false; break; }
+      if (st && i < EI_STATS_MAX_SUBSTEPS) st->degrees[i] = deg;
+      dsum += deg;
+      if (deg > dmax) dmax = deg;
+    }
+    if (ok_all) {
+      if (st) {
+        st->s = s; st->restarts = restarts; st->degree_sum = dsum; st->degree_max = dmax;
+      }
+      EI_LAUNCH(launch_export(out, c->prec, run.p, fmt, 1, 2 * n, (int)(2 * n), 1, (int)(2 * n),
+                              1.0, c->stream));
+      EI_TRY_CUDA(cudaStreamSynchronize(c->stream));
+      return EI_OK;
+    }
+    if (fixed) return EI_ERR_NOT_CONVERGED;
+    ++restarts;
+    s *= 2;
+  }
+  return EI_ERR_NOT_CONVERGED;
+}
+
+ei_status ei_phi_apply_imag(ei_ctx* c, int k, double h, const void* v, void* out, double tol,
+                            const ei_options* opt, ei_stats* st) {
+  stats_reset(st);
+  if (!c || !v || !out) return EI_ERR_INVALID_ARG;
+  acct_begin(c, opt);
+  ei_status rc = phi_imag_impl(c, k, h, v, out, tol, opt, st);
+  acct_end(c, st);
+  log_stats("phi_apply_imag", st, rc);
   return rc;
 }
 

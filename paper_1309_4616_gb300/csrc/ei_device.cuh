@@ -252,6 +252,37 @@ __device__ __forceinline__ double acc_d(double a) { return a; }
 __device__ __forceinline__ double acc_d(float a) { return (double)a; }
 __device__ __forceinline__ double acc_d(dfacc a) { return (double)a.s + (double)a.t; }
 
+// accumulate / finish a row sum (two independent chains; float-float lazily
+// normalised)
+__device__ __forceinline__ dfacc lmac(dfacc c, df a, df b) { return dfa_mac(c, a, b); }
+__device__ __forceinline__ double lmac(double c, double a, double b) { return fma(a, b, c); }
+__device__ __forceinline__ float lmac(float c, float a, float b) { return fmaf(a, b, c); }
+__device__ __forceinline__ df lsum(dfacc a, dfacc b) { return dfa_norm(dfa_add(a, b)); }
+__device__ __forceinline__ double lsum(double a, double b) { return a + b; }
+__device__ __forceinline__ float lsum(float a, float b) { return a + b; }
+
+// CSR row pipelining (ei_kernels.cu, ei_complex.cu): rows walk a grid-stride
+// loop; each thread prefetches the first CSR_PFC columns of its next row into
+// its own shared-memory slots with cp.async.
+constexpr int CSR_PF = 12;
+constexpr int CSR_PFC = 20;
+__device__ __forceinline__ void cp_async4(void* smem, const void* gmem) {
+  const unsigned sa = (unsigned)__cvta_generic_to_shared(smem);
+  asm volatile("cp.async.ca.shared.global [%0], [%1], 4;" ::"r"(sa), "l"(gmem) : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
+template <int N>
+__device__ __forceinline__ void cp_async_wait() { asm volatile("cp.async.wait_group %0;" ::"n"(N) : "memory"); }
+
+// the first CSR_PFC columns of entries [b, e) into this thread's slots
+__device__ __forceinline__ void csr_prefetch_cols(int32_t (*slot)[EI_TPB], const int32_t* col,
+                                                  int64_t b, int64_t e) {
+#pragma unroll
+  for (int q = 0; q < CSR_PFC; ++q)
+    if (b + q < e) cp_async4(&slot[q][threadIdx.x], col + b + q);
+}
+
+
 template <int FMT> struct VT;
 template <> struct VT<VF_DF> { using T = df; using P = df; };
 template <> struct VT<VF_F64> { using T = double; using P = double; };

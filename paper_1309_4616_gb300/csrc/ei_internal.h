@@ -65,6 +65,8 @@ struct NewtonScalars {
   double shift2;       // two-iteration kernel: c/gamma + xi_{j+1}
   int fixed;           // 1: fixed-count mode, m_max steps exactly; only degree m_max
                        //    is tested and a failure counts into ctl->fixfail
+  double d_next_im;    // complex Newton sum (k_csr_newton_c): Im d_{j+1}
+  double d0_im;        //   and Im d_0
 };
 
 // Tensor maps of the TMA-staged Newton kernel (3D maps over the padded
@@ -189,6 +191,21 @@ cudaError_t launch_p_fixup(void* p, const void* w, int fmt, int64_t n_alloc, dou
 cudaError_t launch_csr_newton(const CsrDev& op, const void* w_in, void* w_out, void* p,
                               const NewtonScalars& s, int fmt, double* partials, DevCtl* ctl,
                               cudaStream_t st);
+
+// Complex vectors for phi_k(-i h H) v, H real symmetric (ei_complex.cu):
+// interleaved (re, im) elements of the vector format (df: re.hi, re.lo,
+// im.hi, im.lo) and of the Newton-sum format.  A complex vector of n
+// elements is a real vector of 2n in the same format, so import, the
+// Newton-sum -> vector copy and unscaled export are the real launchers on 2n.
+// One Newton step of the CSR operator on complex w with complex d_j
+// (s.d_next + i s.d_next_im, s.d0 + i s.d0_im); verdict on |d_{j+1}|.
+// lanes: lanes per row (1, 2, 4, 8, 16, 32; other values: by nnz / n).
+cudaError_t launch_csr_newton_c(const CsrDev& op, int64_t nnz, int lanes, const void* w_in,
+                                void* w_out, void* p, const NewtonScalars& s, int fmt,
+                                double* partials, DevCtl* ctl, cudaStream_t st);
+// dst = (sr + i si) * src, src a Newton sum (src_is_p) or a vector of format fmt
+cudaError_t launch_cexport(void* dst, int prec, const void* src, int fmt, int src_is_p,
+                           int64_t n, double sr, double si, cudaStream_t st);
 
 // The schedule network (ei_mlp.cu): outputs (rows x EI_MLP_OUTPUTS, FP32
 // rounding) for host feature rows (FP64); synchronises the model's stream.

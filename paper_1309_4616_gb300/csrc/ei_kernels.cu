@@ -285,12 +285,6 @@ k_stencil_F(StencilDev g, const void* __restrict__ u_, void* __restrict__ F_,
 // and gather loads in batches (eight, then four at a time; two independent
 // accumulators) and keeps every lane busy in the Newton update.
 // ---------------------------------------------------------------------------
-__device__ __forceinline__ dfacc lmac(dfacc c, df a, df b) { return dfa_mac(c, a, b); }
-__device__ __forceinline__ double lmac(double c, double a, double b) { return fma(a, b, c); }
-__device__ __forceinline__ float lmac(float c, float a, float b) { return fmaf(a, b, c); }
-__device__ __forceinline__ df lsum(dfacc a, dfacc b) { return dfa_norm(dfa_add(a, b)); }
-__device__ __forceinline__ double lsum(double a, double b) { return a + b; }
-__device__ __forceinline__ float lsum(float a, float b) { return a + b; }
 
 // (W x)_row
 template <class T>
@@ -339,24 +333,6 @@ __device__ __forceinline__ T csr_row(const CsrDev& op, const T* __restrict__ x, 
 // CSR_PFC columns are prefetched; its entries are consumed in register batches
 // of CSR_PF (value loads and gathers of a batch issued together); columns past
 // CSR_PFC are read directly, four at a time.
-constexpr int CSR_PF = 12;
-constexpr int CSR_PFC = 20;
-__device__ __forceinline__ void cp_async4(void* smem, const void* gmem) {
-  const unsigned sa = (unsigned)__cvta_generic_to_shared(smem);
-  asm volatile("cp.async.ca.shared.global [%0], [%1], 4;" ::"r"(sa), "l"(gmem) : "memory");
-}
-__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
-template <int N>
-__device__ __forceinline__ void cp_async_wait() { asm volatile("cp.async.wait_group %0;" ::"n"(N) : "memory"); }
-
-// the first CSR_PFC columns of entries [b, e) into this thread's slots
-__device__ __forceinline__ void csr_prefetch_cols(int32_t (*slot)[EI_TPB], const int32_t* col,
-                                                  int64_t b, int64_t e) {
-#pragma unroll
-  for (int q = 0; q < CSR_PFC; ++q)
-    if (b + q < e) cp_async4(&slot[q][threadIdx.x], col + b + q);
-}
-
 template <class T>
 __device__ __forceinline__ T csr_row_pf(const CsrDev& op, const T* __restrict__ x, int64_t b,
                                         int64_t e, const int32_t (*slot)[EI_TPB]) {

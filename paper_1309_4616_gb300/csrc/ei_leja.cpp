@@ -12,6 +12,7 @@
 #include <string.h>
 
 #include <algorithm>
+#include <complex>
 #include <mutex>
 #include <vector>
 
@@ -262,6 +263,173 @@ int schedule(int k, double h, double c, double gamma, double tol, int m_max, int
   return 1;
 }
 
+// ---------------------------------------------------------------------------
+// The skew case A = -iH, H real symmetric (products (alpha A + beta I)x with
+// K = C, Sec. II-C): f(xi) = phi_k(-i tau (c + gamma xi)) on H's real interval.
+// Opitz's matrix is the one above with complex entries,
+//     N = bidiag(diag = [0 x k, -i tau (c + gamma xi_j)],
+//                subdiag = [1 x k, -i tau gamma x m]),
+// and d_j = exp(N)[k+j][0].  The Metzler shift does not apply; exp(N) is
+// formed by scaling (entries of X at most 1/2), a degree-24 Taylor
+// polynomial (||X||_1 <= 1, truncation below 1/25!) and squaring.  The
+// entries of every power of exp(2^-q N) are divided differences of unimodular
+// exponentials scaled by (tau gamma 2^-q)^j, bounded by about 1, so the
+// rounding errors stay near eps in absolute terms.
+// ---------------------------------------------------------------------------
+typedef std::complex<double> cplx;
+
+static void expm_bidiag_col0_c(int n, const cplx* dg, const cplx* sd, cplx* out) {
+  double mx = 0.0;
+  for (int i = 0; i < n; ++i) mx = std::max(mx, std::abs(dg[i]));
+  for (int i = 0; i + 1 < n; ++i) mx = std::max(mx, std::abs(sd[i]));
+  int q = 0;
+  while (ldexp(0.5, q) < mx) ++q;
+  const double sc = ldexp(1.0, -q);
+  std::vector<cplx> xd(n), xs(n > 1 ? n - 1 : 1);
+  for (int i = 0; i < n; ++i) xd[i] = dg[i] * sc;
+  for (int i = 0; i + 1 < n; ++i) xs[i] = sd[i] * sc;
+  const int K = 24;
+  std::vector<cplx> T((size_t)n * n, 0.0), U((size_t)n * n, 0.0);
+  for (int i = 0; i < n; ++i) T[(size_t)i * n + i] = 1.0;
+  for (int it = K; it >= 1; --it) {  // T <- I + X T / it (Horner), band K - it + 1
+    const double inv = 1.0 / it;
+    const int band = K - it + 1;
+    U[0] = xd[0] * T[0] * inv + 1.0;
+    for (int r = 1; r < n; ++r) {
+      cplx* Ur = &U[(size_t)r * n];
+      const cplx* Tr = &T[(size_t)r * n];
+      const cplx* Tm = &T[(size_t)(r - 1) * n];
+      const cplx a = xd[r], b = xs[r - 1];
+      const int c0 = r - band > 0 ? r - band : 0;
+      for (int c = c0; c < r; ++c) Ur[c] = (a * Tr[c] + b * Tm[c]) * inv;
+      Ur[r] = a * Tr[r] * inv + 1.0;
+    }
+    std::swap(T, U);
+  }
+  // exp(N) e_0 = T^(2^q) e_0: `sq` squarings, then 2^(q-sq) triangular products
+  int sq = 0;
+  {
+    double best = 0.0;
+    for (int j = 0; j <= q; ++j) {
+      const double cost = j * (double)n * n * n / 6.0 + ldexp((double)n * n / 2.0, q - j);
+      if (j == 0 || cost < best) { best = cost; sq = j; }
+    }
+  }
+  for (int it = 0; it < sq; ++it) {
+    for (int r = 0; r < n; ++r) {
+      cplx* Ur = &U[(size_t)r * n];
+      const cplx* Tr = &T[(size_t)r * n];
+      for (int c = 0; c <= r; ++c) Ur[c] = 0.0;
+      for (int l = 0; l <= r; ++l) {
+        const cplx t = Tr[l];
+        const cplx* Tl = &T[(size_t)l * n];
+        for (int c = 0; c <= l; ++c) Ur[c] += t * Tl[c];
+      }
+    }
+    std::swap(T, U);
+  }
+  std::vector<cplx> y(n), z(n);
+  for (int r = 0; r < n; ++r) y[r] = T[(size_t)r * n];
+  for (long rep = 1; rep < (1L << (q - sq)); ++rep) {
+    for (int r = 0; r < n; ++r) {
+      const cplx* Tr = &T[(size_t)r * n];
+      cplx a = 0.0;
+      for (int l = 0; l <= r; ++l) a += Tr[l] * y[l];
+      z[r] = a;
+    }
+    std::swap(y, z);
+  }
+  for (int r = 0; r < n; ++r) out[r] = y[r];
+}
+
+void divided_differences_imag(int k, double tau, double c, double gamma, int m, double* out) {
+  const int n = k + m + 1;
+  std::vector<cplx> dg(n, 0.0), sd(n > 1 ? n - 1 : 1, 0.0), col(n);
+  const double* xi = leja_table();
+  for (int j = 0; j <= m; ++j) dg[k + j] = cplx(0.0, -(tau * c + tau * gamma * xi[j]));
+  for (int i = 0; i < k; ++i) sd[i] = 1.0;
+  for (int i = k; i + 1 < n; ++i) sd[i] = cplx(0.0, -tau * gamma);
+  expm_bidiag_col0_c(n, dg.data(), sd.data(), col.data());
+  for (int j = 0; j <= m; ++j) {
+    out[2 * j] = col[k + j].real();
+    out[2 * j + 1] = col[k + j].imag();
+  }
+}
+
+// phi_k(z) for complex z: series for |z| < 1, else the recurrence from e^z
+static cplx phi_scalar_c(int k, cplx z) {
+  if (k == 0) return std::exp(z);
+  if (std::abs(z) < 1.0) {
+    double fact = 1.0;
+    for (int i = 2; i <= k; ++i) fact *= i;
+    cplx term = 1.0 / fact, sum = term;
+    for (int i = 0; i < 60; ++i) {
+      term *= z / (double)(i + k + 1);
+      sum += term;
+      if (std::abs(term) < 1e-18 * std::abs(sum)) break;
+    }
+    return sum;
+  }
+  cplx v = (std::exp(z) - 1.0) / z;
+  double fact = 1.0;
+  for (int j = 2; j <= k; ++j) {
+    v = (v - 1.0 / fact) / z;
+    fact *= j;
+  }
+  return v;
+}
+
+void phi_imag(int k, double y, double* re, double* im) {
+  const cplx v = phi_scalar_c(k, cplx(0.0, y));
+  *re = v.real();
+  *im = v.imag();
+}
+
+// The a-priori rule of `schedule` with the complex f (max over the grid of
+// |f - p_m| against tol max |f|); d_out (optional) gets the interleaved
+// divided differences at the chosen s.
+int schedule_imag(int k, double h, double c, double gamma, double tol, int m_max, int* s_out,
+                  int* m_out, double* d_out) {
+  const double* xi = leja_table();
+  std::vector<double> g(kGrid), om(kGrid), d(2 * (m_max + 1));
+  std::vector<cplx> f(kGrid), p(kGrid);
+  const double step = 4.0 / (kGrid - 1);
+  for (int i = 0; i < kGrid; ++i) g[i] = (double)i * step + (-2.0);
+  g[kGrid - 1] = 2.0;
+  for (int q = 0; q <= 20; ++q) {
+    const int s = 1 << q;
+    const double tau = h / s;
+    divided_differences_imag(k, tau, c, gamma, m_max, d.data());
+    double fmax = 0.0;
+    for (int i = 0; i < kGrid; ++i) {
+      f[i] = phi_scalar_c(k, cplx(0.0, -(tau * c + tau * gamma * g[i])));
+      fmax = std::max(fmax, std::abs(f[i]));
+      p[i] = 0.0;
+      om[i] = 1.0;
+    }
+    const double bound = tol * fmax;
+    for (int j = 0; j <= m_max; ++j) {
+      const cplx dj(d[2 * j], d[2 * j + 1]);
+      const double xj = xi[j];
+      for (int i = 0; i < kGrid; ++i) {
+        p[i] += dj * om[i];
+        om[i] *= (g[i] - xj);
+      }
+      bool pass = true;
+      for (int i = 0; i < kGrid; ++i)
+        if (!(std::abs(f[i] - p[i]) <= bound)) { pass = false; break; }
+      if (pass) {
+        *s_out = s;
+        *m_out = j;
+        if (d_out)
+          for (int i = 0; i < 2 * (m_max + 1); ++i) d_out[i] = d[i];
+        return 0;
+      }
+    }
+  }
+  return 1;
+}
+
 }  // namespace ei
 
 // exported host entry points -------------------------------------------------
@@ -287,4 +455,23 @@ extern "C" ei_status ei_schedule(int k, double h, double c, double gamma, double
     return EI_ERR_INVALID_ARG;
   return ei::schedule(k, h, c, gamma, tol, m_max, s_out, m_out, nullptr) ? EI_ERR_NOT_CONVERGED
                                                                           : EI_OK;
+}
+
+extern "C" ei_status ei_divided_differences_imag(int k, double tau, double c, double gamma, int m,
+                                                 double* out) {
+  if (k < 0 || k > 8 || m < 0 || m > ei::kMaxM || !out || !(tau > 0) || !(gamma >= 0) ||
+      !isfinite(tau) || !isfinite(c) || !isfinite(gamma))
+    return EI_ERR_INVALID_ARG;
+  ei::divided_differences_imag(k, tau, c, gamma, m, out);
+  return EI_OK;
+}
+
+extern "C" ei_status ei_schedule_imag(int k, double h, double c, double gamma, double tol,
+                                      int m_max, int* s_out, int* m_out) {
+  if (k < 0 || k > 8 || !(h > 0) || !isfinite(h) || !(tol > 0) || m_max < 1 ||
+      m_max > ei::kMaxM || !s_out || !m_out || !(gamma > 0) || !isfinite(c) || !isfinite(gamma))
+    return EI_ERR_INVALID_ARG;
+  return ei::schedule_imag(k, h, c, gamma, tol, m_max, s_out, m_out, nullptr)
+             ? EI_ERR_NOT_CONVERGED
+             : EI_OK;
 }

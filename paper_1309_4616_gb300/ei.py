@@ -32,14 +32,15 @@ EXPORTS = [
     "ei_mlp_create", "ei_mlp_destroy", "ei_mlp_set_params", "ei_mlp_get_params",
     "ei_mlp_set_decision", "ei_mlp_get_decision", "ei_mlp_forward", "ei_mlp_loss_grad",
     "ei_mlp_train_step", "ei_set_schedule_model", "ei_batch_set_schedule_model",
-    "ei_nonlinearity", "ei_set_dirichlet_values",
+    "ei_nonlinearity", "ei_set_dirichlet_values", "ei_phi_apply_imag",
+    "ei_divided_differences_imag", "ei_schedule_imag",
 ]
 
 
 class Options(C.Structure):
     _fields_ = [("m_max", C.c_int), ("arith", C.c_int), ("fixed_s", C.c_int),
                 ("profile", C.c_int), ("single_iter", C.c_int), ("tile_rows", C.c_int),
-                ("learned", C.c_int), ("no_restart", C.c_int)]
+                ("learned", C.c_int), ("no_restart", C.c_int), ("csr_lanes", C.c_int)]
 
 
 class Stats(C.Structure):
@@ -109,6 +110,11 @@ def lib():
         L.ei_estimate_spectrum.argtypes = [vp, dp, dp]
         L.ei_phi_apply.argtypes = [vp, C.c_int, C.c_double, vp, vp, C.c_double,
                                    C.POINTER(Options), C.POINTER(Stats)]
+        L.ei_phi_apply_imag.argtypes = L.ei_phi_apply.argtypes
+        L.ei_divided_differences_imag.argtypes = [C.c_int, C.c_double, C.c_double,
+                                                  C.c_double, C.c_int, dp]
+        L.ei_schedule_imag.argtypes = [C.c_int, C.c_double, C.c_double, C.c_double,
+                                       C.c_double, C.c_int, ip, ip]
         L.ei_step.argtypes = [vp, C.c_int, C.c_double, vp, C.c_int, C.c_double,
                               C.POINTER(Options), C.POINTER(Stats)]
         L.ei_step_host.argtypes = L.ei_step.argtypes
@@ -179,6 +185,23 @@ def divided_differences(k, tau, c, gamma, m=100):
                                         out.ctypes.data_as(C.POINTER(C.c_double))),
            "ei_divided_differences")
     return out
+
+
+def divided_differences_imag(k, tau, c, gamma, m=100):
+    """d_j of f(xi) = phi_k(-i tau (c + gamma xi)), complex (numpy complex128)."""
+    import numpy as np
+    out = np.zeros(2 * (m + 1))
+    _check(lib().ei_divided_differences_imag(k, tau, c, gamma, m,
+                                             out.ctypes.data_as(C.POINTER(C.c_double))),
+           "ei_divided_differences_imag")
+    return out[0::2] + 1j * out[1::2]
+
+
+def schedule_imag(k, h, c, gamma, tol, m_max=100):
+    s, m = C.c_int(0), C.c_int(0)
+    _check(lib().ei_schedule_imag(k, h, c, gamma, tol, m_max, C.byref(s), C.byref(m)),
+           "ei_schedule_imag")
+    return s.value, m.value
 
 
 def schedule(k, h, c, gamma, tol, m_max=100):
@@ -340,6 +363,19 @@ class Context:
         if not check:
             return rc, st
         _check(rc, "ei_phi_apply")
+        return st
+
+    def phi_apply_imag(self, k, h, v, out, tol, options=None, check=True):
+        """out = phi_k(-i h H) v for the context's CSR operator H (real
+        symmetric); v, out complex128 (FP64 context) or complex64 (FP32)."""
+        dt = self._torch.complex128 if self.prec == PREC_F64 else self._torch.complex64
+        st = Stats()
+        rc = lib().ei_phi_apply_imag(self._h, k, h, _dev_ptr(v, dt, self._n(), "v"),
+                                     _dev_ptr(out, dt, self._n(), "out"), tol,
+                                     self._opts(options), C.byref(st))
+        if not check:
+            return rc, st
+        _check(rc, "ei_phi_apply_imag")
         return st
 
     def step(self, method, h, u, nonlin, tol, options=None, check=True):

@@ -20,6 +20,8 @@ Workloads (sizes as the paper's experiments use them, Sec. III-A to III-D):
   combustion_field  u ~ U[1, 2] on n^3 points (Table 3's evaluation).
   rgg_graph       -(graph Laplacian) of a random geometric graph in the unit
                   cube: 2^20 nodes, mean degree 12, edge weights U[0.5, 2].
+  spin_bath       Hamiltonian of two central spins in a bath (Sec. III-D):
+                  21 spins, n = 2^21 states, 39 XYZ bonds, 40 entries a row.
 """
 from __future__ import annotations
 
@@ -258,3 +260,55 @@ def rgg_graph(n: int = 1 << 20, mean_degree: float = 12.0, seed: int = SEED_BASE
 
 def random_vector(n, seed):
     return np.random.default_rng(seed).standard_normal(n)
+
+
+# --------------------------------------------------------------------------
+# Two central spins in a spin bath (Sec. III-D), CSR in the sigma_z basis
+# --------------------------------------------------------------------------
+@dataclass
+class SpinBath:
+    n: int
+    rowptr: np.ndarray      # int64, n+1
+    col: np.ndarray         # int32, off-diagonal entries (one per bond)
+    val: np.ndarray         # float64
+    diag: np.ndarray        # float64
+    bonds: list             # (i, j, Jx, Jy, Jz)
+
+
+def spin_bath(n_spins: int = 21, seed: int = SEED_BASE + 6) -> SpinBath:
+    """H = sum over bonds (i, j) of Jx X_i X_j + Jy Y_i Y_j + Jz Z_i Z_j for
+    spins 0 and 1 (the central pair, bonded to each other) and the bath
+    spins 2..n_spins-1 (each bonded to both central spins, not to each
+    other): 2 n_spins - 3 bonds, so each row holds one entry per bond plus the
+    diagonal (40 for 21 spins: 2^21 x 40 = 83.9e6 entries, as in the paper).
+    Couplings: central pair U[0.5, 1.5] per component, central-bath
+    U[-0.5, 0.5].  In the sigma_z basis (bit i of the state = spin i down)
+    X_i X_j and Y_i Y_j both flip bits i and j: the entry is Jx - Jy for
+    aligned spins and Jx + Jy for opposite ones; Z_i Z_j is diagonal, +-Jz.
+    H is real symmetric; columns of a row are in bond order."""
+    rng = np.random.default_rng(seed)
+    bonds = [(0, 1, *rng.uniform(0.5, 1.5, 3))]
+    for b in range(2, n_spins):
+        for c in (0, 1):
+            bonds.append((c, b, *rng.uniform(-0.5, 0.5, 3)))
+    n = 1 << n_spins
+    st = np.arange(n, dtype=np.int64)
+    nb = len(bonds)
+    col = np.empty((n, nb), dtype=np.int32)
+    val = np.empty((n, nb), dtype=np.float64)
+    diag = np.zeros(n)
+    for q, (i, j, jx, jy, jz) in enumerate(bonds):
+        anti = ((st >> i) ^ (st >> j)) & 1
+        col[:, q] = st ^ ((1 << i) | (1 << j))
+        val[:, q] = np.where(anti == 1, jx + jy, jx - jy)
+        diag += np.where(anti == 1, -jz, jz)
+    rowptr = np.arange(0, n * nb + 1, nb, dtype=np.int64)
+    return SpinBath(n=n, rowptr=rowptr, col=col.reshape(-1), val=val.reshape(-1), diag=diag,
+                    bonds=bonds)
+
+
+def spin_state(n: int, seed: int = SEED_BASE + 7) -> np.ndarray:
+    """A random normalised complex state (Gaussian real and imaginary parts)."""
+    rng = np.random.default_rng(seed)
+    v = rng.standard_normal(n) + 1j * rng.standard_normal(n)
+    return v / np.linalg.norm(v)

@@ -8,6 +8,7 @@ import numpy as np
 import pytest
 
 from oracle import leja as L
+from oracle import skew as S
 
 ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
 
@@ -75,3 +76,33 @@ def test_invalid_arguments(ei):
     assert e.value.status == ei.ERR_INVALID_ARG
     with pytest.raises(ei.EIError):
         ei.leja_points(101)
+
+
+@pytest.mark.parametrize("k,tau,c,gamma", [
+    (0, 1.0, 0.0, 0.5),
+    (0, 2.0, 3.0, 4.0),
+    (0, 0.3, -50.0, 20.0),
+    (0, 0.35, 0.4, 22.0),                # a substep of the 21-spin bath interval
+    (1, 5.0, 1.0, 2.0),
+    (3, 0.3, -50.0, 20.0),
+])
+def test_divided_differences_imag_match_oracle(ei, k, tau, c, gamma):
+    """The complex Opitz exponential: entries are bounded by about 1, and the
+    library's double-precision scaling and squaring holds them to ~1e-14 in
+    absolute terms against the oracle's decimal divided differences."""
+    xi = L.leja_points(100)
+    d = ei.divided_differences_imag(k, tau, c, gamma, 100)
+    do = S.divided_differences_imag(k, tau, c, gamma, xi)
+    assert np.abs(d - do).max() <= 1e-13 * max(1.0, np.abs(do).max())
+
+
+@pytest.mark.parametrize("k,h,c,gamma,tol", [
+    (0, 20.0, 0.0, 0.5, 1e-10),
+    (0, 200.0, 0.0, 0.5, 1e-10),
+    (0, 7.0, 3.0, 2.0, 1e-5),
+    (1, 3.0, 1.0, 1.0, 1e-10),
+    (2, 1.0, 5.0, 2.0, 1e-8),
+])
+def test_schedule_imag_matches_oracle(ei, k, h, c, gamma, tol):
+    xi = L.leja_points(100)
+    assert ei.schedule_imag(k, h, c, gamma, tol) == S.schedule_imag(k, h, c, gamma, tol, xi)

@@ -102,3 +102,29 @@ def test_diagonal_closed_form(xi):
             zs = np.where(z == 0, 1.0, z)
             ex = np.where(z == 0, 0.5, (np.exp(zs) - 1 - zs) / zs ** 2)
         np.testing.assert_allclose(y, ex, rtol=1e-10, atol=1e-12)
+
+
+def test_spin_bath_hamiltonian_against_kronecker():
+    """The synthetic spin-bath matrix (the input of the Schroedinger workload)
+    equals sum_bonds Jx X_i X_j + Jy Y_i Y_j + Jz Z_i Z_j built from 2x2 Pauli
+    matrices by Kronecker products (spin i = bit i), and is real symmetric."""
+    from paper_1309_4616_gb300 import workloads as W
+    g = W.spin_bath(7)
+    M = O.CsrOperator(g.n, g.rowptr, g.col, g.val, g.diag).dense()
+    X = np.array([[0, 1], [1, 0]], dtype=complex)
+    Y = np.array([[0, -1j], [1j, 0]])
+    Z = np.diag([1.0, -1.0]).astype(complex)
+
+    def site(P, i, N):
+        out = np.ones((1, 1), dtype=complex)
+        for q in range(N - 1, -1, -1):
+            out = np.kron(out, P if q == i else np.eye(2))
+        return out
+
+    H = np.zeros((g.n, g.n), dtype=complex)
+    for i, j, jx, jy, jz in g.bonds:
+        for P, J in ((X, jx), (Y, jy), (Z, jz)):
+            H += J * site(P, i, 7) @ site(P, j, 7)
+    assert np.abs(H.imag).max() == 0.0
+    np.testing.assert_allclose(M, H.real, rtol=0, atol=1e-14)
+    assert len(g.bonds) == 2 * 7 - 3 and len(g.col) == g.n * len(g.bonds)
