@@ -498,7 +498,7 @@ class RggCsr(Workload):
         return st
 
     def kernel(self, fused):
-        return "k_csr_newton<float-float> (rows pipelined across a grid-stride walk)"
+        return "k_csr_newton_g<float-float, 2 lanes a row> (32 rows a warp in 2 rounds)"
 
 
 class PhiKAdr3d(Adr3d):

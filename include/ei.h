@@ -100,10 +100,10 @@ typedef struct {
   int no_restart;  /* with fixed_s: an attempt that reaches m_max returns
                       EI_ERR_NOT_CONVERGED instead of doubling s (stats keep the
                       degrees reached; u and out are left unmodified) */
-  int csr_lanes;   /* ei_phi_apply_imag on CSR: lanes of a warp per row in the
-                      Newton kernel, 1, 2, 4, 8, 16 or 32; 0 (or any other
-                      value) chooses by the mean row length: 1 below 16
-                      entries, 4 below 96, else 8 */
+  int csr_lanes;   /* CSR operators: lanes of a warp per row in the Newton
+                      kernel, 1, 2, 4, 8, 16 or 32; 0 (or any other value)
+                      chooses by the mean row length: 1 below 8 entries,
+                      2 below 24, 4 below 96, else 8 */
 } ei_options;
 
 #define EI_STATS_MAX_SUBSTEPS 64

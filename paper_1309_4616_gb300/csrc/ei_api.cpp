@@ -102,6 +102,7 @@ struct ei_ctx {
   double newton_ms = 0.0;
   int newton_fused = 1;
   bool fuse2 = true;       // two Newton iterations per launch where the kernel allows
+  int csr_lanes = 0;       // lanes per row of the CSR Newton kernels (0: by row length)
   std::vector<cudaEvent_t> ev;
   // learned schedule: the model (caller-owned), the operator's coefficient
   // statistics (computed on first use) and ||v||^2 of the current phi_1 call
@@ -314,7 +315,8 @@ static cudaError_t op_newton(ei_ctx* c, Prepared& P, const void* qc, const void*
     return launch_newton_tma(stencil_view(c, P, qc), M, w_out, P.p, s, P.fmt, c->partials,
                              c->ctl, c->stream);
   }
-  return launch_csr_newton(csr_view(c, P, qc), w_in, w_out, P.p, s, P.fmt, c->partials, c->ctl,
+  return launch_csr_newton(csr_view(c, P, qc), c->nnz, c->csr_lanes, w_in, w_out, P.p, s, P.fmt,
+                           c->partials, c->ctl,
                            c->stream);
 }
 
@@ -1044,6 +1046,7 @@ static void acct_begin(ei_ctx* c, const ei_options* opt) {
   c->newton_fused = 1;
   c->profile = opt && opt->profile;
   c->fuse2 = !(opt && opt->single_iter);
+  c->csr_lanes = opt ? opt->csr_lanes : 0;
 }
 
 static void acct_end(ei_ctx* c, ei_stats* st) {

@@ -195,11 +195,6 @@ k_csr_newton_c(CsrDev op, const void* __restrict__ w_in_, void* __restrict__ w_o
 // with one of the 32 rows and the Newton update (the heavier part for the
 // float-float format) runs on all lanes at once.  The warp walks its rows
 // together (a warp-uniform loop bound), so the shuffles see all 32 lanes.
-__device__ __forceinline__ double shfl_x(double v, int m) { return __shfl_xor_sync(0xffffffffu, v, m); }
-__device__ __forceinline__ float shfl_x(float v, int m) { return __shfl_xor_sync(0xffffffffu, v, m); }
-__device__ __forceinline__ df shfl_x(df v, int m) {
-  return df{__shfl_xor_sync(0xffffffffu, v.hi, m), __shfl_xor_sync(0xffffffffu, v.lo, m)};
-}
 
 template <int FMT, int G, int U = (FMT == VF_F32 ? 8 : 4)>
 __global__ void __launch_bounds__(EI_TPB)
@@ -360,15 +355,6 @@ static int sm_count() {
   return n;
 }
 
-// lanes per row: the caller's choice, else by the mean row length (one lane
-// for short rows, where the pipelined one-lane kernel hides the gather chain)
-static int lanes_for(const CsrDev& op, int64_t nnz, int lanes) {
-  if (lanes == 1 || lanes == 2 || lanes == 4 || lanes == 8 || lanes == 16 || lanes == 32)
-    return lanes;
-  const double mean = op.n > 0 ? (double)nnz / (double)op.n : 0.0;
-  return mean < 16.0 ? 1 : mean < 96.0 ? 4 : 8;
-}
-
 template <class K>
 static int grid_for(K kernel, int64_t rows_per_block, int64_t n) {
   int per = 1;
@@ -417,7 +403,7 @@ static cudaError_t csr_newton_c_fmt(const CsrDev& op, int lanes, const void* w_i
 cudaError_t launch_csr_newton_c(const CsrDev& op, int64_t nnz, int lanes, const void* w_in,
                                 void* w_out, void* p, const NewtonScalars& s, int fmt,
                                 double* partials, DevCtl* ctl, cudaStream_t stm) {
-  const int g = lanes_for(op, nnz, lanes);
+  const int g = csr_lanes_for(op.n, nnz, lanes);
   switch (fmt) {
     case VF_DF: return csr_newton_c_fmt<VF_DF>(op, g, w_in, w_out, p, s, partials, ctl, stm);
     case VF_F64: return csr_newton_c_fmt<VF_F64>(op, g, w_in, w_out, p, s, partials, ctl, stm);

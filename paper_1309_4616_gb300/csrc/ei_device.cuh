@@ -261,6 +261,13 @@ __device__ __forceinline__ df lsum(dfacc a, dfacc b) { return dfa_norm(dfa_add(a
 __device__ __forceinline__ double lsum(double a, double b) { return a + b; }
 __device__ __forceinline__ float lsum(float a, float b) { return a + b; }
 
+// butterfly exchange within a warp (all 32 lanes take part)
+__device__ __forceinline__ double shfl_x(double v, int m) { return __shfl_xor_sync(0xffffffffu, v, m); }
+__device__ __forceinline__ float shfl_x(float v, int m) { return __shfl_xor_sync(0xffffffffu, v, m); }
+__device__ __forceinline__ df shfl_x(df v, int m) {
+  return df{__shfl_xor_sync(0xffffffffu, v.hi, m), __shfl_xor_sync(0xffffffffu, v.lo, m)};
+}
+
 // CSR row pipelining (ei_kernels.cu, ei_complex.cu): rows walk a grid-stride
 // loop; each thread prefetches the first CSR_PFC columns of its next row into
 // its own shared-memory slots with cp.async.

@@ -188,9 +188,13 @@ cudaError_t launch_newton2_tma(const StencilDev& op, const NewtonMaps& M, void* 
 // p -= d * w (elementwise, Newton-sum format p, vector format w)
 cudaError_t launch_p_fixup(void* p, const void* w, int fmt, int64_t n_alloc, double d,
                            cudaStream_t st);
-cudaError_t launch_csr_newton(const CsrDev& op, const void* w_in, void* w_out, void* p,
-                              const NewtonScalars& s, int fmt, double* partials, DevCtl* ctl,
-                              cudaStream_t st);
+// lanes: lanes per row (1, 2, 4, 8, 16, 32; any other value: csr_lanes_for's rule)
+cudaError_t launch_csr_newton(const CsrDev& op, int64_t nnz, int lanes, const void* w_in,
+                              void* w_out, void* p, const NewtonScalars& s, int fmt,
+                              double* partials, DevCtl* ctl, cudaStream_t st);
+// lanes per row of the CSR Newton kernels: `lanes` when valid, else by the
+// mean row length (1 below 8 entries, 2 below 24, 4 below 96, else 8)
+int csr_lanes_for(int64_t n, int64_t nnz, int lanes);
 
 // Complex vectors for phi_k(-i h H) v, H real symmetric (ei_complex.cu):
 // interleaved (re, im) elements of the vector format (df: re.hi, re.lo,

@@ -441,6 +441,111 @@ k_csr_newton(CsrDev op, const void* __restrict__ w_in_, void* __restrict__ w_out
   }
 }
 
+// The Newton step with G lanes per row (G = 2..32): the warp takes 32 rows
+// in G rounds of 32/G rows, the lanes of a group reading consecutive entries
+// of a row (whole sectors of the value and column arrays per warp load);
+// after round t lane t of each group keeps its row's sum, so the update runs
+// on all 32 lanes.  The 33 row pointers of the 32 rows come from one
+// coalesced load and reach the rounds by shuffle.  float-float and double:
+// whole batches of U entries a lane, then one at a time; float: predicated
+// batches.
+template <int FMT, int G, int U = (FMT == VF_F32 ? 8 : 4)>
+__global__ void __launch_bounds__(EI_TPB)
+k_csr_newton_g(CsrDev op, const void* __restrict__ w_in_, void* __restrict__ w_out_,
+               void* __restrict__ p_, NewtonScalars s, double* partials, DevCtl* ctl) {
+  using T = typename VT<FMT>::T;
+  using P = typename VT<FMT>::P;
+  if (*(volatile int*)&ctl->done != 0) return;
+  const T* __restrict__ w_in = static_cast<const T*>(w_in_);
+  T* __restrict__ w_out = static_cast<T*>(w_out_);
+  P* __restrict__ p = static_cast<P*>(p_);
+  const T* __restrict__ qc = static_cast<const T*>(op.qc);
+  const T* __restrict__ val = static_cast<const T*>(op.val);
+  const T invg = from_d<T>(s.inv_gamma);
+  const T nshift = from_d<T>(-s.shift);
+  const P dn = from_d<P>(s.d_next);
+  const P d0 = from_d<P>(s.d0);
+  typename Acc<T>::type aw = Acc<T>::zero();
+  typename Acc<P>::type ap = Acc<P>::zero();
+  constexpr int RPW = 32 / G;
+  const int L = threadIdx.x & 31;
+  const int lane = L & (G - 1);
+  const int gsub = L / G;
+  const int64_t warp = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  const int64_t nwarp = ((int64_t)gridDim.x * blockDim.x) >> 5;
+  const int64_t n = op.n;
+  for (int64_t r0 = warp * 32; r0 < n; r0 += nwarp * 32) {
+    const int64_t rl = r0 + L < n ? r0 + L : n;
+    const int64_t rp_lo = __ldg(op.rowptr + rl);
+    const int64_t rp_hi = __ldg(op.rowptr + (rl + 1 < n ? rl + 1 : n));
+    T mine = zero<T>();
+#pragma unroll 1
+    for (int t = 0; t < G; ++t) {
+      const int src = t * RPW + gsub;
+      const int64_t b = __shfl_sync(0xffffffffu, rp_lo, src);
+      const int64_t e = __shfl_sync(0xffffffffu, rp_hi, src);
+      typename Acc<T>::type a1 = Acc<T>::zero(), a2 = Acc<T>::zero();
+      int64_t k = b + lane;
+      if constexpr (FMT != VF_F32) {
+        for (; k + (U - 1) * G < e; k += U * G) {
+          int c[U];
+          T v[U], xv[U];
+#pragma unroll
+          for (int q = 0; q < U; ++q) c[q] = __ldg(op.col + k + q * G);
+#pragma unroll
+          for (int q = 0; q < U; ++q) v[q] = ldg(val, k + q * G);
+#pragma unroll
+          for (int q = 0; q < U; ++q) xv[q] = ldg(w_in, c[q]);
+#pragma unroll
+          for (int q = 0; q + 1 < U; q += 2) {
+            a1 = lmac(a1, v[q], xv[q]);
+            a2 = lmac(a2, v[q + 1], xv[q + 1]);
+          }
+        }
+        for (; k < e; k += G) a1 = lmac(a1, ldg(val, k), ldg(w_in, __ldg(op.col + k)));
+      }
+      for (; FMT == VF_F32 && k < e; k += U * G) {
+        int c[U];
+        T v[U], xv[U];
+#pragma unroll
+        for (int q = 0; q < U; ++q) c[q] = k + q * G < e ? __ldg(op.col + k + q * G) : -1;
+#pragma unroll
+        for (int q = 0; q < U; ++q) v[q] = c[q] >= 0 ? ldg(val, k + q * G) : zero<T>();
+#pragma unroll
+        for (int q = 0; q < U; ++q) xv[q] = c[q] >= 0 ? ldg(w_in, c[q]) : zero<T>();
+#pragma unroll
+        for (int q = 0; q + 1 < U; q += 2) {
+          a1 = lmac(a1, v[q], xv[q]);
+          a2 = lmac(a2, v[q + 1], xv[q + 1]);
+        }
+      }
+      T h = lsum(a1, a2);
+#pragma unroll
+      for (int m = G / 2; m > 0; m >>= 1) h = add(h, shfl_x(h, m));
+      if (lane == t) mine = h;
+    }
+    const int64_t row = r0 + lane * RPW + gsub;  // the row whose sum this lane kept
+    if (row < n) {
+      const T wc = ldg(w_in, row);
+      const T wn = newton_update(mac(mine, ldg(qc, row), wc), invg, nshift, wc);
+      const P pold = (s.j == 0) ? mul(d0, to_p(wc)) : ld(p, row);
+      const P pn = mac(pold, dn, to_p(wn));
+      st(w_out, row, wn);
+      st(p, row, pn);
+      aw = acc_sq(aw, wn);
+      ap = acc_sq(ap, pn);
+    }
+  }
+  double nw2 = acc_d(aw), np2 = acc_d(ap);
+  if (last_block_reduce2<RED_SUM>(nw2, np2, partials, ctl)) {
+    if (threadIdx.x == 0) {
+      ctl->nw2 = nw2;
+      ctl->np2 = np2;
+      newton_verdict(ctl, s, s.j + 1, s.d_next, nw2, np2);
+    }
+  }
+}
+
 template <int FMT>
 __global__ void __launch_bounds__(EI_TPB)
 k_csr_residual(CsrDev op, const void* __restrict__ y_, const void* __restrict__ v_,
@@ -822,10 +927,47 @@ cudaError_t launch_face_term(const StencilDev& g, int face, int prec, const doub
                                                  b_const, static_cast<const double*>(vals), out);
   return cudaGetLastError();
 }
-cudaError_t launch_csr_newton(const CsrDev& op, const void* w_in, void* w_out, void* p,
-                              const NewtonScalars& s, int fmt, double* partials, DevCtl* ctl,
-                              cudaStream_t stm) {
-  // a grid of resident blocks walking the rows (at most csr_blocks(n))
+template <int FMT, int G>
+static int csr_g_grid(int64_t n) {
+  static int per = 0;
+  if (!per) {
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, k_csr_newton_g<FMT, G>, EI_TPB, 0);
+    per = per < 1 ? 1 : (per > 8 ? 8 : per);
+  }
+  int64_t nb = (n + EI_TPB - 1) / EI_TPB;  // 32 rows a warp and pass
+  if (nb > (int64_t)num_sms() * per) nb = (int64_t)num_sms() * per;
+  return nb < 1 ? 1 : (int)nb;
+}
+
+template <int FMT>
+static void csr_newton_g_fmt(int G, const CsrDev& op, const void* w_in, void* w_out, void* p,
+                             const NewtonScalars& s, double* partials, DevCtl* ctl,
+                             cudaStream_t stm) {
+  switch (G) {
+    case 2: k_csr_newton_g<FMT, 2><<<csr_g_grid<FMT, 2>(op.n), EI_TPB, 0, stm>>>(op, w_in, w_out, p, s, partials, ctl); break;
+    case 4: k_csr_newton_g<FMT, 4><<<csr_g_grid<FMT, 4>(op.n), EI_TPB, 0, stm>>>(op, w_in, w_out, p, s, partials, ctl); break;
+    case 8: k_csr_newton_g<FMT, 8><<<csr_g_grid<FMT, 8>(op.n), EI_TPB, 0, stm>>>(op, w_in, w_out, p, s, partials, ctl); break;
+    case 16: k_csr_newton_g<FMT, 16><<<csr_g_grid<FMT, 16>(op.n), EI_TPB, 0, stm>>>(op, w_in, w_out, p, s, partials, ctl); break;
+    default: k_csr_newton_g<FMT, 32><<<csr_g_grid<FMT, 32>(op.n), EI_TPB, 0, stm>>>(op, w_in, w_out, p, s, partials, ctl); break;
+  }
+}
+
+int csr_lanes_for(int64_t n, int64_t nnz, int lanes) {
+  if (lanes == 1 || lanes == 2 || lanes == 4 || lanes == 8 || lanes == 16 || lanes == 32)
+    return lanes;
+  const double mean = n > 0 ? (double)nnz / (double)n : 0.0;
+  return mean < 8.0 ? 1 : mean < 24.0 ? 2 : mean < 96.0 ? 4 : 8;
+}
+
+cudaError_t launch_csr_newton(const CsrDev& op, int64_t nnz, int lanes, const void* w_in,
+                              void* w_out, void* p, const NewtonScalars& s, int fmt,
+                              double* partials, DevCtl* ctl, cudaStream_t stm) {
+  const int G = csr_lanes_for(op.n, nnz, lanes);
+  if (G > 1) {
+    EI_DISPATCH_FMT(fmt, (csr_newton_g_fmt<F_>(G, op, w_in, w_out, p, s, partials, ctl, stm)));
+    return cudaGetLastError();
+  }
+  // one thread a row: a grid of resident blocks walking the rows (at most csr_blocks(n))
   static int per_sm[3] = {0, 0, 0};
   if (!per_sm[fmt]) {
     int per = 1;
