@@ -45,6 +45,9 @@ BYTES_PER_POINT = 88
 # traffic scales with the points.
 # Valid for the kernel as captured: retake it when the kernel changes.
 PAIR_DRAM_BYTES_PER_POINT = 86.9
+# DRAM bytes of one launch of the float-float 4-lane complex CSR kernel on the
+# 21-spin operator (profiles/k_csr_newton_cg_spin_bath_21.md, the current kernel)
+SPIN_DRAM_BYTES_PER_LAUNCH = 1.240e9
 FLOPS_PER_POINT_PAPER = 10  # the paper's count for (alpha A + beta I)x, Sec. III-A
 
 
@@ -560,6 +563,8 @@ class SpinBath(Workload):
                        "entries_per_row": nnz / g.n + 1, "t": self.h, "tol": self.tol,
                        "method": self.method}
 
+        self.traffic_per_launch = SPIN_DRAM_BYTES_PER_LAUNCH if (n == 21 and not single) else None
+
     def step(self, ctx, opts=None):
         return ctx.phi_apply_imag(0, self.h, self.state, self.out, self.tol, opts)
 
@@ -968,7 +973,8 @@ def run_ours(args):
             "roofline": {"bound": "hbm", "achieved": achieved, "peak": hbm, "unit": "GB/s",
                          "frac": achieved / hbm,
                          "traffic": (PAIR_DRAM_BYTES_PER_POINT * npts
-                                     if isinstance(wl, Adr3d) and fused == 2 else None),
+                                     if isinstance(wl, Adr3d) and fused == 2
+                                     else getattr(wl, "traffic_per_launch", None)),
                          "kernel": wl.kernel(fused),
                          "bytes_per_launch": (prof_bytes / max(prof_n, 1)) if prof_bytes
                          else wl.bytes_per_point * npts * fused,
