@@ -48,6 +48,9 @@ PAIR_DRAM_BYTES_PER_POINT = 86.9
 # DRAM bytes of one launch of the float-float 4-lane complex CSR kernel on the
 # 21-spin operator (profiles/k_csr_newton_cg_spin_bath_21.md, the current kernel)
 SPIN_DRAM_BYTES_PER_LAUNCH = 1.240e9
+# the same for the float-float 2-lane real CSR kernel on the 2^20-node graph
+# (profiles/k_csr_newton_g_rgg_2e20.md)
+RGG_DRAM_BYTES_PER_LAUNCH = 195.6e6
 FLOPS_PER_POINT_PAPER = 10  # the paper's count for (alpha A + beta I)x, Sec. III-A
 
 
@@ -489,6 +492,7 @@ class RggCsr(Workload):
         self.bytes_per_point = 12.0 * nnz / g.n + 48.0
         self.config = {"nodes": g.n, "nnz": int(nnz), "mean_degree": nnz / g.n,
                        "h_rho": 100.0, "tol": self.tol, "method": self.method}
+        self.traffic_per_launch = RGG_DRAM_BYTES_PER_LAUNCH if n == 1 << 20 else None
 
     def step(self, ctx, opts=None):
         return ctx.phi_apply(1, self.h, self.state, self.out, self.tol, opts)
