@@ -45,12 +45,12 @@ BYTES_PER_POINT = 88
 # traffic scales with the points.
 # Valid for the kernel as captured: retake it when the kernel changes.
 PAIR_DRAM_BYTES_PER_POINT = 86.9
-# DRAM bytes of one launch of the float-float 4-lane complex CSR kernel on the
+# DRAM bytes of one launch of the float-float 2-lane complex CSR kernel on the
 # 21-spin operator (profiles/k_csr_newton_cg_spin_bath_21.md, the current kernel)
-SPIN_DRAM_BYTES_PER_LAUNCH = 1.240e9
+SPIN_DRAM_BYTES_PER_LAUNCH = 1.242e9
 # the same for the float-float 2-lane real CSR kernel on the 2^20-node graph
 # (profiles/k_csr_newton_g_rgg_2e20.md)
-RGG_DRAM_BYTES_PER_LAUNCH = 195.6e6
+RGG_DRAM_BYTES_PER_LAUNCH = 196.4e6
 FLOPS_PER_POINT_PAPER = 10  # the paper's count for (alpha A + beta I)x, Sec. III-A
 
 
@@ -580,7 +580,7 @@ class SpinBath(Workload):
 
     def kernel(self, fused):
         fmt = "float" if self.prec == 1 else "float-float"
-        return (f"k_csr_newton_cg<{fmt}, 4 lanes a row> (complex w and p interleaved, "
+        return (f"k_csr_newton_cg<{fmt}, 2 lanes a row> (complex w and p interleaved, "
                 f"real H)")
 
 

@@ -103,7 +103,7 @@ typedef struct {
   int csr_lanes;   /* CSR operators: lanes of a warp per row in the Newton
                       kernel, 1, 2, 4, 8, 16 or 32; 0 (or any other value)
                       chooses by the mean row length: 1 below 8 entries,
-                      2 below 24, 4 below 96, else 8 */
+                      2 below 64, 4 below 128, else 8 */
 } ei_options;
 
 #define EI_STATS_MAX_SUBSTEPS 64

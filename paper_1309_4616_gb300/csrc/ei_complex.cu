@@ -236,36 +236,9 @@ k_csr_newton_cg(CsrDev op, const void* __restrict__ w_in_, void* __restrict__ w_
       typename Acc<T>::type r1 = Acc<T>::zero(), r2 = Acc<T>::zero();
       typename Acc<T>::type i1 = Acc<T>::zero(), i2 = Acc<T>::zero();
       int64_t k = b + lane;
-      if constexpr (FMT != VF_F32) {
-        // float-float and FP64: whole batches of U, then one entry at a time
-        // (predicated slots would cost full multiply-adds on zeros)
-        for (; k + (U - 1) * G < e; k += U * G) {
-          int c[U];
-          T v[U];
-          Cx<T> xv[U];
-#pragma unroll
-          for (int q = 0; q < U; ++q) c[q] = __ldg(op.col + k + q * G);
-#pragma unroll
-          for (int q = 0; q < U; ++q) v[q] = ldg(val, k + q * G);
-#pragma unroll
-          for (int q = 0; q < U; ++q) xv[q] = ldgc(w_in, c[q]);
-#pragma unroll
-          for (int q = 0; q + 1 < U; q += 2) {
-            r1 = lmac(r1, v[q], xv[q].re);
-            i1 = lmac(i1, v[q], xv[q].im);
-            r2 = lmac(r2, v[q + 1], xv[q + 1].re);
-            i2 = lmac(i2, v[q + 1], xv[q + 1].im);
-          }
-        }
-        for (; k < e; k += G) {
-          const Cx<T> x = ldgc(w_in, __ldg(op.col + k));
-          const T v = ldg(val, k);
-          r1 = lmac(r1, v, x.re);
-          i1 = lmac(i1, v, x.im);
-        }
-      }
-      // FP32: U entries a lane per batch, predicated on the row end
-      for (; FMT == VF_F32 && k < e; k += U * G) {
+      // U entries a lane per batch, loads issued together, predicated on the
+      // row end; float-float and double skip the multiply-adds of empty slots
+      for (; k < e; k += U * G) {
         int c[U];
         T v[U];
         Cx<T> xv[U];
@@ -278,10 +251,14 @@ k_csr_newton_cg(CsrDev op, const void* __restrict__ w_in_, void* __restrict__ w_
           xv[q] = c[q] >= 0 ? ldgc(w_in, c[q]) : Cx<T>{zero<T>(), zero<T>()};
 #pragma unroll
         for (int q = 0; q + 1 < U; q += 2) {
-          r1 = lmac(r1, v[q], xv[q].re);
-          i1 = lmac(i1, v[q], xv[q].im);
-          r2 = lmac(r2, v[q + 1], xv[q + 1].re);
-          i2 = lmac(i2, v[q + 1], xv[q + 1].im);
+          if (FMT == VF_F32 || c[q] >= 0) {
+            r1 = lmac(r1, v[q], xv[q].re);
+            i1 = lmac(i1, v[q], xv[q].im);
+          }
+          if (FMT == VF_F32 || c[q + 1] >= 0) {
+            r2 = lmac(r2, v[q + 1], xv[q + 1].re);
+            i2 = lmac(i2, v[q + 1], xv[q + 1].im);
+          }
         }
       }
       T hr = lsum(r1, r2), hi = lsum(i1, i2);

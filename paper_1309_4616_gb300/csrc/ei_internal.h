@@ -193,7 +193,7 @@ cudaError_t launch_csr_newton(const CsrDev& op, int64_t nnz, int lanes, const vo
                               void* w_out, void* p, const NewtonScalars& s, int fmt,
                               double* partials, DevCtl* ctl, cudaStream_t st);
 // lanes per row of the CSR Newton kernels: `lanes` when valid, else by the
-// mean row length (1 below 8 entries, 2 below 24, 4 below 96, else 8)
+// mean row length (1 below 8 entries, 2 below 64, 4 below 128, else 8)
 int csr_lanes_for(int64_t n, int64_t nnz, int lanes);
 
 // Complex vectors for phi_k(-i h H) v, H real symmetric (ei_complex.cu):

@@ -446,10 +446,9 @@ k_csr_newton(CsrDev op, const void* __restrict__ w_in_, void* __restrict__ w_out
 // of a row (whole sectors of the value and column arrays per warp load);
 // after round t lane t of each group keeps its row's sum, so the update runs
 // on all 32 lanes.  The 33 row pointers of the 32 rows come from one
-// coalesced load and reach the rounds by shuffle.  float-float and double:
-// whole batches of U entries a lane, then one at a time; float: predicated
-// batches.
-template <int FMT, int G, int U = (FMT == VF_F32 ? 8 : 4)>
+// coalesced load and reach the rounds by shuffle.  A lane's entries go in
+// predicated batches of U (all loads of a batch in flight together).
+template <int FMT, int G, int U = (FMT == VF_F32 ? 8 : 6)>
 __global__ void __launch_bounds__(EI_TPB)
 k_csr_newton_g(CsrDev op, const void* __restrict__ w_in_, void* __restrict__ w_out_,
                void* __restrict__ p_, NewtonScalars s, double* partials, DevCtl* ctl) {
@@ -486,25 +485,9 @@ k_csr_newton_g(CsrDev op, const void* __restrict__ w_in_, void* __restrict__ w_o
       const int64_t e = __shfl_sync(0xffffffffu, rp_hi, src);
       typename Acc<T>::type a1 = Acc<T>::zero(), a2 = Acc<T>::zero();
       int64_t k = b + lane;
-      if constexpr (FMT != VF_F32) {
-        for (; k + (U - 1) * G < e; k += U * G) {
-          int c[U];
-          T v[U], xv[U];
-#pragma unroll
-          for (int q = 0; q < U; ++q) c[q] = __ldg(op.col + k + q * G);
-#pragma unroll
-          for (int q = 0; q < U; ++q) v[q] = ldg(val, k + q * G);
-#pragma unroll
-          for (int q = 0; q < U; ++q) xv[q] = ldg(w_in, c[q]);
-#pragma unroll
-          for (int q = 0; q + 1 < U; q += 2) {
-            a1 = lmac(a1, v[q], xv[q]);
-            a2 = lmac(a2, v[q + 1], xv[q + 1]);
-          }
-        }
-        for (; k < e; k += G) a1 = lmac(a1, ldg(val, k), ldg(w_in, __ldg(op.col + k)));
-      }
-      for (; FMT == VF_F32 && k < e; k += U * G) {
+      // U entries a lane per batch, loads issued together, predicated on the
+      // row end; float-float and double skip the multiply-adds of empty slots
+      for (; k < e; k += U * G) {
         int c[U];
         T v[U], xv[U];
 #pragma unroll
@@ -515,8 +498,8 @@ k_csr_newton_g(CsrDev op, const void* __restrict__ w_in_, void* __restrict__ w_o
         for (int q = 0; q < U; ++q) xv[q] = c[q] >= 0 ? ldg(w_in, c[q]) : zero<T>();
 #pragma unroll
         for (int q = 0; q + 1 < U; q += 2) {
-          a1 = lmac(a1, v[q], xv[q]);
-          a2 = lmac(a2, v[q + 1], xv[q + 1]);
+          if (FMT == VF_F32 || c[q] >= 0) a1 = lmac(a1, v[q], xv[q]);
+          if (FMT == VF_F32 || c[q + 1] >= 0) a2 = lmac(a2, v[q + 1], xv[q + 1]);
         }
       }
       T h = lsum(a1, a2);
@@ -956,7 +939,7 @@ int csr_lanes_for(int64_t n, int64_t nnz, int lanes) {
   if (lanes == 1 || lanes == 2 || lanes == 4 || lanes == 8 || lanes == 16 || lanes == 32)
     return lanes;
   const double mean = n > 0 ? (double)nnz / (double)n : 0.0;
-  return mean < 8.0 ? 1 : mean < 24.0 ? 2 : mean < 96.0 ? 4 : 8;
+  return mean < 8.0 ? 1 : mean < 64.0 ? 2 : mean < 128.0 ? 4 : 8;
 }
 
 cudaError_t launch_csr_newton(const CsrDev& op, int64_t nnz, int lanes, const void* w_in,
