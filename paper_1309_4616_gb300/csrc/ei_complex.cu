@@ -200,6 +200,7 @@ template <int FMT, int G, int U = (FMT == VF_F32 ? 8 : 4)>
 __global__ void __launch_bounds__(EI_TPB)
 k_csr_newton_cg(CsrDev op, const void* __restrict__ w_in_, void* __restrict__ w_out_,
                 void* __restrict__ p_, NewtonScalars s, double* partials, DevCtl* ctl) {
+  static_assert(U % 2 == 0, "batches accumulate entries in pairs");
   using T = typename VT<FMT>::T;
   using P = typename VT<FMT>::P;
   if (*(volatile int*)&ctl->done != 0) return;

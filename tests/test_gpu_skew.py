@@ -224,3 +224,31 @@ def test_lanes_per_row_ragged(env, xi, lanes):
     assert st.s == s and st.degree_list() == list(degs)
     assert crel(out.cpu().numpy(), ref) <= 1e-9
     ctx.close()
+
+
+def test_m_max_option_and_k1_substep_limit(env, xi):
+    """A small m_max: the rule takes more substeps of lower degree, and the
+    result, s and degrees match the oracle's with the same m_max.  For k >= 1
+    a time step whose rule needs s > 1 is refused (one substep only), as the
+    oracle refuses it."""
+    torch, ei = env
+    g = W.spin_bath(9)
+    op = O.CsrOperator(g.n, g.rowptr, g.col, g.val, g.diag)
+    v0 = W.spin_state(g.n, 4)
+    ctx = spin_context(torch, ei, g)
+    v = cdev(torch, v0)
+    out = torch.empty_like(v)
+    for m_max, h in ((12, 3.0), (20, 1.0)):
+        ref, s, degs = S.phi_apply_imag(op, 0, h, v0, 1e-10, m_max=m_max, xi=xi)
+        st = ctx.phi_apply_imag(0, h, v, out, 1e-10, {"m_max": m_max})
+        assert st.s == s and st.degree_list() == list(degs)
+        assert crel(out.cpu().numpy(), ref) <= 1e-9
+    a, b = op.gershgorin()
+    h = 12.0
+    assert S.schedule_imag(1, h, 0.5 * (a + b), 0.25 * (b - a), 1e-10, xi)[0] > 1
+    with pytest.raises(RuntimeError):
+        S.phi_apply_imag(op, 1, h, v0, 1e-10, xi=xi)
+    with pytest.raises(ei.EIError) as e:
+        ctx.phi_apply_imag(1, h, v, out, 1e-10)
+    assert e.value.status == ei.ERR_NOT_CONVERGED
+    ctx.close()
