@@ -346,7 +346,6 @@ struct CxRun {
   const double* d_im;
   void* w[2];
   void* p;
-  int lanes;  // lanes per row of the CSR kernel (ei_options.csr_lanes)
 };
 
 static ei_status newton_loop(ei_ctx* c, Prepared& P, const void* qc, const void* r,
@@ -392,7 +391,7 @@ static ei_status newton_loop(ei_ctx* c, Prepared& P, const void* qc, const void*
       if (cx) {
         s.d_next_im = cx->d_im[j + 1];
         ++c->launches;
-        EI_TRY_CUDA(launch_csr_newton_c(csr_view(c, P, qc), c->nnz, cx->lanes, w_in, w_out,
+        EI_TRY_CUDA(launch_csr_newton_c(csr_view(c, P, qc), c->nnz, c->csr_lanes, w_in, w_out,
                                         cx->p, s, P.fmt, c->partials, c->ctl, c->stream));
       } else if (two) {
         EI_TRY_CUDA(op_newton2(c, P, qc, w_in, w_out, s));
@@ -1280,7 +1279,7 @@ static ei_status phi_imag_impl(ei_ctx* c, int k, double h, const void* v, void* 
   }
   void* cv = c->cx[0];
   void* cr = c->cx[1];
-  CxRun run{nullptr, {c->cx[2], c->cx[3]}, c->cx[4], opt ? opt->csr_lanes : 0};
+  CxRun run{nullptr, {c->cx[2], c->cx[3]}, c->cx[4]};
   // a complex vector of n is a real vector of 2n in the same format
   EI_LAUNCH(launch_import(cv, fmt, v, c->prec, 2 * n, (int)(2 * n), 1, (int)(2 * n), c->partials,
                           c->ctl, c->stream));

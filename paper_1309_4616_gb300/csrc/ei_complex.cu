@@ -333,48 +333,47 @@ static int sm_count() {
   return n;
 }
 
+// resident blocks per SM of a kernel variant, from the occupancy calculator
+// once per variant (capped at 8, the reduction partials' capacity per SM)
 template <class K>
-static int grid_for(K kernel, int64_t rows_per_block, int64_t n) {
+static int blocks_per_sm(K kernel) {
   int per = 1;
   cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, kernel, EI_TPB, 0);
-  per = per < 1 ? 1 : (per > 8 ? 8 : per);
-  int64_t nb = (n + rows_per_block - 1) / rows_per_block;
-  if (nb > (int64_t)sm_count() * per) nb = (int64_t)sm_count() * per;
+  return per < 1 ? 1 : (per > 8 ? 8 : per);
+}
+
+// a grid of resident blocks walking the rows: at most one block per 256 rows
+static int grid_of(int per_sm, int64_t n) {
+  int64_t nb = (n + EI_TPB - 1) / EI_TPB;
+  if (nb > (int64_t)sm_count() * per_sm) nb = (int64_t)sm_count() * per_sm;
   return nb < 1 ? 1 : (int)nb;
+}
+
+template <int FMT, int G>
+static void launch_cg(const CsrDev& op, const void* w_in, void* w_out, void* p,
+                      const NewtonScalars& s, double* partials, DevCtl* ctl, cudaStream_t stm) {
+  static const int per = blocks_per_sm(k_csr_newton_cg<FMT, G>);
+  k_csr_newton_cg<FMT, G><<<grid_of(per, op.n), EI_TPB, 0, stm>>>(op, w_in, w_out, p, s,
+                                                                 partials, ctl);
 }
 
 template <int FMT>
 static cudaError_t csr_newton_c_fmt(const CsrDev& op, int lanes, const void* w_in, void* w_out,
                                     void* p, const NewtonScalars& s, double* partials,
                                     DevCtl* ctl, cudaStream_t stm) {
-  // the grid of each variant is computed once (occupancy is fixed per kernel)
-  static int nb_cache[6] = {0, 0, 0, 0, 0, 0};
-  static int64_t n_cache[6] = {-1, -1, -1, -1, -1, -1};
-  const int li = lanes == 1 ? 0 : lanes == 2 ? 1 : lanes == 4 ? 2 : lanes == 8 ? 3 : lanes == 16 ? 4 : 5;
-#define EI_CG(G_)                                                                              \
-  {                                                                                            \
-    if (n_cache[li] != op.n) {                                                                 \
-      nb_cache[li] = grid_for(k_csr_newton_cg<FMT, G_>, EI_TPB, op.n);                    \
-      n_cache[li] = op.n;                                                                      \
-    }                                                                                          \
-    k_csr_newton_cg<FMT, G_><<<nb_cache[li], EI_TPB, 0, stm>>>(op, w_in, w_out, p, s, partials, \
-                                                               ctl);                           \
-  }
   switch (lanes) {
-    case 1:
-      if (n_cache[0] != op.n) {
-        nb_cache[0] = grid_for(k_csr_newton_c<FMT>, EI_TPB, op.n);
-        n_cache[0] = op.n;
-      }
-      k_csr_newton_c<FMT><<<nb_cache[0], EI_TPB, 0, stm>>>(op, w_in, w_out, p, s, partials, ctl);
+    case 1: {
+      static const int per = blocks_per_sm(k_csr_newton_c<FMT>);
+      k_csr_newton_c<FMT><<<grid_of(per, op.n), EI_TPB, 0, stm>>>(op, w_in, w_out, p, s,
+                                                                  partials, ctl);
       break;
-    case 2: EI_CG(2) break;
-    case 4: EI_CG(4) break;
-    case 8: EI_CG(8) break;
-    case 16: EI_CG(16) break;
-    default: EI_CG(32) break;
+    }
+    case 2: launch_cg<FMT, 2>(op, w_in, w_out, p, s, partials, ctl, stm); break;
+    case 4: launch_cg<FMT, 4>(op, w_in, w_out, p, s, partials, ctl, stm); break;
+    case 8: launch_cg<FMT, 8>(op, w_in, w_out, p, s, partials, ctl, stm); break;
+    case 16: launch_cg<FMT, 16>(op, w_in, w_out, p, s, partials, ctl, stm); break;
+    default: launch_cg<FMT, 32>(op, w_in, w_out, p, s, partials, ctl, stm); break;
   }
-#undef EI_CG
   return cudaGetLastError();
 }
 

@@ -447,9 +447,11 @@ k_csr_newton(CsrDev op, const void* __restrict__ w_in_, void* __restrict__ w_out
 // after round t lane t of each group keeps its row's sum, so the update runs
 // on all 32 lanes.  The 33 row pointers of the 32 rows come from one
 // coalesced load and reach the rounds by shuffle.  A lane's entries go in
-// predicated batches of U (all loads of a batch in flight together).
-template <int FMT, int G, int U = (FMT == VF_F32 ? 8 : 6)>
-__global__ void __launch_bounds__(EI_TPB)
+// predicated batches of U (all loads of a batch in flight together).  Five
+// blocks of 256 per SM (48 registers) hold more rows in flight; the
+// float-float variants of 4 or more lanes spill 8-12 bytes at that bound.
+template <int FMT, int G, int U = (FMT == VF_F32 ? 8 : 4)>
+__global__ void __launch_bounds__(EI_TPB, 5)
 k_csr_newton_g(CsrDev op, const void* __restrict__ w_in_, void* __restrict__ w_out_,
                void* __restrict__ p_, NewtonScalars s, double* partials, DevCtl* ctl) {
   static_assert(U % 2 == 0, "batches accumulate entries in pairs");
@@ -913,11 +915,12 @@ cudaError_t launch_face_term(const StencilDev& g, int face, int prec, const doub
 }
 template <int FMT, int G>
 static int csr_g_grid(int64_t n) {
-  static int per = 0;
-  if (!per) {
-    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, k_csr_newton_g<FMT, G>, EI_TPB, 0);
-    per = per < 1 ? 1 : (per > 8 ? 8 : per);
-  }
+  // resident blocks per SM, once per variant (capped at 8: the partials' capacity)
+  static const int per = [] {
+    int b = 1;
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, k_csr_newton_g<FMT, G>, EI_TPB, 0);
+    return b < 1 ? 1 : (b > 8 ? 8 : b);
+  }();
   int64_t nb = (n + EI_TPB - 1) / EI_TPB;  // 32 rows a warp and pass
   if (nb > (int64_t)num_sms() * per) nb = (int64_t)num_sms() * per;
   return nb < 1 ? 1 : (int)nb;
