@@ -50,7 +50,7 @@ PAIR_DRAM_BYTES_PER_POINT = 86.9
 SPIN_DRAM_BYTES_PER_LAUNCH = 1.242e9
 # the same for the float-float 2-lane real CSR kernel on the 2^20-node graph
 # (profiles/k_csr_newton_g_rgg_2e20.md)
-RGG_DRAM_BYTES_PER_LAUNCH = None
+RGG_DRAM_BYTES_PER_LAUNCH = 195.8e6
 FLOPS_PER_POINT_PAPER = 10  # the paper's count for (alpha A + beta I)x, Sec. III-A
 
 
