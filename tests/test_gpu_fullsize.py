@@ -10,6 +10,9 @@ and through properties that hold at any size where it does not.
     64^3 restriction (every 8th point, offset 4), within 1e-5; the FP64 path
     itself is held to the oracle by the other tests.  The same FP32 form on a
     64^3 grid against the oracle directly.
+  * 21-spin bath propagator (2^21 complex states, t = 10, tol 1e-5): the
+    substep count against the oracle's rule, unitarity, energy conservation,
+    the group property and the FP32 form against FP64.
 """
 import numpy as np
 import pytest
@@ -17,6 +20,7 @@ import pytest
 from oracle import leja as L
 from oracle import newton as Nw
 from oracle import operators as O
+from oracle import skew as S
 from paper_1309_4616_gb300 import workloads as W
 
 from gpu_helpers import dev, rel_err, require_gpu
@@ -147,4 +151,64 @@ def test_paper_table4_matvec_count(env):
     mv = g["matvecs_per_step"]
     print(f"matvecs per step: {st.matvecs} (paper: {mv:.0f})")
     assert mv / 2.5 <= st.matvecs <= mv * 2.5
+    ctx.close()
+
+
+def test_spin_bath_21_propagator_fullsize(env, xi):
+    """The spin-bath workload as benchmarked: 21 spins (2^21 complex states,
+    40 entries a row), e^{-i t H} psi at t = 10, tol 1e-5.  The oracle cannot
+    run this size; checked instead:
+      * the interval equals the Gershgorin interval computed here in numpy,
+        and s equals the oracle's a-priori rule for it (bit-exact);
+      * e^{-itH} is unitary: | ||psi(t)|| - 1 | <= 1e-4 (s tol, s = 4);
+      * energy is conserved: |<H>_t - <H>_0| <= 2 rho 1e-4 (a perturbation
+        delta of psi moves <H> by at most 2 ||H|| ||delta||);
+      * two calls of t/2 agree with one call of t within 2e-4;
+      * the FP32 form agrees with the FP64 result within 1e-4 (same
+        schedule and degrees, FP32 rounding over 308 steps)."""
+    torch, ei = env
+    g = W.spin_bath(21)
+    n = g.n
+    ctx = ei.Context()
+    keep = [dev(torch, g.rowptr), dev(torch, g.col), dev(torch, g.val), dev(torch, g.diag)]
+    ctx.set_operator_csr(n, *keep)
+    radius = np.abs(g.val).reshape(n, -1).sum(axis=1)
+    alpha, beta = float((g.diag - radius).min()), float((g.diag + radius).max())
+    a, b = ctx.estimate_spectrum()
+    assert a == pytest.approx(alpha, rel=1e-14) and b == pytest.approx(beta, rel=1e-14)
+    c, gamma = 0.5 * (alpha + beta), 0.25 * (beta - alpha)
+    s_ref, _ = S.schedule_imag(0, 10.0, c, gamma, 1e-5, xi)
+    v0 = W.spin_state(n, 5)
+    v = dev(torch, v0)
+    out = torch.empty_like(v)
+    st = ctx.phi_apply_imag(0, 10.0, v, out, 1e-5)
+    assert st.s == s_ref
+    y = out.cpu().numpy()
+    assert abs(np.linalg.norm(y) - 1.0) <= 1e-4
+    Hop = torch.sparse_csr_tensor(keep[0], keep[1].long(), keep[2], (n, n))
+
+    def energy(x):
+        xt = torch.from_numpy(x).cuda()
+        re = (Hop @ xt.real.contiguous().unsqueeze(1)).squeeze(1)
+        im = (Hop @ xt.imag.contiguous().unsqueeze(1)).squeeze(1)
+        hx = torch.complex(re, im)
+        hx = hx + keep[3] * xt
+        return float(torch.vdot(xt, hx).real)
+
+    rho = max(abs(alpha), abs(beta))
+    assert abs(energy(y) - energy(v0)) <= 2 * rho * 1e-4
+    half = torch.empty_like(v)
+    ctx.phi_apply_imag(0, 5.0, v, half, 1e-5)
+    ctx.phi_apply_imag(0, 5.0, half, half, 1e-5)
+    assert np.linalg.norm(half.cpu().numpy() - y) <= 2e-4
+    ctx.close()
+    # the FP32 form on FP32-rounded couplings and state
+    ctx = ei.Context()
+    k32 = [keep[0], keep[1], keep[2].float(), keep[3].float()]
+    ctx.set_operator_csr(n, *k32, prec=ei.PREC_F32)
+    v32 = v.to(torch.complex64)
+    o32 = torch.empty_like(v32)
+    st32 = ctx.phi_apply_imag(0, 10.0, v32, o32, 1e-5)
+    assert st32.s == st.s
+    assert np.linalg.norm(o32.cpu().numpy().astype(complex) - y) <= 1e-4
     ctx.close()
