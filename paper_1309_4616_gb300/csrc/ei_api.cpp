@@ -1248,8 +1248,7 @@ static ei_status phi_apply_impl(ei_ctx* c, int k, double h, const void* v, void*
 // e^{-i tau H} s times; k >= 1 takes one substep (s = 1).
 static ei_status phi_imag_impl(ei_ctx* c, int k, double h, const void* v, void* out, double tol,
                                const ei_options* opt, ei_stats* st) {
-  if (c->kind == KIND_NONE) return EI_ERR_STATE;
-  if (c->kind != KIND_CSR) return EI_ERR_STATE;
+  if (c->kind != KIND_CSR) return EI_ERR_STATE;  // no operator, or a stencil operator
   if (k < 0 || k > 8 || !(h > 0) || !isfinite(h) || !(tol > 0) || !isfinite(tol))
     return EI_ERR_INVALID_ARG;
   if (opt && opt->fixed_s > 1 && k >= 1) return EI_ERR_INVALID_ARG;
