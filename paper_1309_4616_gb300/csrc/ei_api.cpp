@@ -95,6 +95,15 @@ struct ei_ctx {
   // complex workspaces of ei_phi_apply_imag (v, r, w0, w1, p), format cx_fmt
   void* cx[5] = {nullptr, nullptr, nullptr, nullptr, nullptr};
   int cx_fmt = -1;
+  // the last complex plan: for a fixed H, repeated calls with the same
+  // (k, h, tol, m_max) reuse the a-priori s, its degree estimate and the
+  // divided differences at tau = h/s (keyed on the exact values)
+  struct {
+    bool valid = false;
+    int k = 0, m_max = 0, s = 0, m_pred = 0;
+    double h = 0, cc = 0, gamma = 0, tol = 0;
+    std::vector<double> dd;
+  } cx_plan;
   // launch accounting and optional per-launch timing of the Newton kernel
   int launches = 0;
   bool profile = false;
@@ -191,6 +200,7 @@ static void free_operator(ei_ctx* c) {
     a = nullptr;
   }
   c->cx_fmt = -1;
+  c->cx_plan.valid = false;
   c->max_blocks = 0;
   c->kind = KIND_NONE;
   c->cs_valid = false;
@@ -1299,16 +1309,39 @@ static ei_status phi_imag_impl(ei_ctx* c, int k, double h, const void* v, void* 
   const int m_max = (opt && opt->m_max > 0 && opt->m_max <= 100) ? opt->m_max : 100;
   int s = 1, m_pred = 0;
   const bool fixed = opt && opt->fixed_s > 0;
-  if (fixed) s = opt->fixed_s;
-  else if (schedule_imag(k, h, cc, gamma, tol, m_max, &s, &m_pred, nullptr) != 0)
-    return EI_ERR_NOT_CONVERGED;
-  if (st) st->m_sched = m_pred;
+  auto& plan = c->cx_plan;
+  const bool cached = !fixed && plan.valid && plan.k == k && plan.h == h && plan.cc == cc &&
+                      plan.gamma == gamma && plan.tol == tol && plan.m_max == m_max;
   std::vector<double> dd(2 * (m_max + 1)), d(m_max + 1), di(m_max + 1);
+  if (fixed) {
+    s = opt->fixed_s;
+  } else if (cached) {
+    s = plan.s;
+    m_pred = plan.m_pred;
+  } else {
+    if (schedule_imag(k, h, cc, gamma, tol, m_max, &s, &m_pred, dd.data()) != 0)
+      return EI_ERR_NOT_CONVERGED;
+    plan.valid = true;
+    plan.k = k;
+    plan.h = h;
+    plan.cc = cc;
+    plan.gamma = gamma;
+    plan.tol = tol;
+    plan.m_max = m_max;
+    plan.s = s;
+    plan.m_pred = m_pred;
+    plan.dd = dd;
+  }
+  if (st) st->m_sched = m_pred;
   int restarts = 0;
   while (s <= (1 << 20)) {
     if (k >= 1 && s > 1) return EI_ERR_NOT_CONVERGED;  // one substep only for k >= 1
     const double tau = h / s;
-    divided_differences_imag(k, tau, cc, gamma, m_max, dd.data());
+    if (!fixed && plan.valid && plan.k == k && plan.h == h && plan.cc == cc &&
+        plan.gamma == gamma && plan.tol == tol && plan.m_max == m_max && plan.s == s)
+      dd = plan.dd;  // the rule's own divided differences at this s
+    else
+      divided_differences_imag(k, tau, cc, gamma, m_max, dd.data());
     for (int j = 0; j <= m_max; ++j) {
       d[j] = dd[2 * j];
       di[j] = dd[2 * j + 1];
