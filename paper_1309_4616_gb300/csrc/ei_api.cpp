@@ -104,6 +104,15 @@ struct ei_ctx {
     double h = 0, cc = 0, gamma = 0, tol = 0;
     std::vector<double> dd;
   } cx_plan;
+  // the same for the a-priori rule of phi_1 (keyed on h, the interval, tol,
+  // m_max): a fixed A called repeatedly with one h reuses it; a Rosenbrock
+  // step's J moves the interval and misses
+  struct {
+    bool valid = false;
+    int m_max = 0, s = 0, m_pred = 0;
+    double h = 0, cc = 0, gamma = 0, tol = 0;
+    std::vector<double> d;
+  } phi1_plan;
   // launch accounting and optional per-launch timing of the Newton kernel
   int launches = 0;
   bool profile = false;
@@ -201,6 +210,7 @@ static void free_operator(ei_ctx* c) {
   }
   c->cx_fmt = -1;
   c->cx_plan.valid = false;
+  c->phi1_plan.valid = false;
   c->max_blocks = 0;
   c->kind = KIND_NONE;
   c->cs_valid = false;
@@ -767,12 +777,28 @@ static ei_status phi1_substeps(ei_ctx* c, Prepared& P, const void* qc, double h,
   int s = 1, m_pred = 0;
   std::vector<double> d(m_max + 1);
   bool have_d = false;  // the schedule hands back the divided differences of its s
+  auto& plan = c->phi1_plan;
   if (opt && opt->fixed_s > 0) {
     s = opt->fixed_s;
+  } else if (plan.valid && plan.h == h && plan.cc == cc && plan.gamma == gamma &&
+             plan.tol == tol && plan.m_max == m_max) {
+    s = plan.s;  // the same rule on the same interval: its s, estimate and d
+    m_pred = plan.m_pred;
+    d = plan.d;
+    have_d = true;
   } else if (schedule(1, h, cc, gamma, tol, m_max, &s, &m_pred, d.data()) != 0) {
     return EI_ERR_NOT_CONVERGED;
   } else {
     have_d = true;
+    plan.valid = true;
+    plan.h = h;
+    plan.cc = cc;
+    plan.gamma = gamma;
+    plan.tol = tol;
+    plan.m_max = m_max;
+    plan.s = s;
+    plan.m_pred = m_pred;
+    plan.d = d;
   }
   if (st) st->m_sched = m_pred;
   int restarts = 0, matvecs = 0;
