@@ -214,6 +214,10 @@ ei_status ei_estimate_spectrum_stencil_noalloc(int device, void* cuda_stream, in
  * of tau^j phi_j (two Newton runs; stats.degrees sums them per substep).
  * tol: relative stop tolerance of the a-posteriori estimate
  *   |d_{j+1}| ||w_{j+1}||_2 <= tol ||p_{j+1}||_2, per substep.
+ * k = 1 with the a-priori rule: the context keeps the rule's last plan (s, its
+ * degree estimate, the divided differences at h/s) and reuses it for a call
+ * with the same h, tol and m_max on the same interval (bit-identical results;
+ * only host time is saved).  Setting an operator clears it.
  * opt may be NULL (defaults).  stats may be NULL. */
 ei_status ei_phi_apply(ei_ctx* ctx, int k, double h, const void* v, void* out, double tol,
                        const ei_options* opt, ei_stats* stats);
@@ -233,6 +237,9 @@ ei_status ei_phi_apply(ei_ctx* ctx, int k, double h, const void* v, void* out, d
  *     k >= 1 (k <= 8): one substep, s = 1.
  *   tol: per-substep stop rule |d_{j+1}| ||w_{j+1}||_2 <= tol ||p_{j+1}||_2
  *     with |d| the complex modulus and 2-norms over both parts.
+ * The context keeps the last plan (s, the degree estimate, the divided
+ * differences) and reuses it for a call with the same k, h, tol and m_max:
+ * bit-identical results, less host time.  Setting an operator clears it.
  * Only the operator's symmetry is assumed, not checked: for a non-symmetric
  * operator the interval does not bound the spectrum and the result is not
  * phi_k(-i h H) v.
