@@ -74,16 +74,21 @@ def test_propagator_substeps(xi):
     assert np.linalg.norm(y - ex) / np.linalg.norm(ex) <= 1e-8
 
 
-def test_phi1_against_augmented_matrix(xi):
+@pytest.mark.parametrize("k", [1, 2, 3, 4])
+def test_phik_against_augmented_matrix(xi, k):
+    """phi_k(-ihH)v is the top-right column of exp([[-ihH, v e_1^T], [0, J_k]]),
+    J_k the k x k shift (ones above the diagonal)."""
     op = _chain(30, 6)
     n = 30
     v = np.random.default_rng(7).standard_normal(n) + 0.5j
     h = 0.8
-    y, s, _ = S.phi_apply_imag(op, 1, h, v, 1e-12, xi=xi)
-    M = np.zeros((n + 1, n + 1), dtype=complex)
+    y, s, _ = S.phi_apply_imag(op, k, h, v, 1e-12, xi=xi)
+    M = np.zeros((n + k, n + k), dtype=complex)
     M[:n, :n] = -1j * h * op.dense()
     M[:n, n] = v
-    ex = scipy.linalg.expm(M)[:n, n]
+    for i in range(k - 1):
+        M[n + i, n + i + 1] = 1.0
+    ex = scipy.linalg.expm(M)[:n, n + k - 1]
     assert s == 1 and np.linalg.norm(y - ex) / np.linalg.norm(ex) <= 1e-10
 
 
