@@ -106,3 +106,29 @@ def test_divided_differences_imag_match_oracle(ei, k, tau, c, gamma):
 def test_schedule_imag_matches_oracle(ei, k, h, c, gamma, tol):
     xi = L.leja_points(100)
     assert ei.schedule_imag(k, h, c, gamma, tol) == S.schedule_imag(k, h, c, gamma, tol, xi)
+
+
+def test_imag_host_entries_invalid_arguments(ei):
+    """ei_divided_differences_imag / ei_schedule_imag refuse what the header
+    rules out: k outside 0..8, m or m_max outside range, non-positive tau, h
+    or tol, gamma <= 0 for the schedule, non-finite c."""
+    bad_dd = [(9, 1.0, 0.0, 1.0, 10), (-1, 1.0, 0.0, 1.0, 10), (0, 0.0, 0.0, 1.0, 10),
+              (0, 1.0, float("nan"), 1.0, 10), (0, 1.0, 0.0, -1.0, 10), (0, 1.0, 0.0, 1.0, 101)]
+    for k, tau, c, g, m in bad_dd:
+        with pytest.raises(ei.EIError) as e:
+            ei.divided_differences_imag(k, tau, c, g, m)
+        assert e.value.status == ei.ERR_INVALID_ARG
+    bad_s = [(0, -1.0, 0.0, 1.0, 1e-8), (0, 1.0, 0.0, 0.0, 1e-8), (0, 1.0, 0.0, 1.0, 0.0),
+             (9, 1.0, 0.0, 1.0, 1e-8), (0, 1.0, float("inf"), 1.0, 1e-8)]
+    for k, h, c, g, tol in bad_s:
+        with pytest.raises(ei.EIError) as e:
+            ei.schedule_imag(k, h, c, g, tol)
+        assert e.value.status == ei.ERR_INVALID_ARG
+    with pytest.raises(ei.EIError) as e:
+        ei.schedule_imag(0, 1.0, 0.0, 1.0, 1e-8, m_max=0)
+    assert e.value.status == ei.ERR_INVALID_ARG
+    # gamma = 0 is a valid degenerate interval for the divided differences:
+    # f is constant in xi, so d_0 = phi_k(-i tau c) and the rest vanish
+    d = ei.divided_differences_imag(0, 2.0, 0.7, 0.0, 5)
+    assert d[0] == pytest.approx(np.exp(-1j * 1.4), abs=1e-15)
+    assert np.abs(d[1:]).max() == 0.0
