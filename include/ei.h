@@ -85,8 +85,10 @@ typedef struct {
   int fixed_s;    /* > 0: use this substep count instead of the a-priori rule */
   int profile;    /* 1: time every Newton-iteration launch with CUDA events on the
                      context's stream (stats.newton_ms / newton_timed) */
-  int single_iter; /* 1: one Newton iteration per kernel launch (by default stencils
-                      in the F64 formats fuse two iterations per launch) */
+  int single_iter; /* Newton iterations per stencil kernel launch: 0 the format's
+                      default (two for float-float and FP32, whose kernels HBM
+                      bounds; one for native FP64, which its FP64 arithmetic
+                      bounds); 1 one; 2 two */
   int tile_rows;   /* batched form: height in rows (1 to 1024) of a strip, the
                       32-column unit of work of one warp; 0 = the autotuner's
                       choice */
@@ -180,20 +182,23 @@ ei_status ei_estimate_spectrum(ei_ctx* ctx, double* alpha, double* beta);
 /* Gershgorin interval of a stencil operator, computed with no device memory
  * allocation at all.  (The paper has no counterpart: this entry exists for
  * callers that must not allocate.)  Callers that cannot call cudaMalloc:
- * code running while its stream is captured into a CUDA graph, real-time or
- * budgeted code that reserves all device memory up front, and hosts whose
- * framework owns the GPU's memory.  The arguments describe the operator
- * exactly as for ei_set_operator_stencil (device arrays or constants); the
- * result equals the ei_estimate_spectrum interval of that operator.  No
- * context is needed.
+ * real-time or budgeted code that reserves all device memory up front (an
+ * allocation there can fail or stall on a device-wide synchronisation), and
+ * hosts whose framework owns the GPU's memory through its own pool allocator.
+ * The arguments describe the operator exactly as for ei_set_operator_stencil
+ * (device arrays or constants); the result equals the ei_estimate_spectrum
+ * interval of that operator.  No context is needed.
  *   device, cuda_stream: where the reduction runs; the caller's current device
  *     is restored before returning.  The call synchronises the stream.
  *   alpha, beta: host outputs.
  * Scratch: a fixed ~256 KB array inside the library, one per GPU that loads
  * the library, held until the process exits.  It bounds the operator to
  * n0*n1*n2 <= 2^27 points (512^3); larger operators return
- * EI_ERR_INVALID_ARG.  The first call on a device looks the array up
- * (cudaGetSymbolAddress) and so should come before any stream capture.
+ * EI_ERR_INVALID_ARG.  The first call on a device looks the array's device
+ * address up (cudaGetSymbolAddress, with that device current) and keeps it
+ * for the life of the process, so that first call should come before any
+ * stream capture; after cudaDeviceReset the kept address is stale, so do not
+ * call this entry point on a device that was reset.
  * Every call shares the array and the call clears its arrival counter first:
  * calls that overlap on the GPU (other streams, other host threads) race and
  * must be serialised by the caller.

@@ -119,7 +119,9 @@ struct ei_ctx {
   int newton_timed = 0;
   double newton_ms = 0.0;
   int newton_fused = 1;
-  bool fuse2 = true;       // two Newton iterations per launch where the kernel allows
+  int fuse = 0;            // Newton iterations per stencil launch: 0 the format's
+                           // default (two for float-float and float, one for native
+                           // FP64), 1 one, 2 two
   int csr_lanes = 0;       // lanes per row of the CSR Newton kernels (0: by row length)
   std::vector<cudaEvent_t> ev;
   // learned schedule: the model (caller-owned), the operator's coefficient
@@ -357,6 +359,15 @@ static cudaError_t op_newton2(ei_ctx* c, Prepared& P, const void* qc, const void
                             c->stream);
 }
 
+// Whether the Newton loop runs two iterations per launch: explicit-coefficient
+// stencils do, except in native FP64 by default, where the FP64 pipe rather
+// than HBM bounds the kernel and the fused kernel's halo recomputation only
+// adds FP64 work (ei_options.single_iter overrides).
+static bool use_pair(const ei_ctx* c, const Prepared& P) {
+  return c->kind == KIND_STENCIL && P.coef7 &&
+         (c->fuse == 2 || (c->fuse != 1 && P.fmt != VF_F64));
+}
+
 // One Newton loop on w_0 = r into P.p.  Returns the degree in *deg; *ok = 0
 // when m_max was reached without meeting tol.
 // With cx (complex run, CSR only): d and cx->d_im are the real and imaginary
@@ -388,8 +399,7 @@ static ei_status newton_loop(ei_ctx* c, Prepared& P, const void* qc, const void*
       c->ev.push_back(e);
     }
   }
-  // explicit-coefficient stencils take two iterations per launch
-  const bool pair = (c->kind == KIND_STENCIL) && P.coef7 && c->fuse2;
+  const bool pair = use_pair(c, P);
   int lj[128];          // first iteration index of each launch
   bool l2[128];         // whether that launch did two iterations
   int j = 0, nl = 0;
@@ -578,7 +588,7 @@ static ei_status newton_fixed(ei_ctx* c, Prepared& P, const void* qc, const void
   s.tol = tol;
   s.m_max = m;
   s.fixed = 1;
-  const bool pair = (c->kind == KIND_STENCIL) && P.coef7 && c->fuse2;
+  const bool pair = use_pair(c, P);
   if (timed)
     while (c->ev.size() < (size_t)(2 * m + 2)) {
       cudaEvent_t e;
@@ -643,7 +653,7 @@ static ei_status phi1_fixed(ei_ctx* c, Prepared& P, const void* qc, double h, do
       c->newton_ms += ms;
       ++c->newton_timed;
     }
-    c->newton_fused = (c->kind == KIND_STENCIL && P.coef7 && c->fuse2) ? 2 : 1;
+    c->newton_fused = use_pair(c, P) ? 2 : 1;
   }
   if (s == 1) {
     *result = P.p;
@@ -1080,7 +1090,7 @@ static void acct_begin(ei_ctx* c, const ei_options* opt) {
   c->newton_ms = 0.0;
   c->newton_fused = 1;
   c->profile = opt && opt->profile;
-  c->fuse2 = !(opt && opt->single_iter);
+  c->fuse = opt ? opt->single_iter : 0;
   c->csr_lanes = opt ? opt->csr_lanes : 0;
 }
 

@@ -96,6 +96,19 @@ __device__ __forceinline__ bool newton_verdict(DevCtl* ctl, const NewtonScalars&
   return false;
 }
 
+// Gershgorin min/max accumulation of one row's bounds.  fmin/fmax drop a NaN
+// operand, so a row with a NaN bound widens the pair to (-inf, +inf) instead:
+// the host's finiteness check of the interval then sees it.
+__device__ __forceinline__ void minmax_row(double& mn, double& mx, double lo, double hi) {
+  if (isnan(lo) || isnan(hi)) {
+    mn = -INFINITY;
+    mx = INFINITY;
+    return;
+  }
+  mn = fmin(mn, lo);
+  mx = fmax(mx, hi);
+}
+
 // loads / stores (read-only path for data the kernel does not write)
 __device__ __forceinline__ df ldg(const df* p, int64_t i) {
   float2 v = __ldg(reinterpret_cast<const float2*>(p) + i);
@@ -118,7 +131,7 @@ __device__ __forceinline__ void st(float* p, int64_t i, float v) { p[i] = v; }
 // 7-point sum diag*wc + sum_k a_k*w_k and the Newton update
 // w' = (A w)*inv_gamma - shift*wc.  Float-float: two lazily normalised
 // accumulators (independent chains for instruction-level parallelism);
-// double/float: plain FMAs in the same order.
+// float: two chains of FMAs; double: one chain.
 __device__ __forceinline__ df stencil7(df dg, df wc, df a0, df w0, df a1, df w1, df a2, df w2,
                                        df a3, df w3, df a4, df w4, df a5, df w5) {
   dfacc s1 = dfa_mul(dg, wc);
@@ -130,16 +143,19 @@ __device__ __forceinline__ df stencil7(df dg, df wc, df a0, df w0, df a1, df w1,
   s1 = dfa_mac(s1, a2, w2);
   return dfa_norm(dfa_add(s1, s2));
 }
+// Native FP64: one chain of a multiply and six FMAs.  The FP64 pipe, not the
+// latency of the chain, bounds these kernels (a GB300 SM retires about two FP64
+// FMA lanes a clock), so the shortest instruction count wins.
 __device__ __forceinline__ double stencil7(double dg, double wc, double a0, double w0, double a1,
                                            double w1, double a2, double w2, double a3, double w3,
                                            double a4, double w4, double a5, double w5) {
-  double s1 = dg * wc, s2 = a3 * w3;
-  s1 = fma(a0, w0, s1);
-  s2 = fma(a4, w4, s2);
-  s1 = fma(a1, w1, s1);
-  s2 = fma(a5, w5, s2);
-  s1 = fma(a2, w2, s1);
-  return s1 + s2;
+  double s = dg * wc;
+  s = fma(a0, w0, s);
+  s = fma(a1, w1, s);
+  s = fma(a2, w2, s);
+  s = fma(a3, w3, s);
+  s = fma(a4, w4, s);
+  return fma(a5, w5, s);
 }
 __device__ __forceinline__ float stencil7(float dg, float wc, float a0, float w0, float a1,
                                           float w1, float a2, float w2, float a3, float w3,

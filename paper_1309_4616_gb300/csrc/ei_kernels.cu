@@ -138,8 +138,7 @@ k_stencil_gershgorin(UserCoef u, double* lo, double* hi, double* partials, DevCt
     stencil_row<U>(u, i, x, y, z, a, diag, rad);
     lo[i] = diag - rad;
     hi[i] = diag + rad;
-    mn = fmin(mn, diag - rad);
-    mx = fmax(mx, diag + rad);
+    minmax_row(mn, mx, diag - rad, diag + rad);
   }
   if (last_block_reduce2<RED_MINMAX>(mn, mx, partials, ctl)) {
     if (threadIdx.x == 0) {
@@ -608,8 +607,7 @@ k_csr_gershgorin(int64_t n, const int64_t* __restrict__ rowptr, const int32_t* _
     }
     lo[i] = d - r;
     hi[i] = d + r;
-    mn = fmin(mn, d - r);
-    mx = fmax(mx, d + r);
+    minmax_row(mn, mx, d - r, d + r);
   }
   if (last_block_reduce2<RED_MINMAX>(mn, mx, partials, ctl)) {
     if (threadIdx.x == 0) {
@@ -645,8 +643,7 @@ k_shifted_minmax(int64_t n, const double* __restrict__ lo, const double* __restr
   for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;
        i += (int64_t)gridDim.x * blockDim.x) {
     const double q = nonlin_slope(nonlin, u[i]);
-    mn = fmin(mn, lo[i] + q);
-    mx = fmax(mx, hi[i] + q);
+    minmax_row(mn, mx, lo[i] + q, hi[i] + q);
   }
   if (last_block_reduce2<RED_MINMAX>(mn, mx, partials, ctl)) {
     if (threadIdx.x == 0) {
@@ -1235,16 +1232,17 @@ cudaError_t launch_zero(void* x, int fmt, int64_t n, cudaStream_t stm) {
 // ===========================================================================
 // Spectral interval without device allocation
 // ===========================================================================
-// Some callers may not allocate device memory at all: code that runs while a
-// stream is being captured into a CUDA graph (an allocation there breaks the
-// capture), real-time loops and device-memory budgets in which every byte is
-// reserved up front, and hosts whose framework owns all of the GPU's memory.
-// ei_estimate_spectrum_stencil_noalloc serves them: it computes the Gershgorin
-// interval of a stencil operator straight from the caller's coefficient
-// arrays, with its reduction scratch (one pair of doubles per block and the
-// arrival counter) in the fixed array below instead of memory from
-// cudaMalloc.  The array exists once per GPU that loads the library and stays
-// there until the process exits.
+// Some callers may not allocate device memory at all: real-time loops and
+// device-memory budgets in which every byte is reserved up front (a
+// cudaMalloc there can fail, or stall while the driver synchronises the
+// device), and hosts whose framework owns all of the GPU's memory through its
+// own pool allocator (memory from cudaMalloc is invisible to that pool and can
+// push it past its limit).  ei_estimate_spectrum_stencil_noalloc serves them:
+// it computes the Gershgorin interval of a stencil operator straight from the
+// caller's coefficient arrays, with its reduction scratch (the arrival counter
+// and one pair of doubles per block) in the fixed array below instead of
+// memory from cudaMalloc.  The array exists once per GPU that loads the
+// library and stays there until the process exits.
 namespace ei {
 
 static constexpr int kNoallocChunk = 8192;       // grid points per block (256 threads x 32)
@@ -1253,6 +1251,8 @@ static constexpr int kNoallocMaxDevices = 64;
 static constexpr size_t kNoallocBytes = 256 + sizeof(double) * 2 * kNoallocMaxBlocks;
 
 static __device__ __align__(256) unsigned char g_noalloc_scratch[kNoallocBytes];
+// the control block occupies the first 256 bytes, the block partials follow
+static_assert(sizeof(DevCtl) <= 256, "DevCtl must fit the scratch header");
 
 // The Gershgorin row kernel with a fixed chunk of points per block; the
 // control block sits at the start of the scratch, the block partials after it.
@@ -1270,8 +1270,7 @@ __global__ void __launch_bounds__(EI_TPB) k_stencil_gershgorin_chunk(UserCoef u,
     const int z = (int)(i / ((int64_t)u.nx * u.ny));
     double a[6], diag, rad;
     stencil_row<U>(u, i, x, y, z, a, diag, rad);
-    mn = fmin(mn, diag - rad);
-    mx = fmax(mx, diag + rad);
+    minmax_row(mn, mx, diag - rad, diag + rad);
   }
   if (last_block_reduce2<RED_MINMAX>(mn, mx, partials, ctl)) {
     if (threadIdx.x == 0) {
@@ -1282,7 +1281,10 @@ __global__ void __launch_bounds__(EI_TPB) k_stencil_gershgorin_chunk(UserCoef u,
 }
 
 // Device address of the scratch array, looked up once per device (with that
-// device current) and cached.
+// device current, by the first call on it) and cached for the life of the
+// process.  The cache is not invalidated: after cudaDeviceReset the address
+// may no longer be valid, so a process that resets a device must not call the
+// entry point on that device again.
 static void* noalloc_scratch(int device, cudaError_t* err) {
   static std::mutex mu;
   static void* addr[kNoallocMaxDevices] = {nullptr};

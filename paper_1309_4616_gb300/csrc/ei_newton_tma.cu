@@ -13,9 +13,9 @@
 // issues cp.async.bulk.tensor loads of the w tile with its x/y halo (x start
 // rounded down to a 16-byte boundary), the coefficient tiles and the p tile
 // into two rings: the w tiles (planes z-1, z, z+1 are read while plane z is
-// computed) and the coefficient and p tiles (plane z only).  Four planes are in
-// flight ahead of the one being computed; an mbarrier per plane carries the
-// transaction bytes of all its copies.  Halo columns and planes outside the grid arrive as zeros (TMA
+// computed) and the coefficient and p tiles (plane z only).  Four planes (two
+// for native FP64) are in flight ahead of the one being computed; an mbarrier
+// per plane carries the transaction bytes of all its copies.  Halo columns and planes outside the grid arrive as zeros (TMA
 // out-of-bounds fill); with the explicit-coefficient layout every coefficient
 // that would touch them is zero, so no boundary branches are needed.
 //
@@ -35,7 +35,11 @@ struct TmaCfg {
   using T = typename VT<FMT>::T;
   using P = typename VT<FMT>::P;
   static constexpr int TX = 32, TY = 8;
-  static constexpr int PF = 4;          // planes in flight ahead of the one computed
+  // planes in flight ahead of the one computed.  Native FP64 is bound by its
+  // arithmetic rather than by HBM: a shallower ring lets more blocks share an
+  // SM and keep its FP64 pipe busy across the per-plane barriers.
+  static constexpr int PF = FMT == VF_F64 ? 2 : 4;
+  static constexpr int MINB = FMT == VF_F64 ? 3 : 2;  // resident blocks per SM
   static constexpr int NW = PF + 2;     // w ring: planes z-1, z, z+1 resident + PF in flight
   static constexpr int NC = PF + 1;     // coefficient/p ring: plane z resident + PF in flight
   static constexpr int NBAR = 8;        // one mbarrier per plane, reused every 8 planes
@@ -112,7 +116,7 @@ __device__ __forceinline__ bool mbar_wait_bounded(uint32_t bar, uint32_t parity,
 static constexpr uint64_t kWaitLimitNs = 500000000ull;  // 0.5 s; a plane lands in microseconds
 
 template <int FMT>
-__global__ void __launch_bounds__(256, 2)
+__global__ void __launch_bounds__(256, TmaCfg<FMT>::MINB)
 k_newton_tma(const __grid_constant__ NewtonMaps M, const StencilDev g, const NewtonScalars s,
              void* __restrict__ w_out_, void* __restrict__ p_, double* partials, DevCtl* ctl,
              int zc) {

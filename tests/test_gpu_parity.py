@@ -43,7 +43,7 @@ def _check_stats(st, ost):
 # 2D advection-diffusion on 64 x 64, the small configuration in full
 # --------------------------------------------------------------------------
 @pytest.mark.parametrize("arith", [0, 1])
-@pytest.mark.parametrize("single", [0, 1])
+@pytest.mark.parametrize("single", [0, 1, 2])
 def test_adv_diff_2d_phi1(env, xi, arith, single):
     torch, ei = env
     w = W.adv_diff_2d()
@@ -69,7 +69,7 @@ def _fields_3d(rng, n):
     return D, b
 
 
-@pytest.mark.parametrize("single", [0, 1])
+@pytest.mark.parametrize("single", [0, 1, 2])
 @pytest.mark.parametrize("arith", [0, 1])
 def test_rosenbrock_3d_neumann(env, xi, single, arith):
     torch, ei = env

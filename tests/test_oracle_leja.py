@@ -162,3 +162,71 @@ def test_schedule_paper_range(xi):
     s, m, _ = L.plain_schedule(1, g["h"], -rho / 2, rho / 4, g["tol"], xi)
     mv = g["matvecs_per_step"]
     assert s == 1 and mv / 2.5 <= m <= mv * 2.5
+
+
+def _bary_errors(xi, f_of, m_top):
+    """max over the 2001-point grid G of |f - p_m| for m = 0..m_top, where p_m is
+    the degree-m interpolant of f at xi_0..xi_m evaluated in the barycentric
+    (second) form of Lagrange interpolation: no divided differences involved.
+    Returns the errors and max_G |f|."""
+    g = np.linspace(-2.0, 2.0, 2001)
+    fg = f_of(g)
+    errs = np.empty(m_top + 1)
+    for m in range(m_top + 1):
+        nodes = xi[: m + 1]
+        fn = f_of(nodes)
+        diff = nodes[:, None] - nodes[None, :]
+        np.fill_diagonal(diff, 1.0)
+        w = 1.0 / np.prod(diff, axis=1)
+        dx = g[:, None] - nodes[None, :]
+        hit = dx == 0.0
+        dx[hit] = 1.0
+        t = w[None, :] / dx
+        p = (t @ fn) / t.sum(axis=1)
+        rows, cols = np.nonzero(hit)
+        p[rows] = fn[cols]
+        errs[m] = np.max(np.abs(p - fg))
+    return errs, float(np.max(np.abs(fg)))
+
+
+def _phi_np(k):
+    # phi_0 = exp, phi_1 = expm1(z)/z with phi_1(0) = 1 (numpy, independent of the oracle)
+    if k == 0:
+        return np.exp
+    def phi1(z):
+        z = np.asarray(z, dtype=np.float64)
+        out = np.ones_like(z)
+        nz = z != 0.0
+        out[nz] = np.expm1(z[nz]) / z[nz]
+        return out
+    return phi1
+
+
+@pytest.mark.parametrize("k,h,c,gamma,tol", [
+    (1, 1e-3, -1690.0, 845.0, 1e-10),      # the 64^2 advection-diffusion interval
+    (1, 2e-3, -5.0e3, 2.5e3, 1e-8),        # h gamma = 5: one substep, a middle degree
+    (1, 1.0, -60.0, 30.0, 1e-10),          # h gamma = 30: close to the single-substep limit
+    (1, 1.0, -400.0, 200.0, 1e-10),        # h gamma = 200: several substeps
+    (0, 1.0, -150.0, 75.0, 1e-6),          # exp, h gamma = 75
+    (1, 1.0, -35.0, 40.0, 1e-8),           # interval reaching into Re z > 0
+    (1, 1.0, -2000.0, 1000.0, 1e-10),      # h gamma = 1000: s = 8, degree near m_max
+    (0, 1.0, -3000.0, 1500.0, 1e-6),       # exp, h gamma = 1500: s = 16
+])
+def test_schedule_meets_its_definition(xi, k, h, c, gamma, tol):
+    # The a-priori rule by its definition, checked with interpolants built
+    # without divided differences: at the returned (s, m) the degree-m
+    # interpolant at the Leja points meets max_G|f - p_m| <= tol max_G|f| for
+    # f(x) = phi_k(tau c + tau gamma x), tau = h/s; degree m-1 does not; and at
+    # s/2 no degree <= 100 does.  Thresholds carry a 1e-6 relative slack for the
+    # two evaluation orders' rounding.
+    s, m, _ = L.plain_schedule(k, h, c, gamma, tol, xi)
+    phi = _phi_np(k)
+    tau = h / s
+    errs, fmax = _bary_errors(xi, lambda x: phi(tau * c + tau * gamma * x), m)
+    assert errs[m] <= tol * fmax * (1 + 1e-6)
+    if m > 0:
+        assert errs[m - 1] > tol * fmax * (1 - 1e-6)
+    if s > 1:
+        tau2 = 2.0 * tau
+        errs2, fmax2 = _bary_errors(xi, lambda x: phi(tau2 * c + tau2 * gamma * x), L.M_MAX)
+        assert errs2.min() > tol * fmax2 * (1 - 1e-6)
