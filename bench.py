@@ -35,16 +35,34 @@ if ROOT not in sys.path:
 WORKLOAD = "adr3d_256_fp64_rosenbrock"
 METRIC = "phi1(hA)v steps/s at stated rel err vs FP64 oracle; matvec HBM GB/s vs peak"
 N_SIDE = 256
-# Newton launch (float-float, explicit coefficients), j > 0, per grid point:
-# w read 8 + w' write 8 + p read 8 + p write 8 + 7 coefficients x 8.  The
-# two-iteration kernel moves the same 88 bytes per launch for two iterations.
+DTYPE_FF = "float-float (FP32 pairs: 48-bit significand, FP32 exponent range)"
+# Newton launch (explicit coefficients, 8-byte formats), j > 0, per grid point
+# as stored: w read 8 + w' write 8 + p read 8 + p write 8 + 7 coefficients x 8.
+# The two-iteration kernel moves the same 88 bytes per launch for two iterations.
 BYTES_PER_POINT = 88
+# Algorithmic bytes per point-iteration of the 256^3 workload as its scope
+# table counts them: w read 8, w' write 8, p read and write 16, and the operator
+# as its inputs (D 8, b 24, u_n for g' 8).  The library stores the seven
+# coefficients instead (BYTES_PER_POINT).
+ALG_BYTES_PER_POINT = 72
+# FP64 flops of one Newton iteration per grid point (a fused multiply-add counts
+# two), on the scaled operator (A - cI)/gamma the native kernel iterates with:
+# the 7-point product (7 multiplies, 6 adds), the shift -xi_j w (1 multiply, 1
+# add), the Newton sum (1 multiply, 1 add) and the two squared norms
+# (2 multiplies, 2 adds).
+FP64_FLOPS_PER_POINT = 21
+# GB300's FP64 peak from unit counts and clocks: the nominal 1.25 TFLOP/s over
+# 152 SMs at 2070 MHz is 4 FP64 flops (two FMA lanes) per SM and clock.
+SMS, FP64_FLOPS_PER_SM_CLK = 152, 4
 # DRAM bytes per grid point of one launch of the two-iteration float-float
 # kernel, from ncu dram__bytes_read.sum + dram__bytes_write.sum on 192^3
 # (profiles/launches_adr3d_256_rosenbrock.md, taken on the current kernel);
 # traffic scales with the points.
 # Valid for the kernel as captured: retake it when the kernel changes.
 PAIR_DRAM_BYTES_PER_POINT = 86.9
+# the same for one launch of the native-FP64 one-iteration kernel, from ncu on
+# 192^3 (profiles/k_newton_tma_double_192cube.md)
+NATIVE_DRAM_BYTES_PER_POINT = 85.97
 # DRAM bytes of one launch of the float-float 2-lane complex CSR kernel on the
 # 21-spin operator (profiles/k_csr_newton_cg_spin_bath_21.md, the current kernel)
 SPIN_DRAM_BYTES_PER_LAUNCH = 1.242e9
@@ -66,7 +84,7 @@ def parse():
     # batch workloads: fixed tile height instead of the autotuner (profiling)
     ap.add_argument("--tile-rows", type=int, default=0, help=argparse.SUPPRESS)
     ap.add_argument("--workload", default="adr3d",
-                    choices=["adr3d", "adr3d_fp32", "rgg_csr", "batch", "batch_fp32",
+                    choices=["adr3d", "adr3d_ff", "adr3d_fp32", "rgg_csr", "batch", "batch_fp32",
                              "adr3d_learned", "adr3d_fp32_learned", "rgg_csr_learned",
                              "batch_learned_fp32", "batch_plain_fp64_loop", "combustion",
                              "combustion_fast", "combustion_nonlin", "heat_dirichlet_data",
@@ -75,6 +93,14 @@ def parse():
                          "adr3d_fp32: 512^3 FP32 exponential Euler; rgg_csr: 2^20-node CSR phi_1")
     ap.add_argument("--no-cpu", action="store_true", help="skip the CPU baseline sample")
     return ap.parse_args()
+
+
+def peaks_sm_mhz():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            return float(json.load(f)["sm_max_mhz"])
+    except Exception:
+        return 2070.0
 
 
 def peaks():
@@ -137,78 +163,60 @@ class ClockSampler:
 
 
 # --------------------------------------------------------------------------
-# CPU oracle: a bounded sample of one step, extrapolated to a full step
+# the reference arm: the oracle on the host cores
 # --------------------------------------------------------------------------
-def oracle_setup(w):
-    from oracle import leja as L
-    from oracle import operators as O
-    return O.StencilOperator(w.n, w.dx, w.D, w.b, bc=w.bc), L.leja_points(100)
-
-
-def oracle_step_sample(w, u, op, xi, n_iter=3):
-    """Times the oracle's parts of one exponential Rosenbrock-Euler step at the
-    full size: F = A u + g(u), the Gershgorin interval of J, the a-priori
-    schedule and divided differences, and n_iter Newton iterations.  A full step
-    is the setup plus m_sched iterations (the a-priori degree).  Returns
-    (seconds per full step, description)."""
-    from oracle import leja as L
-    from oracle import newton as Nw
-    from oracle import operators as O
-
-    t0 = time.perf_counter()
-    g, dg = Nw.nonlinearity(u, Nw.NONLIN_LOGISTIC)
-    F = op.matvec(u) + g
-    J = O.ShiftedOperator(op, dg)
-    alpha, beta = J.gershgorin()
-    c, gamma = 0.5 * (alpha + beta), 0.25 * (beta - alpha)
-    s, m_sched, _ = L.plain_schedule(1, w.h, c, gamma, w.tol, xi)
-    d = L.divided_differences(1, w.h / s, c, gamma, xi)
-    t1 = time.perf_counter()
-    stats = Nw.Stats()
-    wv = F.copy()
-    p = d[0] * wv
-    for j in range(n_iter):
-        wv = J.matvec(wv) / gamma - (c / gamma + xi[j]) * wv
-        stats.matvecs += 1
-        p = p + d[j + 1] * wv
-        abs(d[j + 1]) * float(np.sqrt(np.sum(wv * wv))) <= w.tol * float(np.sqrt(np.sum(p * p)))
-    t2 = time.perf_counter()
-    t_iter = (t2 - t1) / n_iter
-    per_step = (t1 - t0) + s * m_sched * t_iter
-    desc = (f"oracle (numpy/decimal, 1 thread) at {w.n[0]}^3: F + Gershgorin + schedule + "
-            f"divided differences timed in full ({t1 - t0:.2f} s), {n_iter} Newton iterations "
-            f"timed ({t_iter:.2f} s each) and scaled to the a-priori count s*m = {s}*{m_sched}")
-    return per_step, desc
+REF_BUDGET_S = 150.0   # timed whole steps of the reference arm stop here
 
 
 def run_reference(args):
-    """The CPU oracle on bounded samples of the same workload (rank 0 only)."""
+    """The CPU oracle (rank 0 only) on the same workload and trajectory: whole
+    exponential Rosenbrock-Euler steps from u0 with the oracle's step split
+    over all host cores (oracle/slab.py; equal to the serial oracle up to the
+    norms' summation order).  One untimed warm-up step; then K timed whole
+    steps, or as many as fit in REF_BUDGET_S (at least one), stated in the
+    line."""
     rank = int(os.environ.get("RANK", "0"))
     if rank != 0:
         return
+    from oracle import leja as L
+    from oracle import slab as S
     from paper_1309_4616_gb300 import workloads as W
     w = W.adr_3d(n=args.n if args.n is not None else N_SIDE)
+    xi = L.leja_points(100)
+    sop = S.SlabStencil(w.n, w.dx, w.D, w.b, bc=w.bc)
     u = w.u0.copy()
-    op, xi = oracle_setup(w)
-    for _ in range(args.warmup):
-        oracle_step_sample(w, u, op, xi, n_iter=1)
+    t_warm = 0.0
+    if args.warmup > 0:
+        t0 = time.perf_counter()
+        S.exp_rosenbrock_step(sop, u, w.h, w.tol, xi=xi)
+        t_warm = time.perf_counter() - t0
     times = []
-    desc = ""
     t_start = time.perf_counter()
     for _ in range(args.steps):
-        per_step, desc = oracle_step_sample(w, u, op, xi, n_iter=1)
-        times.append(per_step)
+        t0 = time.perf_counter()
+        u, st = S.exp_rosenbrock_step(sop, u, w.h, w.tol, xi=xi)
+        times.append(time.perf_counter() - t0)
+        if time.perf_counter() - t_start + statistics.mean(times) > REF_BUDGET_S:
+            break
     wall = time.perf_counter() - t_start
-    est = statistics.mean(times)
-    value = 1.0 / est
+    sop.close()
+    k = len(times)
+    per_step = sum(times) / k
+    value = 1.0 / per_step
+    cores = S.host_threads()
+    desc = (f"{k} whole steps of the {w.n[0]}^3 exponential Rosenbrock-Euler trajectory from "
+            f"u0 timed in full ({sum(times):.1f} s), oracle split in z-slabs over {cores} host "
+            f"threads; 1 untimed warm-up step ({t_warm:.1f} s)")
     line = {
         "impl": "reference", "metric": METRIC, "value": value, "unit": "steps/s",
-        "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
-        "ms_per_step": est * 1e3, "higher_is_better": True, "scaling": "weak",
+        "n_gpus": args.gpus, "steps": k, "warmup": min(args.warmup, 1),
+        "ms_per_step": per_step * 1e3, "higher_is_better": True, "scaling": "weak",
         "vs_baseline": None, "dtype": "f64", "data": "synthetic",
         "config": {"workload": WORKLOAD, "grid": list(w.n), "h": w.h, "tol": w.tol,
-                   "bc": "neumann", "sample_wall_s": wall},
-        "cpu_baseline": {"value": value, "unit": "steps/s", "cores": 1, "kind": "oracle",
+                   "bc": "neumann", "steps_requested": args.steps,
+                   "warmup_requested": args.warmup, "timed_wall_s": wall,
+                   "nproc": os.cpu_count()},
+        "cpu_baseline": {"value": value, "unit": "steps/s", "cores": cores, "kind": "oracle",
                          "sample": desc},
         "e2e": {"value": value, "unit": "steps/s", "h2d_bytes_per_step": 0,
                 "d2h_bytes_per_step": 0},
@@ -230,11 +238,14 @@ class Workload:
 
 
 class Adr3d(Workload):
-    """256^3 (or --n) FP64 exponential Rosenbrock-Euler, Neumann, logistic g."""
+    """256^3 (or --n) FP64 exponential Rosenbrock-Euler, Neumann, logistic g, in
+    native IEEE double arithmetic (arith = 1).  arith = 0 runs the same step in
+    the float-float format on the FP32 pipes."""
+
+    arith = 1
 
     def __init__(self, torch, ei, W, dev, ctx, n):
         self.name, self.method = WORKLOAD, "exp_rosenbrock_euler"
-        self.dtype = "f64 (float-float pairs on the FP32 pipes)"
         self.ei, self.w = ei, W.adr_3d(n=n)
         w = self.w
         self.npts = n ** 3
@@ -244,25 +255,48 @@ class Adr3d(Workload):
         self.state0 = torch.from_numpy(w.u0).to(dev)
         self.state = self.state0.clone()
         self.host0 = w.u0
-        self.bytes_per_point = BYTES_PER_POINT
+        self.set_arith(self.arith)
         self.config = {"grid": [n] * 3, "h": w.h, "tol": w.tol, "bc": "neumann",
                        "method": self.method}
 
+    def set_arith(self, arith):
+        self.arith = arith
+        self.dtype = "f64" if arith else DTYPE_FF
+        self.bytes_per_point = BYTES_PER_POINT
+
+    def _o(self, opts):
+        o = {"arith": self.arith}
+        o.update(opts or {})
+        return o
+
     def step(self, ctx, opts=None):
         return ctx.step(self.ei.EXP_ROSENBROCK, self.w.h, self.state, self.ei.NONLIN_LOGISTIC,
-                        self.w.tol, opts)
+                        self.w.tol, self._o(opts))
 
     def step_host(self, ctx, host, opts=None):
         return ctx.step_host(self.ei.EXP_ROSENBROCK, self.w.h, host, self.ei.NONLIN_LOGISTIC,
-                             self.w.tol, opts)
+                             self.w.tol, self._o(opts))
 
     def kernel(self, fused):
-        return ("k_newton2_tma<float-float> (two Newton iterations per launch)"
-                if fused == 2 else "k_newton_tma<float-float>")
+        fmt = "double" if self.arith else "float-float"
+        return (f"k_newton2_tma<{fmt}> (two Newton iterations per launch)"
+                if fused == 2 else f"k_newton_tma<{fmt}> (one Newton iteration per launch)")
+
+
+class Adr3dFF(Adr3d):
+    """The headline step in the float-float format (FP32 pipes)."""
+
+    arith = 0
+
+    def __init__(self, torch, ei, W, dev, ctx, n):
+        Adr3d.__init__(self, torch, ei, W, dev, ctx, n)
+        self.name = WORKLOAD + "_float_float"
 
 
 class Adr3dFp32(Adr3d):
     """512^3 reduced-precision form: FP32 vectors and stencil, exponential Euler."""
+
+    arith = 0
 
     def __init__(self, torch, ei, W, dev, ctx, n):
         self.name, self.method = f"adr3d_{n}_fp32_exp_euler", "exp_euler"
@@ -303,11 +337,12 @@ class Combustion3d(Adr3d):
     kernel, at full precision (float-float) or with FP32 fast math."""
 
     fast = False
+    arith = 0
 
     def __init__(self, torch, ei, W, dev, ctx, n):
         kind = "fast" if self.fast else "full"
         self.name, self.method = f"combustion_{n}_fp64_exp_euler_{kind}", "exp_euler"
-        self.dtype = "f64 (float-float pairs on the FP32 pipes)"
+        self.dtype = DTYPE_FF
         self.ei, self.w = ei, W.combustion_3d(n=n)
         w = self.w
         self.npts = n ** 3
@@ -343,12 +378,13 @@ class HeatDirichlet(Adr3d):
     without: homogeneous."""
 
     data = True
+    arith = 0
 
     def __init__(self, torch, ei, W, dev, ctx, n):
         kind = "sin(pi z)exp(-xy)" if self.data else "homogeneous"
         self.name = f"heat_{n}_dirichlet_{'data' if self.data else 'hom'}_exp_euler"
         self.method = "exp_euler"
-        self.dtype = "f64 (float-float pairs on the FP32 pipes)"
+        self.dtype = DTYPE_FF
         self.ei, self.w = ei, W.combustion_3d(n=n)
         w = self.w
         self.npts = n ** 3
@@ -408,7 +444,7 @@ class NonlinEval(Workload):
 
     def __init__(self, torch, ei, W, dev, ctx, n):
         self.name, self.method = f"combustion_nonlinearity_{n}", "g(u) pointwise"
-        self.dtype = "f64 (float-float on the FP32 pipes)"
+        self.dtype = DTYPE_FF
         self.ei, self.torch = ei, torch
         u = W.combustion_field(n)
         self.npts = n ** 3
@@ -473,7 +509,7 @@ class RggCsr(Workload):
 
     def __init__(self, torch, ei, W, dev, ctx, n):
         self.name, self.method = "rgg_2^20_csr_phi1", "phi1"
-        self.dtype = "f64 (float-float pairs on the FP32 pipes)"
+        self.dtype = DTYPE_FF
         self.ei = ei
         g = W.rgg_graph(n=n)
         self.npts = g.n
@@ -514,6 +550,7 @@ class PhiKAdr3d(Adr3d):
     each an e^{tau A} run on the state and a psi run on v), tol 1e-10, FP64."""
 
     k = 2
+    arith = 0
 
     def __init__(self, torch, ei, W, dev, ctx, n):
         Adr3d.__init__(self, torch, ei, W, dev, ctx, n)
@@ -544,7 +581,7 @@ class SpinBath(Workload):
         self.name = f"spin_bath_{n}_propagator" + ("_fp32" if single else "")
         self.method = "exp(-i t H) psi"
         self.dtype = ("f32 (Newton sum float-float)" if single
-                      else "f64 (float-float pairs on the FP32 pipes)")
+                      else DTYPE_FF)
         g = W.spin_bath(n)
         self.npts = g.n
         dt = torch.float32 if single else torch.float64
@@ -614,7 +651,7 @@ class Batch2d(Workload):
         self.name = "batch_1024_2d" + ("_fp32" if self.prec else "_fp64")
         self.method = "phi1 (batched, persistent kernel)"
         self.dtype = "f32 (float-float Newton sum)" if self.prec else \
-            "f64 (float-float pairs on the FP32 pipes)"
+            DTYPE_FF
         self.ei = ei
         probs = W.batch_2d(count=n)
         self.tol = 1e-6 if self.prec else 1e-10
@@ -685,7 +722,7 @@ class Batch2dPlainLoop(Workload):
     def __init__(self, torch, ei, W, dev, ctx, n):
         self.name = "batch_1024_2d_fp64_plain_loop"
         self.method = "phi1 (one ei_phi_apply per problem, a-priori schedule)"
-        self.dtype = "f64 (float-float pairs on the FP32 pipes)"
+        self.dtype = DTYPE_FF
         self.ei = ei
         probs = W.batch_2d(count=n)
         self.tol = 1e-6
@@ -817,7 +854,7 @@ class RggCsrLearned(Learned, RggCsr):
         self.setup_learned(ctx)
 
 
-WORKLOADS = {"adr3d": Adr3d, "adr3d_fp32": Adr3dFp32, "rgg_csr": RggCsr, "batch": Batch2d,
+WORKLOADS = {"adr3d": Adr3d, "adr3d_ff": Adr3dFF, "adr3d_fp32": Adr3dFp32, "rgg_csr": RggCsr, "batch": Batch2d,
              "batch_fp32": Batch2dFp32, "adr3d_learned": Adr3dLearned,
              "adr3d_fp32_learned": Adr3dFp32Learned, "rgg_csr_learned": RggCsrLearned,
              "batch_learned_fp32": Batch2dLearnedFp32, "batch_plain_fp64_loop": Batch2dPlainLoop,
@@ -825,7 +862,7 @@ WORKLOADS = {"adr3d": Adr3d, "adr3d_fp32": Adr3dFp32, "rgg_csr": RggCsr, "batch"
              "combustion_nonlin": NonlinEval, "heat_dirichlet_data": HeatDirichlet,
              "heat_dirichlet_hom": HeatDirichletHom, "phi2_adr3d": PhiKAdr3d,
              "spin_bath": SpinBath, "spin_bath_fp32": SpinBathFp32}
-DEFAULT_N = {"adr3d": N_SIDE, "adr3d_fp32": 512, "rgg_csr": 1 << 20, "batch": 1024,
+DEFAULT_N = {"adr3d": N_SIDE, "adr3d_ff": N_SIDE, "adr3d_fp32": 512, "rgg_csr": 1 << 20, "batch": 1024,
              "batch_fp32": 1024, "adr3d_learned": N_SIDE, "adr3d_fp32_learned": 512,
              "rgg_csr_learned": 1 << 20, "batch_learned_fp32": 1024,
              "batch_plain_fp64_loop": 1024, "combustion": N_SIDE, "combustion_fast": N_SIDE,
@@ -854,6 +891,181 @@ def max_over_ranks(value, dist, device):
     return float(t.item())
 
 
+def timed_steps(wl, ctx, args, torch, dev, stream, dist, local):
+    """W untimed warm-up steps on a copy, then K steps from the initial state
+    between CUDA events on the library's stream, with the clocks sampled
+    during the timed region."""
+    for _ in range(args.warmup):
+        wl.step(ctx)
+    wl.state_reset()
+    torch.cuda.synchronize(dev)
+    if dist is not None:
+        dist.barrier()
+    sampler = ClockSampler(local)
+    sampler.start()
+    time.sleep(0.3)
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    r = {"launches": 0, "matvecs": [], "degrees": [], "learned_flags": [], "learned_kept": None}
+    torch.cuda.synchronize(dev)
+    e0.record(stream)
+    for _ in range(args.steps):
+        st = wl.step(ctx)
+        r["launches"] += st.launches
+        r["matvecs"].append(st.matvecs)
+        r["degrees"].append(st.degree_list())
+        r["learned_flags"].append(int(getattr(st, "learned", 0)))
+        if hasattr(st, "learned_kept"):
+            r["learned_kept"] = st.learned_kept
+    e1.record(stream)
+    torch.cuda.synchronize(dev)
+    r["clocks"] = sampler.stop()
+    r["ms"] = max_over_ranks(e0.elapsed_time(e1), dist, dev)
+    if dist is not None:
+        dist.barrier()
+    # the dominant kernel: per-launch CUDA events around every Newton launch of
+    # two further steps (profile option), same stream, same sizes
+    wl.state_reset()
+    prof_ms, prof_n, fused, prof_bytes = 0.0, 0, 1, 0.0
+    for _ in range(2):
+        st = wl.step(ctx, {"profile": 1})
+        prof_ms += st.newton_ms
+        prof_n += st.newton_timed
+        fused = st.newton_fused
+        prof_bytes += getattr(st, "timed_bytes", 0.0)
+    r.update(prof_ms=prof_ms, prof_n=prof_n, fused=fused, prof_bytes=prof_bytes, last=st)
+    return r
+
+
+def roofline(wl, r, args, npts):
+    """The roofline object of the dominant kernel from the profiled launches."""
+    hbm, peak_kind = peaks()
+    prof_ms, prof_n, fused, prof_bytes, st = (r["prof_ms"], r["prof_n"], r["fused"],
+                                              r["prof_bytes"], r["last"])
+    if prof_n == 0 and hasattr(st, "point_iters"):
+        # batched pass: one persistent launch; algorithmic bytes of all its sweeps
+        # over the measured time per pass
+        avg_launch_s = r["ms"] * 1e-3 / args.steps
+        achieved = wl.bytes_per_point * st.point_iters / avg_launch_s / 1e9
+    elif hasattr(st, "timed_bytes"):
+        # many problems, one launch sequence each: bytes of all timed launches
+        # over their summed time
+        avg_launch_s = prof_ms / max(prof_n, 1) * 1e-3
+        achieved = prof_bytes / max(prof_ms * 1e-3, 1e-12) / 1e9
+    else:
+        avg_launch_s = prof_ms / max(prof_n, 1) * 1e-3
+        achieved = wl.bytes_per_point * npts * fused / avg_launch_s / 1e9
+    traffic = getattr(wl, "traffic_per_launch", None)
+    if isinstance(wl, Adr3d) and wl.dtype == DTYPE_FF and fused == 2:
+        traffic = PAIR_DRAM_BYTES_PER_POINT * npts  # the float-float pair kernel (ncu)
+    out = {"bound": "hbm", "achieved": achieved, "peak": hbm, "unit": "GB/s",
+           "frac": achieved / hbm,
+           "traffic": traffic,
+           "kernel": wl.kernel(fused),
+           "bytes_per_launch": (prof_bytes / max(prof_n, 1)) if prof_bytes
+           else wl.bytes_per_point * npts * fused,
+           "avg_launch_us": avg_launch_s * 1e6, "launches_timed": prof_n,
+           "iterations_per_launch": fused,
+           "us_per_iteration": avg_launch_s * 1e6 / fused,
+           "peak_kind": peak_kind,
+           "paper_gflops": FLOPS_PER_POINT_PAPER * npts * fused / avg_launch_s / 1e9}
+    if type(wl).__name__ in ("Adr3d", "Adr3dFF", "Adr3dLearned"):
+        # the scope's algorithmic bytes (72 per point-iteration: the operator as
+        # its inputs D, b, u_n) against measured HBM; the stored-coefficient
+        # count (88) kept beside it; DRAM bytes from ncu where captured
+        alg = ALG_BYTES_PER_POINT * npts * fused / avg_launch_s / 1e9
+        dram = (PAIR_DRAM_BYTES_PER_POINT if (not wl.arith and fused == 2)
+                else NATIVE_DRAM_BYTES_PER_POINT if (wl.arith and fused == 1) else None)
+        traffic = dram * npts if dram is not None else None
+        hb = {"bound": "hbm", "achieved": alg, "peak": hbm, "unit": "GB/s", "frac": alg / hbm,
+              "traffic": traffic, "bytes_per_point": ALG_BYTES_PER_POINT,
+              "bytes_per_launch": ALG_BYTES_PER_POINT * npts * fused,
+              "bytes_per_launch_stored": BYTES_PER_POINT * npts,
+              "frac_stored": BYTES_PER_POINT * npts / avg_launch_s / 1e9 / hbm,
+              "dram_frac": (traffic / avg_launch_s / 1e9 / hbm) if traffic else None,
+              "peak_kind": peak_kind}
+        if wl.arith:
+            # native FP64: bound by the FP64 pipe (min of the two rooflines)
+            sm_mhz = peaks_sm_mhz()
+            fpk = SMS * FP64_FLOPS_PER_SM_CLK * sm_mhz * 1e6 / 1e12
+            tf = FP64_FLOPS_PER_POINT * npts * fused / avg_launch_s / 1e12
+            t_alu = FP64_FLOPS_PER_POINT * npts * fused / (fpk * 1e12)
+            t_hbm = ALG_BYTES_PER_POINT * npts * fused / (hbm * 1e9)
+            out.update({"bound": "alu" if t_alu >= t_hbm else "hbm", "achieved": tf,
+                        "peak": fpk, "unit": "TFLOP/s", "frac": tf / fpk, "traffic": traffic,
+                        "alu": "FP64 pipe", "flops_per_point": FP64_FLOPS_PER_POINT,
+                        "peak_kind": f"derived: {SMS} SMs x {FP64_FLOPS_PER_SM_CLK} FP64 "
+                                     f"flop/clk x {sm_mhz:.0f} MHz",
+                        "t_alu_us": t_alu * 1e6, "t_hbm_us": t_hbm * 1e6, "hbm": hb})
+        else:
+            out.update(hb)
+            out["kernel"] = wl.kernel(fused)
+            out.update({"avg_launch_us": avg_launch_s * 1e6, "launches_timed": prof_n,
+                        "iterations_per_launch": fused,
+                        "us_per_iteration": avg_launch_s * 1e6 / fused})
+    return out
+
+
+def first_step_state(wl, ctx, torch):
+    """u_1 of one step from u_0 (the first timed step's result) on the host, and
+    the step's stats."""
+    wl.state_reset()
+    st = wl.step(ctx)
+    torch.cuda.synchronize()
+    return wl.state.double().cpu().numpy().reshape(wl.w.u0.shape), st
+
+
+def rel_errors(u1, ref, u0):
+    inc = np.linalg.norm((u1 - u0) - (ref - u0)) / np.linalg.norm(ref - u0)
+    state = np.linalg.norm(u1 - ref) / np.linalg.norm(ref)
+    return float(inc), float(state)
+
+
+def cpu_leg(w, gpu_states, gpu_stats):
+    """The oracle on the host (rank 0, N = 1): one whole step from u_0 with the
+    serial oracle (the cpu_baseline), one with the all-core slab oracle, and the
+    relative error of each GPU form's first step against the serial result."""
+    from oracle import leja as L
+    from oracle import newton as Nw
+    from oracle import operators as O
+    from oracle import slab as S
+
+    xi = L.leja_points(100)
+    op = O.StencilOperator(w.n, w.dx, w.D, w.b, bc=w.bc)
+    t0 = time.perf_counter()
+    ref, ost = Nw.exp_rosenbrock_step(op, w.u0, w.h, w.tol, xi=xi)
+    t_serial = time.perf_counter() - t0
+    del op
+    sop = S.SlabStencil(w.n, w.dx, w.D, w.b, bc=w.bc)
+    t0 = time.perf_counter()
+    ref_s, sst = S.exp_rosenbrock_step(sop, w.u0, w.h, w.tol, xi=xi)
+    t_all = time.perf_counter() - t0
+    sop.close()
+    errs = {}
+    for name, u1 in gpu_states.items():
+        inc, state = rel_errors(u1, ref, w.u0)
+        gst = gpu_stats[name]
+        errs[name] = {"value": inc, "state": state,
+                      "of": "first step from u0, full field: ||du_gpu - du_oracle|| / "
+                            "||du_oracle|| with du = u1 - u0 (state: ||u1 - u1_oracle|| / "
+                            "||u1_oracle||), FP64 oracle",
+                      "bound": 1e-9,
+                      "s_and_degrees_match_oracle": bool(gst.s == ost.s and
+                                                         gst.degree_list() == list(ost.degrees))}
+    slab_agree, _ = rel_errors(ref_s, ref, w.u0)
+    cores = S.host_threads()
+    cpu = {"value": 1.0 / t_serial, "unit": "steps/s", "cores": 1, "kind": "oracle",
+           "sample": (f"one whole exponential Rosenbrock-Euler step of the {w.n[0]}^3 workload "
+                      f"from u0 with the serial oracle (numpy/decimal, 1 thread): {t_serial:.1f} s, "
+                      f"s = {ost.s}, degrees {list(ost.degrees)}"),
+           "nproc": os.cpu_count(),
+           "all_cores": {"value": 1.0 / t_all, "unit": "steps/s", "cores": cores,
+                         "kind": "oracle (z-slabs on host threads, oracle/slab.py)",
+                         "sample": f"the same whole step: {t_all:.1f} s; increment within "
+                                   f"{slab_agree:.1e} of the serial oracle"}}
+    return cpu, errs
+
+
 def run_ours(args):
     import torch
     from paper_1309_4616_gb300 import build, ei
@@ -877,66 +1089,27 @@ def run_ours(args):
     wl = WORKLOADS[args.workload](torch, ei, W, dev, ctx, n)
     npts = wl.npts
 
-    # warm-up on a copy, then the timed steps from the initial state
-    for _ in range(args.warmup):
-        wl.step(ctx)
-    wl.state_reset()
-    torch.cuda.synchronize(dev)
-    if dist is not None:
-        dist.barrier()
-    sampler = ClockSampler(local)
-    sampler.start()
-    time.sleep(0.3)
-    e0 = torch.cuda.Event(enable_timing=True)
-    e1 = torch.cuda.Event(enable_timing=True)
-    launches = 0
-    matvecs = []
-    degrees = []
-    learned_flags = []
-    learned_kept = None
-    torch.cuda.synchronize(dev)
-    e0.record(stream)
-    for _ in range(args.steps):
-        st = wl.step(ctx)
-        launches += st.launches
-        matvecs.append(st.matvecs)
-        degrees.append(st.degree_list())
-        learned_flags.append(int(getattr(st, "learned", 0)))
-        if hasattr(st, "learned_kept"):
-            learned_kept = st.learned_kept
-    e1.record(stream)
-    torch.cuda.synchronize(dev)
-    clocks = sampler.stop()
-    ms = max_over_ranks(e0.elapsed_time(e1), dist, dev)
-    if dist is not None:
-        dist.barrier()
+    r = timed_steps(wl, ctx, args, torch, dev, stream, dist, local)
+    roof = roofline(wl, r, args, npts)
+    ms = r["ms"]
 
-    # roofline of the dominant kernel: per-launch CUDA events around every Newton
-    # launch of two further steps (profile option), same stream, same sizes
-    wl.state_reset()
-    prof_ms, prof_n, fused, prof_bytes = 0.0, 0, 1, 0.0
-    for _ in range(2):
-        st = wl.step(ctx, {"profile": 1})
-        prof_ms += st.newton_ms
-        prof_n += st.newton_timed
-        fused = st.newton_fused
-        prof_bytes += getattr(st, "timed_bytes", 0.0)
-    hbm, peak_kind = peaks()
-    if prof_n == 0 and hasattr(st, "point_iters"):
-        # batched pass: one persistent launch; algorithmic bytes of all its sweeps
-        # over the measured time per pass
-        avg_launch_s = ms * 1e-3 / args.steps
-        achieved = wl.bytes_per_point * st.point_iters / avg_launch_s / 1e9
-    elif hasattr(st, "timed_bytes"):
-        # many problems, one launch sequence each: bytes of all timed launches
-        # over their summed time
-        avg_launch_s = prof_ms / max(prof_n, 1) * 1e-3
-        achieved = prof_bytes / max(prof_ms * 1e-3, 1e-12) / 1e9
-    else:
-        # unit: one point-iteration; a two-iteration launch processes two per point
-        # (its DRAM traffic is about half of that: w_{j+1} stays on chip)
-        avg_launch_s = prof_ms / max(prof_n, 1) * 1e-3
-        achieved = wl.bytes_per_point * npts * fused / avg_launch_s / 1e9
+    # the headline's float-float form: the same steps in the float-float format,
+    # measured the same way on the same context
+    forms = None
+    headline = type(wl) is Adr3d
+    states, stats1 = {}, {}
+    if headline:
+        states["f64"], stats1["f64"] = first_step_state(wl, ctx, torch)
+        wl.set_arith(0)
+        rf = timed_steps(wl, ctx, args, torch, dev, stream, dist, local)
+        states["float_float"], stats1["float_float"] = first_step_state(wl, ctx, torch)
+        froof = roofline(wl, rf, args, npts)
+        forms = {"float_float": {
+            "value": args.steps * world / (rf["ms"] * 1e-3), "unit": "steps/s",
+            "ms_per_step": rf["ms"] / args.steps, "dtype": DTYPE_FF,
+            "matvecs_per_step": rf["matvecs"], "degrees": rf["degrees"][:3],
+            "gpu_launches": rf["launches"], "roofline": froof, "clocks": rf["clocks"]}}
+        wl.set_arith(1)
 
     # e2e through the public API with host buffers: H2D of the state, the step, D2H
     u_host = torch.from_numpy(np.ascontiguousarray(wl.host0).copy()).pin_memory()
@@ -950,12 +1123,10 @@ def run_ours(args):
     torch.cuda.synchronize(dev)
     e2e_s = max_over_ranks(time.perf_counter() - t0, dist, dev)
 
-    cpu = None
-    if rank == 0 and not args.no_cpu and args.workload == "adr3d":
-        op, xi = oracle_setup(wl.w)
-        per_step, desc = oracle_step_sample(wl.w, wl.w.u0.copy(), op, xi)
-        cpu = {"value": 1.0 / per_step, "unit": "steps/s", "cores": 1, "kind": "oracle",
-               "sample": desc}
+    cpu, errs = None, None
+    if rank == 0 and world == 1 and not args.no_cpu and headline:
+        cpu, errs = cpu_leg(wl.w, states, stats1)
+        forms["float_float"]["rel_err"] = errs["float_float"]
 
     if rank == 0:
         steps_total = args.steps * world
@@ -964,35 +1135,27 @@ def run_ours(args):
         config = {"workload": wl.name, **wl.config, "parallelism": f"replicas x{world}",
                   "l2": "inputs larger than L2 (each vector >= 8 MB and the step's working "
                         "set >= 0.3 GB; 256^3: 134 MB per vector)",
-                  "matvecs_per_step": matvecs, "degrees": degrees[:3]}
-        if learned_kept is not None and getattr(wl, "model", None) is not None:
-            config["learned_problems_kept_per_pass"] = learned_kept
-        elif any(learned_flags):
-            config["learned_accepted_steps"] = sum(1 for f in learned_flags if f == 1)
+                  "matvecs_per_step": r["matvecs"], "degrees": r["degrees"][:3]}
+        if r["learned_kept"] is not None and getattr(wl, "model", None) is not None:
+            config["learned_problems_kept_per_pass"] = r["learned_kept"]
+        elif any(r["learned_flags"]):
+            config["learned_accepted_steps"] = sum(1 for f in r["learned_flags"] if f == 1)
         line = {
             "metric": METRIC, "value": value, "unit": "steps/s", "n_gpus": world,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms / args.steps,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
             "dtype": wl.dtype, "data": "synthetic", "config": config,
-            "roofline": {"bound": "hbm", "achieved": achieved, "peak": hbm, "unit": "GB/s",
-                         "frac": achieved / hbm,
-                         "traffic": (PAIR_DRAM_BYTES_PER_POINT * npts
-                                     if isinstance(wl, Adr3d) and fused == 2
-                                     else getattr(wl, "traffic_per_launch", None)),
-                         "kernel": wl.kernel(fused),
-                         "bytes_per_launch": (prof_bytes / max(prof_n, 1)) if prof_bytes
-                         else wl.bytes_per_point * npts * fused,
-                         "avg_launch_us": avg_launch_s * 1e6, "launches_timed": prof_n,
-                         "iterations_per_launch": fused,
-                         "us_per_iteration": avg_launch_s * 1e6 / fused,
-                         "peak_kind": peak_kind,
-                         "paper_gflops": FLOPS_PER_POINT_PAPER * npts * fused / avg_launch_s / 1e9},
+            "roofline": roof,
             "cpu_baseline": cpu,
             "e2e": {"value": k_e2e * world / e2e_s, "unit": "steps/s",
                     "h2d_bytes_per_step": npts * esz, "d2h_bytes_per_step": npts * esz},
-            "gpu_launches": launches,
-            "clocks": clocks,
+            "gpu_launches": r["launches"],
+            "clocks": r["clocks"],
         }
+        if errs is not None:
+            line["rel_err"] = errs["f64"]
+        if forms is not None:
+            line["forms"] = forms
         print(json.dumps(line))
     ctx.close()
     if dist is not None:

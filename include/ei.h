@@ -62,14 +62,25 @@ typedef enum {
 enum { EI_BC_DIRICHLET0 = 0, EI_BC_NEUMANN0 = 1 };
 
 /* Storage/arithmetic precision of vectors and of the matvec.
- *   F64: vectors exchanged as double; inside the library the Newton vectors
- *        are float-float pairs (48-bit significand) on the FP32 pipes.
+ *   F64: vectors exchanged as double; the arithmetic is chosen by
+ *        ei_options.arith (below).
  *   F32: vectors and stencil matvec in float with float accumulation; the
  *        divided differences, the spectral interval and the Newton sum p
  *        (float-float) keep FP64-class precision. */
 enum { EI_PREC_F64 = 0, EI_PREC_F32 = 1 };
 
-/* Arithmetic of the F64 path (ei_options.arith). */
+/* Arithmetic of the F64 path (ei_options.arith).
+ *   EI_ARITH_DF: the Newton vectors, coefficients and sums are float-float
+ *     pairs (hi + lo floats: a 48-bit significand with FP32's exponent range)
+ *     on the FP32 pipes, which GB300 runs far faster than its FP64 pipe.  The
+ *     format matches native FP64 only inside its range, so a call runs in it
+ *     only when the operator's bound rho = max(|alpha|, |beta|) lies in
+ *     [2^-60, 2^60] (or is 0) and the vector it acts on (v, or u for a step)
+ *     has max |x| in [2^-60, 2^50] (or is zero); a step also needs
+ *     max |u| <= 2^20, rho max|u| <= 2^40 and ||A u + g(u)||^2 in
+ *     [2^-60, 2^100].  Any other call runs in native FP64, and
+ *     ei_stats.arith_used says which arithmetic ran.
+ *   EI_ARITH_NATIVE_F64: IEEE double throughout. */
 enum { EI_ARITH_DF = 0, EI_ARITH_NATIVE_F64 = 1 };
 
 enum { EI_EXP_EULER = 0, EI_EXP_ROSENBROCK = 1 };
@@ -130,6 +141,10 @@ typedef struct {
   int learned_pad;
   double features[12];  /* features of the call at the substep count used
                            (options.learned != 0); see ei_mlp below */
+  int arith_used;       /* EI_ARITH_* the Newton iteration ran in (F64 operators;
+                           a float-float call outside the format's range runs
+                           in native FP64) */
+  int pad_end;
 } ei_stats;
 
 /* Create a context on CUDA device `device`, ordering work on `cuda_stream`
@@ -454,6 +469,15 @@ ei_status ei_batch_offsets(const ei_batch* b, int64_t* offsets);
  * after completion. */
 ei_status ei_batch_phi1(ei_batch* b, void* cuda_stream, const void* v, void* out,
                         ei_batch_stats* per_problem);
+/* The persistent kernel's bounded wait: a warp that finds no work to claim
+ * gives up after limit_us microseconds without progress anywhere in the batch
+ * (<= 0: the default, 5 s); ei_batch_phi1 then returns EI_ERR_TIMEOUT.  A
+ * pass never waits on a warp, so a healthy pass only meets a limit far below
+ * its own strips' durations (a test sets one to see the error path).  On a
+ * timeout in the first pass out is left unmodified; in a rerun of restarted
+ * problems out holds the problems that converged in the first pass.  The
+ * next call runs with the new limit (its graph is re-captured). */
+ei_status ei_batch_set_wait_limit(ei_batch* b, int64_t limit_us);
 /* Plan every later ei_batch_phi1 call with the schedule network `model`
  * (NULL: the a-priori rule), in the adaptive mode of ei_options.learned = 1:
  * per problem the network's substep count with the per-substep a posteriori

@@ -1,10 +1,10 @@
-"""The oracle's exponential Rosenbrock-Euler step on all host cores.
+"""The oracle's exponential Euler and Rosenbrock-Euler steps on all host cores.
 
 ORACLE — test infrastructure only (see oracle/__init__.py).
 
-The same method as newton.exp_rosenbrock_step (the Newton form of the Leja
-interpolant, Eq. (3) products, Sec. II-C and III-C; substeps of
-y' = J y + F from 0), with the element-wise work split into z-slabs that host
+The same method as newton.exp_euler_step and newton.exp_rosenbrock_step (the
+Newton form of the Leja interpolant, Eq. (3) products, Sec. II-C and III-C;
+substeps of y' = J y + F from 0), with the element-wise work split into z-slabs that host
 threads process at once (numpy releases the interpreter lock inside its array
 loops).  Each slab keeps an operators.StencilOperator built on the slab
 extended by one plane on each interior side: the rows of the slab's own planes
@@ -76,6 +76,17 @@ def exp_rosenbrock_step(sop: SlabStencil, u, h, tol, nonlin=NONLIN_LOGISTIC, xi=
                         m_max=L.M_MAX):
     """u_{n+1} = u_n + h phi_1(h J_n)(A u_n + g(u_n)), J_n = A + diag(g'(u_n)),
     as newton.exp_rosenbrock_step.  Returns (u_{n+1}, Stats)."""
+    return _step(sop, u, h, tol, nonlin, xi, m_max, rosenbrock=True)
+
+
+def exp_euler_step(sop: SlabStencil, u, h, tol, nonlin=NONLIN_LOGISTIC, xi=None,
+                   m_max=L.M_MAX):
+    """u_{n+1} = u_n + h phi_1(hA)(A u_n + g(u_n)) (Eq. (2)), as
+    newton.exp_euler_step.  Returns (u_{n+1}, Stats)."""
+    return _step(sop, u, h, tol, nonlin, xi, m_max, rosenbrock=False)
+
+
+def _step(sop, u, h, tol, nonlin, xi, m_max, rosenbrock):
     stats = Stats()
     u = np.asarray(u, dtype=np.float64).reshape(sop.shape)
     if xi is None:
@@ -88,7 +99,9 @@ def exp_rosenbrock_step(sop: SlabStencil, u, h, tol, nonlin=NONLIN_LOGISTIC, xi=
         gs, dgs = nonlinearity(u[z0:z1], nonlin)
         g[z0:z1], dg[z0:z1] = gs, dgs
         F[z0:z1] = SlabStencil.own(op.matvec(u[e0:e1]), z0, z1, e0) + gs
-        d = SlabStencil.own(op.diag, z0, z1, e0) + dgs
+        d = SlabStencil.own(op.diag, z0, z1, e0)
+        if rosenbrock:
+            d = d + dgs
         r = SlabStencil.own(op.radius(), z0, z1, e0)
         return float(np.min(d - r)), float(np.max(d + r)), float(np.sum(F[z0:z1] * F[z0:z1]))
 
@@ -107,8 +120,9 @@ def exp_rosenbrock_step(sop: SlabStencil, u, h, tol, nonlin=NONLIN_LOGISTIC, xi=
         return u + h * L.phi_scalar(1, h * c) * F, stats
 
     def jmatvec_into(src, dst, i, z0, z1, e0, e1, op):
-        # (J x) on the slab's own planes: A x + g'(u) x
-        dst[z0:z1] = SlabStencil.own(op.matvec(src[e0:e1]), z0, z1, e0) + dg[z0:z1] * src[z0:z1]
+        # (J x) on the slab's own planes: A x + g'(u) x (Rosenbrock) or A x
+        ax = SlabStencil.own(op.matvec(src[e0:e1]), z0, z1, e0)
+        dst[z0:z1] = ax + dg[z0:z1] * src[z0:z1] if rosenbrock else ax
 
     s, stats.m_sched, _ = L.plain_schedule(1, h, c, gamma, tol, xi, m_max)
     while s <= L.S_MAX:

@@ -57,6 +57,16 @@ struct Prepared {
   CUtensorMap map_in2[4];  // the same with a two-point halo (two-iteration kernel)
   CUtensorMap map_c[6];    // a[0..5]
   CUtensorMap map_diagA, map_qc, map_p;
+  // native FP64 stencils: the scaled operator (J - cI)/gamma of the current
+  // Newton loop (a[0..5]/gamma, (diag - c)/gamma), keyed on the diagonal array,
+  // its content version and (c, gamma)
+  void* sa[7] = {nullptr, nullptr, nullptr, nullptr, nullptr, nullptr, nullptr};
+  CUtensorMap map_s[7];
+  bool pre_valid = false;
+  const void* pre_diag = nullptr;
+  unsigned pre_ver = 0;
+  double pre_cc = 0.0, pre_gamma = 0.0;
+  unsigned qc_ver = 0;     // bumped whenever qc is rewritten (each Rosenbrock step)
 };
 
 struct ei_ctx {
@@ -179,11 +189,13 @@ static int vec_fmt_for(const ei_ctx* c, const ei_options* opt) {
 static void free_prepared(Prepared& p) {
   void** arrs[] = {&p.cbase, &p.qc,   &p.w[0], &p.w[1], &p.p,    &p.y,    &p.r,
                    &p.v,     &p.u,    &p.csr_val, &p.a[0], &p.a[1], &p.a[2], &p.a[3],
-                   &p.a[4],  &p.a[5], &p.diagA};
+                   &p.a[4],  &p.a[5], &p.diagA, &p.sa[0], &p.sa[1], &p.sa[2], &p.sa[3],
+                   &p.sa[4], &p.sa[5], &p.sa[6]};
   for (void** a : arrs) {
     if (*a) cudaFree(*a);
     *a = nullptr;
   }
+  p.pre_valid = false;
   p.ready = false;
   p.coef7 = false;  // a later operator of another kind must not inherit the layout
   p.n_alloc = 0;
@@ -268,6 +280,11 @@ static ei_status prepare(ei_ctx* c, int fmt) {
     for (int i = 0; i < 4; ++i) ok = ok && encode_map(&P.map_in2[i], ins[i], eb, c->sd, 2);
     for (int k = 0; k < 6; ++k) ok = ok && encode_map(&P.map_c[k], P.a[k], eb, c->sd, 0);
     ok = ok && encode_map(&P.map_diagA, P.diagA, eb, c->sd, 0);
+    if (fmt == VF_F64) {  // the scaled operator of the one-iteration native kernel
+      for (int k = 0; k < 7; ++k)
+        if ((s = take(&P.sa[k], vb)) != EI_OK) { free_prepared(P); return s; }
+      for (int k = 0; k < 7; ++k) ok = ok && encode_map(&P.map_s[k], P.sa[k], eb, c->sd, 0);
+    }
     ok = ok && encode_map(&P.map_qc, P.qc, eb, c->sd, 0);
     ok = ok && encode_map(&P.map_p, P.p, 8, c->sd, 0);
     if (!ok) { free_prepared(P); return EI_ERR_CUDA; }
@@ -320,8 +337,34 @@ static cudaError_t op_residual(ei_ctx* c, Prepared& P, const void* qc, const voi
   return launch_csr_residual(csr_view(c, P, qc), y, v, r, P.fmt, c->partials, c->ctl, c->stream);
 }
 
+// Whether the scaled operator in P.sa was made for the diagonal array qc as it
+// is now (the caller also keys it on c and gamma: ensure_prescaled).
+static bool prescaled_for(const Prepared& P, const void* qc) {
+  return P.pre_valid && P.pre_diag == qc && (qc != P.qc || P.pre_ver == P.qc_ver);
+}
+
+// Native FP64 one-iteration Newton loops run on the scaled operator
+// (J - cI)/gamma: one elementwise pass per interval saves a multiply per point
+// in every iteration of the FP64-bound kernel.
+static bool wants_prescale(const ei_ctx* c, const Prepared& P) {
+  return c->kind == KIND_STENCIL && P.fmt == VF_F64 && P.sa[0] != nullptr;
+}
+static ei_status ensure_prescaled(ei_ctx* c, Prepared& P, const void* qc, double cc,
+                                  double gamma) {
+  if (prescaled_for(P, qc) && P.pre_cc == cc && P.pre_gamma == gamma) return EI_OK;
+  EI_LAUNCH(launch_prescale(P.sa, P.a, qc, P.n_alloc, cc, 1.0 / gamma, c->stream));
+  P.pre_valid = true;
+  P.pre_diag = qc;
+  P.pre_ver = P.qc_ver;
+  P.pre_cc = cc;
+  P.pre_gamma = gamma;
+  return EI_OK;
+}
+
+// pre: run on the scaled operator that ensure_prescaled made current for this
+// loop (native FP64 stencils)
 static cudaError_t op_newton(ei_ctx* c, Prepared& P, const void* qc, const void* w_in,
-                             void* w_out, const NewtonScalars& s) {
+                             void* w_out, const NewtonScalars& s, bool pre = false) {
   ++c->launches;
   if (c->kind == KIND_STENCIL) {
     NewtonMaps M;
@@ -331,11 +374,12 @@ static cudaError_t op_newton(ei_ctx* c, Prepared& P, const void* qc, const void*
       if (ins[i] == w_in) wi = i;
     if (wi < 0) return cudaErrorInvalidValue;
     M.w = P.map_in[wi];
-    for (int k = 0; k < 6; ++k) M.c[k] = P.map_c[k];
-    M.c[6] = (qc == P.qc) ? P.map_qc : P.map_diagA;
+    pre = pre && prescaled_for(P, qc);
+    for (int k = 0; k < 6; ++k) M.c[k] = pre ? P.map_s[k] : P.map_c[k];
+    M.c[6] = pre ? P.map_s[6] : (qc == P.qc) ? P.map_qc : P.map_diagA;
     M.p = P.map_p;
     return launch_newton_tma(stencil_view(c, P, qc), M, w_out, P.p, s, P.fmt, c->partials,
-                             c->ctl, c->stream);
+                             c->ctl, c->stream, pre);
   }
   return launch_csr_newton(csr_view(c, P, qc), c->nnz, c->csr_lanes, w_in, w_out, P.p, s, P.fmt,
                            c->partials, c->ctl,
@@ -400,6 +444,8 @@ static ei_status newton_loop(ei_ctx* c, Prepared& P, const void* qc, const void*
     }
   }
   const bool pair = use_pair(c, P);
+  const bool pre = !pair && !cx && wants_prescale(c, P);
+  if (pre) EI_TRY(ensure_prescaled(c, P, qc, cc, gamma));
   int lj[128];          // first iteration index of each launch
   bool l2[128];         // whether that launch did two iterations
   int j = 0, nl = 0;
@@ -411,6 +457,7 @@ static ei_status newton_loop(ei_ctx* c, Prepared& P, const void* qc, const void*
       s.j = j;
       s.d_next = d[j + 1];
       s.shift = cc / gamma + xi[j];
+      s.xi = xi[j];
       if (two) {
         s.d_next2 = d[j + 2];
         s.shift2 = cc / gamma + xi[j + 1];
@@ -426,7 +473,7 @@ static ei_status newton_loop(ei_ctx* c, Prepared& P, const void* qc, const void*
       } else if (two) {
         EI_TRY_CUDA(op_newton2(c, P, qc, w_in, w_out, s));
       } else {
-        EI_TRY_CUDA(op_newton(c, P, qc, w_in, w_out, s));
+        EI_TRY_CUDA(op_newton(c, P, qc, w_in, w_out, s, pre));
       }
       if (c->profile) EI_TRY_CUDA(cudaEventRecord(c->ev[2 * nl + 1], c->stream));
       lj[nl] = j;
@@ -472,6 +519,40 @@ static void interval(double alpha, double beta, double* cc, double* gamma) {
 
 static void stats_reset(ei_stats* st) {
   if (st) memset(st, 0, sizeof(*st));
+}
+
+// The float-float format carries 48 significand bits over FP32's exponent
+// range, so it matches native FP64 only inside that range.  A float-float
+// call runs there when the operator's spectral bound rho = max(|alpha|, |beta|)
+// lies in [2^-60, 2^60] (or is 0) and the vector it acts on has
+// max |x| in [2^-60, 2^50] (or is zero): every coefficient, iterate and
+// squared-norm partial then stays inside FP32's exponents, and entries that
+// underflow (below 2^-126) lie at least 2^-66 below the largest, far under the
+// 1e-9 bound of the results.  Outside it the call runs in native FP64.
+static bool df_rho_ok(double alpha, double beta) {
+  const double rho = fmax(fabs(alpha), fabs(beta));
+  return rho == 0.0 || (rho >= 0x1p-60 && rho <= 0x1p60);
+}
+static bool df_vec_ok(double vmax) {
+  return vmax == 0.0 || (vmax >= 0x1p-60 && vmax <= 0x1p50);
+}
+// A step forms F = A u + g(u) in the format as well: u's largest magnitude U
+// stays at or below 2^20 (so g(u) <= 2^41), rho U <= 2^40, and the squared
+// norm of F, as the format computed it, lies in [2^-60, 2^100] (a zero or a
+// smaller value may be an underflow: the step then reruns in native FP64,
+// which also settles an exact equilibrium).
+static bool df_step_ok(double alpha, double beta, double umax, double fnorm2) {
+  const double rho = fmax(fabs(alpha), fabs(beta));
+  return df_rho_ok(alpha, beta) && umax <= 0x1p20 && rho * umax <= 0x1p40 &&
+         fnorm2 >= 0x1p-60 && fnorm2 <= 0x1p100;
+}
+// options of a call rerun in native FP64
+static ei_options native_opts(const ei_options* opt) {
+  ei_options o;
+  if (opt) o = *opt;
+  else memset(&o, 0, sizeof(o));
+  o.arith = EI_ARITH_NATIVE_F64;
+  return o;
 }
 
 // ===========================================================================
@@ -589,6 +670,8 @@ static ei_status newton_fixed(ei_ctx* c, Prepared& P, const void* qc, const void
   s.m_max = m;
   s.fixed = 1;
   const bool pair = use_pair(c, P);
+  const bool pre = !pair && wants_prescale(c, P);
+  if (pre) EI_TRY(ensure_prescaled(c, P, qc, cc, gamma));
   if (timed)
     while (c->ev.size() < (size_t)(2 * m + 2)) {
       cudaEvent_t e;
@@ -601,6 +684,7 @@ static ei_status newton_fixed(ei_ctx* c, Prepared& P, const void* qc, const void
     s.j = j;
     s.d_next = d[j + 1];
     s.shift = cc / gamma + xi[j];
+    s.xi = xi[j];
     if (two) {
       s.d_next2 = d[j + 2];
       s.shift2 = cc / gamma + xi[j + 1];
@@ -611,7 +695,7 @@ static ei_status newton_fixed(ei_ctx* c, Prepared& P, const void* qc, const void
     if (two) {
       EI_TRY_CUDA(op_newton2(c, P, qc, w_in, w_out, s));
     } else {
-      EI_TRY_CUDA(op_newton(c, P, qc, w_in, w_out, s));
+      EI_TRY_CUDA(op_newton(c, P, qc, w_in, w_out, s, pre));
     }
     if (timed) EI_TRY_CUDA(cudaEventRecord(c->ev[2 * nl + 1], c->stream));
     ++nl;
@@ -1212,9 +1296,16 @@ static ei_status phi_apply_impl(ei_ctx* c, int k, double h, const void* v, void*
   EI_LAUNCH(launch_import(P.v, fmt, v, c->prec, n, geo_nx(c), c->kind == KIND_STENCIL ? c->sd.ny : 1, geo_pitch(c), c->partials, c->ctl,
                          c->stream));
   EI_TRY(read_ctl(c));
+  const double alpha = c->alphaA, beta = c->betaA;
+  // outside the float-float range (where the format's own squared norm may
+  // have overflowed): the native FP64 call, which also checks finiteness
+  if (fmt == VF_DF && !(df_rho_ok(alpha, beta) && df_vec_ok(c->h_ctl->vmax))) {
+    const ei_options o = native_opts(opt);
+    return phi_apply_impl(c, k, h, v, out, tol, &o, st);
+  }
   if (c->h_ctl->sum1 != 1.0) return EI_ERR_NONFINITE;
   const double vnorm2 = c->h_ctl->sum0;
-  const double alpha = c->alphaA, beta = c->betaA;
+  if (st) st->arith_used = fmt == VF_F64 ? EI_ARITH_NATIVE_F64 : EI_ARITH_DF;
   double cc, gamma;
   interval(alpha, beta, &cc, &gamma);
   if (st) { st->alpha = alpha; st->beta = beta; st->s = 1; }
@@ -1329,9 +1420,16 @@ static ei_status phi_imag_impl(ei_ctx* c, int k, double h, const void* v, void* 
   EI_LAUNCH(launch_import(cv, fmt, v, c->prec, 2 * n, (int)(2 * n), 1, (int)(2 * n), c->partials,
                           c->ctl, c->stream));
   EI_TRY(read_ctl(c));
+  const double alpha = c->alphaA, beta = c->betaA;
+  // outside the float-float range (where the format's own squared norm may
+  // have overflowed): the native FP64 call, which also checks finiteness
+  if (fmt == VF_DF && !(df_rho_ok(alpha, beta) && df_vec_ok(c->h_ctl->vmax))) {
+    const ei_options o = native_opts(opt);
+    return phi_imag_impl(c, k, h, v, out, tol, &o, st);
+  }
   if (c->h_ctl->sum1 != 1.0) return EI_ERR_NONFINITE;
   const double vnorm2 = c->h_ctl->sum0;
-  const double alpha = c->alphaA, beta = c->betaA;
+  if (st) st->arith_used = fmt == VF_F64 ? EI_ARITH_NATIVE_F64 : EI_ARITH_DF;
   double cc, gamma;
   interval(alpha, beta, &cc, &gamma);
   if (st) { st->alpha = alpha; st->beta = beta; st->s = 1; }
@@ -1447,6 +1545,7 @@ static ei_status step_impl(ei_ctx* c, int method, double h, void* u, int nonlin,
     for (int f = 0; f < 6; ++f) bnd.c[f] = c->face_term[f];
     EI_LAUNCH(launch_stencil_F(stencil_view(c, P, base_diag(P)), P.u, P.v, base_diag(P), P.qc,
                                nonlin, rosen, bnd, fmt, c->partials, c->ctl, c->stream));
+    ++P.qc_ver;  // qc now holds this step's J diagonal
   } else {
     EI_LAUNCH(launch_csr_F(csr_view(c, P, P.cbase), P.u, P.v, P.qc, P.cbase, nonlin, rosen,
                              fmt, c->partials, c->ctl, c->stream));
@@ -1455,11 +1554,17 @@ static ei_status step_impl(ei_ctx* c, int method, double h, void* u, int nonlin,
     EI_LAUNCH(launch_shifted_minmax(n, c->ger_lo, c->ger_hi, u, c->prec, nonlin, c->partials,
                                       c->ctl, c->stream));
   EI_TRY(read_ctl(c));
-  if (c->h_ctl->sum1 != 1.0) return EI_ERR_NONFINITE;
-  const double fnorm2 = c->h_ctl->sum0;
   const double alpha = rosen ? c->h_ctl->mn : c->alphaA;
   const double beta = rosen ? c->h_ctl->mx : c->betaA;
+  if (fmt == VF_DF && isfinite(alpha) && isfinite(beta) &&
+      !df_step_ok(alpha, beta, c->h_ctl->vmax, c->h_ctl->sum1 == 1.0 ? c->h_ctl->sum0 : 0.0)) {
+    const ei_options o = native_opts(opt);  // outside the float-float range
+    return step_impl(c, method, h, u, nonlin, tol, &o, st, src, dst);
+  }
+  if (c->h_ctl->sum1 != 1.0) return EI_ERR_NONFINITE;
+  const double fnorm2 = c->h_ctl->sum0;
   if (!isfinite(alpha) || !isfinite(beta)) return EI_ERR_NONFINITE;
+  if (st) st->arith_used = fmt == VF_F64 ? EI_ARITH_NATIVE_F64 : EI_ARITH_DF;
   if (st) { st->alpha = alpha; st->beta = beta; st->s = 1; st->matvecs = 1; }
   if (fnorm2 == 0.0) return EI_OK;  // u is an equilibrium: u_{n+1} = u_n
   double cc, gamma;

@@ -30,8 +30,8 @@
 //   in strip order (deterministic), takes the phase's decision and publishes
 //   the next epoch.
 // No warp waits for another; a warp that finds nothing to claim sleeps
-// briefly, and gives up after 5 s without global progress (status
-// EI_ERR_TIMEOUT).  Data written by other warps in earlier epochs is read
+// briefly, and gives up after 5 s (ei_batch_set_wait_limit) without global
+// progress (status EI_ERR_TIMEOUT; the export then writes nothing).  Data written by other warps in earlier epochs is read
 // through L2 (ld.global.cg).
 #include <cuda_runtime.h>
 #include <math.h>
@@ -107,6 +107,7 @@ struct BatchDev {
   unsigned int* finished;
   unsigned long long* progress;
   int* error;
+  unsigned long long idle_limit_ns;  // an idle warp's no-progress limit
 };
 
 template <class T>
@@ -453,7 +454,7 @@ __global__ void __launch_bounds__(BATCH_THREADS, FMT == VF_F32 ? 7 : 5) k_batch(
     if (k < 0) k = warp_claim(B, gw, t, d);
     if (k < 0) {
       // nothing claimable: finished, failed, or waiting for another warp's
-      // epoch; give up after 5 s without progress anywhere
+      // epoch; give up after B.idle_limit_ns without progress anywhere
       int ex = 0;
       if (lane == 0) {
         if (*(volatile unsigned*)B.finished >= (unsigned)B.count || *(volatile int*)B.error) {
@@ -465,7 +466,7 @@ __global__ void __launch_bounds__(BATCH_THREADS, FMT == VF_F32 ? 7 : 5) k_batch(
           if (pr != seen || idle_t0 == 0) {
             seen = pr;
             idle_t0 = now;
-          } else if (now - idle_t0 > 5000000000ull) {
+          } else if (now - idle_t0 > B.idle_limit_ns) {
             atomicExch(B.error, 1);
           }
           __nanosleep(256);
@@ -554,13 +555,15 @@ __global__ void k_batch_import(const BInst* inst, const int64_t* uoff, const U* 
     st(V, k, from_d<T>((double)src[k]));
 }
 
-// out = phi_1(hA) v: p (s = 1), y/h (s > 1), or scale * v (scalar problems)
+// out = phi_1(hA) v: p (s = 1), y/h (s > 1), or scale * v (scalar problems);
+// nothing when the pass gave up (error set)
 template <int FMT, class U>
 __global__ void k_batch_export(const BInst* inst, const BState* state, const int64_t* uoff,
                                const double* scal, const void* pool, const void* ppool,
-                               U* out) {
+                               U* out, const int* error) {
   using T = typename VT<FMT>::T;
   using P = typename VT<FMT>::P;
+  if (*(volatile const int*)error) return;
   const int i = blockIdx.y;
   const BInst& I = inst[i];
   const T* base = static_cast<const T*>(pool) + I.off;
@@ -619,6 +622,7 @@ struct ei_batch {
   int* error = nullptr;
   int grid = 0;
   cudaGraphExec_t exec = nullptr;
+  unsigned long long idle_limit_ns = 5000000000ull;  // ei_batch_set_wait_limit
   const void* graph_v = nullptr;
   void* graph_out = nullptr;
   int64_t parts_cap = 0;           // partials allocated (doubles)
@@ -769,6 +773,7 @@ static cudaError_t batch_launch_body(ei_batch* B) {
   D.finished = B->finished;
   D.progress = B->progress;
   D.error = B->error;
+  D.idle_limit_ns = B->idle_limit_ns;
   k_batch_init<<<(count + 255) / 256, 256, 0, B->stream>>>(B->order, B->state, B->qword,
                                                            B->avail, B->dinit, count,
                                                            B->finished, B->progress, B->error);
@@ -785,7 +790,8 @@ static cudaError_t batch_io(ei_batch* B, const void* v, void* out, bool import) 
                                                      B->pool);
   else
     k_batch_export<FMT, U><<<g, 256, 0, B->stream>>>(B->inst, B->state, B->duoff, B->dscal,
-                                                     B->pool, B->ppool, static_cast<U*>(out));
+                                                     B->pool, B->ppool, static_cast<U*>(out),
+                                                     B->error);
   return cudaGetLastError();
 }
 
@@ -1282,6 +1288,14 @@ ei_status ei_batch_phi1(ei_batch* B, void* cuda_stream, const void* v, void* out
   BTRY(cudaStreamWaitEvent(us, ev, 0));
   cudaEventDestroy(ev);
   return rc;
+}
+
+ei_status ei_batch_set_wait_limit(ei_batch* B, int64_t limit_us) {
+  if (!B) return EI_ERR_INVALID_ARG;
+  B->idle_limit_ns = limit_us > 0 ? (unsigned long long)limit_us * 1000ull : 5000000000ull;
+  if (B->exec) cudaGraphExecDestroy(B->exec);  // the graph holds the old limit
+  B->exec = nullptr;
+  return EI_OK;
 }
 
 ei_status ei_batch_set_schedule_model(ei_batch* B, const ei_mlp* model) {

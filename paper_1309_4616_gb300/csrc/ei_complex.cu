@@ -322,16 +322,6 @@ k_cexport(U* __restrict__ dst, const Cx<S>* __restrict__ src, int64_t n, double 
   }
 }
 
-static int sm_count() {
-  static int n = 0;
-  if (!n) {
-    int dev = 0;
-    cudaGetDevice(&dev);
-    cudaDeviceGetAttribute(&n, cudaDevAttrMultiProcessorCount, dev);
-    if (n <= 0) n = 1;
-  }
-  return n;
-}
 
 // resident blocks per SM of a kernel variant, from the occupancy calculator
 // once per variant (capped at 8, the reduction partials' capacity per SM)

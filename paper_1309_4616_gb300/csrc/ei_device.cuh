@@ -314,13 +314,18 @@ template <> struct VT<VF_F32> { using T = float; using P = df; };
 // ---------------------------------------------------------------------------
 // block reductions and the last-block pattern
 // ---------------------------------------------------------------------------
-enum { RED_SUM = 0, RED_MINMAX = 1 };
+// RED_SUM: (a, b) summed; RED_MINMAX: min of a, max of b; RED_SUMMAX: a summed,
+// max of b (b >= 0)
+enum { RED_SUM = 0, RED_MINMAX = 1, RED_SUMMAX = 2 };
 
 template <int OP>
 __device__ __forceinline__ void comb(double& a, double& b, double a2, double b2) {
   if (OP == RED_SUM) {
     a += a2;
     b += b2;
+  } else if (OP == RED_SUMMAX) {
+    a += a2;
+    b = fmax(b, b2);
   } else {
     a = fmin(a, a2);
     b = fmax(b, b2);
@@ -347,7 +352,7 @@ __device__ __forceinline__ void block_reduce2(double& a, double& b) {
   __syncthreads();
   const int nw = (nthr + 31) >> 5;
   if (wid == 0) {
-    if (OP == RED_SUM) {
+    if (OP == RED_SUM || OP == RED_SUMMAX) {
       a = lane < nw ? sa[lane] : 0.0;
       b = lane < nw ? sb[lane] : 0.0;
     } else {
@@ -384,7 +389,7 @@ __device__ bool last_block_reduce2(double& a, double& b, double* partials, DevCt
   __syncthreads();
   if (!am_last) return false;
   __threadfence();
-  double ra = (OP == RED_SUM) ? 0.0 : INFINITY, rb = (OP == RED_SUM) ? 0.0 : -INFINITY;
+  double ra = (OP == RED_MINMAX) ? INFINITY : 0.0, rb = (OP == RED_MINMAX) ? -INFINITY : 0.0;
   for (unsigned i = tid; i < nblk; i += nthr) {
     comb<OP>(ra, rb, __ldcg(partials + 2 * i), __ldcg(partials + 2 * i + 1));
   }

@@ -30,6 +30,7 @@ struct DevCtl {
   double mn, mx;       // Gershgorin reductions: min_i (a_ii - r_i), max_i (a_ii + r_i)
   double nw2, np2;     // squared norms of the last Newton iterate / sum
   double cs_sum, cs_max, cs_pe;  // coefficient statistics (launch_coef_stats)
+  double vmax;         // import: largest magnitude of the imported vector (exact)
 };
 
 // Grid geometry of the stencil operator.  Library-owned arrays are stored
@@ -67,6 +68,7 @@ struct NewtonScalars {
                        //    is tested and a failure counts into ctl->fixfail
   double d_next_im;    // complex Newton sum (k_csr_newton_c): Im d_{j+1}
   double d0_im;        //   and Im d_0
+  double xi;           // the Leja point xi_j (kernels on the scaled operator)
 };
 
 // Tensor maps of the TMA-staged Newton kernel (3D maps over the padded
@@ -81,6 +83,8 @@ struct NewtonMaps {
 // ---- launchers (all asynchronous on `st`) ----------------------------------
 int csr_blocks(int64_t n);
 int reduction_capacity();        // block bound of the grid-stride kernels
+int sm_count();                  // SMs of the current device
+// the largest block count any TMA Newton launch on this grid uses
 int newton_tma_blocks(const StencilDev& op);
 
 // tensor maps: encode one 3D map over a padded array (elem 4 or 8 bytes);
@@ -130,7 +134,7 @@ cudaError_t launch_fill_coef(void* dst, int fmt, int64_t n, int nx, int ny, int 
                              const void* src, int src_prec, double cst, double scale,
                              cudaStream_t st);
 // dst (vector format, padded) = src (caller precision, contiguous); squared
-// norm into ctl->sum0, finiteness flag into ctl->sum1.
+// norm into ctl->sum0, finiteness flag into ctl->sum1, max |src| into ctl->vmax.
 // raw (optional): also copy src there, in the caller's precision
 cudaError_t launch_import(void* dst, int fmt, const void* src, int src_prec, int64_t n, int nx,
                           int ny, int pitch, double* partials, DevCtl* ctl, cudaStream_t st,
@@ -176,9 +180,15 @@ cudaError_t launch_csr_residual(const CsrDev& op, const void* y, const void* v, 
 
 // One Newton iteration j: w_out = (J w_in)/gamma - shift w_in; p += d_{j+1} w_out;
 // norms and the device-side stop test.  Skips itself when ctl->done != 0.
+// prescaled (native FP64 only): M.c holds the scaled operator (J - cI)/gamma
+// (launch_prescale) and w_out = M.c-product of w_in - xi_j w_in.
 cudaError_t launch_newton_tma(const StencilDev& op, const NewtonMaps& M, void* w_out, void* p,
                               const NewtonScalars& s, int fmt, double* partials, DevCtl* ctl,
-                              cudaStream_t st);
+                              cudaStream_t st, bool prescaled = false);
+// the scaled operator of the native FP64 Newton kernel, elementwise over the
+// padded arrays: sa[k] = a[k] / gamma (k < 6), sa[6] = (diag - c) / gamma
+cudaError_t launch_prescale(void* const sa[7], const void* const a[6], const void* diag,
+                            int64_t n_alloc, double c, double inv_gamma, cudaStream_t st);
 // Two Newton iterations j+1 and j+2 in one pass (explicit-coefficient stencil,
 // all formats): w_{j+1} is formed on chip over the tile and a one-point
 // halo; only w_{j+2} and p_{j+2} are written.  M.w must be a halo-2 map.

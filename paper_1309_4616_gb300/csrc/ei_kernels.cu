@@ -12,6 +12,7 @@
 #include <stdint.h>
 
 #include <mutex>
+#include <type_traits>
 
 #include "ei.h"
 #include "ei_device.cuh"
@@ -64,6 +65,36 @@ __device__ __forceinline__ void for_points(int64_t n, int nx, int pitch, Fn f) {
     }
   }
 }
+
+// The same walk with K points per thread and pass, the K loads of a pass
+// issued before any of its stores: a warp-wide load of one point per thread
+// moves only 128-256 bytes, and with the grid capped at full occupancy a
+// thread needs several loads in flight to cover HBM latency.  ld(i, j) loads
+// what point i needs (a value or a small struct); body(i, j, v) uses it.  The
+// padded index j of a logical point i is row * pitch + x.
+template <int K, class Ld, class Body>
+__device__ __forceinline__ void for_points_k(int64_t n, int nx, int pitch, Ld ld, Body body) {
+  using V = decltype(ld(int64_t(0), int64_t(0)));
+  const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+  const bool flat = pitch == nx;
+  for (int64_t base = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; base < n;
+       base += K * stride) {
+    V v[K];
+    int64_t jj[K];
+#pragma unroll
+    for (int k = 0; k < K; ++k) {
+      const int64_t i = base + k * stride;
+      jj[k] = flat ? i : (i / nx) * pitch + i % nx;
+      if (i < n) v[k] = ld(i, jj[k]);
+    }
+#pragma unroll
+    for (int k = 0; k < K; ++k) {
+      const int64_t i = base + k * stride;
+      if (i < n) body(i, jj[k], v[k]);
+    }
+  }
+}
+constexpr int EW_K = 4;  // points per thread and pass of the element-wise kernels
 
 // ---------------------------------------------------------------------------
 // one row of the stencil operator in FP64 (shared by the Gershgorin bounds and
@@ -640,11 +671,16 @@ __global__ void __launch_bounds__(EI_TPB)
 k_shifted_minmax(int64_t n, const double* __restrict__ lo, const double* __restrict__ hi,
                  const U* __restrict__ u, int nonlin, double* partials, DevCtl* ctl) {
   double mn = INFINITY, mx = -INFINITY;
-  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;
-       i += (int64_t)gridDim.x * blockDim.x) {
-    const double q = nonlin_slope(nonlin, u[i]);
-    minmax_row(mn, mx, lo[i] + q, hi[i] + q);
-  }
+  struct LHU {
+    double lo, hi;
+    U u;
+  };
+  for_points_k<EW_K>(
+      n, (int)1, (int)1, [&](int64_t i, int64_t) { return LHU{lo[i], hi[i], u[i]}; },
+      [&](int64_t, int64_t, LHU a) {
+        const double q = nonlin_slope(nonlin, a.u);
+        minmax_row(mn, mx, a.lo + q, a.hi + q);
+      });
   if (last_block_reduce2<RED_MINMAX>(mn, mx, partials, ctl)) {
     if (threadIdx.x == 0) {
       ctl->mn = mn;
@@ -675,31 +711,45 @@ k_import(void* dst_, const U* __restrict__ src, int64_t n, int nx, int pitch, U*
          double* partials, DevCtl* ctl) {
   using T = typename VT<FMT>::T;
   T* dst = static_cast<T*>(dst_);
-  double a = 0.0, b = 0.0;
+  double a = 0.0;
+  // max |x| from the IEEE bits with the sign cleared: for non-negative values
+  // the integer order is the value order, and it keeps the FP64 pipe free
+  unsigned long long mbits = 0ull;
+  auto mag = [](U x) -> unsigned long long {
+    if constexpr (sizeof(U) == 8)
+      return (unsigned long long)__double_as_longlong((double)x) & 0x7fffffffffffffffull;
+    else
+      return (unsigned long long)(__float_as_uint((float)x) & 0x7fffffffu);
+  };
+  auto ld = [&](int64_t i, int64_t) { return src[i]; };
   if constexpr (FMT == VF_DF) {
     // the split and the squared norm on the FP32 pipes (the FP64 pipe is slow)
     dfacc acc{0.0f, 0.0f};
-    for_points(n, nx, pitch, [&](int64_t i, int64_t j) {
-      const U x = src[i];
+    for_points_k<EW_K>(n, nx, pitch, ld, [&](int64_t i, int64_t j, U x) {
       if (raw) raw[i] = x;
+      mbits = max(mbits, mag(x));
       const df v = df_split_double((double)x);
       st(dst, j, v);
       acc = dfa_mac(acc, v, v);
     });
     a = acc_d(acc);
   } else {
-    for_points(n, nx, pitch, [&](int64_t i, int64_t j) {
-      const U x = src[i];
+    for_points_k<EW_K>(n, nx, pitch, ld, [&](int64_t i, int64_t j, U x) {
       if (raw) raw[i] = x;
+      mbits = max(mbits, mag(x));
       const double v = (double)x;
       st(dst, j, from_d<T>(v));
       a = fma(v, v, a);
     });
   }
-  if (last_block_reduce2<RED_SUM>(a, b, partials, ctl)) {
+  double b;
+  if constexpr (sizeof(U) == 8) b = __longlong_as_double((long long)mbits);
+  else b = (double)__uint_as_float((unsigned)mbits);
+  if (last_block_reduce2<RED_SUMMAX>(a, b, partials, ctl)) {
     if (threadIdx.x == 0) {
       ctl->sum0 = a;
       ctl->sum1 = finite_d(a) ? 1.0 : 0.0;
+      ctl->vmax = b;
     }
   }
 }
@@ -707,17 +757,25 @@ k_import(void* dst_, const U* __restrict__ src, int64_t n, int nx, int pitch, U*
 template <class S, class U>
 __global__ void k_export(U* dst, const S* __restrict__ src, int64_t n, int nx, int pitch,
                          double scale) {
-  for_points(n, nx, pitch,
-             [&](int64_t i, int64_t j) { dst[i] = (U)(to_d(ldg(src, j)) * scale); });
+  for_points_k<EW_K>(
+      n, nx, pitch, [&](int64_t, int64_t j) { return ldg(src, j); },
+      [&](int64_t i, int64_t, S y) { dst[i] = (U)(to_d(y) * scale); });
 }
 
 // out = u + scale * y (out may be u, or a mapped host buffer)
 template <class S, class U>
+struct AddExportLd {
+  S y;
+  U u;
+};
+template <class S, class U>
 __global__ void k_add_export(U* out, const U* u, const S* __restrict__ y, int64_t n, int nx,
                              int pitch, double scale) {
-  for_points(n, nx, pitch, [&](int64_t i, int64_t j) {
-    out[i] = (U)fma(to_d(ldg(y, j)), scale, (double)u[i]);
-  });
+  for_points_k<EW_K>(
+      n, nx, pitch, [&](int64_t i, int64_t j) { return AddExportLd<S, U>{ldg(y, j), u[i]}; },
+      [&](int64_t i, int64_t, AddExportLd<S, U> v) {
+        out[i] = (U)fma(to_d(v.y), scale, (double)v.u);
+      });
 }
 
 template <int FMT>
@@ -726,14 +784,15 @@ __global__ void k_p_to_vec(void* dst_, const void* p_, int64_t n) {
   using P = typename VT<FMT>::P;
   T* dst = static_cast<T*>(dst_);
   const P* p = static_cast<const P*>(p_);
-  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;
-       i += (int64_t)gridDim.x * blockDim.x) {
-    if constexpr (FMT == VF_F32) {
-      st(dst, i, (float)to_d(ldg(p, i)));
-    } else {
-      st(dst, i, ldg(p, i));
-    }
-  }
+  for_points_k<EW_K>(
+      n, (int)1, (int)1, [&](int64_t i, int64_t) { return ldg(p, i); },
+      [&](int64_t i, int64_t, P v) {
+        if constexpr (FMT == VF_F32) {
+          st(dst, i, (float)to_d(v));
+        } else {
+          st(dst, i, v);
+        }
+      });
 }
 
 // y += tau * p  (y in vector format, p in the Newton-sum format)
@@ -744,15 +803,47 @@ __global__ void k_axpy(void* y_, const void* p_, int64_t n, double tau) {
   T* y = static_cast<T*>(y_);
   const P* p = static_cast<const P*>(p_);
   const P t = from_d<P>(tau);
-  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;
-       i += (int64_t)gridDim.x * blockDim.x) {
-    const P v = mac(to_p(ldg(y, i)), t, ldg(p, i));
-    if constexpr (FMT == VF_F32) {
-      st(y, i, (float)to_d(v));
-    } else {
-      st(y, i, v);
-    }
-  }
+  struct YP {
+    T y;
+    P p;
+  };
+  for_points_k<EW_K>(
+      n, (int)1, (int)1, [&](int64_t i, int64_t) { return YP{ld(y, i), ldg(p, i)}; },
+      [&](int64_t i, int64_t, YP a) {
+        const P v = mac(to_p(a.y), t, a.p);
+        if constexpr (FMT == VF_F32) {
+          st(y, i, (float)to_d(v));
+        } else {
+          st(y, i, v);
+        }
+      });
+}
+
+// (A - cI)/gamma as seven native FP64 coefficient arrays.  The padding stays
+// harmless: padded neighbour coefficients are 0 and stay 0; the padded
+// diagonal becomes -c/gamma but multiplies a padded w = 0.
+struct PrescaleArgs {
+  double* s[7];
+  const double* a[7];  // a[0..5], diagonal
+};
+struct Coef7 {
+  double a[7];
+};
+__global__ void __launch_bounds__(EI_TPB)
+k_prescale(const PrescaleArgs P, int64_t n, double c, double inv_gamma) {
+  for_points_k<EW_K>(
+      n, (int)1, (int)1,
+      [&](int64_t i, int64_t) {
+        Coef7 v;
+#pragma unroll
+        for (int k = 0; k < 7; ++k) v.a[k] = __ldg(P.a[k] + i);
+        return v;
+      },
+      [&](int64_t i, int64_t, Coef7 v) {
+#pragma unroll
+        for (int k = 0; k < 6; ++k) P.s[k][i] = v.a[k] * inv_gamma;
+        P.s[6][i] = (v.a[6] - c) * inv_gamma;
+      });
 }
 
 template <int FMT>
@@ -787,6 +878,7 @@ static int ew_blocks(int64_t n) {
 }
 
 int reduction_capacity() { return num_sms() * 8; }
+int sm_count() { return num_sms(); }
 
 int csr_blocks(int64_t n) {  // one thread per row
   int64_t b = (n + EI_TPB - 1) / EI_TPB;
@@ -986,12 +1078,27 @@ cudaError_t launch_csr_F(const CsrDev& op, const void* u, void* F, void* qc_out,
 
 // Pointwise g(u) and g'(u) (Sec. III-C; Table 3 times this evaluation): U is
 // the array type, T the format the arithmetic runs in.
+// Below this u the combustion term's exponential e^{20(1-1/u)} < 2^-100 leaves
+// the float-float range (FP32 exponents): those points use native FP64.
+constexpr double kDfCombustionU = 0.25;
 template <class T, class U>
 __global__ void __launch_bounds__(EI_TPB)
 k_nonlin_eval(int nonlin, int64_t n, const U* u, U* g, U* dg) {
   const T one = from_d<T>(1.0), mtwo = from_d<T>(-2.0);
   for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;
        i += (int64_t)gridDim.x * blockDim.x) {
+    if constexpr (sizeof(T) == 8 && sizeof(U) == 8 && !std::is_same<T, double>::value) {
+      // float-float: where e^{20(1-1/u)} falls below the format's range
+      // (2^-100, u < 1/4) the full form is evaluated in native FP64
+      const double ud = (double)u[i];
+      if (nonlin == EI_NONLIN_COMBUSTION && ud < kDfCombustionU) {
+        double gd, dd;
+        combustion_eval(ud, gd, dd);
+        g[i] = (U)gd;
+        if (dg) dg[i] = (U)dd;
+        continue;
+      }
+    }
     const T uc = from_d<T>((double)u[i]);
     T gv = zero<T>(), dq = zero<T>();
     if (nonlin == EI_NONLIN_LOGISTIC) {
@@ -1218,6 +1325,16 @@ cudaError_t launch_axpy(void* y, const void* p, int fmt, int64_t n, double tau,
                         cudaStream_t stm) {
   const int nb = ew_blocks(n);
   EI_DISPATCH_FMT(fmt, (k_axpy<F_><<<nb, EI_TPB, 0, stm>>>(y, p, n, tau)));
+  return cudaGetLastError();
+}
+
+cudaError_t launch_prescale(void* const sa[7], const void* const a[6], const void* diag,
+                            int64_t n_alloc, double c, double inv_gamma, cudaStream_t stm) {
+  PrescaleArgs P{};
+  for (int i = 0; i < 7; ++i) P.s[i] = static_cast<double*>(sa[i]);
+  for (int i = 0; i < 6; ++i) P.a[i] = static_cast<const double*>(a[i]);
+  P.a[6] = static_cast<const double*>(diag);
+  k_prescale<<<ew_blocks(n_alloc), EI_TPB, 0, stm>>>(P, n_alloc, c, inv_gamma);
   return cudaGetLastError();
 }
 

@@ -115,7 +115,11 @@ __device__ __forceinline__ bool mbar_wait_bounded(uint32_t bar, uint32_t parity,
 
 static constexpr uint64_t kWaitLimitNs = 500000000ull;  // 0.5 s; a plane lands in microseconds
 
-template <int FMT>
+// PRE: the coefficient tiles hold the scaled operator (A - cI)/gamma (native
+// FP64 only), so w_{j+1} = (A w_j - c w_j)/gamma - xi_j w_j is the 7-point sum
+// and one FMA with -xi_j: the FP64 pipe bounds this kernel, and the scaling
+// saves it a multiply per point.
+template <int FMT, bool PRE>
 __global__ void __launch_bounds__(256, TmaCfg<FMT>::MINB)
 k_newton_tma(const __grid_constant__ NewtonMaps M, const StencilDev g, const NewtonScalars s,
              void* __restrict__ w_out_, void* __restrict__ p_, double* partials, DevCtl* ctl,
@@ -175,7 +179,7 @@ k_newton_tma(const __grid_constant__ NewtonMaps M, const StencilDev g, const New
   }
 
   const T invg = from_d<T>(s.inv_gamma);
-  const T nshift = from_d<T>(-s.shift);
+  const T nshift = from_d<T>(PRE ? -s.xi : -s.shift);
   const P dn = from_d<P>(s.d_next);
   const P d0 = from_d<P>(s.d0);
   typename Acc<T>::type aw = Acc<T>::zero();
@@ -213,7 +217,7 @@ k_newton_tma(const __grid_constant__ NewtonMaps M, const StencilDev g, const New
       const T acc = stencil7(Ct[6 * TT + ci], wc, Ct[0 * TT + ci], Wc[wi - 1], Ct[1 * TT + ci],
                              Wc[wi + 1], Ct[2 * TT + ci], Wc[wi - C::WX], Ct[3 * TT + ci],
                              Wc[wi + C::WX], Ct[4 * TT + ci], Wm[wi], Ct[5 * TT + ci], Wp[wi]);
-      const T wn = newton_update(acc, invg, nshift, wc);
+      const T wn = PRE ? mac(acc, nshift, wc) : newton_update(acc, invg, nshift, wc);
       const P* Pt = reinterpret_cast<const P*>(scq + C::OFF_P);
       const P pold = needp ? Pt[ci] : mul(d0, to_p(wc));
       const P pn = mac(pold, dn, to_p(wn));
@@ -559,51 +563,87 @@ bool encode_map(CUtensorMap* m, const void* base, int elem_bytes, const StencilD
   return r == CUDA_SUCCESS;
 }
 
-static int tma_zchunk(const StencilDev& g) {
-  const int bxy = ((g.nx + 31) / 32) * ((g.ny + 7) / 8);
+// Planes per block (the z-chunk).  Blocks run in waves of `slots` (SMs x
+// resident blocks per SM) and the last, partial wave takes as long as a full
+// one, so the chunk is the candidate whose waves finish soonest: the time is
+// modelled as waves x (zc + halo), `halo` being a block's fixed cost in planes
+// (its extra halo planes and pipeline start).  Ties go to the larger chunk.
+static constexpr int kZChunks[5] = {64, 32, 16, 8, 4};
+static int tma_zchunk(const StencilDev& g, int slots, double halo) {
+  const int64_t bxy = (int64_t)((g.nx + 31) / 32) * ((g.ny + 7) / 8);
+  int best = 1;
+  double best_t = INFINITY;
+  for (int zc : kZChunks) {
+    const int z = zc < g.nz ? zc : g.nz;
+    const int64_t nzb = (g.nz + z - 1) / z;
+    if (nzb > 65535) continue;
+    const int64_t waves = (bxy * nzb + slots - 1) / slots;
+    const double t = (double)waves * (z + halo);
+    if (t < best_t - 1e-9) {
+      best_t = t;
+      best = z;
+    }
+  }
+  return best;
+}
+
+int newton_tma_blocks(const StencilDev& g) {
+  const int64_t bxy = (int64_t)((g.nx + 31) / 32) * ((g.ny + 7) / 8);
+  const int zmin = kZChunks[4] < g.nz ? kZChunks[4] : g.nz;
+  return (int)(bxy * ((g.nz + zmin - 1) / zmin));
+}
+
+// The two-iteration kernel's fixed cost of a block in plane-equivalents: two
+// more w planes, two more coefficient planes and w_{j+1} on two more planes.
+static constexpr double kHaloPair = 2.3;
+
+// The one-iteration kernel: 32 planes a block unless that leaves fewer than
+// 1216 blocks (8 per SM), halving down to 4.  (The wave model above measured
+// no better here: when a last, partial wave runs, its blocks share the SM's
+// FP64 pipe with fewer others and finish sooner.)
+static int tma_zchunk_single(const StencilDev& g) {
+  const int64_t bxy = (int64_t)((g.nx + 31) / 32) * ((g.ny + 7) / 8);
   int zc = 32;
-  while (zc > 4 && (int64_t)bxy * ((g.nz + zc - 1) / zc) < 1216) zc /= 2;
+  while (zc > 4 && bxy * ((g.nz + zc - 1) / zc) < 1216) zc /= 2;
   if (zc > g.nz) zc = g.nz;
   if (zc < 1) zc = 1;
   while ((g.nz + zc - 1) / zc > 65535) zc *= 2;
   return zc;
 }
 
-int newton_tma_blocks(const StencilDev& g) {
-  const int zc = tma_zchunk(g);
-  return ((g.nx + 31) / 32) * ((g.ny + 7) / 8) * ((g.nz + zc - 1) / zc);
-}
-
-template <int FMT>
+template <int FMT, bool PRE>
 static cudaError_t launch_one(const StencilDev& g, const NewtonMaps& M, void* w_out, void* p,
                               const NewtonScalars& s, double* partials, DevCtl* ctl,
                               cudaStream_t st) {
   using C = TmaCfg<FMT>;
   static bool attr = false;
   if (!attr) {
-    cudaError_t e = cudaFuncSetAttribute(k_newton_tma<FMT>,
+    cudaError_t e = cudaFuncSetAttribute(k_newton_tma<FMT, PRE>,
                                          cudaFuncAttributeMaxDynamicSharedMemorySize, C::SMEM);
     if (e != cudaSuccess) return e;
     attr = true;
   }
-  const int zc = tma_zchunk(g);
+  const int zc = tma_zchunk_single(g);
   dim3 grid((g.nx + 31) / 32, (g.ny + 7) / 8, (g.nz + zc - 1) / zc), block(32, 8, 1);
-  k_newton_tma<FMT><<<grid, block, C::SMEM, st>>>(M, g, s, w_out, p, partials, ctl, zc);
+  k_newton_tma<FMT, PRE><<<grid, block, C::SMEM, st>>>(M, g, s, w_out, p, partials, ctl, zc);
   return cudaGetLastError();
 }
 
 cudaError_t launch_newton_tma(const StencilDev& g, const NewtonMaps& M, void* w_out, void* p,
                               const NewtonScalars& s, int fmt, double* partials, DevCtl* ctl,
-                              cudaStream_t st) {
-  if (fmt == VF_DF) return launch_one<VF_DF>(g, M, w_out, p, s, partials, ctl, st);
-  if (fmt == VF_F64) return launch_one<VF_F64>(g, M, w_out, p, s, partials, ctl, st);
-  return launch_one<VF_F32>(g, M, w_out, p, s, partials, ctl, st);
+                              cudaStream_t st, bool prescaled) {
+  if (fmt == VF_DF) return launch_one<VF_DF, false>(g, M, w_out, p, s, partials, ctl, st);
+  if (fmt == VF_F64) {
+    if (prescaled) return launch_one<VF_F64, true>(g, M, w_out, p, s, partials, ctl, st);
+    return launch_one<VF_F64, false>(g, M, w_out, p, s, partials, ctl, st);
+  }
+  return launch_one<VF_F32, false>(g, M, w_out, p, s, partials, ctl, st);
 }
 
 cudaError_t launch_newton2_tma(const StencilDev& g, const NewtonMaps& M, void* w_out, void* p,
                                const NewtonScalars& s, int fmt, double* partials, DevCtl* ctl,
                                cudaStream_t st) {
-  const int zc = tma_zchunk(g);
+  const int zc = tma_zchunk(g, sm_count() * 2, kHaloPair);  // two blocks per SM
   dim3 grid((g.nx + 31) / 32, (g.ny + 7) / 8, (g.nz + zc - 1) / zc), block(32, 8, 1);
   if (fmt == VF_DF) {
     using C = TmaCfg2<VF_DF>;

@@ -33,7 +33,7 @@ EXPORTS = [
     "ei_mlp_set_decision", "ei_mlp_get_decision", "ei_mlp_forward", "ei_mlp_loss_grad",
     "ei_mlp_train_step", "ei_set_schedule_model", "ei_batch_set_schedule_model",
     "ei_nonlinearity", "ei_set_dirichlet_values", "ei_phi_apply_imag",
-    "ei_divided_differences_imag", "ei_schedule_imag",
+    "ei_divided_differences_imag", "ei_schedule_imag", "ei_batch_set_wait_limit",
 ]
 
 
@@ -51,7 +51,8 @@ class Stats(C.Structure):
                 ("newton_timed", C.c_int), ("newton_fused", C.c_int),
                 ("newton_ms", C.c_double), ("learned", C.c_int), ("learned_s", C.c_int),
                 ("learned_m", C.c_int), ("learned_pad", C.c_int),
-                ("features", C.c_double * MLP_INPUTS)]
+                ("features", C.c_double * MLP_INPUTS), ("arith_used", C.c_int),
+                ("pad_end", C.c_int)]
 
     def degree_list(self):
         return [int(self.degrees[i]) for i in range(min(self.s, STATS_MAX_SUBSTEPS))]
@@ -63,7 +64,8 @@ class Stats(C.Structure):
                 "degrees": self.degree_list(), "launches": self.launches,
                 "newton_timed": self.newton_timed, "newton_fused": self.newton_fused,
                 "newton_ms": self.newton_ms, "learned": self.learned,
-                "learned_s": self.learned_s, "learned_m": self.learned_m}
+                "learned_s": self.learned_s, "learned_m": self.learned_m,
+                "arith_used": self.arith_used}
 
     def feature_list(self):
         return [float(self.features[i]) for i in range(MLP_INPUTS)]
@@ -148,6 +150,7 @@ def lib():
                                         C.c_double, dp]
         L.ei_set_schedule_model.argtypes = [vp, vp]
         L.ei_batch_set_schedule_model.argtypes = [vp, vp]
+        L.ei_batch_set_wait_limit.argtypes = [vp, C.c_int64]
         L.ei_nonlinearity.argtypes = [C.c_int, C.c_int, C.c_int, C.c_int64, vp, vp, vp, vp]
         L.ei_set_dirichlet_values.argtypes = [vp, C.POINTER(vp)]
         L.ei_status_string.argtypes = [C.c_int]
@@ -441,6 +444,10 @@ class Batch:
         self._model = model
         _check(lib().ei_batch_set_schedule_model(self._h, model._h if model is not None
                                                  else None), "ei_batch_set_schedule_model")
+
+    def set_wait_limit(self, limit_us):
+        """The persistent kernel's no-progress limit in microseconds (<= 0: 5 s)."""
+        _check(lib().ei_batch_set_wait_limit(self._h, int(limit_us)), "ei_batch_set_wait_limit")
 
     def phi1(self, v, out, stream=None):
         import torch

@@ -216,3 +216,30 @@ def test_batch_learned_fp32_matches_plain_fp64(env):
     kept = sum(1 for s in st if s.learned == 1)
     print(f"worst relative error {worst:.2e}; proposals kept {kept}/{len(probs)}")
     assert kept >= 0.8 * len(probs)
+
+
+def test_batch_wait_limit_timeout_then_normal_pass(env, xi):
+    """The persistent kernel's bounded wait in its one safe form: an idle warp
+    gives up when it sees no progress for longer than the limit, and nothing
+    waits on a warp.  With a 1 us limit (far below a strip's duration) the
+    pass returns EI_ERR_TIMEOUT and leaves out unmodified; with the default
+    limit restored the same batch object runs a normal pass."""
+    torch, ei = env
+    probs = _small_batch(21, 48)
+    b = ei.Batch(probs, prec=0, tol=1e-10)
+    v = _pack(torch, probs, torch.float64)
+    out = torch.full_like(v, 12345.0)
+    b.set_wait_limit(1)
+    with pytest.raises(ei.EIError) as e:
+        b.phi1(v, out)
+    assert e.value.status == ei.ERR_TIMEOUT
+    torch.cuda.synchronize()
+    assert bool((out == 12345.0).all())
+    b.set_wait_limit(0)
+    st = b.phi1(v, out)
+    got = out.cpu().numpy()
+    for i in (2, 17, 47):
+        ref, ost = _oracle(probs[i], xi, 1e-10)
+        assert rel_err(_unpack(got, b.offsets, i), ref) <= 1e-9
+        assert st[i].s == ost.s and st[i].degree_sum == sum(ost.degrees)
+    b.close()

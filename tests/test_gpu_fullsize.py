@@ -6,10 +6,11 @@ and through properties that hold at any size where it does not.
     the oracle (1e-9), identical Leja degree and substep count.
   * 2^20-node CSR phi_1 (h*rho = 100): the full vector against the oracle
     (1e-9), identical degree; phi_1(hA)1 = 1 and 1^T phi_1(hA)v = 1^T v.
-  * 512^3 FP32 form, 10 exponential-Euler steps: against the FP64 path on the
-    64^3 restriction (every 8th point, offset 4), within 1e-5; the FP64 path
-    itself is held to the oracle by the other tests.  The same FP32 form on a
-    64^3 grid against the oracle directly.
+  * 512^3 FP32 form, 10 exponential-Euler steps: against the FP64 oracle on
+    the 64^3 restriction (every 8th point, offset 4), within 1e-5, from a
+    stored result that a committed script wrote with the oracle alone
+    (tests/golden/).  The same FP32 form on a 64^3 grid against the oracle
+    directly.
   * 21-spin bath propagator (2^21 complex states, t = 10, tol 1e-5): the
     substep count against the oracle's rule, unitarity, energy conservation,
     the group property and the FP32 form against FP64.
@@ -107,19 +108,25 @@ def test_fp32_form_64cube_vs_oracle(env, xi):
 
 
 def test_fp32_form_512cube_restriction(env):
+    """The 512^3 FP32 form (10 exponential Euler steps) against the FP64
+    oracle on the 64^3 restriction (every 8th point per axis from offset 4):
+    tests/golden/adr3d_512_fp32_restriction.npz, written by
+    tests/golden/make_adr3d_512_fp32_restriction.py, which calls only the
+    oracle and the seeded inputs (the FP32-rounded D, b and u0 the FP32 form
+    receives).  Bound: 1e-5 relative 2-norm."""
+    import os
     torch, ei = env
+    g = np.load(os.path.join(os.path.dirname(__file__), "golden",
+                             "adr3d_512_fp32_restriction.npz"))
     w = W.adr_3d_fp32(n=512)
+    u0r = w.u0.astype(np.float32).astype(np.float64)[4::8, 4::8, 4::8]
+    assert np.array_equal(g["u0"], u0r) and int(g["steps"]) == w.steps
+    assert float(g["h"]) == w.h and float(g["tol"]) == w.tol
     got = _fp32_run(torch, ei, w, w.steps)[4::8, 4::8, 4::8]
-    ctx = ei.Context()
-    ctx.set_operator_stencil(w.n, w.dx, dev(torch, w.D), [dev(torch, x) for x in w.b], 0.0,
-                             list(w.bc), ei.PREC_F64)
-    u = dev(torch, w.u0)
-    for _ in range(w.steps):
-        ctx.step(ei.EXP_EULER, w.h, u, ei.NONLIN_LOGISTIC, w.tol)
-    ref = u.cpu().numpy()[4::8, 4::8, 4::8]
-    ctx.close()
-    err = rel_err(got, ref)
-    print(f"512^3 FP32 form vs FP64 path on the 64^3 restriction: {err:.3e}")
+    err = rel_err(got, g["u"])
+    inc = rel_err(got - u0r, g["u"] - u0r)
+    print(f"512^3 FP32 form vs the FP64 oracle on the 64^3 restriction: {err:.3e} "
+          f"(increment {inc:.3e})")
     assert err <= 1e-5
 
 

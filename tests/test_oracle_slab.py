@@ -30,3 +30,23 @@ def test_slab_step_equals_serial(parts, bc, h):
     assert st2.s == st.s and st2.degrees == st.degrees and st2.matvecs == st.matvecs
     inc, inc2 = ref - u0, got - u0
     assert np.linalg.norm(inc2 - inc) <= 1e-13 * np.linalg.norm(inc)
+
+
+def test_slab_euler_step_equals_serial():
+    rng = np.random.default_rng(6)
+    n = (17, 15, 12)
+    shape = (12, 15, 17)
+    dx = (1 / 17, 1 / 17, 1 / 17)
+    D = rng.uniform(0.5, 1.5, shape)
+    b = tuple(rng.uniform(-2, 2, shape) for _ in range(3))
+    u0 = rng.uniform(0, 1, shape)
+    h, tol = 2e-2, 1e-8
+    op = O.StencilOperator(n, dx, D, b, bc=(1,) * 6)
+    ref, st = Nw.exp_euler_step(op, u0, h, tol, Nw.NONLIN_LOGISTIC)
+    sop = S.SlabStencil(n, dx, D, b, bc=(1,) * 6, parts=4)
+    got, st2 = S.exp_euler_step(sop, u0, h, tol)
+    sop.close()
+    assert (st2.alpha, st2.beta) == (st.alpha, st.beta)
+    assert st2.s == st.s and st2.degrees == st.degrees
+    inc, inc2 = ref - u0, got - u0
+    assert np.linalg.norm(inc2 - inc) <= 1e-13 * np.linalg.norm(inc)
