@@ -63,12 +63,13 @@ PAIR_DRAM_BYTES_PER_POINT = 86.9
 # the same for one launch of the native-FP64 one-iteration kernel, from ncu on
 # 192^3 (profiles/k_newton_tma_double_192cube.md)
 NATIVE_DRAM_BYTES_PER_POINT = 85.97
-# DRAM bytes of one launch of the float-float 2-lane complex CSR kernel on the
-# 21-spin operator (profiles/k_csr_newton_cg_spin_bath_21.md, the current kernel)
-SPIN_DRAM_BYTES_PER_LAUNCH = 1.242e9
-# the same for the float-float 2-lane real CSR kernel on the 2^20-node graph
-# (profiles/k_csr_newton_g_rgg_2e20.md)
-RGG_DRAM_BYTES_PER_LAUNCH = 195.8e6
+# DRAM bytes of one launch of the float-float sliced complex CSR kernel on the
+# 21-spin operator (None: not captured for the kernel as it is)
+SPIN_DRAM_BYTES_PER_LAUNCH = None
+# the same for the sliced real CSR kernel on the 2^20-node graph, float-float
+# and native FP64 (None: not captured for the kernel as it is)
+RGG_DRAM_BYTES_PER_LAUNCH = None
+RGG_DRAM_BYTES_PER_LAUNCH_F64 = None
 FLOPS_PER_POINT_PAPER = 10  # the paper's count for (alpha A + beta I)x, Sec. III-A
 
 
@@ -88,7 +89,8 @@ def parse():
                              "adr3d_learned", "adr3d_fp32_learned", "rgg_csr_learned",
                              "batch_learned_fp32", "batch_plain_fp64_loop", "combustion",
                              "combustion_fast", "combustion_nonlin", "heat_dirichlet_data",
-                             "heat_dirichlet_hom", "phi2_adr3d", "spin_bath", "spin_bath_fp32"],
+                             "heat_dirichlet_hom", "phi2_adr3d", "spin_bath", "spin_bath_fp32",
+                             "northstar"],
                     help="adr3d (default, the headline): 256^3 FP64 Rosenbrock-Euler; "
                          "adr3d_fp32: 512^3 FP32 exponential Euler; rgg_csr: 2^20-node CSR phi_1")
     ap.add_argument("--no-cpu", action="store_true", help="skip the CPU baseline sample")
@@ -505,12 +507,15 @@ class NonlinEval(Workload):
 
 class RggCsr(Workload):
     """phi_1(hA)v for A = -(graph Laplacian) of the 2^20-node random geometric
-    graph, h*rho(A) = 100, tol 1e-10, FP64."""
+    graph, h*rho(A) = 100, tol 1e-10, in native FP64 (arith = 1; 0: the
+    float-float form)."""
+
+    arith = 1
 
     def __init__(self, torch, ei, W, dev, ctx, n):
         self.name, self.method = "rgg_2^20_csr_phi1", "phi1"
-        self.dtype = DTYPE_FF
         self.ei = ei
+        self.set_arith(self.arith)
         g = W.rgg_graph(n=n)
         self.npts = g.n
         self.keep = [torch.from_numpy(g.rowptr).to(dev), torch.from_numpy(g.col).to(dev),
@@ -528,20 +533,36 @@ class RggCsr(Workload):
         self.bytes_per_point = 12.0 * nnz / g.n + 48.0
         self.config = {"nodes": g.n, "nnz": int(nnz), "mean_degree": nnz / g.n,
                        "h_rho": 100.0, "tol": self.tol, "method": self.method}
-        self.traffic_per_launch = RGG_DRAM_BYTES_PER_LAUNCH if n == 1 << 20 else None
+        self.n_full = n == 1 << 20
+
+    @property
+    def traffic_per_launch(self):
+        if not self.n_full:
+            return None
+        return RGG_DRAM_BYTES_PER_LAUNCH_F64 if self.arith else RGG_DRAM_BYTES_PER_LAUNCH
+
+    def set_arith(self, arith):
+        self.arith = arith
+        self.dtype = "f64" if arith else DTYPE_FF
+
+    def _o(self, opts):
+        o = {"arith": self.arith}
+        o.update(opts or {})
+        return o
 
     def step(self, ctx, opts=None):
-        return ctx.phi_apply(1, self.h, self.state, self.out, self.tol, opts)
+        return ctx.phi_apply(1, self.h, self.state, self.out, self.tol, self._o(opts))
 
     def step_host(self, ctx, host, opts=None):
         # phi_1(hA)v of the same v every call: the result goes to its own buffer
         d = host.to(self.state.device, non_blocking=True)
-        st = ctx.phi_apply(1, self.h, d, self.out, self.tol, opts)
+        st = ctx.phi_apply(1, self.h, d, self.out, self.tol, self._o(opts))
         pinned_like(self, host).copy_(self.out, non_blocking=False)
         return st
 
     def kernel(self, fused):
-        return "k_csr_newton_g<float-float, 2 lanes a row> (32 rows a warp in 2 rounds)"
+        fmt = "double" if self.arith else "float-float"
+        return f"k_csr_newton_sell<{fmt}> (slices of 32 rows, a lane a row)"
 
 
 class PhiKAdr3d(Adr3d):
@@ -617,8 +638,8 @@ class SpinBath(Workload):
 
     def kernel(self, fused):
         fmt = "float" if self.prec == 1 else "float-float"
-        return (f"k_csr_newton_cg<{fmt}, 2 lanes a row> (complex w and p interleaved, "
-                f"real H)")
+        return (f"k_csr_newton_sell_c<{fmt}> (slices of 32 rows, complex w and p "
+                f"interleaved, real H)")
 
 
 class SpinBathFp32(SpinBath):
@@ -715,14 +736,16 @@ class Batch2dLearnedFp32(Batch2d):
 
 class Batch2dPlainLoop(Workload):
     """The plain FP64 GPU method on the same 1024 problems: one context per
-    problem, ei_phi_apply with the a-priori schedule, one problem after the
-    other (tol 1e-6, the accuracy the FP32 form states).  A step is one pass
-    over all problems."""
+    problem, ei_phi_apply in native FP64 with the a-priori schedule, one problem
+    after the other (tol 1e-6, the accuracy the FP32 form states).  A step is
+    one pass over all problems."""
+
+    arith = 1
 
     def __init__(self, torch, ei, W, dev, ctx, n):
         self.name = "batch_1024_2d_fp64_plain_loop"
         self.method = "phi1 (one ei_phi_apply per problem, a-priori schedule)"
-        self.dtype = DTYPE_FF
+        self.dtype = "f64" if self.arith else DTYPE_FF
         self.ei = ei
         probs = W.batch_2d(count=n)
         self.tol = 1e-6
@@ -750,7 +773,9 @@ class Batch2dPlainLoop(Workload):
         agg = LoopStepStats()
         for i, (c, p) in enumerate(zip(self.ctxs, self.probs)):
             a, b = int(self.offsets[i]), int(self.offsets[i + 1])
-            st = c.phi_apply(1, p.h, v[a:b], self.out[a:b], self.tol, opts)
+            o = {"arith": self.arith}
+            o.update(opts or {})
+            st = c.phi_apply(1, p.h, v[a:b], self.out[a:b], self.tol, o)
             agg.add(st, self.bytes_per_point * (b - a))
         return agg
 
@@ -764,7 +789,8 @@ class Batch2dPlainLoop(Workload):
         return st
 
     def kernel(self, fused):
-        return "k_newton2_tma<float-float> (per-problem launches)"
+        return ("k_newton_tma<double> (per-problem launches)" if self.arith
+                else "k_newton2_tma<float-float> (per-problem launches)")
 
 
 class LoopStepStats:
@@ -969,6 +995,23 @@ def roofline(wl, r, args, npts):
            "us_per_iteration": avg_launch_s * 1e6 / fused,
            "peak_kind": peak_kind,
            "paper_gflops": FLOPS_PER_POINT_PAPER * npts * fused / avg_launch_s / 1e9}
+    if type(wl).__name__ in ("RggCsr", "RggCsrLearned") and wl.arith:
+        # native FP64: the HBM bound and the FP64-pipe bound (2 flops an entry,
+        # 12 a row: the update, the Newton sum and two squared norms) are close;
+        # report against the larger
+        sm_mhz = peaks_sm_mhz()
+        fpk = SMS * FP64_FLOPS_PER_SM_CLK * sm_mhz * 1e6 / 1e12
+        flops = 2.0 * wl.config["nnz"] + 12.0 * npts
+        t_alu = flops / (fpk * 1e12)
+        t_hbm = wl.bytes_per_point * npts / (hbm * 1e9)
+        out.update({"t_alu_us": t_alu * 1e6, "t_hbm_us": t_hbm * 1e6,
+                    "fp64_tflops": flops / avg_launch_s / 1e12, "fp64_peak": fpk,
+                    "fp64_frac": flops / avg_launch_s / 1e12 / fpk})
+        if t_alu > t_hbm:
+            out.update({"bound": "alu", "achieved": flops / avg_launch_s / 1e12, "peak": fpk,
+                        "unit": "TFLOP/s", "frac": flops / avg_launch_s / 1e12 / fpk,
+                        "peak_kind": f"derived: {SMS} SMs x {FP64_FLOPS_PER_SM_CLK} FP64 "
+                                     f"flop/clk x {sm_mhz:.0f} MHz"})
     if type(wl).__name__ in ("Adr3d", "Adr3dFF", "Adr3dLearned"):
         # the scope's algorithmic bytes (72 per point-iteration: the operator as
         # its inputs D, b, u_n) against measured HBM; the stored-coefficient
@@ -1066,6 +1109,67 @@ def cpu_leg(w, gpu_states, gpu_stats):
     return cpu, errs
 
 
+def run_northstar(args):
+    """The comparison the learned, FP32 and batched forms are built for: the
+    1024 uneven 2D problems at tol 1e-6, (a) the learned schedule with FP32
+    vectors in one persistent launch per pass, against (b) the plain method in
+    native FP64, one ei_phi_apply per problem.  Both are timed the same way
+    (W warm-up passes, K timed passes between CUDA events); both outputs are
+    held against the FP64 oracle at tol 1e-10 on a fixed sample of problems."""
+    import torch
+    from paper_1309_4616_gb300 import build, ei
+    from paper_1309_4616_gb300 import workloads as W
+    build.build()
+    dev = torch.device("cuda", 0)
+    stream = torch.cuda.current_stream(dev)
+    ctx = ei.Context(0, stream)
+    n = args.n if args.n is not None else 1024
+    res = {}
+    outs = {}
+    for key, cls in (("learned_fp32_batched", Batch2dLearnedFp32),
+                     ("plain_fp64_loop", Batch2dPlainLoop)):
+        wl = cls(torch, ei, W, dev, ctx, n)
+        r = timed_steps(wl, ctx, args, torch, dev, stream, None, 0)
+        wl.state_reset()
+        wl.step(ctx)
+        torch.cuda.synchronize()
+        outs[key] = wl.out.double().cpu().numpy()
+        res[key] = {"value": args.steps / (r["ms"] * 1e-3), "unit": "passes/s",
+                    "ms_per_pass": r["ms"] / args.steps, "dtype": wl.dtype,
+                    "matvecs_per_pass": r["matvecs"][0], "gpu_launches": r["launches"],
+                    "clocks": r["clocks"], "config": wl.config}
+        probs, offsets = wl.probs, np.concatenate([[0], np.cumsum([p.v.size for p in wl.probs])])
+    # errors against the FP64 oracle at tol 1e-10 on every 16th problem with
+    # at most 160^2 points (the oracle finishes those in seconds)
+    from oracle import leja as L
+    from oracle import newton as Nw
+    from oracle import operators as O
+    xi = L.leja_points(100)
+    sample = [i for i in range(0, len(probs), 16) if probs[i].v.size <= 160 * 160]
+    worst = {k: 0.0 for k in outs}
+    for i in sample:
+        p = probs[i]
+        ref, _ = Nw.phi_apply(O.StencilOperator(p.n, p.dx, p.D, p.b, bc=p.bc), 1, p.h,
+                              p.v, 1e-10, xi=xi)
+        for k, o in outs.items():
+            g = o[offsets[i]:offsets[i + 1]].reshape(ref.shape)
+            e = float(np.linalg.norm(g - ref) / max(np.linalg.norm(ref), 1e-300))
+            worst[k] = max(worst[k], e)
+    for k in res:
+        res[k]["max_rel_err_vs_oracle_tol_1e-10"] = worst[k]
+    a, b = res["learned_fp32_batched"], res["plain_fp64_loop"]
+    line = {"metric": "passes/s of 1024 uneven 2D phi_1 problems at tol 1e-6",
+            "value": a["value"], "unit": "passes/s", "n_gpus": 1, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": a["ms_per_pass"], "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": a["dtype"], "data": "synthetic",
+            "config": {"workload": "northstar_learned_fp32_batched_vs_plain_fp64",
+                       "problems": n, "tol": 1e-6,
+                       "error_sample": f"{len(sample)} problems (every 16th with <= 160^2 points)"},
+            "forms": res, "speedup_vs_plain_fp64": a["value"] / b["value"]}
+    print(json.dumps(line))
+    ctx.close()
+
+
 def run_ours(args):
     import torch
     from paper_1309_4616_gb300 import build, ei
@@ -1098,11 +1202,13 @@ def run_ours(args):
     forms = None
     headline = type(wl) is Adr3d
     states, stats1 = {}, {}
-    if headline:
-        states["f64"], stats1["f64"] = first_step_state(wl, ctx, torch)
+    if type(wl) in (Adr3d, RggCsr):
+        if headline:
+            states["f64"], stats1["f64"] = first_step_state(wl, ctx, torch)
         wl.set_arith(0)
         rf = timed_steps(wl, ctx, args, torch, dev, stream, dist, local)
-        states["float_float"], stats1["float_float"] = first_step_state(wl, ctx, torch)
+        if headline:
+            states["float_float"], stats1["float_float"] = first_step_state(wl, ctx, torch)
         froof = roofline(wl, rf, args, npts)
         forms = {"float_float": {
             "value": args.steps * world / (rf["ms"] * 1e-3), "unit": "steps/s",
@@ -1166,6 +1272,8 @@ def main():
     args = parse()
     if args.impl == "reference":
         run_reference(args)
+    elif args.workload == "northstar":
+        run_northstar(args)
     else:
         run_ours(args)
 

@@ -113,10 +113,15 @@ typedef struct {
   int no_restart;  /* with fixed_s: an attempt that reaches m_max returns
                       EI_ERR_NOT_CONVERGED instead of doubling s (stats keep the
                       degrees reached; u and out are left unmodified) */
-  int csr_lanes;   /* CSR operators: lanes of a warp per row in the Newton
-                      kernel, 1, 2, 4, 8, 16 or 32; 0 (or any other value)
-                      chooses by the mean row length: 1 below 8 entries,
-                      2 below 64, 4 below 128, else 8 */
+  int csr_lanes;   /* CSR operators' Newton kernels (real and complex): 0
+                      (default) runs on the sliced copy the library builds at
+                      set_operator (rows sorted by length within windows of 64,
+                      slices of 32 stored column by column: a warp a slice, a
+                      lane a row, every column and value load one coalesced
+                      access); 1, 2, 4, 8, 16 or 32 run on the caller's CSR
+                      arrays with that many lanes of a warp per row; any other
+                      value chooses the lanes by the mean row length (1 below
+                      8 entries, 2 below 64, 4 below 128, else 8). */
 } ei_options;
 
 #define EI_STATS_MAX_SUBSTEPS 64
@@ -181,7 +186,10 @@ ei_status ei_set_operator_stencil(ei_ctx* ctx, int dim, const int64_t n[3], cons
  * rowptr  int64[n+1] (device), nondecreasing from rowptr[0] = 0 to
  *         rowptr[n] = nnz; col int32[nnz] (device), each in [0, n);
  *         val[nnz] (device).  The structure is checked on the device before
- *         use: a violation returns EI_ERR_INVALID_ARG.
+ *         use: a violation returns EI_ERR_INVALID_ARG.  The library then
+ *         builds a sliced copy of the structure (host sort of the row
+ *         lengths, about 20 bytes per entry of device memory; the values are
+ *         copied per format on first use) for the real Newton kernel.
  * diag    device array of n values or NULL (zero).  Entries with col == row
  *         are allowed and count as diagonal.  prec as above. */
 ei_status ei_set_operator_csr(ei_ctx* ctx, int64_t n, int64_t nnz, const int64_t* rowptr,

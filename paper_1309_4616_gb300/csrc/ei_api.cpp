@@ -48,6 +48,7 @@ struct Prepared {
   void* v = nullptr;       // imported right-hand side / F
   void* u = nullptr;       // imported state
   void* csr_val = nullptr; // CSR values in the matvec precision
+  void* sell_val = nullptr; // the sliced form's values in this format
   void* a[6] = {nullptr, nullptr, nullptr, nullptr, nullptr, nullptr};  // stencil coefficients
   void* diagA = nullptr;   // stencil: diagonal of A (coefficient layout)
   bool coef7 = false;      // explicit stencil coefficients present (stencil operators)
@@ -90,6 +91,13 @@ struct ei_ctx {
   int64_t nnz = 0;
   const void* val_u = nullptr;
   const void* diag_u = nullptr;
+  // the sliced form of the CSR operator (SellDev): built at set_operator
+  int64_t sell_slices = 0, sell_entries = 0;
+  int32_t* sell_perm = nullptr;
+  int32_t* sell_rlen = nullptr;
+  int64_t* sell_ptr = nullptr;
+  int32_t* sell_col = nullptr;
+  int64_t* sell_src = nullptr;  // CSR entry of each sliced entry (per-format values)
   // Gershgorin rows of A (without the per-step g') and their interval
   double* ger_lo = nullptr;
   double* ger_hi = nullptr;
@@ -188,7 +196,7 @@ static int vec_fmt_for(const ei_ctx* c, const ei_options* opt) {
 
 static void free_prepared(Prepared& p) {
   void** arrs[] = {&p.cbase, &p.qc,   &p.w[0], &p.w[1], &p.p,    &p.y,    &p.r,
-                   &p.v,     &p.u,    &p.csr_val, &p.a[0], &p.a[1], &p.a[2], &p.a[3],
+                   &p.v,     &p.u,    &p.csr_val, &p.sell_val, &p.a[0], &p.a[1], &p.a[2], &p.a[3],
                    &p.a[4],  &p.a[5], &p.diagA, &p.sa[0], &p.sa[1], &p.sa[2], &p.sa[3],
                    &p.sa[4], &p.sa[5], &p.sa[6]};
   for (void** a : arrs) {
@@ -222,6 +230,13 @@ static void free_operator(ei_ctx* c) {
     if (a) cudaFree(a);
     a = nullptr;
   }
+  void** sell[] = {(void**)&c->sell_perm, (void**)&c->sell_rlen, (void**)&c->sell_ptr,
+                   (void**)&c->sell_col, (void**)&c->sell_src};
+  for (void** a : sell) {
+    if (*a) cudaFree(*a);
+    *a = nullptr;
+  }
+  c->sell_slices = c->sell_entries = 0;
   c->cx_fmt = -1;
   c->cx_plan.valid = false;
   c->phi1_plan.valid = false;
@@ -293,6 +308,14 @@ static ei_status prepare(ei_ctx* c, int fmt) {
     if ((s = alloc(&P.csr_val, vec_elem_bytes(fmt) * (size_t)c->nnz)) != EI_OK) { free_prepared(P); return s; }
     EI_LAUNCH(launch_fill_coef(P.csr_val, fmt, c->nnz, (int)c->nnz, 1, (int)c->nnz, c->val_u,
                                c->prec, 0.0, 1.0, c->stream));
+    if (c->sell_src) {  // the sliced form's values
+      if ((s = alloc(&P.sell_val, vec_elem_bytes(fmt) * (size_t)c->sell_entries)) != EI_OK) {
+        free_prepared(P);
+        return s;
+      }
+      EI_LAUNCH(launch_sell_gather(c->sell_entries, c->sell_src, nullptr, nullptr, c->val_u,
+                                   c->prec, P.sell_val, fmt, c->stream));
+    }
     EI_LAUNCH(launch_fill_coef(P.cbase, fmt, n, nx, ny, pitch, c->diag_u, c->prec, 0.0, 1.0,
                                c->stream));
   }
@@ -381,6 +404,11 @@ static cudaError_t op_newton(ei_ctx* c, Prepared& P, const void* qc, const void*
     return launch_newton_tma(stencil_view(c, P, qc), M, w_out, P.p, s, P.fmt, c->partials,
                              c->ctl, c->stream, pre);
   }
+  if (c->csr_lanes == 0 && P.sell_val) {
+    SellDev d{c->sell_slices, c->sell_perm, c->sell_rlen, c->sell_ptr, c->sell_col, P.sell_val,
+              qc};
+    return launch_csr_newton_sell(d, w_in, w_out, P.p, s, P.fmt, c->partials, c->ctl, c->stream);
+  }
   return launch_csr_newton(csr_view(c, P, qc), c->nnz, c->csr_lanes, w_in, w_out, P.p, s, P.fmt,
                            c->partials, c->ctl,
                            c->stream);
@@ -468,8 +496,16 @@ static ei_status newton_loop(ei_ctx* c, Prepared& P, const void* qc, const void*
       if (cx) {
         s.d_next_im = cx->d_im[j + 1];
         ++c->launches;
-        EI_TRY_CUDA(launch_csr_newton_c(csr_view(c, P, qc), c->nnz, c->csr_lanes, w_in, w_out,
-                                        cx->p, s, P.fmt, c->partials, c->ctl, c->stream));
+        if (c->csr_lanes == 0 && P.sell_val) {
+          SellDev sd{c->sell_slices, c->sell_perm, c->sell_rlen, c->sell_ptr, c->sell_col,
+                     P.sell_val, qc};
+          EI_TRY_CUDA(launch_csr_newton_sell_c(sd, w_in, w_out, cx->p, s, P.fmt, c->partials,
+                                               c->ctl, c->stream));
+        } else {
+          EI_TRY_CUDA(launch_csr_newton_c(csr_view(c, P, qc), c->nnz, c->csr_lanes, w_in,
+                                          w_out, cx->p, s, P.fmt, c->partials, c->ctl,
+                                          c->stream));
+        }
       } else if (two) {
         EI_TRY_CUDA(op_newton2(c, P, qc, w_in, w_out, s));
       } else {
@@ -929,6 +965,76 @@ static ei_status phi1_substeps(ei_ctx* c, Prepared& P, const void* qc, double h,
   return EI_ERR_NOT_CONVERGED;
 }
 
+// The sliced form (SellDev) of the context's CSR operator, from its validated
+// rowptr and col: rows sorted by length (longest first, stable) inside windows
+// of kSellWindow rows, slices of 32, each slice padded to its longest row.
+// The host builds the permutation, the slice offsets and the CSR entry of every
+// sliced entry; the device gathers the columns (and, per format, the values in
+// prepare).
+static ei_status build_sell(ei_ctx* c) {
+  const int64_t n = c->n;
+  std::vector<int64_t> rp(n + 1);
+  EI_TRY_CUDA(cudaMemcpyAsync(rp.data(), c->cd.rowptr, sizeof(int64_t) * (n + 1),
+                              cudaMemcpyDeviceToHost, c->stream));
+  EI_TRY_CUDA(cudaStreamSynchronize(c->stream));
+  const int64_t ns = (n + 31) / 32;
+  std::vector<int32_t> perm(ns * 32, -1);
+  std::vector<int32_t> idx;
+  for (int64_t w0 = 0; w0 < n; w0 += kSellWindow) {
+    const int64_t w1 = std::min(n, w0 + kSellWindow);
+    idx.resize(w1 - w0);
+    for (int64_t i = w0; i < w1; ++i) idx[i - w0] = (int32_t)i;
+    std::stable_sort(idx.begin(), idx.end(), [&](int32_t a, int32_t b) {
+      return rp[a + 1] - rp[a] > rp[b + 1] - rp[b];
+    });
+    std::copy(idx.begin(), idx.end(), perm.begin() + w0);
+  }
+  std::vector<int32_t> rlen(ns * 32, 0);
+  for (int64_t i = 0; i < ns * 32; ++i)
+    if (perm[i] >= 0) rlen[i] = (int32_t)(rp[perm[i] + 1] - rp[perm[i]]);
+  std::vector<int64_t> sptr(ns + 1, 0);
+  for (int64_t sl = 0; sl < ns; ++sl) {
+    int64_t len = 0;
+    for (int l = 0; l < 32; ++l) {
+      const int32_t r = perm[sl * 32 + l];
+      if (r >= 0) len = std::max(len, rp[r + 1] - rp[r]);
+    }
+    sptr[sl + 1] = sptr[sl] + 32 * len;
+  }
+  const int64_t e = sptr[ns];
+  std::vector<int64_t> src(e > 0 ? e : 1, -1);
+  for (int64_t sl = 0; sl < ns; ++sl) {
+    const int64_t len = (sptr[sl + 1] - sptr[sl]) / 32;
+    for (int l = 0; l < 32; ++l) {
+      const int32_t r = perm[sl * 32 + l];
+      const int64_t rl = r >= 0 ? rp[r + 1] - rp[r] : 0;
+      for (int64_t k = 0; k < rl; ++k) src[sptr[sl] + k * 32 + l] = rp[r] + k;
+    }
+    (void)len;
+  }
+  ei_status st;
+  if ((st = alloc((void**)&c->sell_perm, sizeof(int32_t) * ns * 32)) != EI_OK) return st;
+  if ((st = alloc((void**)&c->sell_rlen, sizeof(int32_t) * ns * 32)) != EI_OK) return st;
+  if ((st = alloc((void**)&c->sell_ptr, sizeof(int64_t) * (ns + 1))) != EI_OK) return st;
+  if ((st = alloc((void**)&c->sell_col, sizeof(int32_t) * (e > 0 ? e : 1))) != EI_OK) return st;
+  if ((st = alloc((void**)&c->sell_src, sizeof(int64_t) * (e > 0 ? e : 1))) != EI_OK) return st;
+  EI_TRY_CUDA(cudaMemcpyAsync(c->sell_perm, perm.data(), sizeof(int32_t) * ns * 32,
+                              cudaMemcpyHostToDevice, c->stream));
+  EI_TRY_CUDA(cudaMemcpyAsync(c->sell_rlen, rlen.data(), sizeof(int32_t) * ns * 32,
+                              cudaMemcpyHostToDevice, c->stream));
+  EI_TRY_CUDA(cudaMemcpyAsync(c->sell_ptr, sptr.data(), sizeof(int64_t) * (ns + 1),
+                              cudaMemcpyHostToDevice, c->stream));
+  EI_TRY_CUDA(cudaMemcpyAsync(c->sell_src, src.data(), sizeof(int64_t) * (e > 0 ? e : 1),
+                              cudaMemcpyHostToDevice, c->stream));
+  if (e > 0)
+    EI_TRY_CUDA(launch_sell_gather(e, c->sell_src, c->cd.col, c->sell_col, nullptr, c->prec,
+                                   nullptr, VF_F64, c->stream));
+  EI_TRY_CUDA(cudaStreamSynchronize(c->stream));  // the host tables go out of scope
+  c->sell_slices = ns;
+  c->sell_entries = e;
+  return EI_OK;
+}
+
 static void log_stats(const char* what, const ei_stats* st, ei_status rc) {
   if (!log_on() || !st) return;
   fprintf(stderr,
@@ -1099,6 +1205,7 @@ ei_status ei_set_operator_csr(ei_ctx* c, int64_t n, int64_t nnz, const int64_t* 
   }
   if ((st = read_ctl(c)) != EI_OK) { free_operator(c); return st; }
   if (c->h_ctl->csr_bad) { free_operator(c); return EI_ERR_INVALID_ARG; }
+  if ((st = build_sell(c)) != EI_OK) { free_operator(c); return st; }
   cudaError_t e = launch_csr_gershgorin(c->cd, prec, val, diag, c->ger_lo, c->ger_hi, c->partials,
                                         c->ctl, c->stream);
   if (e != cudaSuccess) { free_operator(c); return EI_ERR_CUDA; }

@@ -367,6 +367,133 @@ static cudaError_t csr_newton_c_fmt(const CsrDev& op, int lanes, const void* w_i
   return cudaGetLastError();
 }
 
+// The complex step on the sliced form (SellDev): a warp a slice of 32 rows, a
+// lane a row, the column and value loads of entry k one coalesced access.  On
+// operators whose rows share a structure (the spin-bath Hamiltonian: column q
+// of row i is i XOR mask_q) the gathers of a slice's entry k fall in one
+// aligned block of 32 rows: whole lines.
+template <int FMT, int U = (FMT == VF_F32 ? 8 : 4)>
+__global__ void __launch_bounds__(EI_TPB)
+k_csr_newton_sell_c(SellDev op, const void* __restrict__ w_in_, void* __restrict__ w_out_,
+                    void* __restrict__ p_, NewtonScalars s, double* partials, DevCtl* ctl) {
+  static_assert(U % 2 == 0, "batches accumulate entries in pairs");
+  using T = typename VT<FMT>::T;
+  using P = typename VT<FMT>::P;
+  if (*(volatile int*)&ctl->done != 0) return;
+  const Cx<T>* __restrict__ w_in = static_cast<const Cx<T>*>(w_in_);
+  Cx<T>* __restrict__ w_out = static_cast<Cx<T>*>(w_out_);
+  Cx<P>* __restrict__ p = static_cast<Cx<P>*>(p_);
+  const T* __restrict__ qc = static_cast<const T*>(op.qc);
+  const T* __restrict__ val = static_cast<const T*>(op.val);
+  const T invg = from_d<T>(s.inv_gamma);
+  const T nshift = from_d<T>(-s.shift);
+  const P dnr = from_d<P>(s.d_next), dni = from_d<P>(s.d_next_im);
+  const P ndni = from_d<P>(-s.d_next_im);
+  typename Acc<T>::type aw = Acc<T>::zero();
+  typename Acc<P>::type ap = Acc<P>::zero();
+  const int L = threadIdx.x & 31;
+  const int64_t warp = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  const int64_t nwarp = ((int64_t)gridDim.x * blockDim.x) >> 5;
+  for (int64_t sl = warp; sl < op.nslices; sl += nwarp) {
+    const int row = __ldg(op.perm + sl * 32 + L);
+    const int myl = __ldg(op.rlen + sl * 32 + L);
+    const int64_t b = __ldg(op.sptr + sl);
+    const int len = (int)((__ldg(op.sptr + sl + 1) - b) >> 5);
+    Cx<T> wc{zero<T>(), zero<T>()};
+    T q = zero<T>();
+    Cx<P> pold{zero<P>(), zero<P>()};
+    if (row >= 0) {
+      wc = ldgc(w_in, row);
+      q = ldg(qc, row);
+      if (s.j > 0) pold = ldc(p, row);
+    }
+    typename Acc<T>::type r1 = Acc<T>::zero(), r2 = Acc<T>::zero();
+    typename Acc<T>::type i1 = Acc<T>::zero(), i2 = Acc<T>::zero();
+    const int32_t* __restrict__ cp = op.col + b + L;
+    const T* __restrict__ vp = val + b + L;
+    for (int k = 0; k < len; k += U) {
+      int c[U];
+      T v[U];
+      Cx<T> xv[U];
+#pragma unroll
+      for (int u = 0; u < U; ++u) {
+        const bool in = k + u < myl;
+        c[u] = in ? __ldg(cp + (int64_t)(k + u) * 32) : -1;
+        v[u] = in ? ldg(vp, (int64_t)(k + u) * 32) : zero<T>();
+      }
+#pragma unroll
+      for (int u = 0; u < U; ++u)
+        xv[u] = c[u] >= 0 ? ldgc(w_in, c[u]) : Cx<T>{zero<T>(), zero<T>()};
+#pragma unroll
+      for (int u = 0; u + 1 < U; u += 2) {
+        if (FMT == VF_F32 || c[u] >= 0) {
+          r1 = lmac(r1, v[u], xv[u].re);
+          i1 = lmac(i1, v[u], xv[u].im);
+        }
+        if (FMT == VF_F32 || c[u + 1] >= 0) {
+          r2 = lmac(r2, v[u + 1], xv[u + 1].re);
+          i2 = lmac(i2, v[u + 1], xv[u + 1].im);
+        }
+      }
+    }
+    if (row >= 0) {
+      const T myr = lsum(r1, r2), myi = lsum(i1, i2);
+      Cx<T> wn;
+      wn.re = newton_update(mac(myr, q, wc.re), invg, nshift, wc.re);
+      wn.im = newton_update(mac(myi, q, wc.im), invg, nshift, wc.im);
+      if (s.j == 0) {
+        const P d0r = from_d<P>(s.d0), d0i = from_d<P>(s.d0_im), nd0i = from_d<P>(-s.d0_im);
+        const P xr = to_p(wc.re), xi = to_p(wc.im);
+        pold.re = mac(mul(d0r, xr), nd0i, xi);
+        pold.im = mac(mul(d0r, xi), d0i, xr);
+      }
+      const P nr = to_p(wn.re), ni = to_p(wn.im);
+      Cx<P> pn;
+      pn.re = mac(mac(pold.re, dnr, nr), ndni, ni);
+      pn.im = mac(mac(pold.im, dnr, ni), dni, nr);
+      stc(w_out, row, wn);
+      stc(p, row, pn);
+      aw = acc_sq(acc_sq(aw, wn.re), wn.im);
+      ap = acc_sq(acc_sq(ap, pn.re), pn.im);
+    }
+  }
+  double nw2 = acc_d(aw), np2 = acc_d(ap);
+  if (last_block_reduce2<RED_SUM>(nw2, np2, partials, ctl)) {
+    if (threadIdx.x == 0) {
+      ctl->nw2 = nw2;
+      ctl->np2 = np2;
+      newton_verdict(ctl, s, s.j + 1, hypot(s.d_next, s.d_next_im), nw2, np2);
+    }
+  }
+}
+
+template <int FMT>
+static int csr_sell_c_grid(int64_t nslices) {
+  static const int per = [] {
+    int b = 1;
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, k_csr_newton_sell_c<FMT>, EI_TPB, 0);
+    return b < 1 ? 1 : (b > 8 ? 8 : b);  // the partials hold 8 blocks per SM
+  }();
+  int64_t nb = (nslices + EI_TPB / 32 - 1) / (EI_TPB / 32);
+  if (nb > (int64_t)sm_count() * per) nb = (int64_t)sm_count() * per;
+  return nb < 1 ? 1 : (int)nb;
+}
+
+cudaError_t launch_csr_newton_sell_c(const SellDev& op, const void* w_in, void* w_out, void* p,
+                                     const NewtonScalars& s, int fmt, double* partials,
+                                     DevCtl* ctl, cudaStream_t stm) {
+  if (fmt == VF_DF)
+    k_csr_newton_sell_c<VF_DF><<<csr_sell_c_grid<VF_DF>(op.nslices), EI_TPB, 0, stm>>>(
+        op, w_in, w_out, p, s, partials, ctl);
+  else if (fmt == VF_F64)
+    k_csr_newton_sell_c<VF_F64><<<csr_sell_c_grid<VF_F64>(op.nslices), EI_TPB, 0, stm>>>(
+        op, w_in, w_out, p, s, partials, ctl);
+  else
+    k_csr_newton_sell_c<VF_F32><<<csr_sell_c_grid<VF_F32>(op.nslices), EI_TPB, 0, stm>>>(
+        op, w_in, w_out, p, s, partials, ctl);
+  return cudaGetLastError();
+}
+
 cudaError_t launch_csr_newton_c(const CsrDev& op, int64_t nnz, int lanes, const void* w_in,
                                 void* w_out, void* p, const NewtonScalars& s, int fmt,
                                 double* partials, DevCtl* ctl, cudaStream_t stm) {

@@ -54,6 +54,28 @@ struct CsrDev {
   const void* qc;      // diagonal, in the vector format
 };
 
+// Sliced form of a CSR operator (SELL-32-sigma): rows sorted by length
+// (longest first) inside windows of kSellWindow consecutive rows, then cut
+// into slices of 32; a slice stores its entries column by column (entry k of
+// its 32 rows contiguous), padded to its longest row with column -1, value 0.
+// A warp takes a slice, a lane a row: the column and value loads of entry k
+// are one 32-wide access, independent of any per-row pointer, and a lane
+// loads only its own row's entries, so with the rows longest first the lanes
+// still loading form a prefix and the padding is never read.  A small window
+// keeps a slice's rows close: their w gathers hit nearby lines, and their own
+// w, p and diagonal few lines (on a 2^20-node random geometric graph in Morton
+// order windows of 64 measured best: 32 pads more, 128 and up scatter more).
+constexpr int64_t kSellWindow = 64;
+struct SellDev {
+  int64_t nslices;
+  const int32_t* perm;  // row of each slice position (-1: past the last row), 32 nslices
+  const int32_t* rlen;  // entries of the row at each slice position (0 past the last row)
+  const int64_t* sptr;  // first entry of each slice, nslices + 1
+  const int32_t* col;   // column of each entry (-1: padding)
+  const void* val;      // value of each entry in the vector format (0: padding)
+  const void* qc;       // diagonal, in the vector format (indexed by row)
+};
+
 struct NewtonScalars {
   double d_next;       // d_{j+1}
   double d0;           // d_0 (used when j == 0)
@@ -205,6 +227,16 @@ cudaError_t launch_csr_newton(const CsrDev& op, int64_t nnz, int lanes, const vo
 // lanes per row of the CSR Newton kernels: `lanes` when valid, else by the
 // mean row length (1 below 8 entries, 2 below 64, 4 below 128, else 8)
 int csr_lanes_for(int64_t n, int64_t nnz, int lanes);
+// One Newton iteration of a CSR operator in the sliced form (a warp a slice).
+cudaError_t launch_csr_newton_sell(const SellDev& op, const void* w_in, void* w_out, void* p,
+                                   const NewtonScalars& s, int fmt, double* partials,
+                                   DevCtl* ctl, cudaStream_t st);
+// The sliced entries from the CSR arrays: src[i] is the CSR entry of sliced
+// entry i (-1: padding).  col_out[i] = col[src[i]] (or -1); val_out (vector
+// format fmt) = val[src[i]] (caller precision val_prec, or 0).
+cudaError_t launch_sell_gather(int64_t e, const int64_t* src, const int32_t* col,
+                               int32_t* col_out, const void* val, int val_prec, void* val_out,
+                               int fmt, cudaStream_t st);
 
 // Complex vectors for phi_k(-i h H) v, H real symmetric (ei_complex.cu):
 // interleaved (re, im) elements of the vector format (df: re.hi, re.lo,
@@ -217,6 +249,10 @@ int csr_lanes_for(int64_t n, int64_t nnz, int lanes);
 cudaError_t launch_csr_newton_c(const CsrDev& op, int64_t nnz, int lanes, const void* w_in,
                                 void* w_out, void* p, const NewtonScalars& s, int fmt,
                                 double* partials, DevCtl* ctl, cudaStream_t st);
+// the same on the sliced form of the operator (SellDev)
+cudaError_t launch_csr_newton_sell_c(const SellDev& op, const void* w_in, void* w_out, void* p,
+                                     const NewtonScalars& s, int fmt, double* partials,
+                                     DevCtl* ctl, cudaStream_t st);
 // dst = (sr + i si) * src, src a Newton sum (src_is_p) or a vector of format fmt
 cudaError_t launch_cexport(void* dst, int prec, const void* src, int fmt, int src_is_p,
                            int64_t n, double sr, double si, cudaStream_t st);

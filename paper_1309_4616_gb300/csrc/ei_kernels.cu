@@ -1002,6 +1002,112 @@ cudaError_t launch_face_term(const StencilDev& g, int face, int prec, const doub
                                                  b_const, static_cast<const double*>(vals), out);
   return cudaGetLastError();
 }
+// One Newton iteration on the sliced form: a warp per slice (grid-stride over
+// slices), a lane per row.  The slice's length is the same for all its lanes,
+// so the entry loop has no divergence; U entries a lane go out per batch, the
+// column and value loads of a batch together, then the gathers of w_in.  The
+// row's own w, diagonal and p are loaded before the entries.
+constexpr int kSellMinB = 4;  // resident blocks per SM the register budget targets
+template <int FMT, int U>
+__global__ void __launch_bounds__(EI_TPB, kSellMinB)
+k_csr_newton_sell(SellDev op, const void* __restrict__ w_in_, void* __restrict__ w_out_,
+                  void* __restrict__ p_, NewtonScalars s, double* partials, DevCtl* ctl) {
+  using T = typename VT<FMT>::T;
+  using P = typename VT<FMT>::P;
+  if (*(volatile int*)&ctl->done != 0) return;
+  const T* __restrict__ w_in = static_cast<const T*>(w_in_);
+  T* __restrict__ w_out = static_cast<T*>(w_out_);
+  P* __restrict__ p = static_cast<P*>(p_);
+  const T* __restrict__ qc = static_cast<const T*>(op.qc);
+  const T* __restrict__ val = static_cast<const T*>(op.val);
+  const T invg = from_d<T>(s.inv_gamma);
+  const T nshift = from_d<T>(-s.shift);
+  const P dn = from_d<P>(s.d_next);
+  const P d0 = from_d<P>(s.d0);
+  typename Acc<T>::type aw = Acc<T>::zero();
+  typename Acc<P>::type ap = Acc<P>::zero();
+  const int L = threadIdx.x & 31;
+  const int64_t warp = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  const int64_t nwarp = ((int64_t)gridDim.x * blockDim.x) >> 5;
+  for (int64_t sl = warp; sl < op.nslices; sl += nwarp) {
+    const int row = __ldg(op.perm + sl * 32 + L);
+    const int myl = __ldg(op.rlen + sl * 32 + L);
+    const int64_t b = __ldg(op.sptr + sl);
+    const int len = (int)((__ldg(op.sptr + sl + 1) - b) >> 5);
+    T wc = zero<T>(), q = zero<T>();
+    P pold = zero<P>();
+    if (row >= 0) {
+      wc = ldg(w_in, row);
+      q = ldg(qc, row);
+      if (s.j > 0) pold = ld(p, row);
+    }
+    typename Acc<T>::type a1 = Acc<T>::zero(), a2 = Acc<T>::zero();
+    const int32_t* __restrict__ cp = op.col + b + L;
+    const T* __restrict__ vp = val + b + L;
+    for (int k = 0; k < len; k += U) {
+      int c[U];
+      T v[U], xv[U];
+#pragma unroll
+      for (int u = 0; u < U; ++u) {
+        const bool in = k + u < myl;  // this lane's row only: the padding is never read
+        c[u] = in ? __ldg(cp + (int64_t)(k + u) * 32) : -1;
+        v[u] = in ? ldg(vp, (int64_t)(k + u) * 32) : zero<T>();
+      }
+#pragma unroll
+      for (int u = 0; u < U; ++u) xv[u] = c[u] >= 0 ? ldg(w_in, c[u]) : zero<T>();
+#pragma unroll
+      for (int u = 0; u + 1 < U; u += 2) {
+        if (FMT == VF_F32 || c[u] >= 0) a1 = lmac(a1, v[u], xv[u]);
+        if (FMT == VF_F32 || c[u + 1] >= 0) a2 = lmac(a2, v[u + 1], xv[u + 1]);
+      }
+    }
+    if (row >= 0) {
+      const T mine = lsum(a1, a2);
+      const T wn = newton_update(mac(mine, q, wc), invg, nshift, wc);
+      if (s.j == 0) pold = mul(d0, to_p(wc));
+      const P pn = mac(pold, dn, to_p(wn));
+      st(w_out, row, wn);
+      st(p, row, pn);
+      aw = acc_sq(aw, wn);
+      ap = acc_sq(ap, pn);
+    }
+  }
+  double nw2 = acc_d(aw), np2 = acc_d(ap);
+  if (last_block_reduce2<RED_SUM>(nw2, np2, partials, ctl)) {
+    if (threadIdx.x == 0) {
+      ctl->nw2 = nw2;
+      ctl->np2 = np2;
+      newton_verdict(ctl, s, s.j + 1, s.d_next, nw2, np2);
+    }
+  }
+}
+
+template <class U, int FMT>
+__global__ void k_sell_gather(int64_t e, const int64_t* __restrict__ src,
+                              const int32_t* __restrict__ col, int32_t* col_out,
+                              const U* __restrict__ val, void* val_out_) {
+  using T = typename VT<FMT>::T;
+  T* val_out = static_cast<T*>(val_out_);
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < e;
+       i += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t k = src[i];
+    if (col_out) col_out[i] = k >= 0 ? col[k] : -1;
+    if (val_out) st(val_out, i, k >= 0 ? from_d<T>((double)val[k]) : zero<T>());
+  }
+}
+
+template <int FMT, int U>
+static int csr_sell_grid(int64_t nslices) {
+  static const int per = [] {
+    int b = 1;
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, k_csr_newton_sell<FMT, U>, EI_TPB, 0);
+    return b < 1 ? 1 : (b > 8 ? 8 : b);  // the partials hold 8 blocks per SM
+  }();
+  int64_t nb = (nslices + EI_TPB / 32 - 1) / (EI_TPB / 32);
+  if (nb > (int64_t)num_sms() * per) nb = (int64_t)num_sms() * per;
+  return nb < 1 ? 1 : (int)nb;
+}
+
 template <int FMT, int G>
 static int csr_g_grid(int64_t n) {
   // resident blocks per SM, once per variant (capped at 8: the partials' capacity)
@@ -1054,6 +1160,37 @@ cudaError_t launch_csr_newton(const CsrDev& op, int64_t nnz, int lanes, const vo
   int nb = csr_blocks(op.n);
   if (nb > num_sms() * per_sm[fmt]) nb = num_sms() * per_sm[fmt];
   EI_DISPATCH_FMT(fmt, (k_csr_newton<F_><<<nb, EI_TPB, 0, stm>>>(op, w_in, w_out, p, s, partials, ctl)));
+  return cudaGetLastError();
+}
+
+// batch sizes of the sliced kernel: entries a lane per batch
+constexpr int kSellU64 = 6, kSellU32 = 8;
+cudaError_t launch_csr_newton_sell(const SellDev& op, const void* w_in, void* w_out, void* p,
+                                   const NewtonScalars& s, int fmt, double* partials,
+                                   DevCtl* ctl, cudaStream_t stm) {
+  if (fmt == VF_DF)
+    k_csr_newton_sell<VF_DF, kSellU64><<<csr_sell_grid<VF_DF, kSellU64>(op.nslices), EI_TPB, 0,
+                                         stm>>>(op, w_in, w_out, p, s, partials, ctl);
+  else if (fmt == VF_F64)
+    k_csr_newton_sell<VF_F64, kSellU64><<<csr_sell_grid<VF_F64, kSellU64>(op.nslices), EI_TPB,
+                                          0, stm>>>(op, w_in, w_out, p, s, partials, ctl);
+  else
+    k_csr_newton_sell<VF_F32, kSellU32><<<csr_sell_grid<VF_F32, kSellU32>(op.nslices), EI_TPB,
+                                          0, stm>>>(op, w_in, w_out, p, s, partials, ctl);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_sell_gather(int64_t e, const int64_t* src, const int32_t* col,
+                               int32_t* col_out, const void* val, int val_prec, void* val_out,
+                               int fmt, cudaStream_t stm) {
+  const int nb = ew_blocks(e);
+  if (val_prec == EI_PREC_F32) {
+    EI_DISPATCH_FMT(fmt, (k_sell_gather<float, F_><<<nb, EI_TPB, 0, stm>>>(
+                             e, src, col, col_out, static_cast<const float*>(val), val_out)));
+  } else {
+    EI_DISPATCH_FMT(fmt, (k_sell_gather<double, F_><<<nb, EI_TPB, 0, stm>>>(
+                             e, src, col, col_out, static_cast<const double*>(val), val_out)));
+  }
   return cudaGetLastError();
 }
 

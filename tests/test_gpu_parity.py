@@ -255,12 +255,13 @@ def _irregular_graph(n, seed, hub_degree):
     return rowptr, col, val, deg
 
 
-@pytest.mark.parametrize("lanes", [0, 2, 4, 32])
+@pytest.mark.parametrize("lanes", [0, 1, 2, 4, 32])
 @pytest.mark.parametrize("n,hub", [(1000, 700), (20, 19), (33, 5)])
 def test_csr_irregular_rows(env, xi, n, hub, lanes):
     """Empty rows, a row longer than a chunk, warps whose entries span several
-    chunks, n below and not a multiple of 32; the one-lane kernel (0: the
-    default for these row lengths) and the 2-, 4- and 32-lane kernels."""
+    chunks, n below and not a multiple of 32; the sliced kernel (0, the
+    default: the hub pads its slice, empty rows end their windows) and the 1-,
+    2-, 4- and 32-lane kernels on the CSR arrays."""
     torch, ei = env
     rowptr, col, val, deg = _irregular_graph(n, 5 + n, hub)
     assert (np.diff(rowptr) == 0).any()
@@ -277,8 +278,9 @@ def test_csr_irregular_rows(env, xi, n, hub, lanes):
     st = ctx.phi_apply(1, h, v, out, 1e-10, {"csr_lanes": lanes})
     assert rel_err(out.cpu().numpy(), ref) <= FP64_TOL
     _check_stats(st, ost)
-    if lanes == 4:  # the native FP64 form of the same kernel
-        st = ctx.phi_apply(1, h, v, out, 1e-10, {"csr_lanes": 4, "arith": ei.ARITH_NATIVE_F64})
+    if lanes in (0, 4):  # the native FP64 form of the same kernel
+        st = ctx.phi_apply(1, h, v, out, 1e-10,
+                           {"csr_lanes": lanes, "arith": ei.ARITH_NATIVE_F64})
         assert rel_err(out.cpu().numpy(), ref) <= FP64_TOL
         _check_stats(st, ost)
 

@@ -204,7 +204,7 @@ def test_degenerate_and_errors(env, xi):
     sc.close()
 
 
-@pytest.mark.parametrize("lanes", [1, 2, 4, 8, 16, 32])
+@pytest.mark.parametrize("lanes", [0, 1, 2, 4, 8, 16, 32])
 def test_lanes_per_row_ragged(env, xi, lanes):
     """Every lanes-per-row variant of the complex CSR kernel on a graph with
     ragged rows (degrees from 0 up): H = W - diag(deg) of a random geometric
