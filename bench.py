@@ -60,16 +60,16 @@ SMS, FP64_FLOPS_PER_SM_CLK = 152, 4
 # traffic scales with the points.
 # Valid for the kernel as captured: retake it when the kernel changes.
 PAIR_DRAM_BYTES_PER_POINT = 86.9
-# the same for one launch of the native-FP64 one-iteration kernel, from ncu on
-# 192^3 (profiles/k_newton_tma_double_192cube.md)
-NATIVE_DRAM_BYTES_PER_POINT = 85.97
+# the same for one launch of the native-FP64 one-iteration kernel on the scaled
+# operator, from ncu on 192^3 (profiles/k_newton_tma_double_192cube.md)
+NATIVE_DRAM_BYTES_PER_POINT = 86.1
 # DRAM bytes of one launch of the float-float sliced complex CSR kernel on the
-# 21-spin operator (None: not captured for the kernel as it is)
-SPIN_DRAM_BYTES_PER_LAUNCH = None
+# 21-spin operator (profiles/k_csr_newton_sell_c_spin_bath_21.md)
+SPIN_DRAM_BYTES_PER_LAUNCH = 1.237e9
 # the same for the sliced real CSR kernel on the 2^20-node graph, float-float
-# and native FP64 (None: not captured for the kernel as it is)
-RGG_DRAM_BYTES_PER_LAUNCH = None
-RGG_DRAM_BYTES_PER_LAUNCH_F64 = None
+# and native FP64 (profiles/k_csr_newton_sell_rgg_2e20.md)
+RGG_DRAM_BYTES_PER_LAUNCH = 228.2e6
+RGG_DRAM_BYTES_PER_LAUNCH_F64 = 227.7e6
 FLOPS_PER_POINT_PAPER = 10  # the paper's count for (alpha A + beta I)x, Sec. III-A
 
 
@@ -85,7 +85,7 @@ def parse():
     # batch workloads: fixed tile height instead of the autotuner (profiling)
     ap.add_argument("--tile-rows", type=int, default=0, help=argparse.SUPPRESS)
     ap.add_argument("--workload", default="adr3d",
-                    choices=["adr3d", "adr3d_ff", "adr3d_fp32", "rgg_csr", "batch", "batch_fp32",
+                    choices=["adr3d", "adr3d_ff", "adr3d_fp32", "rgg_csr", "batch", "batch_ff", "batch_fp32",
                              "adr3d_learned", "adr3d_fp32_learned", "rgg_csr_learned",
                              "batch_learned_fp32", "batch_plain_fp64_loop", "combustion",
                              "combustion_fast", "combustion_nonlin", "heat_dirichlet_data",
@@ -667,17 +667,21 @@ class Batch2d(Workload):
     whole batch."""
 
     prec = 0
+    arith = 1  # FP64 batches: native FP64 (0: float-float)
 
     def __init__(self, torch, ei, W, dev, ctx, n, learned_opt=False):
-        self.name = "batch_1024_2d" + ("_fp32" if self.prec else "_fp64")
+        self.name = "batch_1024_2d" + ("_fp32" if self.prec else
+                                       "_fp64" if self.arith else "_float_float")
         self.method = "phi1 (batched, persistent kernel)"
-        self.dtype = "f32 (float-float Newton sum)" if self.prec else \
-            DTYPE_FF
+        self.dtype = ("f32 (float-float Newton sum)" if self.prec else
+                      "f64" if self.arith else DTYPE_FF)
         self.ei = ei
         probs = W.batch_2d(count=n)
         self.tol = 1e-6 if self.prec else 1e-10
         t0 = time.perf_counter()
         opts = {"tile_rows": TILE_ROWS} if TILE_ROWS else {}
+        if not self.prec and self.arith:
+            opts["arith"] = 1
         if learned_opt:
             opts["learned"] = 1  # plans come from the network at each pass
         self.batch = ei.Batch(probs, prec=self.prec, tol=self.tol, options=opts or None)
@@ -714,6 +718,10 @@ class Batch2d(Workload):
 
 class Batch2dFp32(Batch2d):
     prec = 1
+
+
+class Batch2dFF(Batch2d):
+    arith = 0
 
 
 class Batch2dLearnedFp32(Batch2d):
@@ -880,7 +888,7 @@ class RggCsrLearned(Learned, RggCsr):
         self.setup_learned(ctx)
 
 
-WORKLOADS = {"adr3d": Adr3d, "adr3d_ff": Adr3dFF, "adr3d_fp32": Adr3dFp32, "rgg_csr": RggCsr, "batch": Batch2d,
+WORKLOADS = {"adr3d": Adr3d, "adr3d_ff": Adr3dFF, "adr3d_fp32": Adr3dFp32, "rgg_csr": RggCsr, "batch": Batch2d, "batch_ff": Batch2dFF,
              "batch_fp32": Batch2dFp32, "adr3d_learned": Adr3dLearned,
              "adr3d_fp32_learned": Adr3dFp32Learned, "rgg_csr_learned": RggCsrLearned,
              "batch_learned_fp32": Batch2dLearnedFp32, "batch_plain_fp64_loop": Batch2dPlainLoop,
@@ -888,7 +896,7 @@ WORKLOADS = {"adr3d": Adr3d, "adr3d_ff": Adr3dFF, "adr3d_fp32": Adr3dFp32, "rgg_
              "combustion_nonlin": NonlinEval, "heat_dirichlet_data": HeatDirichlet,
              "heat_dirichlet_hom": HeatDirichletHom, "phi2_adr3d": PhiKAdr3d,
              "spin_bath": SpinBath, "spin_bath_fp32": SpinBathFp32}
-DEFAULT_N = {"adr3d": N_SIDE, "adr3d_ff": N_SIDE, "adr3d_fp32": 512, "rgg_csr": 1 << 20, "batch": 1024,
+DEFAULT_N = {"adr3d": N_SIDE, "adr3d_ff": N_SIDE, "adr3d_fp32": 512, "rgg_csr": 1 << 20, "batch": 1024, "batch_ff": 1024,
              "batch_fp32": 1024, "adr3d_learned": N_SIDE, "adr3d_fp32_learned": 512,
              "rgg_csr_learned": 1 << 20, "batch_learned_fp32": 1024,
              "batch_plain_fp64_loop": 1024, "combustion": N_SIDE, "combustion_fast": N_SIDE,

@@ -1687,6 +1687,9 @@ static ei_status step_impl(ei_ctx* c, int method, double h, void* u, int nonlin,
   int is_p = 0;
   double scale = 1.0;
   c->vnorm2 = fnorm2;
+  // the scaled operator of the native Newton kernel goes out now, so the device
+  // makes it while the host works out the schedule
+  if (wants_prescale(c, P) && !use_pair(c, P)) EI_TRY(ensure_prescaled(c, P, qc, cc, gamma));
   EI_TRY(phi1_substeps(c, P, qc, h, alpha, beta, tol, opt, st, &res, &is_p, &scale));
   EI_LAUNCH(launch_add_export(u, c->prec, res, fmt, is_p, n, geo_nx(c), c->kind == KIND_STENCIL ? c->sd.ny : 1, geo_pitch(c), scale, c->stream, dst));
   EI_TRY_CUDA(cudaStreamSynchronize(c->stream));

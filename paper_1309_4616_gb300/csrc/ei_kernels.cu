@@ -268,6 +268,9 @@ k_stencil_F(StencilDev g, const void* __restrict__ u_, void* __restrict__ F_,
   const T one = from_d<T>(1.0), mtwo = from_d<T>(-2.0);
   const int64_t n = (int64_t)g.nx * g.ny * g.nz;
   T af = zero<T>();
+  // two points a thread per pass: the second point's loads can go out before
+  // the first point's stores (all arrays are restrict-qualified)
+#pragma unroll 2
   for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;
        i += (int64_t)gridDim.x * blockDim.x) {
     int x, y, z;

@@ -40,8 +40,11 @@ struct TmaCfg {
   // SM and keep its FP64 pipe busy across the per-plane barriers.
   static constexpr int PF = FMT == VF_F64 ? 2 : 4;
   static constexpr int MINB = FMT == VF_F64 ? 3 : 2;  // resident blocks per SM
-  static constexpr int NW = PF + 2;     // w ring: planes z-1, z, z+1 resident + PF in flight
-  static constexpr int NC = PF + 1;     // coefficient/p ring: plane z resident + PF in flight
+  // planes per block barrier: a ring one slot deeper per extra plane lets a
+  // thread lag the issuing thread by that many planes
+  static constexpr int SYNC = 1;
+  static constexpr int NW = PF + 1 + SYNC;  // w ring: planes z-1, z, z+1 + PF in flight
+  static constexpr int NC = PF + SYNC;      // coefficient/p ring: plane z + PF in flight
   static constexpr int NBAR = 8;        // one mbarrier per plane, reused every 8 planes
   static constexpr int HX = 16 / (int)sizeof(T);  // x halo, rounded to 16 bytes
   static constexpr int WX = TX + 2 * HX, WY = TY + 2;
@@ -196,7 +199,7 @@ k_newton_tma(const __grid_constant__ NewtonMaps M, const StencilDev g, const New
   for (int q = 1; q <= nplanes - 2; ++q) {
     if (tid == 0 && q + C::PF < nplanes) {
       fence_proxy_async();
-      issue(q + C::PF);  // into the w slot of plane q-2 and the coefficient slot of q-1
+      issue(q + C::PF);  // into the slots of planes q+PF-NW (w) and q+PF-NC (coefficients)
     }
     if (q == 1) {
       if (!bad) bad = !wait(0);
@@ -227,7 +230,7 @@ k_newton_tma(const __grid_constant__ NewtonMaps M, const StencilDev g, const New
       aw = acc_sq(aw, wn);
       ap = acc_sq(ap, pn);
     }
-    if (__syncthreads_or(bad)) {
+    if ((q % C::SYNC == 0 || q == nplanes - 2) && __syncthreads_or(bad)) {
       bad = true;
       break;
     }

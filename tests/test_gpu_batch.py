@@ -57,12 +57,13 @@ def _unpack(out, offsets, i):
     return out[offsets[i]:offsets[i + 1]]
 
 
-@pytest.mark.parametrize("prec", [0, 1])
-def test_batch_vs_oracle(env, xi, prec):
+@pytest.mark.parametrize("prec,arith", [(0, 0), (0, 1), (1, 0)],
+                         ids=["float_float", "native_f64", "f32"])
+def test_batch_vs_oracle(env, xi, prec, arith):
     torch, ei = env
     probs = _small_batch(11 + prec, 48)
     tol = 1e-10 if prec == 0 else 1e-6
-    b = ei.Batch(probs, prec=prec, tol=tol)
+    b = ei.Batch(probs, prec=prec, tol=tol, options={"arith": arith})
     dt = torch.float64 if prec == 0 else torch.float32
     v = _pack(torch, probs, dt)
     out = torch.empty_like(v)
