@@ -45,6 +45,8 @@ BYTES_PER_POINT = 88
 # as its inputs (D 8, b 24, u_n for g' 8).  The library stores the seven
 # coefficients instead (BYTES_PER_POINT).
 ALG_BYTES_PER_POINT = 72
+# the same for a constant-coefficient operator (w 8, w' 8, p 16)
+CONST_BYTES_PER_POINT = 32
 # FP64 flops of one Newton iteration per grid point (a fused multiply-add counts
 # two), on the scaled operator (A - cI)/gamma the native kernel iterates with:
 # the 7-point product (7 multiplies, 6 adds), the shift -xi_j w (1 multiply, 1
@@ -314,8 +316,11 @@ class Adr3dFp32(Adr3d):
         self.state0 = torch.from_numpy(w.u0).to(dev, f32)
         self.state = self.state0.clone()
         self.host0 = w.u0.astype(np.float32)
-        # w 4 + w' 4 + p 8+8 + 7 coefficients x 4
-        self.bytes_per_point = 52
+        # per point-iteration as the scope counts it: w 4 + w' 4 + p 16 + the
+        # operator as its inputs (D 4 + b 12); the library stores the seven
+        # coefficients instead (52 B: bytes_per_point_stored)
+        self.bytes_per_point = 40
+        self.bytes_per_point_stored = 52
         self.config = {"grid": [n] * 3, "h": w.h, "tol": w.tol, "bc": "neumann",
                        "method": self.method}
 
@@ -353,7 +358,10 @@ class Combustion3d(Adr3d):
         self.state0 = torch.from_numpy(w.u0).to(dev)
         self.state = self.state0.clone()
         self.host0 = w.u0
-        self.bytes_per_point = BYTES_PER_POINT
+        # constant coefficients: the scope's count is w 8 + w' 8 + p 16; the
+        # library streams its seven stored coefficient arrays all the same
+        self.bytes_per_point = CONST_BYTES_PER_POINT
+        self.bytes_per_point_stored = BYTES_PER_POINT
         self.nonlin = ei.NONLIN_COMBUSTION_FAST if self.fast else ei.NONLIN_COMBUSTION
         self.config = {"grid": [n] * 3, "h": w.h, "tol": w.tol, "bc": "dirichlet0",
                        "method": self.method, "u0": 1.0,
@@ -405,7 +413,8 @@ class HeatDirichlet(Adr3d):
         self.state0 = torch.from_numpy(u0).to(dev)
         self.state = self.state0.clone()
         self.host0 = u0
-        self.bytes_per_point = BYTES_PER_POINT
+        self.bytes_per_point = CONST_BYTES_PER_POINT
+        self.bytes_per_point_stored = BYTES_PER_POINT
         self.config = {"grid": [n] * 3, "h": w.h, "tol": w.tol, "bc": "dirichlet",
                        "boundary_data": kind, "method": self.method,
                        "u0": "sin(pi x) sin(pi y) sin(pi z)"}
@@ -578,6 +587,8 @@ class PhiKAdr3d(Adr3d):
         self.name, self.method = f"adr3d_{n}_phi{self.k}_substeps", f"phi_{self.k}(hA)v"
         self.h = 5e-4
         self.out = torch.empty_like(self.state)
+        self.bytes_per_point = ALG_BYTES_PER_POINT
+        self.bytes_per_point_stored = BYTES_PER_POINT
         self.config = {"grid": [n] * 3, "h": self.h, "tol": self.w.tol, "k": self.k,
                        "bc": "neumann", "method": self.method}
 
@@ -1003,6 +1014,11 @@ def roofline(wl, r, args, npts):
            "us_per_iteration": avg_launch_s * 1e6 / fused,
            "peak_kind": peak_kind,
            "paper_gflops": FLOPS_PER_POINT_PAPER * npts * fused / avg_launch_s / 1e9}
+    stored = getattr(wl, "bytes_per_point_stored", None)
+    if stored:
+        out["bytes_per_point"] = wl.bytes_per_point
+        out["bytes_per_point_stored"] = stored
+        out["frac_stored"] = stored * npts / avg_launch_s / 1e9 / hbm
     if type(wl).__name__ in ("RggCsr", "RggCsrLearned") and wl.arith:
         # native FP64: the HBM bound and the FP64-pipe bound (2 flops an entry,
         # 12 a row: the update, the Newton sum and two squared norms) are close;

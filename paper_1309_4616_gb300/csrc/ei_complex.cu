@@ -372,9 +372,10 @@ static cudaError_t csr_newton_c_fmt(const CsrDev& op, int lanes, const void* w_i
 // operators whose rows share a structure (the spin-bath Hamiltonian: column q
 // of row i is i XOR mask_q) the gathers of a slice's entry k fall in one
 // aligned block of 32 rows: whole lines.
-constexpr int kSellCMinB = 4;  // resident blocks per SM the register budget targets
+// (a register cap for four blocks a SM measured slower: 263.7 against 255.8
+// us float-float, 155.5 against 145.4 FP32, on the 21-spin bath)
 template <int FMT, int U = (FMT == VF_F32 ? 8 : 4)>
-__global__ void __launch_bounds__(EI_TPB, kSellCMinB)
+__global__ void __launch_bounds__(EI_TPB)
 k_csr_newton_sell_c(SellDev op, const void* __restrict__ w_in_, void* __restrict__ w_out_,
                     void* __restrict__ p_, NewtonScalars s, double* partials, DevCtl* ctl) {
   static_assert(U % 2 == 0, "batches accumulate entries in pairs");

@@ -333,11 +333,42 @@ __device__ __forceinline__ void comb(double& a, double& b, double a2, double b2)
 }
 
 // Reduce (a, b) over the block; result valid in thread 0.  Fixed order.
+// Blocks of 256 threads first halve through shared memory (128, 64, then 32
+// threads add), then one warp finishes by shuffles: about 12 warp-wide adds a
+// value instead of 45 for eight warps of shuffles, which matters on GB300's
+// narrow FP64 pipe.  Other block sizes shuffle in every warp.
 template <int OP>
 __device__ __forceinline__ void block_reduce2(double& a, double& b) {
-  __shared__ double sa[32], sb[32];
+  __shared__ double sa[256], sb[256];
   const int tid = threadIdx.x + blockDim.x * (threadIdx.y + blockDim.y * threadIdx.z);
   const int nthr = blockDim.x * blockDim.y * blockDim.z;
+  if (nthr == 256) {
+    sa[tid] = a;
+    sb[tid] = b;
+    __syncthreads();
+#pragma unroll
+    for (int h = 128; h >= 32; h >>= 1) {
+      if (tid < h) {
+        double a2 = sa[tid + h], b2 = sb[tid + h];
+        comb<OP>(a, b, a2, b2);
+        if (h > 32) {
+          sa[tid] = a;
+          sb[tid] = b;
+        }
+      }
+      if (h > 32) __syncthreads();
+    }
+    if (tid < 32) {
+#pragma unroll
+      for (int off = 16; off > 0; off >>= 1) {
+        double a2 = __shfl_down_sync(0xffffffffu, a, off);
+        double b2 = __shfl_down_sync(0xffffffffu, b, off);
+        comb<OP>(a, b, a2, b2);
+      }
+    }
+    __syncthreads();
+    return;
+  }
   const int lane = tid & 31, wid = tid >> 5;
 #pragma unroll
   for (int off = 16; off > 0; off >>= 1) {

@@ -1058,10 +1058,26 @@ k_csr_newton_sell(SellDev op, const void* __restrict__ w_in_, void* __restrict__
       }
 #pragma unroll
       for (int u = 0; u < U; ++u) xv[u] = c[u] >= 0 ? ldg(w_in, c[u]) : zero<T>();
+      if constexpr (FMT == VF_F64) {
+        // native FP64: the FP64 pipe bounds this kernel and an issued
+        // multiply-add costs the same whether its lanes are active or not, so
+        // the slots past the slice's length (a warp-uniform count) are skipped
+        // by a branch, not predicated (padding inside the length has value 0)
+        static_assert(U == 6, "the fall-through below covers batches of 6");
+        switch (len - k < U ? len - k : U) {
+          case 6: a2 = lmac(a2, v[5], xv[5]); [[fallthrough]];
+          case 5: a1 = lmac(a1, v[4], xv[4]); [[fallthrough]];
+          case 4: a2 = lmac(a2, v[3], xv[3]); [[fallthrough]];
+          case 3: a1 = lmac(a1, v[2], xv[2]); [[fallthrough]];
+          case 2: a2 = lmac(a2, v[1], xv[1]); [[fallthrough]];
+          default: a1 = lmac(a1, v[0], xv[0]);
+        }
+      } else {
 #pragma unroll
-      for (int u = 0; u + 1 < U; u += 2) {
-        if (FMT == VF_F32 || c[u] >= 0) a1 = lmac(a1, v[u], xv[u]);
-        if (FMT == VF_F32 || c[u + 1] >= 0) a2 = lmac(a2, v[u + 1], xv[u + 1]);
+        for (int u = 0; u + 1 < U; u += 2) {
+          if (FMT == VF_F32 || c[u] >= 0) a1 = lmac(a1, v[u], xv[u]);
+          if (FMT == VF_F32 || c[u + 1] >= 0) a2 = lmac(a2, v[u + 1], xv[u + 1]);
+        }
       }
     }
     if (row >= 0) {
