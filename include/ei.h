@@ -149,7 +149,10 @@ typedef struct {
   int arith_used;       /* EI_ARITH_* the Newton iteration ran in (F64 operators;
                            a float-float call outside the format's range runs
                            in native FP64) */
-  int pad_end;
+  int p_rechecks;       /* native FP64 stencils: Newton steps far below the
+                           a-priori degree skip forming ||p||, a bound decides
+                           their stop tests; steps where the bound could not
+                           decide and the host formed ||p|| to take the test */
 } ei_stats;
 
 /* Create a context on CUDA device `device`, ordering work on `cuda_stream`

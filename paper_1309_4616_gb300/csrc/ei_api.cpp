@@ -137,6 +137,7 @@ struct ei_ctx {
   int newton_timed = 0;
   double newton_ms = 0.0;
   int newton_fused = 1;
+  int p_rechecks = 0;      // stop tests the host took with ||p|| formed (bound undecided)
   int fuse = 0;            // Newton iterations per stencil launch: 0 the format's
                            // default (two for float-float and float, one for native
                            // FP64), 1 one, 2 two
@@ -474,10 +475,27 @@ static ei_status newton_loop(ei_ctx* c, Prepared& P, const void* qc, const void*
   const bool pair = use_pair(c, P);
   const bool pre = !pair && !cx && wants_prescale(c, P);
   if (pre) EI_TRY(ensure_prescaled(c, P, qc, cc, gamma));
+  // Native FP64 steps well before the predicted degree do not form ||p||: the
+  // bound ||p_j|| + |d_{j+1}| ||w_{j+1}|| proves their stop tests fail (the
+  // FP64 pipe bounds the kernel, and this saves an FMA a point).  From 8 steps
+  // before the a-priori degree on, every step forms it.
+  int pb_until = (pre && m_pred > 9) ? m_pred - 8 : 0;
   int lj[128];          // first iteration index of each launch
   bool l2[128];         // whether that launch did two iterations
   int j = 0, nl = 0;
   int batch = m_pred > 0 ? m_pred : 8;
+  auto account = [&](int dg) -> ei_status {  // launches that started below dg did the work
+    if (!c->profile) return EI_OK;
+    for (int i = 0; i < nl; ++i) {
+      if (lj[i] >= dg && !(i == 0 && dg == 0)) continue;
+      float ms = 0.f;
+      EI_TRY_CUDA(cudaEventElapsedTime(&ms, c->ev[2 * i], c->ev[2 * i + 1]));
+      c->newton_ms += ms;
+      ++c->newton_timed;
+    }
+    c->newton_fused = pair ? 2 : 1;
+    return EI_OK;
+  };
   while (true) {
     const int jend = (j + batch < m_max) ? j + batch : m_max;
     while (j < jend) {
@@ -486,6 +504,7 @@ static ei_status newton_loop(ei_ctx* c, Prepared& P, const void* qc, const void*
       s.d_next = d[j + 1];
       s.shift = cc / gamma + xi[j];
       s.xi = xi[j];
+      s.pbound = (pre && j >= 1 && j + 1 < pb_until) ? 1 : 0;
       if (two) {
         s.d_next2 = d[j + 2];
         s.shift2 = cc / gamma + xi[j + 1];
@@ -528,17 +547,39 @@ static ei_status newton_loop(ei_ctx* c, Prepared& P, const void* qc, const void*
           if (l2[i] && lj[i] == *deg - 1)
             EI_LAUNCH(launch_p_fixup(P.p, P.w[i & 1], P.fmt, P.n_alloc, d[*deg + 1], c->stream));
       }
-      if (c->profile) {  // launches that started below the degree did the work
-        for (int i = 0; i < nl; ++i) {
-          if (lj[i] >= *deg && !(i == 0 && *deg == 0)) continue;
-          float ms = 0.f;
-          EI_TRY_CUDA(cudaEventElapsedTime(&ms, c->ev[2 * i], c->ev[2 * i + 1]));
-          c->newton_ms += ms;
-          ++c->newton_timed;
-        }
-        c->newton_fused = pair ? 2 : 1;
+      return account(*deg);
+    }
+    if (done == 6) {
+      // the bound of ||p|| could not decide at degree dg: form ||p_dg|| and
+      // take the test as the other steps do; on a fail go on from dg with
+      // ||p|| formed in every step
+      const int dg = c->h_ctl->degree;
+      const double nw2 = c->h_ctl->nw2;
+      ++c->p_rechecks;
+      EI_LAUNCH(launch_p_sqnorm(P.p, P.fmt, P.n_alloc, c->partials, c->ctl, c->stream));
+      EI_TRY(read_ctl(c));
+      const double np2 = c->h_ctl->sum0;
+      if (!isfinite(np2)) return EI_ERR_NONFINITE;
+      if (fabs(d[dg]) * sqrt(nw2) <= tol * sqrt(np2)) {
+        *deg = dg;
+        *ok = 1;
+        return account(dg);
       }
-      return EI_OK;
+      if (dg >= m_max) {
+        *deg = m_max;
+        *ok = 0;
+        return account(dg);
+      }
+      int made = -1;  // the launch that made degree dg; later ones exited at once
+      for (int i = 0; i < nl; ++i)
+        if (lj[i] == dg - 1) made = i;
+      if (made < 0) return EI_ERR_STATE;
+      nl = made + 1;
+      j = dg;
+      pb_until = 0;
+      EI_TRY(reset_done(c));
+      batch = 8;
+      continue;
     }
     if (done == 4) return EI_ERR_NONFINITE;
     if (done == 5) return EI_ERR_TIMEOUT;
@@ -1280,6 +1321,7 @@ static void acct_begin(ei_ctx* c, const ei_options* opt) {
   c->newton_timed = 0;
   c->newton_ms = 0.0;
   c->newton_fused = 1;
+  c->p_rechecks = 0;
   c->profile = opt && opt->profile;
   c->fuse = opt ? opt->single_iter : 0;
   c->csr_lanes = opt ? opt->csr_lanes : 0;
@@ -1291,6 +1333,7 @@ static void acct_end(ei_ctx* c, ei_stats* st) {
   st->newton_timed = c->newton_timed;
   st->newton_ms = c->newton_ms;
   st->newton_fused = c->newton_fused;
+  st->p_rechecks = c->p_rechecks;
 }
 
 static ei_status phi_apply_impl(ei_ctx* c, int k, double h, const void* v, void* out, double tol,

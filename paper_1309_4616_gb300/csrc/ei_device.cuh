@@ -54,7 +54,7 @@ __device__ __forceinline__ double to_p(double x) { return x; }
 __device__ __forceinline__ bool finite_d(double x) { return isfinite(x); }
 
 // Verdict after the Newton step reaching degree `deg`, with squared norms nw2
-// of w_deg and np2 of p_deg and coefficient d = d_deg.  Adaptive mode: stop
+// of w_deg and np2 of p_deg (not formed when s.pbound) and coefficient d = d_deg.  Adaptive mode: stop
 // at the first degree whose estimate |d| ||w|| <= tol ||p|| holds (done = 1),
 // or at m_max (done = 2).  Fixed-count mode: only deg == m_max is judged, and
 // a failed check also counts into ctl->fixfail.  Non-finite norms stop with
@@ -82,6 +82,25 @@ __device__ __forceinline__ bool newton_verdict(DevCtl* ctl, const NewtonScalars&
     return true;
   }
   if (s.fixed && !last) return false;
+  if (s.pbound) {
+    // ||p_deg|| was not formed.  ||p_deg|| <= ||p_{deg-1}|| + |d| ||w_deg||, so an
+    // estimate above tol times that bound (with a 1e-9 margin for the rounding
+    // of both sides) fails the test for certain; otherwise the host forms
+    // ||p_deg|| and takes the test (done = 6)
+    const double e = fabs(d) * sqrt(nw2);
+    const double ub = ctl->pub + e;
+    ctl->pub = ub;
+    if (e > s.tol * ub * (1.0 + 1e-9)) {
+      if (!last) return false;
+      ctl->done = 2;
+      ctl->degree = deg;
+      return true;
+    }
+    ctl->done = 6;
+    ctl->degree = deg;
+    return true;
+  }
+  ctl->pub = sqrt(np2);
   if (fabs(d) * sqrt(nw2) <= s.tol * sqrt(np2)) {
     ctl->done = 1;
     ctl->degree = deg;

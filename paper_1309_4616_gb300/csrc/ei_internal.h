@@ -17,7 +17,9 @@ enum VecFmt { VF_DF = 0, VF_F64 = 1, VF_F32 = 2 };
 struct DevCtl {
   unsigned int count;  // arrivals of the current launch (reset by its last block)
   int done;            // Newton: 0 running, 1 converged, 2 m_max reached,
-                       //         4 non-finite, 5 a bounded device wait ran out
+                       //         4 non-finite, 5 a bounded device wait ran out,
+                       //         6 the bound of ||p|| could not decide (host takes
+                       //         the test with ||p|| formed)
   int degree;          // Newton degree at stop
   int err;             // set by a block whose bounded wait ran out
   int fixup;           // two-iteration kernel stopped at its first iteration: p holds
@@ -31,6 +33,8 @@ struct DevCtl {
   double nw2, np2;     // squared norms of the last Newton iterate / sum
   double cs_sum, cs_max, cs_pe;  // coefficient statistics (launch_coef_stats)
   double vmax;         // import: largest magnitude of the imported vector (exact)
+  double pub;          // Newton: an upper bound of ||p|| after the last step (exact
+                       // where that step formed ||p||, see NewtonScalars::pbound)
 };
 
 // Grid geometry of the stencil operator.  Library-owned arrays are stored
@@ -91,6 +95,9 @@ struct NewtonScalars {
   double d_next_im;    // complex Newton sum (k_csr_newton_c): Im d_{j+1}
   double d0_im;        //   and Im d_0
   double xi;           // the Leja point xi_j (kernels on the scaled operator)
+  int pbound;          // 1: this step does not form ||p_{j+1}||; the stop test uses
+                       //    the bound ctl->pub + |d_{j+1}| ||w_{j+1}|| and reports
+                       //    done = 6 where that bound cannot decide
 };
 
 // Tensor maps of the TMA-staged Newton kernel (3D maps over the padded
@@ -207,6 +214,9 @@ cudaError_t launch_csr_residual(const CsrDev& op, const void* y, const void* v, 
 cudaError_t launch_newton_tma(const StencilDev& op, const NewtonMaps& M, void* w_out, void* p,
                               const NewtonScalars& s, int fmt, double* partials, DevCtl* ctl,
                               cudaStream_t st, bool prescaled = false);
+// ||x||^2 of n_alloc elements of a Newton sum (format fmt) into ctl->sum0
+cudaError_t launch_p_sqnorm(const void* x, int fmt, int64_t n_alloc, double* partials,
+                            DevCtl* ctl, cudaStream_t st);
 // the scaled operator of the native FP64 Newton kernel, elementwise over the
 // padded arrays: sa[k] = a[k] / gamma (k < 6), sa[6] = (diag - c) / gamma
 cudaError_t launch_prescale(void* const sa[7], const void* const a[6], const void* diag,

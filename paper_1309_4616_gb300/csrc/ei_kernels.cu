@@ -1494,6 +1494,29 @@ cudaError_t launch_prescale(void* const sa[7], const void* const a[6], const voi
   return cudaGetLastError();
 }
 
+template <class P>
+__global__ void __launch_bounds__(EI_TPB)
+k_p_sqnorm(const P* __restrict__ x, int64_t n, double* partials, DevCtl* ctl) {
+  typename Acc<P>::type a = Acc<P>::zero();
+  for_points_k<EW_K>(
+      n, (int)1, (int)1, [&](int64_t i, int64_t) { return ldg(x, i); },
+      [&](int64_t, int64_t, P v) { a = acc_sq(a, v); });
+  double s0 = acc_d(a), s1 = 0.0;
+  if (last_block_reduce2<RED_SUM>(s0, s1, partials, ctl)) {
+    if (threadIdx.x == 0) ctl->sum0 = s0;
+  }
+}
+
+cudaError_t launch_p_sqnorm(const void* x, int fmt, int64_t n, double* partials, DevCtl* ctl,
+                            cudaStream_t stm) {
+  const int nb = ew_blocks(n);
+  if (fmt == VF_F64)
+    k_p_sqnorm<double><<<nb, EI_TPB, 0, stm>>>(static_cast<const double*>(x), n, partials, ctl);
+  else
+    k_p_sqnorm<df><<<nb, EI_TPB, 0, stm>>>(static_cast<const df*>(x), n, partials, ctl);
+  return cudaGetLastError();
+}
+
 cudaError_t launch_zero(void* x, int fmt, int64_t n, cudaStream_t stm) {
   const int nb = ew_blocks(n);
   EI_DISPATCH_FMT(fmt, (k_zero<F_><<<nb, EI_TPB, 0, stm>>>(x, n)));

@@ -122,7 +122,9 @@ static constexpr uint64_t kWaitLimitNs = 500000000ull;  // 0.5 s; a plane lands 
 // FP64 only), so w_{j+1} = (A w_j - c w_j)/gamma - xi_j w_j is the 7-point sum
 // and one FMA with -xi_j: the FP64 pipe bounds this kernel, and the scaling
 // saves it a multiply per point.
-template <int FMT, bool PRE>
+// PN: form ||p_{j+1}||^2 (false only with s.pbound: the stop test then uses
+// a bound, and the FP64-bound native kernel saves an FMA a point)
+template <int FMT, bool PRE, bool PN = true>
 __global__ void __launch_bounds__(256, TmaCfg<FMT>::MINB)
 k_newton_tma(const __grid_constant__ NewtonMaps M, const StencilDev g, const NewtonScalars s,
              void* __restrict__ w_out_, void* __restrict__ p_, double* partials, DevCtl* ctl,
@@ -228,7 +230,7 @@ k_newton_tma(const __grid_constant__ NewtonMaps M, const StencilDev g, const New
       st(w_out, idx, wn);
       st(p, idx, pn);
       aw = acc_sq(aw, wn);
-      ap = acc_sq(ap, pn);
+      if (PN) ap = acc_sq(ap, pn);
     }
     if ((q % C::SYNC == 0 || q == nplanes - 2) && __syncthreads_or(bad)) {
       bad = true;
@@ -614,21 +616,22 @@ static int tma_zchunk_single(const StencilDev& g) {
   return zc;
 }
 
-template <int FMT, bool PRE>
+template <int FMT, bool PRE, bool PN = true>
 static cudaError_t launch_one(const StencilDev& g, const NewtonMaps& M, void* w_out, void* p,
                               const NewtonScalars& s, double* partials, DevCtl* ctl,
                               cudaStream_t st) {
   using C = TmaCfg<FMT>;
   static bool attr = false;
   if (!attr) {
-    cudaError_t e = cudaFuncSetAttribute(k_newton_tma<FMT, PRE>,
+    cudaError_t e = cudaFuncSetAttribute(k_newton_tma<FMT, PRE, PN>,
                                          cudaFuncAttributeMaxDynamicSharedMemorySize, C::SMEM);
     if (e != cudaSuccess) return e;
     attr = true;
   }
   const int zc = tma_zchunk_single(g);
   dim3 grid((g.nx + 31) / 32, (g.ny + 7) / 8, (g.nz + zc - 1) / zc), block(32, 8, 1);
-  k_newton_tma<FMT, PRE><<<grid, block, C::SMEM, st>>>(M, g, s, w_out, p, partials, ctl, zc);
+  k_newton_tma<FMT, PRE, PN><<<grid, block, C::SMEM, st>>>(M, g, s, w_out, p, partials, ctl,
+                                                           zc);
   return cudaGetLastError();
 }
 
@@ -637,6 +640,8 @@ cudaError_t launch_newton_tma(const StencilDev& g, const NewtonMaps& M, void* w_
                               cudaStream_t st, bool prescaled) {
   if (fmt == VF_DF) return launch_one<VF_DF, false>(g, M, w_out, p, s, partials, ctl, st);
   if (fmt == VF_F64) {
+    if (prescaled && s.pbound)
+      return launch_one<VF_F64, true, false>(g, M, w_out, p, s, partials, ctl, st);
     if (prescaled) return launch_one<VF_F64, true>(g, M, w_out, p, s, partials, ctl, st);
     return launch_one<VF_F64, false>(g, M, w_out, p, s, partials, ctl, st);
   }

@@ -464,3 +464,33 @@ def test_step_host_paths_match_device(env, method):
     ctx.step_host(m, 3e-4, pageable, ei.NONLIN_LOGISTIC, 1e-10)
     assert np.array_equal(pinned.numpy(), ref) and np.array_equal(pageable.numpy(), ref)
     ctx.close()
+
+
+def test_native_p_bound_rechecks(env, xi):
+    """Native FP64 stencil steps well before the a-priori degree skip forming
+    ||p|| and decide their stop tests by the bound ||p_j|| + |d| ||w||.  With a
+    smooth v the a posteriori degree (55) falls below the a-priori one (65), so
+    the bound meets an undecidable test and the host takes it with ||p|| formed:
+    the result, the degree and the substep count must still be the oracle's."""
+    torch, ei = env
+    n = (37, 29, 21)
+    shape = (21, 29, 37)
+    dx = (1 / 37,) * 3
+    z, y, x = np.meshgrid(*(np.arange(k) + 0.5 for k in shape), indexing="ij")
+    D = 1 + 0.3 * np.sin(np.pi * x / 37) * np.cos(np.pi * y / 29)
+    v0 = np.cos(np.pi * x / 37) * np.cos(np.pi * y / 29) + 0.5 * np.cos(np.pi * z / 21)
+    op = O.StencilOperator(n, dx, D, (0.0, 0.0, 0.0), bc=(O.NEUMANN0,) * 6)
+    h, tol = 1e-2, 1e-10
+    ref, ost = Nw.phi_apply(op, 1, h, v0, tol, xi=xi)
+    assert ost.m_sched - ost.degrees[0] >= 8
+    ctx = stencil_context(torch, ei, n, dx, D, (0.0, 0.0, 0.0), 0.0, (1,) * 6)
+    v = dev(torch, v0)
+    out = torch.empty_like(v)
+    st = ctx.phi_apply(1, h, v, out, tol, {"arith": ei.ARITH_NATIVE_F64})
+    assert st.p_rechecks >= 1 and st.arith_used == ei.ARITH_NATIVE_F64
+    assert rel_err(out.cpu().numpy(), ref) <= FP64_TOL
+    _check_stats(st, ost)
+    st = ctx.phi_apply(1, h, v, out, tol, {"arith": ei.ARITH_DF})
+    assert st.p_rechecks == 0
+    assert rel_err(out.cpu().numpy(), ref) <= FP64_TOL
+    _check_stats(st, ost)
