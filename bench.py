@@ -53,6 +53,8 @@ CONST_BYTES_PER_POINT = 32
 # add), the Newton sum (1 multiply, 1 add) and the two squared norms
 # (2 multiplies, 2 adds).
 FP64_FLOPS_PER_POINT = 21
+# the same for an iteration in the p-norm bound mode (no squared norm of p)
+FP64_FLOPS_PER_POINT_BOUNDED = 19
 # GB300's FP64 peak from unit counts and clocks: the nominal 1.25 TFLOP/s over
 # 152 SMs at 2070 MHz is 4 FP64 flops (two FMA lanes) per SM and clock.
 SMS, FP64_FLOPS_PER_SM_CLK = 152, 4
@@ -971,14 +973,16 @@ def timed_steps(wl, ctx, args, torch, dev, stream, dist, local):
     # the dominant kernel: per-launch CUDA events around every Newton launch of
     # two further steps (profile option), same stream, same sizes
     wl.state_reset()
-    prof_ms, prof_n, fused, prof_bytes = 0.0, 0, 1, 0.0
+    prof_ms, prof_n, fused, prof_bytes, prof_nb = 0.0, 0, 1, 0.0, 0
     for _ in range(2):
         st = wl.step(ctx, {"profile": 1})
         prof_ms += st.newton_ms
         prof_n += st.newton_timed
+        prof_nb += getattr(st, "newton_bounded", 0)
         fused = st.newton_fused
         prof_bytes += getattr(st, "timed_bytes", 0.0)
-    r.update(prof_ms=prof_ms, prof_n=prof_n, fused=fused, prof_bytes=prof_bytes, last=st)
+    r.update(prof_ms=prof_ms, prof_n=prof_n, fused=fused, prof_bytes=prof_bytes, last=st,
+             prof_bounded=prof_nb)
     return r
 
 
@@ -1055,12 +1059,17 @@ def roofline(wl, r, args, npts):
             # native FP64: bound by the FP64 pipe (min of the two rooflines)
             sm_mhz = peaks_sm_mhz()
             fpk = SMS * FP64_FLOPS_PER_SM_CLK * sm_mhz * 1e6 / 1e12
-            tf = FP64_FLOPS_PER_POINT * npts * fused / avg_launch_s / 1e12
-            t_alu = FP64_FLOPS_PER_POINT * npts * fused / (fpk * 1e12)
+            # launches in the p-norm bound mode skip the squared norm of p
+            nb = r.get("prof_bounded", 0)
+            fpp = (FP64_FLOPS_PER_POINT * (prof_n - nb)
+                   + FP64_FLOPS_PER_POINT_BOUNDED * nb) / max(prof_n, 1)
+            tf = fpp * npts * fused / avg_launch_s / 1e12
+            t_alu = fpp * npts * fused / (fpk * 1e12)
             t_hbm = ALG_BYTES_PER_POINT * npts * fused / (hbm * 1e9)
             out.update({"bound": "alu" if t_alu >= t_hbm else "hbm", "achieved": tf,
                         "peak": fpk, "unit": "TFLOP/s", "frac": tf / fpk, "traffic": traffic,
-                        "alu": "FP64 pipe", "flops_per_point": FP64_FLOPS_PER_POINT,
+                        "alu": "FP64 pipe", "flops_per_point": fpp,
+                        "launches_bounded": nb,
                         "peak_kind": f"derived: {SMS} SMs x {FP64_FLOPS_PER_SM_CLK} FP64 "
                                      f"flop/clk x {sm_mhz:.0f} MHz",
                         "t_alu_us": t_alu * 1e6, "t_hbm_us": t_hbm * 1e6, "hbm": hb})

@@ -153,6 +153,9 @@ typedef struct {
                            a-priori degree skip forming ||p||, a bound decides
                            their stop tests; steps where the bound could not
                            decide and the host formed ||p|| to take the test */
+  int newton_bounded;   /* of the newton_timed launches, those that did not
+                           form ||p|| (the bound above decided their tests) */
+  int pad_end;
 } ei_stats;
 
 /* Create a context on CUDA device `device`, ordering work on `cuda_stream`

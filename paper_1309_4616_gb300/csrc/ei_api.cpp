@@ -58,15 +58,20 @@ struct Prepared {
   CUtensorMap map_in2[4];  // the same with a two-point halo (two-iteration kernel)
   CUtensorMap map_c[6];    // a[0..5]
   CUtensorMap map_diagA, map_qc, map_p;
-  // native FP64 stencils: the scaled operator (J - cI)/gamma of the current
-  // Newton loop (a[0..5]/gamma, (diag - c)/gamma), keyed on the diagonal array,
-  // its content version and (c, gamma)
+  // native FP64 stencils: the scaled operator (J - cI)/gamma0 of the current
+  // Newton loop (a[0..5]/gamma0, (diag - c)/gamma0), keyed on the diagonal
+  // array, its content version and (c, gamma).  gamma0 (off_gamma) is the
+  // scale the off-diagonals were written with; it is kept while the ratio
+  // pre_ratio = gamma0/gamma stays near 1, so that a new interval rewrites only
+  // the diagonal (the Newton loop then carries the ratio in its scalars).
   void* sa[7] = {nullptr, nullptr, nullptr, nullptr, nullptr, nullptr, nullptr};
   CUtensorMap map_s[7];
   bool pre_valid = false;
   const void* pre_diag = nullptr;
   unsigned pre_ver = 0;
-  double pre_cc = 0.0, pre_gamma = 0.0;
+  double pre_cc = 0.0, pre_gamma = 0.0, pre_ratio = 1.0;
+  bool off_valid = false;
+  double off_gamma = 0.0;
   unsigned qc_ver = 0;     // bumped whenever qc is rewritten (each Rosenbrock step)
 };
 
@@ -138,6 +143,7 @@ struct ei_ctx {
   double newton_ms = 0.0;
   int newton_fused = 1;
   int p_rechecks = 0;      // stop tests the host took with ||p|| formed (bound undecided)
+  int newton_bounded = 0;  // timed Newton launches that skipped ||p||
   int fuse = 0;            // Newton iterations per stencil launch: 0 the format's
                            // default (two for float-float and float, one for native
                            // FP64), 1 one, 2 two
@@ -205,6 +211,7 @@ static void free_prepared(Prepared& p) {
     *a = nullptr;
   }
   p.pre_valid = false;
+  p.off_valid = false;
   p.ready = false;
   p.coef7 = false;  // a later operator of another kind must not inherit the layout
   p.n_alloc = 0;
@@ -373,10 +380,33 @@ static bool prescaled_for(const Prepared& P, const void* qc) {
 static bool wants_prescale(const ei_ctx* c, const Prepared& P) {
   return c->kind == KIND_STENCIL && P.fmt == VF_F64 && P.sa[0] != nullptr;
 }
+// d_j r^j: the divided differences of the basis w_j / r^j
+static std::vector<double> rescaled_dd(const std::vector<double>& d, double r) {
+  std::vector<double> out(d.size());
+  double sj = 1.0;
+  for (size_t j = 0; j < d.size(); ++j) {
+    out[j] = d[j] * sj;
+    sj *= r;
+  }
+  return out;
+}
+
+// The off-diagonals keep their scale gamma0 while gamma0/gamma lies within
+// 1 +- 1/8: the Newton loop's scale factors (gamma0/gamma)^j then stay within
+// about 1.3e5 over 100 steps.
+static constexpr double kOffRatioSlack = 0.125;
 static ei_status ensure_prescaled(ei_ctx* c, Prepared& P, const void* qc, double cc,
                                   double gamma) {
   if (prescaled_for(P, qc) && P.pre_cc == cc && P.pre_gamma == gamma) return EI_OK;
-  EI_LAUNCH(launch_prescale(P.sa, P.a, qc, P.n_alloc, cc, 1.0 / gamma, c->stream));
+  const double r = P.off_valid ? P.off_gamma / gamma : 0.0;
+  if (P.off_valid && fabs(r - 1.0) <= kOffRatioSlack) {
+    EI_LAUNCH(launch_prescale_diag(P.sa[6], qc, P.n_alloc, cc, 1.0 / P.off_gamma, c->stream));
+  } else {
+    EI_LAUNCH(launch_prescale(P.sa, P.a, qc, P.n_alloc, cc, 1.0 / gamma, c->stream));
+    P.off_valid = true;
+    P.off_gamma = gamma;
+  }
+  P.pre_ratio = P.off_gamma / gamma;
   P.pre_valid = true;
   P.pre_diag = qc;
   P.pre_ver = P.qc_ver;
@@ -475,6 +505,12 @@ static ei_status newton_loop(ei_ctx* c, Prepared& P, const void* qc, const void*
   const bool pair = use_pair(c, P);
   const bool pre = !pair && !cx && wants_prescale(c, P);
   if (pre) EI_TRY(ensure_prescaled(c, P, qc, cc, gamma));
+  // on the operator scaled by 1/gamma0 = r/gamma the loop runs in the basis
+  // w_j / r^j: shifts xi_j / r, coefficients d_j r^j (the same p and tests)
+  std::vector<double> d_r;
+  const double rr = pre ? P.pre_ratio : 1.0;
+  if (rr != 1.0) d_r = rescaled_dd(d, rr);
+  const std::vector<double>& dv = (rr != 1.0) ? d_r : d;
   // Native FP64 steps well before the predicted degree do not form ||p||: the
   // bound ||p_j|| + |d_{j+1}| ||w_{j+1}|| proves their stop tests fail (the
   // FP64 pipe bounds the kernel, and this saves an FMA a point).  From 8 steps
@@ -482,6 +518,7 @@ static ei_status newton_loop(ei_ctx* c, Prepared& P, const void* qc, const void*
   int pb_until = (pre && m_pred > 9) ? m_pred - 8 : 0;
   int lj[128];          // first iteration index of each launch
   bool l2[128];         // whether that launch did two iterations
+  bool lb[128];         // whether that launch skipped ||p|| (bound mode)
   int j = 0, nl = 0;
   int batch = m_pred > 0 ? m_pred : 8;
   auto account = [&](int dg) -> ei_status {  // launches that started below dg did the work
@@ -492,6 +529,7 @@ static ei_status newton_loop(ei_ctx* c, Prepared& P, const void* qc, const void*
       EI_TRY_CUDA(cudaEventElapsedTime(&ms, c->ev[2 * i], c->ev[2 * i + 1]));
       c->newton_ms += ms;
       ++c->newton_timed;
+      if (lb[i]) ++c->newton_bounded;
     }
     c->newton_fused = pair ? 2 : 1;
     return EI_OK;
@@ -501,9 +539,9 @@ static ei_status newton_loop(ei_ctx* c, Prepared& P, const void* qc, const void*
     while (j < jend) {
       const bool two = pair && (j + 2 <= m_max);
       s.j = j;
-      s.d_next = d[j + 1];
+      s.d_next = dv[j + 1];
       s.shift = cc / gamma + xi[j];
-      s.xi = xi[j];
+      s.xi = xi[j] / rr;
       s.pbound = (pre && j >= 1 && j + 1 < pb_until) ? 1 : 0;
       if (two) {
         s.d_next2 = d[j + 2];
@@ -533,6 +571,7 @@ static ei_status newton_loop(ei_ctx* c, Prepared& P, const void* qc, const void*
       if (c->profile) EI_TRY_CUDA(cudaEventRecord(c->ev[2 * nl + 1], c->stream));
       lj[nl] = j;
       l2[nl] = two;
+      lb[nl] = s.pbound != 0;
       ++nl;
       j += two ? 2 : 1;
     }
@@ -545,7 +584,7 @@ static ei_status newton_loop(ei_ctx* c, Prepared& P, const void* qc, const void*
         // stopped at the first of a launch's two iterations: p holds p_{deg+1}
         for (int i = 0; i < nl; ++i)
           if (l2[i] && lj[i] == *deg - 1)
-            EI_LAUNCH(launch_p_fixup(P.p, P.w[i & 1], P.fmt, P.n_alloc, d[*deg + 1], c->stream));
+            EI_LAUNCH(launch_p_fixup(P.p, P.w[i & 1], P.fmt, P.n_alloc, dv[*deg + 1], c->stream));
       }
       return account(*deg);
     }
@@ -560,7 +599,7 @@ static ei_status newton_loop(ei_ctx* c, Prepared& P, const void* qc, const void*
       EI_TRY(read_ctl(c));
       const double np2 = c->h_ctl->sum0;
       if (!isfinite(np2)) return EI_ERR_NONFINITE;
-      if (fabs(d[dg]) * sqrt(nw2) <= tol * sqrt(np2)) {
+      if (fabs(dv[dg]) * sqrt(nw2) <= tol * sqrt(np2)) {
         *deg = dg;
         *ok = 1;
         return account(dg);
@@ -749,6 +788,10 @@ static ei_status newton_fixed(ei_ctx* c, Prepared& P, const void* qc, const void
   const bool pair = use_pair(c, P);
   const bool pre = !pair && wants_prescale(c, P);
   if (pre) EI_TRY(ensure_prescaled(c, P, qc, cc, gamma));
+  std::vector<double> d_r;  // the rescaled basis, as in newton_loop
+  const double rr = pre ? P.pre_ratio : 1.0;
+  if (rr != 1.0) d_r = rescaled_dd(d, rr);
+  const std::vector<double>& dv = (rr != 1.0) ? d_r : d;
   if (timed)
     while (c->ev.size() < (size_t)(2 * m + 2)) {
       cudaEvent_t e;
@@ -759,9 +802,9 @@ static ei_status newton_fixed(ei_ctx* c, Prepared& P, const void* qc, const void
   while (j < m) {
     const bool two = pair && ((m - j) % 2 == 0);
     s.j = j;
-    s.d_next = d[j + 1];
+    s.d_next = dv[j + 1];
     s.shift = cc / gamma + xi[j];
-    s.xi = xi[j];
+    s.xi = xi[j] / rr;
     if (two) {
       s.d_next2 = d[j + 2];
       s.shift2 = cc / gamma + xi[j + 1];
@@ -1322,6 +1365,7 @@ static void acct_begin(ei_ctx* c, const ei_options* opt) {
   c->newton_ms = 0.0;
   c->newton_fused = 1;
   c->p_rechecks = 0;
+  c->newton_bounded = 0;
   c->profile = opt && opt->profile;
   c->fuse = opt ? opt->single_iter : 0;
   c->csr_lanes = opt ? opt->csr_lanes : 0;
@@ -1334,6 +1378,7 @@ static void acct_end(ei_ctx* c, ei_stats* st) {
   st->newton_ms = c->newton_ms;
   st->newton_fused = c->newton_fused;
   st->p_rechecks = c->p_rechecks;
+  st->newton_bounded = c->newton_bounded;
 }
 
 static ei_status phi_apply_impl(ei_ctx* c, int k, double h, const void* v, void* out, double tol,

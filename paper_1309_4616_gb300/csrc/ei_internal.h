@@ -209,8 +209,9 @@ cudaError_t launch_csr_residual(const CsrDev& op, const void* y, const void* v, 
 
 // One Newton iteration j: w_out = (J w_in)/gamma - shift w_in; p += d_{j+1} w_out;
 // norms and the device-side stop test.  Skips itself when ctl->done != 0.
-// prescaled (native FP64 only): M.c holds the scaled operator (J - cI)/gamma
-// (launch_prescale) and w_out = M.c-product of w_in - xi_j w_in.
+// prescaled (native FP64 only): M.c holds the scaled operator (J - cI)/gamma0
+// (launch_prescale) and w_out = M.c-product of w_in - s.xi w_in (the caller
+// passes s.xi = xi_j gamma/gamma0 and the d_j of the rescaled basis).
 cudaError_t launch_newton_tma(const StencilDev& op, const NewtonMaps& M, void* w_out, void* p,
                               const NewtonScalars& s, int fmt, double* partials, DevCtl* ctl,
                               cudaStream_t st, bool prescaled = false);
@@ -221,6 +222,9 @@ cudaError_t launch_p_sqnorm(const void* x, int fmt, int64_t n_alloc, double* par
 // padded arrays: sa[k] = a[k] / gamma (k < 6), sa[6] = (diag - c) / gamma
 cudaError_t launch_prescale(void* const sa[7], const void* const a[6], const void* diag,
                             int64_t n_alloc, double c, double inv_gamma, cudaStream_t st);
+// its diagonal alone: sa6 = (diag - c) * inv_gamma
+cudaError_t launch_prescale_diag(void* sa6, const void* diag, int64_t n_alloc, double c,
+                                 double inv_gamma, cudaStream_t st);
 // Two Newton iterations j+1 and j+2 in one pass (explicit-coefficient stencil,
 // all formats): w_{j+1} is formed on chip over the tile and a one-point
 // halo; only w_{j+2} and p_{j+2} are written.  M.w must be a halo-2 map.

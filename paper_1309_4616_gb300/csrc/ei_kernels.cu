@@ -668,12 +668,27 @@ __device__ __forceinline__ double nonlin_slope(int nonlin, float u) {
   return (double)dq;
 }
 
-// min/max of (lo + q), (hi + q), q = g'(u)
+// A double as a signed 64-bit key whose integer order is the value order:
+// negative values get their magnitude bits inverted (-0 sorts just below +0).
+// A NaN sorts beyond the infinity of its sign bit.  The transform is its own
+// inverse.
+__device__ __forceinline__ long long order_key(double v) {
+  const long long b = __double_as_longlong(v);
+  return b ^ ((b >> 63) & 0x7fffffffffffffffLL);
+}
+__device__ __forceinline__ double key_value(long long k) {
+  return __longlong_as_double(k ^ ((k >> 63) & 0x7fffffffffffffffLL));
+}
+
+// min/max of (lo + q), (hi + q), q = g'(u).  The running min/max compare
+// integer keys (order_key), which keeps the comparisons off the FP64 pipe;
+// a NaN ends up in one of the two keys and makes the thread's interval
+// (-inf, inf), as minmax_row does.
 template <class U>
 __global__ void __launch_bounds__(EI_TPB)
 k_shifted_minmax(int64_t n, const double* __restrict__ lo, const double* __restrict__ hi,
                  const U* __restrict__ u, int nonlin, double* partials, DevCtl* ctl) {
-  double mn = INFINITY, mx = -INFINITY;
+  long long kmn = order_key(INFINITY), kmx = order_key(-INFINITY);
   struct LHU {
     double lo, hi;
     U u;
@@ -682,8 +697,15 @@ k_shifted_minmax(int64_t n, const double* __restrict__ lo, const double* __restr
       n, (int)1, (int)1, [&](int64_t i, int64_t) { return LHU{lo[i], hi[i], u[i]}; },
       [&](int64_t, int64_t, LHU a) {
         const double q = nonlin_slope(nonlin, a.u);
-        minmax_row(mn, mx, a.lo + q, a.hi + q);
+        const long long kl = order_key(a.lo + q), kh = order_key(a.hi + q);
+        kmn = kl < kmn ? kl : kmn;
+        kmx = kh > kmx ? kh : kmx;
       });
+  double mn = key_value(kmn), mx = key_value(kmx);
+  if (isnan(mn) || isnan(mx)) {
+    mn = -INFINITY;
+    mx = INFINITY;
+  }
   if (last_block_reduce2<RED_MINMAX>(mn, mx, partials, ctl)) {
     if (threadIdx.x == 0) {
       ctl->mn = mn;
@@ -847,6 +869,14 @@ k_prescale(const PrescaleArgs P, int64_t n, double c, double inv_gamma) {
         for (int k = 0; k < 6; ++k) P.s[k][i] = v.a[k] * inv_gamma;
         P.s[6][i] = (v.a[6] - c) * inv_gamma;
       });
+}
+
+__global__ void __launch_bounds__(EI_TPB)
+k_prescale_diag(double* __restrict__ sa6, const double* __restrict__ diag, int64_t n, double c,
+                double inv_gamma) {
+  for_points_k<EW_K>(
+      n, (int)1, (int)1, [&](int64_t i, int64_t) { return __ldg(diag + i); },
+      [&](int64_t i, int64_t, double v) { sa6[i] = (v - c) * inv_gamma; });
 }
 
 template <int FMT>
@@ -1491,6 +1521,13 @@ cudaError_t launch_prescale(void* const sa[7], const void* const a[6], const voi
   for (int i = 0; i < 6; ++i) P.a[i] = static_cast<const double*>(a[i]);
   P.a[6] = static_cast<const double*>(diag);
   k_prescale<<<ew_blocks(n_alloc), EI_TPB, 0, stm>>>(P, n_alloc, c, inv_gamma);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_prescale_diag(void* sa6, const void* diag, int64_t n_alloc, double c,
+                                 double inv_gamma, cudaStream_t stm) {
+  k_prescale_diag<<<ew_blocks(n_alloc), EI_TPB, 0, stm>>>(
+      static_cast<double*>(sa6), static_cast<const double*>(diag), n_alloc, c, inv_gamma);
   return cudaGetLastError();
 }
 

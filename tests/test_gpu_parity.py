@@ -381,6 +381,15 @@ def test_errors_leave_outputs_untouched(env):
         ctx.step(ei.EXP_EULER, 0.1, u, ei.NONLIN_LOGISTIC, 1e-10)
     assert e.value.status == ei.ERR_NONFINITE
     assert torch.equal(torch.isnan(u), torch.isnan(bad))
+    # the Rosenbrock interval of J = A + diag(g'(u)) with a NaN of either sign
+    # or an infinity in u, in both arithmetics
+    for arith in (ei.ARITH_NATIVE_F64, ei.ARITH_DF):
+        for val in (float("nan"), -float("nan"), float("inf"), -float("inf")):
+            u = v.clone()
+            u[3] = val
+            with pytest.raises(ei.EIError) as e:
+                ctx.step(ei.EXP_ROSENBROCK, 0.1, u, ei.NONLIN_LOGISTIC, 1e-10, {"arith": arith})
+            assert e.value.status == ei.ERR_NONFINITE
     with pytest.raises(ei.EIError) as e:
         ctx.step(7, 0.1, u, ei.NONLIN_LOGISTIC, 1e-10)
     assert e.value.status == ei.ERR_INVALID_ARG
@@ -494,3 +503,35 @@ def test_native_p_bound_rechecks(env, xi):
     assert st.p_rechecks == 0
     assert rel_err(out.cpu().numpy(), ref) <= FP64_TOL
     _check_stats(st, ost)
+
+
+def test_native_successive_steps_rescaled_operator(env, xi):
+    """Successive native FP64 Rosenbrock steps on one context.  The first step
+    writes the scaled operator (J - cI)/gamma0; a later step whose gamma stays
+    within gamma0 (1 +- 1/8) rewrites only its diagonal and runs the Newton
+    loop in the basis w_j / r^j, r = gamma0/gamma; a step outside that range
+    rewrites all of it.  States u0 * (1, 1.05, 1.1, 3, 3.1, 1) give r = 1, 0.991,
+    0.982, then 1 (rewritten), 0.987, then 1 again.  Each step must give the
+    oracle's result, degree and substep count."""
+    torch, ei = env
+    n = (23, 19, 17)
+    shape = tuple(reversed(n))
+    dx = (1 / 23,) * 3
+    rng = np.random.default_rng(41)
+    D = rng.uniform(0.5, 1.5, shape) * 1e-3
+    b = tuple(rng.uniform(-1, 1, shape) * 1e-2 for _ in range(3))
+    op = O.StencilOperator(n, dx, D, b, bc=(1,) * 6)
+    u0 = rng.uniform(0, 1, shape)
+    ctx = stencil_context(torch, ei, n, dx, D, b, 0.0, (1,) * 6)
+    h, tol = 2.0, 1e-10
+    for scale in (1.0, 1.05, 1.1, 3.0, 3.1, 1.0):
+        uin = u0 * scale
+        ref, ost = Nw.exp_rosenbrock_step(op, uin, h, tol, xi=xi)
+        u = dev(torch, uin)
+        st = ctx.step(ei.EXP_ROSENBROCK, h, u, ei.NONLIN_LOGISTIC, tol,
+                      {"arith": ei.ARITH_NATIVE_F64})
+        got = u.cpu().numpy()
+        assert st.arith_used == ei.ARITH_NATIVE_F64
+        assert rel_err(got - uin, ref - uin) <= FP64_TOL, scale
+        _check_stats(st, ost)
+    ctx.close()
