@@ -593,12 +593,20 @@ static ei_status newton_loop(ei_ctx* c, Prepared& P, const void* qc, const void*
       // take the test as the other steps do; on a fail go on from dg with
       // ||p|| formed in every step
       const int dg = c->h_ctl->degree;
-      const double nw2 = c->h_ctl->nw2;
       ++c->p_rechecks;
+      int made = -1;  // the launch that made degree dg; later ones exited at once
+      for (int i = 0; i < nl; ++i)
+        if (lj[i] == dg - 1) made = i;
+      if (made < 0) return EI_ERR_STATE;
+      // the step bracketed ||w_dg||: form it, and ||p_dg||, exactly
       EI_LAUNCH(launch_p_sqnorm(P.p, P.fmt, P.n_alloc, c->partials, c->ctl, c->stream));
       EI_TRY(read_ctl(c));
       const double np2 = c->h_ctl->sum0;
-      if (!isfinite(np2)) return EI_ERR_NONFINITE;
+      EI_LAUNCH(launch_p_sqnorm(wbuf[made & 1], P.fmt, P.n_alloc, c->partials, c->ctl,
+                                c->stream));
+      EI_TRY(read_ctl(c));
+      const double nw2 = c->h_ctl->sum0;
+      if (!isfinite(np2) || !isfinite(nw2)) return EI_ERR_NONFINITE;
       if (fabs(dv[dg]) * sqrt(nw2) <= tol * sqrt(np2)) {
         *deg = dg;
         *ok = 1;
@@ -609,10 +617,6 @@ static ei_status newton_loop(ei_ctx* c, Prepared& P, const void* qc, const void*
         *ok = 0;
         return account(dg);
       }
-      int made = -1;  // the launch that made degree dg; later ones exited at once
-      for (int i = 0; i < nl; ++i)
-        if (lj[i] == dg - 1) made = i;
-      if (made < 0) return EI_ERR_STATE;
       nl = made + 1;
       j = dg;
       pb_until = 0;

@@ -61,13 +61,22 @@ __device__ __forceinline__ bool finite_d(double x) { return isfinite(x); }
 // done = 4 in both modes, and a bounded device wait that ran out (ctl->err)
 // with done = 5.  Returns true when the iteration stops at `deg`.  Called by
 // one thread after the grid-wide reduction.
+// nw2_hi >= 0 (p-bound steps only): ||w_deg||^2 is not known exactly but lies
+// in [nw2, nw2_hi].
 __device__ __forceinline__ bool newton_verdict(DevCtl* ctl, const NewtonScalars& s, int deg,
-                                               double d, double nw2, double np2) {
+                                               double d, double nw2, double np2,
+                                               double nw2_hi = -1.0) {
   const bool last = deg >= s.m_max;
   if (*(volatile int*)&ctl->err) {
     ctl->done = 5;
     ctl->degree = deg;
     if (s.fixed) atomicAdd(&ctl->fixfail, 1);
+    return true;
+  }
+  if (s.pbound && nw2_hi >= 0.0 && !(nw2_hi < INFINITY && nw2 >= 0x1p-1000)) {
+    // a bracket that left FP64's normal range: the host takes the test
+    ctl->done = 6;
+    ctl->degree = deg;
     return true;
   }
   if (!finite_d(nw2) || !finite_d(np2)) {
@@ -86,9 +95,11 @@ __device__ __forceinline__ bool newton_verdict(DevCtl* ctl, const NewtonScalars&
     // ||p_deg|| was not formed.  ||p_deg|| <= ||p_{deg-1}|| + |d| ||w_deg||, so an
     // estimate above tol times that bound (with a 1e-9 margin for the rounding
     // of both sides) fails the test for certain; otherwise the host forms
-    // ||p_deg|| and takes the test (done = 6)
+    // ||p_deg|| (and ||w_deg|| where it was bracketed) and takes the test
+    // (done = 6).  With a bracket, the estimate takes its lower end and the
+    // bound its upper end.
     const double e = fabs(d) * sqrt(nw2);
-    const double ub = ctl->pub + e;
+    const double ub = ctl->pub + (nw2_hi >= 0.0 ? fabs(d) * sqrt(nw2_hi) : e);
     ctl->pub = ub;
     if (e > s.tol * ub * (1.0 + 1e-9)) {
       if (!last) return false;

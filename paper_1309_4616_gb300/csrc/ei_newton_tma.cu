@@ -7,9 +7,12 @@
 // a fixed-order last-block reduction) and the stop test of the a-posteriori
 // estimate |d_{j+1}| ||w_{j+1}|| <= tol ||p||.
 //
-// Tiling: a block owns a 32 x 8 column of the grid and marches along z over a
-// chunk of planes (Sec. III-A of the paper keeps a 2D slice on chip and iterates
-// over the third index; here the slice is fed by TMA).  Per plane, one thread
+// Tiling: a block marches along z through 32 x 8 columns of the grid (Sec.
+// III-A of the paper keeps a 2D slice on chip and iterates over the third
+// index; here the slice is fed by TMA).  The one-iteration kernel runs one
+// wave of resident blocks, each taking an equal run of the column-planes
+// (one or more z-runs); the two-iteration kernel gives each block one
+// column's chunk of planes.  Per plane, one thread
 // issues cp.async.bulk.tensor loads of the w tile with its x/y halo (x start
 // rounded down to a 16-byte boundary), the coefficient tiles and the p tile
 // into two rings: the w tiles (planes z-1, z, z+1 are read while plane z is
@@ -127,8 +130,7 @@ static constexpr uint64_t kWaitLimitNs = 500000000ull;  // 0.5 s; a plane lands 
 template <int FMT, bool PRE, bool PN = true>
 __global__ void __launch_bounds__(256, TmaCfg<FMT>::MINB)
 k_newton_tma(const __grid_constant__ NewtonMaps M, const StencilDev g, const NewtonScalars s,
-             void* __restrict__ w_out_, void* __restrict__ p_, double* partials, DevCtl* ctl,
-             int zc) {
+             void* __restrict__ w_out_, void* __restrict__ p_, double* partials, DevCtl* ctl) {
   using C = TmaCfg<FMT>;
   using T = typename C::T;
   using P = typename C::P;
@@ -140,10 +142,12 @@ k_newton_tma(const __grid_constant__ NewtonMaps M, const StencilDev g, const New
   unsigned char* smem = smem_raw + (sbase - raw);
   const uint32_t bar0 = sbase + C::BARS;
   const int tx = threadIdx.x, ty = threadIdx.y, tid = ty * C::TX + tx;
-  const int x0 = blockIdx.x * C::TX, y0 = blockIdx.y * C::TY;
-  const int z0 = blockIdx.z * zc;
-  const int z1 = min(z0 + zc, g.nz);
-  const int nplanes = z1 - z0 + 2;  // z0-1 .. z1
+  // this block's equal share [ub, ue) of the column-planes u = column * nz + z
+  // (columns of 32 x 8 points, x fastest): one or more z-runs (segments)
+  const int bxc = (g.nx + C::TX - 1) / C::TX;
+  const int64_t units = (int64_t)bxc * ((g.ny + C::TY - 1) / C::TY) * g.nz;
+  const int64_t ub = units * blockIdx.x / gridDim.x;
+  const int64_t ue = units * (blockIdx.x + 1) / gridDim.x;
   const bool needp = s.j > 0;
   const uint32_t tx_halo = C::W_BYTES;
   const uint32_t tx_full = tx_halo + C::N_CT * C::C_BYTES + (needp ? C::P_BYTES : 0);
@@ -154,88 +158,125 @@ k_newton_tma(const __grid_constant__ NewtonMaps M, const StencilDev g, const New
   }
   __syncthreads();
 
-  int last_issued = -1;  // meaningful in thread 0
-  auto issue = [&](int q) {
-    const uint32_t wb = sbase + (q % C::NW) * C::WSTAGE;
-    const uint32_t cb = sbase + C::CRING + (q % C::NC) * C::CSTAGE;
-    const uint32_t bar = bar0 + 8 * (q % C::NBAR);
-    const int z = z0 - 1 + q;
-    const bool halo = (q == 0) || (q == nplanes - 1);
-    mbar_expect_tx(bar, halo ? tx_halo : tx_full);
-    tma_load_3d(wb + C::OFF_W, &M.w, x0 - C::HX, y0 - 1, z, bar);
-    if (!halo) {
-#pragma unroll
-      for (int k = 0; k < C::N_CT; ++k)
-        tma_load_3d(cb + C::OFF_CT + k * C::C_BYTES, &M.c[k], x0, y0, z, bar);
-      if (needp) tma_load_3d(cb + C::OFF_P, &M.p, x0, y0, z, bar);
-    }
-    last_issued = q;
-  };
-  int waited_ok = -1;  // last plane whose copies this thread saw complete
-  auto wait = [&](int q) {
-    const bool ok =
-        mbar_wait_bounded(bar0 + 8 * (q % C::NBAR), (q / C::NBAR) & 1, kWaitLimitNs);
-    if (ok) waited_ok = q;
-    return ok;
-  };
-
-  if (tid == 0) {
-    for (int q = 0; q <= C::PF && q < nplanes; ++q) issue(q);
-  }
-
   const T invg = from_d<T>(s.inv_gamma);
   const T nshift = from_d<T>(PRE ? -s.xi : -s.shift);
   const P dn = from_d<P>(s.d_next);
   const P d0 = from_d<P>(s.d0);
   typename Acc<T>::type aw = Acc<T>::zero();
   typename Acc<P>::type ap = Acc<P>::zero();
+  // bound mode (!PN, native FP64): ||w_{j+1}||^2 is only bracketed, by an FP32
+  // sum of t^2 where t is |w| cut to its high word: sign cleared, exponent
+  // rebiased so that the last iterate's root mean square lands near 1 (scale
+  // 2^kexp), 20 mantissa bits kept.  t <= |w| 2^kexp < t (1 + 2^-20) wherever
+  // t is a normal float; a |w| below that range gives t = 0, one above it
+  // (or an Inf or NaN) gives t = Inf.  The integer work keeps the FP64 pipe
+  // for the iteration itself.
+  int kexp = 0, rebias = 896 << 20;  // FP64 exponent bias 1023 - FP32's 127
+  float awf = 0.f;
+  if constexpr (!PN) {
+    const double ms = ctl->nw2 / ((double)g.nx * g.ny * g.nz);
+    if (ms > 0.0 && ms < INFINITY) kexp = max(-480, min(480, -(ilogb(ms) >> 1)));
+    rebias = (896 - kexp) << 20;
+  }
   T* __restrict__ w_out = static_cast<T*>(w_out_);
   P* __restrict__ p = static_cast<P*>(p_);
-  const int x = x0 + tx, y = y0 + ty;
-  const bool inside = (x < g.nx) && (y < g.ny);
   const int wi = (ty + 1) * C::WX + tx + C::HX;
   const int ci = ty * C::TX + tx;
   constexpr int TT = C::TX * C::TY;
   bool bad = false;
+  // The mbarriers count planes over all segments (qb: planes of the earlier
+  // ones), so their phases run on; the ring slots restart with each segment.
+  int qb = 0;
+  int last_issued = -1;  // last plane issued (thread 0)
+  int waited_ok = -1;    // last plane whose copies this thread saw complete
 
-  for (int q = 1; q <= nplanes - 2; ++q) {
-    if (tid == 0 && q + C::PF < nplanes) {
-      fence_proxy_async();
-      issue(q + C::PF);  // into the slots of planes q+PF-NW (w) and q+PF-NC (coefficients)
-    }
-    if (q == 1) {
-      if (!bad) bad = !wait(0);
-      if (!bad) bad = !wait(1);
-    }
-    if (!bad) bad = !wait(q + 1);
-    if (!bad && inside) {
+  for (int64_t us = ub; us < ue && !bad;) {
+    const int col = (int)(us / g.nz);
+    const int z0 = (int)(us - (int64_t)col * g.nz);
+    const int z1 = (int)min((int64_t)g.nz, z0 + (ue - us));
+    us += z1 - z0;
+    const int x0 = (col % bxc) * C::TX, y0 = (col / bxc) * C::TY;
+    const int nplanes = z1 - z0 + 2;  // z0-1 .. z1
+    auto issue = [&](int q) {
+      const uint32_t wb = sbase + (q % C::NW) * C::WSTAGE;
+      const uint32_t cb = sbase + C::CRING + (q % C::NC) * C::CSTAGE;
+      const uint32_t bar = bar0 + 8 * ((qb + q) % C::NBAR);
       const int z = z0 - 1 + q;
-      const unsigned char* sm = smem + (q % C::NW) * C::WSTAGE;
-      const unsigned char* smm = smem + ((q - 1) % C::NW) * C::WSTAGE;
-      const unsigned char* smp = smem + ((q + 1) % C::NW) * C::WSTAGE;
-      const unsigned char* scq = smem + C::CRING + (q % C::NC) * C::CSTAGE;
-      const T* Wc = reinterpret_cast<const T*>(sm + C::OFF_W);
-      const T* Wm = reinterpret_cast<const T*>(smm + C::OFF_W);
-      const T* Wp = reinterpret_cast<const T*>(smp + C::OFF_W);
-      const T* Ct = reinterpret_cast<const T*>(scq + C::OFF_CT);
-      const T wc = Wc[wi];
-      const T acc = stencil7(Ct[6 * TT + ci], wc, Ct[0 * TT + ci], Wc[wi - 1], Ct[1 * TT + ci],
-                             Wc[wi + 1], Ct[2 * TT + ci], Wc[wi - C::WX], Ct[3 * TT + ci],
-                             Wc[wi + C::WX], Ct[4 * TT + ci], Wm[wi], Ct[5 * TT + ci], Wp[wi]);
-      const T wn = PRE ? mac(acc, nshift, wc) : newton_update(acc, invg, nshift, wc);
-      const P* Pt = reinterpret_cast<const P*>(scq + C::OFF_P);
-      const P pold = needp ? Pt[ci] : mul(d0, to_p(wc));
-      const P pn = mac(pold, dn, to_p(wn));
-      const int64_t idx = ((int64_t)z * g.ny + y) * g.pitch + x;
-      st(w_out, idx, wn);
-      st(p, idx, pn);
-      aw = acc_sq(aw, wn);
-      if (PN) ap = acc_sq(ap, pn);
+      const bool halo = (q == 0) || (q == nplanes - 1);
+      mbar_expect_tx(bar, halo ? tx_halo : tx_full);
+      tma_load_3d(wb + C::OFF_W, &M.w, x0 - C::HX, y0 - 1, z, bar);
+      if (!halo) {
+#pragma unroll
+        for (int k = 0; k < C::N_CT; ++k)
+          tma_load_3d(cb + C::OFF_CT + k * C::C_BYTES, &M.c[k], x0, y0, z, bar);
+        if (needp) tma_load_3d(cb + C::OFF_P, &M.p, x0, y0, z, bar);
+      }
+      last_issued = qb + q;
+    };
+    auto wait = [&](int q) {
+      const int qg = qb + q;
+      const bool ok =
+          mbar_wait_bounded(bar0 + 8 * (qg % C::NBAR), (qg / C::NBAR) & 1, kWaitLimitNs);
+      if (ok) waited_ok = qg;
+      return ok;
+    };
+
+    if (tid == 0) {
+      // the previous segment's reads of these slots ended at its last barrier
+      fence_proxy_async();
+      for (int q = 0; q <= C::PF && q < nplanes; ++q) issue(q);
     }
-    if ((q % C::SYNC == 0 || q == nplanes - 2) && __syncthreads_or(bad)) {
-      bad = true;
-      break;
+    const int x = x0 + tx, y = y0 + ty;
+    const bool inside = (x < g.nx) && (y < g.ny);
+
+    for (int q = 1; q <= nplanes - 2; ++q) {
+      if (tid == 0 && q + C::PF < nplanes) {
+        fence_proxy_async();
+        issue(q + C::PF);  // into the slots of planes q+PF-NW (w) and q+PF-NC (coefficients)
+      }
+      if (q == 1) {
+        if (!bad) bad = !wait(0);
+        if (!bad) bad = !wait(1);
+      }
+      if (!bad) bad = !wait(q + 1);
+      if (!bad && inside) {
+        const int z = z0 - 1 + q;
+        const unsigned char* sm = smem + (q % C::NW) * C::WSTAGE;
+        const unsigned char* smm = smem + ((q - 1) % C::NW) * C::WSTAGE;
+        const unsigned char* smp = smem + ((q + 1) % C::NW) * C::WSTAGE;
+        const unsigned char* scq = smem + C::CRING + (q % C::NC) * C::CSTAGE;
+        const T* Wc = reinterpret_cast<const T*>(sm + C::OFF_W);
+        const T* Wm = reinterpret_cast<const T*>(smm + C::OFF_W);
+        const T* Wp = reinterpret_cast<const T*>(smp + C::OFF_W);
+        const T* Ct = reinterpret_cast<const T*>(scq + C::OFF_CT);
+        const T wc = Wc[wi];
+        const T acc = stencil7(Ct[6 * TT + ci], wc, Ct[0 * TT + ci], Wc[wi - 1], Ct[1 * TT + ci],
+                               Wc[wi + 1], Ct[2 * TT + ci], Wc[wi - C::WX], Ct[3 * TT + ci],
+                               Wc[wi + C::WX], Ct[4 * TT + ci], Wm[wi], Ct[5 * TT + ci], Wp[wi]);
+        const T wn = PRE ? mac(acc, nshift, wc) : newton_update(acc, invg, nshift, wc);
+        const P* Pt = reinterpret_cast<const P*>(scq + C::OFF_P);
+        const P pold = needp ? Pt[ci] : mul(d0, to_p(wc));
+        const P pn = mac(pold, dn, to_p(wn));
+        const int64_t idx = ((int64_t)z * g.ny + y) * g.pitch + x;
+        st(w_out, idx, wn);
+        st(p, idx, pn);
+        if constexpr (PN) {
+          aw = acc_sq(aw, wn);
+          ap = acc_sq(ap, pn);
+        } else {
+          const int r = min(max((__double2hiint(wn) & 0x7fffffff) - rebias, 0), 0x0ff00000);
+          const float t = __int_as_float(r << 3);
+          awf = fmaf(t, t, awf);
+        }
+      }
+      // every plane: the slots read here are reissued only after this barrier
+      // (the segment's last plane included, which frees all slots for the next)
+      if ((q % C::SYNC == 0 || q == nplanes - 2) && __syncthreads_or(bad)) {
+        bad = true;
+        break;
+      }
     }
+    qb += nplanes;
   }
   if (bad && tid == 0) {
     atomicOr(&ctl->err, 1);
@@ -244,12 +285,30 @@ k_newton_tma(const __grid_constant__ NewtonMaps M, const StencilDev g, const New
       mbar_wait_bounded(bar0 + 8 * (q % C::NBAR), (q / C::NBAR) & 1, kWaitLimitNs / 8);
   }
 
-  double nw2 = acc_d(aw), np2 = acc_d(ap);
+  // 2^(-2 kexp): back from the rebiased FP32 squares (exact)
+  const double unscale = __hiloint2double((1023 - 2 * kexp) << 20, 0);
+  double nw2 = PN ? acc_d(aw) : (double)awf * unscale, np2 = acc_d(ap);
   if (last_block_reduce2<RED_SUM>(nw2, np2, partials, ctl)) {
     if (tid == 0) {
       ctl->nw2 = nw2;
       ctl->np2 = np2;
-      newton_verdict(ctl, s, s.j + 1, s.d_next, nw2, np2);
+      if constexpr (PN) {
+        newton_verdict(ctl, s, s.j + 1, s.d_next, nw2, np2);
+      } else {
+        // The bracket of ||w_{j+1}||^2: each thread's FP32 sum has at most
+        // `terms` roundings of relative 2^-24 (gam bounds their effect), each
+        // cut value lies within a factor 1 + 2^-20 below |w|, and an element
+        // that left FP32's normal range or a square that went subnormal is
+        // off by less than 2^-140 in the rebiased scale (slack).  The FP64
+        // reductions of the thread sums add far less than the 1e-9 margin.
+        const double terms = (double)((units + gridDim.x - 1) / gridDim.x);
+        const double gam = terms * 0x1p-24 / (1.0 - terms * 0x1p-24);
+        const double slack = (double)g.nx * g.ny * g.nz * 0x1p-140 * unscale;
+        const double cut = 1.0 + 0x1p-20;
+        const double lo = fmax(nw2 - slack, 0.0) / (1.0 + gam) * (1.0 - 1e-9);
+        const double hi = (nw2 / (1.0 - gam) * (1.0 + 1e-9) + slack) * cut * cut;
+        newton_verdict(ctl, s, s.j + 1, s.d_next, lo, np2, hi);
+      }
     }
   }
 }
@@ -602,18 +661,18 @@ int newton_tma_blocks(const StencilDev& g) {
 // more w planes, two more coefficient planes and w_{j+1} on two more planes.
 static constexpr double kHaloPair = 2.3;
 
-// The one-iteration kernel: 32 planes a block unless that leaves fewer than
-// 1216 blocks (8 per SM), halving down to 4.  (The wave model above measured
-// no better here: when a last, partial wave runs, its blocks share the SM's
-// FP64 pipe with fewer others and finish sooner.)
-static int tma_zchunk_single(const StencilDev& g) {
-  const int64_t bxy = (int64_t)((g.nx + 31) / 32) * ((g.ny + 7) / 8);
-  int zc = 32;
-  while (zc > 4 && bxy * ((g.nz + zc - 1) / zc) < 1216) zc /= 2;
-  if (zc > g.nz) zc = g.nz;
-  if (zc < 1) zc = 1;
-  while ((g.nz + zc - 1) / zc > 65535) zc *= 2;
-  return zc;
+// The one-iteration kernel's grid: one wave of resident blocks (SMs x blocks
+// an SM holds), each an equal share of the column-planes, so that every SM
+// runs the same work and all finish together.  (Sweeps of 6, 4, 3 and 2 waves
+// of smaller shares on 256^3 were slower: each block start costs two halo
+// planes and a pipeline fill, and a wave boundary leaves SMs waiting.)  No
+// block takes fewer than kMinPlanes column-planes.
+static constexpr int kMinPlanes = 4;
+static int64_t tma_balanced_blocks(const StencilDev& g, int slots) {
+  const int64_t units = (int64_t)((g.nx + 31) / 32) * ((g.ny + 7) / 8) * g.nz;
+  const int64_t cap = (units + kMinPlanes - 1) / kMinPlanes;
+  const int64_t nb = slots < cap ? slots : cap;
+  return nb < 1 ? 1 : nb;
 }
 
 template <int FMT, bool PRE, bool PN = true>
@@ -621,17 +680,20 @@ static cudaError_t launch_one(const StencilDev& g, const NewtonMaps& M, void* w_
                               const NewtonScalars& s, double* partials, DevCtl* ctl,
                               cudaStream_t st) {
   using C = TmaCfg<FMT>;
-  static bool attr = false;
-  if (!attr) {
+  static int slots = 0;
+  if (slots == 0) {
     cudaError_t e = cudaFuncSetAttribute(k_newton_tma<FMT, PRE, PN>,
                                          cudaFuncAttributeMaxDynamicSharedMemorySize, C::SMEM);
     if (e != cudaSuccess) return e;
-    attr = true;
+    int per_sm = 0;
+    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_newton_tma<FMT, PRE, PN>, 256,
+                                                      C::SMEM);
+    if (e != cudaSuccess) return e;
+    slots = (per_sm > 0 ? per_sm : 1) * sm_count();
   }
-  const int zc = tma_zchunk_single(g);
-  dim3 grid((g.nx + 31) / 32, (g.ny + 7) / 8, (g.nz + zc - 1) / zc), block(32, 8, 1);
-  k_newton_tma<FMT, PRE, PN><<<grid, block, C::SMEM, st>>>(M, g, s, w_out, p, partials, ctl,
-                                                           zc);
+  const int64_t nb = tma_balanced_blocks(g, slots);
+  k_newton_tma<FMT, PRE, PN><<<(unsigned)nb, dim3(32, 8, 1), C::SMEM, st>>>(M, g, s, w_out, p,
+                                                                            partials, ctl);
   return cudaGetLastError();
 }
 
