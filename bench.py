@@ -53,8 +53,9 @@ CONST_BYTES_PER_POINT = 32
 # add), the Newton sum (1 multiply, 1 add) and the two squared norms
 # (2 multiplies, 2 adds).
 FP64_FLOPS_PER_POINT = 21
-# the same for an iteration in the p-norm bound mode: no squared norm of p, and
-# the squared norm of w bracketed by FP32 arithmetic on integer-cut values
+# the same for an iteration in bracket mode (every step after the first of a
+# native loop): both squared norms bracketed by FP32 arithmetic on integer-cut
+# values instead of formed in FP64
 FP64_FLOPS_PER_POINT_BOUNDED = 17
 # GB300's FP64 peak from unit counts and clocks: the nominal 1.25 TFLOP/s over
 # 152 SMs at 2070 MHz is 4 FP64 flops (two FMA lanes) per SM and clock.

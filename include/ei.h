@@ -149,12 +149,13 @@ typedef struct {
   int arith_used;       /* EI_ARITH_* the Newton iteration ran in (F64 operators;
                            a float-float call outside the format's range runs
                            in native FP64) */
-  int p_rechecks;       /* native FP64 stencils: Newton steps far below the
-                           a-priori degree skip forming ||p||, a bound decides
-                           their stop tests; steps where the bound could not
-                           decide and the host formed ||p|| to take the test */
-  int newton_bounded;   /* of the newton_timed launches, those that did not
-                           form ||p|| (the bound above decided their tests) */
+  int p_rechecks;       /* native FP64 stencils: Newton steps after the first
+                           bracket ||w|| and ||p|| in FP32 and take the stop
+                           test from the brackets; steps whose brackets could
+                           not decide, where the host formed both norms to
+                           take the test */
+  int newton_bounded;   /* of the newton_timed launches, those that bracketed
+                           the norms */
   int pad_end;
 } ei_stats;
 

@@ -142,8 +142,8 @@ struct ei_ctx {
   int newton_timed = 0;
   double newton_ms = 0.0;
   int newton_fused = 1;
-  int p_rechecks = 0;      // stop tests the host took with ||p|| formed (bound undecided)
-  int newton_bounded = 0;  // timed Newton launches that skipped ||p||
+  int p_rechecks = 0;      // stop tests the host took with the norms formed (brackets undecided)
+  int newton_bounded = 0;  // timed Newton launches that bracketed the norms
   int fuse = 0;            // Newton iterations per stencil launch: 0 the format's
                            // default (two for float-float and float, one for native
                            // FP64), 1 one, 2 two
@@ -511,14 +511,15 @@ static ei_status newton_loop(ei_ctx* c, Prepared& P, const void* qc, const void*
   const double rr = pre ? P.pre_ratio : 1.0;
   if (rr != 1.0) d_r = rescaled_dd(d, rr);
   const std::vector<double>& dv = (rr != 1.0) ? d_r : d;
-  // Native FP64 steps well before the predicted degree do not form ||p||: the
-  // bound ||p_j|| + |d_{j+1}| ||w_{j+1}|| proves their stop tests fail (the
-  // FP64 pipe bounds the kernel, and this saves an FMA a point).  From 8 steps
-  // before the a-priori degree on, every step forms it.
-  int pb_until = (pre && m_pred > 9) ? m_pred - 8 : 0;
+  // Native FP64 steps after the first bracket ||w|| and ||p|| in FP32 and take
+  // the stop test from the brackets (the FP64 pipe bounds the kernel, and this
+  // saves it two FMAs a point); where the brackets cannot decide, the host
+  // takes the test with both norms formed, and every later step of the loop
+  // forms them.
+  bool bracket = pre;
   int lj[128];          // first iteration index of each launch
   bool l2[128];         // whether that launch did two iterations
-  bool lb[128];         // whether that launch skipped ||p|| (bound mode)
+  bool lb[128];         // whether that launch bracketed the norms
   int j = 0, nl = 0;
   int batch = m_pred > 0 ? m_pred : 8;
   auto account = [&](int dg) -> ei_status {  // launches that started below dg did the work
@@ -542,7 +543,7 @@ static ei_status newton_loop(ei_ctx* c, Prepared& P, const void* qc, const void*
       s.d_next = dv[j + 1];
       s.shift = cc / gamma + xi[j];
       s.xi = xi[j] / rr;
-      s.pbound = (pre && j >= 1 && j + 1 < pb_until) ? 1 : 0;
+      s.bracket = (bracket && j >= 1) ? 1 : 0;
       if (two) {
         s.d_next2 = d[j + 2];
         s.shift2 = cc / gamma + xi[j + 1];
@@ -571,7 +572,7 @@ static ei_status newton_loop(ei_ctx* c, Prepared& P, const void* qc, const void*
       if (c->profile) EI_TRY_CUDA(cudaEventRecord(c->ev[2 * nl + 1], c->stream));
       lj[nl] = j;
       l2[nl] = two;
-      lb[nl] = s.pbound != 0;
+      lb[nl] = s.bracket != 0;
       ++nl;
       j += two ? 2 : 1;
     }
@@ -589,16 +590,15 @@ static ei_status newton_loop(ei_ctx* c, Prepared& P, const void* qc, const void*
       return account(*deg);
     }
     if (done == 6) {
-      // the bound of ||p|| could not decide at degree dg: form ||p_dg|| and
-      // take the test as the other steps do; on a fail go on from dg with
-      // ||p|| formed in every step
+      // the norm brackets could not decide at degree dg: form both norms and
+      // take the test as the other steps do; on a fail go on from dg with the
+      // norms formed in every step
       const int dg = c->h_ctl->degree;
       ++c->p_rechecks;
       int made = -1;  // the launch that made degree dg; later ones exited at once
       for (int i = 0; i < nl; ++i)
         if (lj[i] == dg - 1) made = i;
       if (made < 0) return EI_ERR_STATE;
-      // the step bracketed ||w_dg||: form it, and ||p_dg||, exactly
       EI_LAUNCH(launch_p_sqnorm(P.p, P.fmt, P.n_alloc, c->partials, c->ctl, c->stream));
       EI_TRY(read_ctl(c));
       const double np2 = c->h_ctl->sum0;
@@ -619,7 +619,7 @@ static ei_status newton_loop(ei_ctx* c, Prepared& P, const void* qc, const void*
       }
       nl = made + 1;
       j = dg;
-      pb_until = 0;
+      bracket = false;
       EI_TRY(reset_done(c));
       batch = 8;
       continue;

@@ -54,18 +54,22 @@ __device__ __forceinline__ double to_p(double x) { return x; }
 __device__ __forceinline__ bool finite_d(double x) { return isfinite(x); }
 
 // Verdict after the Newton step reaching degree `deg`, with squared norms nw2
-// of w_deg and np2 of p_deg (not formed when s.pbound) and coefficient d = d_deg.  Adaptive mode: stop
+// of w_deg and np2 of p_deg and coefficient d = d_deg.  Adaptive mode: stop
 // at the first degree whose estimate |d| ||w|| <= tol ||p|| holds (done = 1),
 // or at m_max (done = 2).  Fixed-count mode: only deg == m_max is judged, and
 // a failed check also counts into ctl->fixfail.  Non-finite norms stop with
 // done = 4 in both modes, and a bounded device wait that ran out (ctl->err)
 // with done = 5.  Returns true when the iteration stops at `deg`.  Called by
 // one thread after the grid-wide reduction.
-// nw2_hi >= 0 (p-bound steps only): ||w_deg||^2 is not known exactly but lies
-// in [nw2, nw2_hi].
+// Bracket steps (s.bracket, adaptive mode): the squared norms are known only
+// to lie in [nw2, nw2_hi] and [np2, np2_hi].  The test is decided where the
+// brackets decide it for every value inside them (with a 1e-9 margin for the
+// rounding of the comparison); otherwise, or where a bracket left FP64's
+// normal range (an Inf or NaN among the values included), the step stops
+// with done = 6 and the host forms both norms and takes the test.
 __device__ __forceinline__ bool newton_verdict(DevCtl* ctl, const NewtonScalars& s, int deg,
                                                double d, double nw2, double np2,
-                                               double nw2_hi = -1.0) {
+                                               double nw2_hi = -1.0, double np2_hi = -1.0) {
   const bool last = deg >= s.m_max;
   if (*(volatile int*)&ctl->err) {
     ctl->done = 5;
@@ -73,8 +77,24 @@ __device__ __forceinline__ bool newton_verdict(DevCtl* ctl, const NewtonScalars&
     if (s.fixed) atomicAdd(&ctl->fixfail, 1);
     return true;
   }
-  if (s.pbound && nw2_hi >= 0.0 && !(nw2_hi < INFINITY && nw2 >= 0x1p-1000)) {
-    // a bracket that left FP64's normal range: the host takes the test
+  if (s.bracket && nw2_hi >= 0.0) {
+    const bool normal = nw2_hi < INFINITY && np2_hi < INFINITY && nw2 >= 0x1p-1000 &&
+                        np2 >= 0x1p-1000;
+    if (normal) {
+      const double a_lo = fabs(d) * sqrt(nw2), a_hi = fabs(d) * sqrt(nw2_hi);
+      const double b_lo = s.tol * sqrt(np2), b_hi = s.tol * sqrt(np2_hi);
+      if (a_hi * (1.0 + 1e-9) <= b_lo) {  // converged for every value in the brackets
+        ctl->done = 1;
+        ctl->degree = deg;
+        return true;
+      }
+      if (a_lo > b_hi * (1.0 + 1e-9)) {  // fails for every value in the brackets
+        if (!last) return false;
+        ctl->done = 2;
+        ctl->degree = deg;
+        return true;
+      }
+    }
     ctl->done = 6;
     ctl->degree = deg;
     return true;
@@ -91,27 +111,6 @@ __device__ __forceinline__ bool newton_verdict(DevCtl* ctl, const NewtonScalars&
     return true;
   }
   if (s.fixed && !last) return false;
-  if (s.pbound) {
-    // ||p_deg|| was not formed.  ||p_deg|| <= ||p_{deg-1}|| + |d| ||w_deg||, so an
-    // estimate above tol times that bound (with a 1e-9 margin for the rounding
-    // of both sides) fails the test for certain; otherwise the host forms
-    // ||p_deg|| (and ||w_deg|| where it was bracketed) and takes the test
-    // (done = 6).  With a bracket, the estimate takes its lower end and the
-    // bound its upper end.
-    const double e = fabs(d) * sqrt(nw2);
-    const double ub = ctl->pub + (nw2_hi >= 0.0 ? fabs(d) * sqrt(nw2_hi) : e);
-    ctl->pub = ub;
-    if (e > s.tol * ub * (1.0 + 1e-9)) {
-      if (!last) return false;
-      ctl->done = 2;
-      ctl->degree = deg;
-      return true;
-    }
-    ctl->done = 6;
-    ctl->degree = deg;
-    return true;
-  }
-  ctl->pub = sqrt(np2);
   if (fabs(d) * sqrt(nw2) <= s.tol * sqrt(np2)) {
     ctl->done = 1;
     ctl->degree = deg;

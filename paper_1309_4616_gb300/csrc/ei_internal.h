@@ -18,8 +18,8 @@ struct DevCtl {
   unsigned int count;  // arrivals of the current launch (reset by its last block)
   int done;            // Newton: 0 running, 1 converged, 2 m_max reached,
                        //         4 non-finite, 5 a bounded device wait ran out,
-                       //         6 the bound of ||p|| could not decide (host takes
-                       //         the test with ||p|| formed)
+                       //         6 the norm brackets could not decide (the host
+                       //         takes the test with both norms formed)
   int degree;          // Newton degree at stop
   int err;             // set by a block whose bounded wait ran out
   int fixup;           // two-iteration kernel stopped at its first iteration: p holds
@@ -33,8 +33,6 @@ struct DevCtl {
   double nw2, np2;     // squared norms of the last Newton iterate / sum
   double cs_sum, cs_max, cs_pe;  // coefficient statistics (launch_coef_stats)
   double vmax;         // import: largest magnitude of the imported vector (exact)
-  double pub;          // Newton: an upper bound of ||p|| after the last step (exact
-                       // where that step formed ||p||, see NewtonScalars::pbound)
 };
 
 // Grid geometry of the stencil operator.  Library-owned arrays are stored
@@ -95,9 +93,10 @@ struct NewtonScalars {
   double d_next_im;    // complex Newton sum (k_csr_newton_c): Im d_{j+1}
   double d0_im;        //   and Im d_0
   double xi;           // the Leja point xi_j (kernels on the scaled operator)
-  int pbound;          // 1: this step does not form ||p_{j+1}||; the stop test uses
-                       //    the bound ctl->pub + |d_{j+1}| ||w_{j+1}|| and reports
-                       //    done = 6 where that bound cannot decide
+  int bracket;         // 1: this step brackets ||w_{j+1}||^2 and ||p_{j+1}||^2 in
+                       //    FP32 instead of forming them in FP64; the stop test
+                       //    is decided from the brackets, or reported as done = 6
+                       //    where they overlap (the host then forms both norms)
 };
 
 // Tensor maps of the TMA-staged Newton kernel (3D maps over the padded

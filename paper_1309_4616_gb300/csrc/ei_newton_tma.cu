@@ -121,12 +121,27 @@ __device__ __forceinline__ bool mbar_wait_bounded(uint32_t bar, uint32_t parity,
 
 static constexpr uint64_t kWaitLimitNs = 500000000ull;  // 0.5 s; a plane lands in microseconds
 
+// Bracket steps: the scale exponent k that brings a mean square ms to about 1
+// (2^k times the root mean square), 0 where ms is 0 or not finite
+__device__ __forceinline__ int bracket_exponent(double ms) {
+  if (!(ms > 0.0 && ms < INFINITY)) return 0;
+  return max(-480, min(480, -(ilogb(ms) >> 1)));
+}
+// |v| 2^k cut to a float from v's high word (rebias = (896 - k) << 20, 896
+// being FP64's exponent bias less FP32's): 0 below FP32's normal range, Inf
+// above it
+__device__ __forceinline__ float bracket_cut(double v, int rebias) {
+  const int r = min(max((__double2hiint(v) & 0x7fffffff) - rebias, 0), 0x0ff00000);
+  return __int_as_float(r << 3);
+}
+
 // PRE: the coefficient tiles hold the scaled operator (A - cI)/gamma (native
 // FP64 only), so w_{j+1} = (A w_j - c w_j)/gamma - xi_j w_j is the 7-point sum
 // and one FMA with -xi_j: the FP64 pipe bounds this kernel, and the scaling
 // saves it a multiply per point.
-// PN: form ||p_{j+1}||^2 (false only with s.pbound: the stop test then uses
-// a bound, and the FP64-bound native kernel saves an FMA a point)
+// PN: form both squared norms in FP64 (false only with s.bracket, native
+// FP64: both are bracketed in FP32, which saves the FP64-bound kernel two FMAs
+// a point)
 template <int FMT, bool PRE, bool PN = true>
 __global__ void __launch_bounds__(256, TmaCfg<FMT>::MINB)
 k_newton_tma(const __grid_constant__ NewtonMaps M, const StencilDev g, const NewtonScalars s,
@@ -164,20 +179,21 @@ k_newton_tma(const __grid_constant__ NewtonMaps M, const StencilDev g, const New
   const P d0 = from_d<P>(s.d0);
   typename Acc<T>::type aw = Acc<T>::zero();
   typename Acc<P>::type ap = Acc<P>::zero();
-  // bound mode (!PN, native FP64): ||w_{j+1}||^2 is only bracketed, by an FP32
-  // sum of t^2 where t is |w| cut to its high word: sign cleared, exponent
-  // rebiased so that the last iterate's root mean square lands near 1 (scale
-  // 2^kexp), 20 mantissa bits kept.  t <= |w| 2^kexp < t (1 + 2^-20) wherever
-  // t is a normal float; a |w| below that range gives t = 0, one above it
-  // (or an Inf or NaN) gives t = Inf.  The integer work keeps the FP64 pipe
-  // for the iteration itself.
-  int kexp = 0, rebias = 896 << 20;  // FP64 exponent bias 1023 - FP32's 127
-  float awf = 0.f;
+  // bracket steps (!PN, native FP64): ||w_{j+1}||^2 and ||p_{j+1}||^2 are only
+  // bracketed, each by an FP32 sum of t^2 where t is the value cut to its high
+  // word: sign cleared, exponent rebiased so that the last step's root mean
+  // square lands near 1 (scale 2^k), 20 mantissa bits kept.  Then
+  // t <= |v| 2^k < t (1 + 2^-20) wherever t is a normal float; a |v| below
+  // that range gives t = 0, one above it (or an Inf or NaN) t = Inf.  The
+  // integer work keeps the FP64 pipe for the iteration itself.
+  int kw = 0, kp = 0;
+  float awf = 0.f, apf = 0.f;
   if constexpr (!PN) {
-    const double ms = ctl->nw2 / ((double)g.nx * g.ny * g.nz);
-    if (ms > 0.0 && ms < INFINITY) kexp = max(-480, min(480, -(ilogb(ms) >> 1)));
-    rebias = (896 - kexp) << 20;
+    const double npts = (double)g.nx * g.ny * g.nz;
+    kw = bracket_exponent(ctl->nw2 / npts);
+    kp = bracket_exponent(ctl->np2 / npts);
   }
+  const int rebias_w = (896 - kw) << 20, rebias_p = (896 - kp) << 20;
   T* __restrict__ w_out = static_cast<T*>(w_out_);
   P* __restrict__ p = static_cast<P*>(p_);
   const int wi = (ty + 1) * C::WX + tx + C::HX;
@@ -264,9 +280,9 @@ k_newton_tma(const __grid_constant__ NewtonMaps M, const StencilDev g, const New
           aw = acc_sq(aw, wn);
           ap = acc_sq(ap, pn);
         } else {
-          const int r = min(max((__double2hiint(wn) & 0x7fffffff) - rebias, 0), 0x0ff00000);
-          const float t = __int_as_float(r << 3);
-          awf = fmaf(t, t, awf);
+          const float tw = bracket_cut(wn, rebias_w), tp = bracket_cut(pn, rebias_p);
+          awf = fmaf(tw, tw, awf);
+          apf = fmaf(tp, tp, apf);
         }
       }
       // every plane: the slots read here are reissued only after this barrier
@@ -285,9 +301,11 @@ k_newton_tma(const __grid_constant__ NewtonMaps M, const StencilDev g, const New
       mbar_wait_bounded(bar0 + 8 * (q % C::NBAR), (q / C::NBAR) & 1, kWaitLimitNs / 8);
   }
 
-  // 2^(-2 kexp): back from the rebiased FP32 squares (exact)
-  const double unscale = __hiloint2double((1023 - 2 * kexp) << 20, 0);
-  double nw2 = PN ? acc_d(aw) : (double)awf * unscale, np2 = acc_d(ap);
+  // 2^(-2k): back from the rebiased FP32 squares (exact)
+  const double unscale_w = __hiloint2double((1023 - 2 * kw) << 20, 0);
+  const double unscale_p = __hiloint2double((1023 - 2 * kp) << 20, 0);
+  double nw2 = PN ? acc_d(aw) : (double)awf * unscale_w;
+  double np2 = PN ? acc_d(ap) : (double)apf * unscale_p;
   if (last_block_reduce2<RED_SUM>(nw2, np2, partials, ctl)) {
     if (tid == 0) {
       ctl->nw2 = nw2;
@@ -295,19 +313,25 @@ k_newton_tma(const __grid_constant__ NewtonMaps M, const StencilDev g, const New
       if constexpr (PN) {
         newton_verdict(ctl, s, s.j + 1, s.d_next, nw2, np2);
       } else {
-        // The bracket of ||w_{j+1}||^2: each thread's FP32 sum has at most
-        // `terms` roundings of relative 2^-24 (gam bounds their effect), each
-        // cut value lies within a factor 1 + 2^-20 below |w|, and an element
-        // that left FP32's normal range or a square that went subnormal is
-        // off by less than 2^-140 in the rebiased scale (slack).  The FP64
-        // reductions of the thread sums add far less than the 1e-9 margin.
+        // The brackets: each thread's FP32 sum has at most `terms` roundings
+        // of relative 2^-24 (gam bounds their effect), each cut value lies
+        // within a factor 1 + 2^-20 below the true magnitude, and a value that
+        // left FP32's normal range or a square that went subnormal is off by
+        // less than 2^-140 in the rebiased scale (slack).  The FP64 reductions
+        // of the thread sums add far less than the 1e-9 margins.
         const double terms = (double)((units + gridDim.x - 1) / gridDim.x);
         const double gam = terms * 0x1p-24 / (1.0 - terms * 0x1p-24);
-        const double slack = (double)g.nx * g.ny * g.nz * 0x1p-140 * unscale;
-        const double cut = 1.0 + 0x1p-20;
-        const double lo = fmax(nw2 - slack, 0.0) / (1.0 + gam) * (1.0 - 1e-9);
-        const double hi = (nw2 / (1.0 - gam) * (1.0 + 1e-9) + slack) * cut * cut;
-        newton_verdict(ctl, s, s.j + 1, s.d_next, lo, np2, hi);
+        const double npts = (double)g.nx * g.ny * g.nz;
+        const double cut2 = (1.0 + 0x1p-20) * (1.0 + 0x1p-20);
+        auto lo = [&](double v, double slack) {
+          return fmax(v - slack, 0.0) / (1.0 + gam) * (1.0 - 1e-9);
+        };
+        auto hi = [&](double v, double slack) {
+          return (v / (1.0 - gam) * (1.0 + 1e-9) + slack) * cut2;
+        };
+        const double sw = npts * 0x1p-140 * unscale_w, sp = npts * 0x1p-140 * unscale_p;
+        newton_verdict(ctl, s, s.j + 1, s.d_next, lo(nw2, sw), lo(np2, sp), hi(nw2, sw),
+                       hi(np2, sp));
       }
     }
   }
@@ -702,7 +726,7 @@ cudaError_t launch_newton_tma(const StencilDev& g, const NewtonMaps& M, void* w_
                               cudaStream_t st, bool prescaled) {
   if (fmt == VF_DF) return launch_one<VF_DF, false>(g, M, w_out, p, s, partials, ctl, st);
   if (fmt == VF_F64) {
-    if (prescaled && s.pbound)
+    if (prescaled && s.bracket)
       return launch_one<VF_F64, true, false>(g, M, w_out, p, s, partials, ctl, st);
     if (prescaled) return launch_one<VF_F64, true>(g, M, w_out, p, s, partials, ctl, st);
     return launch_one<VF_F64, false>(g, M, w_out, p, s, partials, ctl, st);

@@ -475,34 +475,93 @@ def test_step_host_paths_match_device(env, method):
     ctx.close()
 
 
-def test_native_p_bound_rechecks(env, xi):
-    """Native FP64 stencil steps well before the a-priori degree skip forming
-    ||p|| and decide their stop tests by the bound ||p_j|| + |d| ||w||.  With a
-    smooth v the a posteriori degree (55) falls below the a-priori one (65), so
-    the bound meets an undecidable test and the host takes it with ||p|| formed:
-    the result, the degree and the substep count must still be the oracle's."""
-    torch, ei = env
+def _smooth_case():
     n = (37, 29, 21)
     shape = (21, 29, 37)
     dx = (1 / 37,) * 3
     z, y, x = np.meshgrid(*(np.arange(k) + 0.5 for k in shape), indexing="ij")
     D = 1 + 0.3 * np.sin(np.pi * x / 37) * np.cos(np.pi * y / 29)
     v0 = np.cos(np.pi * x / 37) * np.cos(np.pi * y / 29) + 0.5 * np.cos(np.pi * z / 21)
+    return n, dx, D, v0
+
+
+@pytest.mark.parametrize("side", [1, -1])
+def test_native_bracket_rechecks(env, xi, side):
+    """Native FP64 stencil steps after the first bracket ||w|| and ||p|| in FP32
+    and take the stop test from the brackets.  A tol set 1e-7 (relative) above
+    or below the oracle's estimate ratio |d_m| ||w_m|| / ||p_m|| at a degree m
+    leaves the brackets (about 1e-6 wide on this grid) undecided there, so the
+    host forms both norms and takes the test: converged at m (side 1), or not,
+    going on with the norms formed to converge at m + 1 (side -1).  The result,
+    the degree and the substep count must be the oracle's."""
+    torch, ei = env
+    n, dx, D, v0 = _smooth_case()
     op = O.StencilOperator(n, dx, D, (0.0, 0.0, 0.0), bc=(O.NEUMANN0,) * 6)
-    h, tol = 1e-2, 1e-10
+    h = 1e-2
+    _, ost0 = Nw.phi_apply(op, 1, h, v0, 1e-10, xi=xi)
+    assert ost0.s == 1
+    # the oracle's estimate ratios of the Newton loop on v (s = 1, tau = h);
+    # they are not monotone: m is the last degree below the tol-1e-10 one whose
+    # ratio is a new minimum by 1 %, with the next lower one 1 % below it and
+    # none within 1 % of it in between
+    alpha, beta = op.gershgorin()
+    c, gamma = 0.5 * (alpha + beta), 0.25 * (beta - alpha)
+    d = L.divided_differences(1, h, c, gamma, xi[:101])
+    w = v0.copy()
+    p = d[0] * w
+    ratios = []
+    for j in range(ost0.degrees[0] + 20):
+        w = op.matvec(w) / gamma - (c / gamma + xi[j]) * w
+        p = p + d[j + 1] * w
+        ratios.append(abs(d[j + 1]) * np.linalg.norm(w) / np.linalg.norm(p))
+
+    def first_pass(t):
+        return next(i + 1 for i, r in enumerate(ratios) if r <= t)
+
+    def clear(k):
+        t = ratios[k - 1]
+        if k < 3 or not min(ratios[:k - 1]) > 1.01 * t:
+            return False
+        nxt = first_pass(0.99 * t)
+        return all(not (0.99 * t <= r <= 1.01 * t) for r in ratios[k:nxt - 1])
+
+    m = max(k for k in range(3, ost0.degrees[0]) if clear(k))
+    tol = ratios[m - 1] * (1.0 + side * 1e-7)
+    expect = m if side > 0 else first_pass(tol)
     ref, ost = Nw.phi_apply(op, 1, h, v0, tol, xi=xi)
-    assert ost.m_sched - ost.degrees[0] >= 8
+    assert ost.s == 1 and ost.degrees == [expect]
     ctx = stencil_context(torch, ei, n, dx, D, (0.0, 0.0, 0.0), 0.0, (1,) * 6)
     v = dev(torch, v0)
     out = torch.empty_like(v)
     st = ctx.phi_apply(1, h, v, out, tol, {"arith": ei.ARITH_NATIVE_F64})
-    assert st.p_rechecks >= 1 and st.arith_used == ei.ARITH_NATIVE_F64
+    assert st.p_rechecks == 1 and st.arith_used == ei.ARITH_NATIVE_F64
     assert rel_err(out.cpu().numpy(), ref) <= FP64_TOL
     _check_stats(st, ost)
+    # the same call in float-float forms its norms in every step
     st = ctx.phi_apply(1, h, v, out, tol, {"arith": ei.ARITH_DF})
     assert st.p_rechecks == 0
     assert rel_err(out.cpu().numpy(), ref) <= FP64_TOL
     _check_stats(st, ost)
+    ctx.close()
+
+
+def test_native_brackets_decide(env, xi):
+    """At an ordinary tol the brackets decide every test: no recheck, and the
+    oracle's result and degree."""
+    torch, ei = env
+    n, dx, D, v0 = _smooth_case()
+    op = O.StencilOperator(n, dx, D, (0.0, 0.0, 0.0), bc=(O.NEUMANN0,) * 6)
+    h, tol = 1e-2, 1e-10
+    ref, ost = Nw.phi_apply(op, 1, h, v0, tol, xi=xi)
+    ctx = stencil_context(torch, ei, n, dx, D, (0.0, 0.0, 0.0), 0.0, (1,) * 6)
+    v = dev(torch, v0)
+    out = torch.empty_like(v)
+    st = ctx.phi_apply(1, h, v, out, tol, {"arith": ei.ARITH_NATIVE_F64, "profile": 1})
+    assert st.p_rechecks == 0
+    assert st.newton_bounded == st.newton_timed - 1  # all but the first step
+    assert rel_err(out.cpu().numpy(), ref) <= FP64_TOL
+    _check_stats(st, ost)
+    ctx.close()
 
 
 def test_native_successive_steps_rescaled_operator(env, xi):
