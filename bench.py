@@ -67,8 +67,9 @@ SMS, FP64_FLOPS_PER_SM_CLK = 152, 4
 # Valid for the kernel as captured: retake it when the kernel changes.
 PAIR_DRAM_BYTES_PER_POINT = 86.9
 # the same for one launch of the native-FP64 one-iteration kernel on the scaled
-# operator, from ncu on 192^3 (profiles/k_newton_tma_double_192cube.md)
-NATIVE_DRAM_BYTES_PER_POINT = 86.1
+# operator (a bracket step), from ncu on 192^3
+# (profiles/k_newton_tma_double_192cube.md)
+NATIVE_DRAM_BYTES_PER_POINT = 90.8
 # DRAM bytes of one launch of the float-float sliced complex CSR kernel on the
 # 21-spin operator (profiles/k_csr_newton_sell_c_spin_bath_21.md)
 SPIN_DRAM_BYTES_PER_LAUNCH = 1.237e9

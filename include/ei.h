@@ -80,7 +80,11 @@ enum { EI_PREC_F64 = 0, EI_PREC_F32 = 1 };
  *     max |u| <= 2^20, rho max|u| <= 2^40 and ||A u + g(u)||^2 in
  *     [2^-60, 2^100].  Any other call runs in native FP64, and
  *     ei_stats.arith_used says which arithmetic ran.
- *   EI_ARITH_NATIVE_F64: IEEE double throughout. */
+ *   EI_ARITH_NATIVE_F64: every vector value in IEEE double.  On stencil
+ *     operators the Newton steps after a loop's first bracket the squared
+ *     norms of the stop test in FP32, with proven bounds, and take any test
+ *     the brackets cannot decide with FP64 norms (ei_stats.p_rechecks): each
+ *     decision is the one the exact norms give. */
 enum { EI_ARITH_DF = 0, EI_ARITH_NATIVE_F64 = 1 };
 
 enum { EI_EXP_EULER = 0, EI_EXP_ROSENBROCK = 1 };
