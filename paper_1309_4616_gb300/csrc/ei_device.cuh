@@ -53,6 +53,7 @@ __device__ __forceinline__ double to_p(double x) { return x; }
 
 __device__ __forceinline__ bool finite_d(double x) { return isfinite(x); }
 
+
 // Verdict after the Newton step reaching degree `deg`, with squared norms nw2
 // of w_deg and np2 of p_deg and coefficient d = d_deg.  Adaptive mode: stop
 // at the first degree whose estimate |d| ||w|| <= tol ||p|| holds (done = 1),
@@ -124,6 +125,71 @@ __device__ __forceinline__ bool newton_verdict(DevCtl* ctl, const NewtonScalars&
   }
   return false;
 }
+
+// Bracket steps of the native FP64 Newton kernels (NewtonScalars::bracket):
+// ||w_{j+1}||^2 and ||p_{j+1}||^2 are bracketed by FP32 sums of t^2, t being
+// the value cut to its high word by integer operations: sign cleared, exponent
+// rebiased so that the previous step's root mean square lands near 1 (scale
+// 2^k, from ctl->nw2 and ctl->np2), 20 mantissa bits kept.  Then
+// t <= |v| 2^k < t (1 + 2^-20) wherever t is a normal float; a |v| below that
+// range gives t = 0, one above it (or an Inf or NaN) t = Inf.  The FP64 pipe
+// is left to the iteration itself.
+struct NormBrackets {
+  int kw = 0, kp = 0, rw = 896 << 20, rp = 896 << 20;  // 896: FP64's exponent bias less FP32's
+  float aw = 0.f, ap = 0.f;
+  double npts = 1.0;
+  // the scale exponent that brings a mean square ms to about 1, 0 where ms
+  // is 0 or not finite
+  static __device__ __forceinline__ int scale_exp(double ms) {
+    if (!(ms > 0.0 && ms < INFINITY)) return 0;
+    return max(-480, min(480, -(ilogb(ms) >> 1)));
+  }
+  // |v| 2^k cut to a float (rebias = (896 - k) << 20)
+  static __device__ __forceinline__ float cut(double v, int rebias) {
+    const int r = min(max((__double2hiint(v) & 0x7fffffff) - rebias, 0), 0x0ff00000);
+    return __int_as_float(r << 3);
+  }
+  // 2^(-2k), exact
+  static __device__ __forceinline__ double unscale(int k) {
+    return __hiloint2double((1023 - 2 * k) << 20, 0);
+  }
+  __device__ __forceinline__ void init(const DevCtl* ctl, double n) {
+    npts = n;
+    kw = scale_exp(ctl->nw2 / n);
+    kp = scale_exp(ctl->np2 / n);
+    rw = (896 - kw) << 20;
+    rp = (896 - kp) << 20;
+  }
+  __device__ __forceinline__ void add(double w, double p) {
+    const float tw = cut(w, rw), tp = cut(p, rp);
+    aw = fmaf(tw, tw, aw);
+    ap = fmaf(tp, tp, ap);
+  }
+  // this thread's sums back in the unscaled units (exact)
+  __device__ __forceinline__ double sum_w() const { return (double)aw * unscale(kw); }
+  __device__ __forceinline__ double sum_p() const { return (double)ap * unscale(kp); }
+  // The verdict on the grid's sums nw2, np2 of sum_w, sum_p, `terms` the most
+  // values one thread added.  Each thread's FP32 sum has at most `terms`
+  // roundings of relative 2^-24 (gam bounds their effect), each cut value
+  // lies within a factor 1 + 2^-20 below the true magnitude, and a value that
+  // left FP32's normal range or a square that went subnormal is off by less
+  // than 2^-140 in the rebiased scale (slack).  The FP64 reductions of the
+  // thread sums add far less than the 1e-9 margins.
+  __device__ __forceinline__ bool verdict(DevCtl* ctl, const NewtonScalars& s, double nw2,
+                                          double np2, double terms) const {
+    const double gam = terms * 0x1p-24 / (1.0 - terms * 0x1p-24);
+    const double cut2 = (1.0 + 0x1p-20) * (1.0 + 0x1p-20);
+    const double sw = npts * 0x1p-140 * unscale(kw), sp = npts * 0x1p-140 * unscale(kp);
+    auto lo = [&](double v, double slack) {
+      return fmax(v - slack, 0.0) / (1.0 + gam) * (1.0 - 1e-9);
+    };
+    auto hi = [&](double v, double slack) {
+      return (v / (1.0 - gam) * (1.0 + 1e-9) + slack) * cut2;
+    };
+    return newton_verdict(ctl, s, s.j + 1, s.d_next, lo(nw2, sw), lo(np2, sp), hi(nw2, sw),
+                          hi(np2, sp));
+  }
+};
 
 // Gershgorin min/max accumulation of one row's bounds.  fmin/fmax drop a NaN
 // operand, so a row with a NaN bound widens the pair to (-inf, +inf) instead:

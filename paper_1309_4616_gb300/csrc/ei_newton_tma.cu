@@ -121,20 +121,6 @@ __device__ __forceinline__ bool mbar_wait_bounded(uint32_t bar, uint32_t parity,
 
 static constexpr uint64_t kWaitLimitNs = 500000000ull;  // 0.5 s; a plane lands in microseconds
 
-// Bracket steps: the scale exponent k that brings a mean square ms to about 1
-// (2^k times the root mean square), 0 where ms is 0 or not finite
-__device__ __forceinline__ int bracket_exponent(double ms) {
-  if (!(ms > 0.0 && ms < INFINITY)) return 0;
-  return max(-480, min(480, -(ilogb(ms) >> 1)));
-}
-// |v| 2^k cut to a float from v's high word (rebias = (896 - k) << 20, 896
-// being FP64's exponent bias less FP32's): 0 below FP32's normal range, Inf
-// above it
-__device__ __forceinline__ float bracket_cut(double v, int rebias) {
-  const int r = min(max((__double2hiint(v) & 0x7fffffff) - rebias, 0), 0x0ff00000);
-  return __int_as_float(r << 3);
-}
-
 // PRE: the coefficient tiles hold the scaled operator (A - cI)/gamma (native
 // FP64 only), so w_{j+1} = (A w_j - c w_j)/gamma - xi_j w_j is the 7-point sum
 // and one FMA with -xi_j: the FP64 pipe bounds this kernel, and the scaling
@@ -180,20 +166,9 @@ k_newton_tma(const __grid_constant__ NewtonMaps M, const StencilDev g, const New
   typename Acc<T>::type aw = Acc<T>::zero();
   typename Acc<P>::type ap = Acc<P>::zero();
   // bracket steps (!PN, native FP64): ||w_{j+1}||^2 and ||p_{j+1}||^2 are only
-  // bracketed, each by an FP32 sum of t^2 where t is the value cut to its high
-  // word: sign cleared, exponent rebiased so that the last step's root mean
-  // square lands near 1 (scale 2^k), 20 mantissa bits kept.  Then
-  // t <= |v| 2^k < t (1 + 2^-20) wherever t is a normal float; a |v| below
-  // that range gives t = 0, one above it (or an Inf or NaN) t = Inf.  The
-  // integer work keeps the FP64 pipe for the iteration itself.
-  int kw = 0, kp = 0;
-  float awf = 0.f, apf = 0.f;
-  if constexpr (!PN) {
-    const double npts = (double)g.nx * g.ny * g.nz;
-    kw = bracket_exponent(ctl->nw2 / npts);
-    kp = bracket_exponent(ctl->np2 / npts);
-  }
-  const int rebias_w = (896 - kw) << 20, rebias_p = (896 - kp) << 20;
+  // bracketed, in FP32 off the FP64 pipe (NormBrackets)
+  NormBrackets br;
+  if constexpr (!PN) br.init(ctl, (double)g.nx * g.ny * g.nz);
   T* __restrict__ w_out = static_cast<T*>(w_out_);
   P* __restrict__ p = static_cast<P*>(p_);
   const int wi = (ty + 1) * C::WX + tx + C::HX;
@@ -280,9 +255,7 @@ k_newton_tma(const __grid_constant__ NewtonMaps M, const StencilDev g, const New
           aw = acc_sq(aw, wn);
           ap = acc_sq(ap, pn);
         } else {
-          const float tw = bracket_cut(wn, rebias_w), tp = bracket_cut(pn, rebias_p);
-          awf = fmaf(tw, tw, awf);
-          apf = fmaf(tp, tp, apf);
+          br.add(wn, pn);
         }
       }
       // every plane: the slots read here are reissued only after this barrier
@@ -301,38 +274,15 @@ k_newton_tma(const __grid_constant__ NewtonMaps M, const StencilDev g, const New
       mbar_wait_bounded(bar0 + 8 * (q % C::NBAR), (q / C::NBAR) & 1, kWaitLimitNs / 8);
   }
 
-  // 2^(-2k): back from the rebiased FP32 squares (exact)
-  const double unscale_w = __hiloint2double((1023 - 2 * kw) << 20, 0);
-  const double unscale_p = __hiloint2double((1023 - 2 * kp) << 20, 0);
-  double nw2 = PN ? acc_d(aw) : (double)awf * unscale_w;
-  double np2 = PN ? acc_d(ap) : (double)apf * unscale_p;
+  double nw2 = PN ? acc_d(aw) : br.sum_w(), np2 = PN ? acc_d(ap) : br.sum_p();
   if (last_block_reduce2<RED_SUM>(nw2, np2, partials, ctl)) {
     if (tid == 0) {
       ctl->nw2 = nw2;
       ctl->np2 = np2;
-      if constexpr (PN) {
+      if constexpr (PN)
         newton_verdict(ctl, s, s.j + 1, s.d_next, nw2, np2);
-      } else {
-        // The brackets: each thread's FP32 sum has at most `terms` roundings
-        // of relative 2^-24 (gam bounds their effect), each cut value lies
-        // within a factor 1 + 2^-20 below the true magnitude, and a value that
-        // left FP32's normal range or a square that went subnormal is off by
-        // less than 2^-140 in the rebiased scale (slack).  The FP64 reductions
-        // of the thread sums add far less than the 1e-9 margins.
-        const double terms = (double)((units + gridDim.x - 1) / gridDim.x);
-        const double gam = terms * 0x1p-24 / (1.0 - terms * 0x1p-24);
-        const double npts = (double)g.nx * g.ny * g.nz;
-        const double cut2 = (1.0 + 0x1p-20) * (1.0 + 0x1p-20);
-        auto lo = [&](double v, double slack) {
-          return fmax(v - slack, 0.0) / (1.0 + gam) * (1.0 - 1e-9);
-        };
-        auto hi = [&](double v, double slack) {
-          return (v / (1.0 - gam) * (1.0 + 1e-9) + slack) * cut2;
-        };
-        const double sw = npts * 0x1p-140 * unscale_w, sp = npts * 0x1p-140 * unscale_p;
-        newton_verdict(ctl, s, s.j + 1, s.d_next, lo(nw2, sw), lo(np2, sp), hi(nw2, sw),
-                       hi(np2, sp));
-      }
+      else
+        br.verdict(ctl, s, nw2, np2, (double)((units + gridDim.x - 1) / gridDim.x));
     }
   }
 }

@@ -485,29 +485,19 @@ def _smooth_case():
     return n, dx, D, v0
 
 
-@pytest.mark.parametrize("side", [1, -1])
-def test_native_bracket_rechecks(env, xi, side):
-    """Native FP64 stencil steps after the first bracket ||w|| and ||p|| in FP32
-    and take the stop test from the brackets.  A tol set 1e-7 (relative) above
-    or below the oracle's estimate ratio |d_m| ||w_m|| / ||p_m|| at a degree m
-    leaves the brackets (about 1e-6 wide on this grid) undecided there, so the
-    host forms both norms and takes the test: converged at m (side 1), or not,
-    going on with the norms formed to converge at m + 1 (side -1).  The result,
-    the degree and the substep count must be the oracle's."""
-    torch, ei = env
-    n, dx, D, v0 = _smooth_case()
-    op = O.StencilOperator(n, dx, D, (0.0, 0.0, 0.0), bc=(O.NEUMANN0,) * 6)
-    h = 1e-2
+def _bracket_tol(op, v0, h, xi, side):
+    """A tol 1e-7 (relative) above (side 1) or below (side -1) the oracle's
+    estimate ratio |d_m| ||w_m|| / ||p_m|| at a degree m of the Newton loop on
+    v0 (s = 1, tau = h), and the degree the oracle then stops at.  The ratios
+    are not monotone: m is the last degree below the tol-1e-10 one whose ratio
+    is a new minimum by 1 %, with the next lower one 1 % below it and none
+    within 1 % of it in between."""
     _, ost0 = Nw.phi_apply(op, 1, h, v0, 1e-10, xi=xi)
     assert ost0.s == 1
-    # the oracle's estimate ratios of the Newton loop on v (s = 1, tau = h);
-    # they are not monotone: m is the last degree below the tol-1e-10 one whose
-    # ratio is a new minimum by 1 %, with the next lower one 1 % below it and
-    # none within 1 % of it in between
     alpha, beta = op.gershgorin()
     c, gamma = 0.5 * (alpha + beta), 0.25 * (beta - alpha)
     d = L.divided_differences(1, h, c, gamma, xi[:101])
-    w = v0.copy()
+    w = np.array(v0, dtype=np.float64).reshape(op.shape)
     p = d[0] * w
     ratios = []
     for j in range(ost0.degrees[0] + 20):
@@ -527,7 +517,23 @@ def test_native_bracket_rechecks(env, xi, side):
 
     m = max(k for k in range(3, ost0.degrees[0]) if clear(k))
     tol = ratios[m - 1] * (1.0 + side * 1e-7)
-    expect = m if side > 0 else first_pass(tol)
+    return tol, (m if side > 0 else first_pass(tol))
+
+
+@pytest.mark.parametrize("side", [1, -1])
+def test_native_bracket_rechecks(env, xi, side):
+    """Native FP64 stencil steps after the first bracket ||w|| and ||p|| in FP32
+    and take the stop test from the brackets.  A tol 1e-7 from the oracle's
+    estimate ratio at a degree m (_bracket_tol) leaves the brackets (about 1e-6
+    wide on this grid) undecided there, so the host forms both norms and takes
+    the test: converged at m (side 1), or not, going on with the norms formed
+    (side -1).  The result, the degree and the substep count must be the
+    oracle's."""
+    torch, ei = env
+    n, dx, D, v0 = _smooth_case()
+    op = O.StencilOperator(n, dx, D, (0.0, 0.0, 0.0), bc=(O.NEUMANN0,) * 6)
+    h = 1e-2
+    tol, expect = _bracket_tol(op, v0, h, xi, side)
     ref, ost = Nw.phi_apply(op, 1, h, v0, tol, xi=xi)
     assert ost.s == 1 and ost.degrees == [expect]
     ctx = stencil_context(torch, ei, n, dx, D, (0.0, 0.0, 0.0), 0.0, (1,) * 6)
