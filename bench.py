@@ -92,7 +92,8 @@ def parse():
     # batch workloads: fixed tile height instead of the autotuner (profiling)
     ap.add_argument("--tile-rows", type=int, default=0, help=argparse.SUPPRESS)
     ap.add_argument("--workload", default="adr3d",
-                    choices=["adr3d", "adr3d_ff", "adr3d_fp32", "rgg_csr", "batch", "batch_ff", "batch_fp32",
+                    choices=["adr3d", "adr3d_ff", "adr3d_fp32", "rgg_csr", "adv_diff_2d", "batch",
+                             "batch_ff", "batch_fp32",
                              "adr3d_learned", "adr3d_fp32_learned", "rgg_csr_learned",
                              "batch_learned_fp32", "batch_plain_fp64_loop", "combustion",
                              "combustion_fast", "combustion_nonlin", "heat_dirichlet_data",
@@ -579,6 +580,59 @@ class RggCsr(Workload):
         return f"k_csr_newton_sell<{fmt}> (slices of 32 rows, a lane a row)"
 
 
+class AdvDiff2d(Workload):
+    """phi_1(hA)v on the 64 x 64 advection-diffusion operator (homogeneous
+    Dirichlet, D = 0.1, b = (-1, -0.5), h = 1e-3, tol 1e-10), the small
+    configuration, in native FP64 (arith = 1; 0: the float-float form).  A call
+    moves 131 KB: it is bound by launch and synchronisation latency."""
+
+    arith = 1
+
+    def __init__(self, torch, ei, W, dev, ctx, n):
+        self.name, self.method = f"adv_diff_2d_{n}_phi1", "phi1"
+        self.ei = ei
+        self.set_arith(self.arith)
+        w = W.adv_diff_2d(n=n)
+        self.w = w
+        self.npts = n * n
+        ctx.set_operator_stencil(w.n, w.dx, w.D, [w.b[0], w.b[1]], 0.0, list(w.bc),
+                                 ei.PREC_F64)
+        self.h, self.tol = w.h, w.tol
+        self.host0 = w.v
+        self.state0 = torch.from_numpy(w.v).to(dev)
+        self.state = self.state0.clone()
+        self.out = torch.empty_like(self.state)
+        self.bytes_per_point = 32.0  # w 8 + w' 8 + p 16 (constant coefficients)
+        self.config = {"grid": [n, n], "h": self.h, "tol": self.tol, "bc": "dirichlet",
+                       "method": self.method}
+
+    traffic_per_launch = None
+    l2_note = ("inputs fit in L2 (32 KB a vector) and L2 is not flushed: the call is "
+               "bound by launch and synchronisation latency, not by memory")
+
+    def set_arith(self, arith):
+        self.arith = arith
+        self.dtype = "f64" if arith else DTYPE_FF
+
+    def _o(self, opts):
+        o = {"arith": self.arith}
+        o.update(opts or {})
+        return o
+
+    def step(self, ctx, opts=None):
+        return ctx.phi_apply(1, self.h, self.state, self.out, self.tol, self._o(opts))
+
+    def step_host(self, ctx, host, opts=None):
+        d = host.to(self.state.device, non_blocking=True)
+        st = ctx.phi_apply(1, self.h, d, self.out, self.tol, self._o(opts))
+        pinned_like(self, host).copy_(self.out, non_blocking=False)
+        return st
+
+    def kernel(self, fused):
+        fmt = "double" if self.arith else "float-float"
+        return f"k_newton_tma<{fmt}> / k_newton2_tma (64 x 64, latency-bound)"
+
+
 class PhiKAdr3d(Adr3d):
     """phi_2(hA)v on the 256^3 advection-diffusion operator of the headline
     workload, h = 5e-4 (h rho ~ 600: the a-priori rule takes several substeps,
@@ -904,7 +958,8 @@ class RggCsrLearned(Learned, RggCsr):
         self.setup_learned(ctx)
 
 
-WORKLOADS = {"adr3d": Adr3d, "adr3d_ff": Adr3dFF, "adr3d_fp32": Adr3dFp32, "rgg_csr": RggCsr, "batch": Batch2d, "batch_ff": Batch2dFF,
+WORKLOADS = {"adr3d": Adr3d, "adr3d_ff": Adr3dFF, "adr3d_fp32": Adr3dFp32, "rgg_csr": RggCsr,
+             "adv_diff_2d": AdvDiff2d, "batch": Batch2d, "batch_ff": Batch2dFF,
              "batch_fp32": Batch2dFp32, "adr3d_learned": Adr3dLearned,
              "adr3d_fp32_learned": Adr3dFp32Learned, "rgg_csr_learned": RggCsrLearned,
              "batch_learned_fp32": Batch2dLearnedFp32, "batch_plain_fp64_loop": Batch2dPlainLoop,
@@ -912,7 +967,8 @@ WORKLOADS = {"adr3d": Adr3d, "adr3d_ff": Adr3dFF, "adr3d_fp32": Adr3dFp32, "rgg_
              "combustion_nonlin": NonlinEval, "heat_dirichlet_data": HeatDirichlet,
              "heat_dirichlet_hom": HeatDirichletHom, "phi2_adr3d": PhiKAdr3d,
              "spin_bath": SpinBath, "spin_bath_fp32": SpinBathFp32}
-DEFAULT_N = {"adr3d": N_SIDE, "adr3d_ff": N_SIDE, "adr3d_fp32": 512, "rgg_csr": 1 << 20, "batch": 1024, "batch_ff": 1024,
+DEFAULT_N = {"adr3d": N_SIDE, "adr3d_ff": N_SIDE, "adr3d_fp32": 512, "rgg_csr": 1 << 20,
+             "adv_diff_2d": 64, "batch": 1024, "batch_ff": 1024,
              "batch_fp32": 1024, "adr3d_learned": N_SIDE, "adr3d_fp32_learned": 512,
              "rgg_csr_learned": 1 << 20, "batch_learned_fp32": 1024,
              "batch_plain_fp64_loop": 1024, "combustion": N_SIDE, "combustion_fast": N_SIDE,
@@ -1145,6 +1201,43 @@ def cpu_leg(w, gpu_states, gpu_stats):
     return cpu, errs
 
 
+def cpu_leg_phi(wl, gpu_out, gpu_stats):
+    """The oracle on the host for a phi_1(hA)v workload (graph or 2D stencil):
+    the whole call with the serial oracle (the cpu_baseline, calls/s), and the
+    relative error of each GPU form's result against it (full vector)."""
+    from oracle import leja as L
+    from oracle import newton as Nw
+    from oracle import operators as O
+    from paper_1309_4616_gb300 import workloads as W
+
+    xi = L.leja_points(100)
+    if isinstance(wl, RggCsr):
+        g = W.rgg_graph(n=wl.npts)
+        op = O.CsrOperator(g.n, g.rowptr, g.col, g.val, -g.deg_w)
+        what = f"one phi_1(hA)v call on the {g.n}-node graph"
+    else:
+        w = wl.w
+        op = O.StencilOperator(w.n, w.dx, w.D, w.b, bc=w.bc)
+        what = f"one phi_1(hA)v call on the {w.n[0]} x {w.n[1]} grid"
+    t0 = time.perf_counter()
+    ref, ost = Nw.phi_apply(op, 1, wl.h, wl.host0, wl.tol, xi=xi)
+    t_serial = time.perf_counter() - t0
+    ref = np.asarray(ref).ravel()
+    errs = {}
+    for name, got in gpu_out.items():
+        gst = gpu_stats[name]
+        errs[name] = {"value": float(np.linalg.norm(got.ravel() - ref) / np.linalg.norm(ref)),
+                      "of": "||out_gpu - out_oracle|| / ||out_oracle||, full vector, FP64 oracle",
+                      "bound": 1e-9,
+                      "s_and_degrees_match_oracle": bool(gst.s == ost.s and
+                                                         gst.degree_list() == list(ost.degrees))}
+    cpu = {"value": 1.0 / t_serial, "unit": "steps/s", "cores": 1, "kind": "oracle",
+           "sample": (f"{what} with the serial oracle (numpy, 1 thread): {t_serial:.2f} s, "
+                      f"s = {ost.s}, degrees {list(ost.degrees)}"),
+           "nproc": os.cpu_count()}
+    return cpu, errs
+
+
 def run_northstar(args):
     """The comparison the learned, FP32 and batched forms are built for: the
     1024 uneven 2D problems at tol 1e-6, (a) the learned schedule with FP32
@@ -1238,13 +1331,20 @@ def run_ours(args):
     forms = None
     headline = type(wl) is Adr3d
     states, stats1 = {}, {}
-    if type(wl) in (Adr3d, RggCsr):
+    phi_leg = type(wl) in (RggCsr, AdvDiff2d)
+    if type(wl) in (Adr3d, RggCsr, AdvDiff2d):
         if headline:
             states["f64"], stats1["f64"] = first_step_state(wl, ctx, torch)
+        elif phi_leg:
+            stats1["f64"] = wl.step(ctx)
+            states["f64"] = wl.out.cpu().numpy()
         wl.set_arith(0)
         rf = timed_steps(wl, ctx, args, torch, dev, stream, dist, local)
         if headline:
             states["float_float"], stats1["float_float"] = first_step_state(wl, ctx, torch)
+        elif phi_leg:
+            stats1["float_float"] = wl.step(ctx)
+            states["float_float"] = wl.out.cpu().numpy()
         froof = roofline(wl, rf, args, npts)
         forms = {"float_float": {
             "value": args.steps * world / (rf["ms"] * 1e-3), "unit": "steps/s",
@@ -1269,14 +1369,18 @@ def run_ours(args):
     if rank == 0 and world == 1 and not args.no_cpu and headline:
         cpu, errs = cpu_leg(wl.w, states, stats1)
         forms["float_float"]["rel_err"] = errs["float_float"]
+    elif rank == 0 and world == 1 and not args.no_cpu and phi_leg:
+        cpu, errs = cpu_leg_phi(wl, states, stats1)
+        forms["float_float"]["rel_err"] = errs["float_float"]
 
     if rank == 0:
         steps_total = args.steps * world
         value = steps_total / (ms * 1e-3)
         esz = u_host.element_size()
         config = {"workload": wl.name, **wl.config, "parallelism": f"replicas x{world}",
-                  "l2": "inputs larger than L2 (each vector >= 8 MB and the step's working "
-                        "set >= 0.3 GB; 256^3: 134 MB per vector)",
+                  "l2": getattr(wl, "l2_note",
+                                "inputs larger than L2 (each vector >= 8 MB and the step's "
+                                "working set >= 0.3 GB; 256^3: 134 MB per vector)"),
                   "matvecs_per_step": r["matvecs"], "degrees": r["degrees"][:3]}
         if r["learned_kept"] is not None and getattr(wl, "model", None) is not None:
             config["learned_problems_kept_per_pass"] = r["learned_kept"]
