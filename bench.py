@@ -113,6 +113,18 @@ def peaks_sm_mhz():
         return 2070.0
 
 
+# GB300's nominal HBM3e bandwidth (GB/s), reported beside the measured copy rate
+HBM_NOMINAL_GBS = 7900.0
+
+
+def with_nominal(d):
+    """An HBM roofline object with its fraction of the nominal bandwidth added."""
+    if d.get("unit") == "GB/s":
+        d["nominal_peak"] = HBM_NOMINAL_GBS
+        d["frac_nominal"] = d["achieved"] / HBM_NOMINAL_GBS
+    return d
+
+
 def peaks():
     try:
         with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
@@ -1138,7 +1150,9 @@ def roofline(wl, r, args, npts):
             out.update({"avg_launch_us": avg_launch_s * 1e6, "launches_timed": prof_n,
                         "iterations_per_launch": fused,
                         "us_per_iteration": avg_launch_s * 1e6 / fused})
-    return out
+    if isinstance(out.get("hbm"), dict):
+        with_nominal(out["hbm"])
+    return with_nominal(out)
 
 
 def first_step_state(wl, ctx, torch):

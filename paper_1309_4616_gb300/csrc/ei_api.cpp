@@ -58,6 +58,7 @@ struct Prepared {
   CUtensorMap map_in2[4];  // the same with a two-point halo (two-iteration kernel)
   CUtensorMap map_c[6];    // a[0..5]
   CUtensorMap map_diagA, map_qc, map_p;
+  CUtensorMap map_u;       // the step's state u (halo box): the TMA F pass
   // native FP64 stencils: the scaled operator (J - cI)/gamma0 of the current
   // Newton loop (a[0..5]/gamma0, (diag - c)/gamma0), keyed on the diagonal
   // array, its content version and (c, gamma).  gamma0 (off_gamma) is the
@@ -310,6 +311,7 @@ static ei_status prepare(ei_ctx* c, int fmt) {
     }
     ok = ok && encode_map(&P.map_qc, P.qc, eb, c->sd, 0);
     ok = ok && encode_map(&P.map_p, P.p, 8, c->sd, 0);
+    ok = ok && encode_map(&P.map_u, P.u, eb, c->sd, 1);
     if (!ok) { free_prepared(P); return EI_ERR_CUDA; }
   } else {
     P.coef7 = false;
@@ -1740,7 +1742,28 @@ static ei_status step_impl(ei_ctx* c, int method, double h, void* u, int nonlin,
   EI_LAUNCH(launch_import(P.u, fmt, src ? src : u, c->prec, n, geo_nx(c),
                           c->kind == KIND_STENCIL ? c->sd.ny : 1, geo_pitch(c), c->partials,
                           c->ctl, c->stream, src ? u : nullptr));
-  if (c->kind == KIND_STENCIL) {
+  // native FP64 stencils without Dirichlet data or the combustion term: F, J's
+  // diagonal and J's interval in one pass on the TMA z-march
+  bool faces = false;
+  for (int f = 0; f < 6; ++f) faces = faces || c->face_term[f] != nullptr;
+  const bool f_tma = c->kind == KIND_STENCIL && fmt == VF_F64 && P.coef7 &&
+                     c->prec == EI_PREC_F64 && !faces &&
+                     (nonlin == EI_NONLIN_NONE || nonlin == EI_NONLIN_LOGISTIC);
+  if (f_tma) {
+    NewtonMaps M;
+    M.w = P.map_u;
+    for (int k = 0; k < 6; ++k) M.c[k] = P.map_c[k];
+    M.c[6] = P.map_diagA;
+    M.p = P.map_p;
+    FStepArgs fa;
+    fa.lo = c->ger_lo;
+    fa.hi = c->ger_hi;
+    fa.nonlin = nonlin;
+    fa.rosen = rosen;
+    EI_LAUNCH(launch_f_tma(stencil_view(c, P, base_diag(P)), M, P.v, P.qc, fa, c->partials,
+                           c->ctl, c->stream));
+    ++P.qc_ver;  // qc now holds this step's J diagonal
+  } else if (c->kind == KIND_STENCIL) {
     BndFaces bnd;
     for (int f = 0; f < 6; ++f) bnd.c[f] = c->face_term[f];
     EI_LAUNCH(launch_stencil_F(stencil_view(c, P, base_diag(P)), P.u, P.v, base_diag(P), P.qc,
@@ -1750,7 +1773,7 @@ static ei_status step_impl(ei_ctx* c, int method, double h, void* u, int nonlin,
     EI_LAUNCH(launch_csr_F(csr_view(c, P, P.cbase), P.u, P.v, P.qc, P.cbase, nonlin, rosen,
                              fmt, c->partials, c->ctl, c->stream));
   }
-  if (rosen)
+  if (rosen && !f_tma)
     EI_LAUNCH(launch_shifted_minmax(n, c->ger_lo, c->ger_hi, u, c->prec, nonlin, c->partials,
                                       c->ctl, c->stream));
   EI_TRY(read_ctl(c));

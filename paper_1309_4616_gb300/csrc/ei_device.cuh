@@ -53,6 +53,18 @@ __device__ __forceinline__ double to_p(double x) { return x; }
 
 __device__ __forceinline__ bool finite_d(double x) { return isfinite(x); }
 
+// A double as a signed 64-bit key whose integer order is the value order:
+// negative values get their magnitude bits inverted (-0 sorts just below +0).
+// A NaN sorts beyond the infinity of its sign bit.  The transform is its own
+// inverse.  Running min/max on keys keep the comparisons off the FP64 pipe.
+__device__ __forceinline__ long long order_key(double v) {
+  const long long b = __double_as_longlong(v);
+  return b ^ ((b >> 63) & 0x7fffffffffffffffLL);
+}
+__device__ __forceinline__ double key_value(long long k) {
+  return __longlong_as_double(k ^ ((k >> 63) & 0x7fffffffffffffffLL));
+}
+
 
 // Verdict after the Newton step reaching degree `deg`, with squared norms nw2
 // of w_deg and np2 of p_deg and coefficient d = d_deg.  Adaptive mode: stop
@@ -533,8 +545,11 @@ __device__ bool last_block_reduce2(double& a, double& b, double* partials, DevCt
 }
 
 
-// Four sums: every block publishes its four partial sums; the last block to
-// arrive adds them in block order.  Returns true (in all its threads) there.
+// Four values in two pairs, v[0..1] combined by OPA and v[2..3] by OPB (sums
+// by default): every block publishes its four partials; the last block to
+// arrive combines them in block order.  Returns true (in all its threads)
+// there.
+template <int OPA = RED_SUM, int OPB = RED_SUM>
 __device__ inline bool last_block_reduce4(double v[4], double* partials, DevCtl* ctl) {
   __shared__ bool am_last4;
   __shared__ double f4[4];
@@ -542,8 +557,8 @@ __device__ inline bool last_block_reduce4(double v[4], double* partials, DevCtl*
   const int nthr = blockDim.x * blockDim.y * blockDim.z;
   const unsigned nblk = gridDim.x * gridDim.y * gridDim.z;
   const unsigned bid = blockIdx.x + gridDim.x * (blockIdx.y + gridDim.y * blockIdx.z);
-  block_reduce2<RED_SUM>(v[0], v[1]);
-  block_reduce2<RED_SUM>(v[2], v[3]);
+  block_reduce2<OPA>(v[0], v[1]);
+  block_reduce2<OPB>(v[2], v[3]);
   if (tid == 0) {
     for (int k = 0; k < 4; ++k) partials[4 * bid + k] = v[k];
     __threadfence();
@@ -553,11 +568,14 @@ __device__ inline bool last_block_reduce4(double v[4], double* partials, DevCtl*
   __syncthreads();
   if (!am_last4) return false;
   __threadfence();
-  double r[4] = {0.0, 0.0, 0.0, 0.0};
-  for (unsigned i = tid; i < nblk; i += nthr)
-    for (int k = 0; k < 4; ++k) r[k] += __ldcg(partials + 4 * i + k);
-  block_reduce2<RED_SUM>(r[0], r[1]);
-  block_reduce2<RED_SUM>(r[2], r[3]);
+  double r[4] = {OPA == RED_MINMAX ? INFINITY : 0.0, OPA == RED_MINMAX ? -INFINITY : 0.0,
+                 OPB == RED_MINMAX ? INFINITY : 0.0, OPB == RED_MINMAX ? -INFINITY : 0.0};
+  for (unsigned i = tid; i < nblk; i += nthr) {
+    comb<OPA>(r[0], r[1], __ldcg(partials + 4 * i), __ldcg(partials + 4 * i + 1));
+    comb<OPB>(r[2], r[3], __ldcg(partials + 4 * i + 2), __ldcg(partials + 4 * i + 3));
+  }
+  block_reduce2<OPA>(r[0], r[1]);
+  block_reduce2<OPB>(r[2], r[3]);
   if (tid == 0) {
     for (int k = 0; k < 4; ++k) f4[k] = r[k];
     ctl->count = 0;

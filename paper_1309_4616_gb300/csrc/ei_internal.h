@@ -108,6 +108,17 @@ struct NewtonMaps {
   CUtensorMap p;       // Newton sum, interior box
 };
 
+// The step's F pass on the TMA z-march (native FP64 stencils): F = A u + g(u)
+// into w_out, with a Rosenbrock step J's diagonal diag(A) + g'(u) into p and
+// the interval min/max of (lo + g'(u), hi + g'(u)) over the Gershgorin rows of
+// A (lo, hi: contiguous, n entries).
+struct FStepArgs {
+  const double* lo = nullptr;
+  const double* hi = nullptr;
+  int nonlin = 0;
+  int rosen = 0;
+};
+
 // ---- launchers (all asynchronous on `st`) ----------------------------------
 int csr_blocks(int64_t n);
 int reduction_capacity();        // block bound of the grid-stride kernels
@@ -214,6 +225,12 @@ cudaError_t launch_csr_residual(const CsrDev& op, const void* y, const void* v, 
 cudaError_t launch_newton_tma(const StencilDev& op, const NewtonMaps& M, void* w_out, void* p,
                               const NewtonScalars& s, int fmt, double* partials, DevCtl* ctl,
                               cudaStream_t st, bool prescaled = false);
+// F = A u + g(u) (g: none or logistic) on the TMA z-march, native FP64: M.w maps
+// u (halo box), M.c the raw coefficients a[0..5] and diag(A).  ctl->sum0 gets
+// ||F||^2 and ctl->sum1 its finiteness (1 or 0); with fa.rosen, J's diagonal
+// goes to dout and the interval of J to ctl->mn, ctl->mx (NaN: -inf, inf).
+cudaError_t launch_f_tma(const StencilDev& op, const NewtonMaps& M, void* F, void* dout,
+                         const FStepArgs& fa, double* partials, DevCtl* ctl, cudaStream_t st);
 // ||x||^2 of n_alloc elements of a Newton sum (format fmt) into ctl->sum0
 cudaError_t launch_p_sqnorm(const void* x, int fmt, int64_t n_alloc, double* partials,
                             DevCtl* ctl, cudaStream_t st);

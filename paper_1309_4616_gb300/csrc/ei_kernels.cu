@@ -668,18 +668,6 @@ __device__ __forceinline__ double nonlin_slope(int nonlin, float u) {
   return (double)dq;
 }
 
-// A double as a signed 64-bit key whose integer order is the value order:
-// negative values get their magnitude bits inverted (-0 sorts just below +0).
-// A NaN sorts beyond the infinity of its sign bit.  The transform is its own
-// inverse.
-__device__ __forceinline__ long long order_key(double v) {
-  const long long b = __double_as_longlong(v);
-  return b ^ ((b >> 63) & 0x7fffffffffffffffLL);
-}
-__device__ __forceinline__ double key_value(long long k) {
-  return __longlong_as_double(k ^ ((k >> 63) & 0x7fffffffffffffffLL));
-}
-
 // min/max of (lo + q), (hi + q), q = g'(u).  The running min/max compare
 // integer keys (order_key), which keeps the comparisons off the FP64 pipe;
 // a NaN ends up in one of the two keys and makes the thread's interval

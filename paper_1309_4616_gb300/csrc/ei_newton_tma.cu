@@ -128,14 +128,19 @@ static constexpr uint64_t kWaitLimitNs = 500000000ull;  // 0.5 s; a plane lands 
 // PN: form both squared norms in FP64 (false only with s.bracket, native
 // FP64: both are bracketed in FP32, which saves the FP64-bound kernel two FMAs
 // a point)
-template <int FMT, bool PRE, bool PN = true>
+// FSTEP (native FP64, with PRE false): the step's F pass instead of a Newton
+// iteration (launch_f_tma): u in M.w, A's raw coefficients in M.c, F to w_out,
+// J's diagonal to p_; it runs whatever ctl->done says.
+template <int FMT, bool PRE, bool PN = true, bool FSTEP = false>
 __global__ void __launch_bounds__(256, TmaCfg<FMT>::MINB)
 k_newton_tma(const __grid_constant__ NewtonMaps M, const StencilDev g, const NewtonScalars s,
-             void* __restrict__ w_out_, void* __restrict__ p_, double* partials, DevCtl* ctl) {
+             void* __restrict__ w_out_, void* __restrict__ p_, double* partials, DevCtl* ctl,
+             const FStepArgs fa) {
   using C = TmaCfg<FMT>;
   using T = typename C::T;
   using P = typename C::P;
-  if (*(volatile int*)&ctl->done != 0) return;
+  static_assert(!FSTEP || (FMT == VF_F64 && !PRE), "the F pass is native FP64 on A");
+  if (!FSTEP && *(volatile int*)&ctl->done != 0) return;
   extern __shared__ __align__(128) unsigned char smem_raw[];
   // stage tiles start on 128-byte boundaries whatever the static shared memory
   const uint32_t raw = smem_u32(smem_raw);
@@ -149,7 +154,7 @@ k_newton_tma(const __grid_constant__ NewtonMaps M, const StencilDev g, const New
   const int64_t units = (int64_t)bxc * ((g.ny + C::TY - 1) / C::TY) * g.nz;
   const int64_t ub = units * blockIdx.x / gridDim.x;
   const int64_t ue = units * (blockIdx.x + 1) / gridDim.x;
-  const bool needp = s.j > 0;
+  const bool needp = !FSTEP && s.j > 0;
   const uint32_t tx_halo = C::W_BYTES;
   const uint32_t tx_full = tx_halo + C::N_CT * C::C_BYTES + (needp ? C::P_BYTES : 0);
 
@@ -169,6 +174,9 @@ k_newton_tma(const __grid_constant__ NewtonMaps M, const StencilDev g, const New
   // bracketed, in FP32 off the FP64 pipe (NormBrackets)
   NormBrackets br;
   if constexpr (!PN) br.init(ctl, (double)g.nx * g.ny * g.nz);
+  // F pass: ||F||^2 and the interval keys of J's Gershgorin rows
+  double af = 0.0;
+  long long kmn = order_key(INFINITY), kmx = order_key(-INFINITY);
   T* __restrict__ w_out = static_cast<T*>(w_out_);
   P* __restrict__ p = static_cast<P*>(p_);
   const int wi = (ty + 1) * C::WX + tx + C::HX;
@@ -244,18 +252,37 @@ k_newton_tma(const __grid_constant__ NewtonMaps M, const StencilDev g, const New
         const T acc = stencil7(Ct[6 * TT + ci], wc, Ct[0 * TT + ci], Wc[wi - 1], Ct[1 * TT + ci],
                                Wc[wi + 1], Ct[2 * TT + ci], Wc[wi - C::WX], Ct[3 * TT + ci],
                                Wc[wi + C::WX], Ct[4 * TT + ci], Wm[wi], Ct[5 * TT + ci], Wp[wi]);
-        const T wn = PRE ? mac(acc, nshift, wc) : newton_update(acc, invg, nshift, wc);
-        const P* Pt = reinterpret_cast<const P*>(scq + C::OFF_P);
-        const P pold = needp ? Pt[ci] : mul(d0, to_p(wc));
-        const P pn = mac(pold, dn, to_p(wn));
         const int64_t idx = ((int64_t)z * g.ny + y) * g.pitch + x;
-        st(w_out, idx, wn);
-        st(p, idx, pn);
-        if constexpr (PN) {
-          aw = acc_sq(aw, wn);
-          ap = acc_sq(ap, pn);
+        if constexpr (FSTEP) {
+          // F = A u + g(u), g(u) = u(1 - u), g'(u) = 1 - 2u (logistic)
+          double Fv = acc, gq = 0.0;
+          if (fa.nonlin == EI_NONLIN_LOGISTIC) {
+            Fv = fma(wc, 1.0 - wc, Fv);
+            gq = fma(-2.0, wc, 1.0);
+          }
+          st(w_out, idx, Fv);
+          if (fa.rosen) {
+            st(p, idx, Ct[6 * TT + ci] + gq);
+            const int64_t ic = ((int64_t)z * g.ny + y) * g.nx + x;
+            const long long kl = order_key(__ldg(fa.lo + ic) + gq);
+            const long long kh = order_key(__ldg(fa.hi + ic) + gq);
+            kmn = kl < kmn ? kl : kmn;
+            kmx = kh > kmx ? kh : kmx;
+          }
+          af = fma(Fv, Fv, af);
         } else {
-          br.add(wn, pn);
+          const T wn = PRE ? mac(acc, nshift, wc) : newton_update(acc, invg, nshift, wc);
+          const P* Pt = reinterpret_cast<const P*>(scq + C::OFF_P);
+          const P pold = needp ? Pt[ci] : mul(d0, to_p(wc));
+          const P pn = mac(pold, dn, to_p(wn));
+          st(w_out, idx, wn);
+          st(p, idx, pn);
+          if constexpr (PN) {
+            aw = acc_sq(aw, wn);
+            ap = acc_sq(ap, pn);
+          } else {
+            br.add(wn, pn);
+          }
         }
       }
       // every plane: the slots read here are reissued only after this barrier
@@ -274,6 +301,24 @@ k_newton_tma(const __grid_constant__ NewtonMaps M, const StencilDev g, const New
       mbar_wait_bounded(bar0 + 8 * (q % C::NBAR), (q / C::NBAR) & 1, kWaitLimitNs / 8);
   }
 
+  if constexpr (FSTEP) {
+    double v[4] = {af, 0.0, key_value(kmn), key_value(kmx)};
+    if (isnan(v[2]) || isnan(v[3])) {
+      v[2] = -INFINITY;
+      v[3] = INFINITY;
+    }
+    if (last_block_reduce4<RED_SUM, RED_MINMAX>(v, partials, ctl)) {
+      if (tid == 0) {
+        ctl->sum0 = v[0];
+        ctl->sum1 = finite_d(v[0]) ? 1.0 : 0.0;
+        if (fa.rosen) {
+          ctl->mn = v[2];
+          ctl->mx = v[3];
+        }
+      }
+    }
+    return;
+  }
   double nw2 = PN ? acc_d(aw) : br.sum_w(), np2 = PN ? acc_d(ap) : br.sum_p();
   if (last_block_reduce2<RED_SUM>(nw2, np2, partials, ctl)) {
     if (tid == 0) {
@@ -649,26 +694,32 @@ static int64_t tma_balanced_blocks(const StencilDev& g, int slots) {
   return nb < 1 ? 1 : nb;
 }
 
-template <int FMT, bool PRE, bool PN = true>
+template <int FMT, bool PRE, bool PN = true, bool FSTEP = false>
 static cudaError_t launch_one(const StencilDev& g, const NewtonMaps& M, void* w_out, void* p,
                               const NewtonScalars& s, double* partials, DevCtl* ctl,
-                              cudaStream_t st) {
+                              cudaStream_t st, const FStepArgs& fa = FStepArgs{}) {
   using C = TmaCfg<FMT>;
   static int slots = 0;
   if (slots == 0) {
-    cudaError_t e = cudaFuncSetAttribute(k_newton_tma<FMT, PRE, PN>,
+    cudaError_t e = cudaFuncSetAttribute(k_newton_tma<FMT, PRE, PN, FSTEP>,
                                          cudaFuncAttributeMaxDynamicSharedMemorySize, C::SMEM);
     if (e != cudaSuccess) return e;
     int per_sm = 0;
-    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_newton_tma<FMT, PRE, PN>, 256,
-                                                      C::SMEM);
+    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_newton_tma<FMT, PRE, PN, FSTEP>,
+                                                      256, C::SMEM);
     if (e != cudaSuccess) return e;
     slots = (per_sm > 0 ? per_sm : 1) * sm_count();
   }
   const int64_t nb = tma_balanced_blocks(g, slots);
-  k_newton_tma<FMT, PRE, PN><<<(unsigned)nb, dim3(32, 8, 1), C::SMEM, st>>>(M, g, s, w_out, p,
-                                                                            partials, ctl);
+  k_newton_tma<FMT, PRE, PN, FSTEP><<<(unsigned)nb, dim3(32, 8, 1), C::SMEM, st>>>(
+      M, g, s, w_out, p, partials, ctl, fa);
   return cudaGetLastError();
+}
+
+cudaError_t launch_f_tma(const StencilDev& g, const NewtonMaps& M, void* F, void* dout,
+                         const FStepArgs& fa, double* partials, DevCtl* ctl, cudaStream_t st) {
+  return launch_one<VF_F64, false, true, true>(g, M, F, dout, NewtonScalars{}, partials, ctl,
+                                               st, fa);
 }
 
 cudaError_t launch_newton_tma(const StencilDev& g, const NewtonMaps& M, void* w_out, void* p,

@@ -91,7 +91,10 @@ def test_rosenbrock_3d_neumann(env, xi, single, arith):
     _check_stats(st, ost)
 
 
-def test_exp_euler_3d_mixed_bc_with_c(env, xi):
+@pytest.mark.parametrize("rosenbrock", [False, True])
+@pytest.mark.parametrize("arith", [0, 1])
+def test_step_3d_mixed_bc_with_c(env, xi, arith, rosenbrock):
+    # native FP64 runs F (and J's diagonal and interval) in one TMA pass
     torch, ei = env
     rng = np.random.default_rng(22)
     n = (45, 17, 33)
@@ -102,10 +105,14 @@ def test_exp_euler_3d_mixed_bc_with_c(env, xi):
     u0 = rng.uniform(0, 1, (33, 17, 45))
     op = O.StencilOperator(n, dx, D, b, c=c, bc=bc)
     h, tol = 1e-4, 1e-10
-    ref, ost = Nw.exp_euler_step(op, u0, h, tol, Nw.NONLIN_LOGISTIC, xi=xi)
+    if rosenbrock:
+        ref, ost = Nw.exp_rosenbrock_step(op, u0, h, tol, xi=xi)
+    else:
+        ref, ost = Nw.exp_euler_step(op, u0, h, tol, Nw.NONLIN_LOGISTIC, xi=xi)
     ctx = stencil_context(torch, ei, n, dx, D, b, c, bc)
     u = dev(torch, u0)
-    st = ctx.step(ei.EXP_EULER, h, u, ei.NONLIN_LOGISTIC, tol)
+    st = ctx.step(ei.EXP_ROSENBROCK if rosenbrock else ei.EXP_EULER, h, u, ei.NONLIN_LOGISTIC,
+                  tol, {"arith": arith})
     got = u.cpu().numpy()
     assert rel_err(got - u0, ref - u0) <= FP64_TOL
     _check_stats(st, ost)
