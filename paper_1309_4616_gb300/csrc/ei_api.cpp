@@ -1742,11 +1742,12 @@ static ei_status step_impl(ei_ctx* c, int method, double h, void* u, int nonlin,
   EI_LAUNCH(launch_import(P.u, fmt, src ? src : u, c->prec, n, geo_nx(c),
                           c->kind == KIND_STENCIL ? c->sd.ny : 1, geo_pitch(c), c->partials,
                           c->ctl, c->stream, src ? u : nullptr));
-  // native FP64 stencils without Dirichlet data or the combustion term: F, J's
-  // diagonal and J's interval in one pass on the TMA z-march
+  // FP64 stencils (native or float-float) without Dirichlet data or the
+  // combustion term: F, J's diagonal and J's interval in one pass on the TMA
+  // z-march
   bool faces = false;
   for (int f = 0; f < 6; ++f) faces = faces || c->face_term[f] != nullptr;
-  const bool f_tma = c->kind == KIND_STENCIL && fmt == VF_F64 && P.coef7 &&
+  const bool f_tma = c->kind == KIND_STENCIL && (fmt == VF_F64 || fmt == VF_DF) && P.coef7 &&
                      c->prec == EI_PREC_F64 && !faces &&
                      (nonlin == EI_NONLIN_NONE || nonlin == EI_NONLIN_LOGISTIC);
   if (f_tma) {
@@ -1758,10 +1759,11 @@ static ei_status step_impl(ei_ctx* c, int method, double h, void* u, int nonlin,
     FStepArgs fa;
     fa.lo = c->ger_lo;
     fa.hi = c->ger_hi;
+    fa.u = static_cast<const double*>(u);
     fa.nonlin = nonlin;
     fa.rosen = rosen;
-    EI_LAUNCH(launch_f_tma(stencil_view(c, P, base_diag(P)), M, P.v, P.qc, fa, c->partials,
-                           c->ctl, c->stream));
+    EI_LAUNCH(launch_f_tma(stencil_view(c, P, base_diag(P)), M, P.v, P.qc, fa, fmt,
+                           c->partials, c->ctl, c->stream));
     ++P.qc_ver;  // qc now holds this step's J diagonal
   } else if (c->kind == KIND_STENCIL) {
     BndFaces bnd;

@@ -65,9 +65,11 @@ struct CsrDev {
 // loads only its own row's entries, so with the rows longest first the lanes
 // still loading form a prefix and the padding is never read.  A small window
 // keeps a slice's rows close: their w gathers hit nearby lines, and their own
-// w, p and diagonal few lines (on a 2^20-node random geometric graph in Morton
-// order windows of 64 measured best: 32 pads more, 128 and up scatter more).
-constexpr int64_t kSellWindow = 64;
+// w, p and diagonal few lines.  On a 2^20-node random geometric graph in Morton
+// order, 64 and 128 measured alike in float-float, 32 pads more and 256 and up
+// scatter more; native FP64, which pays for padded multiply-adds, ran 63.7
+// against 64.8 us an iteration at 128.
+constexpr int64_t kSellWindow = 128;
 struct SellDev {
   int64_t nslices;
   const int32_t* perm;  // row of each slice position (-1: past the last row), 32 nslices
@@ -115,6 +117,8 @@ struct NewtonMaps {
 struct FStepArgs {
   const double* lo = nullptr;
   const double* hi = nullptr;
+  const double* u = nullptr;  // the caller's u (contiguous): g'(u) of the interval in
+                              // the float-float format, taken in FP64 as the oracle does
   int nonlin = 0;
   int rosen = 0;
 };
@@ -225,12 +229,14 @@ cudaError_t launch_csr_residual(const CsrDev& op, const void* y, const void* v, 
 cudaError_t launch_newton_tma(const StencilDev& op, const NewtonMaps& M, void* w_out, void* p,
                               const NewtonScalars& s, int fmt, double* partials, DevCtl* ctl,
                               cudaStream_t st, bool prescaled = false);
-// F = A u + g(u) (g: none or logistic) on the TMA z-march, native FP64: M.w maps
-// u (halo box), M.c the raw coefficients a[0..5] and diag(A).  ctl->sum0 gets
-// ||F||^2 and ctl->sum1 its finiteness (1 or 0); with fa.rosen, J's diagonal
-// goes to dout and the interval of J to ctl->mn, ctl->mx (NaN: -inf, inf).
+// F = A u + g(u) (g: none or logistic) on the TMA z-march, native FP64 or
+// float-float (fmt): M.w maps u (halo box), M.c the raw coefficients a[0..5]
+// and diag(A).  ctl->sum0 gets ||F||^2 and ctl->sum1 its finiteness (1 or 0);
+// with fa.rosen, J's diagonal goes to dout and the interval of J to ctl->mn,
+// ctl->mx (NaN: -inf, inf).
 cudaError_t launch_f_tma(const StencilDev& op, const NewtonMaps& M, void* F, void* dout,
-                         const FStepArgs& fa, double* partials, DevCtl* ctl, cudaStream_t st);
+                         const FStepArgs& fa, int fmt, double* partials, DevCtl* ctl,
+                         cudaStream_t st);
 // ||x||^2 of n_alloc elements of a Newton sum (format fmt) into ctl->sum0
 cudaError_t launch_p_sqnorm(const void* x, int fmt, int64_t n_alloc, double* partials,
                             DevCtl* ctl, cudaStream_t st);

@@ -128,9 +128,9 @@ static constexpr uint64_t kWaitLimitNs = 500000000ull;  // 0.5 s; a plane lands 
 // PN: form both squared norms in FP64 (false only with s.bracket, native
 // FP64: both are bracketed in FP32, which saves the FP64-bound kernel two FMAs
 // a point)
-// FSTEP (native FP64, with PRE false): the step's F pass instead of a Newton
-// iteration (launch_f_tma): u in M.w, A's raw coefficients in M.c, F to w_out,
-// J's diagonal to p_; it runs whatever ctl->done says.
+// FSTEP (native FP64 or float-float, with PRE false): the step's F pass
+// instead of a Newton iteration (launch_f_tma): u in M.w, A's raw coefficients
+// in M.c, F to w_out, J's diagonal to p_; it runs whatever ctl->done says.
 template <int FMT, bool PRE, bool PN = true, bool FSTEP = false>
 __global__ void __launch_bounds__(256, TmaCfg<FMT>::MINB)
 k_newton_tma(const __grid_constant__ NewtonMaps M, const StencilDev g, const NewtonScalars s,
@@ -139,7 +139,8 @@ k_newton_tma(const __grid_constant__ NewtonMaps M, const StencilDev g, const New
   using C = TmaCfg<FMT>;
   using T = typename C::T;
   using P = typename C::P;
-  static_assert(!FSTEP || (FMT == VF_F64 && !PRE), "the F pass is native FP64 on A");
+  static_assert(!FSTEP || ((FMT == VF_F64 || FMT == VF_DF) && !PRE),
+                "the F pass runs in the 8-byte formats on A");
   if (!FSTEP && *(volatile int*)&ctl->done != 0) return;
   extern __shared__ __align__(128) unsigned char smem_raw[];
   // stage tiles start on 128-byte boundaries whatever the static shared memory
@@ -175,7 +176,7 @@ k_newton_tma(const __grid_constant__ NewtonMaps M, const StencilDev g, const New
   NormBrackets br;
   if constexpr (!PN) br.init(ctl, (double)g.nx * g.ny * g.nz);
   // F pass: ||F||^2 and the interval keys of J's Gershgorin rows
-  double af = 0.0;
+  T af = zero<T>();
   long long kmn = order_key(INFINITY), kmx = order_key(-INFINITY);
   T* __restrict__ w_out = static_cast<T*>(w_out_);
   P* __restrict__ p = static_cast<P*>(p_);
@@ -255,21 +256,28 @@ k_newton_tma(const __grid_constant__ NewtonMaps M, const StencilDev g, const New
         const int64_t idx = ((int64_t)z * g.ny + y) * g.pitch + x;
         if constexpr (FSTEP) {
           // F = A u + g(u), g(u) = u(1 - u), g'(u) = 1 - 2u (logistic)
-          double Fv = acc, gq = 0.0;
+          const T one = from_d<T>(1.0), mtwo = from_d<T>(-2.0);
+          T Fv = acc, gq = zero<T>();
           if (fa.nonlin == EI_NONLIN_LOGISTIC) {
-            Fv = fma(wc, 1.0 - wc, Fv);
-            gq = fma(-2.0, wc, 1.0);
+            Fv = mac(Fv, wc, sub(one, wc));
+            gq = mac(one, mtwo, wc);
           }
           st(w_out, idx, Fv);
           if (fa.rosen) {
-            st(p, idx, Ct[6 * TT + ci] + gq);
+            st(p, idx, add(Ct[6 * TT + ci], gq));
             const int64_t ic = ((int64_t)z * g.ny + y) * g.nx + x;
-            const long long kl = order_key(__ldg(fa.lo + ic) + gq);
-            const long long kh = order_key(__ldg(fa.hi + ic) + gq);
+            // g'(u) of the interval in FP64 (float-float: of the caller's u)
+            double q;
+            if constexpr (FMT == VF_F64)
+              q = gq;
+            else
+              q = fa.nonlin == EI_NONLIN_LOGISTIC ? 1.0 - 2.0 * __ldg(fa.u + ic) : 0.0;
+            const long long kl = order_key(__ldg(fa.lo + ic) + q);
+            const long long kh = order_key(__ldg(fa.hi + ic) + q);
             kmn = kl < kmn ? kl : kmn;
             kmx = kh > kmx ? kh : kmx;
           }
-          af = fma(Fv, Fv, af);
+          af = mac(af, Fv, Fv);
         } else {
           const T wn = PRE ? mac(acc, nshift, wc) : newton_update(acc, invg, nshift, wc);
           const P* Pt = reinterpret_cast<const P*>(scq + C::OFF_P);
@@ -302,7 +310,7 @@ k_newton_tma(const __grid_constant__ NewtonMaps M, const StencilDev g, const New
   }
 
   if constexpr (FSTEP) {
-    double v[4] = {af, 0.0, key_value(kmn), key_value(kmx)};
+    double v[4] = {to_d(af), 0.0, key_value(kmn), key_value(kmx)};
     if (isnan(v[2]) || isnan(v[3])) {
       v[2] = -INFINITY;
       v[3] = INFINITY;
@@ -717,9 +725,15 @@ static cudaError_t launch_one(const StencilDev& g, const NewtonMaps& M, void* w_
 }
 
 cudaError_t launch_f_tma(const StencilDev& g, const NewtonMaps& M, void* F, void* dout,
-                         const FStepArgs& fa, double* partials, DevCtl* ctl, cudaStream_t st) {
-  return launch_one<VF_F64, false, true, true>(g, M, F, dout, NewtonScalars{}, partials, ctl,
-                                               st, fa);
+                         const FStepArgs& fa, int fmt, double* partials, DevCtl* ctl,
+                         cudaStream_t st) {
+  if (fmt == VF_DF)
+    return launch_one<VF_DF, false, true, true>(g, M, F, dout, NewtonScalars{}, partials, ctl,
+                                                st, fa);
+  if (fmt == VF_F64)
+    return launch_one<VF_F64, false, true, true>(g, M, F, dout, NewtonScalars{}, partials, ctl,
+                                                 st, fa);
+  return cudaErrorInvalidValue;
 }
 
 cudaError_t launch_newton_tma(const StencilDev& g, const NewtonMaps& M, void* w_out, void* p,
