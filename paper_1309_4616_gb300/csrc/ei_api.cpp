@@ -1742,14 +1742,12 @@ static ei_status step_impl(ei_ctx* c, int method, double h, void* u, int nonlin,
   EI_LAUNCH(launch_import(P.u, fmt, src ? src : u, c->prec, n, geo_nx(c),
                           c->kind == KIND_STENCIL ? c->sd.ny : 1, geo_pitch(c), c->partials,
                           c->ctl, c->stream, src ? u : nullptr));
-  // FP64 stencils (native or float-float) without Dirichlet data or the
-  // combustion term: F, J's diagonal and J's interval in one pass on the TMA
-  // z-march
+  // FP64 stencils (native or float-float) without Dirichlet data: F, J's
+  // diagonal and J's interval in one pass on the TMA z-march
   bool faces = false;
   for (int f = 0; f < 6; ++f) faces = faces || c->face_term[f] != nullptr;
   const bool f_tma = c->kind == KIND_STENCIL && (fmt == VF_F64 || fmt == VF_DF) && P.coef7 &&
-                     c->prec == EI_PREC_F64 && !faces &&
-                     (nonlin == EI_NONLIN_NONE || nonlin == EI_NONLIN_LOGISTIC);
+                     c->prec == EI_PREC_F64 && !faces;
   if (f_tma) {
     NewtonMaps M;
     M.w = P.map_u;

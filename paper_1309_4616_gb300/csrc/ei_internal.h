@@ -229,7 +229,7 @@ cudaError_t launch_csr_residual(const CsrDev& op, const void* y, const void* v, 
 cudaError_t launch_newton_tma(const StencilDev& op, const NewtonMaps& M, void* w_out, void* p,
                               const NewtonScalars& s, int fmt, double* partials, DevCtl* ctl,
                               cudaStream_t st, bool prescaled = false);
-// F = A u + g(u) (g: none or logistic) on the TMA z-march, native FP64 or
+// F = A u + g(u) (any EI_NONLIN_*) on the TMA z-march, native FP64 or
 // float-float (fmt): M.w maps u (halo box), M.c the raw coefficients a[0..5]
 // and diag(A).  ctl->sum0 gets ||F||^2 and ctl->sum1 its finiteness (1 or 0);
 // with fa.rosen, J's diagonal goes to dout and the interval of J to ctl->mn,

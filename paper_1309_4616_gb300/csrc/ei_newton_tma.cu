@@ -131,7 +131,9 @@ static constexpr uint64_t kWaitLimitNs = 500000000ull;  // 0.5 s; a plane lands 
 // FSTEP (native FP64 or float-float, with PRE false): the step's F pass
 // instead of a Newton iteration (launch_f_tma): u in M.w, A's raw coefficients
 // in M.c, F to w_out, J's diagonal to p_; it runs whatever ctl->done says.
-template <int FMT, bool PRE, bool PN = true, bool FSTEP = false>
+// 1: g none or logistic; 2: also the combustion terms (a separate
+// instantiation: their exponential and reciprocal take many registers).
+template <int FMT, bool PRE, bool PN = true, int FSTEP = 0>
 __global__ void __launch_bounds__(256, TmaCfg<FMT>::MINB)
 k_newton_tma(const __grid_constant__ NewtonMaps M, const StencilDev g, const NewtonScalars s,
              void* __restrict__ w_out_, void* __restrict__ p_, double* partials, DevCtl* ctl,
@@ -261,17 +263,25 @@ k_newton_tma(const __grid_constant__ NewtonMaps M, const StencilDev g, const New
           if (fa.nonlin == EI_NONLIN_LOGISTIC) {
             Fv = mac(Fv, wc, sub(one, wc));
             gq = mac(one, mtwo, wc);
+          } else if constexpr (FSTEP == 2) {
+            if (fa.nonlin != EI_NONLIN_NONE) {
+              T gv;
+              combustion_term(fa.nonlin, wc, gv, gq);
+              Fv = add(Fv, gv);
+            }
           }
           st(w_out, idx, Fv);
           if (fa.rosen) {
             st(p, idx, add(Ct[6 * TT + ci], gq));
             const int64_t ic = ((int64_t)z * g.ny + y) * g.nx + x;
-            // g'(u) of the interval in FP64 (float-float: of the caller's u)
+            // g'(u) of the interval in FP64: float-float takes the logistic
+            // slope of the caller's u, and the combustion slope in its own
+            // format from u as imported, as the separate interval pass does
             double q;
             if constexpr (FMT == VF_F64)
               q = gq;
             else
-              q = fa.nonlin == EI_NONLIN_LOGISTIC ? 1.0 - 2.0 * __ldg(fa.u + ic) : 0.0;
+              q = fa.nonlin == EI_NONLIN_LOGISTIC ? 1.0 - 2.0 * __ldg(fa.u + ic) : to_d(gq);
             const long long kl = order_key(__ldg(fa.lo + ic) + q);
             const long long kh = order_key(__ldg(fa.hi + ic) + q);
             kmn = kl < kmn ? kl : kmn;
@@ -702,7 +712,7 @@ static int64_t tma_balanced_blocks(const StencilDev& g, int slots) {
   return nb < 1 ? 1 : nb;
 }
 
-template <int FMT, bool PRE, bool PN = true, bool FSTEP = false>
+template <int FMT, bool PRE, bool PN = true, int FSTEP = 0>
 static cudaError_t launch_one(const StencilDev& g, const NewtonMaps& M, void* w_out, void* p,
                               const NewtonScalars& s, double* partials, DevCtl* ctl,
                               cudaStream_t st, const FStepArgs& fa = FStepArgs{}) {
@@ -727,12 +737,15 @@ static cudaError_t launch_one(const StencilDev& g, const NewtonMaps& M, void* w_
 cudaError_t launch_f_tma(const StencilDev& g, const NewtonMaps& M, void* F, void* dout,
                          const FStepArgs& fa, int fmt, double* partials, DevCtl* ctl,
                          cudaStream_t st) {
-  if (fmt == VF_DF)
-    return launch_one<VF_DF, false, true, true>(g, M, F, dout, NewtonScalars{}, partials, ctl,
-                                                st, fa);
+  const NewtonScalars none{};
+  const bool comb = fa.nonlin != EI_NONLIN_NONE && fa.nonlin != EI_NONLIN_LOGISTIC;
+  if (fmt == VF_DF && comb)
+    return launch_one<VF_DF, false, true, 2>(g, M, F, dout, none, partials, ctl, st, fa);
+  if (fmt == VF_DF) return launch_one<VF_DF, false, true, 1>(g, M, F, dout, none, partials, ctl, st, fa);
+  if (fmt == VF_F64 && comb)
+    return launch_one<VF_F64, false, true, 2>(g, M, F, dout, none, partials, ctl, st, fa);
   if (fmt == VF_F64)
-    return launch_one<VF_F64, false, true, true>(g, M, F, dout, NewtonScalars{}, partials, ctl,
-                                                 st, fa);
+    return launch_one<VF_F64, false, true, 1>(g, M, F, dout, none, partials, ctl, st, fa);
   return cudaErrorInvalidValue;
 }
 
