@@ -98,7 +98,7 @@ def parse():
                              "batch_learned_fp32", "batch_plain_fp64_loop", "combustion",
                              "combustion_fast", "combustion_nonlin", "heat_dirichlet_data",
                              "heat_dirichlet_hom", "phi2_adr3d", "spin_bath", "spin_bath_fp32",
-                             "northstar"],
+                             "batch_vs_plain_loop"],
                     help="adr3d (default, the headline): 256^3 FP64 Rosenbrock-Euler; "
                          "adr3d_fp32: 512^3 FP32 exponential Euler; rgg_csr: 2^20-node CSR phi_1")
     ap.add_argument("--no-cpu", action="store_true", help="skip the CPU baseline sample")
@@ -1252,7 +1252,7 @@ def cpu_leg_phi(wl, gpu_out, gpu_stats):
     return cpu, errs
 
 
-def run_northstar(args):
+def run_batch_vs_plain_loop(args):
     """The comparison the learned, FP32 and batched forms are built for: the
     1024 uneven 2D problems at tol 1e-6, (a) the learned schedule with FP32
     vectors in one persistent launch per pass, against (b) the plain method in
@@ -1305,7 +1305,7 @@ def run_northstar(args):
             "value": a["value"], "unit": "passes/s", "n_gpus": 1, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": a["ms_per_pass"], "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": a["dtype"], "data": "synthetic",
-            "config": {"workload": "northstar_learned_fp32_batched_vs_plain_fp64",
+            "config": {"workload": "learned_fp32_batched_vs_plain_fp64_loop",
                        "problems": n, "tol": 1e-6,
                        "error_sample": f"{len(sample)} problems (every 16th with <= 160^2 points)"},
             "forms": res, "speedup_vs_plain_fp64": a["value"] / b["value"]}
@@ -1426,8 +1426,8 @@ def main():
     args = parse()
     if args.impl == "reference":
         run_reference(args)
-    elif args.workload == "northstar":
-        run_northstar(args)
+    elif args.workload == "batch_vs_plain_loop":
+        run_batch_vs_plain_loop(args)
     else:
         run_ours(args)
 

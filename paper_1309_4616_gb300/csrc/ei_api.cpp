@@ -1742,12 +1742,12 @@ static ei_status step_impl(ei_ctx* c, int method, double h, void* u, int nonlin,
   EI_LAUNCH(launch_import(P.u, fmt, src ? src : u, c->prec, n, geo_nx(c),
                           c->kind == KIND_STENCIL ? c->sd.ny : 1, geo_pitch(c), c->partials,
                           c->ctl, c->stream, src ? u : nullptr));
-  // FP64 stencils (native or float-float) without Dirichlet data: F, J's
-  // diagonal and J's interval in one pass on the TMA z-march
+  // stencils without Dirichlet data: F, J's diagonal and J's interval in one
+  // pass on the TMA z-march
   bool faces = false;
   for (int f = 0; f < 6; ++f) faces = faces || c->face_term[f] != nullptr;
-  const bool f_tma = c->kind == KIND_STENCIL && (fmt == VF_F64 || fmt == VF_DF) && P.coef7 &&
-                     c->prec == EI_PREC_F64 && !faces;
+  const bool f_tma = c->kind == KIND_STENCIL && P.coef7 && !faces &&
+                     ((fmt == VF_F32) == (c->prec == EI_PREC_F32));
   if (f_tma) {
     NewtonMaps M;
     M.w = P.map_u;
@@ -1757,7 +1757,7 @@ static ei_status step_impl(ei_ctx* c, int method, double h, void* u, int nonlin,
     FStepArgs fa;
     fa.lo = c->ger_lo;
     fa.hi = c->ger_hi;
-    fa.u = static_cast<const double*>(u);
+    fa.u = u;
     fa.nonlin = nonlin;
     fa.rosen = rosen;
     EI_LAUNCH(launch_f_tma(stencil_view(c, P, base_diag(P)), M, P.v, P.qc, fa, fmt,

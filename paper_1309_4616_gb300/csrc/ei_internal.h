@@ -117,8 +117,9 @@ struct NewtonMaps {
 struct FStepArgs {
   const double* lo = nullptr;
   const double* hi = nullptr;
-  const double* u = nullptr;  // the caller's u (contiguous): g'(u) of the interval in
-                              // the float-float format, taken in FP64 as the oracle does
+  const void* u = nullptr;  // the caller's u (contiguous; float for FP32 storage):
+                            // g'(u) of the interval in the float-float and FP32
+                            // formats, taken in FP64 as the separate pass takes it
   int nonlin = 0;
   int rosen = 0;
 };
@@ -229,8 +230,9 @@ cudaError_t launch_csr_residual(const CsrDev& op, const void* y, const void* v, 
 cudaError_t launch_newton_tma(const StencilDev& op, const NewtonMaps& M, void* w_out, void* p,
                               const NewtonScalars& s, int fmt, double* partials, DevCtl* ctl,
                               cudaStream_t st, bool prescaled = false);
-// F = A u + g(u) (any EI_NONLIN_*) on the TMA z-march, native FP64 or
-// float-float (fmt): M.w maps u (halo box), M.c the raw coefficients a[0..5]
+// F = A u + g(u) (any EI_NONLIN_*) on the TMA z-march, in the vector format
+// fmt (native FP64, float-float or FP32): M.w maps u (halo box), M.c the raw
+// coefficients a[0..5]
 // and diag(A).  ctl->sum0 gets ||F||^2 and ctl->sum1 its finiteness (1 or 0);
 // with fa.rosen, J's diagonal goes to dout and the interval of J to ctl->mn,
 // ctl->mx (NaN: -inf, inf).

@@ -141,8 +141,7 @@ k_newton_tma(const __grid_constant__ NewtonMaps M, const StencilDev g, const New
   using C = TmaCfg<FMT>;
   using T = typename C::T;
   using P = typename C::P;
-  static_assert(!FSTEP || ((FMT == VF_F64 || FMT == VF_DF) && !PRE),
-                "the F pass runs in the 8-byte formats on A");
+  static_assert(!FSTEP || !PRE, "the F pass runs on A");
   if (!FSTEP && *(volatile int*)&ctl->done != 0) return;
   extern __shared__ __align__(128) unsigned char smem_raw[];
   // stage tiles start on 128-byte boundaries whatever the static shared memory
@@ -272,16 +271,22 @@ k_newton_tma(const __grid_constant__ NewtonMaps M, const StencilDev g, const New
           }
           st(w_out, idx, Fv);
           if (fa.rosen) {
-            st(p, idx, add(Ct[6 * TT + ci], gq));
+            st(static_cast<T*>(p_), idx, add(Ct[6 * TT + ci], gq));  // J's diagonal
             const int64_t ic = ((int64_t)z * g.ny + y) * g.nx + x;
-            // g'(u) of the interval in FP64: float-float takes the logistic
-            // slope of the caller's u, and the combustion slope in its own
-            // format from u as imported, as the separate interval pass does
+            // g'(u) of the interval in FP64: the other formats take the
+            // logistic slope of the caller's u, and the combustion slope in
+            // their own format from u as imported, as the separate pass does
             double q;
-            if constexpr (FMT == VF_F64)
+            if constexpr (FMT == VF_F64) {
               q = gq;
-            else
-              q = fa.nonlin == EI_NONLIN_LOGISTIC ? 1.0 - 2.0 * __ldg(fa.u + ic) : to_d(gq);
+            } else if (fa.nonlin == EI_NONLIN_LOGISTIC) {
+              const double ud = FMT == VF_F32
+                                    ? (double)__ldg(static_cast<const float*>(fa.u) + ic)
+                                    : __ldg(static_cast<const double*>(fa.u) + ic);
+              q = 1.0 - 2.0 * ud;
+            } else {
+              q = to_d(gq);
+            }
             const long long kl = order_key(__ldg(fa.lo + ic) + q);
             const long long kh = order_key(__ldg(fa.hi + ic) + q);
             kmn = kl < kmn ? kl : kmn;
@@ -746,7 +751,8 @@ cudaError_t launch_f_tma(const StencilDev& g, const NewtonMaps& M, void* F, void
     return launch_one<VF_F64, false, true, 2>(g, M, F, dout, none, partials, ctl, st, fa);
   if (fmt == VF_F64)
     return launch_one<VF_F64, false, true, 1>(g, M, F, dout, none, partials, ctl, st, fa);
-  return cudaErrorInvalidValue;
+  if (comb) return launch_one<VF_F32, false, true, 2>(g, M, F, dout, none, partials, ctl, st, fa);
+  return launch_one<VF_F32, false, true, 1>(g, M, F, dout, none, partials, ctl, st, fa);
 }
 
 cudaError_t launch_newton_tma(const StencilDev& g, const NewtonMaps& M, void* w_out, void* p,
