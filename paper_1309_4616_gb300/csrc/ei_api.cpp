@@ -144,6 +144,10 @@ struct ei_ctx {
   double newton_ms = 0.0;
   int newton_fused = 1;
   int p_rechecks = 0;      // stop tests the host took with the norms formed (brackets undecided)
+  // a tensor map over the caller's u of the last step that read it in place
+  CUtensorMap umap;
+  const void* umap_ptr = nullptr;
+  int umap_fmt = -1;
   int newton_bounded = 0;  // timed Newton launches that bracketed the norms
   int fuse = 0;            // Newton iterations per stencil launch: 0 the format's
                            // default (two for float-float and float, one for native
@@ -226,6 +230,7 @@ static void free_faces(ei_ctx* c) {
 }
 
 static void free_operator(ei_ctx* c) {
+  c->umap_ptr = nullptr;
   free_faces(c);
   for (auto& p : c->prep) free_prepared(p);
   if (c->ger_lo) cudaFree(c->ger_lo);
@@ -1738,19 +1743,31 @@ static ei_status step_impl(ei_ctx* c, int method, double h, void* u, int nonlin,
   Prepared& P = c->prep[fmt];
   const int64_t n = c->n;
   const int rosen = (method == EI_EXP_ROSENBROCK);
-  // import u; F = A u + g(u); J's diagonal; the interval of J
-  EI_LAUNCH(launch_import(P.u, fmt, src ? src : u, c->prec, n, geo_nx(c),
-                          c->kind == KIND_STENCIL ? c->sd.ny : 1, geo_pitch(c), c->partials,
-                          c->ctl, c->stream, src ? u : nullptr));
   // stencils without Dirichlet data: F, J's diagonal and J's interval in one
   // pass on the TMA z-march
   bool faces = false;
   for (int f = 0; f < 6; ++f) faces = faces || c->face_term[f] != nullptr;
   const bool f_tma = c->kind == KIND_STENCIL && P.coef7 && !faces &&
                      ((fmt == VF_F32) == (c->prec == EI_PREC_F32));
+  // There the native FP64 and FP32 formats read the caller's u in place when
+  // it already has the library's layout (rows of a multiple of 4 elements)
+  // and a 16-byte aligned base: the import would only copy it (its norm is
+  // the F pass's to give, its largest magnitude only float-float's to use).
+  bool in_place = f_tma && !src && fmt != VF_DF && c->sd.pitch == c->sd.nx &&
+                  (reinterpret_cast<uintptr_t>(u) & 15u) == 0;
+  if (in_place && (c->umap_ptr != u || c->umap_fmt != fmt)) {
+    in_place = encode_map(&c->umap, u, (int)vec_elem_bytes(fmt), c->sd, 1);
+    c->umap_ptr = in_place ? u : nullptr;
+    c->umap_fmt = fmt;
+  }
+  // import u; F = A u + g(u); J's diagonal; the interval of J
+  if (!in_place)
+    EI_LAUNCH(launch_import(P.u, fmt, src ? src : u, c->prec, n, geo_nx(c),
+                            c->kind == KIND_STENCIL ? c->sd.ny : 1, geo_pitch(c), c->partials,
+                            c->ctl, c->stream, src ? u : nullptr));
   if (f_tma) {
     NewtonMaps M;
-    M.w = P.map_u;
+    M.w = in_place ? c->umap : P.map_u;
     for (int k = 0; k < 6; ++k) M.c[k] = P.map_c[k];
     M.c[6] = P.map_diagA;
     M.p = P.map_p;

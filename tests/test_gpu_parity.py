@@ -607,3 +607,42 @@ def test_native_successive_steps_rescaled_operator(env, xi):
         assert rel_err(got - uin, ref - uin) <= FP64_TOL, scale
         _check_stats(st, ost)
     ctx.close()
+
+
+@pytest.mark.parametrize("method", ["euler", "rosenbrock"])
+def test_native_step_reads_u_in_place(env, xi, method):
+    """A native FP64 step on a grid whose rows are a multiple of 4 elements
+    reads a 16-byte aligned u in place instead of importing it; a u one
+    element into a larger buffer (8-byte aligned) is imported.  Both give
+    the same bits, and the oracle's step."""
+    torch, ei = env
+    rng = np.random.default_rng(43)
+    n = (40, 24, 20)
+    dx = (1 / 40,) * 3
+    D, b = _fields_3d(rng, n)
+    u0 = rng.uniform(0, 1, (20, 24, 40))
+    op = O.StencilOperator(n, dx, D, b, bc=(1,) * 6)
+    h, tol = 2e-4, 1e-10
+    rosen = method == "rosenbrock"
+    if rosen:
+        ref, ost = Nw.exp_rosenbrock_step(op, u0, h, tol, xi=xi)
+    else:
+        ref, ost = Nw.exp_euler_step(op, u0, h, tol, Nw.NONLIN_LOGISTIC, xi=xi)
+    ctx = stencil_context(torch, ei, n, dx, D, b, 0.0, (1,) * 6)
+    m = ei.EXP_ROSENBROCK if rosen else ei.EXP_EULER
+    opts = {"arith": ei.ARITH_NATIVE_F64}
+    ctx.step(m, h, dev(torch, u0), ei.NONLIN_LOGISTIC, tol, opts)  # the scaled operator made
+    ua = dev(torch, u0)
+    assert ua.data_ptr() % 16 == 0
+    sa = ctx.step(m, h, ua, ei.NONLIN_LOGISTIC, tol, opts)
+    buf = torch.zeros(u0.size + 1, dtype=torch.float64, device=ua.device)
+    ub = buf[1:].view(u0.shape)
+    ub.copy_(dev(torch, u0))
+    assert ub.data_ptr() % 16 == 8
+    sb = ctx.step(m, h, ub, ei.NONLIN_LOGISTIC, tol, opts)
+    assert torch.equal(ua, ub)
+    assert sa.launches == sb.launches - 1  # the import
+    got = ua.cpu().numpy()
+    assert rel_err(got - u0, ref - u0) <= FP64_TOL
+    _check_stats(sa, ost)
+    ctx.close()
