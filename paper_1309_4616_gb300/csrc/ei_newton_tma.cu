@@ -274,8 +274,11 @@ k_newton_tma(const __grid_constant__ NewtonMaps M, const StencilDev g, const New
             st(static_cast<T*>(p_), idx, add(Ct[6 * TT + ci], gq));  // J's diagonal
             const int64_t ic = ((int64_t)z * g.ny + y) * g.nx + x;
             // g'(u) of the interval in FP64: the other formats take the
-            // logistic slope of the caller's u, and the combustion slope in
-            // their own format from u as imported, as the separate pass does
+            // logistic slope of the caller's u (as the separate interval pass
+            // does) and the combustion slope in their own format from u as
+            // imported (the separate pass converts the caller's u itself; both
+            // conversions keep the format's 48 bits, so the slopes agree to
+            // its precision)
             double q;
             if constexpr (FMT == VF_F64) {
               q = gq;
