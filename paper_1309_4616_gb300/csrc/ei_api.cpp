@@ -309,7 +309,7 @@ static ei_status prepare(ei_ctx* c, int fmt) {
     for (int i = 0; i < 4; ++i) ok = ok && encode_map(&P.map_in2[i], ins[i], eb, c->sd, 2);
     for (int k = 0; k < 6; ++k) ok = ok && encode_map(&P.map_c[k], P.a[k], eb, c->sd, 0);
     ok = ok && encode_map(&P.map_diagA, P.diagA, eb, c->sd, 0);
-    if (fmt == VF_F64) {  // the scaled operator of the one-iteration native kernel
+    if (fmt == VF_F64 || fmt == VF_DF) {  // the scaled operator of the Newton kernels
       for (int k = 0; k < 7; ++k)
         if ((s = take(&P.sa[k], vb)) != EI_OK) { free_prepared(P); return s; }
       for (int k = 0; k < 7; ++k) ok = ok && encode_map(&P.map_s[k], P.sa[k], eb, c->sd, 0);
@@ -348,6 +348,13 @@ static StencilDev stencil_view(const ei_ctx* c, const Prepared& P, const void* d
   return s;
 }
 
+static StencilDev stencil_view_scaled(const ei_ctx* c, const Prepared& P) {
+  StencilDev s = c->sd;
+  for (int k = 0; k < 6; ++k) s.a[k] = P.sa[k];
+  s.diag = P.sa[6];
+  return s;
+}
+
 static CsrDev csr_view(const ei_ctx* c, const Prepared& P, const void* qc) {
   CsrDev d = c->cd;
   d.val = P.csr_val;
@@ -381,12 +388,16 @@ static bool prescaled_for(const Prepared& P, const void* qc) {
   return P.pre_valid && P.pre_diag == qc && (qc != P.qc || P.pre_ver == P.qc_ver);
 }
 
-// Native FP64 one-iteration Newton loops run on the scaled operator
-// (J - cI)/gamma: one elementwise pass per interval saves a multiply per point
-// in every iteration of the FP64-bound kernel.
+// Native FP64 and float-float stencil Newton loops run on the scaled operator
+// (J - cI)/gamma: one elementwise pass per interval (per step, the diagonal
+// alone) saves a multiply per point in every iteration.
 static bool wants_prescale(const ei_ctx* c, const Prepared& P) {
-  return c->kind == KIND_STENCIL && P.fmt == VF_F64 && P.sa[0] != nullptr;
+  return c->kind == KIND_STENCIL && (P.fmt == VF_F64 || P.fmt == VF_DF) && P.sa[0] != nullptr;
 }
+
+// the stencil view of the scaled operator (the two-iteration kernel's halo
+// points read their coefficients through it)
+static StencilDev stencil_view_scaled(const ei_ctx* c, const Prepared& P);
 // d_j r^j: the divided differences of the basis w_j / r^j
 static std::vector<double> rescaled_dd(const std::vector<double>& d, double r) {
   std::vector<double> out(d.size());
@@ -407,9 +418,10 @@ static ei_status ensure_prescaled(ei_ctx* c, Prepared& P, const void* qc, double
   if (prescaled_for(P, qc) && P.pre_cc == cc && P.pre_gamma == gamma) return EI_OK;
   const double r = P.off_valid ? P.off_gamma / gamma : 0.0;
   if (P.off_valid && fabs(r - 1.0) <= kOffRatioSlack) {
-    EI_LAUNCH(launch_prescale_diag(P.sa[6], qc, P.n_alloc, cc, 1.0 / P.off_gamma, c->stream));
+    EI_LAUNCH(launch_prescale_diag(P.sa[6], qc, P.n_alloc, cc, 1.0 / P.off_gamma, P.fmt,
+                                   c->stream));
   } else {
-    EI_LAUNCH(launch_prescale(P.sa, P.a, qc, P.n_alloc, cc, 1.0 / gamma, c->stream));
+    EI_LAUNCH(launch_prescale(P.sa, P.a, qc, P.n_alloc, cc, 1.0 / gamma, P.fmt, c->stream));
     P.off_valid = true;
     P.off_gamma = gamma;
   }
@@ -423,7 +435,7 @@ static ei_status ensure_prescaled(ei_ctx* c, Prepared& P, const void* qc, double
 }
 
 // pre: run on the scaled operator that ensure_prescaled made current for this
-// loop (native FP64 stencils)
+// loop (native FP64 and float-float stencils)
 static cudaError_t op_newton(ei_ctx* c, Prepared& P, const void* qc, const void* w_in,
                              void* w_out, const NewtonScalars& s, bool pre = false) {
   ++c->launches;
@@ -453,7 +465,7 @@ static cudaError_t op_newton(ei_ctx* c, Prepared& P, const void* qc, const void*
 }
 
 static cudaError_t op_newton2(ei_ctx* c, Prepared& P, const void* qc, const void* w_in,
-                              void* w_out, const NewtonScalars& s) {
+                              void* w_out, const NewtonScalars& s, bool pre = false) {
   ++c->launches;
   NewtonMaps M;
   const void* ins[4] = {P.v, P.r, P.w[0], P.w[1]};
@@ -462,11 +474,12 @@ static cudaError_t op_newton2(ei_ctx* c, Prepared& P, const void* qc, const void
     if (ins[i] == w_in) wi = i;
   if (wi < 0) return cudaErrorInvalidValue;
   M.w = P.map_in2[wi];
-  for (int k = 0; k < 6; ++k) M.c[k] = P.map_c[k];
-  M.c[6] = (qc == P.qc) ? P.map_qc : P.map_diagA;
+  pre = pre && prescaled_for(P, qc);
+  for (int k = 0; k < 6; ++k) M.c[k] = pre ? P.map_s[k] : P.map_c[k];
+  M.c[6] = pre ? P.map_s[6] : (qc == P.qc) ? P.map_qc : P.map_diagA;
   M.p = P.map_p;
-  return launch_newton2_tma(stencil_view(c, P, qc), M, w_out, P.p, s, P.fmt, c->partials, c->ctl,
-                            c->stream);
+  return launch_newton2_tma(pre ? stencil_view_scaled(c, P) : stencil_view(c, P, qc), M, w_out,
+                            P.p, s, P.fmt, c->partials, c->ctl, c->stream, pre);
 }
 
 // Whether the Newton loop runs two iterations per launch: explicit-coefficient
@@ -510,7 +523,7 @@ static ei_status newton_loop(ei_ctx* c, Prepared& P, const void* qc, const void*
     }
   }
   const bool pair = use_pair(c, P);
-  const bool pre = !pair && !cx && wants_prescale(c, P);
+  const bool pre = !cx && wants_prescale(c, P);
   if (pre) EI_TRY(ensure_prescaled(c, P, qc, cc, gamma));
   // on the operator scaled by 1/gamma0 = r/gamma the loop runs in the basis
   // w_j / r^j: shifts xi_j / r, coefficients d_j r^j (the same p and tests)
@@ -524,7 +537,7 @@ static ei_status newton_loop(ei_ctx* c, Prepared& P, const void* qc, const void*
   // decide, the host takes the test with both norms formed, and every later
   // step of the loop forms them.  (The sliced CSR kernel measured slower with
   // brackets: 72.1 against 64.6 us a launch on the 2^20-node graph.)
-  bool bracket = pre;
+  bool bracket = pre && !pair && P.fmt == VF_F64;
   int lj[128];          // first iteration index of each launch
   bool l2[128];         // whether that launch did two iterations
   bool lb[128];         // whether that launch bracketed the norms
@@ -553,8 +566,9 @@ static ei_status newton_loop(ei_ctx* c, Prepared& P, const void* qc, const void*
       s.xi = xi[j] / rr;
       s.bracket = (bracket && j >= 1) ? 1 : 0;
       if (two) {
-        s.d_next2 = d[j + 2];
+        s.d_next2 = dv[j + 2];
         s.shift2 = cc / gamma + xi[j + 1];
+        s.xi2 = xi[j + 1] / rr;
       }
       const void* w_in = (nl == 0) ? r : wbuf[(nl - 1) & 1];
       void* w_out = wbuf[nl & 1];
@@ -573,7 +587,7 @@ static ei_status newton_loop(ei_ctx* c, Prepared& P, const void* qc, const void*
                                           c->stream));
         }
       } else if (two) {
-        EI_TRY_CUDA(op_newton2(c, P, qc, w_in, w_out, s));
+        EI_TRY_CUDA(op_newton2(c, P, qc, w_in, w_out, s, pre));
       } else {
         EI_TRY_CUDA(op_newton(c, P, qc, w_in, w_out, s, pre));
       }
@@ -798,7 +812,7 @@ static ei_status newton_fixed(ei_ctx* c, Prepared& P, const void* qc, const void
   s.m_max = m;
   s.fixed = 1;
   const bool pair = use_pair(c, P);
-  const bool pre = !pair && wants_prescale(c, P);
+  const bool pre = wants_prescale(c, P);
   if (pre) EI_TRY(ensure_prescaled(c, P, qc, cc, gamma));
   std::vector<double> d_r;  // the rescaled basis, as in newton_loop
   const double rr = pre ? P.pre_ratio : 1.0;
@@ -818,14 +832,15 @@ static ei_status newton_fixed(ei_ctx* c, Prepared& P, const void* qc, const void
     s.shift = cc / gamma + xi[j];
     s.xi = xi[j] / rr;
     if (two) {
-      s.d_next2 = d[j + 2];
+      s.d_next2 = dv[j + 2];
       s.shift2 = cc / gamma + xi[j + 1];
+      s.xi2 = xi[j + 1] / rr;
     }
     const void* w_in = (nl == 0) ? r : P.w[(nl - 1) & 1];
     void* w_out = P.w[nl & 1];
     if (timed) EI_TRY_CUDA(cudaEventRecord(c->ev[2 * nl], c->stream));
     if (two) {
-      EI_TRY_CUDA(op_newton2(c, P, qc, w_in, w_out, s));
+      EI_TRY_CUDA(op_newton2(c, P, qc, w_in, w_out, s, pre));
     } else {
       EI_TRY_CUDA(op_newton(c, P, qc, w_in, w_out, s, pre));
     }
@@ -1820,9 +1835,9 @@ static ei_status step_impl(ei_ctx* c, int method, double h, void* u, int nonlin,
   int is_p = 0;
   double scale = 1.0;
   c->vnorm2 = fnorm2;
-  // the scaled operator of the native Newton kernel goes out now, so the device
+  // the scaled operator of the Newton kernels goes out now, so the device
   // makes it while the host works out the schedule
-  if (wants_prescale(c, P) && !use_pair(c, P)) EI_TRY(ensure_prescaled(c, P, qc, cc, gamma));
+  if (wants_prescale(c, P)) EI_TRY(ensure_prescaled(c, P, qc, cc, gamma));
   EI_TRY(phi1_substeps(c, P, qc, h, alpha, beta, tol, opt, st, &res, &is_p, &scale));
   EI_LAUNCH(launch_add_export(u, c->prec, res, fmt, is_p, n, geo_nx(c), c->kind == KIND_STENCIL ? c->sd.ny : 1, geo_pitch(c), scale, c->stream, dst));
   EI_TRY_CUDA(cudaStreamSynchronize(c->stream));

@@ -94,7 +94,9 @@ struct NewtonScalars {
                        //    is tested and a failure counts into ctl->fixfail
   double d_next_im;    // complex Newton sum (k_csr_newton_c): Im d_{j+1}
   double d0_im;        //   and Im d_0
-  double xi;           // the Leja point xi_j (kernels on the scaled operator)
+  double xi;           // the Leja point xi_j (kernels on the scaled operator; in
+                       // the rescaled basis, xi_j / r)
+  double xi2;          // two-iteration kernel on the scaled operator: xi_{j+1} (/ r)
   int bracket;         // 1: this step brackets ||w_{j+1}||^2 and ||p_{j+1}||^2 in
                        //    FP32 instead of forming them in FP64; the stop test
                        //    is decided from the brackets, or reported as done = 6
@@ -242,19 +244,21 @@ cudaError_t launch_f_tma(const StencilDev& op, const NewtonMaps& M, void* F, voi
 // ||x||^2 of n_alloc elements of a Newton sum (format fmt) into ctl->sum0
 cudaError_t launch_p_sqnorm(const void* x, int fmt, int64_t n_alloc, double* partials,
                             DevCtl* ctl, cudaStream_t st);
-// the scaled operator of the native FP64 Newton kernel, elementwise over the
-// padded arrays: sa[k] = a[k] / gamma (k < 6), sa[6] = (diag - c) / gamma
+// the scaled operator of the Newton kernels (native FP64 and float-float fmt),
+// elementwise over the padded arrays: sa[k] = a[k] / gamma (k < 6),
+// sa[6] = (diag - c) / gamma
 cudaError_t launch_prescale(void* const sa[7], const void* const a[6], const void* diag,
-                            int64_t n_alloc, double c, double inv_gamma, cudaStream_t st);
+                            int64_t n_alloc, double c, double inv_gamma, int fmt,
+                            cudaStream_t st);
 // its diagonal alone: sa6 = (diag - c) * inv_gamma
 cudaError_t launch_prescale_diag(void* sa6, const void* diag, int64_t n_alloc, double c,
-                                 double inv_gamma, cudaStream_t st);
+                                 double inv_gamma, int fmt, cudaStream_t st);
 // Two Newton iterations j+1 and j+2 in one pass (explicit-coefficient stencil,
 // all formats): w_{j+1} is formed on chip over the tile and a one-point
 // halo; only w_{j+2} and p_{j+2} are written.  M.w must be a halo-2 map.
 cudaError_t launch_newton2_tma(const StencilDev& op, const NewtonMaps& M, void* w_out, void* p,
                                const NewtonScalars& s, int fmt, double* partials, DevCtl* ctl,
-                               cudaStream_t st);
+                               cudaStream_t st, bool prescaled = false);
 // p -= d * w (elementwise, Newton-sum format p, vector format w)
 cudaError_t launch_p_fixup(void* p, const void* w, int fmt, int64_t n_alloc, double d,
                            cudaStream_t st);

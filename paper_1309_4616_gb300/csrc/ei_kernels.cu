@@ -836,35 +836,41 @@ __global__ void k_axpy(void* y_, const void* p_, int64_t n, double tau) {
 // harmless: padded neighbour coefficients are 0 and stay 0; the padded
 // diagonal becomes -c/gamma but multiplies a padded w = 0.
 struct PrescaleArgs {
-  double* s[7];
-  const double* a[7];  // a[0..5], diagonal
+  void* s[7];
+  const void* a[7];  // a[0..5], diagonal
 };
-struct Coef7 {
-  double a[7];
+template <class T>
+struct Coef7T {
+  T a[7];
 };
+// the scaled operator, in the vector format T (double or float-float)
+template <class T>
 __global__ void __launch_bounds__(EI_TPB)
 k_prescale(const PrescaleArgs P, int64_t n, double c, double inv_gamma) {
+  const T g = from_d<T>(inv_gamma), cc = from_d<T>(c);
   for_points_k<EW_K>(
       n, (int)1, (int)1,
       [&](int64_t i, int64_t) {
-        Coef7 v;
+        Coef7T<T> v;
 #pragma unroll
-        for (int k = 0; k < 7; ++k) v.a[k] = __ldg(P.a[k] + i);
+        for (int k = 0; k < 7; ++k) v.a[k] = ldg(static_cast<const T*>(P.a[k]), i);
         return v;
       },
-      [&](int64_t i, int64_t, Coef7 v) {
+      [&](int64_t i, int64_t, Coef7T<T> v) {
 #pragma unroll
-        for (int k = 0; k < 6; ++k) P.s[k][i] = v.a[k] * inv_gamma;
-        P.s[6][i] = (v.a[6] - c) * inv_gamma;
+        for (int k = 0; k < 6; ++k) st(static_cast<T*>(P.s[k]), i, mul(v.a[k], g));
+        st(static_cast<T*>(P.s[6]), i, mul(sub(v.a[6], cc), g));
       });
 }
 
+template <class T>
 __global__ void __launch_bounds__(EI_TPB)
-k_prescale_diag(double* __restrict__ sa6, const double* __restrict__ diag, int64_t n, double c,
+k_prescale_diag(T* __restrict__ sa6, const T* __restrict__ diag, int64_t n, double c,
                 double inv_gamma) {
+  const T g = from_d<T>(inv_gamma), cc = from_d<T>(c);
   for_points_k<EW_K>(
-      n, (int)1, (int)1, [&](int64_t i, int64_t) { return __ldg(diag + i); },
-      [&](int64_t i, int64_t, double v) { sa6[i] = (v - c) * inv_gamma; });
+      n, (int)1, (int)1, [&](int64_t i, int64_t) { return ldg(diag, i); },
+      [&](int64_t i, int64_t, T v) { st(sa6, i, mul(sub(v, cc), g)); });
 }
 
 template <int FMT>
@@ -1503,19 +1509,27 @@ cudaError_t launch_axpy(void* y, const void* p, int fmt, int64_t n, double tau,
 }
 
 cudaError_t launch_prescale(void* const sa[7], const void* const a[6], const void* diag,
-                            int64_t n_alloc, double c, double inv_gamma, cudaStream_t stm) {
+                            int64_t n_alloc, double c, double inv_gamma, int fmt,
+                            cudaStream_t stm) {
   PrescaleArgs P{};
-  for (int i = 0; i < 7; ++i) P.s[i] = static_cast<double*>(sa[i]);
-  for (int i = 0; i < 6; ++i) P.a[i] = static_cast<const double*>(a[i]);
-  P.a[6] = static_cast<const double*>(diag);
-  k_prescale<<<ew_blocks(n_alloc), EI_TPB, 0, stm>>>(P, n_alloc, c, inv_gamma);
+  for (int i = 0; i < 7; ++i) P.s[i] = sa[i];
+  for (int i = 0; i < 6; ++i) P.a[i] = a[i];
+  P.a[6] = diag;
+  if (fmt == VF_DF)
+    k_prescale<df><<<ew_blocks(n_alloc), EI_TPB, 0, stm>>>(P, n_alloc, c, inv_gamma);
+  else
+    k_prescale<double><<<ew_blocks(n_alloc), EI_TPB, 0, stm>>>(P, n_alloc, c, inv_gamma);
   return cudaGetLastError();
 }
 
 cudaError_t launch_prescale_diag(void* sa6, const void* diag, int64_t n_alloc, double c,
-                                 double inv_gamma, cudaStream_t stm) {
-  k_prescale_diag<<<ew_blocks(n_alloc), EI_TPB, 0, stm>>>(
-      static_cast<double*>(sa6), static_cast<const double*>(diag), n_alloc, c, inv_gamma);
+                                 double inv_gamma, int fmt, cudaStream_t stm) {
+  if (fmt == VF_DF)
+    k_prescale_diag<df><<<ew_blocks(n_alloc), EI_TPB, 0, stm>>>(
+        static_cast<df*>(sa6), static_cast<const df*>(diag), n_alloc, c, inv_gamma);
+  else
+    k_prescale_diag<double><<<ew_blocks(n_alloc), EI_TPB, 0, stm>>>(
+        static_cast<double*>(sa6), static_cast<const double*>(diag), n_alloc, c, inv_gamma);
   return cudaGetLastError();
 }
 

@@ -122,9 +122,9 @@ __device__ __forceinline__ bool mbar_wait_bounded(uint32_t bar, uint32_t parity,
 static constexpr uint64_t kWaitLimitNs = 500000000ull;  // 0.5 s; a plane lands in microseconds
 
 // PRE: the coefficient tiles hold the scaled operator (A - cI)/gamma (native
-// FP64 only), so w_{j+1} = (A w_j - c w_j)/gamma - xi_j w_j is the 7-point sum
-// and one FMA with -xi_j: the FP64 pipe bounds this kernel, and the scaling
-// saves it a multiply per point.
+// FP64 and float-float), so w_{j+1} = (A w_j - c w_j)/gamma - xi_j w_j is the
+// 7-point sum and one multiply-add with -xi_j: the scaling saves a multiply
+// per point.
 // PN: form both squared norms in FP64 (false only with s.bracket, native
 // FP64: both are bracketed in FP32, which saves the FP64-bound kernel two FMAs
 // a point)
@@ -405,7 +405,7 @@ struct TmaCfg2 {
   static constexpr int SMEM = BARS + 8 * NBAR + 128;
 };
 
-template <int FMT>
+template <int FMT, bool PRE = false>
 __global__ void __launch_bounds__(256, 2)
 k_newton2_tma(const __grid_constant__ NewtonMaps M, const StencilDev g, const NewtonScalars s,
               void* __restrict__ w_out_, void* __restrict__ p_, double* partials, DevCtl* ctl,
@@ -460,9 +460,11 @@ k_newton2_tma(const __grid_constant__ NewtonMaps M, const StencilDev g, const Ne
     for (int q = 0; q <= 2 + C::PF && q < nq; ++q) issue(q);
   }
 
+  // PRE: the coefficient tiles and halo coefficients hold the scaled operator
+  // (the update is the 7-point sum and one multiply-add with the shift)
   const T invg = from_d<T>(s.inv_gamma);
-  const T nsh1 = from_d<T>(-s.shift);
-  const T nsh2 = from_d<T>(-s.shift2);
+  const T nsh1 = from_d<T>(PRE ? -s.xi : -s.shift);
+  const T nsh2 = from_d<T>(PRE ? -s.xi2 : -s.shift2);
   const P d1 = from_d<P>(s.d_next);
   const P d2 = from_d<P>(s.d_next2);
   const P d0 = from_d<P>(s.d0);
@@ -539,7 +541,7 @@ k_newton2_tma(const __grid_constant__ NewtonMaps M, const StencilDev g, const Ne
                                Ct[1 * TT + ci], Wc[wi_own + 1], Ct[2 * TT + ci],
                                Wc[wi_own - C::WJX], Ct[3 * TT + ci], Wc[wi_own + C::WJX],
                                Ct[4 * TT + ci], Wm[wi_own], Ct[5 * TT + ci], Wp[wi_own]);
-        w1own = newton_update(acc, invg, nsh1, wc);
+        w1own = PRE ? mac(acc, nsh1, wc) : newton_update(acc, invg, nsh1, wc);
       }
       if (interior) W1[vi_own] = w1own;
       // ---- w_{j+1}(zc) at this thread's halo point (first three warps)
@@ -551,7 +553,7 @@ k_newton2_tma(const __grid_constant__ NewtonMaps M, const StencilDev g, const Ne
           const T acc = stencil7(hcur[6], wc, hcur[0], Wc[wi - 1], hcur[1], Wc[wi + 1], hcur[2],
                                  Wc[wi - C::WJX], hcur[3], Wc[wi + C::WJX], hcur[4], Wm[wi],
                                  hcur[5], Wp[wi]);
-          w1 = newton_update(acc, invg, nsh1, wc);
+          w1 = PRE ? mac(acc, nsh1, wc) : newton_update(acc, invg, nsh1, wc);
         }
         W1[hly * C::W1X + hlx] = w1;
       }
@@ -569,7 +571,7 @@ k_newton2_tma(const __grid_constant__ NewtonMaps M, const StencilDev g, const Ne
                                Ct[1 * TT + ci], V1[vi_own + 1], Ct[2 * TT + ci],
                                V1[vi_own - C::W1X], Ct[3 * TT + ci], V1[vi_own + C::W1X],
                                Ct[4 * TT + ci], w1_m2, Ct[5 * TT + ci], w1own);
-        const T w2 = newton_update(acc, invg, nsh2, w1c);
+        const T w2 = PRE ? mac(acc, nsh2, w1c) : newton_update(acc, invg, nsh2, w1c);
         const P pj = needp ? Pt[ci] : mul(d0, to_p(Wm[wi_own]));
         const P p1 = mac(pj, d1, to_p(w1c));
         const P p2 = mac(p1, d2, to_p(w2));
@@ -761,6 +763,7 @@ cudaError_t launch_f_tma(const StencilDev& g, const NewtonMaps& M, void* F, void
 cudaError_t launch_newton_tma(const StencilDev& g, const NewtonMaps& M, void* w_out, void* p,
                               const NewtonScalars& s, int fmt, double* partials, DevCtl* ctl,
                               cudaStream_t st, bool prescaled) {
+  if (fmt == VF_DF && prescaled) return launch_one<VF_DF, true>(g, M, w_out, p, s, partials, ctl, st);
   if (fmt == VF_DF) return launch_one<VF_DF, false>(g, M, w_out, p, s, partials, ctl, st);
   if (fmt == VF_F64) {
     if (prescaled && s.bracket)
@@ -771,43 +774,34 @@ cudaError_t launch_newton_tma(const StencilDev& g, const NewtonMaps& M, void* w_
   return launch_one<VF_F32, false>(g, M, w_out, p, s, partials, ctl, st);
 }
 
-cudaError_t launch_newton2_tma(const StencilDev& g, const NewtonMaps& M, void* w_out, void* p,
-                               const NewtonScalars& s, int fmt, double* partials, DevCtl* ctl,
+template <int FMT, bool PRE>
+static cudaError_t launch_pair(const StencilDev& g, const NewtonMaps& M, void* w_out, void* p,
+                               const NewtonScalars& s, double* partials, DevCtl* ctl,
                                cudaStream_t st) {
+  using C = TmaCfg2<FMT>;
+  static bool attr = false;
+  if (!attr) {
+    cudaError_t e = cudaFuncSetAttribute(k_newton2_tma<FMT, PRE>,
+                                         cudaFuncAttributeMaxDynamicSharedMemorySize, C::SMEM);
+    if (e != cudaSuccess) return e;
+    attr = true;
+  }
   const int zc = tma_zchunk(g, sm_count() * 2, kHaloPair);  // two blocks per SM
   dim3 grid((g.nx + 31) / 32, (g.ny + 7) / 8, (g.nz + zc - 1) / zc), block(32, 8, 1);
-  if (fmt == VF_DF) {
-    using C = TmaCfg2<VF_DF>;
-    static bool attr = false;
-    if (!attr) {
-      cudaError_t e = cudaFuncSetAttribute(k_newton2_tma<VF_DF>,
-                                           cudaFuncAttributeMaxDynamicSharedMemorySize, C::SMEM);
-      if (e != cudaSuccess) return e;
-      attr = true;
-    }
-    k_newton2_tma<VF_DF><<<grid, block, C::SMEM, st>>>(M, g, s, w_out, p, partials, ctl, zc);
-  } else if (fmt == VF_F64) {
-    using C = TmaCfg2<VF_F64>;
-    static bool attr = false;
-    if (!attr) {
-      cudaError_t e = cudaFuncSetAttribute(k_newton2_tma<VF_F64>,
-                                           cudaFuncAttributeMaxDynamicSharedMemorySize, C::SMEM);
-      if (e != cudaSuccess) return e;
-      attr = true;
-    }
-    k_newton2_tma<VF_F64><<<grid, block, C::SMEM, st>>>(M, g, s, w_out, p, partials, ctl, zc);
-  } else {
-    using C = TmaCfg2<VF_F32>;
-    static bool attr = false;
-    if (!attr) {
-      cudaError_t e = cudaFuncSetAttribute(k_newton2_tma<VF_F32>,
-                                           cudaFuncAttributeMaxDynamicSharedMemorySize, C::SMEM);
-      if (e != cudaSuccess) return e;
-      attr = true;
-    }
-    k_newton2_tma<VF_F32><<<grid, block, C::SMEM, st>>>(M, g, s, w_out, p, partials, ctl, zc);
-  }
+  k_newton2_tma<FMT, PRE><<<grid, block, C::SMEM, st>>>(M, g, s, w_out, p, partials, ctl, zc);
   return cudaGetLastError();
+}
+
+cudaError_t launch_newton2_tma(const StencilDev& g, const NewtonMaps& M, void* w_out, void* p,
+                               const NewtonScalars& s, int fmt, double* partials, DevCtl* ctl,
+                               cudaStream_t st, bool prescaled) {
+  if (fmt == VF_DF && prescaled)
+    return launch_pair<VF_DF, true>(g, M, w_out, p, s, partials, ctl, st);
+  if (fmt == VF_DF) return launch_pair<VF_DF, false>(g, M, w_out, p, s, partials, ctl, st);
+  if (fmt == VF_F64 && prescaled)
+    return launch_pair<VF_F64, true>(g, M, w_out, p, s, partials, ctl, st);
+  if (fmt == VF_F64) return launch_pair<VF_F64, false>(g, M, w_out, p, s, partials, ctl, st);
+  return launch_pair<VF_F32, false>(g, M, w_out, p, s, partials, ctl, st);
 }
 
 cudaError_t launch_p_fixup(void* p, const void* w, int fmt, int64_t n, double d,

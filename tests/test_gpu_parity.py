@@ -577,8 +577,10 @@ def test_native_brackets_decide(env, xi):
     ctx.close()
 
 
-def test_native_successive_steps_rescaled_operator(env, xi):
-    """Successive native FP64 Rosenbrock steps on one context.  The first step
+@pytest.mark.parametrize("arith", [0, 1])
+def test_successive_steps_rescaled_operator(env, xi, arith):
+    """Successive Rosenbrock steps on one context, native FP64 (one iteration a
+    launch) and float-float (two).  The first step
     writes the scaled operator (J - cI)/gamma0; a later step whose gamma stays
     within gamma0 (1 +- 1/8) rewrites only its diagonal and runs the Newton
     loop in the basis w_j / r^j, r = gamma0/gamma; a step outside that range
@@ -600,10 +602,9 @@ def test_native_successive_steps_rescaled_operator(env, xi):
         uin = u0 * scale
         ref, ost = Nw.exp_rosenbrock_step(op, uin, h, tol, xi=xi)
         u = dev(torch, uin)
-        st = ctx.step(ei.EXP_ROSENBROCK, h, u, ei.NONLIN_LOGISTIC, tol,
-                      {"arith": ei.ARITH_NATIVE_F64})
+        st = ctx.step(ei.EXP_ROSENBROCK, h, u, ei.NONLIN_LOGISTIC, tol, {"arith": arith})
         got = u.cpu().numpy()
-        assert st.arith_used == ei.ARITH_NATIVE_F64
+        assert st.arith_used == (ei.ARITH_NATIVE_F64 if arith else ei.ARITH_DF)
         assert rel_err(got - uin, ref - uin) <= FP64_TOL, scale
         _check_stats(st, ost)
     ctx.close()
