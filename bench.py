@@ -61,15 +61,14 @@ FP64_FLOPS_PER_POINT_BOUNDED = 17
 # 152 SMs at 2070 MHz is 4 FP64 flops (two FMA lanes) per SM and clock.
 SMS, FP64_FLOPS_PER_SM_CLK = 152, 4
 # DRAM bytes per grid point of one launch of the two-iteration float-float
-# kernel, from ncu dram__bytes_read.sum + dram__bytes_write.sum on 192^3
-# (profiles/launches_adr3d_256_rosenbrock.md, taken on the current kernel);
+# kernel on the scaled operator, from ncu dram__bytes_read.sum +
+# dram__bytes_write.sum on 192^3 (profiles/dram_bytes_newton_kernels_192cube.md);
 # traffic scales with the points.
 # Valid for the kernel as captured: retake it when the kernel changes.
-PAIR_DRAM_BYTES_PER_POINT = 86.9
+PAIR_DRAM_BYTES_PER_POINT = 88.6
 # the same for one launch of the native-FP64 one-iteration kernel on the scaled
-# operator (a bracket step), from ncu on 192^3
-# (profiles/k_newton_tma_double_192cube.md)
-NATIVE_DRAM_BYTES_PER_POINT = 90.8
+# operator (a bracket step), from the same capture
+NATIVE_DRAM_BYTES_PER_POINT = 90.4
 # DRAM bytes of one launch of the float-float sliced complex CSR kernel on the
 # 21-spin operator (profiles/k_csr_newton_sell_c_spin_bath_21.md)
 SPIN_DRAM_BYTES_PER_LAUNCH = 1.237e9
