@@ -29,6 +29,8 @@
 #include <cuda_runtime.h>
 #include <stdint.h>
 
+#include <utility>
+
 #include "ei_device.cuh"
 
 namespace ei {
@@ -121,6 +123,18 @@ __device__ __forceinline__ bool mbar_wait_bounded(uint32_t bar, uint32_t parity,
 
 static constexpr uint64_t kWaitLimitNs = 500000000ull;  // 0.5 s; a plane lands in microseconds
 
+// One-iteration Newton launches go out with programmatic stream serialization
+// (launch_pdl): a launch may be scheduled while the previous Newton step
+// drains (15.584 -> 15.466 ms a native 256^3 step; the two-iteration kernel's
+// many-wave grid gained nothing and launches plainly).  Before reading anything that step wrote (w, p, the control block)
+// it waits for that grid to complete and its writes to be visible; then it
+// lets the next launch be scheduled early in turn.  Both are no-ops for a
+// launch without the attribute.
+__device__ __forceinline__ void pdl_wait_and_release() {
+  asm volatile("griddepcontrol.wait;" ::: "memory");
+  asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
+}
+
 // PRE: the coefficient tiles hold the scaled operator (A - cI)/gamma (native
 // FP64 and float-float), so w_{j+1} = (A w_j - c w_j)/gamma - xi_j w_j is the
 // 7-point sum and one multiply-add with -xi_j: the scaling saves a multiply
@@ -142,6 +156,7 @@ k_newton_tma(const __grid_constant__ NewtonMaps M, const StencilDev g, const New
   using T = typename C::T;
   using P = typename C::P;
   static_assert(!FSTEP || !PRE, "the F pass runs on A");
+  if constexpr (!FSTEP) pdl_wait_and_release();
   if (!FSTEP && *(volatile int*)&ctl->done != 0) return;
   extern __shared__ __align__(128) unsigned char smem_raw[];
   // stage tiles start on 128-byte boundaries whatever the static shared memory
@@ -722,6 +737,23 @@ static int64_t tma_balanced_blocks(const StencilDev& g, int slots) {
   return nb < 1 ? 1 : nb;
 }
 
+// a kernel launch with programmatic stream serialization allowed
+template <class... KArgs, class... Args>
+static cudaError_t launch_pdl(void (*kernel)(KArgs...), dim3 grid, dim3 block, size_t smem,
+                              cudaStream_t st, Args&&... args) {
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = grid;
+  cfg.blockDim = block;
+  cfg.dynamicSmemBytes = smem;
+  cfg.stream = st;
+  cudaLaunchAttribute attr[1];
+  attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+  attr[0].val.programmaticStreamSerializationAllowed = 1;
+  cfg.attrs = attr;
+  cfg.numAttrs = 1;
+  return cudaLaunchKernelEx(&cfg, kernel, std::forward<Args>(args)...);
+}
+
 template <int FMT, bool PRE, bool PN = true, int FSTEP = 0>
 static cudaError_t launch_one(const StencilDev& g, const NewtonMaps& M, void* w_out, void* p,
                               const NewtonScalars& s, double* partials, DevCtl* ctl,
@@ -739,6 +771,9 @@ static cudaError_t launch_one(const StencilDev& g, const NewtonMaps& M, void* w_
     slots = (per_sm > 0 ? per_sm : 1) * sm_count();
   }
   const int64_t nb = tma_balanced_blocks(g, slots);
+  if constexpr (FSTEP == 0)
+    return launch_pdl(k_newton_tma<FMT, PRE, PN, FSTEP>, dim3((unsigned)nb), dim3(32, 8, 1),
+                      C::SMEM, st, M, g, s, w_out, p, partials, ctl, fa);
   k_newton_tma<FMT, PRE, PN, FSTEP><<<(unsigned)nb, dim3(32, 8, 1), C::SMEM, st>>>(
       M, g, s, w_out, p, partials, ctl, fa);
   return cudaGetLastError();
