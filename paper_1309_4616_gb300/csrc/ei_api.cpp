@@ -1758,11 +1758,9 @@ static ei_status step_impl(ei_ctx* c, int method, double h, void* u, int nonlin,
   Prepared& P = c->prep[fmt];
   const int64_t n = c->n;
   const int rosen = (method == EI_EXP_ROSENBROCK);
-  // stencils without Dirichlet data: F, J's diagonal and J's interval in one
-  // pass on the TMA z-march
-  bool faces = false;
-  for (int f = 0; f < 6; ++f) faces = faces || c->face_term[f] != nullptr;
-  const bool f_tma = c->kind == KIND_STENCIL && P.coef7 && !faces &&
+  // stencils: F (with any Dirichlet data's face terms), J's diagonal and J's
+  // interval in one pass on the TMA z-march
+  const bool f_tma = c->kind == KIND_STENCIL && P.coef7 &&
                      ((fmt == VF_F32) == (c->prec == EI_PREC_F32));
   // There the native FP64 and FP32 formats read the caller's u in place when
   // it already has the library's layout (rows of a multiple of 4 elements)
@@ -1792,6 +1790,7 @@ static ei_status step_impl(ei_ctx* c, int method, double h, void* u, int nonlin,
     fa.u = u;
     fa.nonlin = nonlin;
     fa.rosen = rosen;
+    for (int f = 0; f < 6; ++f) fa.face[f] = c->face_term[f];
     EI_LAUNCH(launch_f_tma(stencil_view(c, P, base_diag(P)), M, P.v, P.qc, fa, fmt,
                            c->partials, c->ctl, c->stream));
     ++P.qc_ver;  // qc now holds this step's J diagonal

@@ -124,6 +124,9 @@ struct FStepArgs {
                             // formats, taken in FP64 as the separate pass takes it
   int nonlin = 0;
   int rosen = 0;
+  // inhomogeneous Dirichlet data: per face x-, x+, y-, y+, z-, z+ the FP64 face
+  // terms added at the rows next to it (nullptr: none), indexed as BndFaces
+  const double* face[6] = {nullptr, nullptr, nullptr, nullptr, nullptr, nullptr};
 };
 
 // ---- launchers (all asynchronous on `st`) ----------------------------------

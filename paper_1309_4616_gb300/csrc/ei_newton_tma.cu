@@ -274,6 +274,17 @@ k_newton_tma(const __grid_constant__ NewtonMaps M, const StencilDev g, const New
           // F = A u + g(u), g(u) = u(1 - u), g'(u) = 1 - 2u (logistic)
           const T one = from_d<T>(1.0), mtwo = from_d<T>(-2.0);
           T Fv = acc, gq = zero<T>();
+          if (x == 0 || x == g.nx - 1 || y == 0 || y == g.ny - 1 || z == 0 || z == g.nz - 1) {
+            // b_D: the Dirichlet data's face terms at the rows next to a face
+            double bd = 0.0;
+            if (x == 0 && fa.face[0]) bd += fa.face[0][(int64_t)z * g.ny + y];
+            if (x == g.nx - 1 && fa.face[1]) bd += fa.face[1][(int64_t)z * g.ny + y];
+            if (y == 0 && fa.face[2]) bd += fa.face[2][(int64_t)z * g.nx + x];
+            if (y == g.ny - 1 && fa.face[3]) bd += fa.face[3][(int64_t)z * g.nx + x];
+            if (z == 0 && fa.face[4]) bd += fa.face[4][(int64_t)y * g.nx + x];
+            if (z == g.nz - 1 && fa.face[5]) bd += fa.face[5][(int64_t)y * g.nx + x];
+            if (bd != 0.0) Fv = add(Fv, from_d<T>(bd));
+          }
           if (fa.nonlin == EI_NONLIN_LOGISTIC) {
             Fv = mac(Fv, wc, sub(one, wc));
             gq = mac(one, mtwo, wc);
