@@ -1760,8 +1760,7 @@ static ei_status step_impl(ei_ctx* c, int method, double h, void* u, int nonlin,
   const int rosen = (method == EI_EXP_ROSENBROCK);
   // stencils: F (with any Dirichlet data's face terms), J's diagonal and J's
   // interval in one pass on the TMA z-march
-  const bool f_tma = c->kind == KIND_STENCIL && P.coef7 &&
-                     ((fmt == VF_F32) == (c->prec == EI_PREC_F32));
+  const bool f_tma = c->kind == KIND_STENCIL;
   // There the native FP64 and FP32 formats read the caller's u in place when
   // it already has the library's layout (rows of a multiple of 4 elements)
   // and a 16-byte aligned base: the import would only copy it (its norm is
@@ -1793,12 +1792,6 @@ static ei_status step_impl(ei_ctx* c, int method, double h, void* u, int nonlin,
     for (int f = 0; f < 6; ++f) fa.face[f] = c->face_term[f];
     EI_LAUNCH(launch_f_tma(stencil_view(c, P, base_diag(P)), M, P.v, P.qc, fa, fmt,
                            c->partials, c->ctl, c->stream));
-    ++P.qc_ver;  // qc now holds this step's J diagonal
-  } else if (c->kind == KIND_STENCIL) {
-    BndFaces bnd;
-    for (int f = 0; f < 6; ++f) bnd.c[f] = c->face_term[f];
-    EI_LAUNCH(launch_stencil_F(stencil_view(c, P, base_diag(P)), P.u, P.v, base_diag(P), P.qc,
-                               nonlin, rosen, bnd, fmt, c->partials, c->ctl, c->stream));
     ++P.qc_ver;  // qc now holds this step's J diagonal
   } else {
     EI_LAUNCH(launch_csr_F(csr_view(c, P, P.cbase), P.u, P.v, P.qc, P.cbase, nonlin, rosen,

@@ -125,7 +125,8 @@ struct FStepArgs {
   int nonlin = 0;
   int rosen = 0;
   // inhomogeneous Dirichlet data: per face x-, x+, y-, y+, z-, z+ the FP64 face
-  // terms added at the rows next to it (nullptr: none), indexed as BndFaces
+  // terms added at the rows next to it (nullptr: none): x- and x+ faces indexed
+  // z * ny + y, y- and y+ faces z * nx + x, z- and z+ faces y * nx + x
   const double* face[6] = {nullptr, nullptr, nullptr, nullptr, nullptr, nullptr};
 };
 
@@ -201,22 +202,6 @@ cudaError_t launch_p_to_vec(void* dst, const void* p, int fmt, int64_t n_alloc, 
 cudaError_t launch_axpy(void* y, const void* p, int fmt, int64_t n_alloc, double tau,
                         cudaStream_t st);
 cudaError_t launch_zero(void* x, int fmt, int64_t n_alloc, cudaStream_t st);
-
-// Step start: F = A u + g(u), with A's diagonal from `diag_base`, and
-// diag_out = diag_base + g'(u) (Rosenbrock).
-// u in vector format.  ||F||^2 into ctl->sum0, finiteness into ctl->sum1.
-// inhomogeneous Dirichlet data: per face the FP64 term (face coefficient x
-// prescribed value) added to A u at the rows next to that face; NULL: none
-struct BndFaces {
-  const double* c[6];
-};
-// face term of face f from the caller's values (operator precision prec)
-cudaError_t launch_face_term(const StencilDev& g, int face, int prec, const double dx[3],
-                             const void* D, double D_const, const void* b_axis,
-                             double b_const, const void* vals, double* out, cudaStream_t stm);
-cudaError_t launch_stencil_F(const StencilDev& op, const void* u, void* F, const void* diag_base,
-                             void* diag_out, int nonlin, int rosenbrock, const BndFaces& bnd,
-                             int fmt, double* partials, DevCtl* ctl, cudaStream_t st);
 cudaError_t launch_csr_F(const CsrDev& op, const void* u, void* F, void* qc_out,
                          const void* c_base, int nonlin, int rosenbrock, int fmt,
                          double* partials, DevCtl* ctl, cudaStream_t st);
@@ -235,6 +220,12 @@ cudaError_t launch_csr_residual(const CsrDev& op, const void* y, const void* v, 
 cudaError_t launch_newton_tma(const StencilDev& op, const NewtonMaps& M, void* w_out, void* p,
                               const NewtonScalars& s, int fmt, double* partials, DevCtl* ctl,
                               cudaStream_t st, bool prescaled = false);
+// inhomogeneous Dirichlet data: the FP64 face term of face f (face coefficient
+// x prescribed value, added to A u at the rows next to that face) from the
+// caller's values (operator precision prec)
+cudaError_t launch_face_term(const StencilDev& g, int face, int prec, const double dx[3],
+                             const void* D, double D_const, const void* b_axis,
+                             double b_const, const void* vals, double* out, cudaStream_t stm);
 // F = A u + g(u) (any EI_NONLIN_*) on the TMA z-march, in the vector format
 // fmt (native FP64, float-float or FP32): M.w maps u (halo box), M.c the raw
 // coefficients a[0..5]

@@ -251,65 +251,6 @@ k_stencil_residual(StencilDev g, const void* __restrict__ y_, const void* __rest
   }
 }
 
-// F = A u + b_D + g(u); diag_out = diag_base + g'(u) (Rosenbrock).  b_D, the
-// inhomogeneous Dirichlet data, is read only at the rows next to a face that
-// has it (BndFaces).  COMB: the combustion forms are compiled in (a separate
-// instantiation, so the common path keeps its few registers).
-template <int FMT, bool COMB>
-__global__ void __launch_bounds__(EI_TPB, COMB ? 1 : 6)
-k_stencil_F(StencilDev g, const void* __restrict__ u_, void* __restrict__ F_,
-            const void* __restrict__ db_, void* __restrict__ dout_, int nonlin, int rosenbrock,
-            BndFaces bnd, double* partials, DevCtl* ctl) {
-  using T = typename VT<FMT>::T;
-  const T* __restrict__ u = static_cast<const T*>(u_);
-  const T* __restrict__ db = static_cast<const T*>(db_);
-  T* __restrict__ F = static_cast<T*>(F_);
-  T* __restrict__ dout = static_cast<T*>(dout_);
-  const T one = from_d<T>(1.0), mtwo = from_d<T>(-2.0);
-  const int64_t n = (int64_t)g.nx * g.ny * g.nz;
-  T af = zero<T>();
-  // two points a thread per pass: the second point's loads can go out before
-  // the first point's stores (all arrays are restrict-qualified)
-#pragma unroll 2
-  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;
-       i += (int64_t)gridDim.x * blockDim.x) {
-    int x, y, z;
-    int64_t t;
-    grid_coords(g, n, i, x, y, z, t);
-    const int64_t idx = t * g.pitch + x;
-    T uc;
-    T Fv = apply_coef7<T>(g, u, db, x, y, z, idx, uc);
-    if (x == 0 || x == g.nx - 1 || y == 0 || y == g.ny - 1 || z == 0 || z == g.nz - 1) {
-      double bd = 0.0;
-      if (x == 0 && bnd.c[0]) bd += bnd.c[0][(int64_t)z * g.ny + y];
-      if (x == g.nx - 1 && bnd.c[1]) bd += bnd.c[1][(int64_t)z * g.ny + y];
-      if (y == 0 && bnd.c[2]) bd += bnd.c[2][(int64_t)z * g.nx + x];
-      if (y == g.ny - 1 && bnd.c[3]) bd += bnd.c[3][(int64_t)z * g.nx + x];
-      if (z == 0 && bnd.c[4]) bd += bnd.c[4][(int64_t)y * g.nx + x];
-      if (z == g.nz - 1 && bnd.c[5]) bd += bnd.c[5][(int64_t)y * g.nx + x];
-      if (bd != 0.0) Fv = add(Fv, from_d<T>(bd));
-    }
-    T gq = zero<T>();
-    if constexpr (COMB) {
-      T gv;
-      combustion_term(nonlin, uc, gv, gq);
-      Fv = add(Fv, gv);
-    } else if (nonlin == EI_NONLIN_LOGISTIC) {
-      Fv = mac(Fv, uc, sub(one, uc));  // g(u) = u(1-u)
-      gq = mac(one, mtwo, uc);         // g'(u) = 1 - 2u
-    }
-    st(F, idx, Fv);
-    if (rosenbrock) st(dout, idx, nonlin ? add(ldg(db, idx), gq) : ldg(db, idx));
-    af = mac(af, Fv, Fv);
-  }
-  double a = to_d(af), b = 0.0;
-  if (last_block_reduce2<RED_SUM>(a, b, partials, ctl)) {
-    if (threadIdx.x == 0) {
-      ctl->sum0 = a;
-      ctl->sum1 = finite_d(a) ? 1.0 : 0.0;
-    }
-  }
-}
 
 // ---------------------------------------------------------------------------
 // CSR operator (Sec. III-D): one thread per row.  The paper's C2075 code gave
@@ -974,17 +915,6 @@ cudaError_t launch_stencil_residual(const StencilDev& g, const void* y, const vo
   return cudaGetLastError();
 }
 
-cudaError_t launch_stencil_F(const StencilDev& g, const void* u, void* F, const void* diag_base,
-                             void* diag_out, int nonlin, int rosenbrock, const BndFaces& bnd,
-                             int fmt, double* partials, DevCtl* ctl, cudaStream_t stm) {
-  const int nb = ew_blocks((int64_t)g.nx * g.ny * g.nz);
-  if (nonlin >= EI_NONLIN_COMBUSTION) {
-    EI_DISPATCH_FMT(fmt, (k_stencil_F<F_, true><<<nb, EI_TPB, 0, stm>>>(g, u, F, diag_base, diag_out, nonlin, rosenbrock, bnd, partials, ctl)));
-  } else {
-    EI_DISPATCH_FMT(fmt, (k_stencil_F<F_, false><<<nb, EI_TPB, 0, stm>>>(g, u, F, diag_base, diag_out, nonlin, rosenbrock, bnd, partials, ctl)));
-  }
-  return cudaGetLastError();
-}
 
 // Face term of face f (2 ax + side): at each boundary row next to the face,
 // (D_i/dx^2 + sgn b_i/(2 dx)) x the prescribed ghost value (the ghost D is D_i),
