@@ -147,7 +147,10 @@ __device__ __forceinline__ void pdl_wait_and_release() {
 // in M.c, F to w_out, J's diagonal to p_; it runs whatever ctl->done says.
 // 1: g none or logistic; 2: also the combustion terms (a separate
 // instantiation: their exponential and reciprocal take many registers).
-template <int FMT, bool PRE, bool PN = true, int FSTEP = 0>
+// FACES: the Dirichlet data's face terms are compiled in (a separate
+// instantiation: the compiler predicates their FP64 adds onto every point,
+// which the FP64-bound pass cannot afford).
+template <int FMT, bool PRE, bool PN = true, int FSTEP = 0, bool FACES = false>
 __global__ void __launch_bounds__(256, TmaCfg<FMT>::MINB)
 k_newton_tma(const __grid_constant__ NewtonMaps M, const StencilDev g, const NewtonScalars s,
              void* __restrict__ w_out_, void* __restrict__ p_, double* partials, DevCtl* ctl,
@@ -274,7 +277,8 @@ k_newton_tma(const __grid_constant__ NewtonMaps M, const StencilDev g, const New
           // F = A u + g(u), g(u) = u(1 - u), g'(u) = 1 - 2u (logistic)
           const T one = from_d<T>(1.0), mtwo = from_d<T>(-2.0);
           T Fv = acc, gq = zero<T>();
-          if (x == 0 || x == g.nx - 1 || y == 0 || y == g.ny - 1 || z == 0 || z == g.nz - 1) {
+          if (FACES &&
+              (x == 0 || x == g.nx - 1 || y == 0 || y == g.ny - 1 || z == 0 || z == g.nz - 1)) {
             // b_D: the Dirichlet data's face terms at the rows next to a face
             double bd = 0.0;
             if (x == 0 && fa.face[0]) bd += fa.face[0][(int64_t)z * g.ny + y];
@@ -765,19 +769,19 @@ static cudaError_t launch_pdl(void (*kernel)(KArgs...), dim3 grid, dim3 block, s
   return cudaLaunchKernelEx(&cfg, kernel, std::forward<Args>(args)...);
 }
 
-template <int FMT, bool PRE, bool PN = true, int FSTEP = 0>
+template <int FMT, bool PRE, bool PN = true, int FSTEP = 0, bool FACES = false>
 static cudaError_t launch_one(const StencilDev& g, const NewtonMaps& M, void* w_out, void* p,
                               const NewtonScalars& s, double* partials, DevCtl* ctl,
                               cudaStream_t st, const FStepArgs& fa = FStepArgs{}) {
   using C = TmaCfg<FMT>;
   static int slots = 0;
   if (slots == 0) {
-    cudaError_t e = cudaFuncSetAttribute(k_newton_tma<FMT, PRE, PN, FSTEP>,
+    cudaError_t e = cudaFuncSetAttribute(k_newton_tma<FMT, PRE, PN, FSTEP, FACES>,
                                          cudaFuncAttributeMaxDynamicSharedMemorySize, C::SMEM);
     if (e != cudaSuccess) return e;
     int per_sm = 0;
-    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_newton_tma<FMT, PRE, PN, FSTEP>,
-                                                      256, C::SMEM);
+    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(
+        &per_sm, k_newton_tma<FMT, PRE, PN, FSTEP, FACES>, 256, C::SMEM);
     if (e != cudaSuccess) return e;
     slots = (per_sm > 0 ? per_sm : 1) * sm_count();
   }
@@ -785,25 +789,35 @@ static cudaError_t launch_one(const StencilDev& g, const NewtonMaps& M, void* w_
   if constexpr (FSTEP == 0)
     return launch_pdl(k_newton_tma<FMT, PRE, PN, FSTEP>, dim3((unsigned)nb), dim3(32, 8, 1),
                       C::SMEM, st, M, g, s, w_out, p, partials, ctl, fa);
-  k_newton_tma<FMT, PRE, PN, FSTEP><<<(unsigned)nb, dim3(32, 8, 1), C::SMEM, st>>>(
+  k_newton_tma<FMT, PRE, PN, FSTEP, FACES><<<(unsigned)nb, dim3(32, 8, 1), C::SMEM, st>>>(
       M, g, s, w_out, p, partials, ctl, fa);
   return cudaGetLastError();
+}
+
+template <int FMT, int FSTEP>
+static cudaError_t launch_f_faces(const StencilDev& g, const NewtonMaps& M, void* F, void* dout,
+                                  const FStepArgs& fa, double* partials, DevCtl* ctl,
+                                  cudaStream_t st) {
+  bool faces = false;
+  for (int f = 0; f < 6; ++f) faces = faces || fa.face[f] != nullptr;
+  const NewtonScalars none{};
+  if (faces)
+    return launch_one<FMT, false, true, FSTEP, true>(g, M, F, dout, none, partials, ctl, st, fa);
+  return launch_one<FMT, false, true, FSTEP, false>(g, M, F, dout, none, partials, ctl, st, fa);
 }
 
 cudaError_t launch_f_tma(const StencilDev& g, const NewtonMaps& M, void* F, void* dout,
                          const FStepArgs& fa, int fmt, double* partials, DevCtl* ctl,
                          cudaStream_t st) {
-  const NewtonScalars none{};
   const bool comb = fa.nonlin != EI_NONLIN_NONE && fa.nonlin != EI_NONLIN_LOGISTIC;
-  if (fmt == VF_DF && comb)
-    return launch_one<VF_DF, false, true, 2>(g, M, F, dout, none, partials, ctl, st, fa);
-  if (fmt == VF_DF) return launch_one<VF_DF, false, true, 1>(g, M, F, dout, none, partials, ctl, st, fa);
-  if (fmt == VF_F64 && comb)
-    return launch_one<VF_F64, false, true, 2>(g, M, F, dout, none, partials, ctl, st, fa);
+  if (fmt == VF_DF)
+    return comb ? launch_f_faces<VF_DF, 2>(g, M, F, dout, fa, partials, ctl, st)
+                : launch_f_faces<VF_DF, 1>(g, M, F, dout, fa, partials, ctl, st);
   if (fmt == VF_F64)
-    return launch_one<VF_F64, false, true, 1>(g, M, F, dout, none, partials, ctl, st, fa);
-  if (comb) return launch_one<VF_F32, false, true, 2>(g, M, F, dout, none, partials, ctl, st, fa);
-  return launch_one<VF_F32, false, true, 1>(g, M, F, dout, none, partials, ctl, st, fa);
+    return comb ? launch_f_faces<VF_F64, 2>(g, M, F, dout, fa, partials, ctl, st)
+                : launch_f_faces<VF_F64, 1>(g, M, F, dout, fa, partials, ctl, st);
+  return comb ? launch_f_faces<VF_F32, 2>(g, M, F, dout, fa, partials, ctl, st)
+              : launch_f_faces<VF_F32, 1>(g, M, F, dout, fa, partials, ctl, st);
 }
 
 cudaError_t launch_newton_tma(const StencilDev& g, const NewtonMaps& M, void* w_out, void* p,
