@@ -69,6 +69,9 @@ PAIR_DRAM_BYTES_PER_POINT = 88.6
 # the same for one launch of the native-FP64 one-iteration kernel on the scaled
 # operator (a bracket step), from the same capture
 NATIVE_DRAM_BYTES_PER_POINT = 90.4
+# the float-float pair kernel on a constant operator's coefficient table (no
+# coefficient arrays), per point and launch: None until captured
+TABLE_PAIR_DRAM_BYTES_PER_POINT = None
 # DRAM bytes of one launch of the float-float sliced complex CSR kernel on the
 # 21-spin operator (profiles/k_csr_newton_sell_c_spin_bath_21.md)
 SPIN_DRAM_BYTES_PER_LAUNCH = 1.237e9
@@ -376,7 +379,8 @@ class Combustion3d(Adr3d):
         self.state = self.state0.clone()
         self.host0 = w.u0
         # constant coefficients: the scope's count is w 8 + w' 8 + p 16; the
-        # library streams its seven stored coefficient arrays all the same
+        # pair kernel reads the operator from its coefficient table (as stored:
+        # 32 bytes; 88 with the seven coefficient arrays)
         self.bytes_per_point = CONST_BYTES_PER_POINT
         self.bytes_per_point_stored = BYTES_PER_POINT
         self.nonlin = ei.NONLIN_COMBUSTION_FAST if self.fast else ei.NONLIN_COMBUSTION
@@ -1075,12 +1079,18 @@ def roofline(wl, r, args, npts):
         avg_launch_s = prof_ms / max(prof_n, 1) * 1e-3
         achieved = wl.bytes_per_point * npts * fused / avg_launch_s / 1e9
     traffic = getattr(wl, "traffic_per_launch", None)
+    # a constant operator (D, b and c constants): the pair kernel reads the
+    # coefficient table instead of the seven arrays
+    table = getattr(st, "coef_table", 0) > 0
     if isinstance(wl, Adr3d) and wl.dtype == DTYPE_FF and fused == 2:
-        traffic = PAIR_DRAM_BYTES_PER_POINT * npts  # the float-float pair kernel (ncu)
+        # the float-float pair kernel (ncu)
+        per_pt = TABLE_PAIR_DRAM_BYTES_PER_POINT if table else PAIR_DRAM_BYTES_PER_POINT
+        traffic = per_pt * npts if per_pt else None
     out = {"bound": "hbm", "achieved": achieved, "peak": hbm, "unit": "GB/s",
            "frac": achieved / hbm,
            "traffic": traffic,
-           "kernel": wl.kernel(fused),
+           "kernel": wl.kernel(fused) + (", the operator as its coefficient table"
+                                         if table else ""),
            "bytes_per_launch": (prof_bytes / max(prof_n, 1)) if prof_bytes
            else wl.bytes_per_point * npts * fused,
            "avg_launch_us": avg_launch_s * 1e6, "launches_timed": prof_n,
@@ -1089,6 +1099,8 @@ def roofline(wl, r, args, npts):
            "peak_kind": peak_kind,
            "paper_gflops": FLOPS_PER_POINT_PAPER * npts * fused / avg_launch_s / 1e9}
     stored = getattr(wl, "bytes_per_point_stored", None)
+    if table:
+        stored = CONST_BYTES_PER_POINT  # w, w' and p only
     if stored:
         out["bytes_per_point"] = wl.bytes_per_point
         out["bytes_per_point_stored"] = stored

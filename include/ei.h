@@ -160,7 +160,12 @@ typedef struct {
                            take the test */
   int newton_bounded;   /* of the newton_timed launches, those that bracketed
                            the norms */
-  int pad_end;
+  int coef_table;       /* stencil operators whose D, b and c are all constants
+                           (float-float): two-iteration Newton launches that
+                           read the operator from a table of 70 coefficients
+                           (six off-diagonals, the diagonal of each of the 64
+                           classes of points by the faces they touch) instead
+                           of the seven coefficient arrays */
 } ei_stats;
 
 /* Create a context on CUDA device `device`, ordering work on `cuda_stream`

@@ -73,6 +73,11 @@ struct Prepared {
   double pre_cc = 0.0, pre_gamma = 0.0, pre_ratio = 1.0;
   bool off_valid = false;
   double off_gamma = 0.0;
+  // float-float, an operator with constant D, b and c: the scaled operator as
+  // a table of kConstTab coefficients (launch_const_table), current when
+  // ctab_ok (sa made for the operator's own diagonal)
+  void* ctab = nullptr;
+  bool ctab_ok = false;
   unsigned qc_ver = 0;     // bumped whenever qc is rewritten (each Rosenbrock step)
 };
 
@@ -92,6 +97,7 @@ struct ei_ctx {
   double bcst[3] = {0, 0, 0};
   const void* cu = nullptr;
   double cc = 0;
+  bool const_coef = false;  // D, b and c all constants (no arrays)
   // CSR description
   CsrDev cd{};
   int64_t nnz = 0;
@@ -149,6 +155,7 @@ struct ei_ctx {
   const void* umap_ptr = nullptr;
   int umap_fmt = -1;
   int newton_bounded = 0;  // timed Newton launches that bracketed the norms
+  int coef_table = 0;      // two-iteration launches on the constant operator's table
   int fuse = 0;            // Newton iterations per stencil launch: 0 the format's
                            // default (two for float-float and float, one for native
                            // FP64), 1 one, 2 two
@@ -210,13 +217,14 @@ static void free_prepared(Prepared& p) {
   void** arrs[] = {&p.cbase, &p.qc,   &p.w[0], &p.w[1], &p.p,    &p.y,    &p.r,
                    &p.v,     &p.u,    &p.csr_val, &p.sell_val, &p.a[0], &p.a[1], &p.a[2], &p.a[3],
                    &p.a[4],  &p.a[5], &p.diagA, &p.sa[0], &p.sa[1], &p.sa[2], &p.sa[3],
-                   &p.sa[4], &p.sa[5], &p.sa[6]};
+                   &p.sa[4], &p.sa[5], &p.sa[6], &p.ctab};
   for (void** a : arrs) {
     if (*a) cudaFree(*a);
     *a = nullptr;
   }
   p.pre_valid = false;
   p.off_valid = false;
+  p.ctab_ok = false;
   p.ready = false;
   p.coef7 = false;  // a later operator of another kind must not inherit the layout
   p.n_alloc = 0;
@@ -314,6 +322,8 @@ static ei_status prepare(ei_ctx* c, int fmt) {
         if ((s = take(&P.sa[k], vb)) != EI_OK) { free_prepared(P); return s; }
       for (int k = 0; k < 7; ++k) ok = ok && encode_map(&P.map_s[k], P.sa[k], eb, c->sd, 0);
     }
+    if (fmt == VF_DF && c->const_coef)
+      if ((s = alloc(&P.ctab, vec_elem_bytes(fmt) * kConstTab)) != EI_OK) { free_prepared(P); return s; }
     ok = ok && encode_map(&P.map_qc, P.qc, eb, c->sd, 0);
     ok = ok && encode_map(&P.map_p, P.p, 8, c->sd, 0);
     ok = ok && encode_map(&P.map_u, P.u, eb, c->sd, 1);
@@ -409,6 +419,34 @@ static std::vector<double> rescaled_dd(const std::vector<double>& d, double r) {
   return out;
 }
 
+// One point of each entry of the constant operator's table (ConstTabIdx), as
+// a padded index: for the off-diagonal towards side s of axis e, a point whose
+// neighbour there is inside the grid; for the diagonal of class cx + 4 cy +
+// 16 cz, a point on exactly the faces the class names.
+static int class_coord(int cls, int n) {
+  if (cls == 0) return n >= 3 ? 1 : -1;
+  if (cls == 1) return n >= 2 ? 0 : -1;
+  if (cls == 2) return n >= 2 ? n - 1 : -1;
+  return n == 1 ? 0 : -1;
+}
+static void const_table_points(const StencilDev& g, ConstTabIdx& ix) {
+  const int ext[3] = {g.nx, g.ny, g.nz};
+  auto pidx = [&](const int q[3]) {
+    return ((int64_t)q[2] * g.ny + q[1]) * g.pitch + q[0];
+  };
+  for (int k = 0; k < 6; ++k) {
+    const int e = k / 2;
+    int q[3] = {0, 0, 0};
+    q[e] = (k & 1) ? 0 : 1;  // the x- neighbour of x = 1, the x+ neighbour of x = 0
+    ix.idx[k] = ext[e] >= 2 ? pidx(q) : -1;
+  }
+  for (int cls = 0; cls < 64; ++cls) {
+    const int q[3] = {class_coord(cls & 3, g.nx), class_coord((cls >> 2) & 3, g.ny),
+                      class_coord(cls >> 4, g.nz)};
+    ix.idx[6 + cls] = (q[0] < 0 || q[1] < 0 || q[2] < 0) ? -1 : pidx(q);
+  }
+}
+
 // The off-diagonals keep their scale gamma0 while gamma0/gamma lies within
 // 1 +- 1/8: the Newton loop's scale factors (gamma0/gamma)^j then stay within
 // about 1.3e5 over 100 steps.
@@ -431,6 +469,12 @@ static ei_status ensure_prescaled(ei_ctx* c, Prepared& P, const void* qc, double
   P.pre_ver = P.qc_ver;
   P.pre_cc = cc;
   P.pre_gamma = gamma;
+  P.ctab_ok = P.ctab && qc == base_diag(P);
+  if (P.ctab_ok) {
+    ConstTabIdx ix;
+    const_table_points(c->sd, ix);
+    EI_LAUNCH(launch_const_table(P.sa, ix, P.ctab, P.fmt, c->stream));
+  }
   return EI_OK;
 }
 
@@ -478,8 +522,10 @@ static cudaError_t op_newton2(ei_ctx* c, Prepared& P, const void* qc, const void
   for (int k = 0; k < 6; ++k) M.c[k] = pre ? P.map_s[k] : P.map_c[k];
   M.c[6] = pre ? P.map_s[6] : (qc == P.qc) ? P.map_qc : P.map_diagA;
   M.p = P.map_p;
+  const void* tab = pre && P.ctab_ok ? P.ctab : nullptr;
+  if (tab) ++c->coef_table;
   return launch_newton2_tma(pre ? stencil_view_scaled(c, P) : stencil_view(c, P, qc), M, w_out,
-                            P.p, s, P.fmt, c->partials, c->ctl, c->stream, pre);
+                            P.p, s, P.fmt, c->partials, c->ctl, c->stream, pre, tab);
 }
 
 // Whether the Newton loop runs two iterations per launch: explicit-coefficient
@@ -1261,6 +1307,8 @@ ei_status ei_set_operator_stencil(ei_ctx* c, int dim, const int64_t n[3], const 
   }
   c->cu = cdiag;
   c->cc = c_const;
+  c->const_coef = !D && !cdiag;
+  for (int e = 0; e < dim; ++e) c->const_coef = c->const_coef && !c->bu[e];
   // Gershgorin rows of A (FP64 from the caller's arrays) and reduction space
   int nb = newton_tma_blocks(s);
   if (nb < reduction_capacity()) nb = reduction_capacity();
@@ -1393,6 +1441,7 @@ static void acct_begin(ei_ctx* c, const ei_options* opt) {
   c->newton_fused = 1;
   c->p_rechecks = 0;
   c->newton_bounded = 0;
+  c->coef_table = 0;
   c->profile = opt && opt->profile;
   c->fuse = opt ? opt->single_iter : 0;
   c->csr_lanes = opt ? opt->csr_lanes : 0;
@@ -1406,6 +1455,7 @@ static void acct_end(ei_ctx* c, ei_stats* st) {
   st->newton_fused = c->newton_fused;
   st->p_rechecks = c->p_rechecks;
   st->newton_bounded = c->newton_bounded;
+  st->coef_table = c->coef_table;
 }
 
 static ei_status phi_apply_impl(ei_ctx* c, int k, double h, const void* v, void* out, double tol,

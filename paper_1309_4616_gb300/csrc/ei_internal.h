@@ -250,9 +250,28 @@ cudaError_t launch_prescale_diag(void* sa6, const void* diag, int64_t n_alloc, d
 // Two Newton iterations j+1 and j+2 in one pass (explicit-coefficient stencil,
 // all formats): w_{j+1} is formed on chip over the tile and a one-point
 // halo; only w_{j+2} and p_{j+2} are written.  M.w must be a halo-2 map.
+// ctab (float-float on the scaled operator only, or null): the operator's
+// coefficients as a kConstTab-entry table, for an operator whose D, b and c
+// are constants (launch_const_table); the kernel then reads no coefficient
+// tiles.
 cudaError_t launch_newton2_tma(const StencilDev& op, const NewtonMaps& M, void* w_out, void* p,
                                const NewtonScalars& s, int fmt, double* partials, DevCtl* ctl,
-                               cudaStream_t st, bool prescaled = false);
+                               cudaStream_t st, bool prescaled = false,
+                               const void* ctab = nullptr);
+// A stencil operator with constant D, b and c has the same six off-diagonals
+// at every point (a neighbour outside the grid multiplies a zero ghost or is
+// folded into the diagonal), and its diagonal depends only on the faces the
+// point touches: 64 classes cx + 4 cy + 16 cz, bit 0 of each on the low face,
+// bit 1 on the high one.  The table holds the off-diagonals a[0..5] at entries
+// 0-5 and the diagonal of class k at entry 6 + k, each gathered from the
+// coefficient arrays sa[0..6] (vector format) at the padded index idx[entry]
+// of one point where it applies (-1: no such point; the entry is 0 and unused).
+constexpr int kConstTab = 70;
+struct ConstTabIdx {
+  int64_t idx[kConstTab];
+};
+cudaError_t launch_const_table(const void* const sa[7], const ConstTabIdx& ix, void* ctab,
+                               int fmt, cudaStream_t st);
 // p -= d * w (elementwise, Newton-sum format p, vector format w)
 cudaError_t launch_p_fixup(void* p, const void* w, int fmt, int64_t n_alloc, double d,
                            cudaStream_t st);

@@ -408,7 +408,10 @@ k_newton_tma(const __grid_constant__ NewtonMaps M, const StencilDev g, const New
 // step (a ring of 2 in shared memory); the centre and z neighbours are the
 // thread's own values in registers, so a step needs a single barrier.
 // ===========================================================================
-template <int FMT>
+// CONST: the operator's coefficients come from a 70-entry table (kConstTab)
+// instead of seven tiles a plane, so a coefficient-ring slot holds the p tile
+// alone and the table follows the mbarriers.
+template <int FMT, bool CONST = false>
 struct TmaCfg2 {
   using T = typename VT<FMT>::T;
   using P = typename VT<FMT>::P;
@@ -426,21 +429,28 @@ struct TmaCfg2 {
   static constexpr int C_BYTES = TX * TY * (int)sizeof(T);
   static constexpr int P_BYTES = TX * TY * (int)sizeof(P);
   static constexpr int WSTAGE = al(WJ_BYTES);
-  static constexpr int OFF_P = 7 * C_BYTES;
+  static constexpr int OFF_P = CONST ? 0 : 7 * C_BYTES;
   static constexpr int CSTAGE = al(OFF_P + P_BYTES);
   static constexpr int W1STAGE = al(W1X * W1Y * (int)sizeof(T));
   static constexpr int CRING = NW * WSTAGE;
   static constexpr int W1RING = CRING + NC * CSTAGE;
   static constexpr int BARS = W1RING + 2 * W1STAGE;
-  static constexpr int SMEM = BARS + 8 * NBAR + 128;
+  static constexpr int TAB = BARS + 8 * NBAR;
+  static constexpr int SMEM = TAB + (CONST ? kConstTab * (int)sizeof(T) : 0) + 128;
 };
 
-template <int FMT, bool PRE = false>
+// The boundary class of a coordinate: bit 0 on the low face, bit 1 on the
+// high one (both when the extent is 1).  A point's class is cx + 4 cy + 16 cz.
+__device__ __forceinline__ int face_class(int x, int n) {
+  return (x == 0 ? 1 : 0) | (x == n - 1 ? 2 : 0);
+}
+
+template <int FMT, bool PRE = false, bool CONST = false>
 __global__ void __launch_bounds__(256, 2)
 k_newton2_tma(const __grid_constant__ NewtonMaps M, const StencilDev g, const NewtonScalars s,
               void* __restrict__ w_out_, void* __restrict__ p_, double* partials, DevCtl* ctl,
-              int zc_len) {
-  using C = TmaCfg2<FMT>;
+              int zc_len, const void* __restrict__ ctab) {
+  using C = TmaCfg2<FMT, CONST>;
   using T = typename C::T;
   using P = typename C::P;
   if (*(volatile int*)&ctl->done != 0) return;
@@ -456,6 +466,11 @@ k_newton2_tma(const __grid_constant__ NewtonMaps M, const StencilDev g, const Ne
   const int nzc = z1 - z0;
   const int nq = nzc + 4;  // w_j planes z0-2 .. z1+1
   const bool needp = s.j > 0;
+  // CONST: the six off-diagonals, then the diagonal of each boundary class
+  T* ktab = reinterpret_cast<T*>(smem + C::TAB);
+  if constexpr (CONST) {
+    if (tid < kConstTab) ktab[tid] = ldg(static_cast<const T*>(ctab), tid);
+  }
 
   if (tid == 0) {
     for (int i = 0; i < C::NBAR; ++i) mbar_init(bar0 + 8 * i, 1);
@@ -469,7 +484,8 @@ k_newton2_tma(const __grid_constant__ NewtonMaps M, const StencilDev g, const Ne
     const uint32_t cb = sbase + C::CRING + (q % C::NC) * C::CSTAGE;
     const uint32_t bar = bar0 + 8 * (q % C::NBAR);
     const int z = z0 - 2 + q;
-    const bool hasc = (q >= 1) && (q <= nzc + 2);  // coefficient planes z0-1 .. z1
+    // coefficient planes z0-1 .. z1
+    const bool hasc = !CONST && (q >= 1) && (q <= nzc + 2);
     const bool hasp = needp && (q >= 2) && (q <= nzc + 1);
     mbar_expect_tx(bar, C::WJ_BYTES + (hasc ? 7 * C::C_BYTES : 0) + (hasp ? C::P_BYTES : 0));
     tma_load_3d(wb, &M.w, x0 - C::XH, y0 - 2, z, bar);
@@ -517,9 +533,16 @@ k_newton2_tma(const __grid_constant__ NewtonMaps M, const StencilDev g, const Ne
   }
   const int hx = x0 - 1 + hlx, hy = y0 - 1 + hly;
   const bool hxy = hlx >= 0 && hx >= 0 && hx < g.nx && hy >= 0 && hy < g.ny;
+  const int hcls = CONST && hxy ? face_class(hx, g.nx) + 4 * face_class(hy, g.ny) : 0;
   // halo coefficients come from global memory one step ahead of their use
+  // (CONST: from the table; an off-diagonal towards a neighbour outside the
+  // grid multiplies the zero that the w box holds there)
   auto load_halo = [&](int zz, T* a) {
-    if (hxy && zz >= 0 && zz < g.nz) {
+    if (CONST && hxy && zz >= 0 && zz < g.nz) {
+#pragma unroll
+      for (int k = 0; k < 6; ++k) a[k] = ktab[k];
+      a[6] = ktab[6 + hcls + 16 * face_class(zz, g.nz)];
+    } else if (!CONST && hxy && zz >= 0 && zz < g.nz) {
       const int64_t gi = ((int64_t)zz * g.ny + hy) * g.pitch + hx;
 #pragma unroll
       for (int k = 0; k < 6; ++k) a[k] = ldg(static_cast<const T*>(g.a[k]), gi);
@@ -537,6 +560,7 @@ k_newton2_tma(const __grid_constant__ NewtonMaps M, const StencilDev g, const Ne
   T w1_m2 = zero<T>(), w1_m1 = zero<T>();
   const int xi_ = x0 + tx, yi_ = y0 + ty;
   const bool own_xy = interior && (xi_ < g.nx) && (yi_ < g.ny);
+  const int ocls = CONST ? face_class(xi_, g.nx) + 4 * face_class(yi_, g.ny) : 0;
   const int wi_own = (ty + 2) * C::WJX + tx + C::XH;  // own point in the w_j box
   const int vi_own = (ty + 1) * C::W1X + tx + 1;   // own point in the w_{j+1} region
   const int ci = ty * C::TX + tx;
@@ -567,10 +591,16 @@ k_newton2_tma(const __grid_constant__ NewtonMaps M, const StencilDev g, const Ne
       if (interior && zin && own_xy) {
         const T* Ct = reinterpret_cast<const T*>(smem + C::CRING + sc1 * C::CSTAGE);
         const T wc = Wc[wi_own];
-        const T acc = stencil7(Ct[6 * TT + ci], wc, Ct[0 * TT + ci], Wc[wi_own - 1],
-                               Ct[1 * TT + ci], Wc[wi_own + 1], Ct[2 * TT + ci],
-                               Wc[wi_own - C::WJX], Ct[3 * TT + ci], Wc[wi_own + C::WJX],
-                               Ct[4 * TT + ci], Wm[wi_own], Ct[5 * TT + ci], Wp[wi_own]);
+        T acc;
+        if constexpr (CONST)
+          acc = stencil7(ktab[6 + ocls + 16 * face_class(zc, g.nz)], wc, ktab[0],
+                         Wc[wi_own - 1], ktab[1], Wc[wi_own + 1], ktab[2], Wc[wi_own - C::WJX],
+                         ktab[3], Wc[wi_own + C::WJX], ktab[4], Wm[wi_own], ktab[5], Wp[wi_own]);
+        else
+          acc = stencil7(Ct[6 * TT + ci], wc, Ct[0 * TT + ci], Wc[wi_own - 1], Ct[1 * TT + ci],
+                         Wc[wi_own + 1], Ct[2 * TT + ci], Wc[wi_own - C::WJX], Ct[3 * TT + ci],
+                         Wc[wi_own + C::WJX], Ct[4 * TT + ci], Wm[wi_own], Ct[5 * TT + ci],
+                         Wp[wi_own]);
         w1own = PRE ? mac(acc, nsh1, wc) : newton_update(acc, invg, nsh1, wc);
       }
       if (interior) W1[vi_own] = w1own;
@@ -597,10 +627,15 @@ k_newton2_tma(const __grid_constant__ NewtonMaps M, const StencilDev g, const Ne
         const T* Ct = reinterpret_cast<const T*>(cs);
         const P* Pt = reinterpret_cast<const P*>(cs + C::OFF_P);
         const T w1c = w1_m1;
-        const T acc = stencil7(Ct[6 * TT + ci], w1c, Ct[0 * TT + ci], V1[vi_own - 1],
-                               Ct[1 * TT + ci], V1[vi_own + 1], Ct[2 * TT + ci],
-                               V1[vi_own - C::W1X], Ct[3 * TT + ci], V1[vi_own + C::W1X],
-                               Ct[4 * TT + ci], w1_m2, Ct[5 * TT + ci], w1own);
+        T acc;
+        if constexpr (CONST)
+          acc = stencil7(ktab[6 + ocls + 16 * face_class(z, g.nz)], w1c, ktab[0],
+                         V1[vi_own - 1], ktab[1], V1[vi_own + 1], ktab[2], V1[vi_own - C::W1X],
+                         ktab[3], V1[vi_own + C::W1X], ktab[4], w1_m2, ktab[5], w1own);
+        else
+          acc = stencil7(Ct[6 * TT + ci], w1c, Ct[0 * TT + ci], V1[vi_own - 1], Ct[1 * TT + ci],
+                         V1[vi_own + 1], Ct[2 * TT + ci], V1[vi_own - C::W1X], Ct[3 * TT + ci],
+                         V1[vi_own + C::W1X], Ct[4 * TT + ci], w1_m2, Ct[5 * TT + ci], w1own);
         const T w2 = PRE ? mac(acc, nsh2, w1c) : newton_update(acc, invg, nsh2, w1c);
         const P pj = needp ? Pt[ci] : mul(d0, to_p(Wm[wi_own]));
         const P p1 = mac(pj, d1, to_p(w1c));
@@ -834,27 +869,32 @@ cudaError_t launch_newton_tma(const StencilDev& g, const NewtonMaps& M, void* w_
   return launch_one<VF_F32, false>(g, M, w_out, p, s, partials, ctl, st);
 }
 
-template <int FMT, bool PRE>
+template <int FMT, bool PRE, bool CONST = false>
 static cudaError_t launch_pair(const StencilDev& g, const NewtonMaps& M, void* w_out, void* p,
                                const NewtonScalars& s, double* partials, DevCtl* ctl,
-                               cudaStream_t st) {
-  using C = TmaCfg2<FMT>;
+                               cudaStream_t st, const void* ctab = nullptr) {
+  using C = TmaCfg2<FMT, CONST>;
   static bool attr = false;
   if (!attr) {
-    cudaError_t e = cudaFuncSetAttribute(k_newton2_tma<FMT, PRE>,
+    cudaError_t e = cudaFuncSetAttribute(k_newton2_tma<FMT, PRE, CONST>,
                                          cudaFuncAttributeMaxDynamicSharedMemorySize, C::SMEM);
     if (e != cudaSuccess) return e;
     attr = true;
   }
-  const int zc = tma_zchunk(g, sm_count() * 2, kHaloPair);  // two blocks per SM
+  // two blocks per SM (the table form too: three or four, which its shared
+  // memory allows, measured slower at the registers they leave)
+  const int zc = tma_zchunk(g, sm_count() * 2, kHaloPair);
   dim3 grid((g.nx + 31) / 32, (g.ny + 7) / 8, (g.nz + zc - 1) / zc), block(32, 8, 1);
-  k_newton2_tma<FMT, PRE><<<grid, block, C::SMEM, st>>>(M, g, s, w_out, p, partials, ctl, zc);
+  k_newton2_tma<FMT, PRE, CONST><<<grid, block, C::SMEM, st>>>(M, g, s, w_out, p, partials, ctl,
+                                                               zc, ctab);
   return cudaGetLastError();
 }
 
 cudaError_t launch_newton2_tma(const StencilDev& g, const NewtonMaps& M, void* w_out, void* p,
                                const NewtonScalars& s, int fmt, double* partials, DevCtl* ctl,
-                               cudaStream_t st, bool prescaled) {
+                               cudaStream_t st, bool prescaled, const void* ctab) {
+  if (fmt == VF_DF && prescaled && ctab)
+    return launch_pair<VF_DF, true, true>(g, M, w_out, p, s, partials, ctl, st, ctab);
   if (fmt == VF_DF && prescaled)
     return launch_pair<VF_DF, true>(g, M, w_out, p, s, partials, ctl, st);
   if (fmt == VF_DF) return launch_pair<VF_DF, false>(g, M, w_out, p, s, partials, ctl, st);
@@ -862,6 +902,31 @@ cudaError_t launch_newton2_tma(const StencilDev& g, const NewtonMaps& M, void* w
     return launch_pair<VF_F64, true>(g, M, w_out, p, s, partials, ctl, st);
   if (fmt == VF_F64) return launch_pair<VF_F64, false>(g, M, w_out, p, s, partials, ctl, st);
   return launch_pair<VF_F32, false>(g, M, w_out, p, s, partials, ctl, st);
+}
+
+// the constant operator's table: one thread an entry
+template <class T>
+__global__ void k_const_table(const __grid_constant__ ConstTabIdx ix, const T* a0, const T* a1,
+                              const T* a2, const T* a3, const T* a4, const T* a5, const T* dg,
+                              T* tab) {
+  const int t = threadIdx.x;
+  if (t >= kConstTab) return;
+  const T* src = t == 0 ? a0 : t == 1 ? a1 : t == 2 ? a2 : t == 3 ? a3 : t == 4 ? a4
+               : t == 5 ? a5 : dg;
+  st(tab, t, ix.idx[t] >= 0 ? ldg(src, ix.idx[t]) : zero<T>());
+}
+
+cudaError_t launch_const_table(const void* const sa[7], const ConstTabIdx& ix, void* ctab,
+                               int fmt, cudaStream_t st) {
+  if (fmt == VF_DF) {
+    k_const_table<df><<<1, 96, 0, st>>>(
+        ix, static_cast<const df*>(sa[0]), static_cast<const df*>(sa[1]),
+        static_cast<const df*>(sa[2]), static_cast<const df*>(sa[3]),
+        static_cast<const df*>(sa[4]), static_cast<const df*>(sa[5]),
+        static_cast<const df*>(sa[6]), static_cast<df*>(ctab));
+    return cudaGetLastError();
+  }
+  return cudaErrorInvalidValue;  // the table form runs in float-float only
 }
 
 cudaError_t launch_p_fixup(void* p, const void* w, int fmt, int64_t n, double d,

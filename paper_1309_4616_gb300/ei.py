@@ -52,7 +52,7 @@ class Stats(C.Structure):
                 ("newton_ms", C.c_double), ("learned", C.c_int), ("learned_s", C.c_int),
                 ("learned_m", C.c_int), ("learned_pad", C.c_int),
                 ("features", C.c_double * MLP_INPUTS), ("arith_used", C.c_int),
-                ("p_rechecks", C.c_int), ("newton_bounded", C.c_int), ("pad_end", C.c_int)]
+                ("p_rechecks", C.c_int), ("newton_bounded", C.c_int), ("coef_table", C.c_int)]
 
     def degree_list(self):
         return [int(self.degrees[i]) for i in range(min(self.s, STATS_MAX_SUBSTEPS))]
@@ -66,7 +66,7 @@ class Stats(C.Structure):
                 "newton_ms": self.newton_ms, "learned": self.learned,
                 "learned_s": self.learned_s, "learned_m": self.learned_m,
                 "arith_used": self.arith_used, "p_rechecks": self.p_rechecks,
-                "newton_bounded": self.newton_bounded}
+                "newton_bounded": self.newton_bounded, "coef_table": self.coef_table}
 
     def feature_list(self):
         return [float(self.features[i]) for i in range(MLP_INPUTS)]
