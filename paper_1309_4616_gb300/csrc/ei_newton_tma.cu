@@ -446,7 +446,7 @@ __device__ __forceinline__ int face_class(int x, int n) {
 }
 
 template <int FMT, bool PRE = false, bool CONST = false>
-__global__ void __launch_bounds__(256, 2)
+__global__ void __launch_bounds__(256, CONST ? 3 : 2)
 k_newton2_tma(const __grid_constant__ NewtonMaps M, const StencilDev g, const NewtonScalars s,
               void* __restrict__ w_out_, void* __restrict__ p_, double* partials, DevCtl* ctl,
               int zc_len, const void* __restrict__ ctab) {
@@ -535,14 +535,10 @@ k_newton2_tma(const __grid_constant__ NewtonMaps M, const StencilDev g, const Ne
   const bool hxy = hlx >= 0 && hx >= 0 && hx < g.nx && hy >= 0 && hy < g.ny;
   const int hcls = CONST && hxy ? face_class(hx, g.nx) + 4 * face_class(hy, g.ny) : 0;
   // halo coefficients come from global memory one step ahead of their use
-  // (CONST: from the table; an off-diagonal towards a neighbour outside the
-  // grid multiplies the zero that the w box holds there)
+  // (CONST: from the table where they are used; an off-diagonal towards a
+  // neighbour outside the grid multiplies the zero that the w box holds there)
   auto load_halo = [&](int zz, T* a) {
-    if (CONST && hxy && zz >= 0 && zz < g.nz) {
-#pragma unroll
-      for (int k = 0; k < 6; ++k) a[k] = ktab[k];
-      a[6] = ktab[6 + hcls + 16 * face_class(zz, g.nz)];
-    } else if (!CONST && hxy && zz >= 0 && zz < g.nz) {
+    if (hxy && zz >= 0 && zz < g.nz) {
       const int64_t gi = ((int64_t)zz * g.ny + hy) * g.pitch + hx;
 #pragma unroll
       for (int k = 0; k < 6; ++k) a[k] = ldg(static_cast<const T*>(g.a[k]), gi);
@@ -552,8 +548,8 @@ k_newton2_tma(const __grid_constant__ NewtonMaps M, const StencilDev g, const Ne
       for (int k = 0; k < 7; ++k) a[k] = zero<T>();
     }
   };
-  T hcur[7], hnxt[7];
-  load_halo(z0 - 1, hcur);
+  T hcur[CONST ? 1 : 7], hnxt[CONST ? 1 : 7];
+  if constexpr (!CONST) load_halo(z0 - 1, hcur);
   bool bad = false;
 
   // this thread's own w_{j+1} values on planes zc-2 and zc-1 (registers)
@@ -577,7 +573,9 @@ k_newton2_tma(const __grid_constant__ NewtonMaps M, const StencilDev g, const Ne
     }
     if (!bad) bad = !wait(m + 2);
     const int zc = z0 - 1 + m;
-    if (hlx >= 0) load_halo(zc + 1, hnxt);  // in flight while this step computes
+    if constexpr (!CONST) {
+      if (hlx >= 0) load_halo(zc + 1, hnxt);  // in flight while this step computes
+    }
     const int sw1 = (sw + 1 == C::NW) ? 0 : sw + 1, sw2 = (sw1 + 1 == C::NW) ? 0 : sw1 + 1;
     const int sc1 = (sc + 1 == C::NC) ? 0 : sc + 1;
     T w1own = zero<T>();
@@ -610,9 +608,15 @@ k_newton2_tma(const __grid_constant__ NewtonMaps M, const StencilDev g, const Ne
         if (zin && hxy) {
           const int wi = (hly + 1) * C::WJX + hlx + C::XH - 1;
           const T wc = Wc[wi];
-          const T acc = stencil7(hcur[6], wc, hcur[0], Wc[wi - 1], hcur[1], Wc[wi + 1], hcur[2],
-                                 Wc[wi - C::WJX], hcur[3], Wc[wi + C::WJX], hcur[4], Wm[wi],
-                                 hcur[5], Wp[wi]);
+          T acc;
+          if constexpr (CONST)
+            acc = stencil7(ktab[6 + hcls + 16 * face_class(zc, g.nz)], wc, ktab[0], Wc[wi - 1],
+                           ktab[1], Wc[wi + 1], ktab[2], Wc[wi - C::WJX], ktab[3],
+                           Wc[wi + C::WJX], ktab[4], Wm[wi], ktab[5], Wp[wi]);
+          else
+            acc = stencil7(hcur[6], wc, hcur[0], Wc[wi - 1], hcur[1], Wc[wi + 1], hcur[2],
+                           Wc[wi - C::WJX], hcur[3], Wc[wi + C::WJX], hcur[4], Wm[wi], hcur[5],
+                           Wp[wi]);
           w1 = PRE ? mac(acc, nsh1, wc) : newton_update(acc, invg, nsh1, wc);
         }
         W1[hly * C::W1X + hlx] = w1;
@@ -651,7 +655,7 @@ k_newton2_tma(const __grid_constant__ NewtonMaps M, const StencilDev g, const Ne
     }
     w1_m2 = w1_m1;
     w1_m1 = w1own;
-    if (hlx >= 0) {
+    if (!CONST && hlx >= 0) {
 #pragma unroll
       for (int k = 0; k < 7; ++k) hcur[k] = hnxt[k];
     }
@@ -881,9 +885,9 @@ static cudaError_t launch_pair(const StencilDev& g, const NewtonMaps& M, void* w
     if (e != cudaSuccess) return e;
     attr = true;
   }
-  // two blocks per SM (the table form too: three or four, which its shared
-  // memory allows, measured slower at the registers they leave)
-  const int zc = tma_zchunk(g, sm_count() * 2, kHaloPair);
+  // blocks per SM: two (shared memory for the coefficient tiles); the table
+  // form three (its registers)
+  const int zc = tma_zchunk(g, sm_count() * (CONST ? 3 : 2), kHaloPair);
   dim3 grid((g.nx + 31) / 32, (g.ny + 7) / 8, (g.nz + zc - 1) / zc), block(32, 8, 1);
   k_newton2_tma<FMT, PRE, CONST><<<grid, block, C::SMEM, st>>>(M, g, s, w_out, p, partials, ctl,
                                                                zc, ctab);
