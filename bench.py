@@ -70,8 +70,11 @@ PAIR_DRAM_BYTES_PER_POINT = 88.6
 # operator (a bracket step), from the same capture
 NATIVE_DRAM_BYTES_PER_POINT = 90.4
 # the float-float pair kernel on a constant operator's coefficient table (no
-# coefficient arrays), per point and launch: None until captured
-TABLE_PAIR_DRAM_BYTES_PER_POINT = None
+# coefficient arrays), per point and launch: ncu dram__bytes_read.sum +
+# dram__bytes_write.sum over the 49 working launches of the 256^3 combustion
+# step (profiles/k_newton2_tma_table_combustion_192cube.md; 28.6 B a launch
+# that reads p, 20.5 a loop's first, part of w and p staying in L2)
+TABLE_PAIR_DRAM_BYTES_PER_POINT = 27.8
 # DRAM bytes of one launch of the float-float sliced complex CSR kernel on the
 # 21-spin operator (profiles/k_csr_newton_sell_c_spin_bath_21.md)
 SPIN_DRAM_BYTES_PER_LAUNCH = 1.237e9
