@@ -62,13 +62,13 @@ FP64_FLOPS_PER_POINT_BOUNDED = 17
 SMS, FP64_FLOPS_PER_SM_CLK = 152, 4
 # DRAM bytes per grid point of one launch of the two-iteration float-float
 # kernel on the scaled operator, from ncu dram__bytes_read.sum +
-# dram__bytes_write.sum on 192^3 (profiles/dram_bytes_newton_kernels_192cube.md);
-# traffic scales with the points.
+# dram__bytes_write.sum over every working launch of the 256^3 bench step
+# (profiles/dram_bytes_newton_kernels_256cube.md).
 # Valid for the kernel as captured: retake it when the kernel changes.
-PAIR_DRAM_BYTES_PER_POINT = 88.6
+PAIR_DRAM_BYTES_PER_POINT = 87.6
 # the same for one launch of the native-FP64 one-iteration kernel on the scaled
 # operator (a bracket step), from the same capture
-NATIVE_DRAM_BYTES_PER_POINT = 90.4
+NATIVE_DRAM_BYTES_PER_POINT = 96.1
 # the float-float pair kernel on a constant operator's coefficient table (no
 # coefficient arrays), per point and launch: ncu dram__bytes_read.sum +
 # dram__bytes_write.sum over the 49 working launches of the 256^3 combustion
