@@ -192,7 +192,12 @@ ei_status ei_set_stream(ei_ctx* ctx, void* cuda_stream);
  * c        device array or NULL to use c_const (a fixed diagonal term).
  * bc       six face codes EI_BC_*.
  * prec     EI_PREC_F64 (arrays of double) or EI_PREC_F32 (arrays of float).
- * Allocates the library's workspaces (about 8 vectors of the grid size). */
+ * Allocates the library's workspaces (about 8 vectors of the grid size).
+ * With D, every b component and c given as constants (NULL arrays), the
+ * float-float Newton iterations on A (ei_phi_apply, exponential Euler) read
+ * the operator from a table of 70 coefficients instead of its coefficient
+ * arrays (ei_stats.coef_table); results agree with the array form to the
+ * format's rounding. */
 ei_status ei_set_operator_stencil(ei_ctx* ctx, int dim, const int64_t n[3], const double dx[3],
                                   const void* D, double D_const, const void* const b[3],
                                   const double b_const[3], const void* c, double c_const,
